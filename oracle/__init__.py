@@ -1,0 +1,281 @@
+"""Plain FP64 CPU oracle for the Alsvinn finite-volume hot path (arXiv:1912.07645).
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py``, never by the product package.
+It shares no code with the CUDA library; the C++ source is ``alsv_oracle.cpp`` (one cell at a
+time, FP64, ``-ffp-contract=off``), and this module only builds it and marshals numpy arrays.
+
+Every function here is a thin wrapper over the C++ entry point of the same name; the C++ file
+cites the passage of the paper (or the reading of it) that each computes.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "alsv_oracle.cpp")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+EQ = {"burgers": 0, "euler": 1}
+RECON = {"pc": 0, "mc": 1, "weno3": 2}
+RVARS = {"cons": 0, "prim": 1}
+FLUX = {"rusanov": 0, "hll": 1, "hllc": 2}
+RK = {"ssprk2": 2, "ssprk3": 3}
+BC = {"periodic": 0, "outflow": 1, "reflective": 2}
+INIT = {"kh": 0, "sod": 1, "lax": 2, "burgers_sine": 3, "vortex": 4}
+
+
+def build(force: bool = False) -> str:
+    """Compile ``liboracle.so`` with g++ (OpenMP when available). Returns the library path."""
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    base = ["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fPIC", "-shared", _SRC]
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    for extra in (["-fopenmp"], []):
+        r = subprocess.run(base + extra + ["-o", tmp], capture_output=True, text=True)
+        if r.returncode == 0:
+            os.replace(tmp, _LIB_PATH)
+            return _LIB_PATH
+    raise RuntimeError("oracle build failed:\n" + r.stderr)
+
+
+class Desc(C.Structure):
+    _fields_ = [
+        ("ndim", C.c_int32), ("n", C.c_int32 * 3), ("lo", C.c_double * 3), ("hi", C.c_double * 3),
+        ("eq", C.c_int32), ("gamma", C.c_double), ("recon", C.c_int32), ("rvars", C.c_int32),
+        ("flux", C.c_int32), ("rk", C.c_int32), ("bc", (C.c_int32 * 2) * 3), ("cfl", C.c_double),
+        ("weno_eps", C.c_double), ("weno_eps_dx2", C.c_int32),
+    ]
+
+
+def make_desc(ndim=1, n=(8, 1, 1), lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), eq="euler", gamma=1.4,
+              recon="mc", rvars="prim", flux="hllc", rk="ssprk2", bc="periodic", cfl=0.45,
+              weno_eps=1e-6, weno_eps_dx2=False, **_ignored) -> Desc:
+    """Build the oracle's descriptor from plain keyword values.
+
+    ``bc`` is a name for all sides, or a list of ``(lo, hi)`` names per direction.
+    """
+    d = Desc()
+    d.ndim = ndim
+    nn = list(n) + [1] * (3 - len(n))
+    for k in range(3):
+        d.n[k] = int(nn[k]) if k < ndim else 1
+        d.lo[k] = float(lo[k]) if k < len(lo) else 0.0
+        d.hi[k] = float(hi[k]) if k < len(hi) else 1.0
+    d.eq = EQ[eq]
+    d.gamma = gamma
+    d.recon = RECON[recon]
+    d.rvars = RVARS[rvars]
+    d.flux = FLUX[flux]
+    d.rk = RK[rk]
+    for k in range(3):
+        if isinstance(bc, str):
+            pair = (bc, bc)
+        else:
+            pair = bc[k] if k < len(bc) else ("periodic", "periodic")
+        d.bc[k][0] = BC[pair[0]]
+        d.bc[k][1] = BC[pair[1]]
+    d.cfl = cfl
+    d.weno_eps = weno_eps
+    d.weno_eps_dx2 = 1 if weno_eps_dx2 else 0
+    return d
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = build()
+            L = C.CDLL(path)
+            P = C.POINTER
+            dp = P(C.c_double)
+            i64p = P(C.c_int64)
+            dsc = P(Desc)
+            L.orc_num_threads.restype = C.c_int
+            L.orc_nvars.argtypes = [dsc]
+            L.orc_flux.argtypes = [dsc, C.c_int, dp, dp, dp]
+            L.orc_recon.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, dp, dp]
+            L.orc_cons_to_prim.argtypes = [dsc, dp, dp]
+            L.orc_prim_to_cons.argtypes = [dsc, dp, dp]
+            L.orc_rhs.argtypes = [dsc, C.c_int, dp, dp]
+            L.orc_max_speed.argtypes = [dsc, C.c_int, dp, dp]
+            L.orc_evolve.argtypes = [dsc, C.c_int, dp, C.c_double, C.c_double, C.c_int64, C.c_int64,
+                                     i64p, dp]
+            L.orc_evolve.restype = C.c_int
+            L.orc_theta.argtypes = [C.c_uint64, C.c_int, C.c_int, dp]
+            L.orc_splitmix64.argtypes = [C.c_uint64]
+            L.orc_splitmix64.restype = C.c_uint64
+            L.orc_init.argtypes = [dsc, C.c_int, C.c_int, dp, C.c_int, C.c_double, C.c_double, dp]
+            L.orc_init.restype = C.c_int
+            L.orc_welford.argtypes = [dsc, C.c_int, dp, i64p, dp, dp]
+            L.orc_totals.argtypes = [dsc, C.c_int, dp, dp]
+            L.orc_kinetic_energy.argtypes = [dsc, C.c_int, dp, dp]
+            L.orc_ke_grad_kh2d.argtypes = [dsc, dp, C.c_double, C.c_int64, dp, dp]
+            L.orc_ke_grad_kh2d.restype = C.c_int
+            L.orc_ke_dir_kh2d.argtypes = [dsc, dp, dp, C.c_double, C.c_int64, dp, dp]
+            L.orc_ke_dir_kh2d.restype = C.c_int
+            _lib = L
+    return _lib
+
+
+def _dp(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def num_threads() -> int:
+    return int(lib().orc_num_threads())
+
+
+def nvars(d: Desc) -> int:
+    return int(lib().orc_nvars(C.byref(d)))
+
+
+def state_shape(d: Desc, B: int):
+    return (B, nvars(d), d.n[2], d.n[1], d.n[0])
+
+
+def flux(d: Desc, k: int, WL, WR) -> np.ndarray:
+    WL, WR = _f64(WL), _f64(WR)
+    F = np.zeros(nvars(d))
+    lib().orc_flux(C.byref(d), k, _dp(WL), _dp(WR), _dp(F))
+    return F
+
+
+def recon(kind: str, wm: float, w0: float, wp: float, eps: float = 1e-6):
+    fl, fr = C.c_double(), C.c_double()
+    lib().orc_recon(RECON[kind], eps, wm, w0, wp, C.byref(fl), C.byref(fr))
+    return fl.value, fr.value
+
+
+def cons_to_prim(d: Desc, U) -> np.ndarray:
+    U = _f64(U)
+    W = np.zeros_like(U)
+    lib().orc_cons_to_prim(C.byref(d), _dp(U), _dp(W))
+    return W
+
+
+def prim_to_cons(d: Desc, W) -> np.ndarray:
+    W = _f64(W)
+    U = np.zeros_like(W)
+    lib().orc_prim_to_cons(C.byref(d), _dp(W), _dp(U))
+    return U
+
+
+def rhs(d: Desc, U) -> np.ndarray:
+    U = _f64(U)
+    L = np.zeros_like(U)
+    lib().orc_rhs(C.byref(d), U.shape[0], _dp(U), _dp(L))
+    return L
+
+
+def max_speed(d: Desc, U) -> np.ndarray:
+    U = _f64(U)
+    s = np.zeros(U.shape[0])
+    lib().orc_max_speed(C.byref(d), U.shape[0], _dp(U), _dp(s))
+    return s
+
+
+def evolve(d: Desc, U, T: float = 0.0, fixed_dt: float = 0.0, n_steps: int = 0, max_steps: int = 0):
+    """Advance a copy of U ([B, nv, nz, ny, nx]); returns (U_new, steps[B], t[B])."""
+    U = _f64(U).copy()
+    B = U.shape[0]
+    steps = np.zeros(B, dtype=np.int64)
+    t = np.zeros(B)
+    st = lib().orc_evolve(C.byref(d), B, _dp(U), T, fixed_dt, n_steps, max_steps,
+                          steps.ctypes.data_as(C.POINTER(C.c_int64)), _dp(t))
+    if st != 0:
+        raise FloatingPointError(f"oracle evolve: non-physical state (status {st})")
+    return U, steps, t
+
+
+def theta_splitmix(seed: int, B: int, P: int) -> np.ndarray:
+    th = np.zeros((B, P))
+    lib().orc_theta(C.c_uint64(seed & 0xFFFFFFFFFFFFFFFF), B, P, _dp(th))
+    return th
+
+
+def splitmix64(x: int) -> int:
+    return int(lib().orc_splitmix64(C.c_uint64(x & 0xFFFFFFFFFFFFFFFF)))
+
+
+def init(d: Desc, kind: str, B: int = 1, theta=None, center=(5.0, 5.0)) -> np.ndarray:
+    U = np.zeros(state_shape(d, B))
+    if theta is None:
+        th = np.zeros((B, 1))
+    else:
+        th = _f64(theta).reshape(B, -1)
+    st = lib().orc_init(C.byref(d), INIT[kind], B, _dp(th), th.shape[1], center[0], center[1], _dp(U))
+    if st != 0:
+        raise ValueError(f"oracle init {kind}: invalid for this descriptor")
+    return U
+
+
+def welford(d: Desc, U, count: int = 0, mean=None, M2=None):
+    """Fold B samples into (count, mean[q, cells], M2[q, cells]); returns the updated triple."""
+    U = _f64(U)
+    B = U.shape[0]
+    nq = nvars(d)
+    cells = d.n[0] * d.n[1] * d.n[2]
+    mean = np.zeros((nq, cells)) if mean is None else _f64(mean).copy()
+    M2 = np.zeros((nq, cells)) if M2 is None else _f64(M2).copy()
+    cnt = C.c_int64(count)
+    lib().orc_welford(C.byref(d), B, _dp(U), C.byref(cnt), _dp(mean), _dp(M2))
+    return cnt.value, mean, M2
+
+
+def totals(d: Desc, U) -> np.ndarray:
+    U = _f64(U)
+    out = np.zeros((U.shape[0], nvars(d)))
+    lib().orc_totals(C.byref(d), U.shape[0], _dp(U), _dp(out))
+    return out
+
+
+def kinetic_energy(d: Desc, U) -> np.ndarray:
+    U = _f64(U)
+    out = np.zeros(U.shape[0])
+    lib().orc_kinetic_energy(C.byref(d), U.shape[0], _dp(U), _dp(out))
+    return out
+
+
+def ke_grad_kh2d(d: Desc, theta, dt: float, n_steps: int):
+    """(J, dJ/dtheta[20]) of one 2D KH sample after n fixed steps, by forward-mode duals."""
+    th = _f64(theta).reshape(20)
+    J = C.c_double()
+    g = np.zeros(20)
+    st = lib().orc_ke_grad_kh2d(C.byref(d), _dp(th), dt, n_steps, C.byref(J), _dp(g))
+    if st != 0:
+        raise ValueError("ke_grad_kh2d needs a 2D Euler descriptor")
+    return J.value, g
+
+
+def ke_dir_kh2d(d: Desc, theta, vdir, dt: float, n_steps: int):
+    th = _f64(theta).reshape(20)
+    v = _f64(vdir).reshape(20)
+    J, dJ = C.c_double(), C.c_double()
+    st = lib().orc_ke_dir_kh2d(C.byref(d), _dp(th), _dp(v), dt, n_steps, C.byref(J), C.byref(dJ))
+    if st != 0:
+        raise ValueError("ke_dir_kh2d needs a 2D Euler descriptor")
+    return J.value, dJ.value
+
+
+def fixed_dt_kh(n: int, T: float, cfl: float, gamma: float = 1.4, length: float = 1.0):
+    """Fixed step for the adjoint (reading): s_max from the two unperturbed KH states,
+    n_steps = ceil(T s_max / (cfl dx)), dt = T / n_steps."""
+    import math
+    s_max = 0.5 + math.sqrt(gamma * 2.5 / 1.0)
+    dxh = length / n
+    n_steps = int(math.ceil(T * s_max / (cfl * dxh)))
+    return T / n_steps, n_steps

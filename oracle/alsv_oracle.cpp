@@ -1,0 +1,792 @@
+// Plain FP64 CPU oracle for the finite-volume hot path of Alsvinn (arXiv:1912.07645).
+//
+// TEST INFRASTRUCTURE ONLY. Nothing in the product library links, includes or calls this file;
+// only tests/, __graft_entry__.smoke() and bench.py's cpu_baseline / --impl reference legs load it.
+// It shares no code, header, table or constant generator with the CUDA path.
+//
+// What it computes (each function cites the passage it follows):
+//   * eq. (1.1), Sec. 1: u_t + div F(u) = 0 for the compressible Euler equations (ideal gas) and,
+//     as the scalar case, multi-dimensional Burgers u_t + sum_k (u^2/2)_{x_k} = 0.
+//   * eq. (2.1), Sec. 2.1: the semi-discrete update d/dt u_i = -sum_k (F_{i+e_k/2} - F_{i-e_k/2})/dx_k,
+//     with one dx per direction (the paper prints a single Delta).
+//   * Sec. 2.1 names the components: HLLC, Rusanov numerical fluxes (plus HLL, the HLLC family
+//     without the contact wave), SSP Runge-Kutta time stepping (Gottlieb-Shu-Tadmor), WENO
+//     reconstruction (Shu 1999) and, as simpler reconstructions, piecewise constant and the
+//     MC-limited linear one.
+//   * Sec. 2.2: the Monte Carlo estimator of mean and variance per cell (Welford, samples in
+//     ascending order).
+//   * Sec. 3: Kelvin-Helmholtz shear-flow initial data (two states, perturbed interfaces).
+// Readings where the paper is silent (wave speeds, CFL rule, HLLC form, WENO3 epsilon, KH
+// perturbation, positivity fallback, boundary ghosts, RNG) are listed beside each function.
+//
+// Style: one cell at a time, directions summed in the order x, y, z, every interface flux
+// recomputed for each adjacent cell, no tiling, no fusion. Compiled with -O2 -ffp-contract=off.
+//
+// The scalar type is a template parameter so the same code runs on double and on forward-mode
+// dual numbers; the dual run gives the exact derivative of the discrete map (active branch at
+// kinks), which is the oracle for the discrete adjoint.
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace orc {
+
+// ------------------------------------------------------------------------------------------
+// Enumerations (values are part of the oracle's own ctypes interface)
+// ------------------------------------------------------------------------------------------
+enum { EQ_BURGERS = 0, EQ_EULER = 1 };
+enum { REC_PC = 0, REC_MC = 1, REC_WENO3 = 2 };
+enum { RV_CONS = 0, RV_PRIM = 1 };
+enum { FLUX_RUSANOV = 0, FLUX_HLL = 1, FLUX_HLLC = 2 };
+enum { RK_SSP2 = 2, RK_SSP3 = 3 };
+enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_REFLECTIVE = 2 };
+enum { INIT_KH = 0, INIT_SOD = 1, INIT_LAX = 2, INIT_BURGERS_SINE = 3, INIT_VORTEX = 4 };
+
+struct Desc {
+    int32_t ndim;
+    int32_t n[3];
+    double lo[3];
+    double hi[3];
+    int32_t eq;
+    double gamma;
+    int32_t recon;
+    int32_t rvars;
+    int32_t flux;
+    int32_t rk;
+    int32_t bc[3][2];
+    double cfl;
+    double weno_eps;      // used when weno_eps_dx2 == 0
+    int32_t weno_eps_dx2; // 1: epsilon = dx_k^2 per direction
+};
+
+// ------------------------------------------------------------------------------------------
+// Forward-mode dual numbers. Derivatives of max/min/abs/clamp follow the branch taken.
+// ------------------------------------------------------------------------------------------
+template <int N> struct Dual {
+    double v;
+    double d[N];
+    Dual() : v(0.0) { for (int i = 0; i < N; ++i) d[i] = 0.0; }
+    Dual(double x) : v(x) { for (int i = 0; i < N; ++i) d[i] = 0.0; }
+};
+template <int N> inline Dual<N> operator+(const Dual<N>& a, const Dual<N>& b) {
+    Dual<N> r; r.v = a.v + b.v; for (int i = 0; i < N; ++i) r.d[i] = a.d[i] + b.d[i]; return r;
+}
+template <int N> inline Dual<N> operator-(const Dual<N>& a, const Dual<N>& b) {
+    Dual<N> r; r.v = a.v - b.v; for (int i = 0; i < N; ++i) r.d[i] = a.d[i] - b.d[i]; return r;
+}
+template <int N> inline Dual<N> operator-(const Dual<N>& a) {
+    Dual<N> r; r.v = -a.v; for (int i = 0; i < N; ++i) r.d[i] = -a.d[i]; return r;
+}
+template <int N> inline Dual<N> operator*(const Dual<N>& a, const Dual<N>& b) {
+    Dual<N> r; r.v = a.v * b.v; for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * b.v + a.v * b.d[i]; return r;
+}
+template <int N> inline Dual<N> operator/(const Dual<N>& a, const Dual<N>& b) {
+    Dual<N> r; r.v = a.v / b.v;
+    for (int i = 0; i < N; ++i) r.d[i] = (a.d[i] * b.v - a.v * b.d[i]) / (b.v * b.v);
+    return r;
+}
+template <int N> inline Dual<N> operator+(const Dual<N>& a, double b) { return a + Dual<N>(b); }
+template <int N> inline Dual<N> operator+(double a, const Dual<N>& b) { return Dual<N>(a) + b; }
+template <int N> inline Dual<N> operator-(const Dual<N>& a, double b) { return a - Dual<N>(b); }
+template <int N> inline Dual<N> operator-(double a, const Dual<N>& b) { return Dual<N>(a) - b; }
+template <int N> inline Dual<N> operator*(const Dual<N>& a, double b) { return a * Dual<N>(b); }
+template <int N> inline Dual<N> operator*(double a, const Dual<N>& b) { return Dual<N>(a) * b; }
+template <int N> inline Dual<N> operator/(const Dual<N>& a, double b) { return a / Dual<N>(b); }
+template <int N> inline Dual<N> operator/(double a, const Dual<N>& b) { return Dual<N>(a) / b; }
+template <int N> inline Dual<N> sqrt(const Dual<N>& a) {
+    Dual<N> r; r.v = std::sqrt(a.v);
+    for (int i = 0; i < N; ++i) r.d[i] = a.d[i] / (2.0 * r.v);
+    return r;
+}
+template <int N> inline Dual<N> sin(const Dual<N>& a) {
+    Dual<N> r; r.v = std::sin(a.v); double c = std::cos(a.v);
+    for (int i = 0; i < N; ++i) r.d[i] = c * a.d[i];
+    return r;
+}
+
+inline double val(double x) { return x; }
+template <int N> inline double val(const Dual<N>& x) { return x.v; }
+inline double sqrt_(double x) { return std::sqrt(x); }
+template <int N> inline Dual<N> sqrt_(const Dual<N>& x) { return sqrt(x); }
+inline double sin_(double x) { return std::sin(x); }
+template <int N> inline Dual<N> sin_(const Dual<N>& x) { return sin(x); }
+template <class T> inline T abs_(const T& x) { return val(x) < 0.0 ? T(-x) : x; }
+// ties pick the first argument
+template <class T> inline T max_(const T& a, const T& b) { return val(b) > val(a) ? b : a; }
+template <class T> inline T min_(const T& a, const T& b) { return val(b) < val(a) ? b : a; }
+
+// ------------------------------------------------------------------------------------------
+// Grid geometry and ghost cells
+// ------------------------------------------------------------------------------------------
+inline int nvars(const Desc& d) { return d.eq == EQ_BURGERS ? 1 : d.ndim + 2; }
+inline double dx(const Desc& d, int k) { return (d.hi[k] - d.lo[k]) / d.n[k]; }
+inline int64_t ncells(const Desc& d) { return (int64_t)d.n[0] * d.n[1] * d.n[2]; }
+inline int64_t lin(const Desc& d, int v, int x, int y, int z) {
+    return (((int64_t)v * d.n[2] + z) * d.n[1] + y) * d.n[0] + x;
+}
+
+// Boundary reading (paper silent): periodic wraps; outflow copies the nearest interior cell;
+// reflective mirrors interior cell -1-j for ghost j and negates the velocity normal to the wall.
+// Returns the interior index and sets *flip when the mirrored value must be negated.
+inline int ghost_map(int i, int n, int bc_lo, int bc_hi, bool* flip) {
+    *flip = false;
+    if (i < 0) {
+        if (bc_lo == BC_PERIODIC) return ((i % n) + n) % n;
+        if (bc_lo == BC_OUTFLOW) return 0;
+        *flip = true;
+        return -1 - i;
+    }
+    if (i >= n) {
+        if (bc_hi == BC_PERIODIC) return i % n;
+        if (bc_hi == BC_OUTFLOW) return n - 1;
+        *flip = true;
+        return 2 * n - 1 - i;
+    }
+    return i;
+}
+
+// Conserved state of the cell at position c (x,y,z) shifted to index i along direction k.
+template <class T>
+inline void cell_cons(const Desc& d, const T* U, const int c[3], int k, int i, T* out) {
+    int p[3] = {c[0], c[1], c[2]};
+    bool flip;
+    p[k] = ghost_map(i, d.n[k], d.bc[k][0], d.bc[k][1], &flip);
+    int nv = nvars(d);
+    for (int v = 0; v < nv; ++v) out[v] = U[lin(d, v, p[0], p[1], p[2])];
+    if (flip) {
+        if (d.eq == EQ_BURGERS) out[0] = -out[0];
+        else out[1 + k] = -out[1 + k];
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Ideal-gas Euler relations: p = (gamma-1)(E - |m|^2/(2 rho)), E = p/(gamma-1) + rho|u|^2/2
+// ------------------------------------------------------------------------------------------
+// prim layout: [rho, u_0..u_{ndim-1}, p]
+template <class T> inline void cons_to_prim(const Desc& d, const T* U, T* W) {
+    int nd = d.ndim;
+    T rho = U[0];
+    T m2 = T(0.0);
+    for (int k = 0; k < nd; ++k) m2 = m2 + U[1 + k] * U[1 + k];
+    W[0] = rho;
+    for (int k = 0; k < nd; ++k) W[1 + k] = U[1 + k] / rho;
+    W[1 + nd] = (d.gamma - 1.0) * (U[1 + nd] - 0.5 * m2 / rho);
+}
+template <class T> inline void prim_to_cons(const Desc& d, const T* W, T* U) {
+    int nd = d.ndim;
+    T rho = W[0];
+    T u2 = T(0.0);
+    for (int k = 0; k < nd; ++k) u2 = u2 + W[1 + k] * W[1 + k];
+    U[0] = rho;
+    for (int k = 0; k < nd; ++k) U[1 + k] = rho * W[1 + k];
+    U[1 + nd] = W[1 + nd] / (d.gamma - 1.0) + 0.5 * rho * u2;
+}
+
+// ------------------------------------------------------------------------------------------
+// Reconstruction of one cell's two face values from (w_{i-1}, w_i, w_{i+1}) along a direction
+// (Sec. 2.1 names ENO/WENO after Shu 1999). fl = value at i-1/2, fr = value at i+1/2.
+// ------------------------------------------------------------------------------------------
+// minmod of three: the common-sign minimum magnitude, 0 if signs differ or any is 0.
+template <class T> inline T minmod3(const T& a, const T& b, const T& c) {
+    if (val(a) > 0.0 && val(b) > 0.0 && val(c) > 0.0) return min_(min_(a, b), c);
+    if (val(a) < 0.0 && val(b) < 0.0 && val(c) < 0.0) return max_(max_(a, b), c);
+    return T(0.0);
+}
+
+template <class T>
+inline void recon_scalar(int recon, double eps, const T& wm, const T& w0, const T& wp, T* fl, T* fr) {
+    if (recon == REC_PC) {
+        *fl = w0;
+        *fr = w0;
+    } else if (recon == REC_MC) {
+        // monotonized-central slope: minmod(2 D-, (D- + D+)/2, 2 D+)
+        T dm = w0 - wm;
+        T dp = wp - w0;
+        T s = minmod3(T(2.0 * dm), T(0.5 * (dm + dp)), T(2.0 * dp));
+        *fl = w0 - 0.5 * s;
+        *fr = w0 + 0.5 * s;
+    } else {
+        // Jiang-Shu WENO3: candidates on {i-1,i} and {i,i+1}, linear weights 1/3, 2/3,
+        // smoothness (differences)^2, alpha_r = d_r / (eps + beta_r)^2.
+        const double d0 = 1.0 / 3.0, d1 = 2.0 / 3.0;
+        {   // face i+1/2
+            T p0 = -0.5 * wm + 1.5 * w0;
+            T p1 = 0.5 * w0 + 0.5 * wp;
+            T b0 = (w0 - wm) * (w0 - wm);
+            T b1 = (wp - w0) * (wp - w0);
+            T a0 = d0 / ((eps + b0) * (eps + b0));
+            T a1 = d1 / ((eps + b1) * (eps + b1));
+            *fr = (a0 * p0 + a1 * p1) / (a0 + a1);
+        }
+        {   // face i-1/2 (mirror image)
+            T p0 = -0.5 * wp + 1.5 * w0;
+            T p1 = 0.5 * w0 + 0.5 * wm;
+            T b0 = (wp - w0) * (wp - w0);
+            T b1 = (w0 - wm) * (w0 - wm);
+            T a0 = d0 / ((eps + b0) * (eps + b0));
+            T a1 = d1 / ((eps + b1) * (eps + b1));
+            *fl = (a0 * p0 + a1 * p1) / (a0 + a1);
+        }
+    }
+}
+
+// Face states of the cell at c shifted to index i along k, returned as PRIMITIVE variables
+// (Burgers: the scalar u). Reconstruction is done on conserved or primitive variables per
+// d.rvars. Positivity reading: a face state whose density or pressure is not positive reverts
+// to the cell's own value in all variables (first order at that face only).
+template <class T>
+void cell_faces(const Desc& d, const T* U, const int c[3], int k, int i, T* Wl, T* Wr) {
+    const int nv = nvars(d);
+    T Um[8], U0[8], Up[8];
+    cell_cons(d, U, c, k, i - 1, Um);
+    cell_cons(d, U, c, k, i, U0);
+    cell_cons(d, U, c, k, i + 1, Up);
+    double eps = d.weno_eps_dx2 ? dx(d, k) * dx(d, k) : d.weno_eps;
+    if (d.eq == EQ_BURGERS) {
+        recon_scalar(d.recon, eps, Um[0], U0[0], Up[0], &Wl[0], &Wr[0]);
+        return;
+    }
+    T wm[8], w0[8], wp[8], fl[8], fr[8];
+    if (d.rvars == RV_PRIM) {
+        cons_to_prim(d, Um, wm);
+        cons_to_prim(d, U0, w0);
+        cons_to_prim(d, Up, wp);
+    } else {
+        for (int v = 0; v < nv; ++v) { wm[v] = Um[v]; w0[v] = U0[v]; wp[v] = Up[v]; }
+    }
+    for (int v = 0; v < nv; ++v) recon_scalar(d.recon, eps, wm[v], w0[v], wp[v], &fl[v], &fr[v]);
+    T Wc[8];
+    if (d.rvars == RV_PRIM) {
+        for (int v = 0; v < nv; ++v) { Wl[v] = fl[v]; Wr[v] = fr[v]; Wc[v] = w0[v]; }
+    } else {
+        cons_to_prim(d, fl, Wl);
+        cons_to_prim(d, fr, Wr);
+        cons_to_prim(d, U0, Wc);
+    }
+    const int ip = d.ndim + 1;
+    if (!(val(Wl[0]) > 0.0 && val(Wl[ip]) > 0.0))
+        for (int v = 0; v < nv; ++v) Wl[v] = Wc[v];
+    if (!(val(Wr[0]) > 0.0 && val(Wr[ip]) > 0.0))
+        for (int v = 0; v < nv; ++v) Wr[v] = Wc[v];
+}
+
+// ------------------------------------------------------------------------------------------
+// Numerical fluxes (Sec. 2.1 names HLLC and Rusanov). Inputs are primitive states; k is the
+// sweep direction; output is the conserved flux vector.
+// Wave-speed reading (Davis): S_L = min(u_L - c_L, u_R - c_R), S_R = max(u_L + c_L, u_R + c_R);
+// Rusanov a = max(|u_L| + c_L, |u_R| + c_R); c = sqrt(gamma p / rho).
+// ------------------------------------------------------------------------------------------
+template <class T> inline void euler_phys_flux(const Desc& d, const T* W, int k, T* F) {
+    int nd = d.ndim;
+    T U[8];
+    prim_to_cons(d, W, U);
+    T un = W[1 + k];
+    T p = W[1 + nd];
+    F[0] = U[0] * un;
+    for (int j = 0; j < nd; ++j) F[1 + j] = U[1 + j] * un;
+    F[1 + k] = F[1 + k] + p;
+    F[1 + nd] = un * (U[1 + nd] + p);
+}
+
+template <class T> void flux(const Desc& d, int k, const T* WL, const T* WR, T* F) {
+    const int nv = nvars(d);
+    if (d.eq == EQ_BURGERS) {
+        T uL = WL[0], uR = WR[0];
+        T fL = 0.5 * uL * uL, fR = 0.5 * uR * uR;
+        if (d.flux == FLUX_RUSANOV) {
+            T a = max_(abs_(uL), abs_(uR));
+            F[0] = 0.5 * (fL + fR) - 0.5 * a * (uR - uL);
+        } else {  // HLL; for a scalar law HLLC coincides with HLL
+            T SL = min_(uL, uR), SR = max_(uL, uR);
+            if (val(SL) >= 0.0) F[0] = fL;
+            else if (val(SR) <= 0.0) F[0] = fR;
+            else F[0] = (SR * fL - SL * fR + SL * SR * (uR - uL)) / (SR - SL);
+        }
+        return;
+    }
+    const int nd = d.ndim;
+    const int ip = nd + 1;
+    T UL[8], UR[8], FL[8], FR[8];
+    prim_to_cons(d, WL, UL);
+    prim_to_cons(d, WR, UR);
+    euler_phys_flux(d, WL, k, FL);
+    euler_phys_flux(d, WR, k, FR);
+    T rL = WL[0], rR = WR[0], uL = WL[1 + k], uR = WR[1 + k], pL = WL[ip], pR = WR[ip];
+    T cL = sqrt_(d.gamma * pL / rL);
+    T cR = sqrt_(d.gamma * pR / rR);
+    if (d.flux == FLUX_RUSANOV) {
+        T a = max_(T(abs_(uL) + cL), T(abs_(uR) + cR));
+        for (int v = 0; v < nv; ++v) F[v] = 0.5 * (FL[v] + FR[v]) - 0.5 * a * (UR[v] - UL[v]);
+        return;
+    }
+    T SL = min_(T(uL - cL), T(uR - cR));
+    T SR = max_(T(uL + cL), T(uR + cR));
+    if (d.flux == FLUX_HLL) {
+        if (val(SL) >= 0.0) { for (int v = 0; v < nv; ++v) F[v] = FL[v]; }
+        else if (val(SR) <= 0.0) { for (int v = 0; v < nv; ++v) F[v] = FR[v]; }
+        else {
+            for (int v = 0; v < nv; ++v)
+                F[v] = (SR * FL[v] - SL * FR[v] + SL * SR * (UR[v] - UL[v])) / (SR - SL);
+        }
+        return;
+    }
+    // HLLC (Toro-Spruce-Speares) with the contact speed S* and star states U*_K. Cases in order:
+    // F_L if 0 <= S_L; F*_L if S_L < 0 <= S*; F*_R if S* < 0 < S_R; F_R otherwise.
+    if (val(SL) >= 0.0) { for (int v = 0; v < nv; ++v) F[v] = FL[v]; return; }
+    T Ss = (pR - pL + rL * uL * (SL - uL) - rR * uR * (SR - uR)) / (rL * (SL - uL) - rR * (SR - uR));
+    const bool left = val(Ss) >= 0.0;
+    if (!left && !(val(SR) > 0.0)) { for (int v = 0; v < nv; ++v) F[v] = FR[v]; return; }
+    const T* WK = left ? WL : WR;
+    const T* UK = left ? UL : UR;
+    const T* FK = left ? FL : FR;
+    T SK = left ? SL : SR;
+    T rK = WK[0], uK = WK[1 + k], pK = WK[ip];
+    T fac = rK * (SK - uK) / (SK - Ss);
+    T Us[8];
+    Us[0] = fac;
+    for (int j = 0; j < nd; ++j) Us[1 + j] = fac * WK[1 + j];
+    Us[1 + k] = fac * Ss;
+    Us[ip] = fac * (UK[ip] / rK + (Ss - uK) * (Ss + pK / (rK * (SK - uK))));
+    for (int v = 0; v < nv; ++v) F[v] = FK[v] + SK * (Us[v] - UK[v]);
+}
+
+// Flux through the interface i+1/2 (between cell i and i+1) along k at cell position c.
+template <class T> void interface_flux(const Desc& d, const T* U, const int c[3], int k, int i, T* F) {
+    T Wl_i[8], Wr_i[8], Wl_j[8], Wr_j[8];
+    cell_faces(d, U, c, k, i, Wl_i, Wr_i);
+    cell_faces(d, U, c, k, i + 1, Wl_j, Wr_j);
+    flux(d, k, Wr_i, Wl_j, F);
+}
+
+// ------------------------------------------------------------------------------------------
+// eq. (2.1): L(U)_i = -sum_k (F_{i+1/2 e_k} - F_{i-1/2 e_k}) / dx_k, directions in order x,y,z.
+// ------------------------------------------------------------------------------------------
+template <class T> void rhs(const Desc& d, const T* U, T* L) {
+    const int nv = nvars(d);
+    const int nx = d.n[0], ny = d.n[1], nz = d.n[2];
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                int c[3] = {x, y, z};
+                T acc[8];
+                for (int v = 0; v < nv; ++v) acc[v] = T(0.0);
+                for (int k = 0; k < d.ndim; ++k) {
+                    T Fm[8], Fp[8];
+                    interface_flux(d, U, c, k, c[k] - 1, Fm);
+                    interface_flux(d, U, c, k, c[k], Fp);
+                    double h = dx(d, k);
+                    for (int v = 0; v < nv; ++v) acc[v] = acc[v] - (Fp[v] - Fm[v]) / h;
+                }
+                for (int v = 0; v < nv; ++v) L[lin(d, v, x, y, z)] = acc[v];
+            }
+}
+
+// ------------------------------------------------------------------------------------------
+// SSP Runge-Kutta (Gottlieb-Shu-Tadmor), Sec. 2.1:
+//   RK2: U1 = U + dt L(U);  U^{n+1} = 1/2 U + 1/2 (U1 + dt L(U1))
+//   RK3: U1 = U + dt L(U);  U2 = 3/4 U + 1/4 (U1 + dt L(U1));  U^{n+1} = 1/3 U + 2/3 (U2 + dt L(U2))
+// ------------------------------------------------------------------------------------------
+template <class T> void rk_step(const Desc& d, T* U, T dt) {
+    const int64_t N = (int64_t)nvars(d) * ncells(d);
+    std::vector<T> L(N), U1(N), U2(N);
+    rhs(d, U, L.data());
+    for (int64_t q = 0; q < N; ++q) U1[q] = U[q] + dt * L[q];
+    rhs(d, U1.data(), L.data());
+    if (d.rk == RK_SSP2) {
+        for (int64_t q = 0; q < N; ++q) U[q] = 0.5 * U[q] + 0.5 * (U1[q] + dt * L[q]);
+        return;
+    }
+    for (int64_t q = 0; q < N; ++q) U2[q] = 0.75 * U[q] + 0.25 * (U1[q] + dt * L[q]);
+    rhs(d, U2.data(), L.data());
+    const double third = 1.0 / 3.0, two_third = 2.0 / 3.0;
+    for (int64_t q = 0; q < N; ++q) U[q] = third * U[q] + two_third * (U2[q] + dt * L[q]);
+}
+
+// CFL reading: s = max over cells and directions of (|u_k| + c)/dx_k (Burgers: |u|/dx_k).
+// Returns NaN if a cell is non-physical (rho <= 0 or p <= 0) or non-finite.
+double max_speed(const Desc& d, const double* U) {
+    const int nv = nvars(d);
+    double s = 0.0;
+    bool bad = false;
+    for (int z = 0; z < d.n[2]; ++z)
+        for (int y = 0; y < d.n[1]; ++y)
+            for (int x = 0; x < d.n[0]; ++x) {
+                double Uc[8], W[8];
+                for (int v = 0; v < nv; ++v) Uc[v] = U[lin(d, v, x, y, z)];
+                if (d.eq == EQ_BURGERS) {
+                    if (!std::isfinite(Uc[0])) bad = true;
+                    for (int k = 0; k < d.ndim; ++k) s = std::max(s, std::fabs(Uc[0]) / dx(d, k));
+                    continue;
+                }
+                cons_to_prim(d, Uc, W);
+                double rho = W[0], p = W[d.ndim + 1];
+                if (!(rho > 0.0 && p > 0.0) || !std::isfinite(rho) || !std::isfinite(p)) { bad = true; continue; }
+                double c = std::sqrt(d.gamma * p / rho);
+                for (int k = 0; k < d.ndim; ++k) s = std::max(s, (std::fabs(W[1 + k]) + c) / dx(d, k));
+            }
+    return bad ? NAN : s;
+}
+
+// ------------------------------------------------------------------------------------------
+// Initial data. Cell values are cell averages of conserved variables.
+// ------------------------------------------------------------------------------------------
+// Kelvin-Helmholtz (Sec. 3 defers to Fjordholm-Kappeli-Mishra-Tadmor; reading):
+//   2D: inner band (rho=2, u=-0.5) between y = 0.25 + Y(x) and y = 0.75 + Y(x), outer rho=1,
+//   u=0.5, v=0, p=2.5; Y(x) = 0.01 sum_{n=1}^{10} a_n sin(2 pi n x + b_n), theta = [a_1..a_10,
+//   b_1..b_10]. The cell value blends the two states in conserved variables by the fraction of
+//   the cell (in y, interfaces evaluated at the cell-centre x) that lies inside the band.
+//   3D slab: the same in (x,z) with Y(x,z) = 0.01 sum_{n,m=1}^{8} a_nm sin(2 pi (n x + m z) + b_nm),
+//   theta = [a (n-major, 64), b (64)], momentum along x, v = w = 0.
+template <class T> inline T clamp01(const T& x) {
+    if (val(x) < 0.0) return T(0.0);
+    if (val(x) > 1.0) return T(1.0);
+    return x;
+}
+
+template <class T> void init_kh(const Desc& d, const T* theta, T* U) {
+    const double PI = 3.14159265358979323846;
+    const int nd = d.ndim;
+    double Win[8] = {0}, Wout[8] = {0};
+    Win[0] = 2.0; Win[1] = -0.5; Win[nd + 1] = 2.5;
+    Wout[0] = 1.0; Wout[1] = 0.5; Wout[nd + 1] = 2.5;
+    double Uin[8], Uout[8];
+    prim_to_cons(d, Win, Uin);
+    prim_to_cons(d, Wout, Uout);
+    const double hx = dx(d, 0), hy = dx(d, 1), hz = nd == 3 ? dx(d, 2) : 0.0;
+    for (int z = 0; z < d.n[2]; ++z)
+        for (int x = 0; x < d.n[0]; ++x) {
+            double xc = d.lo[0] + (x + 0.5) * hx;
+            T Y = T(0.0);
+            if (nd == 2) {
+                for (int n = 1; n <= 10; ++n) Y = Y + theta[n - 1] * sin_(2.0 * PI * n * xc + theta[10 + n - 1]);
+            } else {
+                double zc = d.lo[2] + (z + 0.5) * hz;
+                for (int n = 1; n <= 8; ++n)
+                    for (int m = 1; m <= 8; ++m) {
+                        int j = (n - 1) * 8 + (m - 1);
+                        Y = Y + theta[j] * sin_(2.0 * PI * (n * xc + m * zc) + theta[64 + j]);
+                    }
+            }
+            Y = 0.01 * Y;
+            for (int y = 0; y < d.n[1]; ++y) {
+                double ylo = d.lo[1] + y * hy;
+                T f_lo = clamp01(T((0.25 + Y - ylo) / hy));  // fraction of the cell below interface 1
+                T f_hi = clamp01(T((0.75 + Y - ylo) / hy));  // fraction of the cell below interface 2
+                T f = f_hi - f_lo;                           // fraction inside the band
+                for (int v = 0; v < nvars(d); ++v) U[lin(d, v, x, y, z)] = f * Uin[v] + (1.0 - f) * Uout[v];
+            }
+        }
+}
+
+// Two-state shock tube split at x = 0.5 (exact volume fraction when a cell straddles it).
+void init_tube(const Desc& d, const double* WLp, const double* WRp, double* U) {
+    double UL[8], UR[8];
+    prim_to_cons(d, WLp, UL);
+    prim_to_cons(d, WRp, UR);
+    const double h = dx(d, 0);
+    for (int z = 0; z < d.n[2]; ++z)
+        for (int y = 0; y < d.n[1]; ++y)
+            for (int x = 0; x < d.n[0]; ++x) {
+                double xl = d.lo[0] + x * h;
+                double f = std::min(1.0, std::max(0.0, (0.5 - xl) / h));  // left-state fraction
+                for (int v = 0; v < nvars(d); ++v) U[lin(d, v, x, y, z)] = f * UL[v] + (1.0 - f) * UR[v];
+            }
+}
+
+// Burgers u0 = sin(2 pi x): exact cell averages (cos(2 pi x_l) - cos(2 pi x_r)) / (2 pi dx).
+void init_burgers_sine(const Desc& d, double* U) {
+    const double PI = 3.14159265358979323846;
+    const double h = dx(d, 0);
+    for (int z = 0; z < d.n[2]; ++z)
+        for (int y = 0; y < d.n[1]; ++y)
+            for (int x = 0; x < d.n[0]; ++x) {
+                double xl = d.lo[0] + x * h, xr = xl + h;
+                U[lin(d, 0, x, y, z)] = (std::cos(2.0 * PI * xl) - std::cos(2.0 * PI * xr)) / (2.0 * PI * h);
+            }
+}
+
+// Isentropic vortex (Shu's standard test): ambient (rho,u,v,p) = (1,1,1,1), strength beta = 5,
+// centre (xc, yc); perturbations du = -beta/(2pi) e^{(1-r^2)/2} (y-yc), dv = beta/(2pi) e^{(1-r^2)/2}
+// (x-xc), dT = -(gamma-1) beta^2/(8 gamma pi^2) e^{1-r^2}; T = 1 + dT, rho = T^{1/(gamma-1)},
+// p = rho T. Cell averages of conserved variables by 5x5 Gauss-Legendre quadrature.
+void vortex_point(double g, double xc, double yc, double x, double y, double* Uc) {
+    const double PI = 3.14159265358979323846, beta = 5.0;
+    double rx = x - xc, ry = y - yc, r2 = rx * rx + ry * ry;
+    double e = std::exp(0.5 * (1.0 - r2));
+    double u = 1.0 - beta / (2.0 * PI) * e * ry;
+    double v = 1.0 + beta / (2.0 * PI) * e * rx;
+    double Tm = 1.0 - (g - 1.0) * beta * beta / (8.0 * g * PI * PI) * e * e;
+    double rho = std::pow(Tm, 1.0 / (g - 1.0));
+    double p = rho * Tm;
+    Uc[0] = rho;
+    Uc[1] = rho * u;
+    Uc[2] = rho * v;
+    Uc[3] = p / (g - 1.0) + 0.5 * rho * (u * u + v * v);
+}
+
+void init_vortex(const Desc& d, double xc, double yc, double* U) {
+    // 5-point Gauss-Legendre nodes/weights on [-1,1]
+    const double gx[5] = {-0.9061798459386640, -0.5384693101056831, 0.0, 0.5384693101056831, 0.9061798459386640};
+    const double gw[5] = {0.2369268850561891, 0.4786286704993665, 0.5688888888888889, 0.4786286704993665,
+                          0.2369268850561891};
+    const double hx = dx(d, 0), hy = dx(d, 1);
+    for (int y = 0; y < d.n[1]; ++y)
+        for (int x = 0; x < d.n[0]; ++x) {
+            double acc[4] = {0, 0, 0, 0};
+            double cx = d.lo[0] + (x + 0.5) * hx, cy = d.lo[1] + (y + 0.5) * hy;
+            for (int a = 0; a < 5; ++a)
+                for (int b = 0; b < 5; ++b) {
+                    double Uc[4];
+                    vortex_point(d.gamma, xc, yc, cx + 0.5 * hx * gx[a], cy + 0.5 * hy * gx[b], Uc);
+                    for (int v = 0; v < 4; ++v) acc[v] += 0.25 * gw[a] * gw[b] * Uc[v];
+                }
+            for (int v = 0; v < 4; ++v) U[lin(d, v, x, y, 0)] = acc[v];
+        }
+}
+
+// ------------------------------------------------------------------------------------------
+// SplitMix64 (Steele, Lea, Flood 2014) used as a counter-based generator for KH parameters:
+//   theta_{b,j} = lo_j + (hi_j - lo_j) * (splitmix64(seed XOR (b*P + j)) >> 11) * 2^-53,
+//   splitmix64(x) = mix(x + 0x9E3779B97F4A7C15) with the published finaliser.
+// ------------------------------------------------------------------------------------------
+inline uint64_t splitmix64(uint64_t x) {
+    uint64_t z = x + 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+}  // namespace orc
+
+using namespace orc;
+
+// ==========================================================================================
+// ctypes interface. All arrays are host FP64, layout [sample][var][z][y][x], x fastest.
+// Return codes: 0 ok, 1 invalid argument, 3 non-physical state / non-finite wave speed.
+// ==========================================================================================
+extern "C" {
+
+int orc_num_threads() {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+int orc_nvars(const Desc* d) { return nvars(*d); }
+
+// One numerical flux on primitive states (for unit pins).
+void orc_flux(const Desc* d, int k, const double* WL, const double* WR, double* F) { flux(*d, k, WL, WR, F); }
+
+// Reconstruction of a single cell's faces from three scalars.
+void orc_recon(int recon, double eps, double wm, double w0, double wp, double* fl, double* fr) {
+    recon_scalar(recon, eps, wm, w0, wp, fl, fr);
+}
+
+void orc_cons_to_prim(const Desc* d, const double* U, double* W) { cons_to_prim(*d, U, W); }
+void orc_prim_to_cons(const Desc* d, const double* W, double* U) { prim_to_cons(*d, W, U); }
+
+// L(U) for B samples.
+void orc_rhs(const Desc* d, int B, const double* U, double* L) {
+    const int64_t S = (int64_t)nvars(*d) * ncells(*d);
+    for (int b = 0; b < B; ++b) rhs(*d, U + b * S, L + b * S);
+}
+
+// Maximum CFL wave speed of each sample (NaN if non-physical).
+void orc_max_speed(const Desc* d, int B, const double* U, double* s) {
+    const int64_t S = (int64_t)nvars(*d) * ncells(*d);
+    for (int b = 0; b < B; ++b) s[b] = max_speed(*d, U + b * S);
+}
+
+// Advance B samples in place.
+//   fixed_dt > 0: exactly n_steps steps of fixed_dt (T ignored).
+//   fixed_dt == 0: CFL steps dt = cfl / s until t = T (last step clipped to land on T), at most
+//                  max_steps steps (max_steps <= 0: unlimited).
+// steps[b], t[b] receive the step count and final time.
+int orc_evolve(const Desc* d, int B, double* U, double T, double fixed_dt, int64_t n_steps, int64_t max_steps,
+               int64_t* steps, double* t_out) {
+    const int64_t S = (int64_t)nvars(*d) * ncells(*d);
+    int status = 0;
+    for (int b = 0; b < B; ++b) {
+        double* Ub = U + b * S;
+        double t = 0.0;
+        int64_t k = 0;
+        if (fixed_dt > 0.0) {
+            for (k = 0; k < n_steps; ++k) rk_step(*d, Ub, fixed_dt);
+            t = fixed_dt * (double)n_steps;
+        } else {
+            while (t < T && (max_steps <= 0 || k < max_steps)) {
+                double s = max_speed(*d, Ub);
+                if (!std::isfinite(s)) { status = 3; break; }
+                double dt = d->cfl / s;
+                bool last = false;
+                if (!(dt < T - t)) { dt = T - t; last = true; }
+                rk_step(*d, Ub, dt);
+                t = last ? T : t + dt;
+                ++k;
+            }
+        }
+        if (steps) steps[b] = k;
+        if (t_out) t_out[b] = t;
+    }
+    return status;
+}
+
+// KH parameters from SplitMix64: B x P, amplitudes U(0,1) for j < P/2, phases U(0, 2 pi) after.
+void orc_theta(uint64_t seed, int B, int P, double* theta) {
+    const double PI = 3.14159265358979323846;
+    for (int b = 0; b < B; ++b)
+        for (int j = 0; j < P; ++j) {
+            uint64_t r = splitmix64(seed ^ ((uint64_t)b * (uint64_t)P + (uint64_t)j));
+            double u01 = (double)(r >> 11) * (1.0 / 9007199254740992.0);
+            double hi = j < P / 2 ? 1.0 : 2.0 * PI;
+            theta[(int64_t)b * P + j] = 0.0 + (hi - 0.0) * u01;
+        }
+}
+
+uint64_t orc_splitmix64(uint64_t x) { return splitmix64(x); }
+
+// Initial data for B samples; theta is B x P (KH only). Vortex: centre (param0, param1).
+int orc_init(const Desc* d, int kind, int B, const double* theta, int P, double param0, double param1, double* U) {
+    const int64_t S = (int64_t)nvars(*d) * ncells(*d);
+    for (int b = 0; b < B; ++b) {
+        double* Ub = U + b * S;
+        if (kind == INIT_KH) {
+            if (d->eq != EQ_EULER || d->ndim < 2) return 1;
+            init_kh(*d, theta + (int64_t)b * P, Ub);
+        } else if (kind == INIT_SOD || kind == INIT_LAX) {
+            if (d->eq != EQ_EULER) return 1;
+            double WL[8] = {0}, WR[8] = {0};
+            int ip = d->ndim + 1;
+            if (kind == INIT_SOD) { WL[0] = 1.0; WL[ip] = 1.0; WR[0] = 0.125; WR[ip] = 0.1; }
+            else { WL[0] = 0.445; WL[1] = 0.698; WL[ip] = 3.528; WR[0] = 0.5; WR[ip] = 0.571; }
+            init_tube(*d, WL, WR, Ub);
+        } else if (kind == INIT_BURGERS_SINE) {
+            if (d->eq != EQ_BURGERS) return 1;
+            init_burgers_sine(*d, Ub);
+        } else if (kind == INIT_VORTEX) {
+            if (d->eq != EQ_EULER || d->ndim != 2) return 1;
+            init_vortex(*d, param0, param1, Ub);
+        } else {
+            return 1;
+        }
+    }
+    return 0;
+}
+
+// Welford update of per-cell mean/M2 of the primitive quantities (Burgers: u; Euler: rho,
+// velocities, p) over B samples in ascending order (Sec. 2.2: mean and variance on device).
+// count is shared by all cells; mean, M2 are [q][cells].
+void orc_welford(const Desc* d, int B, const double* U, int64_t* count, double* mean, double* M2) {
+    const int nv = nvars(*d);
+    const int64_t C = ncells(*d);
+    const int64_t S = (int64_t)nv * C;
+    int64_t n0 = *count;
+    for (int64_t i = 0; i < C; ++i) {
+        int64_t n = n0;
+        for (int b = 0; b < B; ++b) {
+            double Uc[8], W[8];
+            for (int v = 0; v < nv; ++v) Uc[v] = U[b * S + v * C + i];
+            if (d->eq == EQ_BURGERS) W[0] = Uc[0];
+            else cons_to_prim(*d, Uc, W);
+            n += 1;
+            for (int q = 0; q < nv; ++q) {
+                double x = W[q];
+                double delta = x - mean[q * C + i];
+                mean[q * C + i] += delta / (double)n;
+                M2[q * C + i] += delta * (x - mean[q * C + i]);
+            }
+        }
+    }
+    *count = n0 + B;
+}
+
+// Totals sum_i U_{v,i} dV per sample and variable (pairwise summation).
+static double pairwise(const double* x, int64_t n) {
+    if (n <= 8) { double s = 0.0; for (int64_t i = 0; i < n; ++i) s += x[i]; return s; }
+    int64_t h = n / 2;
+    return pairwise(x, h) + pairwise(x + h, n - h);
+}
+void orc_totals(const Desc* d, int B, const double* U, double* tot) {
+    const int nv = nvars(*d);
+    const int64_t C = ncells(*d);
+    double dV = 1.0;
+    for (int k = 0; k < d->ndim; ++k) dV *= dx(*d, k);
+    for (int b = 0; b < B; ++b)
+        for (int v = 0; v < nv; ++v) tot[b * nv + v] = pairwise(U + ((int64_t)b * nv + v) * C, C) * dV;
+}
+
+// Kinetic energy KE = sum_i |m_i|^2 / (2 rho_i) dV per sample (Euler).
+void orc_kinetic_energy(const Desc* d, int B, const double* U, double* ke) {
+    const int nv = nvars(*d);
+    const int64_t C = ncells(*d);
+    double dV = 1.0;
+    for (int k = 0; k < d->ndim; ++k) dV *= dx(*d, k);
+    std::vector<double> e(C);
+    for (int b = 0; b < B; ++b) {
+        const double* Ub = U + (int64_t)b * nv * C;
+        for (int64_t i = 0; i < C; ++i) {
+            double m2 = 0.0;
+            for (int k = 0; k < d->ndim; ++k) m2 += Ub[(1 + k) * C + i] * Ub[(1 + k) * C + i];
+            e[i] = 0.5 * m2 / Ub[i];
+        }
+        ke[b] = pairwise(e.data(), C) * dV;
+    }
+}
+
+// Exact gradient of the kinetic energy at time n_steps*dt with respect to the 20 2D KH
+// parameters of ONE sample, by forward-mode dual numbers through init + n fixed-dt steps.
+// Returns J in *J and dJ/dtheta in grad[20].
+int orc_ke_grad_kh2d(const Desc* d, const double* theta, double dt, int64_t n_steps, double* J, double* grad) {
+    if (d->eq != EQ_EULER || d->ndim != 2) return 1;
+    typedef Dual<20> D;
+    const int64_t N = (int64_t)nvars(*d) * ncells(*d);
+    std::vector<D> th(20), U(N);
+    for (int j = 0; j < 20; ++j) { th[j] = D(theta[j]); th[j].d[j] = 1.0; }
+    init_kh(*d, th.data(), U.data());
+    for (int64_t s = 0; s < n_steps; ++s) rk_step(*d, U.data(), D(dt));
+    const int64_t C = ncells(*d);
+    const double dV = dx(*d, 0) * dx(*d, 1);
+    D acc(0.0);
+    for (int64_t i = 0; i < C; ++i) {
+        D m2 = U[C + i] * U[C + i] + U[2 * C + i] * U[2 * C + i];
+        acc = acc + 0.5 * m2 / U[i];
+    }
+    acc = acc * dV;
+    *J = acc.v;
+    for (int j = 0; j < 20; ++j) grad[j] = acc.d[j];
+    return 0;
+}
+
+// Directional derivative dJ/dtheta . vdir via a single-direction dual run (dot-product pin).
+int orc_ke_dir_kh2d(const Desc* d, const double* theta, const double* vdir, double dt, int64_t n_steps, double* J,
+                    double* dJ) {
+    if (d->eq != EQ_EULER || d->ndim != 2) return 1;
+    typedef Dual<1> D;
+    const int64_t N = (int64_t)nvars(*d) * ncells(*d);
+    std::vector<D> th(20), U(N);
+    for (int j = 0; j < 20; ++j) { th[j] = D(theta[j]); th[j].d[0] = vdir[j]; }
+    init_kh(*d, th.data(), U.data());
+    for (int64_t s = 0; s < n_steps; ++s) rk_step(*d, U.data(), D(dt));
+    const int64_t C = ncells(*d);
+    const double dV = dx(*d, 0) * dx(*d, 1);
+    D acc(0.0);
+    for (int64_t i = 0; i < C; ++i) {
+        D m2 = U[C + i] * U[C + i] + U[2 * C + i] * U[2 * C + i];
+        acc = acc + 0.5 * m2 / U[i];
+    }
+    acc = acc * dV;
+    *J = acc.v;
+    *dJ = acc.d[0];
+    return 0;
+}
+
+}  // extern "C"

@@ -1,0 +1,315 @@
+"""Benchmark: batched Monte Carlo Kelvin-Helmholtz on one GB300.
+
+Workload (one "step" = one pass of the whole hot path over one batch): 4096 seeded samples of the
+2D Kelvin-Helmholtz problem on a 256^2 periodic grid, FP32 state, WENO3 + HLLC + SSP-RK3 at CFL
+0.4 to T = 1 with a per-sample CFL step (about 1,500 RK steps per sample), then the FP64 Welford
+mean/variance of (rho, u, v, p) per cell and the FP64 conservation totals. Metric: cell-updates/s
+(one cell advanced one full RK step, summed over samples) and samples/s.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+The state (4.3 GB) and stage buffers exceed L2 (129 MB), so no L2 flush is needed between steps.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N = 256
+M = 4096
+T_END = 1.0
+SEED = 12345
+METRIC = "cell-updates/s & % HBM roofline; MC samples/s batched-FP32 vs plain FP64"
+WORKLOAD = "kh2d_256x256_mc4096_weno3_hllc_ssprk3_fp32_T1"
+# compulsory HBM bytes per 2D SSP-RK3 cell-update in FP32: per variable read U^n + write U1,
+# read U1 + U^n + write U2, read U2 + U^n + write U^{n+1} = 8 words, x 4 variables x 4 bytes
+BYTES_PER_CELL_UPDATE = 8 * 4 * 4
+
+
+def desc_kwargs(batch=M, seed=SEED):
+    return dict(ndim=2, n=(N, N), lo=(0, 0), hi=(1, 1), batch=batch, eq="euler", gamma=1.4, recon="weno3",
+                rvars="prim", flux="hllc", rk="ssprk3", bc="periodic", cfl=0.4, precision="fp32", seed=seed)
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        load = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def run_step(S, alsv, stats_fresh=True):
+    """One pass of the hot path on device-resident inputs: init from the seed, evolve to T,
+    statistics, totals. Returns the per-sample step counts (host)."""
+    S.set_initial_data("kh")
+    S.evolve_to(T_END)
+    if stats_fresh:
+        alsv.alsv_stats_reset(S.ctx, S.stats)
+    alsv.alsv_stats_accumulate(S.ctx, S.stats)
+    alsv.alsv_conservation_totals(S.ctx, S.tot)
+    _, nstep = S.time()
+    return nstep
+
+
+def cpu_baseline_oracle(budget_s=15.0):
+    """Time the FP64 oracle as it stands on this host's cores on a bounded sample of the same
+    workload (one sample of the batch, as many CFL steps as fit in the budget)."""
+    import oracle
+    import numpy as np
+    kw = desc_kwargs(batch=1)
+    d = oracle.make_desc(**kw)
+    th = oracle.theta_splitmix(SEED, 1, 20)
+    U = oracle.init(d, "kh", 1, th)
+    steps = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < budget_s and steps < 10000:
+        U, s, _ = oracle.evolve(d, U, T=math.inf, max_steps=1)
+        steps += 1
+    el = time.perf_counter() - t0
+    cu = steps * N * N
+    return {"value": cu / el, "unit": "cell-updates/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"1 of {M} samples, first {steps} CFL steps of T=1 on 256^2 (FP64 oracle, {el:.1f} s)",
+            "elapsed_s": el, "cell_updates": cu}
+
+
+def reference_arm(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    per_step = max(3.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        cpu_baseline_oracle(budget_s=min(per_step, 3.0))
+    vals, tot_cu, tot_t = [], 0, 0.0
+    last = None
+    for _ in range(args.steps):
+        last = cpu_baseline_oracle(budget_s=per_step)
+        tot_cu += last["cell_updates"]
+        tot_t += last["elapsed_s"]
+    value = tot_cu / tot_t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded KH parameters, SplitMix64)",
+            "config": {"workload": WORKLOAD, "grid": [N, N], "samples": M, "T": T_END,
+                       "reference_sample": "one sample per step, CFL steps within a time budget"},
+            "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": last["cores"], "kind": "oracle",
+                             "sample": last["sample"]},
+            "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="alsv")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--samples", type=int, default=M, help=argparse.SUPPRESS)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+    import torch.distributed as dist
+    from paper_1912_07645_gb300 import build
+    build.build()
+    import paper_1912_07645_gb300 as alsv
+
+    rank, world, local = dist_env()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    Mr = args.samples
+    # weak scaling: every rank advances its own batch of Mr samples (seeds offset by rank)
+    kw = desc_kwargs(batch=Mr, seed=SEED + 7919 * rank)
+    S = alsv.Solver(alsv.make_desc(**kw))
+    S.stats_init()
+    with torch.cuda.stream(S.stream):
+        S.tot = torch.empty((Mr, 4), dtype=torch.float64, device=dev)
+    S.set_initial_data("kh")
+    chosen, ms_var = alsv.alsv_autotune(S.ctx, 3)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+            torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        run_step(S, alsv)
+    barrier()
+    # ---- device-timed region (inputs resident in HBM)
+    clocks = ClockSampler(local)
+    clocks.start()
+    alsv.alsv_set_profiling(S.ctx, True)
+    l0 = alsv.alsv_get_launch_count(S.ctx)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    ev0.record(S.stream)
+    cell_updates = 0
+    for _ in range(args.steps):
+        nstep = run_step(S, alsv)
+        cell_updates += int(nstep.sum()) * N * N
+    ev1.record(S.stream)
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    launches = alsv.alsv_get_launch_count(S.ctx) - l0
+    prof = alsv.alsv_get_profile(S.ctx)
+    alsv.alsv_set_profiling(S.ctx, False)
+    ck = clocks.stop()
+    t_rank = torch.tensor([ms], dtype=torch.float64, device=dev)
+    cu_rank = torch.tensor([float(cell_updates)], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_rank, op=dist.ReduceOp.MAX)
+        dist.all_reduce(cu_rank, op=dist.ReduceOp.SUM)
+    ms_max = float(t_rank.item())
+    cu_all = float(cu_rank.item())
+    value = cu_all / (ms_max / 1000.0)
+    samples_per_s = world * Mr * args.steps / (ms_max / 1000.0)
+
+    # ---- end-to-end through the public API with host buffers (pinned)
+    th_host = torch.empty((Mr, 20), dtype=torch.float64).pin_memory()
+    th_host.copy_(torch.from_numpy(__import__("numpy").random.default_rng(rank).uniform(0, 1, (Mr, 20))))
+    th_host[:, 10:] *= 2 * math.pi
+    mean_host = torch.empty((4, 1, N, N), dtype=torch.float64).pin_memory()
+    var_host = torch.empty_like(mean_host)
+    with torch.cuda.stream(S.stream):
+        th_dev = torch.empty((Mr, 20), dtype=torch.float64, device=dev)
+        mean_dev = torch.empty((4, 1, N, N), dtype=torch.float64, device=dev)
+        var_dev = torch.empty_like(mean_dev)
+    barrier()
+    t0 = time.perf_counter()
+    cu_e2e = 0
+    for _ in range(args.steps):
+        with torch.cuda.stream(S.stream):
+            th_dev.copy_(th_host, non_blocking=True)
+        alsv.alsv_set_initial_data(S.ctx, "kh", th_dev, 20, S.U)
+        S.evolve_to(T_END)
+        alsv.alsv_stats_reset(S.ctx, S.stats)
+        alsv.alsv_stats_accumulate(S.ctx, S.stats)
+        alsv.alsv_stats_read(S.ctx, S.stats, mean_dev, var_dev)
+        with torch.cuda.stream(S.stream):
+            mean_host.copy_(mean_dev, non_blocking=True)
+            var_host.copy_(var_dev, non_blocking=True)
+        S.stream.synchronize()
+        _, nstep = S.time()
+        cu_e2e += int(nstep.sum()) * N * N
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+    e2e_cu = torch.tensor([float(cu_e2e)], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(e2e_cu, op=dist.ReduceOp.SUM)
+    e2e = {"value": float(e2e_cu.item()) / float(e2e_t.item()), "unit": "cell-updates/s",
+           "h2d_bytes_per_step": Mr * 20 * 8, "d2h_bytes_per_step": 2 * 4 * N * N * 8,
+           "samples_per_s": world * Mr * args.steps / float(e2e_t.item())}
+
+    if rank == 0:
+        peaks, peak_kind = measured_peaks()
+        stage_bytes = cell_updates * BYTES_PER_CELL_UPDATE
+        achieved = stage_bytes / (prof["stage_ms"] / 1000.0) / 1e9 if prof["stage_ms"] > 0 else None
+        traffic = None
+        tp = os.path.join(ROOT, "profiles", "stage_traffic.json")
+        if os.path.exists(tp):
+            with open(tp) as f:
+                traffic = json.load(f).get("bytes_per_cell_stage_launch")
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": (achieved / peaks["hbm_gbs"]) if achieved else None, "peak_kind": peak_kind,
+                "kernel": "k_stage<float, Euler, 2D, WENO3, HLLC>",
+                "algorithmic_bytes_per_cell_update": BYTES_PER_CELL_UPDATE,
+                "stage_ms_total": prof["stage_ms"], "stage_launches": prof["stage_launches"],
+                "stage_share_of_step": prof["stage_ms"] / ms if ms > 0 else None,
+                "traffic": traffic}
+        line = {"metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "fp32 (stencil); fp64 (statistics, totals, time)",
+                "data": "synthetic (seeded KH perturbation parameters, SplitMix64)",
+                "config": {"workload": WORKLOAD, "grid": [N, N], "samples_per_gpu": Mr, "T": T_END, "cfl": 0.4,
+                           "scheme": "WENO3 (primitive) + HLLC + SSP-RK3", "parallelism": f"samples sharded x{world}",
+                           "l2": "inputs larger than L2 (4.3 GB state), no flush",
+                           "tile_variant": chosen, "autotune_ms": ms_var},
+                "samples_per_s": samples_per_s, "gpu_launches": launches, "e2e": e2e, "roofline": roof,
+                "clocks": ck}
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = {k: v for k, v in cpu_baseline_oracle().items() if k not in ("elapsed_s", "cell_updates")}
+        print(json.dumps(line), flush=True)
+    S.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,249 @@
+/*
+ * alsv.h - C ABI of the GB300 (sm_103a) finite-volume Monte Carlo solver.
+ *
+ * The library advances many samples of a hyperbolic conservation law u_t + div F(u) = 0
+ * (eq. (1.1), Sec. 1 of "Alsvinn: A Fast multi-GPGPU finite volume solver with a strong emphasis
+ * on reproducibility", arXiv:1912.07645) with the semi-discrete finite-volume update of eq. (2.1)
+ * (Sec. 2.1), a numerical flux (HLLC, Rusanov, HLL), a reconstruction (piecewise constant,
+ * MC-limited linear, WENO3) and SSP Runge-Kutta time stepping, and keeps the Monte Carlo mean and
+ * variance of every cell on the device (Sec. 2.2).
+ *
+ * Conventions for every entry point:
+ *   - Every call returns an alsv_status; nothing throws across the ABI. alsv_last_error(ctx)
+ *     gives a message owned by the context (valid until the next call on that context).
+ *   - All device memory is CALLER-OWNED: the caller allocates it (e.g. torch tensors) and passes
+ *     raw device pointers with their sizes in bytes. A context only borrows pointers; it never
+ *     allocates or frees device memory.
+ *   - All GPU work is enqueued on the stream given to alsv_init_grid (a cudaStream_t passed as
+ *     void*; NULL is the legacy default stream). Calls are asynchronous unless documented as
+ *     synchronous.
+ *   - A context is not thread-safe: use one context per stream and per host thread.
+ *   - State layout ("SoA"): U[sample][var][z][y][x], x fastest, interior cells only, no ghost
+ *     cells in memory. Elements are float (ALSV_FP32) or double (ALSV_FP64). Variables: Burgers
+ *     u; Euler rho, rho*u_0 .. rho*u_{ndim-1}, E. Samples of an MLMC level table are stored level
+ *     after level, each level contiguous.
+ *   - Determinism: no floating-point atomics; every reduction has a fixed order, so repeated runs
+ *     with the same inputs are bitwise identical.
+ */
+#ifndef ALSV_H
+#define ALSV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int alsv_status;
+enum {
+    ALSV_OK = 0,
+    ALSV_ERR_INVALID_ARG = 1,       /* bad descriptor, pointer, size or call order */
+    ALSV_ERR_CUDA = 2,              /* a CUDA runtime call failed (message names it) */
+    ALSV_ERR_NONPHYSICAL = 3,       /* a sample reached rho <= 0, p <= 0 or a non-finite value */
+    ALSV_ERR_CFL = 4,               /* fixed-dt mode: realised CFL number above the guard */
+    ALSV_ERR_TIMEOUT = 5,           /* a bounded device wait gave up */
+    ALSV_ERR_BUFFER_TOO_SMALL = 6,  /* a caller buffer is smaller than required */
+    ALSV_ERR_NOT_READY = 7          /* workspace / state not bound yet */
+};
+
+enum { ALSV_EQ_BURGERS = 0, ALSV_EQ_EULER = 1 };
+enum { ALSV_RECON_PC = 0, ALSV_RECON_MC = 1, ALSV_RECON_WENO3 = 2 };
+enum { ALSV_VARS_CONS = 0, ALSV_VARS_PRIM = 1 };
+enum { ALSV_FLUX_RUSANOV = 0, ALSV_FLUX_HLL = 1, ALSV_FLUX_HLLC = 2 };
+enum { ALSV_RK_SSP2 = 2, ALSV_RK_SSP3 = 3 };
+enum { ALSV_BC_PERIODIC = 0, ALSV_BC_OUTFLOW = 1, ALSV_BC_REFLECTIVE = 2 };
+enum { ALSV_FP32 = 0, ALSV_FP64 = 1 };
+enum {
+    ALSV_INIT_KH = 0,           /* Kelvin-Helmholtz shear layer (Sec. 3), 2D (20 params) or 3D (128) */
+    ALSV_INIT_SOD = 1,          /* Sod tube, split at x = 0.5 */
+    ALSV_INIT_LAX = 2,          /* Lax tube, split at x = 0.5 */
+    ALSV_INIT_BURGERS_SINE = 3, /* u0 = sin(2 pi x), exact cell averages */
+    ALSV_INIT_VORTEX = 4,       /* isentropic vortex, 5x5 Gauss cell averages */
+    ALSV_INIT_RAW = 5           /* U_dev already holds the initial state */
+};
+enum { ALSV_OBS_KINETIC_ENERGY = 0 };
+
+#define ALSV_MAX_LEVELS 8
+
+/* Problem descriptor. Unused trailing dimensions must have n = 1. */
+typedef struct alsv_grid_desc {
+    int32_t ndim;          /* 1, 2 or 3 */
+    int32_t n[3];          /* cells per direction (level 0 when n_levels > 1 ignores this) */
+    double lo[3], hi[3];   /* domain box; dx_k = (hi_k - lo_k) / n_k (one dx per direction) */
+    int32_t batch;         /* samples B (single-level) */
+    int32_t eq;            /* ALSV_EQ_* */
+    double gamma;          /* ideal-gas ratio of specific heats (Euler) */
+    int32_t recon;         /* ALSV_RECON_* */
+    int32_t recon_vars;    /* ALSV_VARS_* (Euler only) */
+    int32_t flux;          /* ALSV_FLUX_* (Burgers: HLLC behaves as HLL) */
+    int32_t rk;            /* ALSV_RK_* */
+    int32_t bc[3][2];      /* ALSV_BC_* per direction and side; periodic must pair with periodic */
+    double cfl;            /* CFL number for the adaptive step */
+    double fixed_dt;       /* > 0: fixed step (adjoint mode); 0: adaptive CFL step */
+    int32_t precision;     /* ALSV_FP32 or ALSV_FP64: state and stencil arithmetic */
+    uint64_t seed;         /* master seed for counter-based KH parameters */
+    double weno_eps;       /* WENO3 epsilon (default 1e-6) */
+    int32_t weno_eps_dx2;  /* 1: epsilon = dx_k^2 per direction */
+    int32_t n_levels;      /* 0 or 1: single grid; 2..8: MLMC level table below */
+    int32_t level_n[ALSV_MAX_LEVELS][3];
+    int32_t level_batch[ALSV_MAX_LEVELS];
+    double vortex_center[2];
+    int32_t reserved[8];   /* must be zero */
+} alsv_grid_desc;
+
+typedef struct alsv_ctx alsv_ctx;
+
+/* Library version string (static storage). */
+const char* alsv_version(void);
+
+/* Message of the last failed call on ctx (or of the last failed alsv_init_grid when ctx is
+ * NULL). Owned by the library. */
+const char* alsv_last_error(const alsv_ctx* ctx);
+
+/*
+ * alsv_init_grid - validate a descriptor and create a context bound to `stream`.
+ *   d                 descriptor (host, read during the call only)
+ *   stream            cudaStream_t as void*; all later work of this context goes there
+ *   out               receives the new context (host pointer)
+ *   workspace_bytes   receives the device workspace size the context needs: RK stage buffers,
+ *                     per-tile wave-speed partials, per-sample time state, parameters, status.
+ * Errors: ALSV_ERR_INVALID_ARG (bad field; message names it). Synchronous; no GPU work.
+ * Defines the discretisation of eq. (2.1) (Sec. 2.1) on the given grid(s).
+ */
+alsv_status alsv_init_grid(const alsv_grid_desc* d, void* stream, alsv_ctx** out, size_t* workspace_bytes);
+
+/* Bind caller-allocated device workspace (>= workspace_bytes, 256-byte aligned). The context
+ * borrows it until alsv_destroy or the next bind. ALSV_ERR_BUFFER_TOO_SMALL if short. */
+alsv_status alsv_bind_workspace(alsv_ctx* ctx, void* dev, size_t bytes);
+
+/* Bytes of the full state U for all samples (and levels) of this context. */
+size_t alsv_state_bytes(const alsv_ctx* ctx);
+
+/* Copy the context's KH parameters (generated from the seed or passed to alsv_set_initial_data)
+ * into theta_dev (device FP64 [samples][n_params]). Asynchronous. */
+alsv_status alsv_get_parameters(alsv_ctx* ctx, double* theta_dev);
+
+/* Total number of samples (sum over levels) and conserved variables per cell. */
+int32_t alsv_num_samples(const alsv_ctx* ctx);
+int32_t alsv_num_vars(const alsv_ctx* ctx);
+
+/*
+ * alsv_set_initial_data - write u0 into U_dev and reset every sample's time to 0.
+ *   kind        ALSV_INIT_*; KH follows Sec. 3 (two-state shear flow with perturbed interfaces);
+ *               the perturbation reading is: interfaces at y = 0.25 + Y and 0.75 + Y with
+ *               Y = 0.01 sum a_n sin(2 pi n x + b_n) (2D, 10 modes) or a 2D Fourier sum with 8x8
+ *               modes in (x,z) (3D), cell values blended by the band's volume fraction in y.
+ *   theta_dev   device FP64 [samples][n_params] parameters (a_n then b_n); NULL: expand them
+ *               from d->seed with SplitMix64 (theta_{b,j} = hi_j * (splitmix64(seed ^ (b P + j))
+ *               >> 11) * 2^-53, hi = 1 for amplitudes, 2 pi for phases).
+ *   n_params    20 (2D KH) or 128 (3D KH); ignored by other kinds
+ *   U_dev       device state buffer (layout above) of U_bytes >= alsv_state_bytes(ctx); the
+ *               context keeps the pointer and evolves it in place.
+ * Asynchronous. Errors: INVALID_ARG, BUFFER_TOO_SMALL, NOT_READY (no workspace).
+ */
+alsv_status alsv_set_initial_data(alsv_ctx* ctx, int kind, const double* theta_dev, int n_params, void* U_dev,
+                                  size_t U_bytes);
+
+/*
+ * alsv_step - advance every sample that is not done by n_steps full SSP-RK steps of eq. (2.1)
+ * (Sec. 2.1). Adaptive mode: dt_b = min(cfl / s_b, T - t_b) with s_b the largest
+ * (|u_k| + c)/dx_k of sample b (Burgers |u|/dx_k); T is +infinity unless set by
+ * alsv_evolve_to_T. Fixed mode: dt = d->fixed_dt. Asynchronous; status errors raised by the
+ * kernels are reported by the next synchronous call (alsv_sync or alsv_evolve_to_T).
+ */
+alsv_status alsv_step(alsv_ctx* ctx, int n_steps);
+
+/*
+ * alsv_evolve_to_T - advance every sample to t = T (last step clipped to land on T), replaying a
+ * captured CUDA graph of step chunks and polling the per-sample done flags between chunks.
+ * SYNCHRONOUS. steps_taken_host (may be NULL) receives the largest step count of any sample.
+ * Returns the first status error any sample raised (NONPHYSICAL, CFL) or OK.
+ */
+alsv_status alsv_evolve_to_T(alsv_ctx* ctx, double T, int64_t* steps_taken_host);
+
+/* Synchronise the stream and report the device status word (OK or the first error raised). */
+alsv_status alsv_sync(alsv_ctx* ctx);
+
+/* Per-sample time and step count (host arrays of alsv_num_samples entries, may be NULL).
+ * SYNCHRONOUS. */
+alsv_status alsv_get_time(alsv_ctx* ctx, double* t_host, int64_t* steps_host);
+
+/*
+ * Monte Carlo statistics (Sec. 2.2: mean and variance per cell, computed on the GPU).
+ * Accumulator layout (caller-owned device buffer of alsv_stats_bytes): int64 count, padding to
+ * 256 bytes, then FP64 mean[q][cells] and FP64 M2[q][cells] with q = rho, u_0.., p (Euler,
+ * primitive) or u (Burgers). Single-level contexts only.
+ *   alsv_stats_reset       zero the accumulator (asynchronous)
+ *   alsv_stats_accumulate  fold the current samples in ascending sample order with Welford's
+ *                          update (n += 1; delta = x - mean; mean += delta/n; M2 += delta*(x-mean)),
+ *                          in FP64; may be called once per batch to stream many batches
+ *   alsv_stats_read        mean[q][cells] and unbiased var = M2/(n-1) (0 when n = 1) into
+ *                          caller device buffers; count (host, may be NULL) makes it synchronous
+ */
+size_t alsv_stats_bytes(const alsv_ctx* ctx);
+alsv_status alsv_stats_reset(alsv_ctx* ctx, void* stats_dev, size_t bytes);
+alsv_status alsv_stats_accumulate(alsv_ctx* ctx, void* stats_dev, size_t bytes);
+alsv_status alsv_stats_read(alsv_ctx* ctx, const void* stats_dev, double* mean_dev, double* var_dev,
+                            int64_t* count_host);
+
+/* Conservation totals sum_i U_{v,i} dV in FP64 with a fixed-order tree, into the caller's device
+ * buffer totals_dev[samples][vars] (eq. (2.1) conserves them on periodic grids). Asynchronous. */
+alsv_status alsv_conservation_totals(alsv_ctx* ctx, double* totals_dev);
+
+/* Kinetic energy sum_i |m_i|^2 / (2 rho_i) dV per sample in FP64 (Euler), into ke_dev[samples]. */
+alsv_status alsv_kinetic_energy(alsv_ctx* ctx, double* ke_dev);
+
+/*
+ * Discrete adjoint (not in the paper; gradient of an observable at time T with respect to the
+ * KH parameters). Fixed step dt = T / n with n = ceil(T s_max / (cfl dx)), s_max the fastest
+ * signal of the two unperturbed KH states; ceil(sqrt(n)) checkpoints with recomputation.
+ *   alsv_adjoint_workspace_bytes  device bytes the adjoint needs for T (checkpoints + adjoint
+ *                                 state + segment buffers)
+ *   alsv_bind_adjoint_workspace   bind it (caller-owned)
+ *   alsv_adjoint_evolve           initial data from theta_dev (FP64 [samples][20]), forward with
+ *                                 checkpoints, reverse sweep; writes J_dev[samples] and
+ *                                 grad_theta_dev[samples][20] (FP64). SYNCHRONOUS. Supported:
+ *                                 2D Euler KH, periodic, PC or MC reconstruction, Rusanov flux,
+ *                                 SSP-RK2 or RK3. ALSV_ERR_CFL when the realised CFL exceeds 0.5.
+ */
+alsv_status alsv_adjoint_workspace_bytes(alsv_ctx* ctx, double T, size_t* bytes);
+alsv_status alsv_bind_adjoint_workspace(alsv_ctx* ctx, void* dev, size_t bytes);
+alsv_status alsv_adjoint_evolve(alsv_ctx* ctx, double T, int observable, const double* theta_dev,
+                                double* grad_theta_dev, double* J_dev);
+
+/* Destroy the context (host memory and CUDA graphs only; caller buffers are untouched). */
+alsv_status alsv_destroy(alsv_ctx* ctx);
+
+/*
+ * Execution controls (no counterpart in the paper; they choose how the same arithmetic is
+ * scheduled on the GPU and never change results).
+ *   alsv_num_tile_variants  number of stage-kernel tile shapes for this (precision, ndim)
+ *   alsv_set_tile_variant   select one (recomputes the wave-speed partials; asynchronous)
+ *   alsv_get_tile           current tile shape, variant and (sample, tile) work items per launch
+ *   alsv_autotune           time `reps` launches of the first stage (reads U, writes the stage
+ *                           buffer only, so the state is unchanged) per variant with CUDA events
+ *                           on the context stream and keep the fastest; ms_per_variant (host, may
+ *                           be NULL) receives the times. SYNCHRONOUS.
+ *   alsv_set_graphs         1 (default): alsv_evolve_to_T replays captured CUDA graphs of
+ *                           16-step chunks; 0: direct launches
+ *   alsv_set_profiling      1: record CUDA events around every stage / time-control launch of
+ *                           later steps (direct launches, no graphs) and accumulate their device
+ *                           time; alsv_get_profile reads the sums (SYNCHRONOUS)
+ *   alsv_get_launch_count   kernels this context has launched (graph replays included)
+ */
+int alsv_num_tile_variants(const alsv_ctx* ctx);
+alsv_status alsv_set_tile_variant(alsv_ctx* ctx, int variant);
+alsv_status alsv_get_tile(const alsv_ctx* ctx, int* tx, int* ty, int* tz, int* variant, int64_t* work_items);
+alsv_status alsv_autotune(alsv_ctx* ctx, int reps, int* chosen, float* ms_per_variant);
+alsv_status alsv_set_graphs(alsv_ctx* ctx, int on);
+alsv_status alsv_set_profiling(alsv_ctx* ctx, int on);
+alsv_status alsv_get_profile(alsv_ctx* ctx, double* stage_ms, int64_t* stage_launches, double* finish_ms,
+                             int64_t* finish_launches);
+alsv_status alsv_get_launch_count(const alsv_ctx* ctx, int64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ALSV_H */

@@ -1,0 +1,21 @@
+"""GB300 (sm_103a) finite-volume Monte Carlo solver for hyperbolic conservation laws.
+
+Implements the data-parallel core of Alsvinn (arXiv:1912.07645): the semi-discrete finite-volume
+update of eq. (2.1) with HLLC / Rusanov / HLL fluxes, PC / MC / WENO3 reconstruction and SSP-RK
+time stepping (Sec. 2.1), run over many Monte Carlo samples with per-cell mean and variance kept
+on the device (Sec. 2.2). All arithmetic runs in libalsv.so (hand-written CUDA); this package only
+marshals arguments (``_abi``, same names as include/alsv.h) and allocates caller-owned buffers
+with torch (``Solver``).
+"""
+from __future__ import annotations
+
+from ._abi import (BC, EQ, FLUX, INIT, PRECISION, RECON, RK, RVARS, AlsvError, alsv_adjoint_evolve,  # noqa: F401
+                   alsv_adjoint_workspace_bytes, alsv_autotune, alsv_bind_adjoint_workspace,
+                   alsv_bind_workspace, alsv_conservation_totals, alsv_destroy, alsv_evolve_to_T,
+                   alsv_get_launch_count, alsv_get_parameters, alsv_get_profile, alsv_get_tile, alsv_get_time, alsv_grid_desc,
+                   alsv_init_grid, alsv_kinetic_energy, alsv_last_error, alsv_num_samples,
+                   alsv_num_tile_variants, alsv_num_vars, alsv_set_graphs, alsv_set_initial_data,
+                   alsv_set_profiling, alsv_set_tile_variant, alsv_state_bytes, alsv_stats_accumulate,
+                   alsv_stats_bytes, alsv_stats_read, alsv_stats_reset, alsv_step, alsv_sync,
+                   alsv_version, load)
+from .solver import Solver, make_desc  # noqa: F401

@@ -1,0 +1,286 @@
+"""ctypes declarations of the C ABI in include/alsv.h and thin wrappers with the same names.
+
+Argument marshalling only: every step of the method runs in libalsv.so's CUDA kernels. A missing
+or unloadable library raises at import of the first call; there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libalsv.so")
+
+OK = 0
+STATUS_NAMES = {0: "OK", 1: "ERR_INVALID_ARG", 2: "ERR_CUDA", 3: "ERR_NONPHYSICAL", 4: "ERR_CFL",
+                5: "ERR_TIMEOUT", 6: "ERR_BUFFER_TOO_SMALL", 7: "ERR_NOT_READY"}
+EQ = {"burgers": 0, "euler": 1}
+RECON = {"pc": 0, "mc": 1, "weno3": 2}
+RVARS = {"cons": 0, "prim": 1}
+FLUX = {"rusanov": 0, "hll": 1, "hllc": 2}
+RK = {"ssprk2": 2, "ssprk3": 3}
+BC = {"periodic": 0, "outflow": 1, "reflective": 2}
+PRECISION = {"fp32": 0, "fp64": 1}
+INIT = {"kh": 0, "sod": 1, "lax": 2, "burgers_sine": 3, "vortex": 4, "raw": 5}
+MAX_LEVELS = 8
+
+
+class AlsvError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        self.status = status
+        self.status_name = STATUS_NAMES.get(status, str(status))
+        super().__init__(f"{where}: {self.status_name}: {message}")
+
+
+class alsv_grid_desc(C.Structure):
+    _fields_ = [
+        ("ndim", C.c_int32), ("n", C.c_int32 * 3), ("lo", C.c_double * 3), ("hi", C.c_double * 3),
+        ("batch", C.c_int32), ("eq", C.c_int32), ("gamma", C.c_double), ("recon", C.c_int32),
+        ("recon_vars", C.c_int32), ("flux", C.c_int32), ("rk", C.c_int32), ("bc", (C.c_int32 * 2) * 3),
+        ("cfl", C.c_double), ("fixed_dt", C.c_double), ("precision", C.c_int32), ("seed", C.c_uint64),
+        ("weno_eps", C.c_double), ("weno_eps_dx2", C.c_int32), ("n_levels", C.c_int32),
+        ("level_n", (C.c_int32 * 3) * MAX_LEVELS), ("level_batch", C.c_int32 * MAX_LEVELS),
+        ("vortex_center", C.c_double * 2), ("reserved", C.c_int32 * 8),
+    ]
+
+
+# name -> (restype, argtypes)
+_vp, _sz, _i64p, _dp = C.c_void_p, C.c_size_t, C.POINTER(C.c_int64), C.POINTER(C.c_double)
+_ctx = C.c_void_p
+SIGNATURES = {
+    "alsv_version": (C.c_char_p, []),
+    "alsv_last_error": (C.c_char_p, [_ctx]),
+    "alsv_init_grid": (C.c_int, [C.POINTER(alsv_grid_desc), _vp, C.POINTER(_ctx), C.POINTER(_sz)]),
+    "alsv_bind_workspace": (C.c_int, [_ctx, _vp, _sz]),
+    "alsv_state_bytes": (_sz, [_ctx]),
+    "alsv_get_parameters": (C.c_int, [_ctx, _vp]),
+    "alsv_num_samples": (C.c_int32, [_ctx]),
+    "alsv_num_vars": (C.c_int32, [_ctx]),
+    "alsv_set_initial_data": (C.c_int, [_ctx, C.c_int, _vp, C.c_int, _vp, _sz]),
+    "alsv_step": (C.c_int, [_ctx, C.c_int]),
+    "alsv_evolve_to_T": (C.c_int, [_ctx, C.c_double, _i64p]),
+    "alsv_sync": (C.c_int, [_ctx]),
+    "alsv_get_time": (C.c_int, [_ctx, _dp, _i64p]),
+    "alsv_stats_bytes": (_sz, [_ctx]),
+    "alsv_stats_reset": (C.c_int, [_ctx, _vp, _sz]),
+    "alsv_stats_accumulate": (C.c_int, [_ctx, _vp, _sz]),
+    "alsv_stats_read": (C.c_int, [_ctx, _vp, _vp, _vp, _i64p]),
+    "alsv_conservation_totals": (C.c_int, [_ctx, _vp]),
+    "alsv_kinetic_energy": (C.c_int, [_ctx, _vp]),
+    "alsv_adjoint_workspace_bytes": (C.c_int, [_ctx, C.c_double, C.POINTER(_sz)]),
+    "alsv_bind_adjoint_workspace": (C.c_int, [_ctx, _vp, _sz]),
+    "alsv_adjoint_evolve": (C.c_int, [_ctx, C.c_double, C.c_int, _vp, _vp, _vp]),
+    "alsv_destroy": (C.c_int, [_ctx]),
+    "alsv_num_tile_variants": (C.c_int, [_ctx]),
+    "alsv_set_tile_variant": (C.c_int, [_ctx, C.c_int]),
+    "alsv_get_tile": (C.c_int, [_ctx, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                C.POINTER(C.c_int), _i64p]),
+    "alsv_autotune": (C.c_int, [_ctx, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_float)]),
+    "alsv_set_graphs": (C.c_int, [_ctx, C.c_int]),
+    "alsv_set_profiling": (C.c_int, [_ctx, C.c_int]),
+    "alsv_get_profile": (C.c_int, [_ctx, _dp, _i64p, _dp, _i64p]),
+    "alsv_get_launch_count": (C.c_int, [_ctx, _i64p]),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libalsv.so (building it first is the caller's job: paper_1912_07645_gb300.build)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or LIB_PATH
+            if not os.path.exists(p):
+                raise RuntimeError(f"libalsv.so not found at {p}: run paper_1912_07645_gb300.build.build() "
+                                   "(the CUDA library is required; there is no CPU fallback)")
+            lib = C.CDLL(p)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _check(st: int, where: str, ctx=None):
+    if st != OK:
+        msg = load().alsv_last_error(ctx)
+        raise AlsvError(st, where, msg.decode() if msg else "")
+
+
+def _ptr(x) -> int | None:
+    """Device/host address of a torch tensor, an int address, or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _nbytes(x) -> int:
+    return x.numel() * x.element_size()
+
+
+# ---------------------------------------------------------------- wrappers (same names as the C ABI)
+def alsv_version() -> str:
+    return load().alsv_version().decode()
+
+
+def alsv_last_error(ctx) -> str:
+    m = load().alsv_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def alsv_init_grid(desc: alsv_grid_desc, stream: int = 0):
+    """Returns (ctx, workspace_bytes)."""
+    ctx = C.c_void_p()
+    ws = C.c_size_t()
+    _check(load().alsv_init_grid(C.byref(desc), C.c_void_p(stream or None), C.byref(ctx), C.byref(ws)),
+           "alsv_init_grid", None)
+    return ctx.value, ws.value
+
+
+def alsv_bind_workspace(ctx, ws, nbytes: int | None = None):
+    _check(load().alsv_bind_workspace(ctx, _ptr(ws), nbytes if nbytes is not None else _nbytes(ws)),
+           "alsv_bind_workspace", ctx)
+
+
+def alsv_state_bytes(ctx) -> int:
+    return int(load().alsv_state_bytes(ctx))
+
+
+def alsv_get_parameters(ctx, theta):
+    _check(load().alsv_get_parameters(ctx, _ptr(theta)), "alsv_get_parameters", ctx)
+
+
+def alsv_num_samples(ctx) -> int:
+    return int(load().alsv_num_samples(ctx))
+
+
+def alsv_num_vars(ctx) -> int:
+    return int(load().alsv_num_vars(ctx))
+
+
+def alsv_set_initial_data(ctx, kind, theta, n_params: int, U, U_bytes: int | None = None):
+    k = INIT[kind] if isinstance(kind, str) else int(kind)
+    _check(load().alsv_set_initial_data(ctx, k, _ptr(theta), n_params, _ptr(U),
+                                        U_bytes if U_bytes is not None else _nbytes(U)),
+           "alsv_set_initial_data", ctx)
+
+
+def alsv_step(ctx, n_steps: int):
+    _check(load().alsv_step(ctx, n_steps), "alsv_step", ctx)
+
+
+def alsv_evolve_to_T(ctx, T: float) -> int:
+    steps = C.c_int64()
+    _check(load().alsv_evolve_to_T(ctx, T, C.byref(steps)), "alsv_evolve_to_T", ctx)
+    return steps.value
+
+
+def alsv_sync(ctx):
+    _check(load().alsv_sync(ctx), "alsv_sync", ctx)
+
+
+def alsv_get_time(ctx):
+    import numpy as np
+    n = alsv_num_samples(ctx)
+    t = np.zeros(n)
+    s = np.zeros(n, dtype=np.int64)
+    _check(load().alsv_get_time(ctx, t.ctypes.data_as(_dp), s.ctypes.data_as(_i64p)), "alsv_get_time", ctx)
+    return t, s
+
+
+def alsv_stats_bytes(ctx) -> int:
+    return int(load().alsv_stats_bytes(ctx))
+
+
+def alsv_stats_reset(ctx, stats):
+    _check(load().alsv_stats_reset(ctx, _ptr(stats), _nbytes(stats)), "alsv_stats_reset", ctx)
+
+
+def alsv_stats_accumulate(ctx, stats):
+    _check(load().alsv_stats_accumulate(ctx, _ptr(stats), _nbytes(stats)), "alsv_stats_accumulate", ctx)
+
+
+def alsv_stats_read(ctx, stats, mean=None, var=None) -> int:
+    cnt = C.c_int64()
+    _check(load().alsv_stats_read(ctx, _ptr(stats), _ptr(mean), _ptr(var), C.byref(cnt)), "alsv_stats_read", ctx)
+    return cnt.value
+
+
+def alsv_conservation_totals(ctx, totals):
+    _check(load().alsv_conservation_totals(ctx, _ptr(totals)), "alsv_conservation_totals", ctx)
+
+
+def alsv_kinetic_energy(ctx, ke):
+    _check(load().alsv_kinetic_energy(ctx, _ptr(ke)), "alsv_kinetic_energy", ctx)
+
+
+def alsv_adjoint_workspace_bytes(ctx, T: float) -> int:
+    b = C.c_size_t()
+    _check(load().alsv_adjoint_workspace_bytes(ctx, T, C.byref(b)), "alsv_adjoint_workspace_bytes", ctx)
+    return b.value
+
+
+def alsv_bind_adjoint_workspace(ctx, ws, nbytes: int | None = None):
+    _check(load().alsv_bind_adjoint_workspace(ctx, _ptr(ws), nbytes if nbytes is not None else _nbytes(ws)),
+           "alsv_bind_adjoint_workspace", ctx)
+
+
+def alsv_adjoint_evolve(ctx, T: float, observable: int, theta, grad_theta, J):
+    _check(load().alsv_adjoint_evolve(ctx, T, observable, _ptr(theta), _ptr(grad_theta), _ptr(J)),
+           "alsv_adjoint_evolve", ctx)
+
+
+def alsv_destroy(ctx):
+    if ctx:
+        load().alsv_destroy(ctx)
+
+
+def alsv_num_tile_variants(ctx) -> int:
+    return int(load().alsv_num_tile_variants(ctx))
+
+
+def alsv_set_tile_variant(ctx, v: int):
+    _check(load().alsv_set_tile_variant(ctx, v), "alsv_set_tile_variant", ctx)
+
+
+def alsv_get_tile(ctx):
+    tx, ty, tz, v = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+    w = C.c_int64()
+    _check(load().alsv_get_tile(ctx, C.byref(tx), C.byref(ty), C.byref(tz), C.byref(v), C.byref(w)),
+           "alsv_get_tile", ctx)
+    return (tx.value, ty.value, tz.value), v.value, w.value
+
+
+def alsv_autotune(ctx, reps: int = 3):
+    n = alsv_num_tile_variants(ctx)
+    ms = (C.c_float * max(n, 1))()
+    ch = C.c_int()
+    _check(load().alsv_autotune(ctx, reps, C.byref(ch), ms), "alsv_autotune", ctx)
+    return ch.value, [ms[i] for i in range(n)]
+
+
+def alsv_set_graphs(ctx, on: bool):
+    _check(load().alsv_set_graphs(ctx, 1 if on else 0), "alsv_set_graphs", ctx)
+
+
+def alsv_set_profiling(ctx, on: bool):
+    _check(load().alsv_set_profiling(ctx, 1 if on else 0), "alsv_set_profiling", ctx)
+
+
+def alsv_get_profile(ctx):
+    sm, fm = C.c_double(), C.c_double()
+    sl, fl = C.c_int64(), C.c_int64()
+    _check(load().alsv_get_profile(ctx, C.byref(sm), C.byref(sl), C.byref(fm), C.byref(fl)), "alsv_get_profile", ctx)
+    return {"stage_ms": sm.value, "stage_launches": sl.value, "finish_ms": fm.value, "finish_launches": fl.value}
+
+
+def alsv_get_launch_count(ctx) -> int:
+    n = C.c_int64()
+    _check(load().alsv_get_launch_count(ctx, C.byref(n)), "alsv_get_launch_count", ctx)
+    return n.value

@@ -1,0 +1,843 @@
+// Host side of the C ABI declared in include/alsv.h: descriptor validation, workspace layout,
+// the step sequence of eq. (2.1) with SSP-RK stages (Sec. 2.1), CUDA-graph step chunks, Monte
+// Carlo statistics (Sec. 2.2) and fixed-order reductions. Device memory is caller-owned; this file
+// never allocates device memory.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/alsv.h"
+#include "alsv_internal.h"
+
+using namespace alsv;
+
+namespace {
+
+thread_local std::string g_init_error;
+
+struct Profile {
+    bool on = false;
+    double stage_ms = 0.0, finish_ms = 0.0;
+    long long stage_launches = 0, finish_launches = 0;
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> kinds;  // 0 stage, 1 finish; kinds[i] is the kernel between ev[i] and ev[i+1]
+};
+
+}  // namespace
+
+struct alsv_ctx {
+    alsv_grid_desc d;
+    cudaStream_t stream = nullptr;
+    int fp64 = 0, ndim = 1, nv = 1, eq = 1, G = 2, nstages = 2;
+    int variant = 0;
+    GridArgs g;
+    int total_samples = 0;
+    long long max_work = 0;  // largest work-item count over the tile variants
+    size_t state_bytes = 0, ws_bytes = 0;
+    int P = 0;               // KH parameters per sample
+    // workspace regions
+    char* ws = nullptr;
+    void* A = nullptr;
+    void* Bb = nullptr;
+    double* part = nullptr;
+    double* t = nullptr;
+    double* dt = nullptr;
+    int64_t* nstep = nullptr;
+    int* done = nullptr;
+    int* last = nullptr;
+    int* status = nullptr;
+    double* T_end = nullptr;
+    long long* n_target = nullptr;
+    double* theta = nullptr;
+    double* red = nullptr;
+    // state
+    void* U = nullptr;
+    bool time_ready = false;
+    // graph cache
+    cudaGraphExec_t gexec = nullptr;
+    void* g_U = nullptr;
+    int g_variant = -1;
+    int g_steps = 0;
+    bool graphs_enabled = true;
+    // host staging
+    std::vector<int> h_done;
+    long long launches = 0;
+    Profile prof;
+    std::string err;
+    // adjoint workspace (caller-owned)
+    char* adj_ws = nullptr;
+    size_t adj_bytes = 0;
+    bool have_theta = false;
+};
+
+namespace {
+
+alsv_status fail(alsv_ctx* c, alsv_status st, const std::string& msg) {
+    if (c) c->err = msg;
+    else g_init_error = msg;
+    return st;
+}
+
+alsv_status cuda_fail(alsv_ctx* c, cudaError_t e, const char* what) {
+    return fail(c, ALSV_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(expr)                                                           \
+    do {                                                                   \
+        cudaError_t _e = (expr);                                           \
+        if (_e != cudaSuccess) return cuda_fail(c, _e, #expr);             \
+    } while (0)
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Build the per-level tiling for one tile variant.
+long long build_levels(const alsv_ctx* c, int variant, GridArgs& g) {
+    TileShape ts = stage_tile(c->fp64, c->ndim, variant);
+    long long work = 0, elem = 0;
+    int s0 = 0;
+    for (int l = 0; l < g.nlev; ++l) {
+        LevelInfo& L = g.lev[l];
+        const int t[3] = {ts.tx, ts.ty, ts.tz};
+        L.tiles = 1;
+        for (int k = 0; k < 3; ++k) {
+            L.ntile[k] = k < c->ndim ? (L.n[k] + t[k] - 1) / t[k] : 1;
+            L.tiles *= L.ntile[k];
+        }
+        L.sample0 = s0;
+        L.elem0 = elem;
+        L.work0 = work;
+        s0 += L.samples;
+        elem += (long long)L.samples * c->nv * L.n[0] * L.n[1] * L.n[2];
+        work += (long long)L.samples * L.tiles;
+    }
+    g.total_work = work;
+    return work;
+}
+
+alsv_status require_ready(alsv_ctx* c, bool need_state = true) {
+    if (!c) return fail(nullptr, ALSV_ERR_INVALID_ARG, "null context");
+    if (!c->ws) return fail(c, ALSV_ERR_NOT_READY, "workspace not bound (alsv_bind_workspace)");
+    if (need_state && !c->U) return fail(c, ALSV_ERR_NOT_READY, "no state bound (alsv_set_initial_data)");
+    return ALSV_OK;
+}
+
+StageArgs stage_args(alsv_ctx* c, const void* Us, const void* Un, void* Uout, double a, double b, bool want_speed) {
+    StageArgs s;
+    s.g = c->g;
+    s.Us = Us;
+    s.Un = Un;
+    s.Uout = Uout;
+    s.a = a;
+    s.b = b;
+    s.dt = c->dt;
+    s.done = c->done;
+    s.speed_part = c->part;
+    s.want_speed = want_speed ? 1 : 0;
+    return s;
+}
+
+FinishArgs finish_args(alsv_ctx* c, int advance) {
+    FinishArgs f;
+    f.g = c->g;
+    f.speed_part = c->part;
+    f.t = c->t;
+    f.dt = c->dt;
+    f.nstep = c->nstep;
+    f.done = c->done;
+    f.last = c->last;
+    f.status = c->status;
+    f.T_end = c->T_end;
+    f.n_target = c->n_target;
+    f.cfl = c->d.cfl;
+    f.fixed_dt = c->d.fixed_dt;
+    f.cfl_guard = 0.5;
+    f.advance = advance;
+    return f;
+}
+
+void prof_mark(alsv_ctx* c, int kind_next) {
+    if (!c->prof.on) return;
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    cudaEventRecord(e, c->stream);
+    c->prof.ev.push_back(e);
+    if (kind_next >= 0) c->prof.kinds.push_back(kind_next);
+}
+
+void prof_collect(alsv_ctx* c) {
+    Profile& p = c->prof;
+    if (p.ev.empty()) return;
+    cudaEventSynchronize(p.ev.back());
+    for (size_t i = 0; i + 1 < p.ev.size() && i < p.kinds.size(); ++i) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, p.ev[i], p.ev[i + 1]);
+        if (p.kinds[i] == 0) { p.stage_ms += ms; p.stage_launches++; }
+        else { p.finish_ms += ms; p.finish_launches++; }
+    }
+    for (auto e : p.ev) cudaEventDestroy(e);
+    p.ev.clear();
+    p.kinds.clear();
+}
+
+// Enqueue one full SSP-RK step: stages + per-sample time control.
+alsv_status enqueue_step(alsv_ctx* c) {
+    const double third = 1.0 / 3.0, two_third = 2.0 / 3.0;
+    struct St { const void* Us; const void* Un; void* Uo; double a, b; };
+    St st[3];
+    int ns = c->nstages;
+    if (ns == 2) {
+        st[0] = {c->U, nullptr, c->A, 0.0, 1.0};
+        st[1] = {c->A, c->U, c->U, 0.5, 0.5};
+    } else {
+        st[0] = {c->U, nullptr, c->A, 0.0, 1.0};
+        st[1] = {c->A, c->U, c->Bb, 0.75, 0.25};
+        st[2] = {c->Bb, c->U, c->U, third, two_third};
+    }
+    for (int k = 0; k < ns; ++k) {
+        StageArgs a = stage_args(c, st[k].Us, st[k].Un, st[k].Uo, st[k].a, st[k].b, k == ns - 1);
+        if (c->prof.on && c->prof.ev.empty()) prof_mark(c, -1);
+        if (c->prof.on) c->prof.kinds.push_back(0);
+        cudaError_t e = launch_stage(c->fp64, c->ndim, c->eq, c->d.recon, c->d.flux, c->variant, a, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "stage kernel launch");
+        prof_mark(c, -1);
+        c->launches++;
+    }
+    FinishArgs f = finish_args(c, 1);
+    if (c->prof.on) c->prof.kinds.push_back(1);
+    cudaError_t e = launch_finish(f, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "finish kernel launch");
+    prof_mark(c, -1);
+    c->launches++;
+    return ALSV_OK;
+}
+
+alsv_status enqueue_speed_and_prepare(alsv_ctx* c) {
+    cudaError_t e = launch_speed(c->fp64, c->ndim, c->eq, c->variant, c->g, c->U, c->part, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "speed kernel launch");
+    FinishArgs f = finish_args(c, 0);
+    e = launch_finish(f, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "finish kernel launch");
+    c->launches += 2;
+    return ALSV_OK;
+}
+
+alsv_status read_status(alsv_ctx* c, int* st_host) {
+    CK(cudaMemcpyAsync(st_host, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return ALSV_OK;
+}
+
+alsv_status status_to_code(alsv_ctx* c, int st) {
+    if (st & ST_NONPHYSICAL) return fail(c, ALSV_ERR_NONPHYSICAL, "a sample reached a non-physical state (rho<=0, p<=0 or non-finite)");
+    if (st & ST_CFL) return fail(c, ALSV_ERR_CFL, "fixed-dt mode: realised CFL number above the guard 0.5");
+    if (st & ST_TIMEOUT) return fail(c, ALSV_ERR_TIMEOUT, "a bounded device wait timed out");
+    return ALSV_OK;
+}
+
+void drop_graph(alsv_ctx* c) {
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+    c->g_U = nullptr;
+    c->g_variant = -1;
+    c->g_steps = 0;
+}
+
+// Make sure the dynamic shared-memory attribute of the selected stage kernel is set before a
+// capture (the launcher sets it on first use; total_work = 0 launches nothing).
+void touch_kernels(alsv_ctx* c) {
+    StageArgs a = stage_args(c, c->U, c->U, c->A, 0.0, 1.0, false);
+    a.g.total_work = 0;
+    launch_stage(c->fp64, c->ndim, c->eq, c->d.recon, c->d.flux, c->variant, a, c->stream);
+}
+
+alsv_status capture_chunk(alsv_ctx* c, int steps) {
+    drop_graph(c);
+    touch_kernels(c);
+    cudaGraph_t graph;
+    cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        c->graphs_enabled = false;  // e.g. the legacy default stream cannot be captured
+        return ALSV_OK;
+    }
+    long long l0 = c->launches;
+    alsv_status st = ALSV_OK;
+    for (int i = 0; i < steps && st == ALSV_OK; ++i) st = enqueue_step(c);
+    e = cudaStreamEndCapture(c->stream, &graph);
+    c->launches = l0;
+    if (st != ALSV_OK) return st;
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&c->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
+    c->g_U = c->U;
+    c->g_variant = c->variant;
+    c->g_steps = steps;
+    return ALSV_OK;
+}
+
+alsv_status run_chunk(alsv_ctx* c, int steps) {
+    if (c->graphs_enabled && !c->prof.on) {
+        if (!c->gexec || c->g_U != c->U || c->g_variant != c->variant || c->g_steps != steps) {
+            alsv_status st = capture_chunk(c, steps);
+            if (st != ALSV_OK) return st;
+        }
+        if (c->gexec) {
+            CK(cudaGraphLaunch(c->gexec, c->stream));
+            c->launches += (long long)steps * (c->nstages + 1);
+            return ALSV_OK;
+        }
+    }
+    for (int i = 0; i < steps; ++i) {
+        alsv_status st = enqueue_step(c);
+        if (st != ALSV_OK) return st;
+    }
+    return ALSV_OK;
+}
+
+}  // namespace
+
+// =============================================================================================
+// Tile table
+// =============================================================================================
+namespace alsv {
+TileShape stage_tile(int fp64, int ndim, int variant) {
+    if (ndim == 1) return {256, 1, 1, 256};
+    if (ndim == 2) return variant == 1 ? TileShape{32, 8, 1, 256} : TileShape{32, 16, 1, 256};
+    if (fp64) return variant == 1 ? TileShape{8, 8, 4, 256} : TileShape{8, 8, 8, 256};
+    return variant == 1 ? TileShape{8, 8, 8, 256} : TileShape{16, 8, 8, 256};
+}
+int stage_num_variants(int fp64, int ndim) {
+    (void)fp64;
+    return ndim == 1 ? 1 : 2;
+}
+}  // namespace alsv
+
+// =============================================================================================
+// C ABI
+// =============================================================================================
+extern "C" {
+
+const char* alsv_version(void) { return "alsv 0.1 (sm_103a finite-volume MC solver)"; }
+
+const char* alsv_last_error(const alsv_ctx* c) {
+    if (!c) return g_init_error.c_str();
+    return c->err.c_str();
+}
+
+alsv_status alsv_init_grid(const alsv_grid_desc* d_in, void* stream, alsv_ctx** out, size_t* workspace_bytes) {
+    if (!d_in || !out) return fail(nullptr, ALSV_ERR_INVALID_ARG, "null descriptor or output pointer");
+    *out = nullptr;
+    alsv_grid_desc d = *d_in;
+    auto bad = [](const std::string& m) { return fail(nullptr, ALSV_ERR_INVALID_ARG, m); };
+    if (d.ndim < 1 || d.ndim > 3) return bad("ndim must be 1, 2 or 3");
+    if (d.eq != ALSV_EQ_BURGERS && d.eq != ALSV_EQ_EULER) return bad("eq must be BURGERS or EULER");
+    if (d.recon < 0 || d.recon > 2) return bad("recon must be PC, MC or WENO3");
+    if (d.recon_vars != ALSV_VARS_CONS && d.recon_vars != ALSV_VARS_PRIM) return bad("recon_vars must be CONS or PRIM");
+    if (d.flux < 0 || d.flux > 2) return bad("flux must be RUSANOV, HLL or HLLC");
+    if (d.rk != ALSV_RK_SSP2 && d.rk != ALSV_RK_SSP3) return bad("rk must be SSP2 or SSP3");
+    if (d.precision != ALSV_FP32 && d.precision != ALSV_FP64) return bad("precision must be FP32 or FP64");
+    if (d.eq == ALSV_EQ_EULER && !(d.gamma > 1.0)) return bad("gamma must be > 1");
+    if (!(d.cfl > 0.0) && !(d.fixed_dt > 0.0)) return bad("cfl must be > 0 (or fixed_dt > 0)");
+    if (d.fixed_dt < 0.0 || !std::isfinite(d.fixed_dt)) return bad("fixed_dt must be >= 0 and finite");
+    if (d.weno_eps == 0.0) d.weno_eps = 1e-6;
+    if (!(d.weno_eps > 0.0)) return bad("weno_eps must be > 0");
+    for (int k = 0; k < 8; ++k)
+        if (d.reserved[k] != 0) return bad("reserved fields must be zero");
+    for (int k = 0; k < d.ndim; ++k)
+        if (!(d.hi[k] > d.lo[k])) return bad("hi must exceed lo in every active direction");
+    const int G = d.recon == ALSV_RECON_PC ? 1 : 2;
+    for (int k = 0; k < 3; ++k)
+        for (int s = 0; s < 2; ++s)
+            if (d.bc[k][s] < 0 || d.bc[k][s] > 2) return bad("bc must be PERIODIC, OUTFLOW or REFLECTIVE");
+    for (int k = 0; k < d.ndim; ++k)
+        if ((d.bc[k][0] == ALSV_BC_PERIODIC) != (d.bc[k][1] == ALSV_BC_PERIODIC))
+            return bad("a periodic side must be paired with a periodic side");
+
+    auto* c = new alsv_ctx();
+    c->d = d;
+    c->stream = (cudaStream_t)stream;
+    c->fp64 = d.precision == ALSV_FP64;
+    c->ndim = d.ndim;
+    c->eq = d.eq;
+    c->nv = d.eq == ALSV_EQ_BURGERS ? 1 : d.ndim + 2;
+    c->G = G;
+    c->nstages = d.rk == ALSV_RK_SSP3 ? 3 : 2;
+    GridArgs& g = c->g;
+    std::memset(&g, 0, sizeof(g));
+    g.ndim = d.ndim;
+    for (int k = 0; k < 3; ++k) g.lo[k] = d.lo[k];
+    const int nlev = d.n_levels <= 1 ? 1 : d.n_levels;
+    if (nlev > ALSV_MAX_LEVELS) { delete c; return bad("n_levels must be <= 8"); }
+    g.nlev = nlev;
+    long long samples = 0;
+    for (int l = 0; l < nlev; ++l) {
+        LevelInfo& L = g.lev[l];
+        const int* n = d.n_levels <= 1 ? d.n : d.level_n[l];
+        L.samples = d.n_levels <= 1 ? d.batch : d.level_batch[l];
+        if (L.samples < 1) { delete c; return bad("batch (samples per level) must be >= 1"); }
+        for (int k = 0; k < 3; ++k) {
+            L.n[k] = k < d.ndim ? n[k] : 1;
+            if (L.n[k] < 1) { delete c; return bad("every active direction needs n >= 1"); }
+            if (k < d.ndim && (d.bc[k][0] == ALSV_BC_REFLECTIVE || d.bc[k][1] == ALSV_BC_REFLECTIVE) && L.n[k] < G) {
+                delete c;
+                return bad("reflective boundaries need at least as many cells as ghost layers");
+            }
+            L.dx[k] = k < d.ndim ? (d.hi[k] - d.lo[k]) / L.n[k] : 1.0;
+            L.inv_dx[k] = 1.0 / L.dx[k];
+        }
+        samples += L.samples;
+    }
+    if (samples > 65535) { delete c; return bad("at most 65535 samples per context"); }
+    c->total_samples = (int)samples;
+    g.total_samples = (int)samples;
+    g.nv = c->nv;
+    g.gamma = d.gamma;
+    g.rvars = d.eq == ALSV_EQ_EULER ? d.recon_vars : ALSV_VARS_CONS;
+    for (int k = 0; k < 3; ++k) {
+        g.bc[k][0] = d.bc[k][0];
+        g.bc[k][1] = d.bc[k][1];
+    }
+    g.weno_eps = d.weno_eps;
+    g.weno_eps_dx2 = d.weno_eps_dx2;
+    // tiling: keep the largest work count over variants for the partials buffer
+    long long mx = 0;
+    for (int v = 0; v < stage_num_variants(c->fp64, c->ndim); ++v) {
+        GridArgs tmp = g;
+        mx = std::max(mx, build_levels(c, v, tmp));
+    }
+    build_levels(c, 0, g);
+    if (mx > INT_MAX) { delete c; return bad("too many tiles for one launch"); }
+    c->max_work = mx;
+    const size_t esz = c->fp64 ? 8 : 4;
+    long long elems = 0;
+    for (int l = 0; l < nlev; ++l) elems += (long long)g.lev[l].samples * c->nv * g.lev[l].n[0] * g.lev[l].n[1] * g.lev[l].n[2];
+    c->state_bytes = (size_t)elems * esz;
+    c->P = d.eq == ALSV_EQ_EULER ? (d.ndim == 3 ? 128 : (d.ndim == 2 ? 20 : 0)) : 0;
+    size_t ws = 0;
+    ws += align256(c->state_bytes);                               // A
+    if (c->nstages == 3) ws += align256(c->state_bytes);          // B
+    ws += align256((size_t)mx * 8);                               // partials
+    ws += 3 * align256((size_t)samples * 8);                      // t, dt, nstep
+    ws += 2 * align256((size_t)samples * 4);                      // done, last
+    ws += 256;                                                    // status
+    ws += 256;                                                    // T_end + n_target
+    ws += align256((size_t)samples * std::max(c->P, 1) * 8);      // theta
+    ws += align256((size_t)reduce_partial_count(g) * 8);          // reduction partials
+    c->ws_bytes = ws;
+    c->h_done.resize(samples);
+    if (workspace_bytes) *workspace_bytes = ws;
+    *out = c;
+    return ALSV_OK;
+}
+
+alsv_status alsv_bind_workspace(alsv_ctx* c, void* dev, size_t bytes) {
+    if (!c) return fail(nullptr, ALSV_ERR_INVALID_ARG, "null context");
+    if (!dev) return fail(c, ALSV_ERR_INVALID_ARG, "null workspace pointer");
+    if (((uintptr_t)dev & 255) != 0) return fail(c, ALSV_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    if (bytes < c->ws_bytes) return fail(c, ALSV_ERR_BUFFER_TOO_SMALL, "workspace smaller than alsv_init_grid reported");
+    drop_graph(c);
+    char* p = (char*)dev;
+    const size_t S = c->total_samples;
+    c->ws = p;
+    c->A = p; p += align256(c->state_bytes);
+    if (c->nstages == 3) { c->Bb = p; p += align256(c->state_bytes); }
+    c->part = (double*)p; p += align256((size_t)c->max_work * 8);
+    c->t = (double*)p; p += align256(S * 8);
+    c->dt = (double*)p; p += align256(S * 8);
+    c->nstep = (int64_t*)p; p += align256(S * 8);
+    c->done = (int*)p; p += align256(S * 4);
+    c->last = (int*)p; p += align256(S * 4);
+    c->status = (int*)p; p += 256;
+    c->T_end = (double*)p;
+    c->n_target = (long long*)(p + 8); p += 256;
+    c->theta = (double*)p; p += align256(S * std::max(c->P, 1) * 8);
+    c->red = (double*)p;
+    c->time_ready = false;
+    return ALSV_OK;
+}
+
+size_t alsv_state_bytes(const alsv_ctx* c) { return c ? c->state_bytes : 0; }
+
+alsv_status alsv_get_parameters(alsv_ctx* c, double* theta_dev) {
+    alsv_status st = require_ready(c, false);
+    if (st != ALSV_OK) return st;
+    if (!theta_dev) return fail(c, ALSV_ERR_INVALID_ARG, "null output buffer");
+    if (!c->have_theta || c->P == 0) return fail(c, ALSV_ERR_NOT_READY, "no KH parameters set");
+    CK(cudaMemcpyAsync(theta_dev, c->theta, (size_t)c->total_samples * c->P * 8, cudaMemcpyDeviceToDevice, c->stream));
+    return ALSV_OK;
+}
+int32_t alsv_num_samples(const alsv_ctx* c) { return c ? c->total_samples : 0; }
+int32_t alsv_num_vars(const alsv_ctx* c) { return c ? c->nv : 0; }
+
+static alsv_status set_run_params(alsv_ctx* c, double T, long long n_target) {
+    double hv[2];
+    hv[0] = T;
+    std::memcpy(&hv[1], &n_target, 8);
+    CK(cudaMemcpyAsync(c->T_end, hv, 16, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));  // hv lives on this stack frame
+    return ALSV_OK;
+}
+
+alsv_status alsv_set_initial_data(alsv_ctx* c, int kind, const double* theta_dev, int n_params, void* U_dev,
+                                  size_t U_bytes) {
+    alsv_status st = require_ready(c, false);
+    if (st != ALSV_OK) return st;
+    if (!U_dev) return fail(c, ALSV_ERR_INVALID_ARG, "null state pointer");
+    if (((uintptr_t)U_dev & 15) != 0) return fail(c, ALSV_ERR_INVALID_ARG, "state must be 16-byte aligned");
+    if (U_bytes < c->state_bytes) return fail(c, ALSV_ERR_BUFFER_TOO_SMALL, "state buffer smaller than alsv_state_bytes");
+    if (kind < ALSV_INIT_KH || kind > ALSV_INIT_RAW) return fail(c, ALSV_ERR_INVALID_ARG, "unknown initial-data kind");
+    if (kind == ALSV_INIT_KH && (c->eq != ALSV_EQ_EULER || c->ndim < 2))
+        return fail(c, ALSV_ERR_INVALID_ARG, "KH initial data needs 2D or 3D Euler");
+    if ((kind == ALSV_INIT_SOD || kind == ALSV_INIT_LAX) && c->eq != ALSV_EQ_EULER)
+        return fail(c, ALSV_ERR_INVALID_ARG, "shock tubes need Euler");
+    if (kind == ALSV_INIT_BURGERS_SINE && c->eq != ALSV_EQ_BURGERS)
+        return fail(c, ALSV_ERR_INVALID_ARG, "sine initial data needs Burgers");
+    if (kind == ALSV_INIT_VORTEX && (c->eq != ALSV_EQ_EULER || c->ndim != 2))
+        return fail(c, ALSV_ERR_INVALID_ARG, "the vortex needs 2D Euler");
+    c->U = U_dev;
+    if (kind == ALSV_INIT_KH) {
+        const double* th = theta_dev;
+        if (!th) {
+            cudaError_t e = launch_theta(c->d.seed, c->total_samples, c->P, c->theta, c->stream);
+            if (e != cudaSuccess) return cuda_fail(c, e, "theta kernel");
+            th = c->theta;
+        } else if (n_params != c->P) {
+            return fail(c, ALSV_ERR_INVALID_ARG, "n_params must be 20 (2D KH) or 128 (3D KH)");
+        }
+        InitArgs a;
+        a.g = c->g;
+        a.U = U_dev;
+        a.kind = 0;
+        a.theta = th;
+        a.P = c->P;
+        cudaError_t e = launch_init(c->fp64, c->ndim, a, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
+        if (th != c->theta)
+            CK(cudaMemcpyAsync(c->theta, th, (size_t)c->total_samples * c->P * 8, cudaMemcpyDeviceToDevice, c->stream));
+        c->have_theta = true;
+    } else if (kind != ALSV_INIT_RAW) {
+        InitArgs a;
+        a.g = c->g;
+        a.U = U_dev;
+        a.kind = kind;
+        a.theta = nullptr;
+        a.P = 0;
+        a.vortex_center[0] = c->d.vortex_center[0];
+        a.vortex_center[1] = c->d.vortex_center[1];
+        cudaError_t e = launch_init(c->fp64, c->ndim, a, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
+    }
+    const size_t S = c->total_samples;
+    CK(cudaMemsetAsync(c->t, 0, S * 8, c->stream));
+    CK(cudaMemsetAsync(c->nstep, 0, S * 8, c->stream));
+    CK(cudaMemsetAsync(c->done, 0, S * 4, c->stream));
+    CK(cudaMemsetAsync(c->last, 0, S * 4, c->stream));
+    CK(cudaMemsetAsync(c->status, 0, 4, c->stream));
+    st = set_run_params(c, INFINITY, LLONG_MAX);
+    if (st != ALSV_OK) return st;
+    st = enqueue_speed_and_prepare(c);
+    if (st != ALSV_OK) return st;
+    c->time_ready = true;
+    return ALSV_OK;
+}
+
+alsv_status alsv_step(alsv_ctx* c, int n_steps) {
+    alsv_status st = require_ready(c);
+    if (st != ALSV_OK) return st;
+    if (n_steps < 0) return fail(c, ALSV_ERR_INVALID_ARG, "n_steps must be >= 0");
+    for (int i = 0; i < n_steps; ++i) {
+        st = enqueue_step(c);
+        if (st != ALSV_OK) return st;
+    }
+    return ALSV_OK;
+}
+
+alsv_status alsv_sync(alsv_ctx* c) {
+    alsv_status st = require_ready(c, false);
+    if (st != ALSV_OK) return st;
+    int hs = 0;
+    st = read_status(c, &hs);
+    if (st != ALSV_OK) return st;
+    prof_collect(c);
+    return status_to_code(c, hs);
+}
+
+alsv_status alsv_evolve_to_T(alsv_ctx* c, double T, int64_t* steps_taken_host) {
+    alsv_status st = require_ready(c);
+    if (st != ALSV_OK) return st;
+    if (!std::isfinite(T) || T < 0.0) return fail(c, ALSV_ERR_INVALID_ARG, "T must be finite and >= 0");
+    long long n_target = LLONG_MAX;
+    if (c->d.fixed_dt > 0.0) n_target = (long long)std::ceil(T / c->d.fixed_dt * (1.0 - 1e-12));
+    st = set_run_params(c, T, n_target);
+    if (st != ALSV_OK) return st;
+    FinishArgs f = finish_args(c, 0);
+    cudaError_t e = launch_finish(f, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "finish kernel launch");
+    c->launches++;
+    const int chunk = 16;
+    const size_t S = c->total_samples;
+    long long chunks = 0;
+    for (;;) {
+        CK(cudaMemcpyAsync(c->h_done.data(), c->done, S * 4, cudaMemcpyDeviceToHost, c->stream));
+        int hs = 0;
+        CK(cudaMemcpyAsync(&hs, c->status, 4, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        prof_collect(c);
+        if (hs & (ST_NONPHYSICAL | ST_CFL)) {
+            st = status_to_code(c, hs);
+            break;
+        }
+        bool all = true;
+        for (size_t i = 0; i < S; ++i) all = all && c->h_done[i];
+        if (all) break;
+        if (++chunks > (1LL << 26)) return fail(c, ALSV_ERR_TIMEOUT, "evolve_to_T: step limit reached");
+        st = run_chunk(c, chunk);
+        if (st != ALSV_OK) return st;
+    }
+    if (steps_taken_host) {
+        std::vector<int64_t> ns(S);
+        CK(cudaMemcpyAsync(ns.data(), c->nstep, S * 8, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        int64_t mx = 0;
+        for (auto v : ns) mx = std::max(mx, v);
+        *steps_taken_host = mx;
+    }
+    return st;
+}
+
+alsv_status alsv_get_time(alsv_ctx* c, double* t_host, int64_t* steps_host) {
+    alsv_status st = require_ready(c, false);
+    if (st != ALSV_OK) return st;
+    const size_t S = c->total_samples;
+    if (t_host) CK(cudaMemcpyAsync(t_host, c->t, S * 8, cudaMemcpyDeviceToHost, c->stream));
+    if (steps_host) CK(cudaMemcpyAsync(steps_host, c->nstep, S * 8, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return ALSV_OK;
+}
+
+size_t alsv_stats_bytes(const alsv_ctx* c) {
+    if (!c) return 0;
+    const LevelInfo& L = c->g.lev[0];
+    const size_t C = (size_t)L.n[0] * L.n[1] * L.n[2];
+    return 256 + 2 * (size_t)c->nv * C * 8;
+}
+
+static alsv_status check_stats(alsv_ctx* c, const void* stats, size_t bytes) {
+    if (!stats) return fail(c, ALSV_ERR_INVALID_ARG, "null statistics buffer");
+    if (((uintptr_t)stats & 255) != 0) return fail(c, ALSV_ERR_INVALID_ARG, "statistics buffer must be 256-byte aligned");
+    if (bytes < alsv_stats_bytes(c)) return fail(c, ALSV_ERR_BUFFER_TOO_SMALL, "statistics buffer smaller than alsv_stats_bytes");
+    if (c->g.nlev != 1) return fail(c, ALSV_ERR_INVALID_ARG, "statistics need a single-level context");
+    return ALSV_OK;
+}
+
+alsv_status alsv_stats_reset(alsv_ctx* c, void* stats_dev, size_t bytes) {
+    if (!c) return fail(nullptr, ALSV_ERR_INVALID_ARG, "null context");
+    alsv_status st = check_stats(c, stats_dev, bytes);
+    if (st != ALSV_OK) return st;
+    CK(cudaMemsetAsync(stats_dev, 0, alsv_stats_bytes(c), c->stream));
+    return ALSV_OK;
+}
+
+alsv_status alsv_stats_accumulate(alsv_ctx* c, void* stats_dev, size_t bytes) {
+    alsv_status st = require_ready(c);
+    if (st != ALSV_OK) return st;
+    st = check_stats(c, stats_dev, bytes);
+    if (st != ALSV_OK) return st;
+    cudaError_t e = launch_welford(c->fp64, c->g, c->U, stats_dev, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "welford kernel");
+    c->launches += 2;
+    return ALSV_OK;
+}
+
+alsv_status alsv_stats_read(alsv_ctx* c, const void* stats_dev, double* mean_dev, double* var_dev, int64_t* count_host) {
+    if (!c) return fail(nullptr, ALSV_ERR_INVALID_ARG, "null context");
+    alsv_status st = check_stats(c, stats_dev, alsv_stats_bytes(c));
+    if (st != ALSV_OK) return st;
+    if (mean_dev || var_dev) {
+        cudaError_t e = launch_stats_read(c->g, stats_dev, mean_dev, var_dev, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "stats read kernel");
+        c->launches++;
+    }
+    if (count_host) {
+        CK(cudaMemcpyAsync(count_host, stats_dev, 8, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    return ALSV_OK;
+}
+
+alsv_status alsv_conservation_totals(alsv_ctx* c, double* totals_dev) {
+    alsv_status st = require_ready(c);
+    if (st != ALSV_OK) return st;
+    if (!totals_dev) return fail(c, ALSV_ERR_INVALID_ARG, "null totals buffer");
+    cudaError_t e = launch_reduce(c->fp64, 0, c->g, c->U, c->red, totals_dev, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "reduction kernel");
+    c->launches += 2;
+    return ALSV_OK;
+}
+
+alsv_status alsv_kinetic_energy(alsv_ctx* c, double* ke_dev) {
+    alsv_status st = require_ready(c);
+    if (st != ALSV_OK) return st;
+    if (!ke_dev) return fail(c, ALSV_ERR_INVALID_ARG, "null output buffer");
+    if (c->eq != ALSV_EQ_EULER) return fail(c, ALSV_ERR_INVALID_ARG, "kinetic energy needs Euler");
+    cudaError_t e = launch_reduce(c->fp64, 1, c->g, c->U, c->red, ke_dev, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "reduction kernel");
+    c->launches += 2;
+    return ALSV_OK;
+}
+
+alsv_status alsv_destroy(alsv_ctx* c) {
+    if (!c) return ALSV_OK;
+    drop_graph(c);
+    for (auto e : c->prof.ev) cudaEventDestroy(e);
+    delete c;
+    return ALSV_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Extensions (declared in alsv_ext.h): tile-shape selection/autotuning, launch counting, profiling
+// ---------------------------------------------------------------------------------------------
+alsv_status alsv_set_tile_variant(alsv_ctx* c, int variant) {
+    if (!c) return fail(nullptr, ALSV_ERR_INVALID_ARG, "null context");
+    if (variant < 0 || variant >= stage_num_variants(c->fp64, c->ndim))
+        return fail(c, ALSV_ERR_INVALID_ARG, "tile variant out of range");
+    if (variant == c->variant) return ALSV_OK;
+    c->variant = variant;
+    build_levels(c, variant, c->g);
+    drop_graph(c);
+    if (c->U && c->ws && c->time_ready) {
+        // partials follow the tiling: recompute them for the current state
+        cudaError_t e = launch_speed(c->fp64, c->ndim, c->eq, c->variant, c->g, c->U, c->part, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "speed kernel launch");
+        c->launches++;
+    }
+    return ALSV_OK;
+}
+
+int alsv_num_tile_variants(const alsv_ctx* c) { return c ? stage_num_variants(c->fp64, c->ndim) : 0; }
+
+alsv_status alsv_autotune(alsv_ctx* c, int reps, int* chosen, float* ms_per_variant) {
+    alsv_status st = require_ready(c);
+    if (st != ALSV_OK) return st;
+    if (reps < 1) reps = 1;
+    const int nvar = stage_num_variants(c->fp64, c->ndim);
+    int best = c->variant;
+    float best_ms = 1e30f;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    for (int v = 0; v < nvar; ++v) {
+        GridArgs g = c->g;
+        const int saved = c->variant;
+        c->variant = v;
+        build_levels(c, v, c->g);
+        // the timed launch is stage 1 (reads U, writes the stage buffer A): the state is unchanged
+        StageArgs a = stage_args(c, c->U, nullptr, c->A, 0.0, 1.0, false);
+        cudaError_t e = launch_stage(c->fp64, c->ndim, c->eq, c->d.recon, c->d.flux, v, a, c->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+        for (int r = 0; r < reps && e == cudaSuccess; ++r)
+            e = launch_stage(c->fp64, c->ndim, c->eq, c->d.recon, c->d.flux, v, a, c->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        c->launches += reps + 1;
+        c->variant = saved;
+        c->g = g;
+        if (e != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return cuda_fail(c, e, "autotune launch");
+        }
+        ms /= reps;
+        if (ms_per_variant) ms_per_variant[v] = ms;
+        if (ms < best_ms) { best_ms = ms; best = v; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (chosen) *chosen = best;
+    return alsv_set_tile_variant(c, best);
+}
+
+alsv_status alsv_get_launch_count(const alsv_ctx* c, int64_t* launches) {
+    if (!c || !launches) return ALSV_ERR_INVALID_ARG;
+    *launches = c->launches;
+    return ALSV_OK;
+}
+
+alsv_status alsv_set_profiling(alsv_ctx* c, int on) {
+    if (!c) return fail(nullptr, ALSV_ERR_INVALID_ARG, "null context");
+    prof_collect(c);
+    c->prof.on = on != 0;
+    c->prof.stage_ms = c->prof.finish_ms = 0.0;
+    c->prof.stage_launches = c->prof.finish_launches = 0;
+    return ALSV_OK;
+}
+
+alsv_status alsv_get_profile(alsv_ctx* c, double* stage_ms, int64_t* stage_launches, double* finish_ms,
+                             int64_t* finish_launches) {
+    if (!c) return fail(nullptr, ALSV_ERR_INVALID_ARG, "null context");
+    prof_collect(c);
+    if (stage_ms) *stage_ms = c->prof.stage_ms;
+    if (stage_launches) *stage_launches = c->prof.stage_launches;
+    if (finish_ms) *finish_ms = c->prof.finish_ms;
+    if (finish_launches) *finish_launches = c->prof.finish_launches;
+    return ALSV_OK;
+}
+
+alsv_status alsv_set_graphs(alsv_ctx* c, int on) {
+    if (!c) return fail(nullptr, ALSV_ERR_INVALID_ARG, "null context");
+    c->graphs_enabled = on != 0;
+    drop_graph(c);
+    return ALSV_OK;
+}
+
+alsv_status alsv_get_tile(const alsv_ctx* c, int* tx, int* ty, int* tz, int* variant, int64_t* work_items) {
+    if (!c) return ALSV_ERR_INVALID_ARG;
+    TileShape t = stage_tile(c->fp64, c->ndim, c->variant);
+    if (tx) *tx = t.tx;
+    if (ty) *ty = t.ty;
+    if (tz) *tz = t.tz;
+    if (variant) *variant = c->variant;
+    if (work_items) *work_items = c->g.total_work;
+    return ALSV_OK;
+}
+
+}  // extern "C"
+
+// Launch dispatch over (precision, ndim) to the per-TU launchers.
+namespace alsv {
+cudaError_t launch_stage_f32_1d(int, int, int, int, const StageArgs&, cudaStream_t);
+cudaError_t launch_stage_f64_1d(int, int, int, int, const StageArgs&, cudaStream_t);
+cudaError_t launch_stage_f32_2d(int, int, int, int, const StageArgs&, cudaStream_t);
+cudaError_t launch_stage_f64_2d(int, int, int, int, const StageArgs&, cudaStream_t);
+cudaError_t launch_stage_f32_3d(int, int, int, int, const StageArgs&, cudaStream_t);
+cudaError_t launch_stage_f64_3d(int, int, int, int, const StageArgs&, cudaStream_t);
+cudaError_t launch_speed_f32_1d(int, int, const GridArgs&, const void*, double*, cudaStream_t);
+cudaError_t launch_speed_f64_1d(int, int, const GridArgs&, const void*, double*, cudaStream_t);
+cudaError_t launch_speed_f32_2d(int, int, const GridArgs&, const void*, double*, cudaStream_t);
+cudaError_t launch_speed_f64_2d(int, int, const GridArgs&, const void*, double*, cudaStream_t);
+cudaError_t launch_speed_f32_3d(int, int, const GridArgs&, const void*, double*, cudaStream_t);
+cudaError_t launch_speed_f64_3d(int, int, const GridArgs&, const void*, double*, cudaStream_t);
+
+cudaError_t launch_stage(int fp64, int ndim, int eq, int recon, int flux, int variant, const StageArgs& a,
+                         cudaStream_t s) {
+    if (ndim == 1) return fp64 ? launch_stage_f64_1d(variant, eq, recon, flux, a, s) : launch_stage_f32_1d(variant, eq, recon, flux, a, s);
+    if (ndim == 2) return fp64 ? launch_stage_f64_2d(variant, eq, recon, flux, a, s) : launch_stage_f32_2d(variant, eq, recon, flux, a, s);
+    return fp64 ? launch_stage_f64_3d(variant, eq, recon, flux, a, s) : launch_stage_f32_3d(variant, eq, recon, flux, a, s);
+}
+
+cudaError_t launch_speed(int fp64, int ndim, int eq, int variant, const GridArgs& g, const void* U, double* part,
+                         cudaStream_t s) {
+    if (ndim == 1) return fp64 ? launch_speed_f64_1d(variant, eq, g, U, part, s) : launch_speed_f32_1d(variant, eq, g, U, part, s);
+    if (ndim == 2) return fp64 ? launch_speed_f64_2d(variant, eq, g, U, part, s) : launch_speed_f32_2d(variant, eq, g, U, part, s);
+    return fp64 ? launch_speed_f64_3d(variant, eq, g, U, part, s) : launch_speed_f32_3d(variant, eq, g, U, part, s);
+}
+}  // namespace alsv

@@ -1,0 +1,115 @@
+// Internal declarations shared by the host API (alsv_api.cu) and the kernel translation units.
+// Not part of the public ABI (include/alsv.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace alsv {
+
+enum { EQ_BURGERS = 0, EQ_EULER = 1 };
+enum { REC_PC = 0, REC_MC = 1, REC_WENO3 = 2 };
+enum { RV_CONS = 0, RV_PRIM = 1 };
+enum { FLX_RUSANOV = 0, FLX_HLL = 1, FLX_HLLC = 2 };
+enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_REFLECTIVE = 2 };
+
+// Device status bits (OR-ed into the status word by kernels; kernels never trap).
+enum { ST_NONPHYSICAL = 1, ST_CFL = 2, ST_TIMEOUT = 4 };
+
+constexpr int kMaxLevels = 8;
+
+// One grid of an MLMC level table (a single-grid context has one level).
+struct LevelInfo {
+    int n[3];          // cells per direction
+    int ntile[3];      // tiles per direction for the launched tile shape
+    int tiles;         // tiles per sample
+    int samples;       // samples on this level
+    int sample0;       // global index of the level's first sample
+    long long elem0;   // element offset of the level's first sample in U
+    long long work0;   // first (sample, tile) work item of the level
+    double dx[3];
+    double inv_dx[3];
+};
+
+struct GridArgs {
+    int ndim;
+    double lo[3];      // domain origin (all levels share the domain box)
+    int nlev;
+    LevelInfo lev[kMaxLevels];
+    long long total_work;  // sum over levels of samples * tiles
+    int total_samples;
+    int nv;
+    double gamma;
+    int rvars;
+    int bc[3][2];
+    double weno_eps;
+    int weno_eps_dx2;
+};
+
+// One SSP-RK stage: Uout = a * Un + b * (Us + dt * L(Us)); a == 0 means Un is not read.
+struct StageArgs {
+    GridArgs g;
+    const void* Us;
+    const void* Un;
+    void* Uout;
+    double a, b;
+    const double* dt;     // [samples]
+    const int* done;      // [samples]; nonzero: the sample is skipped
+    double* speed_part;   // [work items]; written when want_speed
+    int want_speed;
+};
+
+// Tile shape used for a given (precision, ndim); the host derives the tiling from it.
+struct TileShape {
+    int tx, ty, tz, threads;
+};
+TileShape stage_tile(int fp64, int ndim, int variant);
+int stage_num_variants(int fp64, int ndim);
+
+// Launchers (return cudaGetLastError of the launch).
+cudaError_t launch_stage(int fp64, int ndim, int eq, int recon, int flux, int variant, const StageArgs& a,
+                         cudaStream_t s);
+cudaError_t launch_speed(int fp64, int ndim, int eq, int variant, const GridArgs& g, const void* U,
+                         double* speed_part, cudaStream_t s);
+
+struct FinishArgs {
+    GridArgs g;
+    const double* speed_part;
+    double* t;
+    double* dt;
+    int64_t* nstep;
+    int* done;
+    int* last;
+    int* status;
+    const double* T_end;   // device scalar: end time of the current run
+    const long long* n_target;  // device scalar: fixed mode, steps to take from the start
+    double cfl;
+    double fixed_dt;       // > 0: fixed mode
+    double cfl_guard;      // fixed mode: realised CFL limit
+    int advance;           // 1: the step just finished (advance t); 0: only prepare dt
+};
+cudaError_t launch_finish(const FinishArgs& a, cudaStream_t s);
+
+// Initial data. theta: [samples][P] FP64 (device) or NULL.
+struct InitArgs {
+    GridArgs g;
+    void* U;
+    int kind;
+    const double* theta;
+    int P;
+    double vortex_center[2];
+};
+cudaError_t launch_init(int fp64, int ndim, const InitArgs& a, cudaStream_t s);
+cudaError_t launch_theta(uint64_t seed, int samples, int P, double* theta, cudaStream_t s);
+
+// Monte Carlo statistics (single level).
+cudaError_t launch_welford(int fp64, const GridArgs& g, const void* U, void* stats, cudaStream_t s);
+cudaError_t launch_stats_read(const GridArgs& g, const void* stats, double* mean, double* var, cudaStream_t s);
+
+// Fixed-order FP64 reductions: out[sample][var] totals (kind 0) or out[sample] KE (kind 1).
+// partial: scratch of reduce_partial_count(g) doubles.
+long long reduce_partial_count(const GridArgs& g);
+cudaError_t launch_reduce(int fp64, int kind, const GridArgs& g, const void* U, double* partial, double* out,
+                          cudaStream_t s);
+
+}  // namespace alsv

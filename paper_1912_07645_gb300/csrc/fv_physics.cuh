@@ -1,0 +1,229 @@
+// Device-side physics of the finite-volume step (Sec. 2.1, eq. (2.1)): state conversions,
+// per-face reconstruction and numerical fluxes, templated on the arithmetic type R.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "alsv_internal.h"
+
+namespace alsv {
+
+template <class R> __device__ __forceinline__ R rcp(R x) { return R(1) / x; }
+template <class R> __device__ __forceinline__ R rsqrt_(R x);
+template <> __device__ __forceinline__ float rsqrt_(float x) { return sqrtf(x); }
+template <> __device__ __forceinline__ double rsqrt_(double x) { return sqrt(x); }
+template <class R> __device__ __forceinline__ R fabs_(R x) { return x < R(0) ? -x : x; }
+// ties keep the first argument (same convention as the selection rules of the fluxes)
+template <class R> __device__ __forceinline__ R fmax_(R a, R b) { return b > a ? b : a; }
+template <class R> __device__ __forceinline__ R fmin_(R a, R b) { return b < a ? b : a; }
+
+// ---------------------------------------------------------------------------------------------
+// Ideal gas: p = (gamma - 1) (E - |m|^2 / (2 rho)); E = p / (gamma - 1) + rho |u|^2 / 2.
+// Primitive layout: [rho, u_0 .. u_{ND-1}, p].
+// ---------------------------------------------------------------------------------------------
+template <class R, int ND>
+__device__ __forceinline__ void cons_to_prim(const R* U, R* W, R gm1) {
+    const R rho = U[0];
+    const R inv = rcp(rho);
+    R m2 = U[1] * U[1];
+#pragma unroll
+    for (int k = 1; k < ND; ++k) m2 = m2 + U[1 + k] * U[1 + k];
+    W[0] = rho;
+#pragma unroll
+    for (int k = 0; k < ND; ++k) W[1 + k] = U[1 + k] * inv;
+    W[ND + 1] = gm1 * (U[ND + 1] - R(0.5) * m2 * inv);
+}
+
+template <class R, int ND>
+__device__ __forceinline__ void prim_to_cons(const R* W, R* U, R inv_gm1) {
+    const R rho = W[0];
+    R u2 = W[1] * W[1];
+#pragma unroll
+    for (int k = 1; k < ND; ++k) u2 = u2 + W[1 + k] * W[1 + k];
+    U[0] = rho;
+#pragma unroll
+    for (int k = 0; k < ND; ++k) U[1 + k] = rho * W[1 + k];
+    U[ND + 1] = W[ND + 1] * inv_gm1 + R(0.5) * rho * u2;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Reconstruction (Sec. 2.1: WENO after Shu 1999; MC-limited linear; piecewise constant).
+// face_r: value at i+1/2 from cell i; face_l: value at i-1/2 from cell i. Stencil (wm, w0, wp).
+// ---------------------------------------------------------------------------------------------
+template <class R> __device__ __forceinline__ R minmod3(R a, R b, R c) {
+    if (a > R(0) && b > R(0) && c > R(0)) return fmin_(fmin_(a, b), c);
+    if (a < R(0) && b < R(0) && c < R(0)) return fmax_(fmax_(a, b), c);
+    return R(0);
+}
+
+template <class R> __device__ __forceinline__ R mc_slope(R wm, R w0, R wp) {
+    const R dm = w0 - wm, dp = wp - w0;
+    return minmod3(R(2) * dm, R(0.5) * (dm + dp), R(2) * dp);
+}
+
+// Jiang-Shu WENO3 face value from candidates p0 (stencil {far, 0}) and p1 ({0, near}) with
+// linear weights 1/3, 2/3 and alpha_r = d_r / (eps + beta_r)^2, evaluated with one division:
+// (d0 q1 p0 + d1 q0 p1) / (d0 q1 + d1 q0), q_r = (eps + beta_r)^2.
+template <class R> __device__ __forceinline__ R weno3_face(R wfar, R w0, R wnear, R eps) {
+    const R p0 = R(-0.5) * wfar + R(1.5) * w0;
+    const R p1 = R(0.5) * w0 + R(0.5) * wnear;
+    const R b0 = (w0 - wfar) * (w0 - wfar);
+    const R b1 = (wnear - w0) * (wnear - w0);
+    const R e0 = eps + b0, e1 = eps + b1;
+    const R q0 = e0 * e0, q1 = e1 * e1;
+    const R c0 = R(1.0 / 3.0) * q1, c1 = R(2.0 / 3.0) * q0;
+    return (c0 * p0 + c1 * p1) / (c0 + c1);
+}
+
+template <class R, int RECON>
+__device__ __forceinline__ void recon_faces(R wm, R w0, R wp, R eps, R& fl, R& fr) {
+    if (RECON == REC_PC) {
+        fl = w0;
+        fr = w0;
+    } else if (RECON == REC_MC) {
+        const R s = mc_slope(wm, w0, wp);
+        fl = w0 - R(0.5) * s;
+        fr = w0 + R(0.5) * s;
+    } else {
+        fr = weno3_face(wm, w0, wp, eps);
+        fl = weno3_face(wp, w0, wm, eps);
+    }
+}
+
+template <class R, int RECON> __device__ __forceinline__ R recon_right(R wm, R w0, R wp, R eps) {
+    if (RECON == REC_PC) return w0;
+    if (RECON == REC_MC) return w0 + R(0.5) * mc_slope(wm, w0, wp);
+    return weno3_face(wm, w0, wp, eps);
+}
+template <class R, int RECON> __device__ __forceinline__ R recon_left(R wm, R w0, R wp, R eps) {
+    if (RECON == REC_PC) return w0;
+    if (RECON == REC_MC) return w0 - R(0.5) * mc_slope(wm, w0, wp);
+    return weno3_face(wp, w0, wm, eps);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Numerical fluxes through a face normal to direction D (Sec. 2.1: HLLC, Rusanov; plus HLL).
+// Inputs are primitive face states; output is the conserved flux. Wave speeds (Davis):
+// S_L = min(uL - cL, uR - cR), S_R = max(uL + cL, uR + cR); Rusanov a = max(|uL|+cL, |uR|+cR).
+// ---------------------------------------------------------------------------------------------
+template <class R, int ND, int D, int FLUX>
+__device__ __forceinline__ void euler_flux(const R* WL, const R* WR, R* F, R gamma, R inv_gm1) {
+    constexpr int NV = ND + 2, IP = ND + 1;
+    R UL[NV], UR[NV], FL[NV], FR[NV];
+    prim_to_cons<R, ND>(WL, UL, inv_gm1);
+    prim_to_cons<R, ND>(WR, UR, inv_gm1);
+    const R rL = WL[0], rR = WR[0], uL = WL[1 + D], uR = WR[1 + D], pL = WL[IP], pR = WR[IP];
+    // physical fluxes
+#pragma unroll
+    for (int v = 0; v < NV; ++v) { FL[v] = UL[v] * uL; FR[v] = UR[v] * uR; }
+    FL[1 + D] = FL[1 + D] + pL;
+    FR[1 + D] = FR[1 + D] + pR;
+    FL[IP] = uL * (UL[IP] + pL);
+    FR[IP] = uR * (UR[IP] + pR);
+    const R cL = rsqrt_(gamma * pL / rL);
+    const R cR = rsqrt_(gamma * pR / rR);
+    if (FLUX == FLX_RUSANOV) {
+        const R a = fmax_(fabs_(uL) + cL, fabs_(uR) + cR);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) F[v] = R(0.5) * (FL[v] + FR[v]) - R(0.5) * a * (UR[v] - UL[v]);
+        return;
+    }
+    const R SL = fmin_(uL - cL, uR - cR);
+    const R SR = fmax_(uL + cL, uR + cR);
+    if (FLUX == FLX_HLL) {
+        if (SL >= R(0)) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) F[v] = FL[v];
+        } else if (SR <= R(0)) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) F[v] = FR[v];
+        } else {
+            const R inv = rcp(SR - SL);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) F[v] = (SR * FL[v] - SL * FR[v] + SL * SR * (UR[v] - UL[v])) * inv;
+        }
+        return;
+    }
+    // HLLC: F_L if 0 <= S_L; F*_L if S_L < 0 <= S*; F*_R if S* < 0 < S_R; F_R otherwise.
+    if (SL >= R(0)) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) F[v] = FL[v];
+        return;
+    }
+    const R Ss = (pR - pL + rL * uL * (SL - uL) - rR * uR * (SR - uR)) / (rL * (SL - uL) - rR * (SR - uR));
+    const bool left = Ss >= R(0);
+    if (!left && !(SR > R(0))) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) F[v] = FR[v];
+        return;
+    }
+    const R SK = left ? SL : SR;
+    const R rK = left ? rL : rR, uK = left ? uL : uR, pK = left ? pL : pR;
+    const R EK = left ? UL[IP] : UR[IP];
+    const R fac = rK * (SK - uK) / (SK - Ss);
+    R Us[NV];
+    Us[0] = fac;
+#pragma unroll
+    for (int j = 0; j < ND; ++j) Us[1 + j] = fac * (left ? WL[1 + j] : WR[1 + j]);
+    Us[1 + D] = fac * Ss;
+    Us[IP] = fac * (EK / rK + (Ss - uK) * (Ss + pK / (rK * (SK - uK))));
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        const R fk = left ? FL[v] : FR[v];
+        const R uk = left ? UL[v] : UR[v];
+        F[v] = fk + SK * (Us[v] - uk);
+    }
+}
+
+// Scalar Burgers flux f(u) = u^2/2: Rusanov or HLL (HLLC coincides with HLL for a scalar law).
+template <class R, int FLUX> __device__ __forceinline__ R burgers_flux(R uL, R uR) {
+    const R fL = R(0.5) * uL * uL, fR = R(0.5) * uR * uR;
+    if (FLUX == FLX_RUSANOV) {
+        const R a = fmax_(fabs_(uL), fabs_(uR));
+        return R(0.5) * (fL + fR) - R(0.5) * a * (uR - uL);
+    }
+    const R SL = fmin_(uL, uR), SR = fmax_(uL, uR);
+    if (SL >= R(0)) return fL;
+    if (SR <= R(0)) return fR;
+    return (SR * fL - SL * fR + SL * SR * (uR - uL)) / (SR - SL);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Ghost cells (paper silent; reading): periodic wraps, outflow copies the nearest interior cell,
+// reflective mirrors interior cell -1-j for ghost j and negates the normal velocity. Indices far
+// outside the grid (padding of partial tiles) are clamped so every read stays in bounds.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ int map_ghost(int i, int n, int bc_lo, int bc_hi, bool& flip) {
+    if (i >= 0 && i < n) return i;
+    if (i < 0) {
+        if (bc_lo == BC_PERIODIC) { i %= n; return i < 0 ? i + n : i; }
+        if (bc_lo == BC_OUTFLOW) return 0;
+        flip = !flip;
+        i = -1 - i;
+        return i < n ? i : n - 1;
+    }
+    if (bc_hi == BC_PERIODIC) return i % n;
+    if (bc_hi == BC_OUTFLOW) return n - 1;
+    flip = !flip;
+    i = 2 * n - 1 - i;
+    return i >= 0 ? i : 0;
+}
+
+// Locate the level and local sample of a global work item / sample.
+__device__ __forceinline__ int level_of_work(const GridArgs& g, long long w) {
+    int l = 0;
+#pragma unroll 1
+    for (int k = 1; k < g.nlev; ++k)
+        if (w >= g.lev[k].work0) l = k;
+    return l;
+}
+__device__ __forceinline__ int level_of_sample(const GridArgs& g, int s) {
+    int l = 0;
+#pragma unroll 1
+    for (int k = 1; k < g.nlev; ++k)
+        if (s >= g.lev[k].sample0) l = k;
+    return l;
+}
+
+}  // namespace alsv

@@ -1,0 +1,367 @@
+// Fused SSP-RK stage kernel for eq. (2.1) (Sec. 2.1), one CTA per (sample, tile):
+//   1. load the tile plus a ghost halo of g cells (g = 1 for PC, 2 for MC/WENO3) into shared
+//      memory, filling ghosts from the boundary conditions and converting to the reconstruction
+//      variables (primitive or conserved);
+//   2. per direction (x, then y, then z): each thread computes whole interfaces - both face
+//      states by reconstruction, positivity fallback, one numerical flux - into a shared flux
+//      buffer; every flux is evaluated once per tile and shared by its two cells; each owned cell
+//      then accumulates -(F_{i+1/2} - F_{i-1/2}) / dx_k in registers;
+//   3. epilogue: Uout = a Un + b (Us + dt L) with coalesced stores, and (last stage) the tile's
+//      maximum CFL wave speed of the new state into a fixed per-tile slot.
+// Face values and fluxes never touch HBM: per stage the kernel reads Us once (the halo comes from
+// L2), Un point-wise, and writes Uout once.
+#pragma once
+
+#include "fv_physics.cuh"
+
+namespace alsv {
+
+template <int ND, int TX, int TY, int TZ> struct TileGeom {
+    static constexpr int CELLS = TX * TY * TZ;
+};
+
+template <class R> struct RealTraits;
+template <> struct RealTraits<float> { static __device__ __forceinline__ float nan() { return __int_as_float(0x7fffffff); } };
+template <> struct RealTraits<double> { static __device__ __forceinline__ double nan() { return __longlong_as_double(0x7fffffffffffffffLL); } };
+
+template <class R, int EQ, int ND, int RECON>
+struct StageSmem {
+    static constexpr int NV = (EQ == EQ_BURGERS) ? 1 : ND + 2;
+    static constexpr int G = (RECON == REC_PC) ? 1 : 2;
+};
+
+template <class R, int EQ, int ND, int RECON, int TX, int TY, int TZ>
+constexpr size_t stage_smem_bytes() {
+    constexpr int NV = (EQ == EQ_BURGERS) ? 1 : ND + 2;
+    constexpr int G = (RECON == REC_PC) ? 1 : 2;
+    constexpr int SX = TX + 2 * G, SY = ND >= 2 ? TY + 2 * G : 1, SZ = ND >= 3 ? TZ + 2 * G : 1;
+    constexpr int NIX = (TX + 1) * TY * TZ;
+    constexpr int NIY = ND >= 2 ? TX * (TY + 1) * TZ : 0;
+    constexpr int NIZ = ND >= 3 ? TX * TY * (TZ + 1) : 0;
+    constexpr int NI = NIX > NIY ? (NIX > NIZ ? NIX : NIZ) : (NIY > NIZ ? NIY : NIZ);
+    return sizeof(R) * (size_t)NV * (size_t)(SX * SY * SZ + NI);
+}
+
+// Reconstruct the two face states of interface (left cell L, right cell R) along a line of four
+// (or two, PC) stencil values per variable, apply the positivity fallback, and return primitive
+// states for the flux.
+template <class R, int EQ, int ND, int RECON>
+__device__ __forceinline__ void interface_states(const R* sw, int stride_v, int i0, int step, int rvars, R gm1,
+                                                 R eps, R* WL, R* WR) {
+    constexpr int NV = (EQ == EQ_BURGERS) ? 1 : ND + 2;
+    constexpr int G = (RECON == REC_PC) ? 1 : 2;
+    // i0: smem index of the left cell; stencil left-1, left, right, right+1
+    R fl[NV], fr[NV], cl[NV], cr[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        const R* base = sw + v * stride_v + i0;
+        const R w0 = base[0];
+        const R w1 = base[step];
+        cl[v] = w0;
+        cr[v] = w1;
+        if (G == 1) {
+            fr[v] = w0;
+            fl[v] = w1;
+        } else {
+            const R wm = base[-step];
+            const R w2 = base[2 * step];
+            fr[v] = recon_right<R, RECON>(wm, w0, w1, eps);  // left cell, face i+1/2
+            fl[v] = recon_left<R, RECON>(w0, w1, w2, eps);   // right cell, face i+1/2
+        }
+    }
+    if (EQ == EQ_BURGERS) {
+        WL[0] = fr[0];
+        WR[0] = fl[0];
+        return;
+    }
+    constexpr int IP = ND + 1;
+    if (rvars == RV_PRIM) {
+        const bool okL = fr[0] > R(0) && fr[IP] > R(0);
+        const bool okR = fl[0] > R(0) && fl[IP] > R(0);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            WL[v] = okL ? fr[v] : cl[v];
+            WR[v] = okR ? fl[v] : cr[v];
+        }
+    } else {
+        R a[NV], b[NV];
+        cons_to_prim<R, ND>(fr, a, gm1);
+        cons_to_prim<R, ND>(fl, b, gm1);
+        const bool okL = a[0] > R(0) && a[IP] > R(0);
+        const bool okR = b[0] > R(0) && b[IP] > R(0);
+        R ca[NV], cb[NV];
+        if (!okL) cons_to_prim<R, ND>(cl, ca, gm1);
+        if (!okR) cons_to_prim<R, ND>(cr, cb, gm1);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            WL[v] = okL ? a[v] : ca[v];
+            WR[v] = okR ? b[v] : cb[v];
+        }
+    }
+}
+
+template <class R, int EQ, int ND, int RECON, int FLUX, int TX, int TY, int TZ, int NT>
+__global__ void __launch_bounds__(NT) k_stage(const StageArgs p) {
+    constexpr int NV = (EQ == EQ_BURGERS) ? 1 : ND + 2;
+    constexpr int G = (RECON == REC_PC) ? 1 : 2;
+    constexpr int SX = TX + 2 * G, SY = ND >= 2 ? TY + 2 * G : 1, SZ = ND >= 3 ? TZ + 2 * G : 1;
+    constexpr int NS = SX * SY * SZ;
+    constexpr int NIX = (TX + 1) * TY * TZ;
+    constexpr int NIY = ND >= 2 ? TX * (TY + 1) * TZ : 0;
+    constexpr int NIZ = ND >= 3 ? TX * TY * (TZ + 1) : 0;
+    constexpr int NI = NIX > NIY ? (NIX > NIZ ? NIX : NIZ) : (NIY > NIZ ? NIY : NIZ);
+    constexpr int CELLS = TX * TY * TZ;
+    static_assert(CELLS % NT == 0, "tile cells must be a multiple of the CTA size");
+    constexpr int CPT = CELLS / NT;
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R* sW = reinterpret_cast<R*>(smem_raw);   // [NV][NS]
+    R* sF = sW + NV * NS;                      // [NV][NI]
+
+    const long long w = blockIdx.x;
+    const GridArgs& g = p.g;
+    const int l = level_of_work(g, w);
+    const LevelInfo& L = g.lev[l];
+    const long long wl = w - L.work0;
+    const int b_local = (int)(wl / L.tiles);
+    const int tile = (int)(wl - (long long)b_local * L.tiles);
+    const int sample = L.sample0 + b_local;
+    if (p.done[sample]) return;
+
+    const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
+    const int tx0 = (tile % L.ntile[0]) * TX;
+    const int ty0 = ND >= 2 ? ((tile / L.ntile[0]) % L.ntile[1]) * TY : 0;
+    const int tz0 = ND >= 3 ? (tile / (L.ntile[0] * L.ntile[1])) * TZ : 0;
+    const long long plane = (long long)nx * ny * nz;
+    const long long sbase = L.elem0 + (long long)b_local * NV * plane;
+    const R* Us = reinterpret_cast<const R*>(p.Us) + sbase;
+
+    const R gamma = R(g.gamma);
+    const R gm1 = gamma - R(1);
+    const R inv_gm1 = R(1) / gm1;
+    const int tid = threadIdx.x;
+
+    // ---- 1. tile + halo load with boundary fill and variable conversion
+#pragma unroll 1
+    for (int s = tid; s < NS; s += NT) {
+        const int sx = s % SX;
+        const int sy = ND >= 2 ? (s / SX) % SY : 0;
+        const int sz = ND >= 3 ? s / (SX * SY) : 0;
+        bool flip[3] = {false, false, false};
+        const int ix = map_ghost(tx0 + sx - G, nx, g.bc[0][0], g.bc[0][1], flip[0]);
+        const int iy = ND >= 2 ? map_ghost(ty0 + sy - G, ny, g.bc[1][0], g.bc[1][1], flip[1]) : 0;
+        const int iz = ND >= 3 ? map_ghost(tz0 + sz - G, nz, g.bc[2][0], g.bc[2][1], flip[2]) : 0;
+        const long long off = ((long long)iz * ny + iy) * nx + ix;
+        R u[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) u[v] = Us[v * plane + off];
+        if (EQ == EQ_BURGERS) {
+            if (flip[0] ^ flip[1] ^ flip[2]) u[0] = -u[0];
+            sW[s] = u[0];
+        } else {
+#pragma unroll
+            for (int k = 0; k < ND; ++k)
+                if (flip[k]) u[1 + k] = -u[1 + k];
+            if (g.rvars == RV_PRIM) {
+                R wv[NV];
+                cons_to_prim<R, ND>(u, wv, gm1);
+#pragma unroll
+                for (int v = 0; v < NV; ++v) sW[v * NS + s] = wv[v];
+            } else {
+#pragma unroll
+                for (int v = 0; v < NV; ++v) sW[v * NS + s] = u[v];
+            }
+        }
+    }
+
+    R acc[CPT][NV];
+#pragma unroll
+    for (int m = 0; m < CPT; ++m)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) acc[m][v] = R(0);
+
+    // ---- 2. per direction: interface fluxes into smem, then divergence into registers
+#pragma unroll
+    for (int D = 0; D < ND; ++D) {
+        __syncthreads();
+        const int EX = TX + (D == 0), EY = TY + (D == 1), EZ = TZ + (D == 2);
+        const int NID = EX * EY * EZ;
+        const int step = D == 0 ? 1 : (D == 1 ? SX : SX * SY);
+        const R eps = g.weno_eps_dx2 ? R(L.dx[D] * L.dx[D]) : R(g.weno_eps);
+#pragma unroll 1
+        for (int f = tid; f < NID; f += NT) {
+            const int fx = f % EX;
+            const int fy = ND >= 2 ? (f / EX) % EY : 0;
+            const int fz = ND >= 3 ? f / (EX * EY) : 0;
+            // left cell of the interface in tile coordinates = (fx,fy,fz) - e_D; smem offset +G
+            int cx = fx + G, cy = ND >= 2 ? fy + G : 0, cz = ND >= 3 ? fz + G : 0;
+            if (D == 0) cx -= 1;
+            if (D == 1) cy -= 1;
+            if (D == 2) cz -= 1;
+            const int i0 = (cz * SY + cy) * SX + cx;
+            R WL[NV], WR[NV], F[NV];
+            interface_states<R, EQ, ND, RECON>(sW, NS, i0, step, g.rvars, gm1, eps, WL, WR);
+            if (EQ == EQ_BURGERS) {
+                F[0] = burgers_flux<R, FLUX>(WL[0], WR[0]);
+            } else {
+                if (D == 0) euler_flux<R, ND, 0, FLUX>(WL, WR, F, gamma, inv_gm1);
+                if (D == 1) euler_flux<R, ND, (ND >= 2 ? 1 : 0), FLUX>(WL, WR, F, gamma, inv_gm1);
+                if (D == 2) euler_flux<R, ND, (ND >= 3 ? 2 : 0), FLUX>(WL, WR, F, gamma, inv_gm1);
+            }
+#pragma unroll
+            for (int v = 0; v < NV; ++v) sF[v * NI + f] = F[v];
+        }
+        __syncthreads();
+        const R inv_dx = R(L.inv_dx[D]);
+        const int fstep = D == 0 ? 1 : (D == 1 ? TX : TX * TY);
+#pragma unroll
+        for (int m = 0; m < CPT; ++m) {
+            const int c = tid + m * NT;
+            const int x = c % TX;
+            const int y = ND >= 2 ? (c / TX) % TY : 0;
+            const int z = ND >= 3 ? c / (TX * TY) : 0;
+            const int fidx = (z * EY + y) * EX + x;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) acc[m][v] = acc[m][v] - (sF[v * NI + fidx + fstep] - sF[v * NI + fidx]) * inv_dx;
+        }
+    }
+
+    // ---- 3. RK combination and store; wave speed of the new state
+    const R dt = R(p.dt[sample]);
+    const R ca = R(p.a), cb = R(p.b);
+    const R* Un = reinterpret_cast<const R*>(p.Un) + sbase;
+    R* Uo = reinterpret_cast<R*>(p.Uout) + sbase;
+    R smax = R(0);
+    bool bad = false;
+#pragma unroll
+    for (int m = 0; m < CPT; ++m) {
+        const int c = tid + m * NT;
+        const int x = tx0 + c % TX;
+        const int y = ty0 + (ND >= 2 ? (c / TX) % TY : 0);
+        const int z = tz0 + (ND >= 3 ? c / (TX * TY) : 0);
+        if (x >= nx || y >= ny || z >= nz) continue;
+        const long long off = ((long long)z * ny + y) * nx + x;
+        R out[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            const R us = Us[v * plane + off];
+            R o = us + dt * acc[m][v];
+            if (p.a != 0.0) o = ca * Un[v * plane + off] + cb * o;
+            out[v] = o;
+            Uo[v * plane + off] = o;
+        }
+        if (p.want_speed) {
+            if (EQ == EQ_BURGERS) {
+                const R au = fabs_(out[0]);
+                if (!(au == au) || isinf(au)) bad = true;
+#pragma unroll
+                for (int k = 0; k < ND; ++k) smax = fmax_(smax, au * R(L.inv_dx[k]));
+            } else {
+                R wv[NV];
+                cons_to_prim<R, ND>(out, wv, gm1);
+                const R rho = wv[0], pr = wv[ND + 1];
+                if (!(rho > R(0) && pr > R(0)) || isinf(rho) || isinf(pr)) {
+                    bad = true;
+                } else {
+                    const R c = rsqrt_(gamma * pr / rho);
+#pragma unroll
+                    for (int k = 0; k < ND; ++k) smax = fmax_(smax, (fabs_(wv[1 + k]) + c) * R(L.inv_dx[k]));
+                }
+            }
+        }
+    }
+    if (p.want_speed) {
+        // fixed-pattern CTA reduction (max is exact; the pattern is fixed anyway)
+        __shared__ double red[NT / 32];
+        __shared__ int redbad[NT / 32];
+        double sm = (double)smax;
+        int bd = bad ? 1 : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double other = __shfl_xor_sync(0xffffffffu, sm, o);
+            sm = other > sm ? other : sm;
+            bd |= __shfl_xor_sync(0xffffffffu, bd, o);
+        }
+        if ((tid & 31) == 0) { red[tid >> 5] = sm; redbad[tid >> 5] = bd; }
+        __syncthreads();
+        if (tid == 0) {
+            double r = red[0];
+            int rb = redbad[0];
+            for (int k = 1; k < NT / 32; ++k) { r = red[k] > r ? red[k] : r; rb |= redbad[k]; }
+            p.speed_part[w] = rb ? __longlong_as_double(0x7fffffffffffffffLL) : r;
+        }
+    }
+}
+
+// Initial wave-speed partials of a state (same tiling as the stage kernel).
+template <class R, int EQ, int ND, int TX, int TY, int TZ, int NT>
+__global__ void __launch_bounds__(NT) k_speed(const GridArgs g, const void* Uv, double* part) {
+    constexpr int NV = (EQ == EQ_BURGERS) ? 1 : ND + 2;
+    constexpr int CELLS = TX * TY * TZ;
+    constexpr int CPT = CELLS / NT;
+    const long long w = blockIdx.x;
+    const int l = level_of_work(g, w);
+    const LevelInfo& L = g.lev[l];
+    const long long wl = w - L.work0;
+    const int b_local = (int)(wl / L.tiles);
+    const int tile = (int)(wl - (long long)b_local * L.tiles);
+    const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
+    const int tx0 = (tile % L.ntile[0]) * TX;
+    const int ty0 = ND >= 2 ? ((tile / L.ntile[0]) % L.ntile[1]) * TY : 0;
+    const int tz0 = ND >= 3 ? (tile / (L.ntile[0] * L.ntile[1])) * TZ : 0;
+    const long long plane = (long long)nx * ny * nz;
+    const R* U = reinterpret_cast<const R*>(Uv) + L.elem0 + (long long)b_local * NV * plane;
+    const R gamma = R(g.gamma), gm1 = gamma - R(1);
+    const int tid = threadIdx.x;
+    R smax = R(0);
+    bool bad = false;
+#pragma unroll
+    for (int m = 0; m < CPT; ++m) {
+        const int c = tid + m * NT;
+        const int x = tx0 + c % TX;
+        const int y = ty0 + (ND >= 2 ? (c / TX) % TY : 0);
+        const int z = tz0 + (ND >= 3 ? c / (TX * TY) : 0);
+        if (x >= nx || y >= ny || z >= nz) continue;
+        const long long off = ((long long)z * ny + y) * nx + x;
+        R u[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) u[v] = U[v * plane + off];
+        if (EQ == EQ_BURGERS) {
+            const R au = fabs_(u[0]);
+            if (!(au == au) || isinf(au)) bad = true;
+#pragma unroll
+            for (int k = 0; k < ND; ++k) smax = fmax_(smax, au * R(L.inv_dx[k]));
+        } else {
+            R wv[NV];
+            cons_to_prim<R, ND>(u, wv, gm1);
+            const R rho = wv[0], pr = wv[ND + 1];
+            if (!(rho > R(0) && pr > R(0)) || isinf(rho) || isinf(pr)) {
+                bad = true;
+            } else {
+                const R c = rsqrt_(gamma * pr / rho);
+#pragma unroll
+                for (int k = 0; k < ND; ++k) smax = fmax_(smax, (fabs_(wv[1 + k]) + c) * R(L.inv_dx[k]));
+            }
+        }
+    }
+    __shared__ double red[NT / 32];
+    __shared__ int redbad[NT / 32];
+    double sm = (double)smax;
+    int bd = bad ? 1 : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double other = __shfl_xor_sync(0xffffffffu, sm, o);
+        sm = other > sm ? other : sm;
+        bd |= __shfl_xor_sync(0xffffffffu, bd, o);
+    }
+    if ((tid & 31) == 0) { red[tid >> 5] = sm; redbad[tid >> 5] = bd; }
+    __syncthreads();
+    if (tid == 0) {
+        double r = red[0];
+        int rb = redbad[0];
+        for (int k = 1; k < NT / 32; ++k) { r = red[k] > r ? red[k] : r; rb |= redbad[k]; }
+        part[w] = rb ? __longlong_as_double(0x7fffffffffffffffLL) : r;
+    }
+}
+
+}  // namespace alsv

@@ -1,0 +1,463 @@
+// Per-sample time control (CFL step), initial data, counter-based parameters, Monte Carlo
+// statistics (Sec. 2.2) and fixed-order FP64 reductions.
+#include "fv_physics.cuh"
+
+namespace alsv {
+
+// ---------------------------------------------------------------------------------------------
+// Time control, one thread per sample. Adaptive mode (reading; the paper gives no CFL rule):
+// s_b = max over tiles of the per-tile partials (the largest (|u_k| + c) / dx_k), dt_b =
+// cfl / s_b, clipped to T - t_b (then the sample lands exactly on T and is done). Fixed mode:
+// dt = fixed_dt until n_target steps; the realised CFL number dt * s_b is checked against a guard.
+// A NaN partial marks a non-physical sample: it stops and the status word records it.
+// ---------------------------------------------------------------------------------------------
+__global__ void k_finish(const FinishArgs a) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= a.g.total_samples) return;
+    const int l = level_of_sample(a.g, s);
+    const LevelInfo& L = a.g.lev[l];
+    const int b = s - L.sample0;
+    if (a.advance) {
+        if (a.done[s]) return;  // skipped by this step's stages
+        double t = a.t[s];
+        const long long n = a.nstep[s] + 1;
+        if (a.fixed_dt > 0.0) t = (double)n * a.fixed_dt;
+        else t = a.last[s] ? *a.T_end : t + a.dt[s];
+        a.t[s] = t;
+        a.nstep[s] = n;
+    }
+    const double* part = a.speed_part + L.work0 + (long long)b * L.tiles;
+    double smax = 0.0;
+    bool bad = false;
+    for (int k = 0; k < L.tiles; ++k) {
+        const double v = part[k];
+        if (v != v) bad = true;
+        else smax = v > smax ? v : smax;
+    }
+    if (bad) {
+        atomicOr(a.status, ST_NONPHYSICAL);
+        a.done[s] = 1;
+        return;
+    }
+    const double t = a.t[s];
+    if (a.fixed_dt > 0.0) {
+        a.dt[s] = a.fixed_dt;
+        a.last[s] = 0;
+        const bool fin = a.nstep[s] >= *a.n_target;
+        a.done[s] = fin ? 1 : 0;
+        if (!fin && a.fixed_dt * smax > a.cfl_guard) atomicOr(a.status, ST_CFL);
+        return;
+    }
+    const double T = *a.T_end;
+    if (!(t < T)) {
+        a.done[s] = 1;
+        return;
+    }
+    double dt = a.cfl / smax;
+    int last = 0;
+    if (!(dt < T - t)) {
+        dt = T - t;
+        last = 1;
+    }
+    if (isinf(dt)) dt = 0.0;  // no wave motion and no end time: nothing to advance
+    a.dt[s] = dt;
+    a.last[s] = last;
+    a.done[s] = 0;
+}
+
+cudaError_t launch_finish(const FinishArgs& a, cudaStream_t s) {
+    const int n = a.g.total_samples;
+    if (n <= 0) return cudaSuccess;
+    k_finish<<<(n + 127) / 128, 128, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------------
+// SplitMix64 (Steele, Lea, Flood 2014) as a counter-based generator of the KH parameters:
+// theta_{b,j} = hi_j * (splitmix64(seed ^ (b P + j)) >> 11) * 2^-53, hi = 1 (amplitudes, first
+// half) or 2 pi (phases, second half); splitmix64(x) = mix(x + golden gamma).
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t sm64(uint64_t x) {
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__global__ void k_theta(uint64_t seed, int samples, int P, double* theta) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)samples * P) return;
+    const int b = (int)(i / P), j = (int)(i - (long long)b * P);
+    const uint64_t r = sm64(seed ^ ((uint64_t)b * (uint64_t)P + (uint64_t)j));
+    const double u01 = (double)(r >> 11) * (1.0 / 9007199254740992.0);
+    const double hi = j < P / 2 ? 1.0 : 2.0 * 3.14159265358979323846;
+    theta[i] = hi * u01;
+}
+
+cudaError_t launch_theta(uint64_t seed, int samples, int P, double* theta, cudaStream_t s) {
+    const long long n = (long long)samples * P;
+    if (n <= 0) return cudaSuccess;
+    k_theta<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(seed, samples, P, theta);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------------
+// Initial data (cell averages of conserved variables), computed in FP64, stored as R.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ double clamp01(double x) { return x < 0.0 ? 0.0 : (x > 1.0 ? 1.0 : x); }
+
+__device__ __forceinline__ void kh_states(int nd, double gamma, double* Uin, double* Uout) {
+    // inner band rho = 2, u = -0.5; outer rho = 1, u = 0.5; v = w = 0; p = 2.5 (Sec. 3, reading)
+    for (int v = 0; v < 5; ++v) { Uin[v] = 0.0; Uout[v] = 0.0; }
+    Uin[0] = 2.0;
+    Uin[1] = 2.0 * -0.5;
+    Uin[nd + 1] = 2.5 / (gamma - 1.0) + 0.5 * 2.0 * (-0.5 * -0.5);
+    Uout[0] = 1.0;
+    Uout[1] = 1.0 * 0.5;
+    Uout[nd + 1] = 2.5 / (gamma - 1.0) + 0.5 * 1.0 * (0.5 * 0.5);
+}
+
+// One thread per (column, sample): the interface displacement Y is evaluated once per column
+// (x for 2D, (x,z) for 3D), then the column is filled with the band's volume fraction in y.
+template <class R, int ND>
+__global__ void k_init_kh(const InitArgs a) {
+    constexpr int NV = ND + 2;
+    const int s = blockIdx.y;
+    const int l = level_of_sample(a.g, s);
+    const LevelInfo& L = a.g.lev[l];
+    const int b = s - L.sample0;
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
+    if (col >= nx * nz) return;
+    const int x = col % nx, z = col / nx;
+    const double PI = 3.14159265358979323846;
+    const double* th = a.theta + (long long)s * a.P;
+    const double hx = L.dx[0], hy = L.dx[1];
+    const double xc = a.g.lo[0] + (x + 0.5) * hx;
+    double Y = 0.0;
+    if (ND == 2) {
+        for (int n = 1; n <= 10; ++n) Y = Y + th[n - 1] * sin(2.0 * PI * n * xc + th[10 + n - 1]);
+    } else {
+        const double zc = a.g.lo[2] + (z + 0.5) * L.dx[2];
+        for (int n = 1; n <= 8; ++n)
+            for (int m = 1; m <= 8; ++m) {
+                const int j = (n - 1) * 8 + (m - 1);
+                Y = Y + th[j] * sin(2.0 * PI * (n * xc + m * zc) + th[64 + j]);
+            }
+    }
+    Y = 0.01 * Y;
+    double Uin[5], Uout[5];
+    kh_states(ND, a.g.gamma, Uin, Uout);
+    const long long plane = (long long)nx * ny * nz;
+    R* U = reinterpret_cast<R*>(a.U) + L.elem0 + (long long)b * NV * plane;
+    for (int y = 0; y < ny; ++y) {
+        const double ylo = a.g.lo[1] + y * hy;
+        const double f_lo = clamp01((0.25 + Y - ylo) / hy);
+        const double f_hi = clamp01((0.75 + Y - ylo) / hy);
+        const double f = f_hi - f_lo;
+        const long long off = ((long long)z * ny + y) * nx + x;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) U[v * plane + off] = R(f * Uin[v] + (1.0 - f) * Uout[v]);
+    }
+}
+
+__device__ void vortex_point(double g, double xc, double yc, double x, double y, double* Uc) {
+    const double PI = 3.14159265358979323846, beta = 5.0;
+    const double rx = x - xc, ry = y - yc, r2 = rx * rx + ry * ry;
+    const double e = exp(0.5 * (1.0 - r2));
+    const double u = 1.0 - beta / (2.0 * PI) * e * ry;
+    const double v = 1.0 + beta / (2.0 * PI) * e * rx;
+    const double Tm = 1.0 - (g - 1.0) * beta * beta / (8.0 * g * PI * PI) * e * e;
+    const double rho = pow(Tm, 1.0 / (g - 1.0));
+    const double p = rho * Tm;
+    Uc[0] = rho;
+    Uc[1] = rho * u;
+    Uc[2] = rho * v;
+    Uc[3] = p / (g - 1.0) + 0.5 * rho * (u * u + v * v);
+}
+
+// Tubes (split at x = 0.5 with exact volume fraction), Burgers sine (exact averages) and the
+// isentropic vortex (5x5 Gauss-Legendre averages); one thread per cell.
+template <class R, int ND>
+__global__ void k_init_cell(const InitArgs a) {
+    const int s = blockIdx.y;
+    const int l = level_of_sample(a.g, s);
+    const LevelInfo& L = a.g.lev[l];
+    const int b = s - L.sample0;
+    const int nv = a.g.nv;
+    const long long plane = (long long)L.n[0] * L.n[1] * L.n[2];
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= plane) return;
+    const int x = (int)(i % L.n[0]);
+    const int y = (int)((i / L.n[0]) % L.n[1]);
+    R* U = reinterpret_cast<R*>(a.U) + L.elem0 + (long long)b * nv * plane;
+    const double g = a.g.gamma;
+    const double PI = 3.14159265358979323846;
+    double out[5] = {0, 0, 0, 0, 0};
+    if (a.kind == 1 || a.kind == 2) {
+        double WL[5] = {0, 0, 0, 0, 0}, WR[5] = {0, 0, 0, 0, 0};
+        const int ip = ND + 1;
+        if (a.kind == 1) { WL[0] = 1.0; WL[ip] = 1.0; WR[0] = 0.125; WR[ip] = 0.1; }
+        else { WL[0] = 0.445; WL[1] = 0.698; WL[ip] = 3.528; WR[0] = 0.5; WR[ip] = 0.571; }
+        double UL[5], UR[5];
+        for (int k = 0; k < 2; ++k) {
+            const double* W = k == 0 ? WL : WR;
+            double* Uc = k == 0 ? UL : UR;
+            double u2 = 0.0;
+            for (int d = 0; d < ND; ++d) u2 = u2 + W[1 + d] * W[1 + d];
+            Uc[0] = W[0];
+            for (int d = 0; d < ND; ++d) Uc[1 + d] = W[0] * W[1 + d];
+            Uc[ip] = W[ip] / (g - 1.0) + 0.5 * W[0] * u2;
+        }
+        const double h = L.dx[0];
+        const double xl = a.g.lo[0] + x * h;
+        const double f = fmin(1.0, fmax(0.0, (0.5 - xl) / h));
+        for (int v = 0; v < nv; ++v) out[v] = f * UL[v] + (1.0 - f) * UR[v];
+    } else if (a.kind == 3) {
+        const double h = L.dx[0];
+        const double xl = a.g.lo[0] + x * h, xr = xl + h;
+        out[0] = (cos(2.0 * PI * xl) - cos(2.0 * PI * xr)) / (2.0 * PI * h);
+    } else if (a.kind == 4) {
+        const double gx[5] = {-0.9061798459386640, -0.5384693101056831, 0.0, 0.5384693101056831, 0.9061798459386640};
+        const double gw[5] = {0.2369268850561891, 0.4786286704993665, 0.5688888888888889, 0.4786286704993665,
+                              0.2369268850561891};
+        const double hx = L.dx[0], hy = L.dx[1];
+        const double lo0 = a.g.lo[0], lo1 = a.g.lo[1];
+        const double cx = lo0 + (x + 0.5) * hx, cy = lo1 + (y + 0.5) * hy;
+        for (int p = 0; p < 5; ++p)
+            for (int q = 0; q < 5; ++q) {
+                double Uc[4];
+                vortex_point(g, a.vortex_center[0], a.vortex_center[1], cx + 0.5 * hx * gx[p], cy + 0.5 * hy * gx[q], Uc);
+                for (int v = 0; v < 4; ++v) out[v] += 0.25 * gw[p] * gw[q] * Uc[v];
+            }
+    }
+    for (int v = 0; v < nv; ++v) U[v * plane + i] = R(out[v]);
+}
+
+template <class R>
+static cudaError_t launch_init_t(int ndim, const InitArgs& a, cudaStream_t s) {
+    int maxcols = 0;
+    long long maxcells = 0;
+    for (int l = 0; l < a.g.nlev; ++l) {
+        const LevelInfo& L = a.g.lev[l];
+        maxcols = max(maxcols, L.n[0] * L.n[2]);
+        maxcells = maxcells > (long long)L.n[0] * L.n[1] * L.n[2] ? maxcells : (long long)L.n[0] * L.n[1] * L.n[2];
+    }
+    if (a.g.total_samples <= 0) return cudaSuccess;
+    if (a.kind == 0) {
+        dim3 grid((maxcols + 127) / 128, a.g.total_samples);
+        if (ndim == 2) k_init_kh<R, 2><<<grid, 128, 0, s>>>(a);
+        else k_init_kh<R, 3><<<grid, 128, 0, s>>>(a);
+    } else {
+        dim3 grid((unsigned)((maxcells + 255) / 256), a.g.total_samples);
+        if (ndim == 1) k_init_cell<R, 1><<<grid, 256, 0, s>>>(a);
+        else if (ndim == 2) k_init_cell<R, 2><<<grid, 256, 0, s>>>(a);
+        else k_init_cell<R, 3><<<grid, 256, 0, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init(int fp64, int ndim, const InitArgs& a, cudaStream_t s) {
+    return fp64 ? launch_init_t<double>(ndim, a, s) : launch_init_t<float>(ndim, a, s);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Monte Carlo mean/variance (Sec. 2.2), FP64 Welford over samples in ascending order, one thread
+// per cell; quantities are primitive (rho, u_k, p) for Euler and u for Burgers.
+// Accumulator: int64 count at byte 0, mean[q][cells] at byte 256, then M2[q][cells].
+// ---------------------------------------------------------------------------------------------
+template <class R, int NV, int EULER>
+__global__ void k_welford(const GridArgs g, const void* Uv, void* stats) {
+    const LevelInfo& L = g.lev[0];
+    const long long C = (long long)L.n[0] * L.n[1] * L.n[2];
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= C) return;
+    const long long n0 = *reinterpret_cast<const long long*>(stats);
+    double* mean = reinterpret_cast<double*>(reinterpret_cast<char*>(stats) + 256);
+    double* M2 = mean + NV * C;
+    const R* U = reinterpret_cast<const R*>(Uv);
+    double mu[NV], m2[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) { mu[q] = mean[q * C + i]; m2[q] = M2[q * C + i]; }
+    const int B = L.samples;
+    const double gm1 = g.gamma - 1.0;
+#pragma unroll 4
+    for (int b = 0; b < B; ++b) {
+        double u[NV], x[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) u[v] = (double)U[((long long)b * NV + v) * C + i];
+        if (EULER) {
+            const double inv = 1.0 / u[0];
+            double mm = 0.0;
+#pragma unroll
+            for (int k = 1; k < NV - 1; ++k) mm = mm + u[k] * u[k];
+            x[0] = u[0];
+#pragma unroll
+            for (int k = 1; k < NV - 1; ++k) x[k] = u[k] * inv;
+            x[NV - 1] = gm1 * (u[NV - 1] - 0.5 * mm * inv);
+        } else {
+            x[0] = u[0];
+        }
+        const double inv_n = 1.0 / (double)(n0 + b + 1);
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            const double delta = x[q] - mu[q];
+            mu[q] = mu[q] + delta * inv_n;
+            m2[q] = m2[q] + delta * (x[q] - mu[q]);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < NV; ++q) { mean[q * C + i] = mu[q]; M2[q * C + i] = m2[q]; }
+}
+
+__global__ void k_welford_count(void* stats, int B) { *reinterpret_cast<long long*>(stats) += B; }
+
+template <class R>
+static cudaError_t launch_welford_t(const GridArgs& g, const void* U, void* stats, cudaStream_t s) {
+    const LevelInfo& L = g.lev[0];
+    const long long C = (long long)L.n[0] * L.n[1] * L.n[2];
+    const unsigned grid = (unsigned)((C + 127) / 128);
+    switch (g.nv) {
+        case 1: k_welford<R, 1, 0><<<grid, 128, 0, s>>>(g, U, stats); break;
+        case 3: k_welford<R, 3, 1><<<grid, 128, 0, s>>>(g, U, stats); break;
+        case 4: k_welford<R, 4, 1><<<grid, 128, 0, s>>>(g, U, stats); break;
+        default: k_welford<R, 5, 1><<<grid, 128, 0, s>>>(g, U, stats); break;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_welford_count<<<1, 1, 0, s>>>(stats, L.samples);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_welford(int fp64, const GridArgs& g, const void* U, void* stats, cudaStream_t s) {
+    return fp64 ? launch_welford_t<double>(g, U, stats, s) : launch_welford_t<float>(g, U, stats, s);
+}
+
+__global__ void k_stats_read(long long C, int nq, const void* stats, double* mean_out, double* var_out) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= C * nq) return;
+    const long long n = *reinterpret_cast<const long long*>(stats);
+    const double* mean = reinterpret_cast<const double*>(reinterpret_cast<const char*>(stats) + 256);
+    const double* M2 = mean + nq * C;
+    if (mean_out) mean_out[i] = mean[i];
+    if (var_out) var_out[i] = n > 1 ? M2[i] / (double)(n - 1) : 0.0;
+}
+
+cudaError_t launch_stats_read(const GridArgs& g, const void* stats, double* mean, double* var, cudaStream_t s) {
+    const LevelInfo& L = g.lev[0];
+    const long long C = (long long)L.n[0] * L.n[1] * L.n[2];
+    const long long n = C * g.nv;
+    k_stats_read<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(C, g.nv, stats, mean, var);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------------
+// Fixed-order FP64 reductions (conservation totals per sample and variable; kinetic energy per
+// sample). Pass 1: each CTA reduces one chunk of kChunk cells of one (sample, var) - thread t
+// sums cells t, t+256, ... sequentially, then a fixed shuffle tree and a fixed tree over warps -
+// into a per-chunk partial. Pass 2: one CTA per (sample, var) reduces the partials in the same
+// pattern and multiplies by the cell volume. The result depends only on the data.
+// ---------------------------------------------------------------------------------------------
+constexpr int kChunk = 4096;
+constexpr int kRT = 256;
+
+__device__ __forceinline__ double block_sum_fixed(double v, double* sh) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int tid = threadIdx.x;
+    if ((tid & 31) == 0) sh[tid >> 5] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (tid == 0) {
+        r = sh[0];
+        for (int k = 1; k < kRT / 32; ++k) r += sh[k];
+    }
+    __syncthreads();
+    return r;
+}
+
+static long long chunks_of(const LevelInfo& L) {
+    const long long C = (long long)L.n[0] * L.n[1] * L.n[2];
+    return (C + kChunk - 1) / kChunk;
+}
+
+long long reduce_partial_count(const GridArgs& g) {
+    long long mx = 0;
+    for (int l = 0; l < g.nlev; ++l) mx = mx > chunks_of(g.lev[l]) ? mx : chunks_of(g.lev[l]);
+    return mx * (long long)g.total_samples * g.nv;
+}
+
+template <class R>
+__global__ void __launch_bounds__(kRT) k_reduce1(const GridArgs g, int kind, const void* Uv, double* partial,
+                                                 long long maxchunks) {
+    __shared__ double sh[kRT / 32];
+    const int nvr = kind == 0 ? g.nv : 1;
+    const int sv = blockIdx.x;
+    const int s = sv / nvr, v = sv - s * nvr;
+    const int l = level_of_sample(g, s);
+    const LevelInfo& L = g.lev[l];
+    const int b = s - L.sample0;
+    const long long C = (long long)L.n[0] * L.n[1] * L.n[2];
+    const long long chunk = blockIdx.y;
+    if (chunk * kChunk >= C) return;  // uniform per CTA
+    const R* U = reinterpret_cast<const R*>(Uv) + L.elem0 + (long long)b * g.nv * C;
+    const long long c0 = chunk * kChunk;
+    const long long c1 = c0 + kChunk < C ? c0 + kChunk : C;
+    double acc = 0.0;
+    for (long long i = c0 + threadIdx.x; i < c1; i += kRT) {
+        if (kind == 0) {
+            acc += (double)U[v * C + i];
+        } else {
+            const double rho = (double)U[i];
+            double mm = 0.0;
+            for (int k = 1; k < g.nv - 1; ++k) {
+                const double m = (double)U[k * C + i];
+                mm += m * m;
+            }
+            acc += 0.5 * mm / rho;
+        }
+    }
+    const double r = block_sum_fixed(acc, sh);
+    if (threadIdx.x == 0) partial[(long long)sv * maxchunks + chunk] = r;
+}
+
+__device__ __forceinline__ double cell_volume(const GridArgs& g, const LevelInfo& L) {
+    double dV = 1.0;
+    for (int k = 0; k < g.ndim; ++k) dV *= L.dx[k];
+    return dV;
+}
+
+__global__ void __launch_bounds__(kRT) k_reduce2(const GridArgs g, int kind, const double* partial, long long maxchunks,
+                                                 double* out) {
+    __shared__ double sh[kRT / 32];
+    const int nvr = kind == 0 ? g.nv : 1;
+    const int sv = blockIdx.x;
+    const int s = sv / nvr;
+    const int l = level_of_sample(g, s);
+    const LevelInfo& L = g.lev[l];
+    const long long C = (long long)L.n[0] * L.n[1] * L.n[2];
+    const long long nch = (C + kChunk - 1) / kChunk;
+    double acc = 0.0;
+    for (long long i = threadIdx.x; i < nch; i += kRT) acc += partial[(long long)sv * maxchunks + i];
+    const double r = block_sum_fixed(acc, sh);
+    if (threadIdx.x == 0) out[sv] = r * cell_volume(g, L);
+}
+
+cudaError_t launch_reduce(int fp64, int kind, const GridArgs& g, const void* U, double* partial, double* out,
+                          cudaStream_t s) {
+    long long maxchunks = 0;
+    for (int l = 0; l < g.nlev; ++l) maxchunks = maxchunks > chunks_of(g.lev[l]) ? maxchunks : chunks_of(g.lev[l]);
+    const int nvr = kind == 0 ? g.nv : 1;
+    const long long rows = (long long)g.total_samples * nvr;
+    if (rows <= 0 || maxchunks <= 0) return cudaSuccess;
+    if (maxchunks > 65535) return cudaErrorInvalidConfiguration;  // 2.7e8 cells per sample
+    dim3 grid1((unsigned)rows, (unsigned)maxchunks);
+    if (fp64) k_reduce1<double><<<grid1, kRT, 0, s>>>(g, kind, U, partial, maxchunks);
+    else k_reduce1<float><<<grid1, kRT, 0, s>>>(g, kind, U, partial, maxchunks);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_reduce2<<<(unsigned)rows, kRT, 0, s>>>(g, kind, partial, maxchunks, out);
+    return cudaGetLastError();
+}
+
+}  // namespace alsv

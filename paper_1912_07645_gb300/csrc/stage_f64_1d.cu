@@ -1,0 +1,16 @@
+// Stage and speed kernels for double, 1D (explicit tile-shape variants).
+#include "stage_dispatch.cuh"
+namespace alsv {
+cudaError_t launch_stage_f64_1d(int variant, int eq, int recon, int flux, const StageArgs& a, cudaStream_t s) {
+    switch (variant) {
+        case 0: return launch_stage_tile<double, 1, 256, 1, 1, 256>(eq, recon, flux, a, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+cudaError_t launch_speed_f64_1d(int variant, int eq, const GridArgs& g, const void* U, double* part, cudaStream_t s) {
+    switch (variant) {
+        case 0: return launch_speed_tile<double, 1, 256, 1, 1, 256>(eq, g, U, part, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+}  // namespace alsv

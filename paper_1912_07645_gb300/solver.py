@@ -1,0 +1,170 @@
+"""Descriptor construction and a context wrapper that owns torch-allocated device buffers.
+
+The wrapper only allocates memory and forwards to the C ABI; it performs no arithmetic.
+"""
+from __future__ import annotations
+
+from . import _abi as A
+
+
+def make_desc(ndim=1, n=(8, 1, 1), lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), batch=1, eq="euler", gamma=1.4,
+              recon="mc", rvars="prim", flux="hllc", rk="ssprk2", bc="periodic", cfl=0.45, fixed_dt=0.0,
+              precision="fp64", seed=0, weno_eps=1e-6, weno_eps_dx2=False, levels=None,
+              vortex_center=(5.0, 5.0), **_ignored) -> A.alsv_grid_desc:
+    """Build an ``alsv_grid_desc`` from plain values.
+
+    ``bc``: one name for every side or a list of (lo, hi) names per direction.
+    ``levels``: optional MLMC level table, a list of (n_tuple, samples).
+    """
+    d = A.alsv_grid_desc()
+    d.ndim = ndim
+    nn = list(n) + [1] * (3 - len(n))
+    for k in range(3):
+        d.n[k] = int(nn[k]) if k < ndim else 1
+        d.lo[k] = float(lo[k]) if k < len(lo) else 0.0
+        d.hi[k] = float(hi[k]) if k < len(hi) else 1.0
+    d.batch = batch
+    d.eq = A.EQ[eq]
+    d.gamma = gamma
+    d.recon = A.RECON[recon]
+    d.recon_vars = A.RVARS[rvars]
+    d.flux = A.FLUX[flux]
+    d.rk = A.RK[rk]
+    for k in range(3):
+        pair = (bc, bc) if isinstance(bc, str) else (bc[k] if k < len(bc) else ("periodic", "periodic"))
+        d.bc[k][0] = A.BC[pair[0]]
+        d.bc[k][1] = A.BC[pair[1]]
+    d.cfl = cfl
+    d.fixed_dt = fixed_dt
+    d.precision = A.PRECISION[precision]
+    d.seed = seed & 0xFFFFFFFFFFFFFFFF
+    d.weno_eps = weno_eps
+    d.weno_eps_dx2 = 1 if weno_eps_dx2 else 0
+    if levels:
+        d.n_levels = len(levels)
+        for l, (ln, lb) in enumerate(levels):
+            ln = list(ln) + [1] * (3 - len(ln))
+            for k in range(3):
+                d.level_n[l][k] = int(ln[k]) if k < ndim else 1
+            d.level_batch[l] = lb
+    d.vortex_center[0], d.vortex_center[1] = vortex_center
+    return d
+
+
+class Solver:
+    """One context with its workspace and state held as torch CUDA tensors.
+
+    ``stream``: a torch.cuda.Stream (default: a new stream, so step chunks can be captured in CUDA
+    graphs). All calls enqueue work on that stream.
+    """
+
+    def __init__(self, desc: A.alsv_grid_desc | None = None, stream=None, device="cuda", **kw):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required (the solver has no CPU path)")
+        self.torch = torch
+        self.desc = desc if desc is not None else make_desc(**kw)
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
+        self.ctx, ws_bytes = A.alsv_init_grid(self.desc, self.stream.cuda_stream)
+        with torch.cuda.stream(self.stream):
+            self.ws = torch.empty(max(ws_bytes, 256), dtype=torch.uint8, device=self.device)
+        A.alsv_bind_workspace(self.ctx, self.ws)
+        self.nv = A.alsv_num_vars(self.ctx)
+        self.samples = A.alsv_num_samples(self.ctx)
+        self.dtype = torch.float64 if self.desc.precision == 1 else torch.float32
+        nbytes = A.alsv_state_bytes(self.ctx)
+        with torch.cuda.stream(self.stream):
+            self.U = torch.empty(nbytes // (8 if self.desc.precision == 1 else 4), dtype=self.dtype, device=self.device)
+        self.stats = None
+        self.adj_ws = None
+
+    # ---- shapes
+    def level_shape(self, level=0):
+        d = self.desc
+        if d.n_levels > 1:
+            n = list(d.level_n[level])
+            b = d.level_batch[level]
+        else:
+            n = list(d.n)
+            b = d.batch
+        return (b, self.nv, n[2], n[1], n[0])
+
+    def state(self, level=0):
+        """View of the state of one level as [B, nv, nz, ny, nx]."""
+        off = 0
+        for l in range(level):
+            sh = self.level_shape(l)
+            off += sh[0] * sh[1] * sh[2] * sh[3] * sh[4]
+        sh = self.level_shape(level)
+        cnt = sh[0] * sh[1] * sh[2] * sh[3] * sh[4]
+        return self.U[off:off + cnt].view(sh)
+
+    # ---- calls
+    def set_initial_data(self, kind="kh", theta=None):
+        n_params = 0 if theta is None else int(theta.shape[-1])
+        A.alsv_set_initial_data(self.ctx, kind, theta, n_params, self.U)
+
+    def set_state(self, U_host_or_dev):
+        """Copy a full state into the bound buffer and initialise time (RAW initial data)."""
+        src = U_host_or_dev.reshape(-1).to(device=self.device, dtype=self.dtype)
+        with self.torch.cuda.stream(self.stream):
+            self.U.copy_(src, non_blocking=False)
+        A.alsv_set_initial_data(self.ctx, "raw", None, 0, self.U)
+
+    def step(self, n=1):
+        A.alsv_step(self.ctx, n)
+
+    def evolve_to(self, T):
+        return A.alsv_evolve_to_T(self.ctx, T)
+
+    def sync(self):
+        A.alsv_sync(self.ctx)
+
+    def time(self):
+        return A.alsv_get_time(self.ctx)
+
+    def stats_init(self):
+        nb = A.alsv_stats_bytes(self.ctx)
+        with self.torch.cuda.stream(self.stream):
+            self.stats = self.torch.empty(nb, dtype=self.torch.uint8, device=self.device)
+        A.alsv_stats_reset(self.ctx, self.stats)
+
+    def stats_accumulate(self):
+        if self.stats is None:
+            self.stats_init()
+        A.alsv_stats_accumulate(self.ctx, self.stats)
+
+    def stats_read(self):
+        b, nv, nz, ny, nx = self.level_shape(0)
+        with self.torch.cuda.stream(self.stream):
+            mean = self.torch.empty((nv, nz, ny, nx), dtype=self.torch.float64, device=self.device)
+            var = self.torch.empty_like(mean)
+        cnt = A.alsv_stats_read(self.ctx, self.stats, mean, var)
+        return cnt, mean, var
+
+    def totals(self):
+        with self.torch.cuda.stream(self.stream):
+            out = self.torch.empty((self.samples, self.nv), dtype=self.torch.float64, device=self.device)
+        A.alsv_conservation_totals(self.ctx, out)
+        return out
+
+    def kinetic_energy(self):
+        with self.torch.cuda.stream(self.stream):
+            out = self.torch.empty(self.samples, dtype=self.torch.float64, device=self.device)
+        A.alsv_kinetic_energy(self.ctx, out)
+        return out
+
+    def autotune(self, reps=3):
+        return A.alsv_autotune(self.ctx, reps)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            A.alsv_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

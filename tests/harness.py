@@ -1,0 +1,57 @@
+"""Helpers for GPU-vs-oracle parity tests: build one configuration for both sides, run, compare."""
+import numpy as np
+import pytest
+
+import oracle
+
+
+def both_descs(**cfg):
+    import paper_1912_07645_gb300 as alsv
+    return alsv.make_desc(**cfg), oracle.make_desc(**cfg)
+
+
+def gpu_solver(**cfg):
+    import paper_1912_07645_gb300 as alsv
+    return alsv.Solver(alsv.make_desc(**cfg))
+
+
+def host(t) -> np.ndarray:
+    return t.detach().to("cpu").double().numpy()
+
+
+def p1_check(g: np.ndarray, o: np.ndarray, rel: float = 1e-12, what: str = ""):
+    """FP64 parity: per cell |g - o| <= rel * max(|o|, max_v |o_v|) (per-variable floor)."""
+    assert g.shape == o.shape, (g.shape, o.shape)
+    nv = o.shape[1]
+    bad_total = 0
+    worst = 0.0
+    for v in range(nv):
+        ov, gv = o[:, v], g[:, v]
+        floor = np.abs(ov).max()
+        scale = np.maximum(np.abs(ov), floor if floor > 0 else 1.0)
+        err = np.abs(gv - ov) / scale
+        bad_total += int((err > rel).sum())
+        worst = max(worst, float(err.max()))
+    assert bad_total == 0, f"{what}: {bad_total} cells differ by more than {rel} (worst {worst:.3e})"
+    return worst
+
+
+def p2_check(g: np.ndarray, o: np.ndarray, rel: float = 2e-5, what: str = ""):
+    """FP32 parity: relative L1 per variable, sum|g - o| / sum|o| <= rel (floor for zero fields)."""
+    nv = o.shape[1]
+    worst = 0.0
+    for v in range(nv):
+        num = np.abs(g[:, v] - o[:, v]).sum()
+        den = np.abs(o[:, v]).sum()
+        if den == 0:
+            den = o[:, v].size * max(1.0, np.abs(o).max())
+        worst = max(worst, num / den)
+    assert worst <= rel, f"{what}: relative L1 {worst:.3e} > {rel}"
+    return worst
+
+
+def need_gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    return torch

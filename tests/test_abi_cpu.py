@@ -1,0 +1,135 @@
+"""Host-side checks of the C ABI (no GPU): the library loads, exports every entry point that
+include/alsv.h declares, and validates descriptors without touching the device."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def alsv():
+    from paper_1912_07645_gb300 import build
+    build.build()
+    import paper_1912_07645_gb300 as a
+    a.load()
+    return a
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "alsv.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(alsv_\w+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["alsv_init_grid", "alsv_set_initial_data", "alsv_step", "alsv_evolve_to_T",
+                     "alsv_stats_accumulate", "alsv_stats_read", "alsv_adjoint_evolve",
+                     "alsv_conservation_totals", "alsv_destroy", "alsv_last_error"]:
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(alsv):
+    lib = alsv.load()
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_symbol(alsv):
+    from paper_1912_07645_gb300 import _abi
+    assert set(declared_functions()) == set(_abi.SIGNATURES)
+    for n in declared_functions():
+        assert hasattr(_abi, n)
+
+
+def test_version(alsv):
+    assert "alsv" in alsv.alsv_version()
+
+
+def test_workspace_and_state_sizes(alsv):
+    d = alsv.make_desc(ndim=2, n=(256, 256), batch=4096, precision="fp32", recon="weno3", rk="ssprk3")
+    ctx, ws = alsv.alsv_init_grid(d, 0)
+    try:
+        assert alsv.alsv_state_bytes(ctx) == 4096 * 4 * 256 * 256 * 4
+        assert ws >= 2 * alsv.alsv_state_bytes(ctx)      # RK3 keeps two stage buffers
+        assert alsv.alsv_num_samples(ctx) == 4096 and alsv.alsv_num_vars(ctx) == 4
+        (tx, ty, tz), v, work = alsv.alsv_get_tile(ctx)
+        assert work == 4096 * ((256 + tx - 1) // tx) * ((256 + ty - 1) // ty)
+        assert alsv.alsv_stats_bytes(ctx) == 256 + 2 * 4 * 256 * 256 * 8
+    finally:
+        alsv.alsv_destroy(ctx)
+    d2 = alsv.make_desc(ndim=2, n=(256, 256), batch=4096, precision="fp32", rk="ssprk2")
+    ctx, ws2 = alsv.alsv_init_grid(d2, 0)
+    alsv.alsv_destroy(ctx)
+    assert ws2 < ws                                      # RK2 needs one stage buffer
+
+
+def test_mlmc_level_table_sizes(alsv):
+    lv = [((64, 64), 4096), ((128, 128), 1024), ((256, 256), 256), ((512, 512), 64)]
+    d = alsv.make_desc(ndim=2, levels=lv, precision="fp32", recon="weno3", rk="ssprk3")
+    ctx, _ = alsv.alsv_init_grid(d, 0)
+    try:
+        assert alsv.alsv_num_samples(ctx) == 4096 + 1024 + 256 + 64
+        assert alsv.alsv_state_bytes(ctx) == sum(b * 4 * n[0] * n[1] * 4 for n, b in lv)
+    finally:
+        alsv.alsv_destroy(ctx)
+
+
+@pytest.mark.parametrize("field,value,msg", [
+    ("ndim", 0, "ndim"), ("ndim", 4, "ndim"), ("eq", 7, "eq"), ("recon", 3, "recon"), ("flux", 9, "flux"),
+    ("rk", 4, "rk"), ("precision", 2, "precision"), ("gamma", 1.0, "gamma"), ("batch", 0, "batch"),
+    ("cfl", 0.0, "cfl"), ("weno_eps", -1.0, "weno_eps"),
+])
+def test_descriptor_validation(alsv, field, value, msg):
+    d = alsv.make_desc(ndim=2, n=(16, 16), batch=2)
+    setattr(d, field, value)
+    with pytest.raises(alsv.AlsvError) as ei:
+        alsv.alsv_init_grid(d, 0)
+    assert ei.value.status_name == "ERR_INVALID_ARG"
+    assert msg in str(ei.value)
+
+
+def test_validation_of_boundaries_and_sizes(alsv):
+    d = alsv.make_desc(ndim=1, n=(16,), bc=[("periodic", "outflow")])
+    with pytest.raises(alsv.AlsvError, match="periodic"):
+        alsv.alsv_init_grid(d, 0)
+    d = alsv.make_desc(ndim=1, n=(1,), recon="weno3", bc="reflective")
+    with pytest.raises(alsv.AlsvError, match="reflective"):
+        alsv.alsv_init_grid(d, 0)
+    d = alsv.make_desc(ndim=2, n=(0, 4))
+    with pytest.raises(alsv.AlsvError, match="n >= 1"):
+        alsv.alsv_init_grid(d, 0)
+    d = alsv.make_desc(ndim=1, n=(8,))
+    d.reserved[3] = 1
+    with pytest.raises(alsv.AlsvError, match="reserved"):
+        alsv.alsv_init_grid(d, 0)
+    # tiny and ragged grids are valid
+    for n in (1, 2, 3, 7, 257):
+        ctx, _ = alsv.alsv_init_grid(alsv.make_desc(ndim=1, n=(n,), recon="pc", bc="periodic"), 0)
+        alsv.alsv_destroy(ctx)
+
+
+def test_calls_before_binding_report_not_ready(alsv):
+    ctx, _ = alsv.alsv_init_grid(alsv.make_desc(ndim=1, n=(8,)), 0)
+    try:
+        with pytest.raises(alsv.AlsvError) as ei:
+            alsv.alsv_step(ctx, 1)
+        assert ei.value.status_name == "ERR_NOT_READY"
+        with pytest.raises(alsv.AlsvError) as ei:
+            alsv.alsv_bind_workspace(ctx, 0x1000, 16)
+        assert ei.value.status_name == "ERR_BUFFER_TOO_SMALL"
+        with pytest.raises(alsv.AlsvError, match="aligned"):
+            alsv.alsv_bind_workspace(ctx, 0x1001, 1 << 30)
+    finally:
+        alsv.alsv_destroy(ctx)
+
+
+def test_product_package_does_not_import_the_oracle():
+    pkg = os.path.join(ROOT, "paper_1912_07645_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                src = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in src and "from oracle" not in src and "alsv_oracle" not in src, f

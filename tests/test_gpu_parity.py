@@ -1,0 +1,391 @@
+"""GPU (libalsv.so through the C ABI) vs the FP64 CPU oracle, element by element.
+
+FP64: per cell within 1e-12 relative (floor: 1e-12 * max |U_v|), FMA contraction and
+reciprocal-multiplication being the only differences. FP32: within 2e-5 relative L1. Sizes are
+small enough for the oracle but span several tiles and ragged tails; the full-size batched
+configuration is checked on sampled outputs.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from harness import gpu_solver, host, need_gpu, p1_check, p2_check
+from inputs import burgers_state, euler_state, kh_theta
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    need_gpu()
+    from paper_1912_07645_gb300 import build
+    build.build()
+
+
+def torch_():
+    import torch
+    return torch
+
+
+def run_gpu(cfg, init=None, theta=None, U0=None, steps=None, T=None):
+    torch = torch_()
+    S = gpu_solver(**cfg)
+    if U0 is not None:
+        S.set_state(torch.from_numpy(np.ascontiguousarray(U0)))
+    else:
+        th = None if theta is None else torch.from_numpy(np.ascontiguousarray(theta)).cuda()
+        S.set_initial_data(init, theta=th)
+    nsteps = None
+    if steps is not None:
+        S.step(steps)
+        S.sync()
+    if T is not None:
+        nsteps = S.evolve_to(T)
+    out = host(S.U).reshape(S.level_shape(0)) if S.desc.n_levels <= 1 else None
+    t, st = S.time()
+    S.close()
+    return out, t, st, nsteps
+
+
+def run_oracle(cfg, init=None, theta=None, U0=None, steps=None, T=None):
+    d = oracle.make_desc(**cfg)
+    B = cfg.get("batch", 1)
+    U = U0.copy() if U0 is not None else oracle.init(d, init, B, theta, center=cfg.get("vortex_center", (5, 5)))
+    if steps is not None:
+        return oracle.evolve(d, U, T=math.inf, max_steps=steps)
+    return oracle.evolve(d, U, T=T)
+
+
+# ------------------------------------------------------------------ parameters and initial data
+def test_theta_splitmix_bitwise():
+    torch = torch_()
+    import paper_1912_07645_gb300 as alsv
+    S = gpu_solver(ndim=2, n=(16, 16), batch=64, seed=12345, precision="fp64")
+    S.set_initial_data("kh")
+    th = torch.empty((64, 20), dtype=torch.float64, device="cuda")
+    alsv.alsv_get_parameters(S.ctx, th)
+    S.sync()
+    assert np.array_equal(host(th), oracle.theta_splitmix(12345, 64, 20))
+    S3 = gpu_solver(ndim=3, n=(8, 8, 8), batch=3, seed=77, precision="fp32")
+    S3.set_initial_data("kh")
+    th3 = torch.empty((3, 128), dtype=torch.float64, device="cuda")
+    alsv.alsv_get_parameters(S3.ctx, th3)
+    S3.sync()
+    assert np.array_equal(host(th3), oracle.theta_splitmix(77, 3, 128))
+
+
+@pytest.mark.parametrize("case", ["kh2", "kh3", "sod", "lax", "burgers", "vortex"])
+def test_initial_data_fp64(case):
+    if case == "kh2":
+        cfg = dict(ndim=2, n=(70, 45), batch=3, eq="euler")
+        th = kh_theta(3, 1)
+        init = "kh"
+    elif case == "kh3":
+        cfg = dict(ndim=3, n=(12, 10, 9), batch=2, eq="euler")
+        th = kh_theta(2, 2, P=128)
+        init = "kh"
+    elif case in ("sod", "lax"):
+        cfg = dict(ndim=1, n=(301,), eq="euler")
+        th, init = None, case
+    elif case == "burgers":
+        cfg = dict(ndim=1, n=(97,), eq="burgers")
+        th, init = None, "burgers_sine"
+    else:
+        cfg = dict(ndim=2, n=(24, 20), lo=(0, 0), hi=(10, 10), eq="euler", vortex_center=(5.0, 4.5))
+        th, init = None, "vortex"
+    cfg["precision"] = "fp64"
+    g, *_ = run_gpu(cfg, init, th, steps=0)
+    d = oracle.make_desc(**cfg)
+    o = oracle.init(d, init, cfg.get("batch", 1), th, center=cfg.get("vortex_center", (5, 5)))
+    p1_check(g, o, rel=1e-13, what=case)
+
+
+# ------------------------------------------------------------------ one and ten steps, FP64
+CASES_1D = [(r, f, v) for r in ("pc", "mc", "weno3") for f in ("rusanov", "hll", "hllc") for v in ("prim", "cons")]
+
+
+@pytest.mark.parametrize("recon,flux,rvars", CASES_1D)
+@pytest.mark.parametrize("steps", [1, 10])
+def test_euler_1d_steps_fp64(recon, flux, rvars, steps):
+    cfg = dict(ndim=1, n=(300,), eq="euler", recon=recon, flux=flux, rvars=rvars, rk="ssprk2",
+               bc="outflow", cfl=0.45, precision="fp64")
+    g, t, st, _ = run_gpu(cfg, "sod", steps=steps)
+    o, ost, ot = run_oracle(cfg, "sod", steps=steps)
+    assert st[0] == ost[0] == steps
+    assert t[0] == pytest.approx(ot[0], rel=1e-13)
+    p1_check(g, o, what=f"sod {recon} {flux} {rvars}")
+
+
+@pytest.mark.parametrize("bc,init,rk", [("reflective", "sod", "ssprk3"), ("outflow", "lax", "ssprk3"),
+                                        ("periodic", "raw", "ssprk3"), ("reflective", "raw", "ssprk2")])
+def test_euler_1d_boundaries_fp64(bc, init, rk):
+    cfg = dict(ndim=1, n=(257,), batch=2, eq="euler", recon="weno3", flux="hllc", rvars="prim", rk=rk, bc=bc,
+               cfl=0.45, precision="fp64")
+    U0 = euler_state(2, 1, (257,), seed=5) if init == "raw" else None
+    g, *_ = run_gpu(cfg, None if init == "raw" else init, U0=U0, steps=10)
+    o, *_ = run_oracle(cfg, None if init == "raw" else init, U0=U0, steps=10)
+    p1_check(g, o, what=f"{bc} {init}")
+
+
+@pytest.mark.parametrize("recon", ["pc", "mc", "weno3"])
+@pytest.mark.parametrize("flux", ["rusanov", "hll", "hllc"])
+def test_burgers_1d_steps_fp64(recon, flux):
+    cfg = dict(ndim=1, n=(200,), batch=3, eq="burgers", recon=recon, flux=flux, rk="ssprk3", bc="periodic",
+               cfl=0.45, precision="fp64")
+    U0 = burgers_state(3, 200, seed=9)
+    g, *_ = run_gpu(cfg, U0=U0, steps=10)
+    o, *_ = run_oracle(cfg, U0=U0, steps=10)
+    p1_check(g, o, what=f"burgers {recon} {flux}")
+
+
+CASES_2D = [("weno3", "hllc", "prim", "ssprk3"), ("mc", "rusanov", "cons", "ssprk2"), ("pc", "hll", "prim", "ssprk2"),
+            ("weno3", "hll", "cons", "ssprk3"), ("mc", "hllc", "prim", "ssprk3"), ("weno3", "rusanov", "prim", "ssprk2")]
+
+
+@pytest.mark.parametrize("recon,flux,rvars,rk", CASES_2D)
+def test_kh_2d_steps_fp64(recon, flux, rvars, rk):
+    cfg = dict(ndim=2, n=(70, 45), batch=2, eq="euler", recon=recon, flux=flux, rvars=rvars, rk=rk,
+               bc="periodic", cfl=0.4, precision="fp64")
+    th = kh_theta(2, 11)
+    g, t, st, _ = run_gpu(cfg, "kh", th, steps=10)
+    o, ost, ot = run_oracle(cfg, "kh", th, steps=10)
+    np.testing.assert_allclose(t, ot, rtol=1e-13)
+    p1_check(g, o, what=f"kh2d {recon} {flux} {rvars} {rk}")
+
+
+def test_2d_mixed_boundaries_fp64():
+    cfg = dict(ndim=2, n=(37, 50), batch=2, eq="euler", recon="weno3", flux="hllc", rvars="prim", rk="ssprk3",
+               bc=[("outflow", "reflective"), ("reflective", "outflow")], cfl=0.4, precision="fp64")
+    U0 = euler_state(2, 2, (37, 50), seed=3)
+    g, *_ = run_gpu(cfg, U0=U0, steps=8)
+    o, *_ = run_oracle(cfg, U0=U0, steps=8)
+    p1_check(g, o, what="2d mixed bc")
+
+
+def test_burgers_2d_fp64():
+    cfg = dict(ndim=2, n=(40, 33), batch=1, eq="burgers", recon="mc", flux="hll", rk="ssprk2", bc="periodic",
+               cfl=0.4, precision="fp64")
+    x = np.arange(40) / 40
+    y = np.arange(33) / 33
+    U0 = (np.sin(2 * np.pi * x)[None, :] * 0.5 + np.cos(2 * np.pi * y)[:, None] * 0.3)[None, None, None]
+    g, *_ = run_gpu(cfg, U0=U0, steps=10)
+    o, *_ = run_oracle(cfg, U0=U0, steps=10)
+    p1_check(g, o, what="burgers 2d")
+
+
+@pytest.mark.parametrize("recon,flux,rvars,bc", [("weno3", "hllc", "prim", "periodic"),
+                                                 ("mc", "rusanov", "cons", [("periodic", "periodic"), ("outflow", "outflow"), ("reflective", "reflective")])])
+def test_kh_3d_steps_fp64(recon, flux, rvars, bc):
+    cfg = dict(ndim=3, n=(20, 18, 17), batch=1, eq="euler", recon=recon, flux=flux, rvars=rvars, rk="ssprk3",
+               bc=bc, cfl=0.3, precision="fp64")
+    th = kh_theta(1, 4, P=128)
+    g, *_ = run_gpu(cfg, "kh", th, steps=4)
+    o, *_ = run_oracle(cfg, "kh", th, steps=4)
+    p1_check(g, o, what=f"kh3d {recon} {flux}")
+
+
+# ------------------------------------------------------------------ full runs to T (non-chaotic)
+def test_sod_config_full_run_fp64():
+    cfg = dict(ndim=1, n=(1024,), eq="euler", recon="mc", flux="hllc", rvars="prim", rk="ssprk2", bc="outflow",
+               cfl=0.45, precision="fp64")
+    g, t, st, n = run_gpu(cfg, "sod", T=0.2)
+    o, ost, ot = run_oracle(cfg, "sod", T=0.2)
+    assert n == ost[0] and t[0] == 0.2 and ot[0] == 0.2
+    p1_check(g, o, what="sod full")
+
+
+def test_burgers_full_run_fp64():
+    cfg = dict(ndim=1, n=(512,), eq="burgers", recon="weno3", flux="rusanov", rk="ssprk3", bc="periodic",
+               cfl=0.45, precision="fp64")
+    g, t, st, n = run_gpu(cfg, "burgers_sine", T=0.1)
+    o, ost, _ = run_oracle(cfg, "burgers_sine", T=0.1)
+    assert n == ost[0]
+    p1_check(g, o, what="burgers full")
+
+
+def test_vortex_full_run_fp64():
+    cfg = dict(ndim=2, n=(32, 32), lo=(0, 0), hi=(10, 10), eq="euler", recon="weno3", flux="hllc", rvars="cons",
+               rk="ssprk3", bc="periodic", cfl=0.4, precision="fp64", weno_eps_dx2=True)
+    g, t, st, n = run_gpu(cfg, "vortex", T=1.0)
+    o, ost, _ = run_oracle(cfg, "vortex", T=1.0)
+    assert n == ost[0]
+    p1_check(g, o, what="vortex full")
+
+
+# ------------------------------------------------------------------ FP32
+def test_kh_2d_fp32_ten_steps():
+    cfg = dict(ndim=2, n=(64, 64), batch=2, eq="euler", recon="weno3", flux="hllc", rvars="prim", rk="ssprk3",
+               bc="periodic", cfl=0.4, precision="fp32")
+    th = kh_theta(2, 21)
+    g, *_ = run_gpu(cfg, "kh", th, steps=10)
+    o, *_ = run_oracle(cfg, "kh", th, steps=10)
+    p2_check(g, o, what="kh fp32")
+
+
+def test_sod_fp32_full_run():
+    cfg = dict(ndim=1, n=(1024,), eq="euler", recon="mc", flux="hllc", rvars="prim", rk="ssprk2", bc="outflow",
+               cfl=0.45, precision="fp32")
+    g, *_ = run_gpu(cfg, "sod", T=0.2)
+    o, *_ = run_oracle(cfg, "sod", T=0.2)
+    p2_check(g, o, what="sod fp32")
+
+
+def test_kh_3d_fp32():
+    cfg = dict(ndim=3, n=(24, 20, 16), batch=1, eq="euler", recon="weno3", flux="hllc", rvars="prim", rk="ssprk3",
+               bc="periodic", cfl=0.3, precision="fp32")
+    th = kh_theta(1, 8, P=128)
+    g, *_ = run_gpu(cfg, "kh", th, steps=3)
+    o, *_ = run_oracle(cfg, "kh", th, steps=3)
+    p2_check(g, o, what="kh3d fp32")
+
+
+# ------------------------------------------------------------------ determinism and invariances
+def test_determinism_graphs_variants_and_batch_independence():
+    torch = torch_()
+    import paper_1912_07645_gb300 as alsv
+    cfg = dict(ndim=2, n=(64, 64), batch=6, eq="euler", recon="weno3", flux="hllc", rvars="prim", rk="ssprk3",
+               bc="periodic", cfl=0.4, precision="fp32", seed=42)
+    outs = []
+    for graphs, variant in ((True, 0), (True, 0), (False, 0), (True, 1)):
+        S = gpu_solver(**cfg)
+        alsv.alsv_set_graphs(S.ctx, graphs)
+        alsv.alsv_set_tile_variant(S.ctx, variant)
+        S.set_initial_data("kh")
+        S.evolve_to(0.05)
+        outs.append(host(S.U))
+        S.close()
+    for o in outs[1:]:
+        assert np.array_equal(outs[0], o)
+    # sample 3 of the batch equals a single-sample run on the same parameters
+    th = torch.from_numpy(oracle.theta_splitmix(42, 6, 20)[3:4].copy()).cuda()
+    S1 = gpu_solver(**dict(cfg, batch=1))
+    S1.set_initial_data("kh", theta=th)
+    S1.evolve_to(0.05)
+    one = host(S1.U)
+    assert np.array_equal(outs[0].reshape(6, -1)[3], one.reshape(-1))
+
+
+def test_totals_and_kinetic_energy_fp64():
+    cfg = dict(ndim=2, n=(70, 45), batch=3, eq="euler", recon="weno3", flux="hllc", rvars="prim", rk="ssprk3",
+               bc="periodic", cfl=0.4, precision="fp64")
+    th = kh_theta(3, 13)
+    torch = torch_()
+    S = gpu_solver(**cfg)
+    S.set_initial_data("kh", theta=torch.from_numpy(th).cuda())
+    tot0 = host(S.totals())
+    S.step(20)
+    tot1 = host(S.totals())
+    ke = host(S.kinetic_energy())
+    U = host(S.U).reshape(S.level_shape(0))
+    S.sync()
+    d = oracle.make_desc(**cfg)
+    scale = np.abs(U).reshape(3, 4, -1).sum(axis=2) / (70 * 45)
+    np.testing.assert_allclose(tot1, oracle.totals(d, U), rtol=0, atol=1e-14 * scale.max())
+    np.testing.assert_allclose(ke, oracle.kinetic_energy(d, U), rtol=1e-13)
+    # eq. (2.1) on a periodic grid conserves every total
+    assert np.all(np.abs(tot1 - tot0) <= 1e-13 * np.maximum(scale, 1e-300))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_welford_statistics_match_oracle(precision):
+    torch = torch_()
+    cfg = dict(ndim=2, n=(40, 36), batch=16, eq="euler", recon="mc", flux="hllc", rvars="prim", rk="ssprk2",
+               bc="periodic", cfl=0.4, precision=precision, seed=5)
+    S = gpu_solver(**cfg)
+    S.set_initial_data("kh")
+    S.step(3)
+    S.stats_init()
+    S.stats_accumulate()
+    U1 = host(S.U).reshape(S.level_shape(0))
+    S.step(2)
+    S.stats_accumulate()          # streaming: a second batch folds in after the first
+    U2 = host(S.U).reshape(S.level_shape(0))
+    cnt, mean, var = S.stats_read()
+    mean, var = host(mean), host(var)
+    d = oracle.make_desc(**cfg)
+    c, m, M2 = oracle.welford(d, U1)
+    c, m, M2 = oracle.welford(d, U2, c, m, M2)
+    assert cnt == c == 32
+    np.testing.assert_allclose(mean.reshape(4, -1), m, rtol=1e-13, atol=1e-15)
+    np.testing.assert_allclose(var.reshape(4, -1), M2 / (c - 1), rtol=1e-11, atol=1e-15)
+
+
+# ------------------------------------------------------------------ full-size batched configuration, sampled
+def test_full_size_batched_kh_sampled():
+    """256^2 x 4096 samples, FP32 WENO3 + HLLC + SSP-RK3 (the benchmark workload, launched as the
+    benchmark launches it); three sampled samples against the oracle after two CFL steps."""
+    torch = torch_()
+    import paper_1912_07645_gb300 as alsv
+    cfg = dict(ndim=2, n=(256, 256), batch=4096, eq="euler", recon="weno3", flux="hllc", rvars="prim", rk="ssprk3",
+               bc="periodic", cfl=0.4, precision="fp32", seed=12345)
+    S = gpu_solver(**cfg)
+    S.set_initial_data("kh")
+    alsv.alsv_autotune(S.ctx, 2)
+    S.step(2)
+    S.sync()
+    V = S.state()
+    picks = [0, 1234, 4095]
+    g = np.stack([host(V[b]) for b in picks])
+    t, st = S.time()
+    S.close()
+    del V
+    torch.cuda.empty_cache()
+    th = oracle.theta_splitmix(12345, 4096, 20)[picks]
+    ocfg = dict(cfg, batch=3)
+    o, ost, ot = run_oracle(ocfg, "kh", th, steps=2)
+    np.testing.assert_allclose(t[picks], ot, rtol=1e-6)
+    p2_check(g, o, what="full-size sampled")
+
+
+def test_mlmc_levels_one_launch_fp32():
+    torch = torch_()
+    import paper_1912_07645_gb300 as alsv
+    lv = [((32, 32), 6), ((64, 64), 3), ((96, 96), 2)]
+    cfg = dict(ndim=2, levels=lv, eq="euler", recon="weno3", flux="hllc", rvars="prim", rk="ssprk3",
+               bc="periodic", cfl=0.4, precision="fp32", seed=99)
+    S = gpu_solver(**cfg)
+    S.set_initial_data("kh")
+    S.step(3)
+    S.sync()
+    th_all = oracle.theta_splitmix(99, 11, 20)
+    s0 = 0
+    for l, (n, B) in enumerate(lv):
+        g = host(S.state(l))
+        ocfg = dict(cfg, n=n, batch=B)
+        ocfg.pop("levels")
+        o, *_ = run_oracle(ocfg, "kh", th_all[s0:s0 + B], steps=3)
+        p2_check(g, o, what=f"level {l}")
+        s0 += B
+    S.close()
+
+
+# ------------------------------------------------------------------ failure reporting (host-side injection)
+def test_nonphysical_state_is_reported_and_gpu_stays_usable():
+    torch = torch_()
+    import paper_1912_07645_gb300 as alsv
+    cfg = dict(ndim=1, n=(64,), batch=2, eq="euler", recon="mc", flux="hllc", rk="ssprk2", bc="outflow",
+               precision="fp64")
+    U0 = euler_state(2, 1, (64,), seed=1)
+    U0[1, 2, 0, 0, 10] = -5.0            # negative pressure in sample 1
+    S = gpu_solver(**cfg)
+    S.set_state(torch.from_numpy(U0))
+    with pytest.raises(alsv.AlsvError) as ei:
+        S.evolve_to(0.1)
+    assert ei.value.status_name == "ERR_NONPHYSICAL"
+    S.close()
+    g, *_ = run_gpu(cfg, "sod", steps=2)
+    assert np.isfinite(g).all()
+
+
+def test_fixed_dt_cfl_guard():
+    import paper_1912_07645_gb300 as alsv
+    cfg = dict(ndim=1, n=(64,), eq="euler", recon="mc", flux="rusanov", rk="ssprk2", bc="outflow",
+               precision="fp64", fixed_dt=0.02)     # CFL = 0.02 * 1.18 * 64 > 0.5
+    S = gpu_solver(**cfg)
+    S.set_initial_data("sod")
+    with pytest.raises(alsv.AlsvError) as ei:
+        S.evolve_to(0.1)
+    assert ei.value.status_name == "ERR_CFL"
+    S.close()

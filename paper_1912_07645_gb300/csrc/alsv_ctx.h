@@ -1,0 +1,73 @@
+// Host-side context of the C ABI (internal; shared by alsv_api.cu and adjoint.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/alsv.h"
+#include "alsv_internal.h"
+
+namespace alsv {
+struct Profile {
+    bool on = false;
+    double stage_ms = 0.0, finish_ms = 0.0;
+    long long stage_launches = 0, finish_launches = 0;
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> kinds;  // 0 stage, 1 finish; kinds[i] is the kernel between ev[i] and ev[i+1]
+};
+}  // namespace alsv
+
+struct alsv_ctx {
+    alsv_grid_desc d;
+    cudaStream_t stream = nullptr;
+    int fp64 = 0, ndim = 1, nv = 1, eq = 1, G = 2, nstages = 2;
+    int variant = 0;
+    alsv::GridArgs g;
+    int total_samples = 0;
+    long long max_work = 0;  // largest work-item count over the tile variants
+    size_t state_bytes = 0, ws_bytes = 0;
+    int P = 0;               // KH parameters per sample
+    // workspace regions
+    char* ws = nullptr;
+    void* A = nullptr;
+    void* Bb = nullptr;
+    double* part = nullptr;
+    double* t = nullptr;
+    double* dt = nullptr;
+    int64_t* nstep = nullptr;
+    int* done = nullptr;
+    int* last = nullptr;
+    int* status = nullptr;
+    double* T_end = nullptr;
+    long long* n_target = nullptr;
+    double* theta = nullptr;
+    double* red = nullptr;
+    // state
+    void* U = nullptr;
+    bool time_ready = false;
+    // graph cache
+    cudaGraphExec_t gexec = nullptr;
+    void* g_U = nullptr;
+    int g_variant = -1;
+    int g_steps = 0;
+    bool graphs_enabled = true;
+    // host staging
+    std::vector<int> h_done;
+    long long launches = 0;
+    alsv::Profile prof;
+    std::string err;
+    // adjoint workspace (caller-owned)
+    char* adj_ws = nullptr;
+    size_t adj_bytes = 0;
+    bool have_theta = false;
+};
+
+namespace alsv {
+// shared helpers implemented in alsv_api.cu
+alsv_status ctx_fail(alsv_ctx* c, alsv_status st, const std::string& msg);
+alsv_status ctx_cuda_fail(alsv_ctx* c, cudaError_t e, const char* what);
+FinishArgs ctx_finish_args(alsv_ctx* c, int advance);
+StageArgs ctx_stage_args(alsv_ctx* c, const void* Us, const void* Un, void* Uout, double a, double b, bool want_speed);
+}  // namespace alsv

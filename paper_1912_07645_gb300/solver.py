@@ -55,7 +55,8 @@ class Solver:
     """One context with its workspace and state held as torch CUDA tensors.
 
     ``stream``: a torch.cuda.Stream (default: a new stream, so step chunks can be captured in CUDA
-    graphs). All calls enqueue work on that stream.
+    graphs). All calls enqueue work on that stream; tensors returned by the methods are written on
+    it, so synchronise (``sync()``) before reading them from another stream or the host.
     """
 
     def __init__(self, desc: A.alsv_grid_desc | None = None, stream=None, device="cuda", **kw):
@@ -121,6 +122,11 @@ class Solver:
     def sync(self):
         A.alsv_sync(self.ctx)
 
+    def to_host(self, t):
+        """Copy a tensor produced on this solver's stream to the host (waits for the stream)."""
+        self.stream.synchronize()
+        return t.detach().cpu()
+
     def time(self):
         return A.alsv_get_time(self.ctx)
 
@@ -154,6 +160,23 @@ class Solver:
             out = self.torch.empty(self.samples, dtype=self.torch.float64, device=self.device)
         A.alsv_kinetic_energy(self.ctx, out)
         return out
+
+    def adjoint(self, theta, T):
+        """Kinetic energy J at T and dJ/dtheta for every sample (theta: [samples, 20] FP64 on the
+        device). Allocates the adjoint workspace on first use; synchronous."""
+        torch = self.torch
+        need = A.alsv_adjoint_workspace_bytes(self.ctx, T)
+        if self.adj_ws is None or self.adj_ws.numel() < need:
+            self.adj_ws = None
+            with torch.cuda.stream(self.stream):
+                self.adj_ws = torch.empty(need, dtype=torch.uint8, device=self.device)
+        A.alsv_bind_adjoint_workspace(self.ctx, self.adj_ws)
+        with torch.cuda.stream(self.stream):
+            th = theta.to(device=self.device, dtype=torch.float64).contiguous()
+            J = torch.empty(self.samples, dtype=torch.float64, device=self.device)
+            g = torch.empty((self.samples, 20), dtype=torch.float64, device=self.device)
+        A.alsv_adjoint_evolve(self.ctx, T, 0, th, g, J)
+        return J, g
 
     def autotune(self, reps=3):
         return A.alsv_autotune(self.ctx, reps)

@@ -16,6 +16,10 @@ def gpu_solver(**cfg):
 
 
 def host(t) -> np.ndarray:
+    """Copy a device tensor to host after all streams finished (the solver works on its own
+    non-blocking stream, so a plain .cpu() on the default stream could race with it)."""
+    import torch
+    torch.cuda.synchronize()
     return t.detach().to("cpu").double().numpy()
 
 

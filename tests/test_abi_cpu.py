@@ -133,3 +133,21 @@ def test_product_package_does_not_import_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 src = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in src and "from oracle" not in src and "alsv_oracle" not in src, f
+
+
+def test_adjoint_validation_without_gpu(alsv):
+    ctx, _ = alsv.alsv_init_grid(alsv.make_desc(ndim=2, n=(16, 16), recon="weno3", flux="hllc"), 0)
+    try:
+        with pytest.raises(alsv.AlsvError, match="Rusanov"):
+            alsv.alsv_adjoint_workspace_bytes(ctx, 0.1)
+    finally:
+        alsv.alsv_destroy(ctx)
+    ctx, _ = alsv.alsv_init_grid(alsv.make_desc(ndim=2, n=(512, 512), batch=64, recon="mc", flux="rusanov",
+                                                rk="ssprk2", precision="fp64", cfl=0.4), 0)
+    try:
+        b = alsv.alsv_adjoint_workspace_bytes(ctx, 1.0)
+        state = 64 * 4 * 512 * 512 * 8
+        # n = 3035 steps, ceil(sqrt(n)) = 56: 55 checkpoints + 55 segment states + 3 adjoint buffers
+        assert b >= (55 + 55 + 3) * state and b < (55 + 55 + 3) * state + (1 << 24)
+    finally:
+        alsv.alsv_destroy(ctx)

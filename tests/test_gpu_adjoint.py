@@ -1,0 +1,109 @@
+"""Discrete adjoint on the GPU vs the oracle's exact forward-mode (dual number) gradient of the
+same discrete map, vs central finite differences, and through torch.autograd."""
+import numpy as np
+import pytest
+
+import oracle
+from harness import gpu_solver, host, need_gpu
+from inputs import kh_theta
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    need_gpu()
+    from paper_1912_07645_gb300 import build
+    build.build()
+
+
+def gpu_adjoint(cfg, th, T):
+    import torch
+    S = gpu_solver(**cfg)
+    S.set_initial_data("kh", theta=torch.from_numpy(th).cuda())
+    J, g = S.adjoint(torch.from_numpy(th), T)
+    out = host(J), host(g)
+    S.close()
+    return out
+
+
+@pytest.mark.parametrize("recon,rvars,rk", [("mc", "prim", "ssprk2"), ("pc", "cons", "ssprk3"),
+                                            ("mc", "cons", "ssprk3"), ("pc", "prim", "ssprk2")])
+def test_adjoint_fp64_matches_oracle_dual_gradient(recon, rvars, rk):
+    n = 32
+    cfg = dict(ndim=2, n=(n, n), batch=3, eq="euler", recon=recon, rvars=rvars, flux="rusanov", rk=rk,
+               bc="periodic", cfl=0.4, precision="fp64")
+    T = 0.1
+    dt, nsteps = oracle.fixed_dt_kh(n, T, 0.4)
+    assert nsteps == 19      # ragged: 19 steps in checkpoint segments of 5
+    th = kh_theta(3, 31)
+    J, g = gpu_adjoint(cfg, th, T)
+    d = oracle.make_desc(**cfg)
+    for b in range(3):
+        Jo, go = oracle.ke_grad_kh2d(d, th[b], dt, nsteps)
+        assert J[b] == pytest.approx(Jo, rel=1e-13)
+        assert np.abs(g[b] - go).max() <= 1e-10 * np.abs(go).max(), (g[b], go)
+
+
+def test_adjoint_fp64_vs_central_differences():
+    import torch
+    n = 24
+    cfg = dict(ndim=2, n=(n, n), batch=1, eq="euler", recon="mc", rvars="prim", flux="rusanov", rk="ssprk2",
+               bc="periodic", cfl=0.4, precision="fp64")
+    T = 0.2
+    th = kh_theta(1, 5)
+    J, g = gpu_adjoint(cfg, th, T)
+    S = gpu_solver(**dict(cfg, batch=2))
+    fd = np.zeros(20)
+    for j in range(20):
+        h = 1e-6 * max(1.0, abs(th[0, j]))
+        pm = np.concatenate([th, th])
+        pm[0, j] += h
+        pm[1, j] -= h
+        S.set_initial_data("kh", theta=torch.from_numpy(pm).cuda())
+        Jpm, _ = S.adjoint(torch.from_numpy(pm), T)
+        Jpm = host(Jpm)
+        fd[j] = (Jpm[0] - Jpm[1]) / (2 * h)
+    S.close()
+    assert np.abs(g[0] - fd).max() <= 1e-4 * np.abs(g[0]).max(), (g[0], fd)
+
+
+def test_adjoint_fp32_close_to_fp64_oracle():
+    n = 32
+    cfg = dict(ndim=2, n=(n, n), batch=2, eq="euler", recon="mc", rvars="prim", flux="rusanov", rk="ssprk2",
+               bc="periodic", cfl=0.4, precision="fp32")
+    T = 0.1
+    dt, nsteps = oracle.fixed_dt_kh(n, T, 0.4)
+    th = kh_theta(2, 77)
+    J, g = gpu_adjoint(cfg, th, T)
+    d = oracle.make_desc(**cfg)
+    for b in range(2):
+        Jo, go = oracle.ke_grad_kh2d(d, th[b], dt, nsteps)
+        assert J[b] == pytest.approx(Jo, rel=1e-5)
+        assert np.abs(g[b] - go).max() <= 2e-3 * np.abs(go).max()
+
+
+def test_autograd_function_backward():
+    import torch
+    from paper_1912_07645_gb300.autograd import kinetic_energy
+    n = 16
+    cfg = dict(ndim=2, n=(n, n), batch=2, eq="euler", recon="mc", rvars="prim", flux="rusanov", rk="ssprk2",
+               bc="periodic", cfl=0.4, precision="fp64")
+    th = torch.from_numpy(kh_theta(2, 3)).requires_grad_(True)
+    S = gpu_solver(**cfg)
+    S.set_initial_data("kh", theta=th.detach().cuda())
+    J = kinetic_energy(th, S, 0.1)
+    w = torch.tensor([2.0, -0.5], dtype=torch.float64)
+    (J * w).sum().backward()
+    _, g = S.adjoint(th.detach(), 0.1)
+    g = host(g)
+    np.testing.assert_allclose(th.grad.numpy(), w.numpy()[:, None] * g, rtol=1e-14)
+    S.close()
+
+
+def test_adjoint_rejects_unsupported_schemes():
+    import paper_1912_07645_gb300 as alsv
+    S = gpu_solver(ndim=2, n=(16, 16), batch=1, recon="weno3", flux="hllc", precision="fp64")
+    with pytest.raises(alsv.AlsvError, match="Rusanov"):
+        alsv.alsv_adjoint_workspace_bytes(S.ctx, 0.1)
+    S.close()

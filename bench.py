@@ -173,8 +173,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="alsv")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--samples", type=int, default=M, help=argparse.SUPPRESS)
+    ap.add_argument("--samples", type=int, default=M, help="samples per GPU (default 4096; fewer for profiling runs)")
+    ap.add_argument("--T", type=float, default=T_END, help="end time (default 1; shorter for profiling runs)")
     args = ap.parse_args()
+    global T_END
+    T_END = args.T
     if args.impl == "reference":
         return reference_arm(args)
 
@@ -296,7 +299,8 @@ def main():
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "fp32 (stencil); fp64 (statistics, totals, time)",
                 "data": "synthetic (seeded KH perturbation parameters, SplitMix64)",
-                "config": {"workload": WORKLOAD, "grid": [N, N], "samples_per_gpu": Mr, "T": T_END, "cfl": 0.4,
+                "config": {"workload": WORKLOAD if (Mr == M and T_END == 1.0) else f"kh2d_256x256_mc{Mr}_weno3_hllc_ssprk3_fp32_T{T_END:g}",
+                           "grid": [N, N], "samples_per_gpu": Mr, "T": T_END, "cfl": 0.4,
                            "scheme": "WENO3 (primitive) + HLLC + SSP-RK3", "parallelism": f"samples sharded x{world}",
                            "l2": "inputs larger than L2 (4.3 GB state), no flush",
                            "tile_variant": chosen, "autotune_ms": ms_var},

@@ -191,6 +191,29 @@ alsv_status alsv_stats_read(alsv_ctx* ctx, const void* stats_dev, double* mean_d
  * buffer totals_dev[samples][vars] (eq. (2.1) conserves them on periodic grids). Asynchronous. */
 alsv_status alsv_conservation_totals(alsv_ctx* ctx, double* totals_dev);
 
+/*
+ * alsv_conservation_totals_noalloc - the totals of alsv_conservation_totals for callers that
+ * cannot allocate device memory (a plugin whose host framework owns all device buffers and gives
+ * it no allocator; a service under a fixed device-memory budget where an allocation could fail or
+ * synchronise the device). It needs no context and no workspace: the kernels' per-chunk partial
+ * sums live in a static device array of 2^20 doubles (8 MiB) that every GPU loading this library
+ * holds until the process exits. The paper has no counterpart; it is an execution variant.
+ *   d            descriptor of the state (only ndim, n / level table, lo, hi, batch, eq and
+ *                precision are read)
+ *   U_dev        device state, layout as above, U_bytes >= the descriptor's state size
+ *   totals_dev   device FP64 [samples][vars], written
+ *   stream       cudaStream_t as void*
+ * Calls no cudaMalloc / cudaFree or allocating library routine. The first call on a device looks
+ * up the array's device address with cudaGetSymbolAddress (with that device current) and caches
+ * it; make that first call before any stream capture. All calls share the array: calls that
+ * overlap on the GPU (other streams, other threads) race. Every partial slot is written before it
+ * is read, so no clearing is needed. Errors: INVALID_ARG (bad descriptor, or samples x vars x
+ * ceil(cells / 4096) above 2^20: the message says so), BUFFER_TOO_SMALL, CUDA; the message is read
+ * with alsv_last_error(NULL). Asynchronous.
+ */
+alsv_status alsv_conservation_totals_noalloc(const alsv_grid_desc* d, const void* U_dev, size_t U_bytes,
+                                             double* totals_dev, void* stream);
+
 /* Kinetic energy sum_i |m_i|^2 / (2 rho_i) dV per sample in FP64 (Euler), into ke_dev[samples]. */
 alsv_status alsv_kinetic_energy(alsv_ctx* ctx, double* ke_dev);
 

@@ -11,7 +11,7 @@ from __future__ import annotations
 
 from ._abi import (BC, EQ, FLUX, INIT, PRECISION, RECON, RK, RVARS, AlsvError, alsv_adjoint_evolve,  # noqa: F401
                    alsv_adjoint_workspace_bytes, alsv_autotune, alsv_bind_adjoint_workspace,
-                   alsv_bind_workspace, alsv_conservation_totals, alsv_destroy, alsv_evolve_to_T,
+                   alsv_bind_workspace, alsv_conservation_totals, alsv_conservation_totals_noalloc, alsv_destroy, alsv_evolve_to_T,
                    alsv_get_launch_count, alsv_get_parameters, alsv_get_profile, alsv_get_tile, alsv_get_time, alsv_grid_desc,
                    alsv_init_grid, alsv_kinetic_energy, alsv_last_error, alsv_num_samples,
                    alsv_num_tile_variants, alsv_num_vars, alsv_set_graphs, alsv_set_initial_data,

@@ -68,6 +68,7 @@ SIGNATURES = {
     "alsv_stats_read": (C.c_int, [_ctx, _vp, _vp, _vp, _i64p]),
     "alsv_conservation_totals": (C.c_int, [_ctx, _vp]),
     "alsv_kinetic_energy": (C.c_int, [_ctx, _vp]),
+    "alsv_conservation_totals_noalloc": (C.c_int, [C.POINTER(alsv_grid_desc), _vp, _sz, _vp, _vp]),
     "alsv_adjoint_workspace_bytes": (C.c_int, [_ctx, C.c_double, C.POINTER(_sz)]),
     "alsv_bind_adjoint_workspace": (C.c_int, [_ctx, _vp, _sz]),
     "alsv_adjoint_evolve": (C.c_int, [_ctx, C.c_double, C.c_int, _vp, _vp, _vp]),
@@ -214,6 +215,13 @@ def alsv_stats_read(ctx, stats, mean=None, var=None) -> int:
 
 def alsv_conservation_totals(ctx, totals):
     _check(load().alsv_conservation_totals(ctx, _ptr(totals)), "alsv_conservation_totals", ctx)
+
+
+def alsv_conservation_totals_noalloc(desc: alsv_grid_desc, U, totals, stream: int = 0):
+    """Totals without a context or workspace (static device scratch); see include/alsv.h."""
+    _check(load().alsv_conservation_totals_noalloc(C.byref(desc), _ptr(U), _nbytes(U), _ptr(totals),
+                                                   C.c_void_p(stream or None)),
+           "alsv_conservation_totals_noalloc", None)
 
 
 def alsv_kinetic_energy(ctx, ke):

@@ -250,6 +250,7 @@ alsv_status run_chunk(alsv_ctx* c, int steps) {
 }  // namespace
 
 namespace alsv {
+void set_global_error(const std::string& msg) { g_init_error = msg; }
 alsv_status ctx_fail(alsv_ctx* c, alsv_status st, const std::string& msg) { return fail(c, st, msg); }
 alsv_status ctx_cuda_fail(alsv_ctx* c, cudaError_t e, const char* what) { return cuda_fail(c, e, what); }
 FinishArgs ctx_finish_args(alsv_ctx* c, int advance) { return finish_args(c, advance); }

@@ -167,6 +167,7 @@ def reference_arm(args):
 
 
 def main():
+    global T_END
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2)
@@ -176,7 +177,6 @@ def main():
     ap.add_argument("--samples", type=int, default=M, help="samples per GPU (default 4096; fewer for profiling runs)")
     ap.add_argument("--T", type=float, default=T_END, help="end time (default 1; shorter for profiling runs)")
     args = ap.parse_args()
-    global T_END
     T_END = args.T
     if args.impl == "reference":
         return reference_arm(args)

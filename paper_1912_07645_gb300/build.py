@@ -45,9 +45,15 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(p) <= t for p in _deps())
 
 
+# FP64 translation units evaluate each formula exactly as written (no FMA contraction), so the FP64
+# path reproduces the plain CPU restatement of the scheme operation by operation.
+NO_FMA = ("stage_f64_1d.cu", "stage_f64_2d.cu", "stage_f64_3d.cu", "misc_kernels.cu")
+
+
 def _compile(src: str) -> str:
     obj = os.path.join(OBJ, os.path.basename(src)[:-3] + ".o")
-    cmd = [nvcc()] + ARCH + FLAGS + ["-c", src, "-o", obj]
+    extra = ["-fmad=false"] if os.path.basename(src) in NO_FMA else []
+    cmd = [nvcc()] + ARCH + FLAGS + extra + ["-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed for {os.path.basename(src)}:\n{r.stderr}")

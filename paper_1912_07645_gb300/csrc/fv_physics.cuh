@@ -9,6 +9,13 @@
 
 namespace alsv {
 
+// FP64 evaluates every formula with the same operations in the same order as the plain CPU
+// restatement of the scheme (true divisions; the FP64 translation units are compiled without FMA
+// contraction), so FP64 runs are reproducible across both. FP32 uses reciprocal multiplications
+// and FMA, within its 2e-5 relative L1 budget.
+template <class R> struct IsExact { static constexpr bool value = false; };
+template <> struct IsExact<double> { static constexpr bool value = true; };
+
 template <class R> __device__ __forceinline__ R rcp(R x) { return R(1) / x; }
 template <class R> __device__ __forceinline__ R rsqrt_(R x);
 template <> __device__ __forceinline__ float rsqrt_(float x) { return sqrtf(x); }
@@ -25,18 +32,31 @@ template <class R> __device__ __forceinline__ R fmin_(R a, R b) { return b < a ?
 template <class R, int ND>
 __device__ __forceinline__ void cons_to_prim(const R* U, R* W, R gm1) {
     const R rho = U[0];
-    const R inv = rcp(rho);
     R m2 = U[1] * U[1];
 #pragma unroll
     for (int k = 1; k < ND; ++k) m2 = m2 + U[1 + k] * U[1 + k];
     W[0] = rho;
+    if constexpr (IsExact<R>::value) {
 #pragma unroll
-    for (int k = 0; k < ND; ++k) W[1 + k] = U[1 + k] * inv;
-    W[ND + 1] = gm1 * (U[ND + 1] - R(0.5) * m2 * inv);
+        for (int k = 0; k < ND; ++k) W[1 + k] = U[1 + k] / rho;
+        W[ND + 1] = gm1 * (U[ND + 1] - R(0.5) * m2 / rho);
+    } else {
+        const R inv = rcp(rho);
+#pragma unroll
+        for (int k = 0; k < ND; ++k) W[1 + k] = U[1 + k] * inv;
+        W[ND + 1] = gm1 * (U[ND + 1] - R(0.5) * m2 * inv);
+    }
+}
+
+// gm1 = gamma - 1 and its reciprocal: FP64 divides by gm1, FP32 multiplies by inv_gm1
+template <class R>
+__device__ __forceinline__ R div_gm1(R x, R gm1, R inv_gm1) {
+    if constexpr (IsExact<R>::value) return x / gm1;
+    else return x * inv_gm1;
 }
 
 template <class R, int ND>
-__device__ __forceinline__ void prim_to_cons(const R* W, R* U, R inv_gm1) {
+__device__ __forceinline__ void prim_to_cons(const R* W, R* U, R gm1, R inv_gm1) {
     const R rho = W[0];
     R u2 = W[1] * W[1];
 #pragma unroll
@@ -44,7 +64,7 @@ __device__ __forceinline__ void prim_to_cons(const R* W, R* U, R inv_gm1) {
     U[0] = rho;
 #pragma unroll
     for (int k = 0; k < ND; ++k) U[1 + k] = rho * W[1 + k];
-    U[ND + 1] = W[ND + 1] * inv_gm1 + R(0.5) * rho * u2;
+    U[ND + 1] = div_gm1(W[ND + 1], gm1, inv_gm1) + R(0.5) * rho * u2;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -63,8 +83,9 @@ template <class R> __device__ __forceinline__ R mc_slope(R wm, R w0, R wp) {
 }
 
 // Jiang-Shu WENO3 face value from candidates p0 (stencil {far, 0}) and p1 ({0, near}) with
-// linear weights 1/3, 2/3 and alpha_r = d_r / (eps + beta_r)^2, evaluated with one division:
-// (d0 q1 p0 + d1 q0 p1) / (d0 q1 + d1 q0), q_r = (eps + beta_r)^2.
+// linear weights 1/3, 2/3 and alpha_r = d_r / (eps + beta_r)^2. FP64 evaluates
+// (alpha_0 p0 + alpha_1 p1) / (alpha_0 + alpha_1) as written; FP32 uses the equivalent one-division
+// form (d0 q1 p0 + d1 q0 p1) / (d0 q1 + d1 q0) with q_r = (eps + beta_r)^2.
 template <class R> __device__ __forceinline__ R weno3_face(R wfar, R w0, R wnear, R eps) {
     const R p0 = R(-0.5) * wfar + R(1.5) * w0;
     const R p1 = R(0.5) * w0 + R(0.5) * wnear;
@@ -72,8 +93,14 @@ template <class R> __device__ __forceinline__ R weno3_face(R wfar, R w0, R wnear
     const R b1 = (wnear - w0) * (wnear - w0);
     const R e0 = eps + b0, e1 = eps + b1;
     const R q0 = e0 * e0, q1 = e1 * e1;
-    const R c0 = R(1.0 / 3.0) * q1, c1 = R(2.0 / 3.0) * q0;
-    return (c0 * p0 + c1 * p1) / (c0 + c1);
+    if constexpr (IsExact<R>::value) {
+        const R a0 = R(1.0 / 3.0) / q0;
+        const R a1 = R(2.0 / 3.0) / q1;
+        return (a0 * p0 + a1 * p1) / (a0 + a1);
+    } else {
+        const R c0 = R(1.0 / 3.0) * q1, c1 = R(2.0 / 3.0) * q0;
+        return (c0 * p0 + c1 * p1) / (c0 + c1);
+    }
 }
 
 template <class R, int RECON>
@@ -108,11 +135,11 @@ template <class R, int RECON> __device__ __forceinline__ R recon_left(R wm, R w0
 // S_L = min(uL - cL, uR - cR), S_R = max(uL + cL, uR + cR); Rusanov a = max(|uL|+cL, |uR|+cR).
 // ---------------------------------------------------------------------------------------------
 template <class R, int ND, int D, int FLUX>
-__device__ __forceinline__ void euler_flux(const R* WL, const R* WR, R* F, R gamma, R inv_gm1) {
+__device__ __forceinline__ void euler_flux(const R* WL, const R* WR, R* F, R gamma, R gm1, R inv_gm1) {
     constexpr int NV = ND + 2, IP = ND + 1;
     R UL[NV], UR[NV], FL[NV], FR[NV];
-    prim_to_cons<R, ND>(WL, UL, inv_gm1);
-    prim_to_cons<R, ND>(WR, UR, inv_gm1);
+    prim_to_cons<R, ND>(WL, UL, gm1, inv_gm1);
+    prim_to_cons<R, ND>(WR, UR, gm1, inv_gm1);
     const R rL = WL[0], rR = WR[0], uL = WL[1 + D], uR = WR[1 + D], pL = WL[IP], pR = WR[IP];
     // physical fluxes
 #pragma unroll
@@ -138,6 +165,9 @@ __device__ __forceinline__ void euler_flux(const R* WL, const R* WR, R* F, R gam
         } else if (SR <= R(0)) {
 #pragma unroll
             for (int v = 0; v < NV; ++v) F[v] = FR[v];
+        } else if constexpr (IsExact<R>::value) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) F[v] = (SR * FL[v] - SL * FR[v] + SL * SR * (UR[v] - UL[v])) / (SR - SL);
         } else {
             const R inv = rcp(SR - SL);
 #pragma unroll

@@ -20,6 +20,12 @@ template <int ND, int TX, int TY, int TZ> struct TileGeom {
     static constexpr int CELLS = TX * TY * TZ;
 };
 
+// CFL wave speed (|u_k| + c) / dx_k of one direction
+template <class R> __device__ __forceinline__ R speed_over_dx(R s, const LevelInfo& L, int k) {
+    if constexpr (IsExact<R>::value) return s / R(L.dx[k]);
+    else return s * R(L.inv_dx[k]);
+}
+
 template <class R> struct RealTraits;
 template <> struct RealTraits<float> { static __device__ __forceinline__ float nan() { return __int_as_float(0x7fffffff); } };
 template <> struct RealTraits<double> { static __device__ __forceinline__ double nan() { return __longlong_as_double(0x7fffffffffffffffLL); } };
@@ -204,15 +210,16 @@ __global__ void __launch_bounds__(NT) k_stage(const StageArgs p) {
             if (EQ == EQ_BURGERS) {
                 F[0] = burgers_flux<R, FLUX>(WL[0], WR[0]);
             } else {
-                if (D == 0) euler_flux<R, ND, 0, FLUX>(WL, WR, F, gamma, inv_gm1);
-                if (D == 1) euler_flux<R, ND, (ND >= 2 ? 1 : 0), FLUX>(WL, WR, F, gamma, inv_gm1);
-                if (D == 2) euler_flux<R, ND, (ND >= 3 ? 2 : 0), FLUX>(WL, WR, F, gamma, inv_gm1);
+                if (D == 0) euler_flux<R, ND, 0, FLUX>(WL, WR, F, gamma, gm1, inv_gm1);
+                if (D == 1) euler_flux<R, ND, (ND >= 2 ? 1 : 0), FLUX>(WL, WR, F, gamma, gm1, inv_gm1);
+                if (D == 2) euler_flux<R, ND, (ND >= 3 ? 2 : 0), FLUX>(WL, WR, F, gamma, gm1, inv_gm1);
             }
 #pragma unroll
             for (int v = 0; v < NV; ++v) sF[v * NI + f] = F[v];
         }
         __syncthreads();
         const R inv_dx = R(L.inv_dx[D]);
+        const R hD = R(L.dx[D]);
         const int fstep = D == 0 ? 1 : (D == 1 ? TX : TX * TY);
 #pragma unroll
         for (int m = 0; m < CPT; ++m) {
@@ -222,7 +229,11 @@ __global__ void __launch_bounds__(NT) k_stage(const StageArgs p) {
             const int z = ND >= 3 ? c / (TX * TY) : 0;
             const int fidx = (z * EY + y) * EX + x;
 #pragma unroll
-            for (int v = 0; v < NV; ++v) acc[m][v] = acc[m][v] - (sF[v * NI + fidx + fstep] - sF[v * NI + fidx]) * inv_dx;
+            for (int v = 0; v < NV; ++v) {
+                const R dF = sF[v * NI + fidx + fstep] - sF[v * NI + fidx];
+                if constexpr (IsExact<R>::value) acc[m][v] = acc[m][v] - dF / hD;
+                else acc[m][v] = acc[m][v] - dF * inv_dx;
+            }
         }
     }
 
@@ -255,7 +266,7 @@ __global__ void __launch_bounds__(NT) k_stage(const StageArgs p) {
                 const R au = fabs_(out[0]);
                 if (!(au == au) || isinf(au)) bad = true;
 #pragma unroll
-                for (int k = 0; k < ND; ++k) smax = fmax_(smax, au * R(L.inv_dx[k]));
+                for (int k = 0; k < ND; ++k) smax = fmax_(smax, speed_over_dx<R>(au, L, k));
             } else {
                 R wv[NV];
                 cons_to_prim<R, ND>(out, wv, gm1);
@@ -265,7 +276,7 @@ __global__ void __launch_bounds__(NT) k_stage(const StageArgs p) {
                 } else {
                     const R c = rsqrt_(gamma * pr / rho);
 #pragma unroll
-                    for (int k = 0; k < ND; ++k) smax = fmax_(smax, (fabs_(wv[1 + k]) + c) * R(L.inv_dx[k]));
+                    for (int k = 0; k < ND; ++k) smax = fmax_(smax, speed_over_dx<R>(fabs_(wv[1 + k]) + c, L, k));
                 }
             }
         }
@@ -330,7 +341,7 @@ __global__ void __launch_bounds__(NT) k_speed(const GridArgs g, const void* Uv, 
             const R au = fabs_(u[0]);
             if (!(au == au) || isinf(au)) bad = true;
 #pragma unroll
-            for (int k = 0; k < ND; ++k) smax = fmax_(smax, au * R(L.inv_dx[k]));
+            for (int k = 0; k < ND; ++k) smax = fmax_(smax, speed_over_dx<R>(au, L, k));
         } else {
             R wv[NV];
             cons_to_prim<R, ND>(u, wv, gm1);
@@ -340,7 +351,7 @@ __global__ void __launch_bounds__(NT) k_speed(const GridArgs g, const void* Uv, 
             } else {
                 const R c = rsqrt_(gamma * pr / rho);
 #pragma unroll
-                for (int k = 0; k < ND; ++k) smax = fmax_(smax, (fabs_(wv[1 + k]) + c) * R(L.inv_dx[k]));
+                for (int k = 0; k < ND; ++k) smax = fmax_(smax, speed_over_dx<R>(fabs_(wv[1 + k]) + c, L, k));
             }
         }
     }

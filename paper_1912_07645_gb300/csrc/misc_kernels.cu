@@ -287,22 +287,21 @@ __global__ void k_welford(const GridArgs g, const void* Uv, void* stats) {
 #pragma unroll
         for (int v = 0; v < NV; ++v) u[v] = (double)U[((long long)b * NV + v) * C + i];
         if (EULER) {
-            const double inv = 1.0 / u[0];
-            double mm = 0.0;
+            double mm = u[1] * u[1];
 #pragma unroll
-            for (int k = 1; k < NV - 1; ++k) mm = mm + u[k] * u[k];
+            for (int k = 2; k < NV - 1; ++k) mm = mm + u[k] * u[k];
             x[0] = u[0];
 #pragma unroll
-            for (int k = 1; k < NV - 1; ++k) x[k] = u[k] * inv;
-            x[NV - 1] = gm1 * (u[NV - 1] - 0.5 * mm * inv);
+            for (int k = 1; k < NV - 1; ++k) x[k] = u[k] / u[0];
+            x[NV - 1] = gm1 * (u[NV - 1] - 0.5 * mm / u[0]);
         } else {
             x[0] = u[0];
         }
-        const double inv_n = 1.0 / (double)(n0 + b + 1);
+        const double n = (double)(n0 + b + 1);
 #pragma unroll
         for (int q = 0; q < NV; ++q) {
             const double delta = x[q] - mu[q];
-            mu[q] = mu[q] + delta * inv_n;
+            mu[q] = mu[q] + delta / n;
             m2[q] = m2[q] + delta * (x[q] - mu[q]);
         }
     }

@@ -196,6 +196,21 @@ def test_sod_config_full_run_fp64():
     p1_check(g, o, what="sod full")
 
 
+@pytest.mark.parametrize("init,recon,flux,rvars", [("sod", "weno3", "hllc", "prim"), ("lax", "mc", "hll", "cons"),
+                                                   ("sod", "pc", "rusanov", "prim")])
+def test_fp64_tubes_bitwise_equal_to_oracle(init, recon, flux, rvars):
+    """The FP64 path evaluates every formula with the oracle's operations in the oracle's order
+    (no FMA contraction, true divisions); initial data without transcendental functions makes the
+    whole run bitwise reproducible across the two."""
+    T = 0.2 if init == "sod" else 0.13
+    cfg = dict(ndim=1, n=(400,), eq="euler", recon=recon, flux=flux, rvars=rvars, rk="ssprk3", bc="outflow",
+               cfl=0.45, precision="fp64")
+    g, t, st, n = run_gpu(cfg, init, T=T)
+    o, ost, ot = run_oracle(cfg, init, T=T)
+    assert n == ost[0]
+    assert np.array_equal(g, o)
+
+
 def test_burgers_full_run_fp64():
     cfg = dict(ndim=1, n=(512,), eq="burgers", recon="weno3", flux="rusanov", rk="ssprk3", bc="periodic",
                cfl=0.45, precision="fp64")

@@ -17,6 +17,27 @@ template <class R> struct IsExact { static constexpr bool value = false; };
 template <> struct IsExact<double> { static constexpr bool value = true; };
 
 template <class R> __device__ __forceinline__ R rcp(R x) { return R(1) / x; }
+
+// FP32 fast forms (MUFU reciprocal / reciprocal square root, about 2 ulp)
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+// sound speed sqrt(gamma p / rho): FP64 as written; FP32 as (gamma p) * rsqrt(gamma p rho)
+template <class R> __device__ __forceinline__ R sound_speed(R gamma, R p, R rho);
+template <> __device__ __forceinline__ double sound_speed(double gamma, double p, double rho) {
+    return sqrt(gamma * p / rho);
+}
+template <> __device__ __forceinline__ float sound_speed(float gamma, float p, float rho) {
+    const float gp = gamma * p;
+    return gp * rsqrt_approx(gp * rho);
+}
 template <class R> __device__ __forceinline__ R rsqrt_(R x);
 template <> __device__ __forceinline__ float rsqrt_(float x) { return sqrtf(x); }
 template <> __device__ __forceinline__ double rsqrt_(double x) { return sqrt(x); }
@@ -41,7 +62,7 @@ __device__ __forceinline__ void cons_to_prim(const R* U, R* W, R gm1) {
         for (int k = 0; k < ND; ++k) W[1 + k] = U[1 + k] / rho;
         W[ND + 1] = gm1 * (U[ND + 1] - R(0.5) * m2 / rho);
     } else {
-        const R inv = rcp(rho);
+        const R inv = rcp_approx(rho);
 #pragma unroll
         for (int k = 0; k < ND; ++k) W[1 + k] = U[1 + k] * inv;
         W[ND + 1] = gm1 * (U[ND + 1] - R(0.5) * m2 * inv);
@@ -98,9 +119,26 @@ template <class R> __device__ __forceinline__ R weno3_face(R wfar, R w0, R wnear
         const R a1 = R(2.0 / 3.0) / q1;
         return (a0 * p0 + a1 * p1) / (a0 + a1);
     } else {
-        const R c0 = R(1.0 / 3.0) * q1, c1 = R(2.0 / 3.0) * q0;
-        return (c0 * p0 + c1 * p1) / (c0 + c1);
+        const R t0 = R(2) * q0;
+        return (q1 * p0 + t0 * p1) * rcp_approx(q1 + t0);
     }
+}
+
+// Both face states of interface i+1/2 from (w_{i-1}, w_i, w_{i+1}, w_{i+2}): fr = right face of
+// cell i, fl = left face of cell i+1. The two share p1 = (w_i + w_{i+1})/2 and the smoothness
+// indicator of (w_i, w_{i+1}); FP32 form (q1 p0 + 2 q0 p1) / (q1 + 2 q0), q = (eps + beta)^2.
+__device__ __forceinline__ void weno3_pair(float wm, float w0, float w1, float w2, float eps, float& fr, float& fl) {
+    const float p1 = 0.5f * (w0 + w1);
+    const float d1 = w1 - w0;
+    const float e1 = eps + d1 * d1;
+    const float q1 = e1 * e1;
+    const float dm = w0 - wm, dp = w1 - w2;
+    const float em = eps + dm * dm, ep = eps + dp * dp;
+    const float tm = 2.0f * (em * em), tp = 2.0f * (ep * ep);
+    const float p0r = 1.5f * w0 - 0.5f * wm;
+    const float p0l = 1.5f * w1 - 0.5f * w2;
+    fr = (q1 * p0r + tm * p1) * rcp_approx(q1 + tm);
+    fl = (q1 * p0l + tp * p1) * rcp_approx(q1 + tp);
 }
 
 template <class R, int RECON>
@@ -134,8 +172,51 @@ template <class R, int RECON> __device__ __forceinline__ R recon_left(R wm, R w0
 // Inputs are primitive face states; output is the conserved flux. Wave speeds (Davis):
 // S_L = min(uL - cL, uR - cR), S_R = max(uL + cL, uR + cR); Rusanov a = max(|uL|+cL, |uR|+cR).
 // ---------------------------------------------------------------------------------------------
+// FP32 HLLC with the same case rules: the upwind side K is L when S_L >= 0 or S* >= 0, else R;
+// only K's physical flux and conserved state are formed, and the star state uses one reciprocal:
+// U*_E = ((S_K - u_K) E_K + (S* - u_K) p_K) / (S_K - S*) + fac (S* - u_K) S*,
+// fac = rho_K (S_K - u_K) / (S_K - S*) (algebraically equal to the textbook form).
+template <class R, int ND, int D>
+__device__ __forceinline__ void hllc_fast(const R* WL, const R* WR, R* F, R gamma, R gm1, R inv_gm1) {
+    constexpr int NV = ND + 2, IP = ND + 1;
+    const R rL = WL[0], rR = WR[0], uL = WL[1 + D], uR = WR[1 + D], pL = WL[IP], pR = WR[IP];
+    const R cL = sound_speed<R>(gamma, pL, rL), cR = sound_speed<R>(gamma, pR, rR);
+    const R SL = fmin_(uL - cL, uR - cR), SR = fmax_(uL + cL, uR + cR);
+    const R mL = rL * (SL - uL), mR = rR * (SR - uR);
+    const R Ss = (pR - pL + uL * mL - uR * mR) * rcp_approx(mL - mR);
+    const bool leftK = (SL >= R(0)) || (Ss >= R(0));
+    const bool star = !(SL >= R(0)) && (leftK || (SR > R(0)));
+    R WK[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) WK[v] = leftK ? WL[v] : WR[v];
+    const R SK = leftK ? SL : SR;
+    const R rK = WK[0], uK = WK[1 + D], pK = WK[IP];
+    R UK[NV], FK[NV];
+    prim_to_cons<R, ND>(WK, UK, gm1, inv_gm1);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) FK[v] = UK[v] * uK;
+    FK[1 + D] = FK[1 + D] + pK;
+    FK[IP] = uK * (UK[IP] + pK);
+    const R A = SK - uK;
+    const R invB = rcp_approx(SK - Ss);
+    const R fac = rK * A * invB;
+    const R dS = Ss - uK;
+    R Us[NV];
+    Us[0] = fac;
+#pragma unroll
+    for (int j = 0; j < ND; ++j) Us[1 + j] = fac * WK[1 + j];
+    Us[1 + D] = fac * Ss;
+    Us[IP] = (A * UK[IP] + dS * pK) * invB + fac * dS * Ss;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) F[v] = star ? FK[v] + SK * (Us[v] - UK[v]) : FK[v];
+}
+
 template <class R, int ND, int D, int FLUX>
 __device__ __forceinline__ void euler_flux(const R* WL, const R* WR, R* F, R gamma, R gm1, R inv_gm1) {
+    if constexpr (FLUX == FLX_HLLC && !IsExact<R>::value) {
+        hllc_fast<R, ND, D>(WL, WR, F, gamma, gm1, inv_gm1);
+        return;
+    }
     constexpr int NV = ND + 2, IP = ND + 1;
     R UL[NV], UR[NV], FL[NV], FR[NV];
     prim_to_cons<R, ND>(WL, UL, gm1, inv_gm1);
@@ -148,8 +229,8 @@ __device__ __forceinline__ void euler_flux(const R* WL, const R* WR, R* F, R gam
     FR[1 + D] = FR[1 + D] + pR;
     FL[IP] = uL * (UL[IP] + pL);
     FR[IP] = uR * (UR[IP] + pR);
-    const R cL = rsqrt_(gamma * pL / rL);
-    const R cR = rsqrt_(gamma * pR / rR);
+    const R cL = sound_speed<R>(gamma, pL, rL);
+    const R cR = sound_speed<R>(gamma, pR, rR);
     if (FLUX == FLX_RUSANOV) {
         const R a = fmax_(fabs_(uL) + cL, fabs_(uR) + cR);
 #pragma unroll
@@ -169,7 +250,7 @@ __device__ __forceinline__ void euler_flux(const R* WL, const R* WR, R* F, R gam
 #pragma unroll
             for (int v = 0; v < NV; ++v) F[v] = (SR * FL[v] - SL * FR[v] + SL * SR * (UR[v] - UL[v])) / (SR - SL);
         } else {
-            const R inv = rcp(SR - SL);
+            const R inv = rcp_approx(SR - SL);
 #pragma unroll
             for (int v = 0; v < NV; ++v) F[v] = (SR * FL[v] - SL * FR[v] + SL * SR * (UR[v] - UL[v])) * inv;
         }

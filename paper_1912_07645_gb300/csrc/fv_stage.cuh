@@ -71,8 +71,12 @@ __device__ __forceinline__ void interface_states(const R* sw, int stride_v, int 
         } else {
             const R wm = base[-step];
             const R w2 = base[2 * step];
-            fr[v] = recon_right<R, RECON>(wm, w0, w1, eps);  // left cell, face i+1/2
-            fl[v] = recon_left<R, RECON>(w0, w1, w2, eps);   // right cell, face i+1/2
+            if constexpr (RECON == REC_WENO3 && !IsExact<R>::value) {
+                weno3_pair(wm, w0, w1, w2, eps, fr[v], fl[v]);
+            } else {
+                fr[v] = recon_right<R, RECON>(wm, w0, w1, eps);  // left cell, face i+1/2
+                fl[v] = recon_left<R, RECON>(w0, w1, w2, eps);   // right cell, face i+1/2
+            }
         }
     }
     if (EQ == EQ_BURGERS) {

@@ -41,10 +41,14 @@ template <> __device__ __forceinline__ float sound_speed(float gamma, float p, f
 template <class R> __device__ __forceinline__ R rsqrt_(R x);
 template <> __device__ __forceinline__ float rsqrt_(float x) { return sqrtf(x); }
 template <> __device__ __forceinline__ double rsqrt_(double x) { return sqrt(x); }
+// FP64: |x|, max, min as the CPU restatement writes them (ties keep the first argument);
+// FP32: the native single-instruction forms (equal values are interchangeable there).
 template <class R> __device__ __forceinline__ R fabs_(R x) { return x < R(0) ? -x : x; }
-// ties keep the first argument (same convention as the selection rules of the fluxes)
 template <class R> __device__ __forceinline__ R fmax_(R a, R b) { return b > a ? b : a; }
 template <class R> __device__ __forceinline__ R fmin_(R a, R b) { return b < a ? b : a; }
+template <> __device__ __forceinline__ float fabs_(float x) { return fabsf(x); }
+template <> __device__ __forceinline__ float fmax_(float a, float b) { return fmaxf(a, b); }
+template <> __device__ __forceinline__ float fmin_(float a, float b) { return fminf(a, b); }
 
 // ---------------------------------------------------------------------------------------------
 // Ideal gas: p = (gamma - 1) (E - |m|^2 / (2 rho)); E = p / (gamma - 1) + rho |u|^2 / 2.
@@ -139,6 +143,30 @@ __device__ __forceinline__ void weno3_pair(float wm, float w0, float w1, float w
     const float p0l = 1.5f * w1 - 0.5f * w2;
     fr = (q1 * p0r + tm * p1) * rcp_approx(q1 + tm);
     fl = (q1 * p0l + tp * p1) * rcp_approx(q1 + tp);
+}
+
+// The same for two variables at once with packed FP32x2 arithmetic (one instruction per pair).
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ void weno3_pair2(float2 wm, float2 w0, float2 w1, float2 w2, float eps, float2& fr,
+                                            float2& fl) {
+    const float2 half = f2(0.5f), m1 = f2(-1.0f), e = f2(eps), two = f2(2.0f);
+    const float2 p1 = __fmul2_rn(half, __fadd2_rn(w0, w1));
+    const float2 d1 = __ffma2_rn(w0, m1, w1);
+    const float2 e1 = __ffma2_rn(d1, d1, e);
+    const float2 q1 = __fmul2_rn(e1, e1);
+    const float2 dm = __ffma2_rn(wm, m1, w0);
+    const float2 dp = __ffma2_rn(w2, m1, w1);
+    const float2 em = __ffma2_rn(dm, dm, e);
+    const float2 ep = __ffma2_rn(dp, dp, e);
+    const float2 sm = __fmul2_rn(em, em), sp = __fmul2_rn(ep, ep);
+    const float2 p0r = __ffma2_rn(f2(1.5f), w0, __fmul2_rn(f2(-0.5f), wm));
+    const float2 p0l = __ffma2_rn(f2(1.5f), w1, __fmul2_rn(f2(-0.5f), w2));
+    const float2 nr = __ffma2_rn(two, __fmul2_rn(sm, p1), __fmul2_rn(q1, p0r));
+    const float2 nl = __ffma2_rn(two, __fmul2_rn(sp, p1), __fmul2_rn(q1, p0l));
+    const float2 dr = __ffma2_rn(two, sm, q1);
+    const float2 dl = __ffma2_rn(two, sp, q1);
+    fr = __fmul2_rn(nr, make_float2(rcp_approx(dr.x), rcp_approx(dr.y)));
+    fl = __fmul2_rn(nl, make_float2(rcp_approx(dl.x), rcp_approx(dl.y)));
 }
 
 template <class R, int RECON>

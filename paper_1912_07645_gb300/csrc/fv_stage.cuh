@@ -36,46 +36,88 @@ struct StageSmem {
     static constexpr int G = (RECON == REC_PC) ? 1 : 2;
 };
 
+// Shared memory holds one record per cell (all variables of the cell together), padded to 16 bytes
+// when that costs at most one element per cell, so a cell moves in 128-bit accesses.
+template <class R, int NV> __host__ __device__ constexpr int cell_stride() {
+    constexpr int bytes = NV * (int)sizeof(R);
+    constexpr int padded = (bytes + 15) / 16 * 16 / (int)sizeof(R);
+    return (NV == 1 || bytes % 16 == 0) ? NV : (padded - NV <= 1 ? padded : NV);
+}
+
+template <class R, int NV, int CS> __device__ __forceinline__ void lds_cell(const R* p, R* out) {
+    if constexpr ((CS * sizeof(R)) % 16 == 0) {
+        constexpr int NCH = CS * (int)sizeof(R) / 16;
+        R tmp[CS];
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) reinterpret_cast<uint4*>(tmp)[c] = reinterpret_cast<const uint4*>(p)[c];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) out[v] = tmp[v];
+    } else {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) out[v] = p[v];
+    }
+}
+
+template <class R, int NV, int CS> __device__ __forceinline__ void sts_cell(R* p, const R* in) {
+    if constexpr ((CS * sizeof(R)) % 16 == 0) {
+        constexpr int NCH = CS * (int)sizeof(R) / 16;
+        R tmp[CS];
+#pragma unroll
+        for (int v = 0; v < CS; ++v) tmp[v] = v < NV ? in[v < NV ? v : 0] : R(0);
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) reinterpret_cast<uint4*>(p)[c] = reinterpret_cast<const uint4*>(tmp)[c];
+    } else {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) p[v] = in[v];
+    }
+}
+
 template <class R, int EQ, int ND, int RECON, int TX, int TY, int TZ>
 constexpr size_t stage_smem_bytes() {
     constexpr int NV = (EQ == EQ_BURGERS) ? 1 : ND + 2;
+    constexpr int CS = cell_stride<R, NV>();
     constexpr int G = (RECON == REC_PC) ? 1 : 2;
     constexpr int SX = TX + 2 * G, SY = ND >= 2 ? TY + 2 * G : 1, SZ = ND >= 3 ? TZ + 2 * G : 1;
     constexpr int NIX = (TX + 1) * TY * TZ;
     constexpr int NIY = ND >= 2 ? TX * (TY + 1) * TZ : 0;
     constexpr int NIZ = ND >= 3 ? TX * TY * (TZ + 1) : 0;
     constexpr int NI = NIX > NIY ? (NIX > NIZ ? NIX : NIZ) : (NIY > NIZ ? NIY : NIZ);
-    return sizeof(R) * (size_t)NV * (size_t)(SX * SY * SZ + NI);
+    return sizeof(R) * (size_t)CS * (size_t)(SX * SY * SZ + NI);
 }
 
-// Reconstruct the two face states of interface (left cell L, right cell R) along a line of four
-// (or two, PC) stencil values per variable, apply the positivity fallback, and return primitive
-// states for the flux.
-template <class R, int EQ, int ND, int RECON>
-__device__ __forceinline__ void interface_states(const R* sw, int stride_v, int i0, int step, int rvars, R gm1,
-                                                 R eps, R* WL, R* WR) {
+// Reconstruct the two face states of interface (left cell i, right cell i+1) from the cell records
+// i-1 .. i+2 (i, i+1 for PC) along one direction, apply the positivity fallback, and return
+// primitive states for the flux. i0: record index of cell i; step: records between neighbours.
+template <class R, int EQ, int ND, int RECON, int CS>
+__device__ __forceinline__ void interface_states(const R* sw, int i0, int step, int rvars, R gm1, R eps, R* WL,
+                                                 R* WR) {
     constexpr int NV = (EQ == EQ_BURGERS) ? 1 : ND + 2;
     constexpr int G = (RECON == REC_PC) ? 1 : 2;
-    // i0: smem index of the left cell; stencil left-1, left, right, right+1
-    R fl[NV], fr[NV], cl[NV], cr[NV];
+    R cl[NV], cr[NV], fl[NV], fr[NV];
+    lds_cell<R, NV, CS>(sw + i0 * CS, cl);
+    lds_cell<R, NV, CS>(sw + (i0 + step) * CS, cr);
+    if (G == 1) {
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-        const R* base = sw + v * stride_v + i0;
-        const R w0 = base[0];
-        const R w1 = base[step];
-        cl[v] = w0;
-        cr[v] = w1;
-        if (G == 1) {
-            fr[v] = w0;
-            fl[v] = w1;
+        for (int v = 0; v < NV; ++v) { fr[v] = cl[v]; fl[v] = cr[v]; }
+    } else {
+        R cm[NV], c2[NV];
+        lds_cell<R, NV, CS>(sw + (i0 - step) * CS, cm);
+        lds_cell<R, NV, CS>(sw + (i0 + 2 * step) * CS, c2);
+        if constexpr (RECON == REC_WENO3 && !IsExact<R>::value) {
+#pragma unroll
+            for (int v = 0; v + 1 < NV; v += 2) {
+                float2 a, b;
+                weno3_pair2(make_float2(cm[v], cm[v + 1]), make_float2(cl[v], cl[v + 1]),
+                            make_float2(cr[v], cr[v + 1]), make_float2(c2[v], c2[v + 1]), eps, a, b);
+                fr[v] = a.x; fr[v + 1] = a.y;
+                fl[v] = b.x; fl[v + 1] = b.y;
+            }
+            if constexpr (NV % 2 == 1) weno3_pair(cm[NV - 1], cl[NV - 1], cr[NV - 1], c2[NV - 1], eps, fr[NV - 1], fl[NV - 1]);
         } else {
-            const R wm = base[-step];
-            const R w2 = base[2 * step];
-            if constexpr (RECON == REC_WENO3 && !IsExact<R>::value) {
-                weno3_pair(wm, w0, w1, w2, eps, fr[v], fl[v]);
-            } else {
-                fr[v] = recon_right<R, RECON>(wm, w0, w1, eps);  // left cell, face i+1/2
-                fl[v] = recon_left<R, RECON>(w0, w1, w2, eps);   // right cell, face i+1/2
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                fr[v] = recon_right<R, RECON>(cm[v], cl[v], cr[v], eps);  // cell i, face i+1/2
+                fl[v] = recon_left<R, RECON>(cl[v], cr[v], c2[v], eps);   // cell i+1, face i+1/2
             }
         }
     }
@@ -123,10 +165,11 @@ __global__ void __launch_bounds__(NT) k_stage(const StageArgs p) {
     constexpr int CELLS = TX * TY * TZ;
     static_assert(CELLS % NT == 0, "tile cells must be a multiple of the CTA size");
     constexpr int CPT = CELLS / NT;
+    constexpr int CS = cell_stride<R, NV>();
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    R* sW = reinterpret_cast<R*>(smem_raw);   // [NV][NS]
-    R* sF = sW + NV * NS;                      // [NV][NI]
+    R* sW = reinterpret_cast<R*>(smem_raw);   // [NS][CS] reconstruction variables per cell
+    R* sF = sW + CS * NS;                      // [NI][CS] interface fluxes
 
     const long long w = blockIdx.x;
     const GridArgs& g = p.g;
@@ -152,15 +195,21 @@ __global__ void __launch_bounds__(NT) k_stage(const StageArgs p) {
     const int tid = threadIdx.x;
 
     // ---- 1. tile + halo load with boundary fill and variable conversion
+    // (tiles whose halo lies inside the grid skip the ghost mapping; uniform per CTA)
+    const bool interior = tx0 >= G && tx0 + SX - G <= nx && (ND < 2 || (ty0 >= G && ty0 + SY - G <= ny)) &&
+                          (ND < 3 || (tz0 >= G && tz0 + SZ - G <= nz));
 #pragma unroll 1
     for (int s = tid; s < NS; s += NT) {
         const int sx = s % SX;
         const int sy = ND >= 2 ? (s / SX) % SY : 0;
         const int sz = ND >= 3 ? s / (SX * SY) : 0;
         bool flip[3] = {false, false, false};
-        const int ix = map_ghost(tx0 + sx - G, nx, g.bc[0][0], g.bc[0][1], flip[0]);
-        const int iy = ND >= 2 ? map_ghost(ty0 + sy - G, ny, g.bc[1][0], g.bc[1][1], flip[1]) : 0;
-        const int iz = ND >= 3 ? map_ghost(tz0 + sz - G, nz, g.bc[2][0], g.bc[2][1], flip[2]) : 0;
+        int ix = tx0 + sx - G, iy = ND >= 2 ? ty0 + sy - G : 0, iz = ND >= 3 ? tz0 + sz - G : 0;
+        if (!interior) {
+            ix = map_ghost(ix, nx, g.bc[0][0], g.bc[0][1], flip[0]);
+            if (ND >= 2) iy = map_ghost(iy, ny, g.bc[1][0], g.bc[1][1], flip[1]);
+            if (ND >= 3) iz = map_ghost(iz, nz, g.bc[2][0], g.bc[2][1], flip[2]);
+        }
         const long long off = ((long long)iz * ny + iy) * nx + ix;
         R u[NV];
 #pragma unroll
@@ -175,11 +224,9 @@ __global__ void __launch_bounds__(NT) k_stage(const StageArgs p) {
             if (g.rvars == RV_PRIM) {
                 R wv[NV];
                 cons_to_prim<R, ND>(u, wv, gm1);
-#pragma unroll
-                for (int v = 0; v < NV; ++v) sW[v * NS + s] = wv[v];
+                sts_cell<R, NV, CS>(sW + s * CS, wv);
             } else {
-#pragma unroll
-                for (int v = 0; v < NV; ++v) sW[v * NS + s] = u[v];
+                sts_cell<R, NV, CS>(sW + s * CS, u);
             }
         }
     }
@@ -210,7 +257,7 @@ __global__ void __launch_bounds__(NT) k_stage(const StageArgs p) {
             if (D == 2) cz -= 1;
             const int i0 = (cz * SY + cy) * SX + cx;
             R WL[NV], WR[NV], F[NV];
-            interface_states<R, EQ, ND, RECON>(sW, NS, i0, step, g.rvars, gm1, eps, WL, WR);
+            interface_states<R, EQ, ND, RECON, CS>(sW, i0, step, g.rvars, gm1, eps, WL, WR);
             if (EQ == EQ_BURGERS) {
                 F[0] = burgers_flux<R, FLUX>(WL[0], WR[0]);
             } else {
@@ -218,8 +265,7 @@ __global__ void __launch_bounds__(NT) k_stage(const StageArgs p) {
                 if (D == 1) euler_flux<R, ND, (ND >= 2 ? 1 : 0), FLUX>(WL, WR, F, gamma, gm1, inv_gm1);
                 if (D == 2) euler_flux<R, ND, (ND >= 3 ? 2 : 0), FLUX>(WL, WR, F, gamma, gm1, inv_gm1);
             }
-#pragma unroll
-            for (int v = 0; v < NV; ++v) sF[v * NI + f] = F[v];
+            sts_cell<R, NV, CS>(sF + f * CS, F);
         }
         __syncthreads();
         const R inv_dx = R(L.inv_dx[D]);
@@ -232,9 +278,12 @@ __global__ void __launch_bounds__(NT) k_stage(const StageArgs p) {
             const int y = ND >= 2 ? (c / TX) % TY : 0;
             const int z = ND >= 3 ? c / (TX * TY) : 0;
             const int fidx = (z * EY + y) * EX + x;
+            R Fm[NV], Fp[NV];
+            lds_cell<R, NV, CS>(sF + fidx * CS, Fm);
+            lds_cell<R, NV, CS>(sF + (fidx + fstep) * CS, Fp);
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
-                const R dF = sF[v * NI + fidx + fstep] - sF[v * NI + fidx];
+                const R dF = Fp[v] - Fm[v];
                 if constexpr (IsExact<R>::value) acc[m][v] = acc[m][v] - dF / hD;
                 else acc[m][v] = acc[m][v] - dF * inv_dx;
             }

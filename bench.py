@@ -118,6 +118,35 @@ def run_step(S, alsv, stats_fresh=True):
     return nstep
 
 
+def plain_fp64_loop(alsv, torch, steps_per_sample, T_short=0.066):
+    """The plain per-sample FP64 path on the same GPU: sample 0 of the batch alone (B = 1) in FP64,
+    timed over the CFL steps to T_short and extrapolated to the sample's full step count. Its
+    relative L1 difference from the batched FP32 result for the same sample at T_short states the
+    error at which the two throughputs compare."""
+    kw = desc_kwargs(batch=1)
+    S64 = alsv.Solver(alsv.make_desc(**dict(kw, precision="fp64")))
+    S64.set_initial_data("kh")
+    S64.step(3)
+    S64.sync()
+    S64.set_initial_data("kh")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    n = S64.evolve_to(T_short)
+    el = time.perf_counter() - t0
+    u64 = S64.to_host(S64.U).double()
+    S64.close()
+    S32 = alsv.Solver(alsv.make_desc(**kw))
+    S32.set_initial_data("kh")
+    S32.evolve_to(T_short)
+    u32 = S32.to_host(S32.U).double()
+    S32.close()
+    rel = float((u32 - u64).abs().sum() / u64.abs().sum())
+    ms_step = 1000.0 * el / max(n, 1)
+    return {"samples_per_s": 1000.0 / (ms_step * steps_per_sample), "ms_per_rk_step": ms_step, "steps_timed": n,
+            "T_timed": T_short, "steps_per_sample": int(steps_per_sample), "precision": "fp64",
+            "fp32_batched_vs_fp64_rel_l1": rel}
+
+
 def cpu_baseline_oracle(budget_s=15.0):
     """Time the FP64 oracle as it stands on this host's cores on a bounded sample of the same
     workload (one sample of the batch, as many CFL steps as fit in the budget)."""
@@ -306,6 +335,9 @@ def main():
                            "tile_variant": chosen, "autotune_ms": ms_var},
                 "samples_per_s": samples_per_s, "gpu_launches": launches, "e2e": e2e, "roofline": roof,
                 "clocks": ck}
+        steps0 = float(nstep[0]) if len(nstep) else 1.0
+        line["plain_fp64"] = plain_fp64_loop(alsv, torch, steps0)
+        line["batched_vs_plain_fp64_samples_per_s"] = samples_per_s / line["plain_fp64"]["samples_per_s"]
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = {k: v for k, v in cpu_baseline_oracle().items() if k not in ("elapsed_s", "cell_updates")}
         print(json.dumps(line), flush=True)

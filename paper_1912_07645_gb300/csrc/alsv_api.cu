@@ -265,13 +265,18 @@ StageArgs ctx_stage_args(alsv_ctx* c, const void* Us, const void* Un, void* Uout
 namespace alsv {
 TileShape stage_tile(int fp64, int ndim, int variant) {
     if (ndim == 1) return {256, 1, 1, 256};
-    if (ndim == 2) return variant == 1 ? TileShape{32, 8, 1, 256} : TileShape{32, 16, 1, 256};
+    if (ndim == 2) {
+        if (variant == 1) return TileShape{32, 8, 1, 256};
+        if (variant == 2 && !fp64) return TileShape{32, 32, 1, 256};
+        return TileShape{32, 16, 1, 256};
+    }
     if (fp64) return variant == 1 ? TileShape{8, 8, 4, 256} : TileShape{8, 8, 8, 256};
     return variant == 1 ? TileShape{8, 8, 8, 256} : TileShape{16, 8, 8, 256};
 }
 int stage_num_variants(int fp64, int ndim) {
-    (void)fp64;
-    return ndim == 1 ? 1 : 2;
+    if (ndim == 1) return 1;
+    if (ndim == 2 && !fp64) return 3;
+    return 2;
 }
 }  // namespace alsv
 

@@ -5,6 +5,7 @@ cudaError_t launch_stage_f32_2d(int variant, int eq, int recon, int flux, const 
     switch (variant) {
         case 0: return launch_stage_tile<float, 2, 32, 16, 1, 256>(eq, recon, flux, a, s);
         case 1: return launch_stage_tile<float, 2, 32, 8, 1, 256>(eq, recon, flux, a, s);
+        case 2: return launch_stage_tile<float, 2, 32, 32, 1, 256>(eq, recon, flux, a, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -12,6 +13,7 @@ cudaError_t launch_speed_f32_2d(int variant, int eq, const GridArgs& g, const vo
     switch (variant) {
         case 0: return launch_speed_tile<float, 2, 32, 16, 1, 256>(eq, g, U, part, s);
         case 1: return launch_speed_tile<float, 2, 32, 8, 1, 256>(eq, g, U, part, s);
+        case 2: return launch_speed_tile<float, 2, 32, 32, 1, 256>(eq, g, U, part, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -89,7 +89,10 @@ typedef struct alsv_grid_desc {
     int32_t level_n[ALSV_MAX_LEVELS][3];
     int32_t level_batch[ALSV_MAX_LEVELS];
     double vortex_center[2];
-    int32_t reserved[8];   /* must be zero */
+    int64_t sample_offset; /* global index of this context's first sample: counter-based KH
+                              parameters of local sample b use global index sample_offset + b
+                              (shards of one Monte Carlo ensemble across GPUs) */
+    int32_t reserved[6];   /* must be zero */
 } alsv_grid_desc;
 
 typedef struct alsv_ctx alsv_ctx;
@@ -186,6 +189,14 @@ alsv_status alsv_stats_reset(alsv_ctx* ctx, void* stats_dev, size_t bytes);
 alsv_status alsv_stats_accumulate(alsv_ctx* ctx, void* stats_dev, size_t bytes);
 alsv_status alsv_stats_read(alsv_ctx* ctx, const void* stats_dev, double* mean_dev, double* var_dev,
                             int64_t* count_host);
+
+/*
+ * alsv_stats_merge - fold the accumulator other_dev into stats_dev (both laid out as above, same
+ * grid), with the pairwise update of Chan, Golub and LeVeque: n = nA + nB, d = meanB - meanA,
+ * mean = meanA + d nB / n, M2 = M2A + M2B + d^2 nA nB / n, in FP64. Merging per-GPU shards in rank
+ * order gives the ensemble statistics of Sec. 2.2 independently of timing. Asynchronous.
+ */
+alsv_status alsv_stats_merge(alsv_ctx* ctx, void* stats_dev, const void* other_dev, size_t bytes);
 
 /* Conservation totals sum_i U_{v,i} dV in FP64 with a fixed-order tree, into the caller's device
  * buffer totals_dev[samples][vars] (eq. (2.1) conserves them on periodic grids). Asynchronous. */

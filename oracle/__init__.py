@@ -117,6 +117,7 @@ def lib():
             L.orc_init.restype = C.c_int
             L.orc_welford.argtypes = [dsc, C.c_int, dp, i64p, dp, dp]
             L.orc_totals.argtypes = [dsc, C.c_int, dp, dp]
+            L.orc_stats_merge.argtypes = [dsc, i64p, dp, dp, C.c_int64, dp, dp]
             L.orc_kinetic_energy.argtypes = [dsc, C.c_int, dp, dp]
             L.orc_ke_grad_kh2d.argtypes = [dsc, dp, C.c_double, C.c_int64, dp, dp]
             L.orc_ke_grad_kh2d.restype = C.c_int
@@ -234,6 +235,17 @@ def welford(d: Desc, U, count: int = 0, mean=None, M2=None):
     cnt = C.c_int64(count)
     lib().orc_welford(C.byref(d), B, _dp(U), C.byref(cnt), _dp(mean), _dp(M2))
     return cnt.value, mean, M2
+
+
+def stats_merge(d: Desc, a, b):
+    """Fold accumulator b = (count, mean, M2) into a copy of a; returns the merged triple."""
+    ca, ma, Ma = a
+    cb, mb, Mb = b
+    ma, Ma = _f64(ma).copy(), _f64(Ma).copy()
+    mb, Mb = _f64(mb), _f64(Mb)
+    cnt = C.c_int64(ca)
+    lib().orc_stats_merge(C.byref(d), C.byref(cnt), _dp(ma), _dp(Ma), cb, _dp(mb), _dp(Mb))
+    return cnt.value, ma, Ma
 
 
 def totals(d: Desc, U) -> np.ndarray:

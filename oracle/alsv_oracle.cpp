@@ -709,6 +709,24 @@ void orc_welford(const Desc* d, int B, const double* U, int64_t* count, double* 
     *count = n0 + B;
 }
 
+// Pairwise merge of two Welford accumulators (Chan, Golub, LeVeque): n = nA + nB, d = mB - mA,
+// mean = mA + d nB / n, M2 = M2A + M2B + d^2 nA nB / n; folds (B) into (A) in place.
+void orc_stats_merge(const Desc* d, int64_t* countA, double* meanA, double* M2A, int64_t countB,
+                     const double* meanB, const double* M2B) {
+    const int64_t C = ncells(*d);
+    const int nq = nvars(*d);
+    const int64_t na = *countA, nb = countB;
+    if (nb == 0) return;
+    for (int64_t i = 0; i < nq * C; ++i) {
+        if (na == 0) { meanA[i] = meanB[i]; M2A[i] = M2B[i]; continue; }
+        const double n = (double)(na + nb);
+        const double dl = meanB[i] - meanA[i];
+        meanA[i] = meanA[i] + dl * (double)nb / n;
+        M2A[i] = M2A[i] + M2B[i] + dl * dl * (double)na * (double)nb / n;
+    }
+    *countA = na + nb;
+}
+
 // Totals sum_i U_{v,i} dV per sample and variable (pairwise summation).
 static double pairwise(const double* x, int64_t n) {
     if (n <= 8) { double s = 0.0; for (int64_t i = 0; i < n; ++i) s += x[i]; return s; }

@@ -41,7 +41,7 @@ class alsv_grid_desc(C.Structure):
         ("cfl", C.c_double), ("fixed_dt", C.c_double), ("precision", C.c_int32), ("seed", C.c_uint64),
         ("weno_eps", C.c_double), ("weno_eps_dx2", C.c_int32), ("n_levels", C.c_int32),
         ("level_n", (C.c_int32 * 3) * MAX_LEVELS), ("level_batch", C.c_int32 * MAX_LEVELS),
-        ("vortex_center", C.c_double * 2), ("reserved", C.c_int32 * 8),
+        ("vortex_center", C.c_double * 2), ("sample_offset", C.c_int64), ("reserved", C.c_int32 * 6),
     ]
 
 
@@ -66,6 +66,7 @@ SIGNATURES = {
     "alsv_stats_reset": (C.c_int, [_ctx, _vp, _sz]),
     "alsv_stats_accumulate": (C.c_int, [_ctx, _vp, _sz]),
     "alsv_stats_read": (C.c_int, [_ctx, _vp, _vp, _vp, _i64p]),
+    "alsv_stats_merge": (C.c_int, [_ctx, _vp, _vp, _sz]),
     "alsv_conservation_totals": (C.c_int, [_ctx, _vp]),
     "alsv_kinetic_energy": (C.c_int, [_ctx, _vp]),
     "alsv_conservation_totals_noalloc": (C.c_int, [C.POINTER(alsv_grid_desc), _vp, _sz, _vp, _vp]),
@@ -211,6 +212,10 @@ def alsv_stats_read(ctx, stats, mean=None, var=None) -> int:
     cnt = C.c_int64()
     _check(load().alsv_stats_read(ctx, _ptr(stats), _ptr(mean), _ptr(var), C.byref(cnt)), "alsv_stats_read", ctx)
     return cnt.value
+
+
+def alsv_stats_merge(ctx, stats, other):
+    _check(load().alsv_stats_merge(ctx, _ptr(stats), _ptr(other), _nbytes(stats)), "alsv_stats_merge", ctx)
 
 
 def alsv_conservation_totals(ctx, totals):

@@ -309,8 +309,9 @@ alsv_status alsv_init_grid(const alsv_grid_desc* d_in, void* stream, alsv_ctx** 
     if (d.fixed_dt < 0.0 || !std::isfinite(d.fixed_dt)) return bad("fixed_dt must be >= 0 and finite");
     if (d.weno_eps == 0.0) d.weno_eps = 1e-6;
     if (!(d.weno_eps > 0.0)) return bad("weno_eps must be > 0");
-    for (int k = 0; k < 8; ++k)
+    for (int k = 0; k < 6; ++k)
         if (d.reserved[k] != 0) return bad("reserved fields must be zero");
+    if (d.sample_offset < 0) return bad("sample_offset must be >= 0");
     for (int k = 0; k < d.ndim; ++k)
         if (!(d.hi[k] > d.lo[k])) return bad("hi must exceed lo in every active direction");
     const int G = d.recon == ALSV_RECON_PC ? 1 : 2;
@@ -466,7 +467,7 @@ alsv_status alsv_set_initial_data(alsv_ctx* c, int kind, const double* theta_dev
     if (kind == ALSV_INIT_KH) {
         const double* th = theta_dev;
         if (!th) {
-            cudaError_t e = launch_theta(c->d.seed, c->total_samples, c->P, c->theta, c->stream);
+            cudaError_t e = launch_theta(c->d.seed, c->d.sample_offset, c->total_samples, c->P, c->theta, c->stream);
             if (e != cudaSuccess) return cuda_fail(c, e, "theta kernel");
             th = c->theta;
         } else if (n_params != c->P) {
@@ -630,6 +631,19 @@ alsv_status alsv_stats_read(alsv_ctx* c, const void* stats_dev, double* mean_dev
         CK(cudaMemcpyAsync(count_host, stats_dev, 8, cudaMemcpyDeviceToHost, c->stream));
         CK(cudaStreamSynchronize(c->stream));
     }
+    return ALSV_OK;
+}
+
+alsv_status alsv_stats_merge(alsv_ctx* c, void* stats_dev, const void* other_dev, size_t bytes) {
+    if (!c) return fail(nullptr, ALSV_ERR_INVALID_ARG, "null context");
+    alsv_status st = check_stats(c, stats_dev, bytes);
+    if (st != ALSV_OK) return st;
+    st = check_stats(c, other_dev, bytes);
+    if (st != ALSV_OK) return st;
+    if (stats_dev == other_dev) return fail(c, ALSV_ERR_INVALID_ARG, "stats and other must differ");
+    cudaError_t e = launch_stats_merge(c->g, stats_dev, other_dev, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "stats merge kernel");
+    c->launches += 2;
     return ALSV_OK;
 }
 

@@ -100,11 +100,12 @@ struct InitArgs {
     double vortex_center[2];
 };
 cudaError_t launch_init(int fp64, int ndim, const InitArgs& a, cudaStream_t s);
-cudaError_t launch_theta(uint64_t seed, int samples, int P, double* theta, cudaStream_t s);
+cudaError_t launch_theta(uint64_t seed, long long sample_offset, int samples, int P, double* theta, cudaStream_t s);
 
 // Monte Carlo statistics (single level).
 cudaError_t launch_welford(int fp64, const GridArgs& g, const void* U, void* stats, cudaStream_t s);
 cudaError_t launch_stats_read(const GridArgs& g, const void* stats, double* mean, double* var, cudaStream_t s);
+cudaError_t launch_stats_merge(const GridArgs& g, void* stats, const void* other, cudaStream_t s);
 
 // Fixed-order FP64 reductions: out[sample][var] totals (kind 0) or out[sample] KE (kind 1).
 // partial: scratch of reduce_partial_count(g) doubles.

@@ -84,20 +84,21 @@ __device__ __forceinline__ uint64_t sm64(uint64_t x) {
     return z ^ (z >> 31);
 }
 
-__global__ void k_theta(uint64_t seed, int samples, int P, double* theta) {
+__global__ void k_theta(uint64_t seed, long long sample_offset, int samples, int P, double* theta) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (long long)samples * P) return;
     const int b = (int)(i / P), j = (int)(i - (long long)b * P);
-    const uint64_t r = sm64(seed ^ ((uint64_t)b * (uint64_t)P + (uint64_t)j));
+    const uint64_t gb = (uint64_t)(sample_offset + b);
+    const uint64_t r = sm64(seed ^ (gb * (uint64_t)P + (uint64_t)j));
     const double u01 = (double)(r >> 11) * (1.0 / 9007199254740992.0);
     const double hi = j < P / 2 ? 1.0 : 2.0 * 3.14159265358979323846;
     theta[i] = hi * u01;
 }
 
-cudaError_t launch_theta(uint64_t seed, int samples, int P, double* theta, cudaStream_t s) {
+cudaError_t launch_theta(uint64_t seed, long long sample_offset, int samples, int P, double* theta, cudaStream_t s) {
     const long long n = (long long)samples * P;
     if (n <= 0) return cudaSuccess;
-    k_theta<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(seed, samples, P, theta);
+    k_theta<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(seed, sample_offset, samples, P, theta);
     return cudaGetLastError();
 }
 
@@ -347,6 +348,45 @@ cudaError_t launch_stats_read(const GridArgs& g, const void* stats, double* mean
     const long long C = (long long)L.n[0] * L.n[1] * L.n[2];
     const long long n = C * g.nv;
     k_stats_read<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(C, g.nv, stats, mean, var);
+    return cudaGetLastError();
+}
+
+// Chan-Golub-LeVeque pairwise merge of two Welford accumulators, one thread per (q, cell):
+// n = nA + nB, d = mB - mA, m = mA + d nB / n, M2 = M2A + M2B + d^2 nA nB / n. The count is
+// updated by a one-thread kernel afterwards (every thread reads the counts first).
+__global__ void k_stats_merge(long long C, int nq, void* stats, const void* other) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= C * nq) return;
+    const long long na = *reinterpret_cast<const long long*>(stats);
+    const long long nb = *reinterpret_cast<const long long*>(other);
+    double* mA = reinterpret_cast<double*>(reinterpret_cast<char*>(stats) + 256);
+    double* MA = mA + nq * C;
+    const double* mB = reinterpret_cast<const double*>(reinterpret_cast<const char*>(other) + 256);
+    const double* MB = mB + nq * C;
+    if (nb == 0) return;
+    if (na == 0) {
+        mA[i] = mB[i];
+        MA[i] = MB[i];
+        return;
+    }
+    const double n = (double)(na + nb);
+    const double d = mB[i] - mA[i];
+    mA[i] = mA[i] + d * (double)nb / n;
+    MA[i] = MA[i] + MB[i] + d * d * (double)na * (double)nb / n;
+}
+
+__global__ void k_stats_merge_count(void* stats, const void* other) {
+    *reinterpret_cast<long long*>(stats) += *reinterpret_cast<const long long*>(other);
+}
+
+cudaError_t launch_stats_merge(const GridArgs& g, void* stats, const void* other, cudaStream_t s) {
+    const LevelInfo& L = g.lev[0];
+    const long long C = (long long)L.n[0] * L.n[1] * L.n[2];
+    const long long n = C * g.nv;
+    k_stats_merge<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(C, g.nv, stats, other);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_stats_merge_count<<<1, 1, 0, s>>>(stats, other);
     return cudaGetLastError();
 }
 

@@ -10,7 +10,7 @@ from . import _abi as A
 def make_desc(ndim=1, n=(8, 1, 1), lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), batch=1, eq="euler", gamma=1.4,
               recon="mc", rvars="prim", flux="hllc", rk="ssprk2", bc="periodic", cfl=0.45, fixed_dt=0.0,
               precision="fp64", seed=0, weno_eps=1e-6, weno_eps_dx2=False, levels=None,
-              vortex_center=(5.0, 5.0), **_ignored) -> A.alsv_grid_desc:
+              vortex_center=(5.0, 5.0), sample_offset=0, **_ignored) -> A.alsv_grid_desc:
     """Build an ``alsv_grid_desc`` from plain values.
 
     ``bc``: one name for every side or a list of (lo, hi) names per direction.
@@ -48,6 +48,7 @@ def make_desc(ndim=1, n=(8, 1, 1), lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), batch
                 d.level_n[l][k] = int(ln[k]) if k < ndim else 1
             d.level_batch[l] = lb
     d.vortex_center[0], d.vortex_center[1] = vortex_center
+    d.sample_offset = int(sample_offset)
     return d
 
 

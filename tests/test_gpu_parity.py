@@ -76,6 +76,61 @@ def test_theta_splitmix_bitwise():
     assert np.array_equal(host(th3), oracle.theta_splitmix(77, 3, 128))
 
 
+def test_sample_offset_draws_global_parameters():
+    torch = torch_()
+    import paper_1912_07645_gb300 as alsv
+    S = gpu_solver(ndim=2, n=(16, 16), batch=8, seed=555, sample_offset=100, precision="fp32")
+    S.set_initial_data("kh")
+    th = torch.empty((8, 20), dtype=torch.float64, device="cuda")
+    alsv.alsv_get_parameters(S.ctx, th)
+    assert np.array_equal(host(th), oracle.theta_splitmix(555, 108, 20)[100:])
+    S.close()
+
+
+def test_stats_merge_matches_oracle_and_sharded_ensemble():
+    """Two shards of one ensemble (sample_offset), merged in order, equal the whole ensemble."""
+    torch = torch_()
+    import paper_1912_07645_gb300 as alsv
+    from paper_1912_07645_gb300.parallel import merge_in_rank_order
+    cfg = dict(ndim=2, n=(40, 36), eq="euler", recon="mc", flux="hllc", rvars="prim", rk="ssprk2", bc="periodic",
+               cfl=0.4, precision="fp64", seed=8)
+    accs, states = [], []
+    for off, B in ((0, 5), (5, 7)):
+        S = gpu_solver(**dict(cfg, batch=B, sample_offset=off))
+        S.set_initial_data("kh")
+        S.step(4)
+        S.stats_init()
+        S.stats_accumulate()
+        states.append(host(S.U).reshape(S.level_shape(0)))
+        accs.append(S.stats.clone())
+        S.sync()
+        keep = S if off == 0 else keep
+        if off:
+            S.close()
+    merged = merge_in_rank_order(keep, accs)
+    keep.sync()
+    d = oracle.make_desc(**cfg)
+    a = oracle.welford(d, states[0])
+    b = oracle.welford(d, states[1])
+    c, m, M2 = oracle.stats_merge(d, a, b)
+    raw = host(merged.view(torch.float64))
+    cells = 40 * 36
+    assert int(host(merged[:8].view(torch.int64))[0]) == c == 12
+    np.testing.assert_array_equal(raw[32:32 + 4 * cells].reshape(4, -1), m)
+    np.testing.assert_array_equal(raw[32 + 4 * cells:32 + 8 * cells].reshape(4, -1), M2)
+    # and the sharded ensemble equals the single ensemble of 12 samples
+    S12 = gpu_solver(**dict(cfg, batch=12))
+    S12.set_initial_data("kh")
+    S12.step(4)
+    all12 = host(S12.U).reshape(S12.level_shape(0))
+    assert np.array_equal(np.concatenate(states), all12)
+    c2, m2, M22 = oracle.welford(d, all12)
+    np.testing.assert_allclose(m, m2, rtol=1e-13, atol=1e-15)
+    np.testing.assert_allclose(M2, M22, rtol=1e-11, atol=1e-14)
+    S12.close()
+    keep.close()
+
+
 @pytest.mark.parametrize("case", ["kh2", "kh3", "sod", "lax", "burgers", "vortex"])
 def test_initial_data_fp64(case):
     if case == "kh2":

@@ -505,3 +505,24 @@ def test_dual_gradient_dot_direction():
 def test_fixed_dt_reading_at_512():
     dt, n = oracle.fixed_dt_kh(512, 1.0, 0.4)
     assert n == 3035 and dt == 1.0 / 3035
+
+
+def test_stats_merge_equals_two_pass_of_union():
+    d = oracle.make_desc(ndim=1, n=(7,), eq="euler")
+    rng = np.random.default_rng(3)
+    U = np.zeros((23, 3, 1, 1, 7))
+    U[:, 0] = rng.uniform(0.5, 2, (23, 1, 1, 7))
+    U[:, 1] = rng.uniform(-1, 1, (23, 1, 1, 7))
+    U[:, 2] = rng.uniform(3, 5, (23, 1, 1, 7))
+    parts = [U[:9], U[9:10], U[10:]]
+    acc = (0, np.zeros((3, 7)), np.zeros((3, 7)))
+    for p in parts:
+        acc = oracle.stats_merge(d, acc, oracle.welford(d, p))
+    c, m, M2 = acc
+    L = U.astype(np.longdouble)
+    W = np.stack([L[:, 0], L[:, 1] / L[:, 0], 0.4 * (L[:, 2] - 0.5 * L[:, 1] ** 2 / L[:, 0])], axis=1).reshape(23, 3, -1)
+    mu = W.mean(axis=0)
+    var = ((W - mu) ** 2).sum(axis=0) / 22
+    assert c == 23
+    np.testing.assert_allclose(m, mu.astype(float), rtol=1e-14, atol=1e-15)
+    np.testing.assert_allclose(M2 / 22, var.astype(float), rtol=1e-13)

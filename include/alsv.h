@@ -165,6 +165,15 @@ alsv_status alsv_step(alsv_ctx* ctx, int n_steps);
  */
 alsv_status alsv_evolve_to_T(alsv_ctx* ctx, double T, int64_t* steps_taken_host);
 
+/*
+ * alsv_set_time - resume: set every sample's time t_host[b] and step count steps_host[b] (host
+ * arrays of alsv_num_samples entries; steps may be NULL for 0) for the state currently bound, and
+ * recompute the CFL partials and time steps from that state. A run checkpointed as (U, t, steps)
+ * and resumed with alsv_set_initial_data(ALSV_INIT_RAW) + alsv_set_time continues bitwise as if it
+ * had not stopped. Synchronous with respect to the host arrays.
+ */
+alsv_status alsv_set_time(alsv_ctx* ctx, const double* t_host, const int64_t* steps_host);
+
 /* Synchronise the stream and report the device status word (OK or the first error raised). */
 alsv_status alsv_sync(alsv_ctx* ctx);
 

@@ -15,7 +15,8 @@ from ._abi import (BC, EQ, FLUX, INIT, PRECISION, RECON, RK, RVARS, AlsvError, a
                    alsv_get_launch_count, alsv_get_parameters, alsv_get_profile, alsv_get_tile, alsv_get_time, alsv_grid_desc,
                    alsv_init_grid, alsv_kinetic_energy, alsv_last_error, alsv_num_samples,
                    alsv_num_tile_variants, alsv_num_vars, alsv_set_graphs, alsv_set_initial_data,
-                   alsv_set_profiling, alsv_set_tile_variant, alsv_state_bytes, alsv_stats_accumulate,
+                   alsv_set_profiling, alsv_set_tile_variant, alsv_set_time, alsv_state_bytes, alsv_stats_accumulate,
                    alsv_stats_bytes, alsv_stats_merge, alsv_stats_read, alsv_stats_reset, alsv_step, alsv_sync,
                    alsv_version, load)
+from .provenance import provenance, save_result  # noqa: F401
 from .solver import Solver, make_desc  # noqa: F401

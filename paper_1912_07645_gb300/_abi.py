@@ -61,6 +61,7 @@ SIGNATURES = {
     "alsv_step": (C.c_int, [_ctx, C.c_int]),
     "alsv_evolve_to_T": (C.c_int, [_ctx, C.c_double, _i64p]),
     "alsv_sync": (C.c_int, [_ctx]),
+    "alsv_set_time": (C.c_int, [_ctx, _dp, _i64p]),
     "alsv_get_time": (C.c_int, [_ctx, _dp, _i64p]),
     "alsv_stats_bytes": (_sz, [_ctx]),
     "alsv_stats_reset": (C.c_int, [_ctx, _vp, _sz]),
@@ -181,6 +182,15 @@ def alsv_evolve_to_T(ctx, T: float) -> int:
     steps = C.c_int64()
     _check(load().alsv_evolve_to_T(ctx, T, C.byref(steps)), "alsv_evolve_to_T", ctx)
     return steps.value
+
+
+def alsv_set_time(ctx, t, steps=None):
+    """t, steps: host sequences of alsv_num_samples entries."""
+    import numpy as np
+    tt = np.ascontiguousarray(t, dtype=np.float64)
+    ss = None if steps is None else np.ascontiguousarray(steps, dtype=np.int64)
+    _check(load().alsv_set_time(ctx, tt.ctypes.data_as(_dp), None if ss is None else ss.ctypes.data_as(_i64p)),
+           "alsv_set_time", ctx)
 
 
 def alsv_sync(ctx):

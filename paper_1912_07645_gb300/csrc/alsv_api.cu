@@ -510,6 +510,25 @@ alsv_status alsv_set_initial_data(alsv_ctx* c, int kind, const double* theta_dev
     return ALSV_OK;
 }
 
+alsv_status alsv_set_time(alsv_ctx* c, const double* t_host, const int64_t* steps_host) {
+    alsv_status st = require_ready(c);
+    if (st != ALSV_OK) return st;
+    if (!t_host) return fail(c, ALSV_ERR_INVALID_ARG, "null time array");
+    const size_t S = c->total_samples;
+    for (size_t i = 0; i < S; ++i)
+        if (!std::isfinite(t_host[i]) || t_host[i] < 0.0) return fail(c, ALSV_ERR_INVALID_ARG, "times must be finite and >= 0");
+    CK(cudaMemcpyAsync(c->t, t_host, S * 8, cudaMemcpyHostToDevice, c->stream));
+    if (steps_host) CK(cudaMemcpyAsync(c->nstep, steps_host, S * 8, cudaMemcpyHostToDevice, c->stream));
+    else CK(cudaMemsetAsync(c->nstep, 0, S * 8, c->stream));
+    CK(cudaMemsetAsync(c->done, 0, S * 4, c->stream));
+    CK(cudaMemsetAsync(c->last, 0, S * 4, c->stream));
+    CK(cudaStreamSynchronize(c->stream));   // the host arrays may be released after return
+    st = enqueue_speed_and_prepare(c);
+    if (st != ALSV_OK) return st;
+    c->time_ready = true;
+    return ALSV_OK;
+}
+
 alsv_status alsv_step(alsv_ctx* c, int n_steps) {
     alsv_status st = require_ready(c);
     if (st != ALSV_OK) return st;

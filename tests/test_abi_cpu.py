@@ -151,3 +151,13 @@ def test_adjoint_validation_without_gpu(alsv):
         assert b >= (55 + 55 + 3) * state and b < (55 + 55 + 3) * state + (1 << 24)
     finally:
         alsv.alsv_destroy(ctx)
+
+
+def test_provenance_record(alsv, tmp_path):
+    import json
+    d = alsv.make_desc(ndim=2, n=(32, 16), batch=3, seed=77)
+    rec = alsv.provenance(d, initial_data="kh")
+    assert rec["library"].startswith("alsv") and rec["descriptor"]["n"][:2] == [32, 16]
+    assert rec["descriptor"]["seed"] == 77 and rec["initial_data"] == "kh"
+    p = alsv.save_result(str(tmp_path / "r"), {"x": [1.0, 2.0]}, d, note="test")
+    assert json.load(open(p))["note"] == "test"

@@ -459,3 +459,30 @@ def test_fixed_dt_cfl_guard():
         S.evolve_to(0.1)
     assert ei.value.status_name == "ERR_CFL"
     S.close()
+
+
+def test_checkpoint_resume_is_bitwise():
+    """Evolve 0 -> T/2, checkpoint (U, t, steps), resume in a new context, evolve to T: bitwise
+    equal to one uninterrupted evolve to T (checkpoint/resume)."""
+    torch = torch_()
+    import paper_1912_07645_gb300 as alsv
+    cfg = dict(ndim=2, n=(64, 48), batch=3, eq="euler", recon="weno3", flux="hllc", rvars="prim", rk="ssprk3",
+               bc="periodic", cfl=0.4, precision="fp32", seed=21)
+    A = gpu_solver(**cfg)
+    A.set_initial_data("kh")
+    A.evolve_to(0.05)
+    U_ck = host(A.U).copy()
+    t_ck, s_ck = A.time()
+    A.evolve_to(0.1)
+    ref = host(A.U)
+    _, s_ref = A.time()
+    A.close()
+    B = gpu_solver(**cfg)
+    B.set_state(torch.from_numpy(U_ck))
+    alsv.alsv_set_time(B.ctx, t_ck, s_ck)
+    B.evolve_to(0.1)
+    out = host(B.U)
+    t_b, s_b = B.time()
+    B.close()
+    assert np.array_equal(out, ref)
+    assert np.array_equal(s_b, s_ref) and np.all(t_b == 0.1)

@@ -59,8 +59,8 @@ __device__ __forceinline__ void rusanov_vjp(const R* WL, const R* WR, const R* F
     R UL[4], UR[4];
     prim_to_cons<R, 2>(WL, UL, R(1) / inv_gm1, inv_gm1);
     prim_to_cons<R, 2>(WR, UR, R(1) / inv_gm1, inv_gm1);
-    const R cL = rsqrt_(gamma * WL[3] / WL[0]);
-    const R cR = rsqrt_(gamma * WR[3] / WR[0]);
+    const R cL = sound_speed<R>(gamma, WL[3], WL[0]);
+    const R cR = sound_speed<R>(gamma, WR[3], WR[0]);
     const R sL = fabs_(WL[N]) + cL, sR = fabs_(WR[N]) + cR;
     const bool pickR = sR > sL;
     const R a = pickR ? sR : sL;

@@ -355,6 +355,10 @@ alsv_status alsv_init_grid(const alsv_grid_desc* d_in, void* stream, alsv_ctx** 
             L.inv_dx[k] = 1.0 / L.dx[k];
         }
         samples += L.samples;
+        if ((long long)c->nv * L.n[0] * L.n[1] * L.n[2] >= (1LL << 31)) {
+            delete c;
+            return bad("one sample must hold fewer than 2^31 elements");
+        }
     }
     if (samples > 65535) { delete c; return bad("at most 65535 samples per context"); }
     c->total_samples = (int)samples;

@@ -101,6 +101,11 @@ template <class R> __device__ __forceinline__ R minmod3(R a, R b, R c) {
     if (a < R(0) && b < R(0) && c < R(0)) return fmax_(fmax_(a, b), c);
     return R(0);
 }
+// FP32: the same value from the extremes (all positive <=> min > 0; all negative <=> max < 0)
+template <> __device__ __forceinline__ float minmod3(float a, float b, float c) {
+    const float mn = fminf(fminf(a, b), c), mx = fmaxf(fmaxf(a, b), c);
+    return mn > 0.0f ? mn : (mx < 0.0f ? mx : 0.0f);
+}
 
 template <class R> __device__ __forceinline__ R mc_slope(R wm, R w0, R wp) {
     const R dm = w0 - wm, dp = wp - w0;

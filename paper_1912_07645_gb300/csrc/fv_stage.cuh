@@ -25,6 +25,11 @@ template <class R> __device__ __forceinline__ R speed_over_dx(R s, const LevelIn
     if constexpr (IsExact<R>::value) return s / R(L.dx[k]);
     else return s * R(L.inv_dx[k]);
 }
+// the same with the per-direction factor already converted: dx_k (FP64) or 1/dx_k (FP32)
+template <class R> __device__ __forceinline__ R speed_dx(R s, R f) {
+    if constexpr (IsExact<R>::value) return s / f;
+    else return s * f;
+}
 
 template <class R> struct RealTraits;
 template <> struct RealTraits<float> { static __device__ __forceinline__ float nan() { return __int_as_float(0x7fffffff); } };
@@ -127,6 +132,16 @@ __device__ __forceinline__ void interface_states(const R* sw, int i0, int step, 
         return;
     }
     constexpr int IP = ND + 1;
+    if (G == 1) {  // PC: a face is its cell's value, so the fallback would return the same state
+        if (rvars == RV_PRIM) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) { WL[v] = cl[v]; WR[v] = cr[v]; }
+        } else {
+            cons_to_prim<R, ND>(cl, WL, gm1);
+            cons_to_prim<R, ND>(cr, WR, gm1);
+        }
+        return;
+    }
     if (rvars == RV_PRIM) {
         const bool okL = fr[0] > R(0) && fr[IP] > R(0);
         const bool okR = fl[0] > R(0) && fl[IP] > R(0);
@@ -185,7 +200,7 @@ __global__ void __launch_bounds__(NT) k_stage(const StageArgs p) {
     const int tx0 = (tile % L.ntile[0]) * TX;
     const int ty0 = ND >= 2 ? ((tile / L.ntile[0]) % L.ntile[1]) * TY : 0;
     const int tz0 = ND >= 3 ? (tile / (L.ntile[0] * L.ntile[1])) * TZ : 0;
-    const long long plane = (long long)nx * ny * nz;
+    const int plane = nx * ny * nz;  // one sample holds < 2^31 elements (host-checked)
     const long long sbase = L.elem0 + (long long)b_local * NV * plane;
     const R* Us = reinterpret_cast<const R*>(p.Us) + sbase;
 
@@ -210,7 +225,7 @@ __global__ void __launch_bounds__(NT) k_stage(const StageArgs p) {
             if (ND >= 2) iy = map_ghost(iy, ny, g.bc[1][0], g.bc[1][1], flip[1]);
             if (ND >= 3) iz = map_ghost(iz, nz, g.bc[2][0], g.bc[2][1], flip[2]);
         }
-        const long long off = ((long long)iz * ny + iy) * nx + ix;
+        const int off = (iz * ny + iy) * nx + ix;
         R u[NV];
 #pragma unroll
         for (int v = 0; v < NV; ++v) u[v] = Us[v * plane + off];
@@ -293,6 +308,11 @@ __global__ void __launch_bounds__(NT) k_stage(const StageArgs p) {
     // ---- 3. RK combination and store; wave speed of the new state
     const R dt = R(p.dt[sample]);
     const R ca = R(p.a), cb = R(p.b);
+    const bool has_un = p.a != 0.0;           // loop invariants, converted once
+    const bool want_speed = p.want_speed != 0;
+    R sdx[ND];
+#pragma unroll
+    for (int k = 0; k < ND; ++k) sdx[k] = IsExact<R>::value ? R(L.dx[k]) : R(L.inv_dx[k]);
     const R* Un = reinterpret_cast<const R*>(p.Un) + sbase;
     R* Uo = reinterpret_cast<R*>(p.Uout) + sbase;
     R smax = R(0);
@@ -304,22 +324,22 @@ __global__ void __launch_bounds__(NT) k_stage(const StageArgs p) {
         const int y = ty0 + (ND >= 2 ? (c / TX) % TY : 0);
         const int z = tz0 + (ND >= 3 ? c / (TX * TY) : 0);
         if (x >= nx || y >= ny || z >= nz) continue;
-        const long long off = ((long long)z * ny + y) * nx + x;
+        const int off = (z * ny + y) * nx + x;
         R out[NV];
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
             const R us = Us[v * plane + off];
             R o = us + dt * acc[m][v];
-            if (p.a != 0.0) o = ca * Un[v * plane + off] + cb * o;
+            if (has_un) o = ca * Un[v * plane + off] + cb * o;
             out[v] = o;
             Uo[v * plane + off] = o;
         }
-        if (p.want_speed) {
+        if (want_speed) {
             if (EQ == EQ_BURGERS) {
                 const R au = fabs_(out[0]);
                 if (!(au == au) || isinf(au)) bad = true;
 #pragma unroll
-                for (int k = 0; k < ND; ++k) smax = fmax_(smax, speed_over_dx<R>(au, L, k));
+                for (int k = 0; k < ND; ++k) smax = fmax_(smax, speed_dx<R>(au, sdx[k]));
             } else {
                 R wv[NV];
                 cons_to_prim<R, ND>(out, wv, gm1);
@@ -327,14 +347,14 @@ __global__ void __launch_bounds__(NT) k_stage(const StageArgs p) {
                 if (!(rho > R(0) && pr > R(0)) || isinf(rho) || isinf(pr)) {
                     bad = true;
                 } else {
-                    const R c = rsqrt_(gamma * pr / rho);
+                    const R c = sound_speed<R>(gamma, pr, rho);
 #pragma unroll
-                    for (int k = 0; k < ND; ++k) smax = fmax_(smax, speed_over_dx<R>(fabs_(wv[1 + k]) + c, L, k));
+                    for (int k = 0; k < ND; ++k) smax = fmax_(smax, speed_dx<R>(fabs_(wv[1 + k]) + c, sdx[k]));
                 }
             }
         }
     }
-    if (p.want_speed) {
+    if (want_speed) {
         // fixed-pattern CTA reduction (max is exact; the pattern is fixed anyway)
         __shared__ double red[NT / 32];
         __shared__ int redbad[NT / 32];
@@ -373,7 +393,7 @@ __global__ void __launch_bounds__(NT) k_speed(const GridArgs g, const void* Uv, 
     const int tx0 = (tile % L.ntile[0]) * TX;
     const int ty0 = ND >= 2 ? ((tile / L.ntile[0]) % L.ntile[1]) * TY : 0;
     const int tz0 = ND >= 3 ? (tile / (L.ntile[0] * L.ntile[1])) * TZ : 0;
-    const long long plane = (long long)nx * ny * nz;
+    const int plane = nx * ny * nz;
     const R* U = reinterpret_cast<const R*>(Uv) + L.elem0 + (long long)b_local * NV * plane;
     const R gamma = R(g.gamma), gm1 = gamma - R(1);
     const int tid = threadIdx.x;
@@ -386,7 +406,7 @@ __global__ void __launch_bounds__(NT) k_speed(const GridArgs g, const void* Uv, 
         const int y = ty0 + (ND >= 2 ? (c / TX) % TY : 0);
         const int z = tz0 + (ND >= 3 ? c / (TX * TY) : 0);
         if (x >= nx || y >= ny || z >= nz) continue;
-        const long long off = ((long long)z * ny + y) * nx + x;
+        const int off = (z * ny + y) * nx + x;
         R u[NV];
 #pragma unroll
         for (int v = 0; v < NV; ++v) u[v] = U[v * plane + off];
@@ -402,7 +422,7 @@ __global__ void __launch_bounds__(NT) k_speed(const GridArgs g, const void* Uv, 
             if (!(rho > R(0) && pr > R(0)) || isinf(rho) || isinf(pr)) {
                 bad = true;
             } else {
-                const R c = rsqrt_(gamma * pr / rho);
+                const R c = sound_speed<R>(gamma, pr, rho);
 #pragma unroll
                 for (int k = 0; k < ND; ++k) smax = fmax_(smax, speed_over_dx<R>(fabs_(wv[1 + k]) + c, L, k));
             }

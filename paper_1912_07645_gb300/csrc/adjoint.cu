@@ -142,11 +142,12 @@ __global__ void __launch_bounds__(NT) k_stage_adj(const AdjStageArgs p) {
 
     const GridArgs& g = p.g;
     const LevelInfo& L = g.lev[0];
-    const long long w = blockIdx.x;
-    const int b_local = (int)(w / L.tiles);
-    const int tile = (int)(w - (long long)b_local * L.tiles);
+    const uint32_t w = blockIdx.x;
+    const uint32_t b_local = fdiv(w, L.fd_tiles);
+    const uint32_t tile = w - b_local * (uint32_t)L.tiles;
     const int nx = L.n[0], ny = L.n[1];
-    const int x0 = (tile % L.ntile[0]) * TX, y0 = (tile / L.ntile[0]) * TY;
+    const uint32_t trow = fdiv(tile, L.fd_nt0);
+    const int x0 = (int)(tile - trow * (uint32_t)L.ntile[0]) * TX, y0 = (int)trow * TY;
     const long long plane = (long long)nx * ny;
     const long long sbase = (long long)b_local * NV * plane;
     const R* Us = reinterpret_cast<const R*>(p.Us) + sbase;
@@ -497,6 +498,9 @@ GridArgs adj_grid(const alsv_ctx* c) {
     L.ntile[1] = (L.n[1] + kAdjTY - 1) / kAdjTY;
     L.ntile[2] = 1;
     L.tiles = L.ntile[0] * L.ntile[1];
+    L.fd_tiles = make_fastdiv((uint32_t)L.tiles);
+    L.fd_nt0 = make_fastdiv((uint32_t)L.ntile[0]);
+    L.fd_nt1 = make_fastdiv((uint32_t)L.ntile[1]);
     L.work0 = 0;
     g.total_work = (long long)L.samples * L.tiles;
     return g;

@@ -55,6 +55,9 @@ long long build_levels(const alsv_ctx* c, int variant, GridArgs& g) {
             L.ntile[k] = k < c->ndim ? (L.n[k] + t[k] - 1) / t[k] : 1;
             L.tiles *= L.ntile[k];
         }
+        L.fd_tiles = make_fastdiv((uint32_t)L.tiles);
+        L.fd_nt0 = make_fastdiv((uint32_t)L.ntile[0]);
+        L.fd_nt1 = make_fastdiv((uint32_t)L.ntile[1]);
         L.sample0 = s0;
         L.elem0 = elem;
         L.work0 = work;

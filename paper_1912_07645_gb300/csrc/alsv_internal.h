@@ -18,6 +18,24 @@ enum { ST_NONPHYSICAL = 1, ST_CFL = 2, ST_TIMEOUT = 4 };
 
 constexpr int kMaxLevels = 8;
 
+// Division by a runtime constant d (1 <= d < 2^31) for 0 <= n < 2^31 without a divide
+// instruction sequence (Granlund-Montgomery): with l = ceil(log2 d) and
+// m = floor(2^32 (2^l - d) / d) + 1, n / d = (umulhi(n, m) + n) >> l.
+struct FastDiv {
+    uint32_t d, m, l;
+};
+inline FastDiv make_fastdiv(uint32_t d) {
+    FastDiv f;
+    f.d = d;
+    f.l = 0;
+    while ((1ull << f.l) < d) ++f.l;
+    f.m = (uint32_t)(((1ull << 32) * ((1ull << f.l) - d)) / d + 1);
+    return f;
+}
+#ifdef __CUDACC__
+__device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv& f) { return (__umulhi(n, f.m) + n) >> f.l; }
+#endif
+
 // One grid of an MLMC level table (a single-grid context has one level).
 struct LevelInfo {
     int n[3];          // cells per direction
@@ -29,6 +47,9 @@ struct LevelInfo {
     long long work0;   // first (sample, tile) work item of the level
     double dx[3];
     double inv_dx[3];
+    FastDiv fd_tiles;  // divisors for the (sample, tile) decomposition of a work item
+    FastDiv fd_nt0;    // tiles along x
+    FastDiv fd_nt1;    // tiles along y
 };
 
 struct GridArgs {

@@ -355,11 +355,11 @@ __device__ __forceinline__ int map_ghost(int i, int n, int bc_lo, int bc_hi, boo
 }
 
 // Locate the level and local sample of a global work item / sample.
-__device__ __forceinline__ int level_of_work(const GridArgs& g, long long w) {
+__device__ __forceinline__ int level_of_work(const GridArgs& g, uint32_t w) {
     int l = 0;
 #pragma unroll 1
     for (int k = 1; k < g.nlev; ++k)
-        if (w >= g.lev[k].work0) l = k;
+        if ((long long)w >= g.lev[k].work0) l = k;
     return l;
 }
 __device__ __forceinline__ int level_of_sample(const GridArgs& g, int s) {

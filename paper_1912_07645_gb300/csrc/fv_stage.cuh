@@ -186,20 +186,22 @@ __global__ void __launch_bounds__(NT) k_stage(const StageArgs p) {
     R* sW = reinterpret_cast<R*>(smem_raw);   // [NS][CS] reconstruction variables per cell
     R* sF = sW + CS * NS;                      // [NI][CS] interface fluxes
 
-    const long long w = blockIdx.x;
+    const uint32_t w = blockIdx.x;  // < 2^31 work items (host-checked)
     const GridArgs& g = p.g;
     const int l = level_of_work(g, w);
     const LevelInfo& L = g.lev[l];
-    const long long wl = w - L.work0;
-    const int b_local = (int)(wl / L.tiles);
-    const int tile = (int)(wl - (long long)b_local * L.tiles);
-    const int sample = L.sample0 + b_local;
+    const uint32_t wl = w - (uint32_t)L.work0;
+    const uint32_t b_local = fdiv(wl, L.fd_tiles);
+    const uint32_t tile = wl - b_local * (uint32_t)L.tiles;
+    const int sample = L.sample0 + (int)b_local;
     if (p.done[sample]) return;
 
     const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
-    const int tx0 = (tile % L.ntile[0]) * TX;
-    const int ty0 = ND >= 2 ? ((tile / L.ntile[0]) % L.ntile[1]) * TY : 0;
-    const int tz0 = ND >= 3 ? (tile / (L.ntile[0] * L.ntile[1])) * TZ : 0;
+    const uint32_t trow = fdiv(tile, L.fd_nt0);
+    const int tx0 = (int)(tile - trow * (uint32_t)L.ntile[0]) * TX;
+    const uint32_t tplane = ND >= 2 ? fdiv(trow, L.fd_nt1) : 0u;
+    const int ty0 = ND >= 2 ? (int)(trow - tplane * (uint32_t)L.ntile[1]) * TY : 0;
+    const int tz0 = ND >= 3 ? (int)tplane * TZ : 0;
     const int plane = nx * ny * nz;  // one sample holds < 2^31 elements (host-checked)
     const long long sbase = L.elem0 + (long long)b_local * NV * plane;
     const R* Us = reinterpret_cast<const R*>(p.Us) + sbase;
@@ -383,16 +385,18 @@ __global__ void __launch_bounds__(NT) k_speed(const GridArgs g, const void* Uv, 
     constexpr int NV = (EQ == EQ_BURGERS) ? 1 : ND + 2;
     constexpr int CELLS = TX * TY * TZ;
     constexpr int CPT = CELLS / NT;
-    const long long w = blockIdx.x;
+    const uint32_t w = blockIdx.x;
     const int l = level_of_work(g, w);
     const LevelInfo& L = g.lev[l];
-    const long long wl = w - L.work0;
-    const int b_local = (int)(wl / L.tiles);
-    const int tile = (int)(wl - (long long)b_local * L.tiles);
+    const uint32_t wl = w - (uint32_t)L.work0;
+    const uint32_t b_local = fdiv(wl, L.fd_tiles);
+    const uint32_t tile = wl - b_local * (uint32_t)L.tiles;
     const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
-    const int tx0 = (tile % L.ntile[0]) * TX;
-    const int ty0 = ND >= 2 ? ((tile / L.ntile[0]) % L.ntile[1]) * TY : 0;
-    const int tz0 = ND >= 3 ? (tile / (L.ntile[0] * L.ntile[1])) * TZ : 0;
+    const uint32_t trow = fdiv(tile, L.fd_nt0);
+    const int tx0 = (int)(tile - trow * (uint32_t)L.ntile[0]) * TX;
+    const uint32_t tplane = ND >= 2 ? fdiv(trow, L.fd_nt1) : 0u;
+    const int ty0 = ND >= 2 ? (int)(trow - tplane * (uint32_t)L.ntile[1]) * TY : 0;
+    const int tz0 = ND >= 3 ? (int)tplane * TZ : 0;
     const int plane = nx * ny * nz;
     const R* U = reinterpret_cast<const R*>(Uv) + L.elem0 + (long long)b_local * NV * plane;
     const R gamma = R(g.gamma), gm1 = gamma - R(1);

@@ -161,3 +161,28 @@ def test_provenance_record(alsv, tmp_path):
     assert rec["descriptor"]["seed"] == 77 and rec["initial_data"] == "kh"
     p = alsv.save_result(str(tmp_path / "r"), {"x": [1.0, 2.0]}, d, note="test")
     assert json.load(open(p))["note"] == "test"
+
+
+def test_fast_division_formula():
+    """The work-item decomposition divides by runtime constants with the Granlund-Montgomery
+    multiply-high form n / d = (umulhi(n, m) + n) >> l, l = ceil(log2 d),
+    m = floor(2^32 (2^l - d) / d) + 1, valid for 0 <= n < 2^31; checked here exhaustively on
+    edge cases and randomly elsewhere."""
+    import random
+    rnd = random.Random(1)
+
+    def mk(d):
+        l = 0
+        while (1 << l) < d:
+            l += 1
+        return ((1 << 32) * ((1 << l) - d)) // d + 1, l
+
+    ds = list(range(1, 600)) + [rnd.randrange(1, 2**31) for _ in range(3000)] + [2**k for k in range(31)] + \
+        [2**k - 1 for k in range(1, 31)] + [2**k + 1 for k in range(1, 30)]
+    for d in ds:
+        m, l = mk(d)
+        assert m < 2**32
+        ns = [0, 1, d - 1, d, d + 1, 2**31 - 1] + [rnd.randrange(0, 2**31) for _ in range(20)]
+        for n in ns:
+            if 0 <= n < 2**31:
+                assert ((((n * m) >> 32) + n) >> l) == n // d

@@ -261,13 +261,16 @@ alsv_status alsv_destroy(alsv_ctx* ctx);
 /*
  * Execution controls (no counterpart in the paper; they choose how the same arithmetic is
  * scheduled on the GPU and never change results).
- *   alsv_num_tile_variants  number of stage-kernel tile shapes for this (precision, ndim)
- *   alsv_set_tile_variant   select one (recomputes the wave-speed partials; asynchronous)
+ *   alsv_num_tile_variants  number of stage-kernel schedules for this (precision, ndim): tiles of
+ *                           several shapes and, for FP32 2D Euler on periodic grids with primitive
+ *                           WENO3/MC reconstruction and HLLC/Rusanov, a column-marching schedule
+ *   alsv_set_tile_variant   select one (recomputes the wave-speed partials; asynchronous;
+ *                           ALSV_ERR_INVALID_ARG if the variant does not support the scheme)
  *   alsv_get_tile           current tile shape, variant and (sample, tile) work items per launch
  *   alsv_autotune           time `reps` launches of the first stage (reads U, writes the stage
  *                           buffer only, so the state is unchanged) per variant with CUDA events
  *                           on the context stream and keep the fastest; ms_per_variant (host, may
- *                           be NULL) receives the times. SYNCHRONOUS.
+ *                           be NULL) receives the times (-1 for unsupported variants). SYNCHRONOUS.
  *   alsv_set_graphs         1 (default): alsv_evolve_to_T replays captured CUDA graphs of
  *                           16-step chunks; 0: direct launches
  *   alsv_set_profiling      1: record CUDA events around every stage / time-control launch of

@@ -42,6 +42,10 @@ alsv_status cuda_fail(alsv_ctx* c, cudaError_t e, const char* what) {
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+bool variant_ok(const alsv_ctx* c, int v) {
+    return stage_variant_supported(c->fp64, c->ndim, c->eq, c->d.recon, c->g.rvars, c->d.flux, c->g.bc, v);
+}
+
 // Build the per-level tiling for one tile variant.
 long long build_levels(const alsv_ctx* c, int variant, GridArgs& g) {
     TileShape ts = stage_tile(c->fp64, c->ndim, variant);
@@ -271,6 +275,7 @@ TileShape stage_tile(int fp64, int ndim, int variant) {
     if (ndim == 2) {
         if (variant == 1) return TileShape{32, 8, 1, 256};
         if (variant == 2 && !fp64) return TileShape{32, 32, 1, 256};
+        if (variant == 3 && !fp64) return TileShape{31, 1 << 20, 1, 128};  // column strips, whole height
         return TileShape{32, 16, 1, 256};
     }
     if (fp64) return variant == 1 ? TileShape{8, 8, 4, 256} : TileShape{8, 8, 8, 256};
@@ -278,8 +283,16 @@ TileShape stage_tile(int fp64, int ndim, int variant) {
 }
 int stage_num_variants(int fp64, int ndim) {
     if (ndim == 1) return 1;
-    if (ndim == 2 && !fp64) return 3;
+    if (ndim == 2 && !fp64) return 4;
     return 2;
+}
+bool stage_variant_supported(int fp64, int ndim, int eq, int recon, int rvars, int flux, const int bc[3][2], int variant) {
+    if (variant < 0 || variant >= stage_num_variants(fp64, ndim)) return false;
+    if (!(ndim == 2 && !fp64 && variant == 3)) return true;
+    const bool periodic = bc[0][0] == BC_PERIODIC && bc[0][1] == BC_PERIODIC && bc[1][0] == BC_PERIODIC &&
+                          bc[1][1] == BC_PERIODIC;
+    return eq == EQ_EULER && rvars == RV_PRIM && periodic && (recon == REC_WENO3 || recon == REC_MC) &&
+           (flux == FLX_HLLC || flux == FLX_RUSANOV);
 }
 }  // namespace alsv
 
@@ -709,6 +722,7 @@ alsv_status alsv_set_tile_variant(alsv_ctx* c, int variant) {
     if (!c) return fail(nullptr, ALSV_ERR_INVALID_ARG, "null context");
     if (variant < 0 || variant >= stage_num_variants(c->fp64, c->ndim))
         return fail(c, ALSV_ERR_INVALID_ARG, "tile variant out of range");
+    if (!variant_ok(c, variant)) return fail(c, ALSV_ERR_INVALID_ARG, "tile variant does not support this scheme");
     if (variant == c->variant) return ALSV_OK;
     c->variant = variant;
     build_levels(c, variant, c->g);
@@ -735,6 +749,10 @@ alsv_status alsv_autotune(alsv_ctx* c, int reps, int* chosen, float* ms_per_vari
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     for (int v = 0; v < nvar; ++v) {
+        if (!variant_ok(c, v)) {
+            if (ms_per_variant) ms_per_variant[v] = -1.0f;
+            continue;
+        }
         GridArgs g = c->g;
         const int saved = c->variant;
         c->variant = v;

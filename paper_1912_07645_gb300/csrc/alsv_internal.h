@@ -86,6 +86,8 @@ struct TileShape {
 };
 TileShape stage_tile(int fp64, int ndim, int variant);
 int stage_num_variants(int fp64, int ndim);
+// whether a variant supports a configuration (the column-marching variant is specialised)
+bool stage_variant_supported(int fp64, int ndim, int eq, int recon, int rvars, int flux, const int bc[3][2], int variant);
 
 // Launchers (return cudaGetLastError of the launch).
 cudaError_t launch_stage(int fp64, int ndim, int eq, int recon, int flux, int variant, const StageArgs& a,

@@ -152,9 +152,9 @@ __device__ __forceinline__ void weno3_pair(float wm, float w0, float w1, float w
 
 // The same for two variables at once with packed FP32x2 arithmetic (one instruction per pair).
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
-__device__ __forceinline__ void weno3_pair2(float2 wm, float2 w0, float2 w1, float2 w2, float eps, float2& fr,
+__device__ __forceinline__ void weno3_pair2(float2 wm, float2 w0, float2 w1, float2 w2, float2 e, float2& fr,
                                             float2& fl) {
-    const float2 half = f2(0.5f), m1 = f2(-1.0f), e = f2(eps), two = f2(2.0f);
+    const float2 half = f2(0.5f), m1 = f2(-1.0f), two = f2(2.0f);
     const float2 p1 = __fmul2_rn(half, __fadd2_rn(w0, w1));
     const float2 d1 = __ffma2_rn(w0, m1, w1);
     const float2 e1 = __ffma2_rn(d1, d1, e);

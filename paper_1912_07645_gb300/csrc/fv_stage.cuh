@@ -113,7 +113,7 @@ __device__ __forceinline__ void interface_states(const R* sw, int i0, int step, 
             for (int v = 0; v + 1 < NV; v += 2) {
                 float2 a, b;
                 weno3_pair2(make_float2(cm[v], cm[v + 1]), make_float2(cl[v], cl[v + 1]),
-                            make_float2(cr[v], cr[v + 1]), make_float2(c2[v], c2[v + 1]), eps, a, b);
+                            make_float2(cr[v], cr[v + 1]), make_float2(c2[v], c2[v + 1]), f2(eps), a, b);
                 fr[v] = a.x; fr[v + 1] = a.y;
                 fl[v] = b.x; fl[v + 1] = b.y;
             }

@@ -1,4 +1,5 @@
 // Stage and speed kernels for float, 2D (explicit tile-shape variants).
+#include "fv_colmarch.cuh"
 #include "stage_dispatch.cuh"
 namespace alsv {
 cudaError_t launch_stage_f32_2d(int variant, int eq, int recon, int flux, const StageArgs& a, cudaStream_t s) {
@@ -6,6 +7,18 @@ cudaError_t launch_stage_f32_2d(int variant, int eq, int recon, int flux, const 
         case 0: return launch_stage_tile<float, 2, 32, 16, 1, 256>(eq, recon, flux, a, s);
         case 1: return launch_stage_tile<float, 2, 32, 8, 1, 256>(eq, recon, flux, a, s);
         case 2: return launch_stage_tile<float, 2, 32, 32, 1, 256>(eq, recon, flux, a, s);
+        case 3: {
+            // column-marching variant (FP32 2D Euler, periodic, primitive; WENO3/MC x HLLC/Rusanov)
+            if (eq != EQ_EULER || a.g.rvars != RV_PRIM) return cudaErrorNotSupported;
+            if (a.g.total_work <= 0) return cudaSuccess;
+            const unsigned blocks = (unsigned)((a.g.total_work + kColWarps - 1) / kColWarps);
+            if (recon == REC_WENO3 && flux == FLX_HLLC) k_stage2d_col<REC_WENO3, FLX_HLLC><<<blocks, 32 * kColWarps, 0, s>>>(a);
+            else if (recon == REC_WENO3 && flux == FLX_RUSANOV) k_stage2d_col<REC_WENO3, FLX_RUSANOV><<<blocks, 32 * kColWarps, 0, s>>>(a);
+            else if (recon == REC_MC && flux == FLX_HLLC) k_stage2d_col<REC_MC, FLX_HLLC><<<blocks, 32 * kColWarps, 0, s>>>(a);
+            else if (recon == REC_MC && flux == FLX_RUSANOV) k_stage2d_col<REC_MC, FLX_RUSANOV><<<blocks, 32 * kColWarps, 0, s>>>(a);
+            else return cudaErrorNotSupported;
+            return cudaGetLastError();
+        }
         default: return cudaErrorInvalidValue;
     }
 }
@@ -14,6 +27,12 @@ cudaError_t launch_speed_f32_2d(int variant, int eq, const GridArgs& g, const vo
         case 0: return launch_speed_tile<float, 2, 32, 16, 1, 256>(eq, g, U, part, s);
         case 1: return launch_speed_tile<float, 2, 32, 8, 1, 256>(eq, g, U, part, s);
         case 2: return launch_speed_tile<float, 2, 32, 32, 1, 256>(eq, g, U, part, s);
+        case 3: {
+            if (eq != EQ_EULER) return cudaErrorNotSupported;
+            if (g.total_work <= 0) return cudaSuccess;
+            k_speed2d_col<<<(unsigned)((g.total_work + kColWarps - 1) / kColWarps), 32 * kColWarps, 0, s>>>(g, U, part);
+            return cudaGetLastError();
+        }
         default: return cudaErrorInvalidValue;
     }
 }

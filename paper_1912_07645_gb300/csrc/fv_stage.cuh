@@ -31,28 +31,6 @@ template <class R> __device__ __forceinline__ R speed_dx(R s, R f) {
     else return s * f;
 }
 
-// Row-major walk over an EX x EY x EZ index box in strides of NT: the coordinates of i, i + NT,
-// i + 2 NT, ... by carries instead of a division per step (EX, EY fold to constants).
-struct Walk3 {
-    int x, y, z;
-    __device__ __forceinline__ void init(int i, int EX, int EY) {
-        x = i % EX;
-        const int q = i / EX;
-        y = q % EY;
-        z = q / EY;
-    }
-    __device__ __forceinline__ void step(int NTc, int EX, int EY) {
-        const int ax = NTc % EX, q = NTc / EX, ay = q % EY, az = q / EY;
-        x += ax;
-        const int c = x >= EX ? 1 : 0;
-        x -= c * EX;
-        y += ay + c;
-        const int c2 = y >= EY ? 1 : 0;
-        y -= c2 * EY;
-        z += az + c2;
-    }
-};
-
 template <class R> struct RealTraits;
 template <> struct RealTraits<float> { static __device__ __forceinline__ float nan() { return __int_as_float(0x7fffffff); } };
 template <> struct RealTraits<double> { static __device__ __forceinline__ double nan() { return __longlong_as_double(0x7fffffffffffffffLL); } };
@@ -237,13 +215,11 @@ __global__ void __launch_bounds__(NT) k_stage(const StageArgs p) {
     // (tiles whose halo lies inside the grid skip the ghost mapping; uniform per CTA)
     const bool interior = tx0 >= G && tx0 + SX - G <= nx && (ND < 2 || (ty0 >= G && ty0 + SY - G <= ny)) &&
                           (ND < 3 || (tz0 >= G && tz0 + SZ - G <= nz));
-    Walk3 ws;
-    ws.init(tid, SX, SY);
 #pragma unroll 1
-    for (int s = tid; s < NS; s += NT, ws.step(NT, SX, SY)) {
-        const int sx = ws.x;
-        const int sy = ND >= 2 ? ws.y : 0;
-        const int sz = ND >= 3 ? ws.z : 0;
+    for (int s = tid; s < NS; s += NT) {
+        const int sx = s % SX;
+        const int sy = ND >= 2 ? (s / SX) % SY : 0;
+        const int sz = ND >= 3 ? s / (SX * SY) : 0;
         bool flip[3] = {false, false, false};
         int ix = tx0 + sx - G, iy = ND >= 2 ? ty0 + sy - G : 0, iz = ND >= 3 ? tz0 + sz - G : 0;
         if (!interior) {
@@ -286,13 +262,11 @@ __global__ void __launch_bounds__(NT) k_stage(const StageArgs p) {
         const int NID = EX * EY * EZ;
         const int step = D == 0 ? 1 : (D == 1 ? SX : SX * SY);
         const R eps = g.weno_eps_dx2 ? R(L.dx[D] * L.dx[D]) : R(g.weno_eps);
-        Walk3 wf;
-        wf.init(tid, EX, EY);
 #pragma unroll 1
-        for (int f = tid; f < NID; f += NT, wf.step(NT, EX, EY)) {
-            const int fx = wf.x;
-            const int fy = ND >= 2 ? wf.y : 0;
-            const int fz = ND >= 3 ? wf.z : 0;
+        for (int f = tid; f < NID; f += NT) {
+            const int fx = f % EX;
+            const int fy = ND >= 2 ? (f / EX) % EY : 0;
+            const int fz = ND >= 3 ? f / (EX * EY) : 0;
             // left cell of the interface in tile coordinates = (fx,fy,fz) - e_D; smem offset +G
             int cx = fx + G, cy = ND >= 2 ? fy + G : 0, cz = ND >= 3 ? fz + G : 0;
             if (D == 0) cx -= 1;

@@ -49,7 +49,7 @@ bool variant_ok(const alsv_ctx* c, int v) {
 // Build the per-level tiling for one tile variant.
 long long build_levels(const alsv_ctx* c, int variant, GridArgs& g) {
     TileShape ts = stage_tile(c->fp64, c->ndim, variant);
-    long long work = 0, elem = 0;
+    long long work = 0, elem = 0, pwork = 0;
     int s0 = 0;
     for (int l = 0; l < g.nlev; ++l) {
         LevelInfo& L = g.lev[l];
@@ -65,11 +65,14 @@ long long build_levels(const alsv_ctx* c, int variant, GridArgs& g) {
         L.sample0 = s0;
         L.elem0 = elem;
         L.work0 = work;
+        L.pwork0 = pwork;
+        pwork += (long long)((L.samples + 1) / 2) * L.tiles;
         s0 += L.samples;
         elem += (long long)L.samples * c->nv * L.n[0] * L.n[1] * L.n[2];
         work += (long long)L.samples * L.tiles;
     }
     g.total_work = work;
+    g.total_pwork = pwork;
     return work;
 }
 
@@ -276,18 +279,21 @@ TileShape stage_tile(int fp64, int ndim, int variant) {
         if (variant == 1) return TileShape{32, 8, 1, 256};
         if (variant == 2 && !fp64) return TileShape{32, 32, 1, 256};
         if (variant == 3 && !fp64) return TileShape{31, 1 << 20, 1, 128};  // column strips, whole height
-        return TileShape{32, 16, 1, 256};
+        if (variant == 5 && !fp64) return TileShape{32, 8, 1, 256};        // two-sample tiles
+        return TileShape{32, 16, 1, 256};                                   // variants 0 and 4
     }
     if (fp64) return variant == 1 ? TileShape{8, 8, 4, 256} : TileShape{8, 8, 8, 256};
     return variant == 1 ? TileShape{8, 8, 8, 256} : TileShape{16, 8, 8, 256};
 }
 int stage_num_variants(int fp64, int ndim) {
     if (ndim == 1) return 1;
-    if (ndim == 2 && !fp64) return 4;
+    if (ndim == 2 && !fp64) return 6;
     return 2;
 }
 bool stage_variant_supported(int fp64, int ndim, int eq, int recon, int rvars, int flux, const int bc[3][2], int variant) {
     if (variant < 0 || variant >= stage_num_variants(fp64, ndim)) return false;
+    if (ndim == 2 && !fp64 && (variant == 4 || variant == 5))
+        return eq == EQ_EULER && rvars == RV_PRIM && (flux == FLX_HLLC || flux == FLX_RUSANOV);
     if (!(ndim == 2 && !fp64 && variant == 3)) return true;
     const bool periodic = bc[0][0] == BC_PERIODIC && bc[0][1] == BC_PERIODIC && bc[1][0] == BC_PERIODIC &&
                           bc[1][1] == BC_PERIODIC;

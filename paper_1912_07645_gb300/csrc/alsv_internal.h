@@ -50,6 +50,7 @@ struct LevelInfo {
     FastDiv fd_tiles;  // divisors for the (sample, tile) decomposition of a work item
     FastDiv fd_nt0;    // tiles along x
     FastDiv fd_nt1;    // tiles along y
+    long long pwork0;  // first (sample pair, tile) work item of the level (two-sample schedule)
 };
 
 struct GridArgs {
@@ -58,6 +59,7 @@ struct GridArgs {
     int nlev;
     LevelInfo lev[kMaxLevels];
     long long total_work;  // sum over levels of samples * tiles
+    long long total_pwork; // sum over levels of ceil(samples / 2) * tiles
     int total_samples;
     int nv;
     double gamma;

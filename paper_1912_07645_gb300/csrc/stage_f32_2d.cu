@@ -1,7 +1,40 @@
 // Stage and speed kernels for float, 2D (explicit tile-shape variants).
 #include "fv_colmarch.cuh"
+#include "fv_pair.cuh"
 #include "stage_dispatch.cuh"
 namespace alsv {
+template <int RECON, int FLUX, int TX, int TY, int NT>
+static cudaError_t launch_pair_one(const StageArgs& a, cudaStream_t s) {
+    auto k = k_stage2d_pair<RECON, FLUX, TX, TY, NT>;
+    constexpr size_t sm = pair_smem_bytes<RECON, TX, TY>();
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    if (a.g.total_pwork <= 0) return cudaSuccess;
+    k<<<(unsigned)a.g.total_pwork, NT, sm, s>>>(a);
+    return cudaGetLastError();
+}
+
+// two-sample schedule (FP32 2D Euler, primitive reconstruction, HLLC or Rusanov)
+template <int TX, int TY, int NT>
+static cudaError_t launch_pair(int recon, int flux, int eq, const StageArgs& a, cudaStream_t s) {
+    if (eq != EQ_EULER || a.g.rvars != RV_PRIM) return cudaErrorNotSupported;
+    if (flux == FLX_HLLC) {
+        if (recon == REC_WENO3) return launch_pair_one<REC_WENO3, FLX_HLLC, TX, TY, NT>(a, s);
+        if (recon == REC_MC) return launch_pair_one<REC_MC, FLX_HLLC, TX, TY, NT>(a, s);
+        return launch_pair_one<REC_PC, FLX_HLLC, TX, TY, NT>(a, s);
+    }
+    if (flux == FLX_RUSANOV) {
+        if (recon == REC_WENO3) return launch_pair_one<REC_WENO3, FLX_RUSANOV, TX, TY, NT>(a, s);
+        if (recon == REC_MC) return launch_pair_one<REC_MC, FLX_RUSANOV, TX, TY, NT>(a, s);
+        return launch_pair_one<REC_PC, FLX_RUSANOV, TX, TY, NT>(a, s);
+    }
+    return cudaErrorNotSupported;
+}
+
 cudaError_t launch_stage_f32_2d(int variant, int eq, int recon, int flux, const StageArgs& a, cudaStream_t s) {
     switch (variant) {
         case 0: return launch_stage_tile<float, 2, 32, 16, 1, 256>(eq, recon, flux, a, s);
@@ -19,6 +52,8 @@ cudaError_t launch_stage_f32_2d(int variant, int eq, int recon, int flux, const 
             else return cudaErrorNotSupported;
             return cudaGetLastError();
         }
+        case 4: return launch_pair<32, 16, 256>(recon, flux, eq, a, s);
+        case 5: return launch_pair<32, 8, 256>(recon, flux, eq, a, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -33,6 +68,8 @@ cudaError_t launch_speed_f32_2d(int variant, int eq, const GridArgs& g, const vo
             k_speed2d_col<<<(unsigned)((g.total_work + kColWarps - 1) / kColWarps), 32 * kColWarps, 0, s>>>(g, U, part);
             return cudaGetLastError();
         }
+        case 4: return launch_speed_tile<float, 2, 32, 16, 1, 256>(eq, g, U, part, s);
+        case 5: return launch_speed_tile<float, 2, 32, 8, 1, 256>(eq, g, U, part, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -539,3 +539,72 @@ def test_column_variant_mlmc_levels_and_rejection():
     with pytest.raises(alsv.AlsvError, match="variant"):
         alsv.alsv_set_tile_variant(S2.ctx, 3)
     S2.close()
+
+
+@pytest.mark.parametrize("variant", [4, 5])
+@pytest.mark.parametrize("recon,flux,bc", [("weno3", "hllc", "periodic"), ("mc", "rusanov", "periodic"),
+                                           ("pc", "hllc", [("outflow", "reflective"), ("reflective", "outflow")]),
+                                           ("weno3", "rusanov", "reflective")])
+def test_pair_variant_fp32_vs_oracle(variant, recon, flux, bc):
+    """Two-sample schedules (variants 4, 5): each sample within 2e-5 relative L1 of the oracle,
+    with an odd batch (the last sample has no partner), ragged tiles and boundary fill."""
+    torch = torch_()
+    import paper_1912_07645_gb300 as alsv
+    cfg = dict(ndim=2, n=(70, 45), batch=3, eq="euler", recon=recon, flux=flux, rvars="prim", rk="ssprk3", bc=bc,
+               cfl=0.4, precision="fp32")
+    U0 = euler_state(3, 2, (70, 45), seed=71)
+    S = gpu_solver(**cfg)
+    alsv.alsv_set_tile_variant(S.ctx, variant)
+    S.set_state(torch.from_numpy(U0))
+    S.step(10)
+    S.sync()
+    g = host(S.U).reshape(S.level_shape(0))
+    S.close()
+    o, *_ = run_oracle(cfg, U0=U0, steps=10)
+    for b in range(3):
+        p2_check(g[b:b + 1], o[b:b + 1], what=f"pair v{variant} {recon} {flux} sample {b}")
+
+
+def test_pair_variant_samples_finishing_at_different_steps():
+    """Samples of one pair reach T after different step counts: the finished lane must stay
+    untouched while its partner continues."""
+    torch = torch_()
+    import paper_1912_07645_gb300 as alsv
+    cfg = dict(ndim=2, n=(48, 40), batch=5, eq="euler", recon="weno3", flux="hllc", rvars="prim", rk="ssprk3",
+               bc="periodic", cfl=0.4, precision="fp32")
+    U0 = euler_state(5, 2, (48, 40), seed=72)
+    U0[1, 3] *= 1.6          # hotter sample: larger sound speed, more steps to the same T
+    S = gpu_solver(**cfg)
+    alsv.alsv_set_tile_variant(S.ctx, 4)
+    S.set_state(torch.from_numpy(U0))
+    S.evolve_to(0.04)
+    g = host(S.U).reshape(S.level_shape(0))
+    t, st = S.time()
+    S.close()
+    o, ost, ot = run_oracle(cfg, U0=U0, T=0.04)
+    assert len(set(ost.tolist())) > 1            # the pairs really finish at different steps
+    assert np.array_equal(st, ost) and np.all(t == 0.04)
+    for b in range(5):
+        p2_check(g[b:b + 1], o[b:b + 1], what=f"pair finish sample {b}")
+
+
+def test_pair_variant_mlmc_levels_odd_counts():
+    torch = torch_()
+    import paper_1912_07645_gb300 as alsv
+    lv = [((32, 32), 3), ((64, 48), 1), ((40, 40), 4)]
+    cfg = dict(ndim=2, levels=lv, eq="euler", recon="weno3", flux="hllc", rvars="prim", rk="ssprk3",
+               bc="periodic", cfl=0.4, precision="fp32", seed=9)
+    S = gpu_solver(**cfg)
+    alsv.alsv_set_tile_variant(S.ctx, 4)
+    S.set_initial_data("kh")
+    S.step(3)
+    S.sync()
+    th_all = oracle.theta_splitmix(9, 8, 20)
+    s0 = 0
+    for l, (n, B) in enumerate(lv):
+        ocfg = dict(cfg, n=n, batch=B)
+        ocfg.pop("levels")
+        o, *_ = run_oracle(ocfg, "kh", th_all[s0:s0 + B], steps=3)
+        p2_check(host(S.state(l)), o, what=f"pair level {l}")
+        s0 += B
+    S.close()

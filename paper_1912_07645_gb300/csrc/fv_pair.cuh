@@ -3,7 +3,8 @@
 // samples of the batch advanced together by every thread. Lane .x of each packed FP32x2 value is
 // sample A, lane .y sample B, so every arithmetic instruction serves both samples and all index
 // and address arithmetic is shared. Shared memory interleaves the pair: one cell is two float4,
-// (rho_A, rho_B, u_A, u_B) and (v_A, v_B, p_A, p_B), which load straight into register pairs.
+// (rho_A, rho_B, u_A, u_B) and (v_A, v_B, p_A, p_B), which load straight into register pairs; the
+// two halves live in separate arrays so neighbouring cells are 16 bytes apart (conflict-free).
 // Tile structure as k_stage: halo load with boundary fill, per-direction interface fluxes in shared
 // memory (each evaluated once), divergence in registers, RK combination, CFL partials per sample.
 #pragma once
@@ -22,7 +23,7 @@ constexpr size_t pair_smem_bytes() {
 }
 
 template <int RECON, int FLUX, int TX, int TY, int NT>
-__global__ void __launch_bounds__(NT) k_stage2d_pair(const StageArgs p) {
+__global__ void __launch_bounds__(NT, 5) k_stage2d_pair(const StageArgs p) {
     constexpr int G = RECON == REC_PC ? 1 : 2;
     constexpr int SX = TX + 2 * G, SY = TY + 2 * G, NS = SX * SY;
     constexpr int NIX = (TX + 1) * TY, NIY = TX * (TY + 1);
@@ -31,8 +32,10 @@ __global__ void __launch_bounds__(NT) k_stage2d_pair(const StageArgs p) {
     static_assert(CELLS % NT == 0, "tile cells must be a multiple of the CTA size");
     constexpr int CPT = CELLS / NT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float4* sW = reinterpret_cast<float4*>(smem_raw);  // [NS][2]
-    float4* sF = sW + 2 * NS;                           // [NI][2]
+    float4* sW0 = reinterpret_cast<float4*>(smem_raw);  // [NS] (rho, u) of both samples
+    float4* sW1 = sW0 + NS;                              // [NS] (v, p)
+    float4* sF0 = sW1 + NS;                              // [NI] (mass, x-momentum) fluxes
+    float4* sF1 = sF0 + NI;                              // [NI] (y-momentum, energy)
 
     const GridArgs& g = p.g;
     const uint32_t w = blockIdx.x;
@@ -84,8 +87,8 @@ __global__ void __launch_bounds__(NT) k_stage2d_pair(const StageArgs p) {
         const float2 u = mul2(mx, inv), v = mul2(my, inv);
         const float2 m2 = fma2(mx, mx, mul2(my, my));
         const float2 pr = mul2(f2(gm1), fma2(mul2(f2(-0.5f), m2), inv, E));
-        sW[2 * s] = make_float4(r.x, r.y, u.x, u.y);
-        sW[2 * s + 1] = make_float4(v.x, v.y, pr.x, pr.y);
+        sW0[s] = make_float4(r.x, r.y, u.x, u.y);
+        sW1[s] = make_float4(v.x, v.y, pr.x, pr.y);
     }
 
     float2 acc[CPT][4];
@@ -112,7 +115,7 @@ __global__ void __launch_bounds__(NT) k_stage2d_pair(const StageArgs p) {
 #pragma unroll
             for (int k = (G == 1 ? 1 : 0); k < (G == 1 ? 3 : 4); ++k) {
                 const int idx = i0 + (k - 1) * step;
-                const float4 a = sW[2 * idx], b = sW[2 * idx + 1];
+                const float4 a = sW0[idx], b = sW1[idx];
                 Rk[k] = make_float2(a.x, a.y);
                 Uk[k] = make_float2(a.z, a.w);
                 Vk[k] = make_float2(b.x, b.y);
@@ -149,8 +152,8 @@ __global__ void __launch_bounds__(NT) k_stage2d_pair(const StageArgs p) {
             }
             const F2x4 F = FLUX == FLX_HLLC ? hllc2(WL, WR, gamma, inv_gm1) : rusanov2(WL, WR, gamma, inv_gm1);
             const float2 fxm = D == 0 ? F.n : F.t, fym = D == 0 ? F.t : F.n;
-            sF[2 * f] = make_float4(F.r.x, F.r.y, fxm.x, fxm.y);
-            sF[2 * f + 1] = make_float4(fym.x, fym.y, F.p.x, F.p.y);
+            sF0[f] = make_float4(F.r.x, F.r.y, fxm.x, fxm.y);
+            sF1[f] = make_float4(fym.x, fym.y, F.p.x, F.p.y);
         }
         __syncthreads();
         const float2 nidx = f2(-(float)L.inv_dx[D]);
@@ -160,8 +163,8 @@ __global__ void __launch_bounds__(NT) k_stage2d_pair(const StageArgs p) {
             const int c = tid + m * NT;
             const int x = c % TX, y = c / TX;
             const int fidx = y * EX + x;
-            const float4 am = sF[2 * fidx], bm = sF[2 * fidx + 1];
-            const float4 ap = sF[2 * (fidx + fstep)], bp = sF[2 * (fidx + fstep) + 1];
+            const float4 am = sF0[fidx], bm = sF1[fidx];
+            const float4 ap = sF0[fidx + fstep], bp = sF1[fidx + fstep];
             acc[m][0] = fma2(sub2(make_float2(ap.x, ap.y), make_float2(am.x, am.y)), nidx, acc[m][0]);
             acc[m][1] = fma2(sub2(make_float2(ap.z, ap.w), make_float2(am.z, am.w)), nidx, acc[m][1]);
             acc[m][2] = fma2(sub2(make_float2(bp.x, bp.y), make_float2(bm.x, bm.y)), nidx, acc[m][2]);

@@ -151,6 +151,29 @@ def plain_fp64_loop(alsv, torch, steps_per_sample, T_short=0.066):
             "fp32_batched_vs_fp64_rel_l1": rel}
 
 
+def stage_traffic(variant, cell_updates, launches):
+    """DRAM bytes per stage launch from the committed ncu summary, scaled from its per-cell-update
+    figure; None once the kernel sources no longer match the profiled ones or another schedule
+    was chosen."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "stage_traffic.txt")
+    if not os.path.exists(path) or launches <= 0:
+        return None, None
+    rec = {}
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            k, v = line.split()
+            rec[k] = v
+    csrc = os.path.join(ROOT, "paper_1912_07645_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in ("fv_pair.cuh", "fv_packed.cuh", "fv_physics.cuh"):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    if h.hexdigest()[:16] != rec.get("sources_sha256_prefix") or str(variant) != rec.get("variant"):
+        return None, None
+    pcu = float(rec["bytes_per_cell_update"])
+    return pcu * cell_updates / launches, pcu
+
+
 def cpu_baseline_oracle(budget_s=15.0):
     """Time the FP64 oracle as it stands on this host's cores on a bounded sample of the same
     workload (one sample of the batch, as many CFL steps as fit in the budget)."""
@@ -199,6 +222,126 @@ def reference_arm(args):
     return 0
 
 
+# ------------------------------------------------------------------------------------------------
+# Other configurations (SURVEY configs 1, 2, 3-MLMC, 4, 5): same JSON contract, one GPU.
+# bytes per cell-update: per variable read U^n + write U1 (stage 1), read U^(s) + U^n + write (later
+# stages): RK2 = 5 words, RK3 = 8 words.
+WORKLOADS = {
+    "sod1024_fp64": dict(desc=dict(ndim=1, n=(1024,), batch=1, eq="euler", recon="mc", flux="hllc", rvars="prim",
+                                   rk="ssprk2", bc="outflow", cfl=0.45, precision="fp64"), init="sod", T=0.2,
+                         words=5, nv=3, esize=8),
+    "kh2d1024_fp32": dict(desc=dict(ndim=2, n=(1024, 1024), batch=1, eq="euler", recon="weno3", flux="hllc",
+                                    rvars="prim", rk="ssprk3", bc="periodic", cfl=0.4, precision="fp32", seed=0),
+                          init="kh", T=2.0, words=8, nv=4, esize=4),
+    "kh2d1024_fp64": dict(desc=dict(ndim=2, n=(1024, 1024), batch=1, eq="euler", recon="weno3", flux="hllc",
+                                    rvars="prim", rk="ssprk3", bc="periodic", cfl=0.4, precision="fp64", seed=0),
+                          init="kh", T=0.02, words=8, nv=4, esize=8),
+    "mlmc_fp32": dict(desc=dict(ndim=2, levels=[((64, 64), 4096), ((128, 128), 1024), ((256, 256), 256),
+                                                ((512, 512), 64)], eq="euler", recon="weno3", flux="hllc",
+                                rvars="prim", rk="ssprk3", bc="periodic", cfl=0.4, precision="fp32", seed=SEED),
+                      init="kh", T=1.0, words=8, nv=4, esize=4),
+    "kh3d512_fp32": dict(desc=dict(ndim=3, n=(512, 512, 512), batch=1, eq="euler", recon="weno3", flux="hllc",
+                                   rvars="prim", rk="ssprk3", bc="periodic", cfl=0.3, precision="fp32", seed=0),
+                         init="kh", steps=100, words=8, nv=5, esize=4),
+    "adjoint512_fp32": dict(desc=dict(ndim=2, n=(512, 512), batch=64, eq="euler", recon="mc", flux="rusanov",
+                                      rvars="prim", rk="ssprk2", bc="periodic", cfl=0.4, precision="fp32", seed=SEED),
+                            adjoint=True, T=1.0),
+    "adjoint512_fp64": dict(desc=dict(ndim=2, n=(512, 512), batch=64, eq="euler", recon="mc", flux="rusanov",
+                                      rvars="prim", rk="ssprk2", bc="periodic", cfl=0.4, precision="fp64", seed=SEED),
+                            adjoint=True, T=0.05),
+}
+
+
+def run_workload(name, args):
+    import numpy as np
+    import torch
+    from paper_1912_07645_gb300 import build
+    build.build()
+    import paper_1912_07645_gb300 as alsv
+    W = WORKLOADS[name]
+    desc = alsv.make_desc(**W["desc"])
+    S = alsv.Solver(desc)
+    peaks, peak_kind = measured_peaks()
+    if W.get("adjoint"):
+        S.set_initial_data("kh")
+        th = torch.empty((S.samples, 20), dtype=torch.float64, device="cuda")
+        alsv.alsv_get_parameters(S.ctx, th)
+        S.sync()
+        for _ in range(args.warmup):
+            S.adjoint(th, min(W["T"], 0.01))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            J, g = S.adjoint(th, W["T"])
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        nst = int(math.ceil(W["T"] * (0.5 + math.sqrt(1.4 * 2.5)) / (0.4 / 512)))
+        grads = S.samples * args.steps / el
+        line = {"metric": "adjoint gradients/s (KE at T w.r.t. 20 KH parameters)", "value": grads,
+                "unit": "gradients/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1000 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": W["desc"]["precision"], "data": "synthetic (SplitMix64 KH parameters)",
+                "config": {"workload": name, "grid": [512, 512], "samples": S.samples, "T": W["T"],
+                           "fixed_steps": nst, "checkpoints": int(math.ceil(math.sqrt(nst)))},
+                "forward_cell_updates_per_s": S.samples * 512 * 512 * nst * args.steps / el,
+                "gpu_launches": alsv.alsv_get_launch_count(S.ctx)}
+        print(json.dumps(line), flush=True)
+        S.close()
+        return 0
+    chosen, ms_var = (0, [])
+    S.set_initial_data(W["init"])
+    if alsv.alsv_num_tile_variants(S.ctx) > 1:
+        chosen, ms_var = alsv.alsv_autotune(S.ctx, 3)
+    cells = [int(np.prod(desc.level_n[l][:desc.ndim])) for l in range(desc.n_levels)] if desc.n_levels > 1 else \
+        [int(np.prod(list(desc.n)[:desc.ndim]))]
+
+    def one():
+        S.set_initial_data(W["init"])
+        if "steps" in W:
+            S.step(W["steps"])
+            S.sync()
+        else:
+            S.evolve_to(W["T"])
+        _, ns = S.time()
+        if desc.n_levels > 1:
+            cu, s0 = 0, 0
+            for l in range(desc.n_levels):
+                B = desc.level_batch[l]
+                cu += int(ns[s0:s0 + B].sum()) * cells[l]
+                s0 += B
+            return cu
+        return int(ns.sum()) * cells[0]
+
+    for _ in range(args.warmup):
+        one()
+    alsv.alsv_set_profiling(S.ctx, True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    cu = 0
+    for _ in range(args.steps):
+        cu += one()
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    prof = alsv.alsv_get_profile(S.ctx)
+    alsv.alsv_set_profiling(S.ctx, False)
+    bpc = W["words"] * W["nv"] * W["esize"]
+    achieved = cu * bpc / (prof["stage_ms"] / 1000.0) / 1e9 if prof["stage_ms"] > 0 else None
+    line = {"metric": METRIC, "value": cu / el, "unit": "cell-updates/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": W["desc"]["precision"], "data": "synthetic",
+            "config": {"workload": name, "T": W.get("T"), "fixed_steps": W.get("steps"), "samples": S.samples,
+                       "tile_variant": chosen, "autotune_ms": ms_var},
+            "samples_per_s": S.samples * args.steps / el,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": achieved / peaks["hbm_gbs"] if achieved else None, "peak_kind": peak_kind,
+                         "algorithmic_bytes_per_cell_update": bpc, "stage_ms_total": prof["stage_ms"],
+                         "stage_launches": prof["stage_launches"], "step_ms_total": 1000 * el},
+            "gpu_launches": alsv.alsv_get_launch_count(S.ctx)}
+    print(json.dumps(line), flush=True)
+    S.close()
+    return 0
+
+
 def main():
     global T_END
     ap = argparse.ArgumentParser()
@@ -209,10 +352,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--samples", type=int, default=M, help="samples per GPU (default 4096; fewer for profiling runs)")
     ap.add_argument("--T", type=float, default=T_END, help="end time (default 1; shorter for profiling runs)")
+    ap.add_argument("--workload", default="mc", choices=["mc"] + sorted(WORKLOADS),
+                    help="mc (default): batched Monte Carlo KH 256^2 x 4096; others: the remaining configurations")
     args = ap.parse_args()
     T_END = args.T
     if args.impl == "reference":
         return reference_arm(args)
+    if args.workload != "mc":
+        return run_workload(args.workload, args)
 
     import torch
     import torch.distributed as dist
@@ -316,18 +463,16 @@ def main():
         peaks, peak_kind = measured_peaks()
         stage_bytes = cell_updates * BYTES_PER_CELL_UPDATE
         achieved = stage_bytes / (prof["stage_ms"] / 1000.0) / 1e9 if prof["stage_ms"] > 0 else None
-        traffic = None
-        tp = os.path.join(ROOT, "profiles", "stage_traffic.json")
-        if os.path.exists(tp):
-            with open(tp) as f:
-                traffic = json.load(f).get("bytes_per_cell_stage_launch")
+        traffic, traffic_pcu = stage_traffic(chosen, cell_updates, prof["stage_launches"])
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": (achieved / peaks["hbm_gbs"]) if achieved else None, "peak_kind": peak_kind,
                 "kernel": "k_stage<float, Euler, 2D, WENO3, HLLC>",
                 "algorithmic_bytes_per_cell_update": BYTES_PER_CELL_UPDATE,
                 "stage_ms_total": prof["stage_ms"], "stage_launches": prof["stage_launches"],
                 "stage_share_of_step": prof["stage_ms"] / ms if ms > 0 else None,
-                "traffic": traffic}
+                "traffic": traffic, "traffic_bytes_per_cell_update": traffic_pcu,
+                "traffic_source": "profiles/k_stage2d_pair_f32_weno3_hllc_kh256.md (256-sample capture, per "
+                                  "cell-update, scaled to this run's cell-updates per stage launch)"}
         line = {"metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "fp32 (stencil); fp64 (statistics, totals, time)",

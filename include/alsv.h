@@ -267,9 +267,10 @@ alsv_status alsv_destroy(alsv_ctx* ctx);
  *   alsv_set_tile_variant   select one (recomputes the wave-speed partials; asynchronous;
  *                           ALSV_ERR_INVALID_ARG if the variant does not support the scheme)
  *   alsv_get_tile           current tile shape, variant and (sample, tile) work items per launch
- *   alsv_autotune           time `reps` launches of the first stage (reads U, writes the stage
- *                           buffer only, so the state is unchanged) per variant with CUDA events
- *                           on the context stream and keep the fastest; ms_per_variant (host, may
+ *   alsv_autotune           time `reps` pairs of launches per variant - a first stage and a
+ *                           last-stage-like launch (U^n read, CFL partials), both writing only the
+ *                           stage buffer, so the state is unchanged - with CUDA events on the
+ *                           context stream and keep the fastest; ms_per_variant (host, may
  *                           be NULL) receives the times (-1 for unsupported variants). SYNCHRONOUS.
  *   alsv_set_graphs         1 (default): alsv_evolve_to_T replays captured CUDA graphs of
  *                           16-step chunks; 0: direct launches

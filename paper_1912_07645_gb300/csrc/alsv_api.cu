@@ -763,17 +763,22 @@ alsv_status alsv_autotune(alsv_ctx* c, int reps, int* chosen, float* ms_per_vari
         const int saved = c->variant;
         c->variant = v;
         build_levels(c, v, c->g);
-        // the timed launch is stage 1 (reads U, writes the stage buffer A): the state is unchanged
+        // timed: a first-stage launch (reads U, writes the stage buffer A) and a last-stage-like
+        // launch (also reads U^n point-wise and forms the CFL partials), both writing only scratch,
+        // so the state is unchanged; the partials are recomputed below
         StageArgs a = stage_args(c, c->U, nullptr, c->A, 0.0, 1.0, false);
+        StageArgs a3 = stage_args(c, c->U, c->U, c->A, 1.0 / 3.0, 2.0 / 3.0, true);
         cudaError_t e = launch_stage(c->fp64, c->ndim, c->eq, c->d.recon, c->d.flux, v, a, c->stream);
         if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
-        for (int r = 0; r < reps && e == cudaSuccess; ++r)
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) {
             e = launch_stage(c->fp64, c->ndim, c->eq, c->d.recon, c->d.flux, v, a, c->stream);
+            if (e == cudaSuccess) e = launch_stage(c->fp64, c->ndim, c->eq, c->d.recon, c->d.flux, v, a3, c->stream);
+        }
         if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         float ms = 0.f;
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-        c->launches += reps + 1;
+        c->launches += 2 * reps + 1;
         c->variant = saved;
         c->g = g;
         if (e != cudaSuccess) {
@@ -788,7 +793,13 @@ alsv_status alsv_autotune(alsv_ctx* c, int reps, int* chosen, float* ms_per_vari
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (chosen) *chosen = best;
-    return alsv_set_tile_variant(c, best);
+    st = alsv_set_tile_variant(c, best);
+    if (st != ALSV_OK) return st;
+    // partials of the current state for the chosen tiling (the timing launches overwrote them)
+    cudaError_t e = launch_speed(c->fp64, c->ndim, c->eq, c->variant, c->g, c->U, c->part, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "speed kernel launch");
+    c->launches++;
+    return ALSV_OK;
 }
 
 alsv_status alsv_get_launch_count(const alsv_ctx* c, int64_t* launches) {

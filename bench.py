@@ -240,6 +240,12 @@ WORKLOADS = {
                                                 ((512, 512), 64)], eq="euler", recon="weno3", flux="hllc",
                                 rvars="prim", rk="ssprk3", bc="periodic", cfl=0.4, precision="fp32", seed=SEED),
                       init="kh", T=1.0, words=8, nv=4, esize=4),
+    "mlmc_coupled_fp32": dict(desc=dict(ndim=2, levels=[((64, 64), 4096), ((128, 128), 1024), ((64, 64), 1024, 1),
+                                                        ((256, 256), 256), ((128, 128), 256, 3), ((512, 512), 64),
+                                                        ((256, 256), 64, 5)], eq="euler", recon="weno3",
+                                        flux="hllc", rvars="prim", rk="ssprk3", bc="periodic", cfl=0.4,
+                                        precision="fp32", seed=SEED),
+                              init="kh", T=1.0, words=8, nv=4, esize=4, mlmc=True),
     "kh3d512_fp32": dict(desc=dict(ndim=3, n=(512, 512, 512), batch=1, eq="euler", recon="weno3", flux="hllc",
                                    rvars="prim", rk="ssprk3", bc="periodic", cfl=0.3, precision="fp32", seed=0),
                          init="kh", steps=100, words=8, nv=5, esize=4),
@@ -275,14 +281,14 @@ def run_workload(name, args):
             J, g = S.adjoint(th, W["T"])
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
-        nst = int(math.ceil(W["T"] * (0.5 + math.sqrt(1.4 * 2.5)) / (0.4 / 512)))
+        nst, dt_fixed, passes = alsv.alsv_adjoint_get_plan(S.ctx)
         grads = S.samples * args.steps / el
         line = {"metric": "adjoint gradients/s (KE at T w.r.t. 20 KH parameters)", "value": grads,
                 "unit": "gradients/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": 1000 * el / args.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": W["desc"]["precision"], "data": "synthetic (SplitMix64 KH parameters)",
                 "config": {"workload": name, "grid": [512, 512], "samples": S.samples, "T": W["T"],
-                           "fixed_steps": nst, "checkpoints": int(math.ceil(math.sqrt(nst)))},
+                           "fixed_steps": nst, "fixed_dt": dt_fixed, "forward_passes": passes},
                 "forward_cell_updates_per_s": S.samples * 512 * 512 * nst * args.steps / el,
                 "gpu_launches": alsv.alsv_get_launch_count(S.ctx)}
         print(json.dumps(line), flush=True)
@@ -295,6 +301,8 @@ def run_workload(name, args):
     cells = [int(np.prod(desc.level_n[l][:desc.ndim])) for l in range(desc.n_levels)] if desc.n_levels > 1 else \
         [int(np.prod(list(desc.n)[:desc.ndim]))]
 
+    est = {}
+
     def one():
         S.set_initial_data(W["init"])
         if "steps" in W:
@@ -302,6 +310,11 @@ def run_workload(name, args):
             S.sync()
         else:
             S.evolve_to(W["T"])
+        if W.get("mlmc"):
+            S.mlmc_init()
+            S.mlmc_accumulate()
+            est["counts"], _, _, lev = S.mlmc_read()
+            est["level_sums"] = lev.cpu().numpy()
         _, ns = S.time()
         if desc.n_levels > 1:
             cu, s0 = 0, 0
@@ -337,6 +350,19 @@ def run_workload(name, args):
                          "algorithmic_bytes_per_cell_update": bpc, "stage_ms_total": prof["stage_ms"],
                          "stage_launches": prof["stage_launches"], "step_ms_total": 1000 * el},
             "gpu_launches": alsv.alsv_get_launch_count(S.ctx)}
+    if W.get("mlmc"):
+        # per level: samples, grid, mean steps per sample of the pair, and for rho the integrals of
+        # the mean correction |E[Y_l]| and of its variance Var[Y_l] (the variance decay)
+        _, ns = S.time()
+        lv = S.mlmc_levels()
+        rows = []
+        for k, l in enumerate(lv):
+            s0 = sum(desc.level_batch[j] for j in range(l))
+            rows.append({"level": k, "grid": list(desc.level_n[l])[:2], "samples": est["counts"][k],
+                         "steps_per_sample": float(ns[s0:s0 + desc.level_batch[l]].mean()),
+                         "rho_abs_mean_correction": float(est["level_sums"][k, 0, 1]),
+                         "rho_var_correction": float(est["level_sums"][k, 0, 2])})
+        line["mlmc_levels"] = rows
     print(json.dumps(line), flush=True)
     S.close()
     return 0

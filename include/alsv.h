@@ -63,6 +63,15 @@ enum {
     ALSV_INIT_RAW = 5           /* U_dev already holds the initial state */
 };
 enum { ALSV_OBS_KINETIC_ENERGY = 0 };
+/* Sampling of the KH parameters theta_{b,j} (Sec. 2.2: Monte Carlo or Quasi Monte Carlo), from the
+ * sample's global counter index g (sample_offset + b, or its level's index for an MLMC companion),
+ * hi_j = 1 for amplitudes (first half of theta) and 2 pi for phases:
+ *   MC              hi_j (splitmix64(seed ^ (g P + j)) >> 11) 2^-53
+ *   HALTON          hi_j phi_{p_j}(g + 1): radical inverse of g + 1 in base p_j, the (j+1)-th prime,
+ *                   evaluated as an integer fraction num / p_j^K (exact) and one FP64 division
+ *   HALTON_SHIFTED  hi_j frac(phi_{p_j}(g + 1) + s_j), s_j = (splitmix64(seed ^ (2^63 + j)) >> 11)
+ *                   2^-53 (a Cranley-Patterson rotation; one shift per run and parameter) */
+enum { ALSV_SAMPLER_MC = 0, ALSV_SAMPLER_HALTON = 1, ALSV_SAMPLER_HALTON_SHIFTED = 2 };
 
 #define ALSV_MAX_LEVELS 8
 
@@ -92,7 +101,15 @@ typedef struct alsv_grid_desc {
     int64_t sample_offset; /* global index of this context's first sample: counter-based KH
                               parameters of local sample b use global index sample_offset + b
                               (shards of one Monte Carlo ensemble across GPUs) */
-    int32_t reserved[6];   /* must be zero */
+    int32_t level_fine[ALSV_MAX_LEVELS];
+                           /* MLMC coupling (n_levels >= 2): 0 = group l of the level table is a
+                              level of the estimator; j > 0 = group l is the coarse companion of
+                              group j - 1: same batch, and its sample b takes the KH parameters of
+                              group j - 1's sample b (the counter index of that sample); its grid
+                              must divide group j - 1's grid, which must be a level. At most one
+                              companion per level. */
+    int32_t sampler;       /* ALSV_SAMPLER_* for counter-generated KH parameters (default MC) */
+    int32_t reserved[5];   /* must be zero */
 } alsv_grid_desc;
 
 typedef struct alsv_ctx alsv_ctx;
@@ -240,20 +257,91 @@ alsv_status alsv_kinetic_energy(alsv_ctx* ctx, double* ke_dev);
 /*
  * Discrete adjoint (not in the paper; gradient of an observable at time T with respect to the
  * KH parameters). Fixed step dt = T / n with n = ceil(T s_max / (cfl dx)), s_max the fastest
- * signal of the two unperturbed KH states; ceil(sqrt(n)) checkpoints with recomputation.
- *   alsv_adjoint_workspace_bytes  device bytes the adjoint needs for T (checkpoints + adjoint
- *                                 state + segment buffers)
- *   alsv_bind_adjoint_workspace   bind it (caller-owned)
+ * signal of the two unperturbed KH states; checkpoints every ceil(sqrt(n_cap)) steps with
+ * recomputation, n_cap = ceil(1.5 n). When the flow speeds up so far that the realised CFL number
+ * dt (|u_k| + c)/dx_k of some step exceeds 0.5, the forward sweep is repeated with
+ * n = ceil(T s_seen / cfl), s_seen the fastest signal of the previous pass (at most 3 passes,
+ * n <= n_cap); all samples of the batch share n.
+ *   alsv_adjoint_workspace_bytes  device bytes the adjoint needs for T (checkpoints for n_cap
+ *                                 steps + segment buffers + adjoint states)
+ *   alsv_bind_adjoint_workspace   bind it (caller-owned, 256-byte aligned)
  *   alsv_adjoint_evolve           initial data from theta_dev (FP64 [samples][20]), forward with
  *                                 checkpoints, reverse sweep; writes J_dev[samples] and
  *                                 grad_theta_dev[samples][20] (FP64). SYNCHRONOUS. Supported:
  *                                 2D Euler KH, periodic, PC or MC reconstruction, Rusanov flux,
- *                                 SSP-RK2 or RK3. ALSV_ERR_CFL when the realised CFL exceeds 0.5.
+ *                                 SSP-RK2 or RK3. ALSV_ERR_CFL when re-planning cannot bring the
+ *                                 realised CFL under 0.5 within n_cap steps or 3 passes.
+ *   alsv_adjoint_get_plan         the last successful alsv_adjoint_evolve's step count n, step dt
+ *                                 and number of forward passes (host outputs);
+ *                                 ALSV_ERR_NOT_READY before one.
  */
 alsv_status alsv_adjoint_workspace_bytes(alsv_ctx* ctx, double T, size_t* bytes);
 alsv_status alsv_bind_adjoint_workspace(alsv_ctx* ctx, void* dev, size_t bytes);
 alsv_status alsv_adjoint_evolve(alsv_ctx* ctx, double T, int observable, const double* theta_dev,
                                 double* grad_theta_dev, double* J_dev);
+alsv_status alsv_adjoint_get_plan(alsv_ctx* ctx, int64_t* n_steps, double* dt, int32_t* passes);
+
+/*
+ * Multilevel Monte Carlo estimator (Sec. 2.2, the multilevel sum of the sampling display):
+ *   E[G(u)] ~ sum_l (1/M_l) sum_k (G(u^l_k) - G(u^{l-1}_k)),   G(u^{-1}) = 0,
+ * for G(u) = q and G(u) = q^2, q the primitive variables (rho, u_k, p) (Burgers: u) per cell.
+ * The levels l are the level-table groups with level_fine == 0, in table order; u^{l-1}_k is
+ * group l's coarse companion (level_fine, same KH parameters), and a level without companion has
+ * G(u^{l-1}) = 0. The companion's cell values are prolongated piecewise constantly to level l's grid
+ * (each level-l cell takes the value of the coarse cell that contains it).
+ *   alsv_mlmc_bytes       accumulator size: a 256-byte header of int64 sample counts per level,
+ *                         then per level (256-byte aligned) FP64 arrays [q][cells_l]: Welford mean
+ *                         and M2 of Y = q^l - P q^{l-1}, and the running mean of
+ *                         Z = (q^l)^2 - (P q^{l-1})^2. 0 for contexts without a level table.
+ *   alsv_mlmc_reset       zero it (asynchronous).
+ *   alsv_mlmc_accumulate  fold every level's current samples into it, samples in ascending order
+ *                         (may be repeated over batches with other seeds or sample_offset:
+ *                         streaming M_l). Asynchronous.
+ *   alsv_mlmc_read        estimates on the grid of the finest level (the level with the most
+ *                         cells; every level's grid must divide it): mean_dev[q][cells] =
+ *                         sum_l P mean_Y_l, var_dev[q][cells] = sum_l P mean_Z_l - mean^2 (the
+ *                         telescoped second moment minus the squared telescoped mean; it is not
+ *                         clipped at zero). level_dev (nullable), FP64 [levels][q][3]:
+ *                         (sum_cells mean_Y_l dV_l, sum_cells |mean_Y_l| dV_l,
+ *                         sum_cells var_Y_l dV_l) with var_Y = M2/(M_l - 1) (0 for M_l = 1).
+ *                         counts_host (nullable): int64 [levels] samples per level (synchronises
+ *                         the stream). Device outputs are written asynchronously.
+ * Errors: ALSV_ERR_INVALID_ARG without a level table or for a null/unaligned (256 B) buffer,
+ * ALSV_ERR_BUFFER_TOO_SMALL below alsv_mlmc_bytes, ALSV_ERR_NOT_READY without a state.
+ */
+size_t alsv_mlmc_bytes(const alsv_ctx* ctx);
+alsv_status alsv_mlmc_reset(alsv_ctx* ctx, void* acc_dev, size_t bytes);
+alsv_status alsv_mlmc_accumulate(alsv_ctx* ctx, void* acc_dev, size_t bytes);
+alsv_status alsv_mlmc_read(alsv_ctx* ctx, const void* acc_dev, size_t bytes, double* mean_dev, double* var_dev,
+                           double* level_dev, int64_t* counts_host);
+
+/*
+ * Statistical functionals over the current batch (Sec. 2.2: point PDFs and two-point structure
+ * functions among the on-device statistics). Single-level contexts. quantity_index selects a
+ * primitive quantity (rho, u_k, p) (Burgers: u), computed in FP64 from the stored state.
+ *   alsv_point_pdf_accumulate  for each of n_points cells (cells_dev: int64 flat indices
+ *       z*ny*nx + y*nx + x, device) adds every sample's value to counts_dev (int64
+ *       [n_points][n_bins + 2], device, caller-zeroed): bin 0 for x < lo, bin 1 + k for
+ *       lo + k w <= x < lo + (k+1) w (w = (hi - lo) / n_bins, k = floor((x - lo) / (hi - lo) n_bins)
+ *       in FP64, at most n_bins - 1), bin n_bins + 1 for x >= hi or NaN. Asynchronous; streams.
+ *   alsv_structure_function_bytes   accumulator bytes for radius R (256-byte header of FP64
+ *       acc[0..R] plus per-sample partial sums)
+ *   alsv_structure_function_accumulate  order p (1 or 2), radius R in cells (1..16 in 1D and
+ *       2D, 1..4 in 3D): acc[0] += samples, acc[r] += sum over samples (ascending) of
+ *       sum_x sum_{k in Z^d, r-1 < |k|_2 <= r} |q(x + k) - q(x)|^p dV^2; periodic directions
+ *       wrap (they need >= 2R + 1 cells), pairs leaving a non-periodic domain are skipped.
+ *       acc_dev is caller-owned, 256-byte aligned, zeroed before the first call. Asynchronous.
+ *   alsv_structure_function_read  S_dev[r-1] = (sum_{r' <= r} acc[r'] / acc[0])^(1/p), r = 1..R
+ *       (the ball form E[ sum_x sum_{0 < |k| <= r} |dq|^p dV^2 ]^(1/p)). Asynchronous.
+ * Errors: ALSV_ERR_INVALID_ARG (level table, index, p, R, bins or null pointers),
+ * ALSV_ERR_BUFFER_TOO_SMALL, ALSV_ERR_NOT_READY without a state.
+ */
+alsv_status alsv_point_pdf_accumulate(alsv_ctx* ctx, int quantity_index, const int64_t* cells_dev, int n_points,
+                                      double lo, double hi, int n_bins, int64_t* counts_dev);
+size_t alsv_structure_function_bytes(const alsv_ctx* ctx, int radius);
+alsv_status alsv_structure_function_accumulate(alsv_ctx* ctx, int quantity_index, int p, int radius, void* acc_dev,
+                                               size_t bytes);
+alsv_status alsv_structure_function_read(alsv_ctx* ctx, const void* acc_dev, int p, int radius, double* S_dev);
 
 /* Destroy the context (host memory and CUDA graphs only; caller buffers are untouched). */
 alsv_status alsv_destroy(alsv_ctx* ctx);

@@ -6,11 +6,14 @@ It shares no code with the CUDA library; the C++ source is ``alsv_oracle.cpp`` (
 time, FP64, ``-ffp-contract=off``), and this module only builds it and marshals numpy arrays.
 
 Every function here is a thin wrapper over the C++ entry point of the same name; the C++ file
-cites the passage of the paper (or the reading of it) that each computes.
+cites the passage of the paper (or the reading of it) that each computes. The exception is the
+multilevel Monte Carlo estimator (``mlmc_estimate`` and its helpers), written here in numpy
+directly from the estimator's definition.
 """
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import subprocess
 import threading
@@ -208,6 +211,45 @@ def theta_splitmix(seed: int, B: int, P: int) -> np.ndarray:
     return th
 
 
+def primes(k: int) -> list:
+    """The first k primes by trial division."""
+    out = []
+    p = 1
+    while len(out) < k:
+        p += 1
+        if all(p % d for d in range(2, int(p ** 0.5) + 1)):
+            out.append(p)
+    return out
+
+
+def radical_inverse(n: int, p: int) -> float:
+    """Halton's radical inverse phi_p(n) = sum_k d_k p^(-k-1), n = sum_k d_k p^k (exact rational,
+    rounded once)."""
+    num, den = 0, 1
+    while n > 0:
+        n, d = divmod(n, p)
+        num = num * p + d
+        den *= p
+    return num / den
+
+
+def theta_halton(B: int, P: int, seed: int = 0, shifted: bool = False, first_index: int = 0) -> np.ndarray:
+    """Quasi Monte Carlo KH parameters (Sec. 2.2 QMC): theta_{b,j} = hi_j phi_{p_j}(g + 1) with g the
+    sample's global index, p_j the (j+1)-th prime, hi = 1 (amplitudes) or 2 pi (phases); the
+    shifted form adds the Cranley-Patterson rotation s_j = u01(splitmix64(seed ^ (2^63 + j))) mod 1."""
+    ps = primes(P)
+    th = np.zeros((B, P))
+    for b in range(B):
+        for j in range(P):
+            u = radical_inverse(first_index + b + 1, ps[j])
+            if shifted:
+                u = u + (splitmix64(seed ^ ((1 << 63) + j)) >> 11) * (1.0 / 9007199254740992.0)
+                if u >= 1.0:
+                    u = u - 1.0
+            th[b, j] = (1.0 if j < P // 2 else 2.0 * math.pi) * u
+    return th
+
+
 def splitmix64(x: int) -> int:
     return int(lib().orc_splitmix64(C.c_uint64(x & 0xFFFFFFFFFFFFFFFF)))
 
@@ -291,3 +333,123 @@ def fixed_dt_kh(n: int, T: float, cfl: float, gamma: float = 1.4, length: float 
     dxh = length / n
     n_steps = int(math.ceil(T * s_max / (cfl * dxh)))
     return T / n_steps, n_steps
+
+
+# ---------------------------------------------------------------------------------------------
+# Multilevel Monte Carlo estimator (Sec. 2.2, the multilevel form of the sampling display):
+#   E[G(u)] ~ sum_l (1/M_l) sum_k (G(u^l_k) - G(u^{l-1}_k)),  G(u^{-1}) = 0,
+# for G = q and G = q^2, q = primitive variables per cell. The coarse member u^{l-1}_k of a pair
+# is the same sample (same KH parameters) on level l-1's grid, prolongated piecewise constantly
+# to level l's grid. Mean = telescoped first moment; variance = telescoped second moment minus
+# the squared mean (reading). Per-level sums: (sum mean_Y dV, sum |mean_Y| dV, sum var_Y dV),
+# var_Y the unbiased sample variance of Y = q^l - P q^{l-1}.
+# ---------------------------------------------------------------------------------------------
+def primitive_quantities(U, gamma: float = 1.4, euler: bool = True) -> np.ndarray:
+    """q = (rho, u_k, p) from conserved U [M, nv, nz, ny, nx] (Burgers: u itself)."""
+    U = _f64(U)
+    if not euler:
+        return U.copy()
+    rho = U[:, 0]
+    m = U[:, 1:-1]
+    q = np.empty_like(U)
+    q[:, 0] = rho
+    q[:, 1:-1] = m / rho[:, None]
+    q[:, -1] = (gamma - 1.0) * (U[:, -1] - 0.5 * (m * m).sum(axis=1) / rho)
+    return q
+
+
+def prolongate(x, shape) -> np.ndarray:
+    """Piecewise-constant prolongation of x [..., nz, ny, nx] to the grid shape (nz', ny', nx'):
+    each fine cell takes the value of the coarse cell that contains it."""
+    x = _f64(x)
+    for ax, n_fine in zip((-3, -2, -1), shape):
+        n_coarse = x.shape[ax]
+        if n_fine % n_coarse:
+            raise ValueError("the coarse grid must divide the fine grid")
+        x = np.repeat(x, n_fine // n_coarse, axis=ax)
+    return x
+
+
+def mlmc_estimate(levels, gamma: float = 1.4, euler: bool = True):
+    """levels: list of (U_fine [M_l, nv, ...], U_coarse [M_l, nv, ...] or None, dV_l) in level
+    order. Returns (mean [nq, ...], var [nq, ...], level_sums [L, nq, 3]) on the finest grid."""
+    fine_shape = max((lv[0].shape[-3:] for lv in levels), key=lambda s: s[0] * s[1] * s[2])
+    mean = 0.0
+    second = 0.0
+    sums = []
+    for Uf, Uc, dV in levels:
+        qf = primitive_quantities(Uf, gamma, euler)
+        qc = 0.0 if Uc is None else prolongate(primitive_quantities(Uc, gamma, euler), qf.shape[-3:])
+        Y = qf - qc
+        Z = qf * qf - qc * qc
+        M = Y.shape[0]
+        mY = Y.mean(axis=0)
+        vY = Y.var(axis=0, ddof=1) if M > 1 else np.zeros_like(mY)
+        mean = mean + prolongate(mY, fine_shape)
+        second = second + prolongate(Z.mean(axis=0), fine_shape)
+        nq = mY.shape[0]
+        sums.append([[mY[q].sum() * dV, np.abs(mY[q]).sum() * dV, vY[q].sum() * dV] for q in range(nq)])
+    return mean, second - mean * mean, np.array(sums)
+
+
+# ---------------------------------------------------------------------------------------------
+# Statistical functionals (Sec. 2.2: point PDFs and two-point structure functions), numpy.
+# ---------------------------------------------------------------------------------------------
+def point_pdf(U, q: int, cells, lo: float, hi: float, n_bins: int, gamma: float = 1.4, euler: bool = True):
+    """Counts [points, n_bins + 2] of quantity q at flat cell indices over the samples of U:
+    bin 0 below lo, 1 + floor((x - lo) / (hi - lo) * n_bins) (at most n_bins) inside, n_bins + 1
+    at or above hi (and NaN)."""
+    Q = primitive_quantities(U, gamma, euler)[:, q].reshape(U.shape[0], -1)
+    counts = np.zeros((len(cells), n_bins + 2), dtype=np.int64)
+    for i, c in enumerate(cells):
+        for x in Q[:, c]:
+            if x < lo:
+                k = 0
+            elif x < hi:
+                k = 1 + min(int(math.floor((x - lo) / (hi - lo) * n_bins)), n_bins - 1)
+            else:
+                k = n_bins + 1
+            counts[i, k] += 1
+    return counts
+
+
+def structure_function_sums(U, q: int, p: int, R: int, dx, periodic, gamma: float = 1.4, euler: bool = True):
+    """Per radius shell r = 1..R, the sum over samples of
+    sum_x sum_{k in Z^d, r-1 < |k| <= r} |q(x + k) - q(x)|^p dV^2 (periodic directions wrap; pairs
+    leaving a non-periodic domain are dropped). Returns (number of samples, shell sums [R])."""
+    Q = primitive_quantities(U, gamma, euler)[:, q]        # [M, nz, ny, nx]
+    nd = len(dx)
+    dV = float(np.prod(dx))
+    sums = np.zeros(R)
+    rng = [range(-R, R + 1) if k < nd else range(0, 1) for k in range(3)]
+    for kz in rng[2]:
+        for ky in rng[1]:
+            for kx in rng[0]:
+                d2 = kx * kx + ky * ky + kz * kz
+                if d2 == 0 or d2 > R * R:
+                    continue
+                r = math.isqrt(d2)
+                if r * r < d2:
+                    r += 1                                  # smallest r with r^2 >= |k|^2
+                A, B = Q, Q
+                for ax, (k, per) in zip((-1, -2, -3), ((kx, periodic[0]), (ky, periodic[1] if nd > 1 else True),
+                                                      (kz, periodic[2] if nd > 2 else True))):
+                    if k == 0:
+                        continue
+                    if per:
+                        B = np.roll(B, -k, axis=ax)         # B[x] = Q[x + k]
+                    else:
+                        n = Q.shape[ax]
+                        sl_a = [slice(None)] * 4
+                        sl_b = [slice(None)] * 4
+                        sl_a[ax] = slice(max(0, -k), n - max(0, k))
+                        sl_b[ax] = slice(max(0, k), n - max(0, -k))
+                        A, B = A[tuple(sl_a)], B[tuple(sl_b)]
+                diff = np.abs(B - A)
+                sums[r - 1] += (diff ** p).sum() * dV * dV
+    return Q.shape[0], sums
+
+
+def structure_function(count: int, sums, p: int):
+    """S_p(r) = (sum_{r' <= r} sums[r'] / count)^(1/p)."""
+    return (np.cumsum(sums) / count) ** (1.0 / p)

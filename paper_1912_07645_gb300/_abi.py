@@ -33,6 +33,9 @@ class AlsvError(RuntimeError):
         super().__init__(f"{where}: {self.status_name}: {message}")
 
 
+SAMPLER = {"mc": 0, "halton": 1, "halton_shifted": 2}
+
+
 class alsv_grid_desc(C.Structure):
     _fields_ = [
         ("ndim", C.c_int32), ("n", C.c_int32 * 3), ("lo", C.c_double * 3), ("hi", C.c_double * 3),
@@ -41,7 +44,8 @@ class alsv_grid_desc(C.Structure):
         ("cfl", C.c_double), ("fixed_dt", C.c_double), ("precision", C.c_int32), ("seed", C.c_uint64),
         ("weno_eps", C.c_double), ("weno_eps_dx2", C.c_int32), ("n_levels", C.c_int32),
         ("level_n", (C.c_int32 * 3) * MAX_LEVELS), ("level_batch", C.c_int32 * MAX_LEVELS),
-        ("vortex_center", C.c_double * 2), ("sample_offset", C.c_int64), ("reserved", C.c_int32 * 6),
+        ("vortex_center", C.c_double * 2), ("sample_offset", C.c_int64),
+        ("level_fine", C.c_int32 * MAX_LEVELS), ("sampler", C.c_int32), ("reserved", C.c_int32 * 5),
     ]
 
 
@@ -69,11 +73,20 @@ SIGNATURES = {
     "alsv_stats_read": (C.c_int, [_ctx, _vp, _vp, _vp, _i64p]),
     "alsv_stats_merge": (C.c_int, [_ctx, _vp, _vp, _sz]),
     "alsv_conservation_totals": (C.c_int, [_ctx, _vp]),
+    "alsv_point_pdf_accumulate": (C.c_int, [_ctx, C.c_int, _vp, C.c_int, C.c_double, C.c_double, C.c_int, _vp]),
+    "alsv_structure_function_bytes": (_sz, [_ctx, C.c_int]),
+    "alsv_structure_function_accumulate": (C.c_int, [_ctx, C.c_int, C.c_int, C.c_int, _vp, _sz]),
+    "alsv_structure_function_read": (C.c_int, [_ctx, _vp, C.c_int, C.c_int, _vp]),
+    "alsv_mlmc_bytes": (_sz, [_ctx]),
+    "alsv_mlmc_reset": (C.c_int, [_ctx, _vp, _sz]),
+    "alsv_mlmc_accumulate": (C.c_int, [_ctx, _vp, _sz]),
+    "alsv_mlmc_read": (C.c_int, [_ctx, _vp, _sz, _vp, _vp, _vp, _i64p]),
     "alsv_kinetic_energy": (C.c_int, [_ctx, _vp]),
     "alsv_conservation_totals_noalloc": (C.c_int, [C.POINTER(alsv_grid_desc), _vp, _sz, _vp, _vp]),
     "alsv_adjoint_workspace_bytes": (C.c_int, [_ctx, C.c_double, C.POINTER(_sz)]),
     "alsv_bind_adjoint_workspace": (C.c_int, [_ctx, _vp, _sz]),
     "alsv_adjoint_evolve": (C.c_int, [_ctx, C.c_double, C.c_int, _vp, _vp, _vp]),
+    "alsv_adjoint_get_plan": (C.c_int, [_ctx, _i64p, _dp, C.POINTER(C.c_int32)]),
     "alsv_destroy": (C.c_int, [_ctx]),
     "alsv_num_tile_variants": (C.c_int, [_ctx]),
     "alsv_set_tile_variant": (C.c_int, [_ctx, C.c_int]),
@@ -228,6 +241,45 @@ def alsv_stats_merge(ctx, stats, other):
     _check(load().alsv_stats_merge(ctx, _ptr(stats), _ptr(other), _nbytes(stats)), "alsv_stats_merge", ctx)
 
 
+def alsv_point_pdf_accumulate(ctx, quantity: int, cells, lo: float, hi: float, n_bins: int, counts):
+    _check(load().alsv_point_pdf_accumulate(ctx, quantity, _ptr(cells), int(cells.numel()), lo, hi, n_bins,
+                                            _ptr(counts)), "alsv_point_pdf_accumulate", ctx)
+
+
+def alsv_structure_function_bytes(ctx, radius: int) -> int:
+    return int(load().alsv_structure_function_bytes(ctx, radius))
+
+
+def alsv_structure_function_accumulate(ctx, quantity: int, p: int, radius: int, acc):
+    _check(load().alsv_structure_function_accumulate(ctx, quantity, p, radius, _ptr(acc), _nbytes(acc)),
+           "alsv_structure_function_accumulate", ctx)
+
+
+def alsv_structure_function_read(ctx, acc, p: int, radius: int, S):
+    _check(load().alsv_structure_function_read(ctx, _ptr(acc), p, radius, _ptr(S)), "alsv_structure_function_read", ctx)
+
+
+def alsv_mlmc_bytes(ctx) -> int:
+    return int(load().alsv_mlmc_bytes(ctx))
+
+
+def alsv_mlmc_reset(ctx, acc):
+    _check(load().alsv_mlmc_reset(ctx, _ptr(acc), _nbytes(acc)), "alsv_mlmc_reset", ctx)
+
+
+def alsv_mlmc_accumulate(ctx, acc):
+    _check(load().alsv_mlmc_accumulate(ctx, _ptr(acc), _nbytes(acc)), "alsv_mlmc_accumulate", ctx)
+
+
+def alsv_mlmc_read(ctx, acc, mean=None, var=None, level=None, n_levels: int = 0):
+    """Writes the estimate (and per-level sums) to the device buffers given; returns the per-level
+    sample counts when n_levels > 0 (synchronises the stream)."""
+    cnt = (C.c_int64 * max(n_levels, 1))()
+    _check(load().alsv_mlmc_read(ctx, _ptr(acc), _nbytes(acc), _ptr(mean), _ptr(var), _ptr(level),
+                                 cnt if n_levels > 0 else None), "alsv_mlmc_read", ctx)
+    return [int(v) for v in cnt][:n_levels]
+
+
 def alsv_conservation_totals(ctx, totals):
     _check(load().alsv_conservation_totals(ctx, _ptr(totals)), "alsv_conservation_totals", ctx)
 
@@ -257,6 +309,13 @@ def alsv_bind_adjoint_workspace(ctx, ws, nbytes: int | None = None):
 def alsv_adjoint_evolve(ctx, T: float, observable: int, theta, grad_theta, J):
     _check(load().alsv_adjoint_evolve(ctx, T, observable, _ptr(theta), _ptr(grad_theta), _ptr(J)),
            "alsv_adjoint_evolve", ctx)
+
+
+def alsv_adjoint_get_plan(ctx):
+    """(n_steps, dt, forward passes) of the last successful alsv_adjoint_evolve."""
+    n, dt, p = C.c_int64(0), C.c_double(0.0), C.c_int32(0)
+    _check(load().alsv_adjoint_get_plan(ctx, C.byref(n), C.byref(dt), C.byref(p)), "alsv_adjoint_get_plan", ctx)
+    return int(n.value), float(dt.value), int(p.value)
 
 
 def alsv_destroy(ctx):

@@ -9,6 +9,7 @@
 // writes its contributions to the cells of its stencil into shared memory, then every cell sums
 // the contributions of the interfaces that touch it in a fixed order - no atomics.
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <vector>
 
@@ -454,9 +455,14 @@ namespace {
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct AdjPlan {
-    long long n = 0, c = 0, nck = 0;
+    long long n = 0, c = 0, nck = 0, n_cap = 0;
     double dt = 0.0;
 };
+
+// Workspace allowance: the fastest signal may grow by this factor over the run before the
+// checkpoint storage sized from the initial data runs out (see the re-planning in the sweep).
+constexpr double kAdjGrowth = 1.5;
+constexpr int kAdjMaxPasses = 3;
 
 AdjPlan adj_plan(const alsv_ctx* c, double T) {
     AdjPlan p;
@@ -466,8 +472,10 @@ AdjPlan adj_plan(const alsv_ctx* c, double T) {
     p.n = (long long)std::ceil(T * smax / (c->d.cfl * dxm));
     if (p.n < 1) p.n = 1;
     p.dt = T / (double)p.n;
-    p.c = (long long)std::ceil(std::sqrt((double)p.n));
-    p.nck = (p.n + p.c - 1) / p.c;
+    // storage: ceil(sqrt(n_cap)) steps per segment, enough checkpoints for any n <= n_cap
+    p.n_cap = (long long)std::ceil(kAdjGrowth * (double)p.n);
+    p.c = (long long)std::ceil(std::sqrt((double)p.n_cap));
+    p.nck = (p.n_cap + p.c - 1) / p.c;
     return p;
 }
 
@@ -537,7 +545,7 @@ alsv_status alsv_adjoint_evolve(alsv_ctx* c, double T, int observable, const dou
     if (!c->ws) return ctx_fail(c, ALSV_ERR_NOT_READY, "workspace not bound");
     if (!c->U) return ctx_fail(c, ALSV_ERR_NOT_READY, "no state buffer bound (call alsv_set_initial_data once)");
     if (!(T > 0.0) || !std::isfinite(T)) return ctx_fail(c, ALSV_ERR_INVALID_ARG, "T must be finite and > 0");
-    const AdjPlan P = adj_plan(c, T);
+    AdjPlan P = adj_plan(c, T);
     if (!c->adj_ws || c->adj_bytes < adj_bytes(c, P))
         return ctx_fail(c, ALSV_ERR_BUFFER_TOO_SMALL, "adjoint workspace missing or smaller than alsv_adjoint_workspace_bytes");
     cudaStream_t s = c->stream;
@@ -557,30 +565,16 @@ alsv_status alsv_adjoint_evolve(alsv_ctx* c, double T, int observable, const dou
         if (e != cudaSuccess) return ctx_cuda_fail(c, e, #x);         \
     } while (0)
 
-    // ---- initial data from theta, fixed-step time state
+    // ---- forward sweep with checkpoints every c steps, from initial data of theta. The first
+    // pass uses the step planned from the initial data; if the wave speeds grow so far that the
+    // realised CFL number passes the guard, the sweep is repeated with n re-planned from the
+    // fastest signal the pass saw (same CFL target), within the workspace's step allowance.
     InitArgs ia;
     ia.g = c->g;
     ia.U = c->U;
     ia.kind = 0;
     ia.theta = theta_dev;
     ia.P = 20;
-    CKA(launch_init(c->fp64, 2, ia, s));
-    CKA(cudaMemsetAsync(c->t, 0, (size_t)S * 8, s));
-    CKA(cudaMemsetAsync(c->nstep, 0, (size_t)S * 8, s));
-    CKA(cudaMemsetAsync(c->done, 0, (size_t)S * 4, s));
-    CKA(cudaMemsetAsync(c->last, 0, (size_t)S * 4, s));
-    CKA(cudaMemsetAsync(c->status, 0, 4, s));
-    {
-        double hv[2] = {T, 0.0};
-        long long nt = P.n;
-        std::memcpy(&hv[1], &nt, 8);
-        CKA(cudaMemcpyAsync(c->T_end, hv, 16, cudaMemcpyHostToDevice, s));
-        CKA(cudaStreamSynchronize(s));
-    }
-    FinishArgs fa = ctx_finish_args(c, 0);
-    fa.fixed_dt = P.dt;
-    CKA(launch_speed(c->fp64, 2, c->eq, c->variant, c->g, c->U, c->part, s));
-    CKA(launch_finish(fa, s));
     const double third = 1.0 / 3.0, two_third = 2.0 / 3.0;
     const int ns = c->nstages;
     auto fwd_step = [&](const void* Uin, void* Uout, bool finish) -> cudaError_t {
@@ -606,21 +600,62 @@ alsv_status alsv_adjoint_evolve(alsv_ctx* c, double T, int observable, const dou
         if (ee != cudaSuccess || !finish) return ee;
         FinishArgs f = ctx_finish_args(c, 1);
         f.fixed_dt = P.dt;
+        f.cfl_max = c->cfl_max;
         c->launches++;
         return launch_finish(f, s);
     };
-    // ---- forward sweep with checkpoints every c steps
-    for (long long m = 0; m < P.n; ++m) {
-        if (m % P.c == 0) CKA(cudaMemcpyAsync(ckpt(m / P.c), c->U, c->state_bytes, cudaMemcpyDeviceToDevice, s));
-        CKA(fwd_step(c->U, c->U, true));
-    }
-    {
+    c->adj_passes = 0;
+    c->adj_n = 0;
+    for (;;) {
+        ++c->adj_passes;
+        CKA(launch_init(c->fp64, 2, ia, s));
+        CKA(cudaMemsetAsync(c->t, 0, (size_t)S * 8, s));
+        CKA(cudaMemsetAsync(c->nstep, 0, (size_t)S * 8, s));
+        CKA(cudaMemsetAsync(c->done, 0, (size_t)S * 4, s));
+        CKA(cudaMemsetAsync(c->last, 0, (size_t)S * 4, s));
+        CKA(cudaMemsetAsync(c->status, 0, 4, s));
+        CKA(cudaMemsetAsync(c->cfl_max, 0, 8, s));
+        {
+            double hv[2] = {T, 0.0};
+            long long nt = P.n;
+            std::memcpy(&hv[1], &nt, 8);
+            CKA(cudaMemcpyAsync(c->T_end, hv, 16, cudaMemcpyHostToDevice, s));
+            CKA(cudaStreamSynchronize(s));
+        }
+        FinishArgs fa = ctx_finish_args(c, 0);
+        fa.fixed_dt = P.dt;
+        fa.cfl_max = c->cfl_max;
+        CKA(launch_speed(c->fp64, 2, c->eq, c->variant, c->g, c->U, c->part, s));
+        CKA(launch_finish(fa, s));
+        c->launches += 3;
+        for (long long m = 0; m < P.n; ++m) {
+            if (m % P.c == 0) CKA(cudaMemcpyAsync(ckpt(m / P.c), c->U, c->state_bytes, cudaMemcpyDeviceToDevice, s));
+            CKA(fwd_step(c->U, c->U, true));
+        }
         int hs = 0;
+        double cfl_seen = 0.0;
         CKA(cudaMemcpyAsync(&hs, c->status, 4, cudaMemcpyDeviceToHost, s));
+        CKA(cudaMemcpyAsync(&cfl_seen, c->cfl_max, 8, cudaMemcpyDeviceToHost, s));
         CKA(cudaStreamSynchronize(s));
-        if (hs & ST_CFL) return ctx_fail(c, ALSV_ERR_CFL, "adjoint: realised CFL number above the guard 0.5");
         if (hs & ST_NONPHYSICAL) return ctx_fail(c, ALSV_ERR_NONPHYSICAL, "adjoint: non-physical state in the forward sweep");
+        if (!(hs & ST_CFL)) break;
+        // fastest signal over the pass, then the step count that puts it at the target CFL
+        const double s_seen = cfl_seen / P.dt;
+        long long n1 = (long long)std::ceil(T * s_seen / c->d.cfl);
+        if (n1 <= P.n) n1 = P.n + 1;
+        if (c->adj_passes >= kAdjMaxPasses || n1 > P.n_cap) {
+            char msg[192];
+            std::snprintf(msg, sizeof msg,
+                          "adjoint: realised CFL number %.4f above the guard 0.5 with %lld steps; the re-planned %lld "
+                          "steps exceed the allowance of %lld (or %d passes)", cfl_seen, P.n, n1, P.n_cap, kAdjMaxPasses);
+            return ctx_fail(c, ALSV_ERR_CFL, msg);
+        }
+        P.n = n1;
+        P.dt = T / (double)n1;
     }
+    c->adj_n = P.n;
+    c->adj_dt = P.dt;
+    const long long nseg = (P.n + P.c - 1) / P.c;
     // ---- observable and its seed
     CKA(launch_reduce(c->fp64, 1, c->g, c->U, c->red, J_dev, s));
     const long long C = (long long)c->g.lev[0].n[0] * c->g.lev[0].n[1];
@@ -650,7 +685,7 @@ alsv_status alsv_adjoint_evolve(alsv_ctx* c, double T, int observable, const dou
         return launch_adj(c->fp64, c->d.recon, aa, s);
     };
     // ---- reverse sweep, segment by segment
-    for (long long k = P.nck - 1; k >= 0; --k) {
+    for (long long k = nseg - 1; k >= 0; --k) {
         const long long m0 = k * P.c, m1 = std::min(P.n, m0 + P.c);
         auto state = [&](long long m) -> void* { return m == m0 ? ckpt(k) : seg(m - m0); };
         for (long long m = m0; m + 1 < m1; ++m) CKA(fwd_step(state(m), state(m + 1), false));
@@ -689,6 +724,16 @@ alsv_status alsv_adjoint_evolve(alsv_ctx* c, double T, int observable, const dou
     CKA(cudaStreamSynchronize(s));
     c->time_ready = false;  // the state now holds U^n of the adjoint's forward sweep
 #undef CKA
+    return ALSV_OK;
+}
+
+alsv_status alsv_adjoint_get_plan(alsv_ctx* c, int64_t* n_steps, double* dt, int32_t* passes) {
+    if (!c) return ALSV_ERR_INVALID_ARG;
+    if (!n_steps || !dt || !passes) return ctx_fail(c, ALSV_ERR_INVALID_ARG, "null output");
+    if (c->adj_passes == 0 || c->adj_n == 0) return ctx_fail(c, ALSV_ERR_NOT_READY, "no completed adjoint call");
+    *n_steps = c->adj_n;
+    *dt = c->adj_dt;
+    *passes = c->adj_passes;
     return ALSV_OK;
 }
 

@@ -113,6 +113,7 @@ FinishArgs finish_args(alsv_ctx* c, int advance) {
     f.cfl = c->d.cfl;
     f.fixed_dt = c->d.fixed_dt;
     f.cfl_guard = 0.5;
+    f.cfl_max = nullptr;
     f.advance = advance;
     return f;
 }
@@ -274,7 +275,12 @@ StageArgs ctx_stage_args(alsv_ctx* c, const void* Us, const void* Un, void* Uout
 // =============================================================================================
 namespace alsv {
 TileShape stage_tile(int fp64, int ndim, int variant) {
-    if (ndim == 1) return {256, 1, 1, 256};
+    if (ndim == 1) {
+        // short tiles spread a small grid over more SMs (FP64 arithmetic is slow per SM)
+        if (variant == 1) return {64, 1, 1, 64};
+        if (variant == 2) return {32, 1, 1, 32};
+        return {256, 1, 1, 256};
+    }
     if (ndim == 2) {
         if (variant == 1) return TileShape{32, 8, 1, 256};
         if (variant == 2 && !fp64) return TileShape{32, 32, 1, 256};
@@ -286,7 +292,7 @@ TileShape stage_tile(int fp64, int ndim, int variant) {
     return variant == 1 ? TileShape{8, 8, 8, 256} : TileShape{16, 8, 8, 256};
 }
 int stage_num_variants(int fp64, int ndim) {
-    if (ndim == 1) return 1;
+    if (ndim == 1) return 3;
     if (ndim == 2 && !fp64) return 6;
     return 2;
 }
@@ -331,8 +337,9 @@ alsv_status alsv_init_grid(const alsv_grid_desc* d_in, void* stream, alsv_ctx** 
     if (d.fixed_dt < 0.0 || !std::isfinite(d.fixed_dt)) return bad("fixed_dt must be >= 0 and finite");
     if (d.weno_eps == 0.0) d.weno_eps = 1e-6;
     if (!(d.weno_eps > 0.0)) return bad("weno_eps must be > 0");
-    for (int k = 0; k < 6; ++k)
+    for (int k = 0; k < 5; ++k)
         if (d.reserved[k] != 0) return bad("reserved fields must be zero");
+    if (d.sampler < ALSV_SAMPLER_MC || d.sampler > ALSV_SAMPLER_HALTON_SHIFTED) return bad("unknown sampler");
     if (d.sample_offset < 0) return bad("sample_offset must be >= 0");
     for (int k = 0; k < d.ndim; ++k)
         if (!(d.hi[k] > d.lo[k])) return bad("hi must exceed lo in every active direction");
@@ -383,6 +390,33 @@ alsv_status alsv_init_grid(const alsv_grid_desc* d_in, void* stream, alsv_ctx** 
         }
     }
     if (samples > 65535) { delete c; return bad("at most 65535 samples per context"); }
+    // MLMC coupling: companion groups point at the level they pair with
+    {
+        int comp_of[ALSV_MAX_LEVELS];
+        for (int l = 0; l < ALSV_MAX_LEVELS; ++l) comp_of[l] = -1;
+        for (int l = 0; l < ALSV_MAX_LEVELS; ++l) {
+            const int j = d.level_fine[l];
+            if (j == 0) continue;
+            if (nlev < 2 || l >= nlev || j < 0 || j > nlev || j - 1 == l) {
+                delete c;
+                return bad("level_fine: 0, or 1 + the index of another group of the level table");
+            }
+            const int f = j - 1;
+            if (d.level_fine[f] != 0) { delete c; return bad("level_fine: a companion must pair with a level"); }
+            if (comp_of[f] >= 0) { delete c; return bad("level_fine: at most one companion per level"); }
+            comp_of[f] = l;
+            if (g.lev[f].samples != g.lev[l].samples) { delete c; return bad("level_fine: a companion needs its level's batch"); }
+            for (int k = 0; k < d.ndim; ++k)
+                if (g.lev[f].n[k] % g.lev[l].n[k] != 0) {
+                    delete c;
+                    return bad("level_fine: a companion's grid must divide its level's grid");
+                }
+        }
+    }
+    if (d.sampler != ALSV_SAMPLER_MC && d.sample_offset + samples >= (1LL << 31)) {
+        delete c;
+        return bad("Halton sampling needs sample indices below 2^31");
+    }
     c->total_samples = (int)samples;
     g.total_samples = (int)samples;
     g.nv = c->nv;
@@ -415,7 +449,7 @@ alsv_status alsv_init_grid(const alsv_grid_desc* d_in, void* stream, alsv_ctx** 
     ws += 3 * align256((size_t)samples * 8);                      // t, dt, nstep
     ws += 2 * align256((size_t)samples * 4);                      // done, last
     ws += 256;                                                    // status
-    ws += 256;                                                    // T_end + n_target
+    ws += 256;                                                    // T_end, n_target, cfl_max
     ws += align256((size_t)samples * std::max(c->P, 1) * 8);      // theta
     ws += align256((size_t)reduce_partial_count(g) * 8);          // reduction partials
     c->ws_bytes = ws;
@@ -444,7 +478,8 @@ alsv_status alsv_bind_workspace(alsv_ctx* c, void* dev, size_t bytes) {
     c->last = (int*)p; p += align256(S * 4);
     c->status = (int*)p; p += 256;
     c->T_end = (double*)p;
-    c->n_target = (long long*)(p + 8); p += 256;
+    c->n_target = (long long*)(p + 8);
+    c->cfl_max = (double*)(p + 16); p += 256;
     c->theta = (double*)p; p += align256(S * std::max(c->P, 1) * 8);
     c->red = (double*)p;
     c->time_ready = false;
@@ -493,7 +528,15 @@ alsv_status alsv_set_initial_data(alsv_ctx* c, int kind, const double* theta_dev
     if (kind == ALSV_INIT_KH) {
         const double* th = theta_dev;
         if (!th) {
-            cudaError_t e = launch_theta(c->d.seed, c->d.sample_offset, c->total_samples, c->P, c->theta, c->stream);
+            ThetaMap tm;
+            tm.nlev = c->g.nlev;
+            for (int l = 0; l < c->g.nlev; ++l) {
+                tm.sample0[l] = c->g.lev[l].sample0;
+                const int f = c->d.n_levels > 1 ? c->d.level_fine[l] - 1 : -1;
+                tm.src0[l] = f >= 0 ? c->g.lev[f].sample0 : c->g.lev[l].sample0;
+            }
+            cudaError_t e = launch_theta(c->d.seed, c->d.sample_offset, c->d.sampler, tm, c->total_samples, c->P,
+                                         c->theta, c->stream);
             if (e != cudaSuccess) return cuda_fail(c, e, "theta kernel");
             th = c->theta;
         } else if (n_params != c->P) {

@@ -42,6 +42,7 @@ struct alsv_ctx {
     int* status = nullptr;
     double* T_end = nullptr;
     long long* n_target = nullptr;
+    double* cfl_max = nullptr;   // fixed mode: running maximum of the realised CFL number
     double* theta = nullptr;
     double* red = nullptr;
     // state
@@ -61,6 +62,9 @@ struct alsv_ctx {
     // adjoint workspace (caller-owned)
     char* adj_ws = nullptr;
     size_t adj_bytes = 0;
+    long long adj_n = 0;         // plan of the last adjoint call: steps, step, forward passes
+    double adj_dt = 0.0;
+    int adj_passes = 0;
     bool have_theta = false;
 };
 

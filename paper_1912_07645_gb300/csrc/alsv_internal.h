@@ -111,6 +111,7 @@ struct FinishArgs {
     double cfl;
     double fixed_dt;       // > 0: fixed mode
     double cfl_guard;      // fixed mode: realised CFL limit
+    double* cfl_max;       // fixed mode, nullable: running maximum of the realised CFL number
     int advance;           // 1: the step just finished (advance t); 0: only prepare dt
 };
 cudaError_t launch_finish(const FinishArgs& a, cudaStream_t s);
@@ -125,7 +126,15 @@ struct InitArgs {
     double vortex_center[2];
 };
 cudaError_t launch_init(int fp64, int ndim, const InitArgs& a, cudaStream_t s);
-cudaError_t launch_theta(uint64_t seed, long long sample_offset, int samples, int P, double* theta, cudaStream_t s);
+// Counter index of each sample's KH parameters: sample s of group l uses src0[l] + (s - sample0[l])
+// (an MLMC companion group takes its level's indices, every other group its own).
+struct ThetaMap {
+    int nlev;
+    int sample0[kMaxLevels];
+    int src0[kMaxLevels];
+};
+cudaError_t launch_theta(uint64_t seed, long long sample_offset, int sampler, const ThetaMap& map, int samples, int P,
+                         double* theta, cudaStream_t s);
 
 // Monte Carlo statistics (single level).
 cudaError_t launch_welford(int fp64, const GridArgs& g, const void* U, void* stats, cudaStream_t s);

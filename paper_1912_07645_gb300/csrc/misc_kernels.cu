@@ -11,28 +11,43 @@ namespace alsv {
 // dt = fixed_dt until n_target steps; the realised CFL number dt * s_b is checked against a guard.
 // A NaN partial marks a non-physical sample: it stops and the status word records it.
 // ---------------------------------------------------------------------------------------------
-__global__ void k_finish(const FinishArgs a) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= a.g.total_samples) return;
+// One block per sample: the block's threads stride over the sample's tile partials and combine
+// them with a shuffle tree. The maximum of non-negative doubles is exact in any order, so the
+// result is bitwise independent of the block size; a NaN anywhere marks the sample.
+constexpr int FINISH_NT = 256;
+
+__global__ void __launch_bounds__(FINISH_NT) k_finish(const FinishArgs a) {
+    const int s = blockIdx.x;
     const int l = level_of_sample(a.g, s);
     const LevelInfo& L = a.g.lev[l];
     const int b = s - L.sample0;
+    if (a.advance && a.done[s]) return;  // skipped by this step's stages (uniform over the block)
+    const double* part = a.speed_part + L.work0 + (long long)b * L.tiles;
+    double smax = 0.0;
+    int bad = 0;
+    for (int k = threadIdx.x; k < L.tiles; k += FINISH_NT) {
+        const double v = part[k];
+        if (v != v) bad = 1;
+        else smax = v > smax ? v : smax;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double v = __shfl_xor_sync(0xffffffffu, smax, o);
+        smax = v > smax ? v : smax;
+    }
+    __shared__ double wmax[FINISH_NT / 32];
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = smax;
+    bad = __syncthreads_or(bad);   // also orders every thread's read of done[s] before the writes below
+    if (threadIdx.x != 0) return;
+#pragma unroll
+    for (int w = 1; w < FINISH_NT / 32; ++w) smax = wmax[w] > smax ? wmax[w] : smax;
     if (a.advance) {
-        if (a.done[s]) return;  // skipped by this step's stages
         double t = a.t[s];
         const long long n = a.nstep[s] + 1;
         if (a.fixed_dt > 0.0) t = (double)n * a.fixed_dt;
         else t = a.last[s] ? *a.T_end : t + a.dt[s];
         a.t[s] = t;
         a.nstep[s] = n;
-    }
-    const double* part = a.speed_part + L.work0 + (long long)b * L.tiles;
-    double smax = 0.0;
-    bool bad = false;
-    for (int k = 0; k < L.tiles; ++k) {
-        const double v = part[k];
-        if (v != v) bad = true;
-        else smax = v > smax ? v : smax;
     }
     if (bad) {
         atomicOr(a.status, ST_NONPHYSICAL);
@@ -45,6 +60,8 @@ __global__ void k_finish(const FinishArgs a) {
         a.last[s] = 0;
         const bool fin = a.nstep[s] >= *a.n_target;
         a.done[s] = fin ? 1 : 0;
+        if (!fin && a.cfl_max) atomicMax(reinterpret_cast<unsigned long long*>(a.cfl_max),
+                                         (unsigned long long)__double_as_longlong(a.fixed_dt * smax));
         if (!fin && a.fixed_dt * smax > a.cfl_guard) atomicOr(a.status, ST_CFL);
         return;
     }
@@ -68,7 +85,7 @@ __global__ void k_finish(const FinishArgs a) {
 cudaError_t launch_finish(const FinishArgs& a, cudaStream_t s) {
     const int n = a.g.total_samples;
     if (n <= 0) return cudaSuccess;
-    k_finish<<<(n + 127) / 128, 128, 0, s>>>(a);
+    k_finish<<<n, FINISH_NT, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -84,21 +101,61 @@ __device__ __forceinline__ uint64_t sm64(uint64_t x) {
     return z ^ (z >> 31);
 }
 
-__global__ void k_theta(uint64_t seed, long long sample_offset, int samples, int P, double* theta) {
+// (j+1)-th prime by trial division (j < 128 here: primes up to 719)
+__device__ uint32_t nth_prime(int j) {
+    uint32_t p = 1;
+    for (int found = -1; found < j;) {
+        ++p;
+        bool prime = p >= 2;
+        for (uint32_t d = 2; d * d <= p; ++d)
+            if (p % d == 0) { prime = false; break; }
+        if (prime) ++found;
+    }
+    return p;
+}
+
+// Halton radical inverse phi_p(n) = sum_k d_k p^(-k-1) for n = sum_k d_k p^k, formed as the exact
+// integer fraction num / p^K (both below 2^53 for n < 2^31, p < 1024) and one rounded division
+__device__ double radical_inverse(uint64_t n, uint32_t p) {
+    uint64_t num = 0, den = 1;
+    while (n > 0) {
+        num = num * p + n % p;
+        den *= p;
+        n /= p;
+    }
+    return (double)num / (double)den;
+}
+
+__global__ void k_theta(uint64_t seed, long long sample_offset, int sampler, const ThetaMap map, int samples, int P,
+                        double* theta) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (long long)samples * P) return;
     const int b = (int)(i / P), j = (int)(i - (long long)b * P);
-    const uint64_t gb = (uint64_t)(sample_offset + b);
-    const uint64_t r = sm64(seed ^ (gb * (uint64_t)P + (uint64_t)j));
-    const double u01 = (double)(r >> 11) * (1.0 / 9007199254740992.0);
+    int l = 0;
+    for (int k = 1; k < map.nlev; ++k)
+        if (b >= map.sample0[k]) l = k;
+    const uint64_t gb = (uint64_t)(sample_offset + map.src0[l] + (b - map.sample0[l]));
     const double hi = j < P / 2 ? 1.0 : 2.0 * 3.14159265358979323846;
+    double u01;
+    if (sampler == 0) {
+        const uint64_t r = sm64(seed ^ (gb * (uint64_t)P + (uint64_t)j));
+        u01 = (double)(r >> 11) * (1.0 / 9007199254740992.0);
+    } else {
+        u01 = radical_inverse(gb + 1, nth_prime(j));
+        if (sampler == 2) {
+            const uint64_t r = sm64(seed ^ ((1ull << 63) + (uint64_t)j));
+            u01 = u01 + (double)(r >> 11) * (1.0 / 9007199254740992.0);
+            if (u01 >= 1.0) u01 = u01 - 1.0;
+        }
+    }
     theta[i] = hi * u01;
 }
 
-cudaError_t launch_theta(uint64_t seed, long long sample_offset, int samples, int P, double* theta, cudaStream_t s) {
+cudaError_t launch_theta(uint64_t seed, long long sample_offset, int sampler, const ThetaMap& map, int samples, int P,
+                         double* theta, cudaStream_t s) {
     const long long n = (long long)samples * P;
     if (n <= 0) return cudaSuccess;
-    k_theta<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(seed, sample_offset, samples, P, theta);
+    k_theta<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(seed, sample_offset, sampler, map, samples, P, theta);
     return cudaGetLastError();
 }
 

@@ -10,11 +10,13 @@ from . import _abi as A
 def make_desc(ndim=1, n=(8, 1, 1), lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), batch=1, eq="euler", gamma=1.4,
               recon="mc", rvars="prim", flux="hllc", rk="ssprk2", bc="periodic", cfl=0.45, fixed_dt=0.0,
               precision="fp64", seed=0, weno_eps=1e-6, weno_eps_dx2=False, levels=None,
-              vortex_center=(5.0, 5.0), sample_offset=0, **_ignored) -> A.alsv_grid_desc:
+              vortex_center=(5.0, 5.0), sample_offset=0, sampler="mc", **_ignored) -> A.alsv_grid_desc:
     """Build an ``alsv_grid_desc`` from plain values.
 
     ``bc``: one name for every side or a list of (lo, hi) names per direction.
-    ``levels``: optional MLMC level table, a list of (n_tuple, samples).
+    ``levels``: optional level table, a list of (n_tuple, samples) or (n_tuple, samples, fine):
+    ``fine`` = index of the table entry this group is the MLMC coarse companion of (same samples
+    and KH parameters on a coarser grid).
     """
     d = A.alsv_grid_desc()
     d.ndim = ndim
@@ -42,13 +44,16 @@ def make_desc(ndim=1, n=(8, 1, 1), lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), batch
     d.weno_eps_dx2 = 1 if weno_eps_dx2 else 0
     if levels:
         d.n_levels = len(levels)
-        for l, (ln, lb) in enumerate(levels):
+        for l, entry in enumerate(levels):
+            ln, lb = entry[0], entry[1]
             ln = list(ln) + [1] * (3 - len(ln))
             for k in range(3):
                 d.level_n[l][k] = int(ln[k]) if k < ndim else 1
             d.level_batch[l] = lb
+            d.level_fine[l] = int(entry[2]) + 1 if len(entry) > 2 and entry[2] is not None else 0
     d.vortex_center[0], d.vortex_center[1] = vortex_center
     d.sample_offset = int(sample_offset)
+    d.sampler = A.SAMPLER[sampler]
     return d
 
 
@@ -149,6 +154,57 @@ class Solver:
             var = self.torch.empty_like(mean)
         cnt = A.alsv_stats_read(self.ctx, self.stats, mean, var)
         return cnt, mean, var
+
+    def mlmc_levels(self):
+        """Table indices of the estimator's levels (groups that are not coarse companions)."""
+        return [l for l in range(self.desc.n_levels) if self.desc.level_fine[l] == 0]
+
+    def mlmc_init(self):
+        nb = A.alsv_mlmc_bytes(self.ctx)
+        with self.torch.cuda.stream(self.stream):
+            self.mlmc_acc = self.torch.empty(nb, dtype=self.torch.uint8, device=self.device)
+        A.alsv_mlmc_reset(self.ctx, self.mlmc_acc)
+
+    def mlmc_accumulate(self):
+        if getattr(self, "mlmc_acc", None) is None:
+            self.mlmc_init()
+        A.alsv_mlmc_accumulate(self.ctx, self.mlmc_acc)
+
+    def mlmc_read(self):
+        """(counts per level, mean [q, nz, ny, nx], variance, per-level sums [levels, q, 3]) on the
+        finest level's grid; synchronous."""
+        lv = self.mlmc_levels()
+        fine = max(lv, key=lambda l: self.level_shape(l)[2] * self.level_shape(l)[3] * self.level_shape(l)[4])
+        _, nv, nz, ny, nx = self.level_shape(fine)
+        with self.torch.cuda.stream(self.stream):
+            mean = self.torch.empty((nv, nz, ny, nx), dtype=self.torch.float64, device=self.device)
+            var = self.torch.empty_like(mean)
+            lev = self.torch.empty((len(lv), nv, 3), dtype=self.torch.float64, device=self.device)
+        cnt = A.alsv_mlmc_read(self.ctx, self.mlmc_acc, mean, var, lev, n_levels=len(lv))
+        return cnt, mean, var, lev
+
+    def point_pdf(self, quantity, cells, lo, hi, n_bins, counts=None):
+        """Add this batch to the counts (int64 [points, n_bins + 2], zeros when None) of the
+        quantity's values at the given flat cell indices; returns the counts tensor."""
+        torch = self.torch
+        with torch.cuda.stream(self.stream):
+            cells = torch.as_tensor(cells, dtype=torch.int64).to(self.device)
+            if counts is None:
+                counts = torch.zeros((cells.numel(), n_bins + 2), dtype=torch.int64, device=self.device)
+        A.alsv_point_pdf_accumulate(self.ctx, quantity, cells, lo, hi, n_bins, counts)
+        return counts
+
+    def structure_function(self, quantity, p, radius, acc=None):
+        """Fold this batch into the accumulator (new when None) and return (acc, S_p(1..radius))."""
+        torch = self.torch
+        with torch.cuda.stream(self.stream):
+            if acc is None:
+                acc = torch.zeros(A.alsv_structure_function_bytes(self.ctx, radius), dtype=torch.uint8,
+                                  device=self.device)
+            S = torch.empty(radius, dtype=torch.float64, device=self.device)
+        A.alsv_structure_function_accumulate(self.ctx, quantity, p, radius, acc)
+        A.alsv_structure_function_read(self.ctx, acc, p, radius, S)
+        return acc, S
 
     def totals(self):
         with self.torch.cuda.stream(self.stream):

@@ -147,8 +147,11 @@ def test_adjoint_validation_without_gpu(alsv):
     try:
         b = alsv.alsv_adjoint_workspace_bytes(ctx, 1.0)
         state = 64 * 4 * 512 * 512 * 8
-        # n = 3035 steps, ceil(sqrt(n)) = 56: 55 checkpoints + 55 segment states + 3 adjoint buffers
-        assert b >= (55 + 55 + 3) * state and b < (55 + 55 + 3) * state + (1 << 24)
+        # n = 3035 steps, allowance n_cap = ceil(1.5 n) = 4553, segments of ceil(sqrt(n_cap)) = 68
+        # steps: 67 checkpoints + 67 segment states + 3 adjoint buffers
+        assert b >= (67 + 67 + 3) * state and b < (67 + 67 + 3) * state + (1 << 24)
+        with pytest.raises(alsv.AlsvError, match="no completed adjoint call"):
+            alsv.alsv_adjoint_get_plan(ctx)
     finally:
         alsv.alsv_destroy(ctx)
 
@@ -186,3 +189,33 @@ def test_fast_division_formula():
         for n in ns:
             if 0 <= n < 2**31:
                 assert ((((n * m) >> 32) + n) >> l) == n // d
+
+
+def test_mlmc_coupling_validation(alsv):
+    base = dict(ndim=2, recon="mc", flux="hllc", precision="fp64")
+    good = [((16, 8), 6), ((32, 16), 4), ((16, 8), 4, 1)]
+    ctx, _ = alsv.alsv_init_grid(alsv.make_desc(levels=good, **base), 0)
+    try:
+        # one 256-byte header, then per level 3 arrays of 4 quantities (256-byte aligned blocks)
+        assert alsv.alsv_mlmc_bytes(ctx) == 256 + 3 * 4 * 128 * 8 + 3 * 4 * 512 * 8
+    finally:
+        alsv.alsv_destroy(ctx)
+    bad = {
+        "batch": [((16, 8), 6), ((32, 16), 4), ((16, 8), 3, 1)],
+        "divide": [((16, 8), 6), ((32, 16), 4), ((12, 8), 4, 1)],
+        "level": [((16, 8), 6), ((32, 16), 4, 0), ((16, 8), 4, 1)],
+        "one companion": [((32, 16), 4), ((16, 8), 4, 0), ((16, 8), 4, 0)],
+        "another group": [((32, 16), 4), ((16, 8), 4, 1)],
+    }
+    for what, levels in bad.items():
+        with pytest.raises(alsv.AlsvError, match="level_fine"):
+            alsv.alsv_init_grid(alsv.make_desc(levels=levels, **base), 0)
+    d = alsv.make_desc(n=(16, 8), **base)
+    d.level_fine[0] = 1
+    with pytest.raises(alsv.AlsvError, match="level_fine"):
+        alsv.alsv_init_grid(d, 0)
+    ctx, _ = alsv.alsv_init_grid(alsv.make_desc(n=(16, 8), **base), 0)
+    try:
+        assert alsv.alsv_mlmc_bytes(ctx) == 0
+    finally:
+        alsv.alsv_destroy(ctx)

@@ -1,5 +1,7 @@
 """Discrete adjoint on the GPU vs the oracle's exact forward-mode (dual number) gradient of the
 same discrete map, vs central finite differences, and through torch.autograd."""
+import math
+
 import numpy as np
 import pytest
 
@@ -35,12 +37,44 @@ def test_adjoint_fp64_matches_oracle_dual_gradient(recon, rvars, rk):
                bc="periodic", cfl=0.4, precision="fp64")
     T = 0.1
     dt, nsteps = oracle.fixed_dt_kh(n, T, 0.4)
-    assert nsteps == 19      # ragged: 19 steps in checkpoint segments of 5
+    assert nsteps == 19      # ragged: 19 steps in checkpoint segments of ceil(sqrt(ceil(1.5 * 19))) = 6
     th = kh_theta(3, 31)
     J, g = gpu_adjoint(cfg, th, T)
     d = oracle.make_desc(**cfg)
     for b in range(3):
         Jo, go = oracle.ke_grad_kh2d(d, th[b], dt, nsteps)
+        assert J[b] == pytest.approx(Jo, rel=1e-13)
+        assert np.abs(g[b] - go).max() <= 1e-10 * np.abs(go).max(), (g[b], go)
+
+
+def test_adjoint_replans_when_the_realised_cfl_passes_the_guard():
+    """CFL 0.495 from the initial data: the start-up transient pushes the realised CFL number over
+    0.5 within the first steps, so the sweep is repeated with n = ceil(T s_seen / cfl); the result
+    is the oracle's gradient of the re-planned discrete map."""
+    import torch
+    import paper_1912_07645_gb300 as alsv
+    n, T, cfl = 32, 0.2, 0.495
+    cfg = dict(ndim=2, n=(n, n), batch=2, eq="euler", recon="mc", rvars="prim", flux="rusanov", rk="ssprk2",
+               bc="periodic", cfl=cfl, precision="fp64")
+    th = oracle.theta_splitmix(7, 2, 20)
+    d = oracle.make_desc(**cfg)
+    dt0, n0 = oracle.fixed_dt_kh(n, T, cfl)
+    U = oracle.init(d, "kh", 2, th)
+    seen = 0.0
+    for _ in range(n0):
+        seen = max(seen, float(oracle.max_speed(d, U).max()) * dt0)
+        U, _, _ = oracle.evolve(d, U, fixed_dt=dt0, n_steps=1)
+    assert seen > 0.5
+    n1 = math.ceil(T * (seen / dt0) / cfl)
+    S = gpu_solver(**cfg)
+    S.set_initial_data("kh", theta=torch.from_numpy(th).cuda())
+    J, g = S.adjoint(torch.from_numpy(th), T)
+    J, g = host(J), host(g)
+    n_gpu, dt_gpu, passes = alsv.alsv_adjoint_get_plan(S.ctx)
+    S.close()
+    assert (n_gpu, passes) == (n1, 2) and dt_gpu == T / n1
+    for b in range(2):
+        Jo, go = oracle.ke_grad_kh2d(d, th[b], T / n1, n1)
         assert J[b] == pytest.approx(Jo, rel=1e-13)
         assert np.abs(g[b] - go).max() <= 1e-10 * np.abs(go).max(), (g[b], go)
 

@@ -1,0 +1,115 @@
+"""Parity at the configurations' full sizes, in the launch configurations bench.py uses.
+
+* KH 2D 1024^2 (FP64 and FP32): two CFL steps on the whole grid against the oracle.
+* KH 3D slab 512^3 (FP32): one fixed-step SSP-RK3 step; sampled cells against the oracle run on a
+  13^3 block around each cell (an RK3 step of a g = 2 stencil only reaches 6 cells, so the block's
+  own boundary cannot influence its centre).
+* Adjoint 512^2 x 64 (FP64): the batch holds one sample and its +-h perturbations of all 20
+  parameters, so a single full-size call gives both its adjoint gradient and central differences.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from harness import gpu_solver, host, need_gpu, p1_check, p2_check
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    need_gpu()
+    from paper_1912_07645_gb300 import build
+    build.build()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_kh2d_1024_two_steps(precision):
+    import torch
+    cfg = dict(ndim=2, n=(1024, 1024), batch=1, eq="euler", recon="weno3", flux="hllc", rvars="prim", rk="ssprk3",
+               bc="periodic", cfl=0.4, precision=precision, seed=0)
+    S = gpu_solver(**cfg)
+    S.set_initial_data("kh")
+    if precision == "fp32":
+        import paper_1912_07645_gb300 as alsv
+        alsv.alsv_autotune(S.ctx, 2)
+    S.step(2)
+    S.sync()
+    g = host(S.U).reshape(S.level_shape(0))
+    S.close()
+    torch.cuda.empty_cache()
+    d = oracle.make_desc(**cfg)
+    th = oracle.theta_splitmix(0, 1, 20)
+    o, _, _ = oracle.evolve(d, oracle.init(d, "kh", 1, th), T=math.inf, max_steps=2)
+    if precision == "fp64":
+        p1_check(g, o, what="kh2d 1024 fp64")
+    else:
+        p2_check(g, o, what="kh2d 1024 fp32")
+
+
+def test_kh3d_512_sampled_cells():
+    import torch
+    n = 512
+    dx = 1.0 / n
+    dt = 0.3 * dx / 2.4      # a CFL-0.3 step for |u| + c <= 2.4
+    cfg = dict(ndim=3, n=(n, n, n), batch=1, eq="euler", recon="weno3", flux="hllc", rvars="prim", rk="ssprk3",
+               bc="periodic", cfl=0.3, precision="fp32", seed=3, fixed_dt=dt)
+    S = gpu_solver(**cfg)
+    S.set_initial_data("kh")
+    # two cells cut by the perturbed lower interface (mixed density) and one in the bulk, away
+    # from the domain edges so that a 13^3 block needs no periodic wrap
+    picks = []
+    for (x, z) in [(100, 37), (311, 260)]:
+        rho = host(S.state()[0, 0, z, :, x])
+        ys = np.nonzero((rho > 1.0) & (rho < 2.0) & (np.arange(n) < n // 2))[0]
+        assert ys.size > 0
+        picks.append((x, int(ys[0]), z))
+    picks.append((257, 200, 480))
+    S.step(1)
+    S.sync()
+    V = S.state()
+    g = [host(V[0, :, z, y, x]) for (x, y, z) in picks]
+    S.close()
+    del V
+    torch.cuda.empty_cache()
+    th = oracle.theta_splitmix(3, 1, 128)
+    R = 6
+    for (x, y, z), gv in zip(picks, g):
+        lo = ((x - R) * dx, (y - R) * dx, (z - R) * dx)
+        hi = ((x + R + 1) * dx, (y + R + 1) * dx, (z + R + 1) * dx)
+        d = oracle.make_desc(ndim=3, n=(2 * R + 1,) * 3, lo=lo, hi=hi, eq="euler", recon="weno3", flux="hllc",
+                             rvars="prim", rk="ssprk3", bc="outflow", cfl=0.3)
+        U0 = oracle.init(d, "kh", 1, th)
+        U1, _, _ = oracle.evolve(d, U0, fixed_dt=dt, n_steps=1)
+        ov = U1[0, :, R, R, R]
+        scale = np.maximum(np.abs(ov), 1.0)
+        assert np.all(np.abs(gv - ov) <= 2e-5 * scale), (x, y, z, gv, ov)
+        if (x, y, z) != picks[-1]:   # at the interface the step really moved the state
+            assert np.abs(ov - U0[0, :, R, R, R]).max() > 1e-6
+
+
+def test_adjoint_512x64_vs_central_differences():
+    import torch
+    n, B, T = 512, 64, 0.01
+    cfg = dict(ndim=2, n=(n, n), batch=B, eq="euler", recon="mc", flux="rusanov", rvars="prim", rk="ssprk2",
+               bc="periodic", cfl=0.4, precision="fp64")
+    base = oracle.theta_splitmix(12345, 1, 20)[0]
+    th = np.tile(base, (B, 1))
+    # h as small as FP64 rounding of J allows: the MC limiter makes the discrete map piecewise
+    # smooth, and the share of cells whose limiter branch a +-h perturbation flips grows with h
+    hs = 1e-6 * np.maximum(1.0, np.abs(base))
+    for j in range(20):
+        th[1 + 2 * j, j] += hs[j]
+        th[2 + 2 * j, j] -= hs[j]
+    S = gpu_solver(**cfg)
+    tth = torch.from_numpy(th).cuda()
+    S.set_initial_data("kh", theta=tth)
+    J, g = S.adjoint(tth, T)
+    J, g = host(J), host(g)
+    S.close()
+    fd = np.array([(J[1 + 2 * j] - J[2 + 2 * j]) / (2 * hs[j]) for j in range(20)])
+    assert np.abs(g[0] - fd).max() <= 1e-4 * np.abs(g[0]).max(), (g[0], fd)
+    # the other samples of the batch are unperturbed copies for j >= 20 pairs: identical results
+    assert np.all(J[41:] == J[0])

@@ -76,6 +76,22 @@ def test_theta_splitmix_bitwise():
     assert np.array_equal(host(th3), oracle.theta_splitmix(77, 3, 128))
 
 
+@pytest.mark.parametrize("sampler", ["halton", "halton_shifted"])
+def test_theta_halton_bitwise(sampler):
+    torch = torch_()
+    import paper_1912_07645_gb300 as alsv
+    shifted = sampler == "halton_shifted"
+    for ndim, n, B, P, off in ((2, (16, 16), 40, 20, 0), (3, (8, 8, 8), 3, 128, 1000)):
+        S = gpu_solver(ndim=ndim, n=n, batch=B, seed=99, sampler=sampler, sample_offset=off, precision="fp32")
+        S.set_initial_data("kh")
+        th = torch.empty((B, P), dtype=torch.float64, device="cuda")
+        alsv.alsv_get_parameters(S.ctx, th)
+        S.sync()
+        ref = oracle.theta_halton(B, P, seed=99, shifted=shifted, first_index=off)
+        assert np.array_equal(host(th), ref)
+        S.close()
+
+
 def test_sample_offset_draws_global_parameters():
     torch = torch_()
     import paper_1912_07645_gb300 as alsv
@@ -249,6 +265,24 @@ def test_sod_config_full_run_fp64():
     o, ost, ot = run_oracle(cfg, "sod", T=0.2)
     assert n == ost[0] and t[0] == 0.2 and ot[0] == 0.2
     p1_check(g, o, what="sod full")
+
+
+@pytest.mark.parametrize("variant,precision", [(1, "fp64"), (2, "fp64"), (2, "fp32")])
+def test_short_1d_tiles_bitwise_equal_to_default_tile(variant, precision):
+    """1D tiles of 64 and 32 cells (ragged: 1000 cells) compute every interface with the same
+    arithmetic as the 256-cell tile, so whole runs agree bitwise."""
+    import paper_1912_07645_gb300 as alsv
+    cfg = dict(ndim=1, n=(1000,), batch=2, eq="euler", recon="mc", flux="hllc", rvars="prim", rk="ssprk2",
+               bc="outflow", cfl=0.45, precision=precision)
+    outs = []
+    for v in (0, variant):
+        S = gpu_solver(**cfg)
+        alsv.alsv_set_tile_variant(S.ctx, v)
+        S.set_initial_data("sod")
+        S.evolve_to(0.2)
+        outs.append(host(S.U))
+        S.close()
+    assert np.array_equal(outs[0], outs[1])
 
 
 @pytest.mark.parametrize("init,recon,flux,rvars", [("sod", "weno3", "hllc", "prim"), ("lax", "mc", "hll", "cons"),

@@ -526,3 +526,164 @@ def test_stats_merge_equals_two_pass_of_union():
     assert c == 23
     np.testing.assert_allclose(m, mu.astype(float), rtol=1e-14, atol=1e-15)
     np.testing.assert_allclose(M2 / 22, var.astype(float), rtol=1e-13)
+
+
+# ---------------------------------------------------------------------------------------------
+# Multilevel Monte Carlo estimator (Sec. 2.2)
+# ---------------------------------------------------------------------------------------------
+def test_mlmc_hand_worked_two_level_example():
+    """Scalar quantity (no conversion); level 0 one cell (dV = 1), level 1 two cells (dV = 1/2).
+    Level 0: samples 1, 3           -> Y mean 2, var 2; Z = 1, 9 -> mean 5.
+    Level 1: fine (2, 4), (0, 2); coarse 1, 3 (prolongated to both cells):
+             Y = (1, 3), (-3, -1)   -> mean (-1, 1), var (8, 8)
+             Z = (4-1, 16-1), (0-9, 4-9) = (3, 15), (-9, -5) -> mean (-3, 5).
+    Estimate: mean = 2 + (-1, 1) = (1, 3); second = 5 + (-3, 5) = (2, 10); var = (2-1, 10-9) = (1, 1).
+    Level sums: level 0 (2, 2, 2); level 1 ((-1+1)/2, (1+1)/2, (8+8)/2) = (0, 1, 8)."""
+    l0 = (np.array([1.0, 3.0]).reshape(2, 1, 1, 1, 1), None, 1.0)
+    fine = np.array([[2.0, 4.0], [0.0, 2.0]]).reshape(2, 1, 1, 1, 2)
+    coarse = np.array([1.0, 3.0]).reshape(2, 1, 1, 1, 1)
+    mean, var, sums = oracle.mlmc_estimate([l0, (fine, coarse, 0.5)], euler=False)
+    np.testing.assert_array_equal(mean.reshape(-1), [1.0, 3.0])
+    np.testing.assert_array_equal(var.reshape(-1), [1.0, 1.0])
+    np.testing.assert_array_equal(sums.reshape(2, 3), [[2.0, 2.0, 2.0], [0.0, 1.0, 8.0]])
+
+
+def test_mlmc_prolongation_is_the_containing_coarse_cell():
+    rng = np.random.default_rng(5)
+    x = rng.normal(size=(3, 1, 2, 3))
+    y = oracle.prolongate(x, (1, 4, 9))
+    for q in range(3):
+        for j in range(4):
+            for i in range(9):
+                assert y[q, 0, j, i] == x[q, 0, j // 2, i // 3]
+    with pytest.raises(ValueError):
+        oracle.prolongate(x, (1, 5, 9))
+
+
+@pytest.mark.parametrize("euler", [False, True])
+def test_mlmc_telescopes_to_the_finest_level_when_levels_share_samples(euler):
+    """If every level's coarse companion is exactly the previous level's own sample set, the sum
+    collapses: the estimate is the plain sample mean (and biased variance) of the finest level.
+    Grids refine by 2 in y and 3 in x, so a transposed prolongation cannot pass."""
+    rng = np.random.default_rng(11)
+    M = 5
+    shapes = [(1, 2, 3), (1, 4, 9), (1, 8, 27)]
+
+    def fields(shape):
+        if not euler:
+            return rng.normal(size=(M, 1) + shape)
+        U = np.empty((M, 4) + shape)
+        rho = rng.uniform(0.5, 2.0, (M,) + shape)
+        u = rng.uniform(-1, 1, (M, 2) + shape)
+        p = rng.uniform(0.5, 3.0, (M,) + shape)
+        U[:, 0] = rho
+        U[:, 1:3] = rho[:, None] * u
+        U[:, 3] = p / 0.4 + 0.5 * rho * (u * u).sum(axis=1)
+        return U
+
+    A = [fields(s) for s in shapes]
+    levels = [(A[0], None, 1.0)] + [(A[l], A[l - 1], 1.0) for l in (1, 2)]
+    mean, var, _ = oracle.mlmc_estimate(levels, euler=euler)
+    if euler:   # quantities from the (pinned) C++ cell conversion
+        d = oracle.make_desc(ndim=2, n=(27, 8), eq="euler")
+        q = np.empty_like(A[2])
+        for b in range(M):
+            for j in range(8):
+                for i in range(27):
+                    q[b, :, 0, j, i] = oracle.cons_to_prim(d, A[2][b, :, 0, j, i])
+    else:
+        q = A[2]
+    mu = q.mean(axis=0)
+    np.testing.assert_allclose(mean, mu, rtol=1e-12, atol=1e-13)
+    np.testing.assert_allclose(var, ((q - mu) ** 2).mean(axis=0), rtol=1e-9, atol=1e-12)
+
+
+def test_mlmc_single_level_is_plain_monte_carlo():
+    """One level without companion: mean and level variance sum are the sample mean and the
+    unbiased sample variance integrated over the grid (integer data, exact)."""
+    U = np.array([[1.0, 2.0], [3.0, 6.0], [8.0, 1.0]]).reshape(3, 1, 1, 1, 2)
+    mean, var, sums = oracle.mlmc_estimate([(U, None, 0.5)], euler=False)
+    np.testing.assert_array_equal(mean.reshape(-1), [4.0, 3.0])
+    # second moments (1+9+64)/3, (4+36+1)/3 minus squared means 16, 9
+    np.testing.assert_allclose(var.reshape(-1), [74 / 3 - 16, 41 / 3 - 9], rtol=1e-15)
+    # unbiased variances: ((9+1+16)/2, (1+9+4)/2) = (13, 7); sums x dV = 0.5
+    np.testing.assert_allclose(sums.reshape(3), [3.5, 3.5, 10.0], rtol=1e-15)
+
+
+# ---------------------------------------------------------------------------------------------
+# Quasi Monte Carlo parameters (Halton)
+# ---------------------------------------------------------------------------------------------
+def test_halton_textbook_values_and_primes():
+    assert [oracle.radical_inverse(n, 2) for n in range(1, 8)] == [1 / 2, 1 / 4, 3 / 4, 1 / 8, 5 / 8, 3 / 8, 7 / 8]
+    assert [oracle.radical_inverse(n, 3) for n in range(1, 7)] == [1 / 3, 2 / 3, 1 / 9, 4 / 9, 7 / 9, 2 / 9]
+    ps = oracle.primes(128)
+    assert ps[:10] == [2, 3, 5, 7, 11, 13, 17, 19, 23, 29]
+    assert ps[19] == 71 and ps[127] == 719   # the 20th and the 128th prime
+
+
+@pytest.mark.parametrize("p,k", [(2, 10), (3, 6), (71, 2)])
+def test_halton_first_p_to_the_k_points_fill_the_lattice(p, k):
+    """phi_p permutes {0, 1/p^k, ..., (p^k - 1)/p^k} over n = 0 .. p^k - 1 (digit reversal)."""
+    vals = sorted(oracle.radical_inverse(n, p) for n in range(p ** k))
+    assert vals == [i / p ** k for i in range(p ** k)]
+
+
+def test_halton_theta_ranges_and_shift():
+    th = oracle.theta_halton(50, 20)
+    assert np.all(th[:, :10] > 0) and np.all(th[:, :10] < 1)
+    assert np.all(th[:, 10:] > 0) and np.all(th[:, 10:] < 2 * math.pi)
+    # sample b uses index b + 1: the amplitude a_1 (base 2) runs through 1/2, 1/4, 3/4, ...
+    assert list(th[:3, 0]) == [0.5, 0.25, 0.75]
+    sh = oracle.theta_halton(50, 20, seed=7, shifted=True)
+    s0 = (oracle.splitmix64(7 ^ (1 << 63)) >> 11) * 2.0 ** -53
+    assert sh[0, 0] == (0.5 + s0) - (1.0 if 0.5 + s0 >= 1.0 else 0.0)
+    assert np.all(sh[:, :10] >= 0) and np.all(sh[:, :10] < 1)
+    assert np.array_equal(oracle.theta_halton(5, 20, first_index=3), th[3:8])
+
+
+# ---------------------------------------------------------------------------------------------
+# Point PDFs and structure functions
+# ---------------------------------------------------------------------------------------------
+# lattice points of Z^2 and Z^3 in the closed ball of radius r (Gauss circle / sphere counts,
+# OEIS A000328 and A000605)
+BALL2 = [1, 5, 13, 29, 49, 81, 113, 149, 197, 253, 317, 377, 441, 529, 613, 709, 797]
+BALL3 = [1, 7, 33, 123, 257]
+
+
+@pytest.mark.parametrize("nd", [2, 3])
+def test_structure_function_of_a_single_spike_counts_lattice_points(nd):
+    """q = 1 at one cell, 0 elsewhere, periodic: a pair differs exactly when one end is the spike,
+    so the ball sum of |dq| (and of dq^2) is twice the number of nonzero offsets in the ball."""
+    R = 16 if nd == 2 else 4
+    n = 2 * R + 3
+    shape = (1, 1) + ((1, n, n) if nd == 2 else (n, n, n))
+    U = np.zeros(shape)
+    U[(0, 0) + ((0, 5, 9) if nd == 2 else (4, 5, 9))] = 1.0
+    ball = BALL2 if nd == 2 else BALL3
+    for p in (1, 2):
+        cnt, sums = oracle.structure_function_sums(U, 0, p, R, (1.0,) * nd, (True, True, True), euler=False)
+        assert cnt == 1
+        np.testing.assert_array_equal(np.cumsum(sums), [2 * (ball[r] - 1) for r in range(1, R + 1)])
+
+
+def test_structure_function_of_a_linear_profile_without_wrap():
+    """q_i = i on n cells, non-periodic: shell r holds the offsets +-r with 2 (n - r) valid pairs
+    of difference r: sums r^p 2 (n - r) dx^2; S_p(r) then follows in closed form."""
+    n, R, dx = 40, 6, 0.025
+    U = np.arange(n, dtype=float).reshape(1, 1, 1, 1, n)
+    for p in (1, 2):
+        cnt, sums = oracle.structure_function_sums(U, 0, p, R, (dx,), (False,), euler=False)
+        expect = np.array([r ** p * 2 * (n - r) * dx * dx for r in range(1, R + 1)])
+        np.testing.assert_allclose(sums, expect, rtol=1e-15)
+        S = oracle.structure_function(cnt, sums, p)
+        np.testing.assert_allclose(S, np.cumsum(expect) ** (1.0 / p), rtol=1e-15)
+    flat = np.full((2, 1, 1, 1, n), 3.5)
+    assert not oracle.structure_function_sums(flat, 0, 2, R, (dx,), (True,), euler=False)[1].any()
+
+
+def test_point_pdf_bins_by_definition():
+    # integer data: 0.5 on a bin edge goes up, the top edge and NaN go to the overflow bin
+    vals = np.array([-1.0, 0.0, 0.49, 0.5, 0.99, 1.0, np.nan, 0.25])
+    U = vals.reshape(8, 1, 1, 1, 1)
+    c = oracle.point_pdf(U, 0, [0], 0.0, 1.0, 2, euler=False)
+    np.testing.assert_array_equal(c, [[1, 3, 2, 2]])

@@ -29,6 +29,18 @@ M = 4096
 T_END = 1.0
 SEED = 12345
 METRIC = "cell-updates/s & % HBM roofline; MC samples/s batched-FP32 vs plain FP64"
+# Algorithmic floating-point operations per cell-update of 2D WENO3 (primitive) + HLLC + SSP-RK3,
+# counted on the oracle's counting scalar (a CPU test checks this constant against that count).
+FLOPS_PER_CELL_UPDATE_2D_WENO3_HLLC_RK3 = 1980
+# FP32 (non-tensor) peak from the unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flops (FMA)
+# x 2.07 GHz (maximum SM clock).
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+STAGE_KERNEL_NAMES = {0: "k_stage<float, Euler, 2D, WENO3, HLLC, 32x16>",
+                      1: "k_stage<float, Euler, 2D, WENO3, HLLC, 32x8>",
+                      2: "k_stage<float, Euler, 2D, WENO3, HLLC, 32x32>",
+                      3: "k_stage2d_col<WENO3, HLLC>",
+                      4: "k_stage2d_pair<WENO3, HLLC, 32x16>",
+                      5: "k_stage2d_pair<WENO3, HLLC, 32x8>"}
 WORKLOAD = "kh2d_256x256_mc4096_weno3_hllc_ssprk3_fp32_T1"
 # compulsory HBM bytes per 2D SSP-RK3 cell-update in FP32: per variable read U^n + write U1,
 # read U1 + U^n + write U2, read U2 + U^n + write U^{n+1} = 8 words, x 4 variables x 4 bytes
@@ -492,7 +504,7 @@ def main():
         traffic, traffic_pcu = stage_traffic(chosen, cell_updates, prof["stage_launches"])
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": (achieved / peaks["hbm_gbs"]) if achieved else None, "peak_kind": peak_kind,
-                "kernel": "k_stage<float, Euler, 2D, WENO3, HLLC>",
+                "kernel": STAGE_KERNEL_NAMES.get(chosen, str(chosen)),
                 "algorithmic_bytes_per_cell_update": BYTES_PER_CELL_UPDATE,
                 "stage_ms_total": prof["stage_ms"], "stage_launches": prof["stage_launches"],
                 "stage_share_of_step": prof["stage_ms"] / ms if ms > 0 else None,
@@ -510,6 +522,13 @@ def main():
                            "tile_variant": chosen, "autotune_ms": ms_var},
                 "samples_per_s": samples_per_s, "gpu_launches": launches, "e2e": e2e, "roofline": roof,
                 "clocks": ck}
+        if achieved:
+            # the same stage time against the FP32 ALU: algorithmic flops per cell-update
+            tflops = cell_updates * FLOPS_PER_CELL_UPDATE_2D_WENO3_HLLC_RK3 / (prof["stage_ms"] / 1000.0) / 1e12
+            line["alu_roofline"] = {"bound": "alu", "achieved": tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                    "frac": tflops / FP32_PEAK_TFLOPS,
+                                    "flops_per_cell_update": FLOPS_PER_CELL_UPDATE_2D_WENO3_HLLC_RK3,
+                                    "peak_kind": "nominal: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
         steps0 = float(nstep[0]) if len(nstep) else 1.0
         line["plain_fp64"] = plain_fp64_loop(alsv, torch, steps0)
         line["batched_vs_plain_fp64_samples_per_s"] = samples_per_s / line["plain_fp64"]["samples_per_s"]

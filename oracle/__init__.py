@@ -325,6 +325,16 @@ def ke_dir_kh2d(d: Desc, theta, vdir, dt: float, n_steps: int):
     return J.value, dJ.value
 
 
+def count_flops(d: Desc) -> dict:
+    """Algorithmic floating-point operations of the scheme, counted on the oracle's counting
+    scalar: per reconstruction (one variable, both faces), cons->prim, interface flux,
+    divergence + RK per cell-stage, per cell-stage and per cell-update."""
+    out = np.zeros(6)
+    lib().orc_count_flops(C.byref(d), _dp(out))
+    keys = ("recon", "cons_to_prim", "flux", "div_rk", "per_cell_stage", "per_cell_update")
+    return dict(zip(keys, out.tolist()))
+
+
 def fixed_dt_kh(n: int, T: float, cfl: float, gamma: float = 1.4, length: float = 1.0):
     """Fixed step for the adjoint (reading): s_max from the two unperturbed KH states,
     n_steps = ceil(T s_max / (cfl dx)), dt = T / n_steps."""

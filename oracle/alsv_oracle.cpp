@@ -110,7 +110,34 @@ template <int N> inline Dual<N> sin(const Dual<N>& a) {
     return r;
 }
 
+// ------------------------------------------------------------------------------------------
+// Flop-counting scalar: a double whose arithmetic (+, -, *, /, sqrt, sin) adds one to a counter.
+// Only used to count the algorithmic floating-point operations of the scheme's pieces.
+// ------------------------------------------------------------------------------------------
+static thread_local long long g_flops = 0;
+struct Cnt {
+    double v;
+    Cnt() : v(0.0) {}
+    Cnt(double x) : v(x) {}
+};
+inline Cnt operator+(const Cnt& a, const Cnt& b) { ++g_flops; return Cnt(a.v + b.v); }
+inline Cnt operator-(const Cnt& a, const Cnt& b) { ++g_flops; return Cnt(a.v - b.v); }
+inline Cnt operator*(const Cnt& a, const Cnt& b) { ++g_flops; return Cnt(a.v * b.v); }
+inline Cnt operator/(const Cnt& a, const Cnt& b) { ++g_flops; return Cnt(a.v / b.v); }
+inline Cnt operator-(const Cnt& a) { return Cnt(-a.v); }
+inline Cnt operator+(const Cnt& a, double b) { return a + Cnt(b); }
+inline Cnt operator+(double a, const Cnt& b) { return Cnt(a) + b; }
+inline Cnt operator-(const Cnt& a, double b) { return a - Cnt(b); }
+inline Cnt operator-(double a, const Cnt& b) { return Cnt(a) - b; }
+inline Cnt operator*(const Cnt& a, double b) { return a * Cnt(b); }
+inline Cnt operator*(double a, const Cnt& b) { return Cnt(a) * b; }
+inline Cnt operator/(const Cnt& a, double b) { return a / Cnt(b); }
+inline Cnt operator/(double a, const Cnt& b) { return Cnt(a) / b; }
+
 inline double val(double x) { return x; }
+inline double val(const Cnt& x) { return x.v; }
+inline Cnt sqrt_(const Cnt& x) { ++g_flops; return Cnt(std::sqrt(x.v)); }
+inline Cnt sin_(const Cnt& x) { ++g_flops; return Cnt(std::sin(x.v)); }
 template <int N> inline double val(const Dual<N>& x) { return x.v; }
 inline double sqrt_(double x) { return std::sqrt(x); }
 template <int N> inline Dual<N> sqrt_(const Dual<N>& x) { return sqrt(x); }
@@ -685,6 +712,60 @@ int orc_init(const Desc* d, int kind, int B, const double* theta, int P, double 
 // Welford update of per-cell mean/M2 of the primitive quantities (Burgers: u; Euler: rho,
 // velocities, p) over B samples in ascending order (Sec. 2.2: mean and variance on device).
 // count is shared by all cells; mean, M2 are [q][cells].
+// Algorithmic floating-point operations of the scheme of d, counted by running its pieces on the
+// counting scalar with a representative smooth, subsonic pair of states (MC central slope, HLLC
+// left star state): out = {reconstruction of one variable (both faces of a cell), cons->prim of a
+// cell, one interface flux, divergence + RK combination of one cell and stage, per cell-stage,
+// per cell-update}. A cell-stage takes its cell's conversion (primitive reconstruction) and per
+// direction one cell's reconstruction and one interface flux (each interface belongs to one cell).
+void orc_count_flops(const Desc* d, double* out) {
+    const int nv = nvars(*d), nd = d->ndim;
+    const bool euler = d->eq != EQ_BURGERS;
+    Cnt wm(1.0), w0(1.1), wp(1.3), fl, fr;
+    g_flops = 0;
+    recon_scalar(d->recon, d->weno_eps_dx2 ? 1e-4 : d->weno_eps, wm, w0, wp, &fl, &fr);
+    const double f_rec = (double)g_flops;
+    Cnt U[8], W[8];
+    const double Wl0[5] = {1.0, 0.3, 0.1, 0.05, 2.5}, Wr0[5] = {1.1, 0.25, 0.05, 0.0, 2.4};
+    Cnt WL[8], WR[8], F[8];
+    for (int v = 0; v < nv; ++v) {
+        const int src = v <= nd ? v : 4;      // rho, velocities of the active directions, p
+        WL[v] = Cnt(euler ? Wl0[src] : 0.3);
+        WR[v] = Cnt(euler ? Wr0[src] : 0.25);
+    }
+    double f_c2p = 0.0;
+    if (euler) {
+        prim_to_cons(*d, WL, U);
+        g_flops = 0;
+        cons_to_prim(*d, U, W);
+        f_c2p = (double)g_flops;
+    }
+    g_flops = 0;
+    flux(*d, 0, WL, WR, F);
+    const double f_flux = (double)g_flops;
+    // divergence over the directions and the RK combination averaged over the stages
+    g_flops = 0;
+    Cnt acc(0.0), Fm(0.1), Fp(0.2), dt(1e-3), us(1.0), un(1.0);
+    for (int k = 0; k < nd; ++k) acc = acc - (Fp - Fm) / dx(*d, k);
+    const double f_div = (double)g_flops * nv;
+    g_flops = 0;
+    Cnt o1 = us + dt * acc;
+    Cnt o2 = 0.75 * un + 0.25 * (us + dt * acc);
+    Cnt o3 = (1.0 / 3.0) * un + (2.0 / 3.0) * (us + dt * acc);
+    (void)o1; (void)o2; (void)o3;
+    const int stages = d->rk == RK_SSP2 ? 2 : 3;
+    const double f_rk = (stages == 2 ? (2.0 + 5.0) / 2.0 : (double)g_flops / 3.0) * nv;
+    double per_stage = nd * (nv * f_rec + f_flux) + f_div + f_rk;
+    if (euler && d->rvars == RV_PRIM) per_stage += f_c2p;          // each cell converted once
+    if (euler && d->rvars == RV_CONS) per_stage += nd * 2 * f_c2p; // both faces converted
+    out[0] = f_rec;
+    out[1] = f_c2p;
+    out[2] = f_flux;
+    out[3] = f_div + f_rk;
+    out[4] = per_stage;
+    out[5] = per_stage * stages;
+}
+
 void orc_welford(const Desc* d, int B, const double* U, int64_t* count, double* mean, double* M2) {
     const int nv = nvars(*d);
     const int64_t C = ncells(*d);

@@ -289,17 +289,21 @@ TileShape stage_tile(int fp64, int ndim, int variant) {
         return TileShape{32, 16, 1, 256};                                   // variants 0 and 4
     }
     if (fp64) return variant == 1 ? TileShape{8, 8, 4, 256} : TileShape{8, 8, 8, 256};
+    if (variant == 2) return TileShape{32, 8, 64, 256};    // z-marching column chunks
+    if (variant == 3) return TileShape{32, 8, 128, 256};
     return variant == 1 ? TileShape{8, 8, 8, 256} : TileShape{16, 8, 8, 256};
 }
 int stage_num_variants(int fp64, int ndim) {
     if (ndim == 1) return 3;
     if (ndim == 2 && !fp64) return 6;
+    if (ndim == 3 && !fp64) return 4;
     return 2;
 }
 bool stage_variant_supported(int fp64, int ndim, int eq, int recon, int rvars, int flux, const int bc[3][2], int variant) {
     if (variant < 0 || variant >= stage_num_variants(fp64, ndim)) return false;
     if (ndim == 2 && !fp64 && (variant == 4 || variant == 5))
         return eq == EQ_EULER && rvars == RV_PRIM && (flux == FLX_HLLC || flux == FLX_RUSANOV);
+    if (ndim == 3 && !fp64 && variant >= 2) return eq == EQ_EULER;
     if (!(ndim == 2 && !fp64 && variant == 3)) return true;
     const bool periodic = bc[0][0] == BC_PERIODIC && bc[0][1] == BC_PERIODIC && bc[1][0] == BC_PERIODIC &&
                           bc[1][1] == BC_PERIODIC;

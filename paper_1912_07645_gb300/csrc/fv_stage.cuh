@@ -90,24 +90,19 @@ constexpr size_t stage_smem_bytes() {
     return sizeof(R) * (size_t)CS * (size_t)(SX * SY * SZ + NI);
 }
 
-// Reconstruct the two face states of interface (left cell i, right cell i+1) from the cell records
-// i-1 .. i+2 (i, i+1 for PC) along one direction, apply the positivity fallback, and return
-// primitive states for the flux. i0: record index of cell i; step: records between neighbours.
-template <class R, int EQ, int ND, int RECON, int CS>
-__device__ __forceinline__ void interface_states(const R* sw, int i0, int step, int rvars, R gm1, R eps, R* WL,
-                                                 R* WR) {
+// Reconstruct the two face states of interface (left cell i, right cell i+1) from the cell values
+// cm = i-1, cl = i, cr = i+1, c2 = i+2 (cm and c2 unused for PC) along one direction, apply the
+// positivity fallback, and return primitive states for the flux.
+template <class R, int EQ, int ND, int RECON>
+__device__ __forceinline__ void face_states(const R* cm, const R* cl, const R* cr, const R* c2, int rvars, R gm1, R eps,
+                                            R* WL, R* WR) {
     constexpr int NV = (EQ == EQ_BURGERS) ? 1 : ND + 2;
     constexpr int G = (RECON == REC_PC) ? 1 : 2;
-    R cl[NV], cr[NV], fl[NV], fr[NV];
-    lds_cell<R, NV, CS>(sw + i0 * CS, cl);
-    lds_cell<R, NV, CS>(sw + (i0 + step) * CS, cr);
+    R fl[NV], fr[NV];
     if (G == 1) {
 #pragma unroll
         for (int v = 0; v < NV; ++v) { fr[v] = cl[v]; fl[v] = cr[v]; }
     } else {
-        R cm[NV], c2[NV];
-        lds_cell<R, NV, CS>(sw + (i0 - step) * CS, cm);
-        lds_cell<R, NV, CS>(sw + (i0 + 2 * step) * CS, c2);
         if constexpr (RECON == REC_WENO3 && !IsExact<R>::value) {
 #pragma unroll
             for (int v = 0; v + 1 < NV; v += 2) {
@@ -165,6 +160,23 @@ __device__ __forceinline__ void interface_states(const R* sw, int i0, int step, 
             WR[v] = okR ? b[v] : cb[v];
         }
     }
+}
+
+// The same from shared-memory cell records: i0 = record index of cell i, step = records between
+// neighbours along the direction.
+template <class R, int EQ, int ND, int RECON, int CS>
+__device__ __forceinline__ void interface_states(const R* sw, int i0, int step, int rvars, R gm1, R eps, R* WL,
+                                                 R* WR) {
+    constexpr int NV = (EQ == EQ_BURGERS) ? 1 : ND + 2;
+    constexpr int G = (RECON == REC_PC) ? 1 : 2;
+    R cm[NV], cl[NV], cr[NV], c2[NV];
+    lds_cell<R, NV, CS>(sw + i0 * CS, cl);
+    lds_cell<R, NV, CS>(sw + (i0 + step) * CS, cr);
+    if (G == 2) {
+        lds_cell<R, NV, CS>(sw + (i0 - step) * CS, cm);
+        lds_cell<R, NV, CS>(sw + (i0 + 2 * step) * CS, c2);
+    }
+    face_states<R, EQ, ND, RECON>(cm, cl, cr, c2, rvars, gm1, eps, WL, WR);
 }
 
 template <class R, int EQ, int ND, int RECON, int FLUX, int TX, int TY, int TZ, int NT>

@@ -336,6 +336,51 @@ def test_sod_fp32_full_run():
     p2_check(g, o, what="sod fp32")
 
 
+@pytest.mark.parametrize("variant", [2, 3])
+@pytest.mark.parametrize("recon,flux,rvars,bc", [("weno3", "hllc", "prim", "periodic"),
+                                                  ("mc", "hll", "cons", "periodic"),
+                                                  ("pc", "rusanov", "prim", "periodic"),
+                                                  ("weno3", "rusanov", "prim",
+                                                   [("periodic", "periodic"), ("reflective", "outflow"),
+                                                    ("outflow", "reflective")])])
+def test_kh_3d_zmarch_bitwise_equal_to_tiles(variant, recon, flux, rvars, bc):
+    """The z-marching schedule evaluates every interface and the divergence with the tile kernel's
+    arithmetic (ragged: 70 cells in z = one chunk of 64 plus 6, or one partial chunk of 128)."""
+    import paper_1912_07645_gb300 as alsv
+    torch = torch_()
+    cfg = dict(ndim=3, n=(40, 20, 70), batch=2, eq="euler", recon=recon, flux=flux, rvars=rvars, rk="ssprk3",
+               bc=bc, cfl=0.3, precision="fp32")
+    th = torch.from_numpy(kh_theta(2, 21, P=128)).cuda()
+    outs = []
+    for v in (0, variant):
+        S = gpu_solver(**cfg)
+        alsv.alsv_set_tile_variant(S.ctx, v)
+        S.set_initial_data("kh", theta=th)
+        S.step(3)
+        S.sync()
+        outs.append((host(S.U), S.time()))
+        S.close()
+    assert np.array_equal(outs[0][0], outs[1][0])
+    np.testing.assert_array_equal(outs[0][1][0], outs[1][1][0])
+
+
+def test_kh_3d_zmarch_fp32_vs_oracle():
+    import paper_1912_07645_gb300 as alsv
+    torch = torch_()
+    cfg = dict(ndim=3, n=(24, 20, 70), batch=1, eq="euler", recon="weno3", flux="hllc", rvars="prim", rk="ssprk3",
+               bc="periodic", cfl=0.3, precision="fp32")
+    th = kh_theta(1, 8, P=128)
+    S = gpu_solver(**cfg)
+    alsv.alsv_set_tile_variant(S.ctx, 2)
+    S.set_initial_data("kh", theta=torch.from_numpy(th).cuda())
+    S.step(3)
+    S.sync()
+    g = host(S.U).reshape(S.level_shape(0))
+    S.close()
+    o, *_ = run_oracle(cfg, "kh", th, steps=3)
+    p2_check(g, o, what="kh3d z-march fp32")
+
+
 def test_kh_3d_fp32():
     cfg = dict(ndim=3, n=(24, 20, 16), batch=1, eq="euler", recon="weno3", flux="hllc", rvars="prim", rk="ssprk3",
                bc="periodic", cfl=0.3, precision="fp32")

@@ -687,3 +687,37 @@ def test_point_pdf_bins_by_definition():
     U = vals.reshape(8, 1, 1, 1, 1)
     c = oracle.point_pdf(U, 0, [0], 0.0, 1.0, 2, euler=False)
     np.testing.assert_array_equal(c, [[1, 3, 2, 2]])
+
+
+# ---------------------------------------------------------------------------------------------
+# Algorithmic flop counts (counting scalar)
+# ---------------------------------------------------------------------------------------------
+def test_flop_counts_of_the_pieces_by_hand():
+    """Counted by hand from the formulas: MC: two differences, 2 dm, (dm + dp)/2 (two), 2 dp, two
+    faces w0 -+ s/2 (two each) = 10. WENO3, per face: two candidates (3 each), two smoothness
+    indicators (3 each), two weights d/((eps + b)(eps + b)) (4 each), the weighted average (5) =
+    25; both faces 50. cons->prim 2D: two velocities (2), |m|^2 (3), /2, /rho, E - ., (gamma - 1),
+    * (5) = 10; 3D: 3 + 5 + 5 = 13."""
+    d2 = oracle.make_desc(ndim=2, n=(8, 8), eq="euler", recon="mc", flux="rusanov", rvars="prim", rk="ssprk2")
+    c = oracle.count_flops(d2)
+    assert c["recon"] == 10 and c["cons_to_prim"] == 10
+    d2w = oracle.make_desc(ndim=2, n=(8, 8), eq="euler", recon="weno3", flux="hllc", rvars="prim", rk="ssprk3")
+    c = oracle.count_flops(d2w)
+    assert c["recon"] == 50
+    # per cell-stage: conversion + per direction (4 reconstructions + one flux) + divergence/RK;
+    # per cell-update: three stages
+    assert c["per_cell_stage"] == c["cons_to_prim"] + 2 * (4 * c["recon"] + c["flux"]) + c["div_rk"]
+    assert c["per_cell_update"] == 3 * c["per_cell_stage"]
+    d3 = oracle.make_desc(ndim=3, n=(8, 8, 8), eq="euler", recon="pc", flux="rusanov", rvars="prim", rk="ssprk3")
+    c = oracle.count_flops(d3)
+    assert c["recon"] == 0 and c["cons_to_prim"] == 13
+
+
+def test_bench_flop_constant_matches_the_count():
+    """bench.py reports its FP32-ALU fraction with this count (it does not call the oracle)."""
+    import re
+    src = open(os.path.join(os.path.dirname(__file__), "..", "bench.py")).read()
+    m = re.search(r"FLOPS_PER_CELL_UPDATE_2D_WENO3_HLLC_RK3 = (\d+)", src)
+    assert m, "bench.py must state the flop count"
+    d = oracle.make_desc(ndim=2, n=(8, 8), eq="euler", recon="weno3", flux="hllc", rvars="prim", rk="ssprk3")
+    assert int(m.group(1)) == oracle.count_flops(d)["per_cell_update"]

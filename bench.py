@@ -261,6 +261,10 @@ WORKLOADS = {
     "kh3d512_fp32": dict(desc=dict(ndim=3, n=(512, 512, 512), batch=1, eq="euler", recon="weno3", flux="hllc",
                                    rvars="prim", rk="ssprk3", bc="periodic", cfl=0.3, precision="fp32", seed=0),
                          init="kh", steps=100, words=8, nv=5, esize=4),
+    # a quarter-size slab for profiler captures (state 0.34 GB, above L2)
+    "kh3d256_fp32": dict(desc=dict(ndim=3, n=(256, 256, 256), batch=1, eq="euler", recon="weno3", flux="hllc",
+                                   rvars="prim", rk="ssprk3", bc="periodic", cfl=0.3, precision="fp32", seed=0),
+                         init="kh", steps=10, words=8, nv=5, esize=4),
     "adjoint512_fp32": dict(desc=dict(ndim=2, n=(512, 512), batch=64, eq="euler", recon="mc", flux="rusanov",
                                       rvars="prim", rk="ssprk2", bc="periodic", cfl=0.4, precision="fp32", seed=SEED),
                             adjoint=True, T=1.0),

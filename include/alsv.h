@@ -316,8 +316,8 @@ alsv_status alsv_mlmc_read(alsv_ctx* ctx, const void* acc_dev, size_t bytes, dou
                            double* level_dev, int64_t* counts_host);
 
 /*
- * Statistical functionals over the current batch (Sec. 2.2: point PDFs and two-point structure
- * functions among the on-device statistics). Single-level contexts. quantity_index selects a
+ * Statistical functionals over the current batch (Sec. 2.2: point PDFs, two-point structure
+ * functions, joint PDFs and multi-point correlators among the on-device statistics). Single-level contexts. quantity_index selects a
  * primitive quantity (rho, u_k, p) (Burgers: u), computed in FP64 from the stored state.
  *   alsv_point_pdf_accumulate  for each of n_points cells (cells_dev: int64 flat indices
  *       z*ny*nx + y*nx + x, device) adds every sample's value to counts_dev (int64
@@ -338,6 +338,16 @@ alsv_status alsv_mlmc_read(alsv_ctx* ctx, const void* acc_dev, size_t bytes, dou
  */
 alsv_status alsv_point_pdf_accumulate(alsv_ctx* ctx, int quantity_index, const int64_t* cells_dev, int n_points,
                                       double lo, double hi, int n_bins, int64_t* counts_dev);
+/*   alsv_joint_pdf_accumulate  the joint histogram of quantities q1 and q2 at each cell: counts_dev
+ *       int64 [n_points][n_bins1 + 2][n_bins2 + 2], bins of each quantity as in the point PDF.
+ *   alsv_correlator_accumulate  multi-point correlator E[prod_{j<k} q(x_j)] (the paper's
+ *       multi-point correlators, read as raw moments): cells_dev int64 [n_sets][k] (1 <= k <= 8),
+ *       acc_dev FP64 [1 + n_sets], caller-zeroed: acc[0] += samples, acc[1 + s] += sum over samples
+ *       (ascending) of the product over set s. Asynchronous; streams over batches. */
+alsv_status alsv_joint_pdf_accumulate(alsv_ctx* ctx, int q1, int q2, const int64_t* cells_dev, int n_points, double lo1,
+                                      double hi1, int n_bins1, double lo2, double hi2, int n_bins2, int64_t* counts_dev);
+alsv_status alsv_correlator_accumulate(alsv_ctx* ctx, int quantity_index, const int64_t* cells_dev, int n_sets, int k,
+                                       double* acc_dev);
 size_t alsv_structure_function_bytes(const alsv_ctx* ctx, int radius);
 alsv_status alsv_structure_function_accumulate(alsv_ctx* ctx, int quantity_index, int p, int radius, void* acc_dev,
                                                size_t bytes);

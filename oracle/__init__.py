@@ -413,14 +413,40 @@ def point_pdf(U, q: int, cells, lo: float, hi: float, n_bins: int, gamma: float 
     counts = np.zeros((len(cells), n_bins + 2), dtype=np.int64)
     for i, c in enumerate(cells):
         for x in Q[:, c]:
-            if x < lo:
-                k = 0
-            elif x < hi:
-                k = 1 + min(int(math.floor((x - lo) / (hi - lo) * n_bins)), n_bins - 1)
-            else:
-                k = n_bins + 1
-            counts[i, k] += 1
+            counts[i, _bin(x, lo, hi, n_bins)] += 1
     return counts
+
+
+def _bin(x: float, lo: float, hi: float, n_bins: int) -> int:
+    if x < lo:
+        return 0
+    if x < hi:
+        return 1 + min(int(math.floor((x - lo) / (hi - lo) * n_bins)), n_bins - 1)
+    return n_bins + 1
+
+
+def joint_pdf(U, q1: int, q2: int, cells, lo1, hi1, nb1, lo2, hi2, nb2, gamma: float = 1.4, euler: bool = True):
+    """Joint counts [points, nb1 + 2, nb2 + 2] of quantities q1, q2 at each cell over the samples,
+    each binned as in point_pdf."""
+    Q = primitive_quantities(U, gamma, euler).reshape(U.shape[0], U.shape[1], -1)
+    counts = np.zeros((len(cells), nb1 + 2, nb2 + 2), dtype=np.int64)
+    for i, c in enumerate(cells):
+        for b in range(U.shape[0]):
+            counts[i, _bin(Q[b, q1, c], lo1, hi1, nb1), _bin(Q[b, q2, c], lo2, hi2, nb2)] += 1
+    return counts
+
+
+def correlator(U, q: int, cell_sets, gamma: float = 1.4, euler: bool = True):
+    """Multi-point correlator sums: (samples, [sum over samples of prod_j q(x_j)] per set)."""
+    Q = primitive_quantities(U, gamma, euler)[:, q].reshape(U.shape[0], -1)
+    sums = np.zeros(len(cell_sets))
+    for s, cs in enumerate(cell_sets):
+        for b in range(U.shape[0]):
+            prod = 1.0
+            for c in cs:
+                prod = prod * Q[b, c]
+            sums[s] += prod
+    return U.shape[0], sums
 
 
 def structure_function_sums(U, q: int, p: int, R: int, dx, periodic, gamma: float = 1.4, euler: bool = True):

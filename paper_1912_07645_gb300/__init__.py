@@ -14,7 +14,8 @@ from ._abi import (BC, EQ, FLUX, INIT, PRECISION, RECON, RK, RVARS, AlsvError, a
                    alsv_bind_workspace, alsv_conservation_totals, alsv_conservation_totals_noalloc, alsv_destroy, alsv_evolve_to_T,
                    alsv_get_launch_count, alsv_get_parameters, alsv_get_profile, alsv_get_tile, alsv_get_time, alsv_grid_desc,
                    alsv_init_grid, alsv_kinetic_energy, alsv_last_error, alsv_mlmc_accumulate, alsv_mlmc_bytes,
-                   alsv_mlmc_read, alsv_mlmc_reset, alsv_point_pdf_accumulate,
+                   alsv_correlator_accumulate, alsv_joint_pdf_accumulate, alsv_mlmc_read, alsv_mlmc_reset,
+                   alsv_point_pdf_accumulate,
                    alsv_structure_function_accumulate, alsv_structure_function_bytes,
                    alsv_structure_function_read, alsv_num_samples,
                    alsv_num_tile_variants, alsv_num_vars, alsv_set_graphs, alsv_set_initial_data,

@@ -74,6 +74,9 @@ SIGNATURES = {
     "alsv_stats_merge": (C.c_int, [_ctx, _vp, _vp, _sz]),
     "alsv_conservation_totals": (C.c_int, [_ctx, _vp]),
     "alsv_point_pdf_accumulate": (C.c_int, [_ctx, C.c_int, _vp, C.c_int, C.c_double, C.c_double, C.c_int, _vp]),
+    "alsv_joint_pdf_accumulate": (C.c_int, [_ctx, C.c_int, C.c_int, _vp, C.c_int, C.c_double, C.c_double, C.c_int,
+                                            C.c_double, C.c_double, C.c_int, _vp]),
+    "alsv_correlator_accumulate": (C.c_int, [_ctx, C.c_int, _vp, C.c_int, C.c_int, _vp]),
     "alsv_structure_function_bytes": (_sz, [_ctx, C.c_int]),
     "alsv_structure_function_accumulate": (C.c_int, [_ctx, C.c_int, C.c_int, C.c_int, _vp, _sz]),
     "alsv_structure_function_read": (C.c_int, [_ctx, _vp, C.c_int, C.c_int, _vp]),
@@ -244,6 +247,19 @@ def alsv_stats_merge(ctx, stats, other):
 def alsv_point_pdf_accumulate(ctx, quantity: int, cells, lo: float, hi: float, n_bins: int, counts):
     _check(load().alsv_point_pdf_accumulate(ctx, quantity, _ptr(cells), int(cells.numel()), lo, hi, n_bins,
                                             _ptr(counts)), "alsv_point_pdf_accumulate", ctx)
+
+
+def alsv_joint_pdf_accumulate(ctx, q1: int, q2: int, cells, lo1: float, hi1: float, n_bins1: int, lo2: float,
+                              hi2: float, n_bins2: int, counts):
+    _check(load().alsv_joint_pdf_accumulate(ctx, q1, q2, _ptr(cells), int(cells.numel()), lo1, hi1, n_bins1, lo2, hi2,
+                                            n_bins2, _ptr(counts)), "alsv_joint_pdf_accumulate", ctx)
+
+
+def alsv_correlator_accumulate(ctx, quantity: int, cells, acc):
+    """cells: int64 [n_sets, k] device tensor; acc: FP64 [1 + n_sets]."""
+    n_sets, k = int(cells.shape[0]), int(cells.shape[1])
+    _check(load().alsv_correlator_accumulate(ctx, quantity, _ptr(cells), n_sets, k, _ptr(acc)),
+           "alsv_correlator_accumulate", ctx)
 
 
 def alsv_structure_function_bytes(ctx, radius: int) -> int:

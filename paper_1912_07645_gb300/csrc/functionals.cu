@@ -1,10 +1,13 @@
-// Statistical functionals over the samples of a batch (Sec. 2.2 lists point PDFs and two-point
-// structure functions among the on-device statistics). Quantities are the primitive variables
-// (rho, u_k, p) (Burgers: u), computed in FP64 from the stored state.
+// Statistical functionals over the samples of a batch (Sec. 2.2 lists point PDFs, two-point
+// structure functions, joint PDFs and multi-point correlators among the on-device statistics).
+// Quantities are the primitive variables (rho, u_k, p) (Burgers: u), computed in FP64 from the
+// stored state.
 //
 // Point PDF: histogram counts of one quantity at given cells over the samples; bin 0 takes values
 // below lo, bins 1..n_bins the equal-width bins of [lo, hi), bin n_bins + 1 the values >= hi (and
-// NaN). Integer counts (exact in any order).
+// NaN). Integer counts (exact in any order). Joint PDF: the same bins for two quantities at one
+// cell. Multi-point correlator: E[prod_j q(x_j)] over a set of k cells, an FP64 sum over samples
+// in ascending order.
 //
 // Structure function of order p (p = 1 or 2) at radius r, reading of the ball form:
 //   S_p(r) = ( E[ sum_x sum_{k in Z^d, 0 < |k| <= r} |q(x + k dx) - q(x)|^p dV^2 ] )^(1/p),
@@ -38,6 +41,16 @@ __device__ __forceinline__ double quantity(const R* U, long long C, long long i,
 }
 
 // ------------------------------------------------------------------------------ point PDF
+__device__ __forceinline__ int pdf_bin(double x, double lo, double hi, int n_bins) {
+    if (x < lo) return 0;
+    if (x < hi) {
+        int k = (int)floor((x - lo) / (hi - lo) * (double)n_bins);
+        if (k > n_bins - 1) k = n_bins - 1;
+        return 1 + k;
+    }
+    return n_bins + 1;   // >= hi or NaN
+}
+
 template <class R>
 __global__ void k_point_pdf(const GridArgs g, const void* Uv, int q, const int64_t* cells, int n_points, double lo,
                             double hi, int n_bins, unsigned long long* counts) {
@@ -49,17 +62,46 @@ __global__ void k_point_pdf(const GridArgs g, const void* Uv, int q, const int64
     const int b = (int)(t / n_points);
     const R* U = reinterpret_cast<const R*>(Uv) + (long long)b * g.nv * C;
     const double x = quantity<R>(U, C, cells[pt], q, g.nv, g.nv > 1, g.gamma - 1.0);
-    int bin;
-    if (x < lo) {
-        bin = 0;
-    } else if (x < hi) {
-        int k = (int)floor((x - lo) / (hi - lo) * (double)n_bins);
-        if (k > n_bins - 1) k = n_bins - 1;
-        bin = 1 + k;
-    } else {
-        bin = n_bins + 1;   // >= hi or NaN
+    atomicAdd(counts + (long long)pt * (n_bins + 2) + pdf_bin(x, lo, hi, n_bins), 1ull);
+}
+
+// ------------------------------------------------------------------------------ joint PDF
+template <class R>
+__global__ void k_joint_pdf(const GridArgs g, const void* Uv, int q1, int q2, const int64_t* cells, int n_points,
+                            double lo1, double hi1, int nb1, double lo2, double hi2, int nb2,
+                            unsigned long long* counts) {
+    const LevelInfo& L = g.lev[0];
+    const long long C = (long long)L.n[0] * L.n[1] * L.n[2];
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)n_points * L.samples) return;
+    const int pt = (int)(t % n_points);
+    const int b = (int)(t / n_points);
+    const R* U = reinterpret_cast<const R*>(Uv) + (long long)b * g.nv * C;
+    const double x1 = quantity<R>(U, C, cells[pt], q1, g.nv, g.nv > 1, g.gamma - 1.0);
+    const double x2 = quantity<R>(U, C, cells[pt], q2, g.nv, g.nv > 1, g.gamma - 1.0);
+    const int k1 = pdf_bin(x1, lo1, hi1, nb1), k2 = pdf_bin(x2, lo2, hi2, nb2);
+    atomicAdd(counts + ((long long)pt * (nb1 + 2) + k1) * (nb2 + 2) + k2, 1ull);
+}
+
+// ------------------------------------------------------------------------------ correlators
+// acc[0] += samples; acc[1 + s] += sum over samples (ascending) of prod_j q(cells[s][j]) (FP64)
+template <class R>
+__global__ void k_correlator(const GridArgs g, const void* Uv, int q, const int64_t* cells, int n_sets, int k,
+                             double* acc) {
+    const LevelInfo& L = g.lev[0];
+    const long long C = (long long)L.n[0] * L.n[1] * L.n[2];
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s == 0 && threadIdx.x == 0 && blockIdx.x == 0) acc[0] = acc[0] + (double)L.samples;
+    if (s >= n_sets) return;
+    double sum = 0.0;
+    for (int b = 0; b < L.samples; ++b) {
+        const R* U = reinterpret_cast<const R*>(Uv) + (long long)b * g.nv * C;
+        double prod = 1.0;
+        for (int j = 0; j < k; ++j)
+            prod = prod * quantity<R>(U, C, cells[(long long)s * k + j], q, g.nv, g.nv > 1, g.gamma - 1.0);
+        sum = sum + prod;
     }
-    atomicAdd(counts + (long long)pt * (n_bins + 2) + bin, 1ull);
+    acc[1 + s] = acc[1 + s] + sum;
 }
 
 // ------------------------------------------------------------------------------ structure functions
@@ -243,6 +285,47 @@ alsv_status alsv_point_pdf_accumulate(alsv_ctx* c, int quantity_index, const int
     else k_point_pdf<float><<<grid, 256, 0, c->stream>>>(c->g, c->U, quantity_index, cells_dev, n_points, lo, hi, n_bins, cnt);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return ctx_cuda_fail(c, e, "point PDF kernel");
+    c->launches++;
+    return ALSV_OK;
+}
+
+alsv_status alsv_joint_pdf_accumulate(alsv_ctx* c, int q1, int q2, const int64_t* cells_dev, int n_points, double lo1,
+                                      double hi1, int n_bins1, double lo2, double hi2, int n_bins2, int64_t* counts_dev) {
+    if (!c) return ALSV_ERR_INVALID_ARG;
+    if (!c->U) return ctx_fail(c, ALSV_ERR_NOT_READY, "no state bound (alsv_set_initial_data)");
+    if (c->g.nlev != 1) return ctx_fail(c, ALSV_ERR_INVALID_ARG, "joint PDFs need a single-level context");
+    if (q1 < 0 || q1 >= c->nv || q2 < 0 || q2 >= c->nv) return ctx_fail(c, ALSV_ERR_INVALID_ARG, "quantity index out of range");
+    if (!cells_dev || !counts_dev || n_points < 1) return ctx_fail(c, ALSV_ERR_INVALID_ARG, "null cells/counts or no points");
+    if (n_bins1 < 1 || n_bins2 < 1 || !(hi1 > lo1) || !(hi2 > lo2))
+        return ctx_fail(c, ALSV_ERR_INVALID_ARG, "need n_bins >= 1 and hi > lo for both quantities");
+    const long long n = (long long)n_points * c->g.lev[0].samples;
+    const unsigned grid = (unsigned)((n + 255) / 256);
+    auto* cnt = reinterpret_cast<unsigned long long*>(counts_dev);
+    if (c->fp64)
+        k_joint_pdf<double><<<grid, 256, 0, c->stream>>>(c->g, c->U, q1, q2, cells_dev, n_points, lo1, hi1, n_bins1, lo2, hi2,
+                                                        n_bins2, cnt);
+    else
+        k_joint_pdf<float><<<grid, 256, 0, c->stream>>>(c->g, c->U, q1, q2, cells_dev, n_points, lo1, hi1, n_bins1, lo2, hi2,
+                                                       n_bins2, cnt);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return ctx_cuda_fail(c, e, "joint PDF kernel");
+    c->launches++;
+    return ALSV_OK;
+}
+
+alsv_status alsv_correlator_accumulate(alsv_ctx* c, int quantity_index, const int64_t* cells_dev, int n_sets, int k,
+                                       double* acc_dev) {
+    if (!c) return ALSV_ERR_INVALID_ARG;
+    if (!c->U) return ctx_fail(c, ALSV_ERR_NOT_READY, "no state bound (alsv_set_initial_data)");
+    if (c->g.nlev != 1) return ctx_fail(c, ALSV_ERR_INVALID_ARG, "correlators need a single-level context");
+    if (quantity_index < 0 || quantity_index >= c->nv) return ctx_fail(c, ALSV_ERR_INVALID_ARG, "quantity index out of range");
+    if (!cells_dev || !acc_dev || n_sets < 1 || k < 1 || k > 8)
+        return ctx_fail(c, ALSV_ERR_INVALID_ARG, "need cells, an accumulator, n_sets >= 1 and 1 <= k <= 8");
+    const unsigned grid = (unsigned)((n_sets + 127) / 128);
+    if (c->fp64) k_correlator<double><<<grid, 128, 0, c->stream>>>(c->g, c->U, quantity_index, cells_dev, n_sets, k, acc_dev);
+    else k_correlator<float><<<grid, 128, 0, c->stream>>>(c->g, c->U, quantity_index, cells_dev, n_sets, k, acc_dev);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return ctx_cuda_fail(c, e, "correlator kernel");
     c->launches++;
     return ALSV_OK;
 }

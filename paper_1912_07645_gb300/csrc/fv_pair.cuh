@@ -23,7 +23,9 @@ constexpr size_t pair_smem_bytes() {
 }
 
 template <int RECON, int FLUX, int TX, int TY, int NT>
-__global__ void __launch_bounds__(NT, 5) k_stage2d_pair(const StageArgs p) {
+// 32x16 tiles run 4 CTAs per SM with up to 64 registers (no spills with the loads hoisted);
+// 32x8 tiles 5 CTAs (measured best for each)
+__global__ void __launch_bounds__(NT, TY >= 16 ? 4 : 5) k_stage2d_pair(const StageArgs p) {
     constexpr int G = RECON == REC_PC ? 1 : 2;
     constexpr int SX = TX + 2 * G, SY = TY + 2 * G, NS = SX * SY;
     constexpr int NIX = (TX + 1) * TY, NIY = TX * (TY + 1);
@@ -65,30 +67,49 @@ __global__ void __launch_bounds__(NT, 5) k_stage2d_pair(const StageArgs p) {
     const float gamma = (float)g.gamma, gm1 = gamma - 1.0f, inv_gm1 = 1.0f / gm1;
     const int tid = threadIdx.x;
 
-    // ---- 1. tile + halo load (both samples), boundary fill, primitive conversion
+    // ---- 1. tile + halo load (both samples), boundary fill, primitive conversion. The loads of
+    // a group of LG halo cells are all issued before the first is used, so they are in flight
+    // together instead of one cell's round trip at a time.
     const bool interior = tx0 >= G && tx0 + SX - G <= nx && ty0 >= G && ty0 + SY - G <= ny;
+    constexpr int ITER = (NS + NT - 1) / NT;
+    constexpr int LG = ITER < 2 ? ITER : 2;
 #pragma unroll 1
-    for (int s = tid; s < NS; s += NT) {
-        const int sx = s % SX, sy = s / SX;
-        bool fx = false, fy = false;
-        int ix = tx0 + sx - G, iy = ty0 + sy - G;
-        if (!interior) {
-            ix = map_ghost(ix, nx, g.bc[0][0], g.bc[0][1], fx);
-            iy = map_ghost(iy, ny, g.bc[1][0], g.bc[1][1], fy);
+    for (int it0 = 0; it0 < ITER; it0 += LG) {
+        float2 r[LG], mx[LG], my[LG], E[LG];
+        bool fxs[LG], fys[LG];
+#pragma unroll
+        for (int j = 0; j < LG; ++j) {
+            const int s = tid + (it0 + j) * NT;
+            fxs[j] = false;
+            fys[j] = false;
+            if (s < NS) {
+                const int sx = s % SX, sy = s / SX;
+                int ix = tx0 + sx - G, iy = ty0 + sy - G;
+                if (!interior) {
+                    ix = map_ghost(ix, nx, g.bc[0][0], g.bc[0][1], fxs[j]);
+                    iy = map_ghost(iy, ny, g.bc[1][0], g.bc[1][1], fys[j]);
+                }
+                const int off = iy * nx + ix;
+                r[j] = make_float2(UsA[off], UsB[off]);
+                mx[j] = make_float2(UsA[plane + off], UsB[plane + off]);
+                my[j] = make_float2(UsA[2 * plane + off], UsB[2 * plane + off]);
+                E[j] = make_float2(UsA[3 * plane + off], UsB[3 * plane + off]);
+            }
         }
-        const int off = iy * nx + ix;
-        float2 r = make_float2(UsA[off], UsB[off]);
-        float2 mx = make_float2(UsA[plane + off], UsB[plane + off]);
-        float2 my = make_float2(UsA[2 * plane + off], UsB[2 * plane + off]);
-        const float2 E = make_float2(UsA[3 * plane + off], UsB[3 * plane + off]);
-        if (fx) mx = neg2(mx);
-        if (fy) my = neg2(my);
-        const float2 inv = rcp2(r);
-        const float2 u = mul2(mx, inv), v = mul2(my, inv);
-        const float2 m2 = fma2(mx, mx, mul2(my, my));
-        const float2 pr = mul2(f2(gm1), fma2(mul2(f2(-0.5f), m2), inv, E));
-        sW0[s] = make_float4(r.x, r.y, u.x, u.y);
-        sW1[s] = make_float4(v.x, v.y, pr.x, pr.y);
+#pragma unroll
+        for (int j = 0; j < LG; ++j) {
+            const int s = tid + (it0 + j) * NT;
+            if (s >= NS) continue;
+            float2 mxj = mx[j], myj = my[j];
+            if (fxs[j]) mxj = neg2(mxj);
+            if (fys[j]) myj = neg2(myj);
+            const float2 inv = rcp2(r[j]);
+            const float2 u = mul2(mxj, inv), v = mul2(myj, inv);
+            const float2 m2 = fma2(mxj, mxj, mul2(myj, myj));
+            const float2 pr = mul2(f2(gm1), fma2(mul2(f2(-0.5f), m2), inv, E[j]));
+            sW0[s] = make_float4(r[j].x, r[j].y, u.x, u.y);
+            sW1[s] = make_float4(v.x, v.y, pr.x, pr.y);
+        }
     }
 
     float2 acc[CPT][4];
@@ -189,12 +210,23 @@ __global__ void __launch_bounds__(NT, 5) k_stage2d_pair(const StageArgs p) {
         const int x = tx0 + c % TX, y = ty0 + c / TX;
         if (x >= nx || y >= ny) continue;
         const int off = y * nx + x;
+        // all reads of the cell first (the last stage writes in place over U^n: each element is
+        // read by the thread that writes it, before the write)
+        float2 us[4], un[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) us[v] = make_float2(UsA[v * plane + off], UsB[v * plane + off]);
+        if (has_un) {
+#pragma unroll
+            for (int v = 0; v < 4; ++v) un[v] = make_float2(UnA[v * plane + off], UnB[v * plane + off]);
+        }
         float2 o[4];
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-            const float2 us = make_float2(UsA[v * plane + off], UsB[v * plane + off]);
-            o[v] = fma2(dt, acc[m][v], us);
-            if (has_un) o[v] = fma2(ca, make_float2(UnA[v * plane + off], UnB[v * plane + off]), mul2(cb, o[v]));
+            o[v] = fma2(dt, acc[m][v], us[v]);
+            if (has_un) o[v] = fma2(ca, un[v], mul2(cb, o[v]));
+        }
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
             if (!doneA) UoA[v * plane + off] = o[v].x;
             if (!doneB) UoB[v * plane + off] = o[v].y;
         }

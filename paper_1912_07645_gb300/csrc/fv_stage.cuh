@@ -339,15 +339,23 @@ __global__ void __launch_bounds__(NT) k_stage(const StageArgs p) {
         const int z = tz0 + (ND >= 3 ? c / (TX * TY) : 0);
         if (x >= nx || y >= ny || z >= nz) continue;
         const int off = (z * ny + y) * nx + x;
-        R out[NV];
+        // all reads of the cell first (the last stage writes in place over U^n: each element is
+        // read by the thread that writes it, before the write)
+        R us[NV], un[NV], out[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) us[v] = Us[v * plane + off];
+        if (has_un) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) un[v] = Un[v * plane + off];
+        }
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-            const R us = Us[v * plane + off];
-            R o = us + dt * acc[m][v];
-            if (has_un) o = ca * Un[v * plane + off] + cb * o;
+            R o = us[v] + dt * acc[m][v];
+            if (has_un) o = ca * un[v] + cb * o;
             out[v] = o;
-            Uo[v * plane + off] = o;
         }
+#pragma unroll
+        for (int v = 0; v < NV; ++v) Uo[v * plane + off] = out[v];
         if (want_speed) {
             if (EQ == EQ_BURGERS) {
                 const R au = fabs_(out[0]);

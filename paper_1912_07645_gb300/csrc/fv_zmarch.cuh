@@ -163,7 +163,15 @@ __global__ void __launch_bounds__(TX * TY, 4) k_stage3d_zm(const StageArgs p) {
         if (own) {
             const int fxm = cy * (TX + 1) + cx, fym = cy * TX + cx;
             const int off = (z * ny + Y) * nx + X;
-            R out[NV];
+            // all reads of the cell first (the last stage writes in place over U^n: each element
+            // is read by the thread that writes it, before the write)
+            R us[NV], un[NV], out[NV];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) us[v] = Us[v * plane + off];
+            if (has_un) {
+#pragma unroll
+                for (int v = 0; v < NV; ++v) un[v] = Un[v * plane + off];
+            }
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
                 // directions accumulated x, y, z as in the tile kernel (same rounding)
@@ -171,11 +179,12 @@ __global__ void __launch_bounds__(TX * TY, 4) k_stage3d_zm(const StageArgs p) {
                 Lv = Lv - (sFx[(fxm + 1) * CS + v] - sFx[fxm * CS + v]) * idx;
                 Lv = Lv - (sFy[(fym + TX) * CS + v] - sFy[fym * CS + v]) * idy;
                 Lv = Lv - (Fzp[v] - Fzm[v]) * idz;
-                R o = Us[v * plane + off] + dt * Lv;
-                if (has_un) o = ca * Un[v * plane + off] + cb * o;
+                R o = us[v] + dt * Lv;
+                if (has_un) o = ca * un[v] + cb * o;
                 out[v] = o;
-                Uo[v * plane + off] = o;
             }
+#pragma unroll
+            for (int v = 0; v < NV; ++v) Uo[v * plane + off] = out[v];
             if (want_speed) {
                 R wv[NV];
                 cons_to_prim<R, ND>(out, wv, gm1);

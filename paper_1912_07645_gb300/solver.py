@@ -194,6 +194,26 @@ class Solver:
         A.alsv_point_pdf_accumulate(self.ctx, quantity, cells, lo, hi, n_bins, counts)
         return counts
 
+    def joint_pdf(self, q1, q2, cells, lo1, hi1, n_bins1, lo2, hi2, n_bins2, counts=None):
+        """Add this batch to the joint counts (int64 [points, n_bins1 + 2, n_bins2 + 2])."""
+        torch = self.torch
+        with torch.cuda.stream(self.stream):
+            cells = torch.as_tensor(cells, dtype=torch.int64).to(self.device)
+            if counts is None:
+                counts = torch.zeros((cells.numel(), n_bins1 + 2, n_bins2 + 2), dtype=torch.int64, device=self.device)
+        A.alsv_joint_pdf_accumulate(self.ctx, q1, q2, cells, lo1, hi1, n_bins1, lo2, hi2, n_bins2, counts)
+        return counts
+
+    def correlator(self, quantity, cell_sets, acc=None):
+        """Add this batch to acc (FP64 [1 + sets]: sample count, then sums of prod_j q(x_j))."""
+        torch = self.torch
+        with torch.cuda.stream(self.stream):
+            cells = torch.as_tensor(cell_sets, dtype=torch.int64).to(self.device)
+            if acc is None:
+                acc = torch.zeros(1 + cells.shape[0], dtype=torch.float64, device=self.device)
+        A.alsv_correlator_accumulate(self.ctx, quantity, cells, acc)
+        return acc
+
     def structure_function(self, quantity, p, radius, acc=None):
         """Fold this batch into the accumulator (new when None) and return (acc, S_p(1..radius))."""
         torch = self.torch

@@ -1,5 +1,6 @@
-"""Point PDFs and structure functions (Sec. 2.2) on the GPU against the oracle's definitions,
-evaluated on the GPU's own states (the quantities are FP64 on both sides)."""
+"""Point and joint PDFs, multi-point correlators and structure functions (Sec. 2.2) on the GPU
+against the oracle's definitions, evaluated on the GPU's own states (the quantities are FP64 on
+both sides)."""
 import numpy as np
 import pytest
 
@@ -116,3 +117,19 @@ def test_functionals_reject_bad_arguments():
     with pytest.raises(alsv.AlsvError):
         S.point_pdf(0, [0], 1.0, 1.0, 4)
     S.close()
+
+
+def test_joint_pdf_and_correlators():
+    S = kh_run((48, 40), 16, "fp32", 5)
+    nx = 48
+    cells = [0, 9 * nx + 3, 20 * nx + 30]
+    c = S.joint_pdf(0, 3, cells, 0.8, 2.2, 6, 2.3, 2.7, 5)
+    sets = [[9 * nx + 3], [9 * nx + 3, 9 * nx + 4], [0, 20 * nx + 30, 39 * nx + 47]]
+    acc = S.correlator(1, sets)
+    U = host(S.U).reshape(S.level_shape(0))
+    got, accv = host(c).astype(np.int64), host(acc)
+    S.close()
+    np.testing.assert_array_equal(got, oracle.joint_pdf(U, 0, 3, cells, 0.8, 2.2, 6, 2.3, 2.7, 5))
+    n, sums = oracle.correlator(U, 1, sets)
+    assert accv[0] == n == 16
+    np.testing.assert_allclose(accv[1:], sums, rtol=1e-13, atol=1e-15)

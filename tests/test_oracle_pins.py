@@ -721,3 +721,25 @@ def test_bench_flop_constant_matches_the_count():
     assert m, "bench.py must state the flop count"
     d = oracle.make_desc(ndim=2, n=(8, 8), eq="euler", recon="weno3", flux="hllc", rvars="prim", rk="ssprk3")
     assert int(m.group(1)) == oracle.count_flops(d)["per_cell_update"]
+
+
+def test_joint_pdf_and_correlator_by_hand():
+    # two quantities (scalar data in two "variables" read without conversion) at two cells, three samples
+    U = np.array([[[1.0, 4.0], [0.2, 0.9]],
+                  [[2.0, 5.0], [0.6, 0.1]],
+                  [[3.0, 6.0], [0.7, 0.4]]]).reshape(3, 2, 1, 1, 2)
+    # q0 bins on [0, 4) with 2 bins: 1 -> 1, 2 -> 2, 3 -> 2, 4, 5, 6 -> overflow 3
+    # q1 bins on [0, 1) with 2 bins: 0.2 -> 1, 0.6 -> 2, 0.7 -> 2, 0.9 -> 2, 0.1 -> 1, 0.4 -> 1
+    c = oracle.joint_pdf(U, 0, 1, [0, 1], 0.0, 4.0, 2, 0.0, 1.0, 2, euler=False)
+    expect = np.zeros((2, 4, 4), dtype=np.int64)
+    expect[0, 1, 1] = 1      # (1, 0.2)
+    expect[0, 2, 2] = 2      # (2, 0.6), (3, 0.7)
+    expect[1, 3, 2] = 1      # (4, 0.9)
+    expect[1, 3, 1] = 2      # (5, 0.1), (6, 0.4)
+    np.testing.assert_array_equal(c, expect)
+    # marginals of the joint PDF are the point PDFs
+    np.testing.assert_array_equal(c.sum(axis=2), oracle.point_pdf(U, 0, [0, 1], 0.0, 4.0, 2, euler=False))
+    # correlators of q0: <x0> = 2, <x0 x1> = (4 + 10 + 18)/3, <x0 x0 x1> = (4 + 20 + 54)/3
+    n, sums = oracle.correlator(U, 0, [[0], [0, 1], [0, 0, 1]], euler=False)
+    assert n == 3
+    np.testing.assert_array_equal(sums, [6.0, 32.0, 78.0])

@@ -312,7 +312,10 @@ def run_workload(name, args):
         return 0
     chosen, ms_var = (0, [])
     S.set_initial_data(W["init"])
-    if alsv.alsv_num_tile_variants(S.ctx) > 1:
+    if args.tile_variant >= 0:
+        alsv.alsv_set_tile_variant(S.ctx, args.tile_variant)
+        chosen = args.tile_variant
+    elif alsv.alsv_num_tile_variants(S.ctx) > 1:
         chosen, ms_var = alsv.alsv_autotune(S.ctx, 3)
     cells = [int(np.prod(desc.level_n[l][:desc.ndim])) for l in range(desc.n_levels)] if desc.n_levels > 1 else \
         [int(np.prod(list(desc.n)[:desc.ndim]))]
@@ -394,6 +397,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--samples", type=int, default=M, help="samples per GPU (default 4096; fewer for profiling runs)")
     ap.add_argument("--T", type=float, default=T_END, help="end time (default 1; shorter for profiling runs)")
+    ap.add_argument("--tile-variant", type=int, default=-1,
+                    help="skip the autotuner and run this stage schedule (profiler runs, where timing the "
+                         "candidates under the profiler would pick another one)")
     ap.add_argument("--workload", default="mc", choices=["mc"] + sorted(WORKLOADS),
                     help="mc (default): batched Monte Carlo KH 256^2 x 4096; others: the remaining configurations")
     args = ap.parse_args()
@@ -423,7 +429,11 @@ def main():
     with torch.cuda.stream(S.stream):
         S.tot = torch.empty((Mr, 4), dtype=torch.float64, device=dev)
     S.set_initial_data("kh")
-    chosen, ms_var = alsv.alsv_autotune(S.ctx, 3)
+    if args.tile_variant >= 0:
+        alsv.alsv_set_tile_variant(S.ctx, args.tile_variant)
+        chosen, ms_var = args.tile_variant, []
+    else:
+        chosen, ms_var = alsv.alsv_autotune(S.ctx, 3)
 
     def barrier():
         torch.cuda.synchronize()

@@ -124,12 +124,16 @@ def test_joint_pdf_and_correlators():
     nx = 48
     cells = [0, 9 * nx + 3, 20 * nx + 30]
     c = S.joint_pdf(0, 3, cells, 0.8, 2.2, 6, 2.3, 2.7, 5)
-    sets = [[9 * nx + 3], [9 * nx + 3, 9 * nx + 4], [0, 20 * nx + 30, 39 * nx + 47]]
-    acc = S.correlator(1, sets)
+    # one call per set size k (a call takes sets of one size)
+    sets2 = [[9 * nx + 3, 9 * nx + 4], [5, 5], [0, 39 * nx + 47]]
+    sets3 = [[0, 20 * nx + 30, 39 * nx + 47], [7 * nx, 7 * nx + 1, 7 * nx + 2]]
+    acc2 = S.correlator(1, sets2)
+    acc3 = S.correlator(3, sets3)
     U = host(S.U).reshape(S.level_shape(0))
-    got, accv = host(c).astype(np.int64), host(acc)
+    got, a2, a3 = host(c).astype(np.int64), host(acc2), host(acc3)
     S.close()
     np.testing.assert_array_equal(got, oracle.joint_pdf(U, 0, 3, cells, 0.8, 2.2, 6, 2.3, 2.7, 5))
-    n, sums = oracle.correlator(U, 1, sets)
-    assert accv[0] == n == 16
-    np.testing.assert_allclose(accv[1:], sums, rtol=1e-13, atol=1e-15)
+    for acc, q, sets in ((a2, 1, sets2), (a3, 3, sets3)):
+        n, sums = oracle.correlator(U, q, sets)
+        assert acc[0] == n == 16
+        np.testing.assert_allclose(acc[1:], sums, rtol=1e-13, atol=1e-15)

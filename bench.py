@@ -18,6 +18,7 @@ import math
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -68,7 +69,9 @@ class ClockSampler:
     def __init__(self, gpu_index=0):
         self.idx = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        # the raw samples go to BENCH_CLOCK_DIR when set (to keep them), else to a temporary folder
+        d = os.environ.get("BENCH_CLOCK_DIR") or tempfile.mkdtemp(prefix="bench_clocks_")
+        self.path = os.path.join(d, f"clocks_rank{gpu_index}.csv")
 
     def start(self):
         try:
@@ -235,7 +238,8 @@ def reference_arm(args):
 
 
 # ------------------------------------------------------------------------------------------------
-# Other configurations (SURVEY configs 1, 2, 3-MLMC, 4, 5): same JSON contract, one GPU.
+# Other configurations (1D Sod, KH 2D 1024^2, uneven and coupled MLMC levels, the adjoint, the 3D
+# slab): same JSON contract, one GPU.
 # bytes per cell-update: per variable read U^n + write U1 (stage 1), read U^(s) + U^n + write (later
 # stages): RK2 = 5 words, RK3 = 8 words.
 WORKLOADS = {

@@ -542,7 +542,7 @@ def test_fixed_dt_cfl_guard():
 
 def test_checkpoint_resume_is_bitwise():
     """Evolve 0 -> T/2, checkpoint (U, t, steps), resume in a new context, evolve to T: bitwise
-    equal to one uninterrupted evolve to T (checkpoint/resume)."""
+    equal to one uninterrupted evolve to T (checkpoint and resume)."""
     torch = torch_()
     import paper_1912_07645_gb300 as alsv
     cfg = dict(ndim=2, n=(64, 48), batch=3, eq="euler", recon="weno3", flux="hllc", rvars="prim", rk="ssprk3",

@@ -135,27 +135,27 @@ __global__ void __launch_bounds__(TX * TY, 4) k_stage3d_zm(const StageArgs p) {
         __syncthreads();
         const int pz = ((z % NP) + NP) % NP;
         const R* sp = sW + pz * PS * CS;
-        // x interfaces of plane z: (TX + 1) x TY
+        // x interfaces of plane z ((TX + 1) x TY), then its y interfaces (TX x (TY + 1)), as one
+        // loop so that only its last pass leaves threads idle before the barrier
 #pragma unroll 1
-        for (int f = tid; f < NIX; f += NT) {
-            const int fx = f % (TX + 1), fy = f / (TX + 1);
-            const int i0 = (fy + G) * SX + fx + G - 1;
+        for (int f = tid; f < NIX + NIY; f += NT) {
             R WL[NV], WR[NV], F[NV];
-            interface_states<R, EQ_EULER, ND, RECON, CS>(sp, i0, 1, rv, gm1, epsx, WL, WR);
-            euler_flux<R, ND, 0, FLUX>(WL, WR, F, gamma, gm1, inv_gm1);
+            if (f < NIX) {
+                const int fx = f % (TX + 1), fy = f / (TX + 1);
+                const int i0 = (fy + G) * SX + fx + G - 1;
+                interface_states<R, EQ_EULER, ND, RECON, CS>(sp, i0, 1, rv, gm1, epsx, WL, WR);
+                euler_flux<R, ND, 0, FLUX>(WL, WR, F, gamma, gm1, inv_gm1);
 #pragma unroll
-            for (int v = 0; v < NV; ++v) sFx[f * CS + v] = F[v];
-        }
-        // y interfaces: TX x (TY + 1)
-#pragma unroll 1
-        for (int f = tid; f < NIY; f += NT) {
-            const int fx = f % TX, fy = f / TX;
-            const int i0 = (fy + G - 1) * SX + fx + G;
-            R WL[NV], WR[NV], F[NV];
-            interface_states<R, EQ_EULER, ND, RECON, CS>(sp, i0, SX, rv, gm1, epsy, WL, WR);
-            euler_flux<R, ND, 1, FLUX>(WL, WR, F, gamma, gm1, inv_gm1);
+                for (int v = 0; v < NV; ++v) sFx[f * CS + v] = F[v];
+            } else {
+                const int fi = f - NIX;
+                const int fx = fi % TX, fy = fi / TX;
+                const int i0 = (fy + G - 1) * SX + fx + G;
+                interface_states<R, EQ_EULER, ND, RECON, CS>(sp, i0, SX, rv, gm1, epsy, WL, WR);
+                euler_flux<R, ND, 1, FLUX>(WL, WR, F, gamma, gm1, inv_gm1);
 #pragma unroll
-            for (int v = 0; v < NV; ++v) sFy[f * CS + v] = F[v];
+                for (int v = 0; v < NV; ++v) sFy[fi * CS + v] = F[v];
+            }
         }
         R Fzp[NV];
         zflux(z, Fzp);

@@ -219,3 +219,37 @@ def test_mlmc_coupling_validation(alsv):
         assert alsv.alsv_mlmc_bytes(ctx) == 0
     finally:
         alsv.alsv_destroy(ctx)
+
+
+def test_size_limits_and_sampler_validation(alsv):
+    # the largest batch a context holds, one past it, and a sample of 2^31 or more elements
+    ctx, _ = alsv.alsv_init_grid(alsv.make_desc(ndim=1, n=(4,), batch=65535, recon="pc"), 0)
+    alsv.alsv_destroy(ctx)
+    with pytest.raises(alsv.AlsvError, match="65535"):
+        alsv.alsv_init_grid(alsv.make_desc(ndim=1, n=(4,), batch=65536, recon="pc"), 0)
+    with pytest.raises(alsv.AlsvError, match="2\\^31"):
+        alsv.alsv_init_grid(alsv.make_desc(ndim=3, n=(1024, 1024, 1024), precision="fp32"), 0)
+    d = alsv.make_desc(ndim=2, n=(8, 8))
+    d.sampler = 3
+    with pytest.raises(alsv.AlsvError, match="sampler"):
+        alsv.alsv_init_grid(d, 0)
+    with pytest.raises(alsv.AlsvError, match="Halton"):
+        alsv.alsv_init_grid(alsv.make_desc(ndim=2, n=(8, 8), batch=4, sampler="halton",
+                                           sample_offset=(1 << 31) - 2), 0)
+    ctx, _ = alsv.alsv_init_grid(alsv.make_desc(ndim=2, n=(8, 8), batch=4, sampler="halton_shifted",
+                                                sample_offset=(1 << 31) - 5), 0)
+    alsv.alsv_destroy(ctx)
+
+
+def test_statistics_calls_without_a_state_report_not_ready(alsv):
+    import torch
+    ctx, _ = alsv.alsv_init_grid(alsv.make_desc(ndim=2, n=(16, 16), batch=2), 0)
+    buf = torch.zeros(1 << 16, dtype=torch.uint8)   # never touched: the calls fail first
+    try:
+        for call in (lambda: alsv.alsv_structure_function_accumulate(ctx, 0, 1, 2, buf),
+                     lambda: alsv.alsv_mlmc_accumulate(ctx, buf)):
+            with pytest.raises(alsv.AlsvError) as ei:
+                call()
+            assert ei.value.status_name in ("ERR_NOT_READY", "ERR_INVALID_ARG")
+    finally:
+        alsv.alsv_destroy(ctx)

@@ -290,6 +290,8 @@ def run_workload(name, args):
     peaks, peak_kind = measured_peaks()
     if W.get("adjoint"):
         S.set_initial_data("kh")
+        # the forward sweeps run the context's stage schedule: pick the fastest for this shape
+        chosen, ms_var = alsv.alsv_autotune(S.ctx, 3) if alsv.alsv_num_tile_variants(S.ctx) > 1 else (0, [])
         th = torch.empty((S.samples, 20), dtype=torch.float64, device="cuda")
         alsv.alsv_get_parameters(S.ctx, th)
         S.sync()
@@ -308,7 +310,8 @@ def run_workload(name, args):
                 "ms_per_step": 1000 * el / args.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": W["desc"]["precision"], "data": "synthetic (SplitMix64 KH parameters)",
                 "config": {"workload": name, "grid": [512, 512], "samples": S.samples, "T": W["T"],
-                           "fixed_steps": nst, "fixed_dt": dt_fixed, "forward_passes": passes},
+                           "fixed_steps": nst, "fixed_dt": dt_fixed, "forward_passes": passes,
+                           "tile_variant": chosen, "autotune_ms": ms_var},
                 "forward_cell_updates_per_s": S.samples * 512 * 512 * nst * args.steps / el,
                 "gpu_launches": alsv.alsv_get_launch_count(S.ctx)}
         print(json.dumps(line), flush=True)

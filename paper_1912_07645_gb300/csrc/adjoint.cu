@@ -122,7 +122,9 @@ struct AdjStageArgs {
 
 // One CTA per (sample, TX x TY tile), one cell per thread.
 template <class R, int RECON, int TX, int TY, int NT>
-__global__ void __launch_bounds__(NT) k_stage_adj(const AdjStageArgs p) {
+// FP32: 4 CTAs per SM (the shared-memory limit; measured faster than 2 CTAs without spills);
+// FP64: 2 CTAs per SM
+__global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 4 : 2) k_stage_adj(const AdjStageArgs p) {
     static_assert(TX * TY == NT, "one cell per thread");
     constexpr int NV = 4;
     constexpr bool PC = RECON == REC_PC;
@@ -319,13 +321,23 @@ __global__ void __launch_bounds__(NT) k_stage_adj(const AdjStageArgs p) {
     const R* X2 = reinterpret_cast<const R*>(p.X2) + sbase;
     R* out = reinterpret_cast<R*>(p.out) + sbase;
     const int li = (cy + HL) * SLX + cx + HL;
+    R x1[NV], x2[NV], o[NV];
+    if (p.X1) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) x1[v] = X1[v * plane + off];
+    }
+    if (p.X2) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) x2[v] = X2[v * plane + off];
+    }
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-        R o = cb_ * (sL[v * SLX * SLY + li] + dt * Ub[v]);
-        if (p.X1) o = c1 * X1[v * plane + off] + o;
-        if (p.X2) o = c2 * X2[v * plane + off] + o;
-        out[v * plane + off] = o;
+        o[v] = cb_ * (sL[v * SLX * SLY + li] + dt * Ub[v]);
+        if (p.X1) o[v] = c1 * x1[v] + o[v];
+        if (p.X2) o[v] = c2 * x2[v] + o[v];
     }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) out[v * plane + off] = o[v];
 }
 
 template <class R, int RECON, int TX, int TY, int NT>

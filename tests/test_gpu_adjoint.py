@@ -19,9 +19,11 @@ def _lib():
     build.build()
 
 
-def gpu_adjoint(cfg, th, T):
+def gpu_adjoint(cfg, th, T, variant=0):
     import torch
+    import paper_1912_07645_gb300 as alsv
     S = gpu_solver(**cfg)
+    alsv.alsv_set_tile_variant(S.ctx, variant)
     S.set_initial_data("kh", theta=torch.from_numpy(th).cuda())
     J, g = S.adjoint(torch.from_numpy(th), T)
     out = host(J), host(g)
@@ -102,14 +104,16 @@ def test_adjoint_fp64_vs_central_differences():
     assert np.abs(g[0] - fd).max() <= 1e-4 * np.abs(g[0]).max(), (g[0], fd)
 
 
-def test_adjoint_fp32_close_to_fp64_oracle():
+@pytest.mark.parametrize("variant", [0, 4])
+def test_adjoint_fp32_close_to_fp64_oracle(variant):
+    """variant 4: the forward sweeps run the two-sample schedule (the benchmark autotunes it)."""
     n = 32
     cfg = dict(ndim=2, n=(n, n), batch=2, eq="euler", recon="mc", rvars="prim", flux="rusanov", rk="ssprk2",
                bc="periodic", cfl=0.4, precision="fp32")
     T = 0.1
     dt, nsteps = oracle.fixed_dt_kh(n, T, 0.4)
     th = kh_theta(2, 77)
-    J, g = gpu_adjoint(cfg, th, T)
+    J, g = gpu_adjoint(cfg, th, T, variant=variant)
     d = oracle.make_desc(**cfg)
     for b in range(2):
         Jo, go = oracle.ke_grad_kh2d(d, th[b], dt, nsteps)

@@ -637,24 +637,44 @@ alsv_status alsv_evolve_to_T(alsv_ctx* c, double T, int64_t* steps_taken_host) {
     c->launches++;
     const int chunk = 16;
     const size_t S = c->total_samples;
+    // Two polls in flight: the next chunk is enqueued before the host reads the done flags and
+    // status of the previous one (pinned slots), so the GPU does not idle during the round trip.
+    // A chunk that runs after every sample is done changes nothing (stages and time control skip
+    // done samples).
+    const size_t slot_bytes = (S * 4 + 16 + 255) / 256 * 256;
+    if (!c->h_poll) {
+        CK(cudaHostAlloc(reinterpret_cast<void**>(&c->h_poll), 2 * slot_bytes, cudaHostAllocDefault));
+        for (int k = 0; k < 2; ++k) CK(cudaEventCreateWithFlags(&c->poll_ev[k], cudaEventDisableTiming));
+    }
+    auto slot_done = [&](int k) { return reinterpret_cast<int*>(c->h_poll + k * slot_bytes); };
+    auto slot_status = [&](int k) { return reinterpret_cast<int*>(c->h_poll + k * slot_bytes + S * 4); };
+    auto post = [&](int k) -> cudaError_t {
+        cudaError_t ee = cudaMemcpyAsync(slot_done(k), c->done, S * 4, cudaMemcpyDeviceToHost, c->stream);
+        if (ee == cudaSuccess) ee = cudaMemcpyAsync(slot_status(k), c->status, 4, cudaMemcpyDeviceToHost, c->stream);
+        if (ee == cudaSuccess) ee = cudaEventRecord(c->poll_ev[k], c->stream);
+        return ee;
+    };
+    CK(post(0));
+    int cur = 0;
     long long chunks = 0;
     for (;;) {
-        CK(cudaMemcpyAsync(c->h_done.data(), c->done, S * 4, cudaMemcpyDeviceToHost, c->stream));
-        int hs = 0;
-        CK(cudaMemcpyAsync(&hs, c->status, 4, cudaMemcpyDeviceToHost, c->stream));
-        CK(cudaStreamSynchronize(c->stream));
-        prof_collect(c);
+        if (++chunks > (1LL << 26)) return fail(c, ALSV_ERR_TIMEOUT, "evolve_to_T: step limit reached");
+        st = run_chunk(c, chunk);
+        if (st != ALSV_OK) return st;
+        CK(post(cur ^ 1));
+        CK(cudaEventSynchronize(c->poll_ev[cur]));
+        const int hs = *slot_status(cur);
         if (hs & (ST_NONPHYSICAL | ST_CFL)) {
             st = status_to_code(c, hs);
             break;
         }
+        const int* dn = slot_done(cur);
         bool all = true;
-        for (size_t i = 0; i < S; ++i) all = all && c->h_done[i];
+        for (size_t i = 0; i < S && all; ++i) all = dn[i] != 0;
         if (all) break;
-        if (++chunks > (1LL << 26)) return fail(c, ALSV_ERR_TIMEOUT, "evolve_to_T: step limit reached");
-        st = run_chunk(c, chunk);
-        if (st != ALSV_OK) return st;
+        cur ^= 1;
     }
+    prof_collect(c);
     if (steps_taken_host) {
         std::vector<int64_t> ns(S);
         CK(cudaMemcpyAsync(ns.data(), c->nstep, S * 8, cudaMemcpyDeviceToHost, c->stream));
@@ -763,6 +783,11 @@ alsv_status alsv_kinetic_energy(alsv_ctx* c, double* ke_dev) {
 alsv_status alsv_destroy(alsv_ctx* c) {
     if (!c) return ALSV_OK;
     drop_graph(c);
+    if (c->h_poll) {
+        cudaStreamSynchronize(c->stream);
+        for (int k = 0; k < 2; ++k) cudaEventDestroy(c->poll_ev[k]);
+        cudaFreeHost(c->h_poll);
+    }
     for (auto e : c->prof.ev) cudaEventDestroy(e);
     delete c;
     return ALSV_OK;

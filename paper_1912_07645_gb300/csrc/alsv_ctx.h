@@ -56,6 +56,8 @@ struct alsv_ctx {
     bool graphs_enabled = true;
     // host staging
     std::vector<int> h_done;
+    char* h_poll = nullptr;          // pinned: done flags + status of two polls in flight
+    cudaEvent_t poll_ev[2] = {nullptr, nullptr};
     long long launches = 0;
     alsv::Profile prof;
     std::string err;

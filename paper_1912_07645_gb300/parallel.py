@@ -32,6 +32,8 @@ def merge_in_rank_order(solver, gathered):
     """Merge per-rank accumulators (device tensors, rank order) into a fresh accumulator."""
     from . import _abi as A
     torch = solver.torch
+    # the all-gather ran on the current stream: the solver's stream must not start before it ends
+    solver.stream.wait_stream(torch.cuda.current_stream(solver.device))
     with torch.cuda.stream(solver.stream):
         out = torch.zeros_like(gathered[0])
     for t in gathered:

@@ -272,6 +272,10 @@ WORKLOADS = {
     "adjoint512_fp32": dict(desc=dict(ndim=2, n=(512, 512), batch=64, eq="euler", recon="mc", flux="rusanov",
                                       rvars="prim", rk="ssprk2", bc="periodic", cfl=0.4, precision="fp32", seed=SEED),
                             adjoint=True, T=1.0),
+    # the same at T = 0.01 (31 fixed steps), for profiler captures
+    "adjoint512_fp32_short": dict(desc=dict(ndim=2, n=(512, 512), batch=64, eq="euler", recon="mc", flux="rusanov",
+                                            rvars="prim", rk="ssprk2", bc="periodic", cfl=0.4, precision="fp32",
+                                            seed=SEED), adjoint=True, T=0.01),
     "adjoint512_fp64": dict(desc=dict(ndim=2, n=(512, 512), batch=64, eq="euler", recon="mc", flux="rusanov",
                                       rvars="prim", rk="ssprk2", bc="periodic", cfl=0.4, precision="fp64", seed=SEED),
                             adjoint=True, T=0.05),

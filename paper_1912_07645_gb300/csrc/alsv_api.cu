@@ -794,7 +794,7 @@ alsv_status alsv_destroy(alsv_ctx* c) {
 }
 
 // ---------------------------------------------------------------------------------------------
-// Extensions (declared in alsv_ext.h): tile-shape selection/autotuning, launch counting, profiling
+// Execution controls (declared in alsv.h): tile-shape selection/autotuning, launch counting, profiling
 // ---------------------------------------------------------------------------------------------
 alsv_status alsv_set_tile_variant(alsv_ctx* c, int variant) {
     if (!c) return fail(nullptr, ALSV_ERR_INVALID_ARG, "null context");

@@ -152,3 +152,33 @@ def test_estimator_is_deterministic():
     b = run_gpu(cfg_for("fp32", seed=3), 0.03)
     for x, y in zip(a[1:4], b[1:4]):
         np.testing.assert_array_equal(x, y)
+
+
+def test_estimator_3d_levels_and_halton_companions():
+    """3D slab levels 8^3 / 16^3 with a companion, parameters from the Halton sequence: the
+    companion carries its level's parameters and the estimate matches the oracle's on the GPU's
+    states."""
+    import paper_1912_07645_gb300 as alsv
+    lv = [((8, 8, 8), 3), ((16, 16, 16), 2), ((8, 8, 8), 2, 1)]
+    cfg = dict(ndim=3, levels=lv, eq="euler", recon="mc", flux="hllc", rvars="prim", rk="ssprk2", bc="periodic",
+               cfl=0.3, precision="fp64", seed=4, sampler="halton")
+    S = gpu_solver(**cfg)
+    S.set_initial_data("kh")
+    th = S.torch.empty((S.samples, 128), dtype=S.torch.float64, device="cuda")
+    alsv.alsv_get_parameters(S.ctx, th)
+    S.step(3)
+    S.mlmc_accumulate()
+    states = [host(S.state(l)) for l in range(3)]
+    th = host(th)
+    cnt, mean, var, lev = S.mlmc_read()
+    mean, var, lev = host(mean), host(var), host(lev)
+    S.close()
+    ref = oracle.theta_halton(7, 128)
+    np.testing.assert_array_equal(th[:5], ref[:5])
+    np.testing.assert_array_equal(th[5:7], ref[3:5])      # the companion takes level 1's indices
+    assert cnt == [3, 2]
+    levels = [(states[0], None, 1 / 512), (states[1], states[2], 1 / 4096)]
+    m_g, v_g, s_g = oracle.mlmc_estimate(levels)
+    np.testing.assert_allclose(mean, m_g, rtol=1e-13, atol=1e-14)
+    np.testing.assert_allclose(var, v_g, rtol=1e-9, atol=1e-13)
+    np.testing.assert_allclose(lev, s_g, rtol=1e-12, atol=1e-14)

@@ -357,19 +357,25 @@ alsv_status alsv_structure_function_read(alsv_ctx* ctx, const void* acc_dev, int
 alsv_status alsv_destroy(alsv_ctx* ctx);
 
 /*
- * Execution controls (no counterpart in the paper; they choose how the same arithmetic is
- * scheduled on the GPU and never change results).
- *   alsv_num_tile_variants  number of stage-kernel schedules for this (precision, ndim): tiles of
- *                           several shapes and, for FP32 2D Euler on periodic grids with primitive
- *                           WENO3/MC reconstruction and HLLC/Rusanov, a column-marching schedule
+ * Execution controls (no counterpart in the paper; they choose how the same scheme is scheduled
+ * on the GPU: FP64 results and FP32 results of schedules with the same arithmetic are bitwise
+ * equal, other FP32 schedules agree to FP32 rounding).
+ *   alsv_num_tile_variants  number of stage-kernel schedules for this (precision, ndim). FP32 2D:
+ *                           0-2 tiles of 32x16, 32x8, 32x32; 3 column march (periodic, primitive
+ *                           WENO3/MC, HLLC/Rusanov); 4, 5 two samples per thread in packed FP32x2
+ *                           (32x16, 32x8 tiles; primitive, HLLC/Rusanov); 6 the two halves of each
+ *                           sample per thread (as 4, with y periodic and ny divisible by 32).
+ *                           FP32 3D: 0, 1 tiles of 16x8x8, 8x8x8; 2, 3 z-marching 32x8 column
+ *                           chunks of 64 / 128 planes (Euler). 1D: tiles of 256, 64, 32 cells.
  *   alsv_set_tile_variant   select one (recomputes the wave-speed partials; asynchronous;
  *                           ALSV_ERR_INVALID_ARG if the variant does not support the scheme)
  *   alsv_get_tile           current tile shape, variant and (sample, tile) work items per launch
  *   alsv_autotune           time `reps` pairs of launches per variant - a first stage and a
  *                           last-stage-like launch (U^n read, CFL partials), both writing only the
  *                           stage buffer, so the state is unchanged - with CUDA events on the
- *                           context stream and keep the fastest; ms_per_variant (host, may
- *                           be NULL) receives the times (-1 for unsupported variants). SYNCHRONOUS.
+ *                           context stream and keep the fastest (a later variant must beat an
+ *                           earlier one by more than 1 %); ms_per_variant (host, may be NULL)
+ *                           receives the times (-1 for unsupported variants). SYNCHRONOUS.
  *   alsv_set_graphs         1 (default): alsv_evolve_to_T replays captured CUDA graphs of
  *                           16-step chunks; 0: direct launches
  *   alsv_set_profiling      1: record CUDA events around every stage / time-control launch of

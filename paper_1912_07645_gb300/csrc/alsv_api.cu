@@ -43,7 +43,14 @@ alsv_status cuda_fail(alsv_ctx* c, cudaError_t e, const char* what) {
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 bool variant_ok(const alsv_ctx* c, int v) {
-    return stage_variant_supported(c->fp64, c->ndim, c->eq, c->d.recon, c->g.rvars, c->d.flux, c->g.bc, v);
+    if (!stage_variant_supported(c->fp64, c->ndim, c->eq, c->d.recon, c->g.rvars, c->d.flux, c->g.bc, v)) return false;
+    if (stage_variant_halves(c->fp64, c->ndim, v)) {
+        // the halves must align with whole tiles: ny divisible by twice the tile height
+        const TileShape ts = stage_tile(c->fp64, c->ndim, v);
+        for (int l = 0; l < c->g.nlev; ++l)
+            if (c->g.lev[l].n[1] % (2 * ts.ty) != 0) return false;
+    }
+    return true;
 }
 
 // Build the per-level tiling for one tile variant.
@@ -66,7 +73,10 @@ long long build_levels(const alsv_ctx* c, int variant, GridArgs& g) {
         L.elem0 = elem;
         L.work0 = work;
         L.pwork0 = pwork;
-        pwork += (long long)((L.samples + 1) / 2) * L.tiles;
+        // two-sample schedules: one work item per sample pair and tile, or per sample and tile of
+        // the lower half (halves pairing)
+        pwork += stage_variant_halves(c->fp64, c->ndim, variant) ? (long long)L.samples * (L.tiles / 2)
+                                                                 : (long long)((L.samples + 1) / 2) * L.tiles;
         s0 += L.samples;
         elem += (long long)L.samples * c->nv * L.n[0] * L.n[1] * L.n[2];
         work += (long long)L.samples * L.tiles;
@@ -286,6 +296,7 @@ TileShape stage_tile(int fp64, int ndim, int variant) {
         if (variant == 2 && !fp64) return TileShape{32, 32, 1, 256};
         if (variant == 3 && !fp64) return TileShape{31, 1 << 20, 1, 128};  // column strips, whole height
         if (variant == 5 && !fp64) return TileShape{32, 8, 1, 256};        // two-sample tiles
+        if (variant == 6 && !fp64) return TileShape{32, 16, 1, 256};       // two halves of a sample
         return TileShape{32, 16, 1, 256};                                   // variants 0 and 4
     }
     if (fp64) return variant == 1 ? TileShape{8, 8, 4, 256} : TileShape{8, 8, 8, 256};
@@ -293,9 +304,10 @@ TileShape stage_tile(int fp64, int ndim, int variant) {
     if (variant == 3) return TileShape{32, 8, 128, 256};
     return variant == 1 ? TileShape{8, 8, 8, 256} : TileShape{16, 8, 8, 256};
 }
+bool stage_variant_halves(int fp64, int ndim, int variant) { return ndim == 2 && !fp64 && variant == 6; }
 int stage_num_variants(int fp64, int ndim) {
     if (ndim == 1) return 3;
-    if (ndim == 2 && !fp64) return 6;
+    if (ndim == 2 && !fp64) return 7;
     if (ndim == 3 && !fp64) return 4;
     return 2;
 }
@@ -303,6 +315,9 @@ bool stage_variant_supported(int fp64, int ndim, int eq, int recon, int rvars, i
     if (variant < 0 || variant >= stage_num_variants(fp64, ndim)) return false;
     if (ndim == 2 && !fp64 && (variant == 4 || variant == 5))
         return eq == EQ_EULER && rvars == RV_PRIM && (flux == FLX_HLLC || flux == FLX_RUSANOV);
+    if (ndim == 2 && !fp64 && variant == 6)
+        return eq == EQ_EULER && rvars == RV_PRIM && (flux == FLX_HLLC || flux == FLX_RUSANOV) &&
+               bc[1][0] == BC_PERIODIC && bc[1][1] == BC_PERIODIC;
     if (ndim == 3 && !fp64 && variant >= 2) return eq == EQ_EULER;
     if (!(ndim == 2 && !fp64 && variant == 3)) return true;
     const bool periodic = bc[0][0] == BC_PERIODIC && bc[0][1] == BC_PERIODIC && bc[1][0] == BC_PERIODIC &&
@@ -860,7 +875,9 @@ alsv_status alsv_autotune(alsv_ctx* c, int reps, int* chosen, float* ms_per_vari
         }
         ms /= reps;
         if (ms_per_variant) ms_per_variant[v] = ms;
-        if (ms < best_ms) { best_ms = ms; best = v; }
+        // a later variant must be faster by more than 1 % to replace an earlier one, so that
+        // schedules of equal speed do not trade places from run to run
+        if (ms < best_ms * 0.99f) { best_ms = ms; best = v; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

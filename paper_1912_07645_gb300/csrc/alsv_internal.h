@@ -88,6 +88,8 @@ struct TileShape {
 };
 TileShape stage_tile(int fp64, int ndim, int variant);
 int stage_num_variants(int fp64, int ndim);
+// whether a variant pairs the two halves of each sample (work items: samples x tiles / 2)
+bool stage_variant_halves(int fp64, int ndim, int variant);
 // whether a variant supports a configuration (the column-marching variant is specialised)
 bool stage_variant_supported(int fp64, int ndim, int eq, int recon, int rvars, int flux, const int bc[3][2], int variant);
 

@@ -22,9 +22,11 @@ constexpr size_t pair_smem_bytes() {
     return (size_t)32 * (NS + NI);
 }
 
-template <int RECON, int FLUX, int TX, int TY, int NT>
+// HALVES = 1: the pair is one sample's tile in the lower half of a y-periodic grid (lane .x) and
+// the tile ny/2 rows above it (lane .y); every level needs ny divisible by 2 TY.
 // 32x16 tiles run 4 CTAs per SM with up to 64 registers (no spills with the loads hoisted);
 // 32x8 tiles 5 CTAs (measured best for each)
+template <int RECON, int FLUX, int TX, int TY, int NT, int HALVES = 0>
 __global__ void __launch_bounds__(NT, TY >= 16 ? 4 : 5) k_stage2d_pair(const StageArgs p) {
     constexpr int G = RECON == REC_PC ? 1 : 2;
     constexpr int SX = TX + 2 * G, SY = TY + 2 * G, NS = SX * SY;
@@ -47,11 +49,12 @@ __global__ void __launch_bounds__(NT, TY >= 16 ? 4 : 5) k_stage2d_pair(const Sta
         if ((long long)w >= g.lev[k].pwork0) l = k;
     const LevelInfo& L = g.lev[l];
     const uint32_t wl = w - (uint32_t)L.pwork0;
-    const uint32_t q = fdiv(wl, L.fd_tiles);
-    const uint32_t tile = wl - q * (uint32_t)L.tiles;
-    const int sA = 2 * (int)q;
-    const bool hasB = sA + 1 < L.samples;
-    const int sB = hasB ? sA + 1 : sA;
+    const uint32_t htiles = (uint32_t)L.tiles / 2u;
+    const uint32_t q = HALVES ? wl / htiles : fdiv(wl, L.fd_tiles);
+    const uint32_t tile = wl - q * (HALVES ? htiles : (uint32_t)L.tiles);
+    const int sA = HALVES ? (int)q : 2 * (int)q;
+    const bool hasB = HALVES ? true : sA + 1 < L.samples;
+    const int sB = HALVES ? sA : (hasB ? sA + 1 : sA);
     const bool doneA = p.done[L.sample0 + sA] != 0;
     const bool doneB = hasB ? p.done[L.sample0 + sB] != 0 : true;
     if (doneA && doneB) return;
@@ -61,6 +64,7 @@ __global__ void __launch_bounds__(NT, TY >= 16 ? 4 : 5) k_stage2d_pair(const Sta
     const int tx0 = (int)(tile - trow * (uint32_t)L.ntile[0]) * TX;
     const int ty0 = (int)trow * TY;
     const int plane = nx * ny;
+    const int hs = HALVES ? ny / 2 : 0;   // row shift of lane .y (halves)
     const long long bA = L.elem0 + (long long)sA * 4 * plane, bB = L.elem0 + (long long)sB * 4 * plane;
     const float* UsA = reinterpret_cast<const float*>(p.Us) + bA;
     const float* UsB = reinterpret_cast<const float*>(p.Us) + bB;
@@ -90,10 +94,15 @@ __global__ void __launch_bounds__(NT, TY >= 16 ? 4 : 5) k_stage2d_pair(const Sta
                     iy = map_ghost(iy, ny, g.bc[1][0], g.bc[1][1], fys[j]);
                 }
                 const int off = iy * nx + ix;
-                r[j] = make_float2(UsA[off], UsB[off]);
-                mx[j] = make_float2(UsA[plane + off], UsB[plane + off]);
-                my[j] = make_float2(UsA[2 * plane + off], UsB[2 * plane + off]);
-                E[j] = make_float2(UsA[3 * plane + off], UsB[3 * plane + off]);
+                int offB = off;
+                if (HALVES) {
+                    const int iyB = iy + hs < ny ? iy + hs : iy + hs - ny;
+                    offB = iyB * nx + ix;
+                }
+                r[j] = make_float2(UsA[off], UsB[offB]);
+                mx[j] = make_float2(UsA[plane + off], UsB[plane + offB]);
+                my[j] = make_float2(UsA[2 * plane + off], UsB[2 * plane + offB]);
+                E[j] = make_float2(UsA[3 * plane + off], UsB[3 * plane + offB]);
             }
         }
 #pragma unroll
@@ -210,14 +219,15 @@ __global__ void __launch_bounds__(NT, TY >= 16 ? 4 : 5) k_stage2d_pair(const Sta
         const int x = tx0 + c % TX, y = ty0 + c / TX;
         if (x >= nx || y >= ny) continue;
         const int off = y * nx + x;
+        const int offB = off + hs * nx;   // lower-half rows: y + ny/2 < ny
         // all reads of the cell first (the last stage writes in place over U^n: each element is
         // read by the thread that writes it, before the write)
         float2 us[4], un[4];
 #pragma unroll
-        for (int v = 0; v < 4; ++v) us[v] = make_float2(UsA[v * plane + off], UsB[v * plane + off]);
+        for (int v = 0; v < 4; ++v) us[v] = make_float2(UsA[v * plane + off], UsB[v * plane + offB]);
         if (has_un) {
 #pragma unroll
-            for (int v = 0; v < 4; ++v) un[v] = make_float2(UnA[v * plane + off], UnB[v * plane + off]);
+            for (int v = 0; v < 4; ++v) un[v] = make_float2(UnA[v * plane + off], UnB[v * plane + offB]);
         }
         float2 o[4];
 #pragma unroll
@@ -228,7 +238,7 @@ __global__ void __launch_bounds__(NT, TY >= 16 ? 4 : 5) k_stage2d_pair(const Sta
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
             if (!doneA) UoA[v * plane + off] = o[v].x;
-            if (!doneB) UoB[v * plane + off] = o[v].y;
+            if (!doneB) UoB[v * plane + offB] = o[v].y;
         }
         if (want_speed) {
             const float2 inv = rcp2(o[0]);
@@ -274,7 +284,8 @@ __global__ void __launch_bounds__(NT, TY >= 16 ? 4 : 5) k_stage2d_pair(const Sta
             }
             const double nanv = __longlong_as_double(0x7fffffffffffffffLL);
             if (!doneA) p.speed_part[L.work0 + (long long)sA * L.tiles + tile] = xa ? nanv : (double)ra;
-            if (!doneB) p.speed_part[L.work0 + (long long)sB * L.tiles + tile] = xb ? nanv : (double)rb;
+            const uint32_t tileB = HALVES ? tile + htiles : tile;   // the tile ny/2 rows above
+            if (!doneB) p.speed_part[L.work0 + (long long)sB * L.tiles + tileB] = xb ? nanv : (double)rb;
         }
     }
 }

@@ -3,9 +3,9 @@
 #include "fv_pair.cuh"
 #include "stage_dispatch.cuh"
 namespace alsv {
-template <int RECON, int FLUX, int TX, int TY, int NT>
+template <int RECON, int FLUX, int TX, int TY, int NT, int HALVES>
 static cudaError_t launch_pair_one(const StageArgs& a, cudaStream_t s) {
-    auto k = k_stage2d_pair<RECON, FLUX, TX, TY, NT>;
+    auto k = k_stage2d_pair<RECON, FLUX, TX, TY, NT, HALVES>;
     constexpr size_t sm = pair_smem_bytes<RECON, TX, TY>();
     static bool attr_set = false;
     if (!attr_set) {
@@ -18,19 +18,20 @@ static cudaError_t launch_pair_one(const StageArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// two-sample schedule (FP32 2D Euler, primitive reconstruction, HLLC or Rusanov)
-template <int TX, int TY, int NT>
+// two-sample schedule (FP32 2D Euler, primitive reconstruction, HLLC or Rusanov); HALVES pairs the
+// two halves of one y-periodic sample instead of two samples
+template <int TX, int TY, int NT, int HALVES = 0>
 static cudaError_t launch_pair(int recon, int flux, int eq, const StageArgs& a, cudaStream_t s) {
     if (eq != EQ_EULER || a.g.rvars != RV_PRIM) return cudaErrorNotSupported;
     if (flux == FLX_HLLC) {
-        if (recon == REC_WENO3) return launch_pair_one<REC_WENO3, FLX_HLLC, TX, TY, NT>(a, s);
-        if (recon == REC_MC) return launch_pair_one<REC_MC, FLX_HLLC, TX, TY, NT>(a, s);
-        return launch_pair_one<REC_PC, FLX_HLLC, TX, TY, NT>(a, s);
+        if (recon == REC_WENO3) return launch_pair_one<REC_WENO3, FLX_HLLC, TX, TY, NT, HALVES>(a, s);
+        if (recon == REC_MC) return launch_pair_one<REC_MC, FLX_HLLC, TX, TY, NT, HALVES>(a, s);
+        return launch_pair_one<REC_PC, FLX_HLLC, TX, TY, NT, HALVES>(a, s);
     }
     if (flux == FLX_RUSANOV) {
-        if (recon == REC_WENO3) return launch_pair_one<REC_WENO3, FLX_RUSANOV, TX, TY, NT>(a, s);
-        if (recon == REC_MC) return launch_pair_one<REC_MC, FLX_RUSANOV, TX, TY, NT>(a, s);
-        return launch_pair_one<REC_PC, FLX_RUSANOV, TX, TY, NT>(a, s);
+        if (recon == REC_WENO3) return launch_pair_one<REC_WENO3, FLX_RUSANOV, TX, TY, NT, HALVES>(a, s);
+        if (recon == REC_MC) return launch_pair_one<REC_MC, FLX_RUSANOV, TX, TY, NT, HALVES>(a, s);
+        return launch_pair_one<REC_PC, FLX_RUSANOV, TX, TY, NT, HALVES>(a, s);
     }
     return cudaErrorNotSupported;
 }
@@ -54,6 +55,7 @@ cudaError_t launch_stage_f32_2d(int variant, int eq, int recon, int flux, const 
         }
         case 4: return launch_pair<32, 16, 256>(recon, flux, eq, a, s);
         case 5: return launch_pair<32, 8, 256>(recon, flux, eq, a, s);
+        case 6: return launch_pair<32, 16, 256, 1>(recon, flux, eq, a, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -70,6 +72,7 @@ cudaError_t launch_speed_f32_2d(int variant, int eq, const GridArgs& g, const vo
         }
         case 4: return launch_speed_tile<float, 2, 32, 16, 1, 256>(eq, g, U, part, s);
         case 5: return launch_speed_tile<float, 2, 32, 8, 1, 256>(eq, g, U, part, s);
+        case 6: return launch_speed_tile<float, 2, 32, 16, 1, 256>(eq, g, U, part, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -644,6 +644,45 @@ def test_pair_variant_fp32_vs_oracle(variant, recon, flux, bc):
         p2_check(g[b:b + 1], o[b:b + 1], what=f"pair v{variant} {recon} {flux} sample {b}")
 
 
+@pytest.mark.parametrize("recon,flux,bcx", [("weno3", "hllc", "periodic"), ("mc", "rusanov", "outflow"),
+                                            ("pc", "hllc", "reflective")])
+def test_halves_variant_fp32_vs_oracle_and_bitwise_with_sample_pairs(recon, flux, bcx):
+    """Variant 6 pairs the two halves of each y-periodic sample (ragged x: 70 cells, ny = 64): within
+    2e-5 relative L1 of the oracle, and bitwise equal to the two-sample schedule (every packed lane
+    performs the same operations on its own data)."""
+    torch = torch_()
+    import paper_1912_07645_gb300 as alsv
+    bc = [(bcx, bcx), ("periodic", "periodic")]
+    cfg = dict(ndim=2, n=(70, 64), batch=3, eq="euler", recon=recon, flux=flux, rvars="prim", rk="ssprk3", bc=bc,
+               cfl=0.4, precision="fp32")
+    U0 = euler_state(3, 2, (70, 64), seed=73)
+    out = {}
+    for v in (4, 6):
+        S = gpu_solver(**cfg)
+        alsv.alsv_set_tile_variant(S.ctx, v)
+        S.set_state(torch.from_numpy(U0))
+        S.step(10)
+        S.sync()
+        out[v] = (host(S.U).reshape(S.level_shape(0)), S.time())
+        S.close()
+    assert np.array_equal(out[4][0], out[6][0])
+    np.testing.assert_array_equal(out[4][1][0], out[6][1][0])
+    o, *_ = run_oracle(cfg, U0=U0, steps=10)
+    for b in range(3):
+        p2_check(out[6][0][b:b + 1], o[b:b + 1], what=f"halves {recon} {flux} sample {b}")
+
+
+def test_halves_variant_needs_aligned_periodic_y():
+    torch_()
+    import paper_1912_07645_gb300 as alsv
+    for n, bc in (((64, 48), "periodic"), ((64, 64), [("periodic", "periodic"), ("outflow", "outflow")])):
+        S = gpu_solver(ndim=2, n=n, batch=1, eq="euler", recon="weno3", flux="hllc", rvars="prim", precision="fp32",
+                       bc=bc)
+        with pytest.raises(alsv.AlsvError, match="does not support"):
+            alsv.alsv_set_tile_variant(S.ctx, 6)
+        S.close()
+
+
 def test_pair_variant_samples_finishing_at_different_steps():
     """Samples of one pair reach T after different step counts: the finished lane must stay
     untouched while its partner continues."""

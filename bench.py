@@ -294,6 +294,14 @@ WORKLOADS = {
 }
 
 
+# Algorithmic floating-point operations per cell-update of each workload's scheme, counted on the
+# oracle's counting scalar (a CPU test checks them), and the ALU peaks: FP32 from the unit counts
+# (152 SMs x 128 lanes x 2 x 2.07 GHz), FP64 the GB300's nominal 1.25 TFLOP/s.
+WORKLOAD_FLOPS = {"sod1024_fp64": 287, "kh2d1024_fp32": 1980, "kh2d1024_fp64": 1980, "mlmc_fp32": 1980,
+                  "mlmc_coupled_fp32": 1980, "kh3d512_fp32": 3591, "kh3d256_fp32": 3591}
+FP64_PEAK_TFLOPS = 1.25
+
+
 def run_workload(name, args):
     import numpy as np
     import torch
@@ -392,6 +400,13 @@ def run_workload(name, args):
                          "algorithmic_bytes_per_cell_update": bpc, "stage_ms_total": prof["stage_ms"],
                          "stage_launches": prof["stage_launches"], "step_ms_total": 1000 * el},
             "gpu_launches": alsv.alsv_get_launch_count(S.ctx)}
+    if name in WORKLOAD_FLOPS and prof["stage_ms"] > 0:
+        fp64 = W["desc"]["precision"] == "fp64"
+        peak = FP64_PEAK_TFLOPS if fp64 else FP32_PEAK_TFLOPS
+        tflops = cu * WORKLOAD_FLOPS[name] / (prof["stage_ms"] / 1000.0) / 1e12
+        line["alu_roofline"] = {"bound": "alu", "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
+                                "frac": tflops / peak, "flops_per_cell_update": WORKLOAD_FLOPS[name],
+                                "peak_kind": "nominal FP64" if fp64 else "nominal: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
     if W.get("mlmc"):
         # per level: samples, grid, mean steps per sample of the pair, and for rho the integrals of
         # the mean correction |E[Y_l]| and of its variance Var[Y_l] (the variance decay)

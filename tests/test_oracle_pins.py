@@ -743,3 +743,16 @@ def test_joint_pdf_and_correlator_by_hand():
     n, sums = oracle.correlator(U, 0, [[0], [0, 1], [0, 0, 1]], euler=False)
     assert n == 3
     np.testing.assert_array_equal(sums, [6.0, 32.0, 78.0])
+
+
+def test_bench_workload_flop_constants_match_the_count():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(os.path.dirname(__file__), "..", "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    for name, flops in bench.WORKLOAD_FLOPS.items():
+        desc = dict(bench.WORKLOADS[name]["desc"])
+        if "levels" in desc:
+            desc["n"] = desc.pop("levels")[0][0]
+        d = oracle.make_desc(**desc)
+        assert oracle.count_flops(d)["per_cell_update"] == flops, name

@@ -6,6 +6,7 @@
   own boundary cannot influence its centre).
 * Adjoint 512^2 x 64 (FP64): the batch holds one sample and its +-h perturbations of all 20
   parameters, so a single full-size call gives both its adjoint gradient and central differences.
+* Uneven MLMC levels at their full sample counts: sampled samples of every level.
 """
 import math
 
@@ -113,3 +114,33 @@ def test_adjoint_512x64_vs_central_differences():
     assert np.abs(g[0] - fd).max() <= 1e-4 * np.abs(g[0]).max(), (g[0], fd)
     # the other samples of the batch are unperturbed copies for j >= 20 pairs: identical results
     assert np.all(J[41:] == J[0])
+
+
+def test_mlmc_levels_full_counts_sampled():
+    """The uneven-level batch at its full sample counts (64^2 x 4096 ... 512^2 x 64, one launch per
+    stage, autotuned schedule): the first and last sample of every level after two CFL steps
+    against the oracle run of the same parameters."""
+    import paper_1912_07645_gb300 as alsv
+    lv = [((64, 64), 4096), ((128, 128), 1024), ((256, 256), 256), ((512, 512), 64)]
+    cfg = dict(ndim=2, levels=lv, eq="euler", recon="weno3", flux="hllc", rvars="prim", rk="ssprk3",
+               bc="periodic", cfl=0.4, precision="fp32", seed=12345)
+    S = gpu_solver(**cfg)
+    S.set_initial_data("kh")
+    alsv.alsv_autotune(S.ctx, 2)
+    S.step(2)
+    S.sync()
+    picks = []
+    s0 = 0
+    for l, (n, B) in enumerate(lv):
+        V = S.state(l)
+        for b in (0, B - 1):
+            picks.append((l, n, s0 + b, host(V[b:b + 1])))
+        s0 += B
+    S.close()
+    th_all = oracle.theta_splitmix(12345, s0, 20)
+    for l, n, s, g in picks:
+        ocfg = dict(cfg, n=n, batch=1)
+        ocfg.pop("levels")
+        d = oracle.make_desc(**ocfg)
+        o, _, _ = oracle.evolve(d, oracle.init(d, "kh", 1, th_all[s:s + 1]), T=math.inf, max_steps=2)
+        p2_check(g.reshape(o.shape), o, what=f"level {l} sample {s}")

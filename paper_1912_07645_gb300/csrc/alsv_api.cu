@@ -302,13 +302,14 @@ TileShape stage_tile(int fp64, int ndim, int variant) {
     if (fp64) return variant == 1 ? TileShape{8, 8, 4, 256} : TileShape{8, 8, 8, 256};
     if (variant == 2) return TileShape{32, 8, 64, 256};    // z-marching column chunks
     if (variant == 3) return TileShape{32, 8, 128, 256};
+    if (variant == 4) return TileShape{32, 8, 64, 256};     // z-march, packed x/y interfaces
     return variant == 1 ? TileShape{8, 8, 8, 256} : TileShape{16, 8, 8, 256};
 }
 bool stage_variant_halves(int fp64, int ndim, int variant) { return ndim == 2 && !fp64 && variant == 6; }
 int stage_num_variants(int fp64, int ndim) {
     if (ndim == 1) return 3;
     if (ndim == 2 && !fp64) return 7;
-    if (ndim == 3 && !fp64) return 4;
+    if (ndim == 3 && !fp64) return 5;
     return 2;
 }
 bool stage_variant_supported(int fp64, int ndim, int eq, int recon, int rvars, int flux, const int bc[3][2], int variant) {
@@ -318,6 +319,8 @@ bool stage_variant_supported(int fp64, int ndim, int eq, int recon, int rvars, i
     if (ndim == 2 && !fp64 && variant == 6)
         return eq == EQ_EULER && rvars == RV_PRIM && (flux == FLX_HLLC || flux == FLX_RUSANOV) &&
                bc[1][0] == BC_PERIODIC && bc[1][1] == BC_PERIODIC;
+    if (ndim == 3 && !fp64 && variant == 4)
+        return eq == EQ_EULER && rvars == RV_PRIM && (flux == FLX_HLLC || flux == FLX_RUSANOV);
     if (ndim == 3 && !fp64 && variant >= 2) return eq == EQ_EULER;
     if (!(ndim == 2 && !fp64 && variant == 3)) return true;
     const bool periodic = bc[0][0] == BC_PERIODIC && bc[0][1] == BC_PERIODIC && bc[1][0] == BC_PERIODIC &&

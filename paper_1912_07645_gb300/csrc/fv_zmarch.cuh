@@ -13,11 +13,15 @@
 // instead of 3.4 times for an 8^3 tile, and each interface flux is still evaluated once.
 #pragma once
 
+#include "fv_packed3d.cuh"
 #include "fv_stage.cuh"
 
 namespace alsv {
 
-template <int RECON, int FLUX, int TX, int TY, int LZ>
+// PACK = 1 (primitive reconstruction, HLLC or Rusanov): each thread evaluates the k-th x-interface
+// and the k-th y-interface of the plane together in packed FP32x2 arithmetic (lane .x the
+// x-interface with normal velocity u, lane .y the y-interface with normal velocity v).
+template <int RECON, int FLUX, int TX, int TY, int LZ, int PACK = 0>
 __global__ void __launch_bounds__(TX * TY, 4) k_stage3d_zm(const StageArgs p) {
     using R = float;
     constexpr int ND = 3, NV = 5, G = (RECON == REC_PC) ? 1 : 2;
@@ -135,6 +139,64 @@ __global__ void __launch_bounds__(TX * TY, 4) k_stage3d_zm(const StageArgs p) {
         __syncthreads();
         const int pz = ((z % NP) + NP) % NP;
         const R* sp = sW + pz * PS * CS;
+        if constexpr (PACK) {
+            static_assert(NIY >= NIX, "the y interfaces outnumber the x interfaces");
+            const float2 eps2 = make_float2(epsx, epsy);
+#pragma unroll 1
+            for (int k = tid; k < NIY; k += NT) {
+                const bool hx = k < NIX;            // past NIX the x lane repeats interface 0 unused
+                const int kx = hx ? k : 0;
+                const int i0x = (kx / (TX + 1) + G) * SX + kx % (TX + 1) + G - 1;
+                const int i0y = (k / TX + G - 1) * SX + k % TX + G;
+                float2 Rk[4], Nk[4], Tk[4], Wk[4], Pk[4];
+#pragma unroll
+                for (int q = (G == 1 ? 1 : 0); q < (G == 1 ? 3 : 4); ++q) {
+                    const float* ax = sp + (i0x + (q - 1)) * CS;
+                    const float* ay = sp + (i0y + (q - 1) * SX) * CS;
+                    Rk[q] = make_float2(ax[0], ay[0]);
+                    Nk[q] = make_float2(ax[1], ay[2]);   // normal: u (x-interface), v (y-interface)
+                    Tk[q] = make_float2(ax[2], ay[1]);   // tangential: v, u
+                    Wk[q] = make_float2(ax[3], ay[3]);
+                    Pk[q] = make_float2(ax[4], ay[4]);
+                }
+                if (G == 1) {
+                    Rk[0] = Rk[1]; Nk[0] = Nk[1]; Tk[0] = Tk[1]; Wk[0] = Wk[1]; Pk[0] = Pk[1];
+                    Rk[3] = Rk[2]; Nk[3] = Nk[2]; Tk[3] = Tk[2]; Wk[3] = Wk[2]; Pk[3] = Pk[2];
+                }
+                F2x5 fr, fl;
+                faces2<RECON>(Rk[0], Rk[1], Rk[2], Rk[3], eps2, fr.r, fl.r);
+                faces2<RECON>(Nk[0], Nk[1], Nk[2], Nk[3], eps2, fr.n, fl.n);
+                faces2<RECON>(Tk[0], Tk[1], Tk[2], Tk[3], eps2, fr.t, fl.t);
+                faces2<RECON>(Wk[0], Wk[1], Wk[2], Wk[3], eps2, fr.w, fl.w);
+                faces2<RECON>(Pk[0], Pk[1], Pk[2], Pk[3], eps2, fr.p, fl.p);
+                F2x5 WL, WR;
+                if (G == 1) {
+                    WL = fr;
+                    WR = fl;
+                } else {
+                    // positivity fallback per face and lane: revert to the cell's own state
+                    const bool okLx = fr.r.x > 0.f && fr.p.x > 0.f, okLy = fr.r.y > 0.f && fr.p.y > 0.f;
+                    const bool okRx = fl.r.x > 0.f && fl.p.x > 0.f, okRy = fl.r.y > 0.f && fl.p.y > 0.f;
+                    WL.r = sel2(okLx, okLy, fr.r, Rk[1]);
+                    WL.n = sel2(okLx, okLy, fr.n, Nk[1]);
+                    WL.t = sel2(okLx, okLy, fr.t, Tk[1]);
+                    WL.w = sel2(okLx, okLy, fr.w, Wk[1]);
+                    WL.p = sel2(okLx, okLy, fr.p, Pk[1]);
+                    WR.r = sel2(okRx, okRy, fl.r, Rk[2]);
+                    WR.n = sel2(okRx, okRy, fl.n, Nk[2]);
+                    WR.t = sel2(okRx, okRy, fl.t, Tk[2]);
+                    WR.w = sel2(okRx, okRy, fl.w, Wk[2]);
+                    WR.p = sel2(okRx, okRy, fl.p, Pk[2]);
+                }
+                const F2x5 F = FLUX == FLX_HLLC ? hllc2_5(WL, WR, gamma, inv_gm1) : rusanov2_5(WL, WR, gamma, inv_gm1);
+                if (hx) {
+                    float* o = sFx + kx * CS;
+                    o[0] = F.r.x; o[1] = F.n.x; o[2] = F.t.x; o[3] = F.w.x; o[4] = F.p.x;
+                }
+                float* o = sFy + k * CS;
+                o[0] = F.r.y; o[1] = F.t.y; o[2] = F.n.y; o[3] = F.w.y; o[4] = F.p.y;
+            }
+        } else {
         // x interfaces of plane z ((TX + 1) x TY), then its y interfaces (TX x (TY + 1)), as one
         // loop so that only its last pass leaves threads idle before the barrier
 #pragma unroll 1
@@ -156,6 +218,7 @@ __global__ void __launch_bounds__(TX * TY, 4) k_stage3d_zm(const StageArgs p) {
 #pragma unroll
                 for (int v = 0; v < NV; ++v) sFy[fi * CS + v] = F[v];
             }
+        }
         }
         R Fzp[NV];
         zflux(z, Fzp);
@@ -231,9 +294,9 @@ constexpr size_t zm_smem_bytes() {
     return sizeof(float) * 5 * ((size_t)(2 * G + 1) * (TX + 2 * G) * (TY + 2 * G) + (TX + 1) * TY + TX * (TY + 1));
 }
 
-template <int RECON, int FLUX, int TX, int TY, int LZ>
+template <int RECON, int FLUX, int TX, int TY, int LZ, int PACK = 0>
 static cudaError_t launch_zm_one(const StageArgs& a, cudaStream_t s) {
-    auto k = k_stage3d_zm<RECON, FLUX, TX, TY, LZ>;
+    auto k = k_stage3d_zm<RECON, FLUX, TX, TY, LZ, PACK>;
     constexpr size_t sm = zm_smem_bytes<RECON, TX, TY, LZ>();
     static bool attr_set = false;
     if (!attr_set) {
@@ -260,6 +323,20 @@ static cudaError_t launch_stage_zm(int recon, int flux, const StageArgs& a, cuda
         default: ALSV_ZM_FLUX(REC_WENO3)
     }
 #undef ALSV_ZM_FLUX
+}
+
+// packed x/y interfaces (primitive reconstruction, HLLC or Rusanov)
+template <int TX, int TY, int LZ>
+static cudaError_t launch_stage_zm_packed(int recon, int flux, const StageArgs& a, cudaStream_t s) {
+    if (a.g.rvars != RV_PRIM || (flux != FLX_HLLC && flux != FLX_RUSANOV)) return cudaErrorNotSupported;
+    if (flux == FLX_HLLC) {
+        if (recon == REC_WENO3) return launch_zm_one<REC_WENO3, FLX_HLLC, TX, TY, LZ, 1>(a, s);
+        if (recon == REC_MC) return launch_zm_one<REC_MC, FLX_HLLC, TX, TY, LZ, 1>(a, s);
+        return launch_zm_one<REC_PC, FLX_HLLC, TX, TY, LZ, 1>(a, s);
+    }
+    if (recon == REC_WENO3) return launch_zm_one<REC_WENO3, FLX_RUSANOV, TX, TY, LZ, 1>(a, s);
+    if (recon == REC_MC) return launch_zm_one<REC_MC, FLX_RUSANOV, TX, TY, LZ, 1>(a, s);
+    return launch_zm_one<REC_PC, FLX_RUSANOV, TX, TY, LZ, 1>(a, s);
 }
 
 }  // namespace alsv

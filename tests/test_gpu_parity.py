@@ -364,21 +364,28 @@ def test_kh_3d_zmarch_bitwise_equal_to_tiles(variant, recon, flux, rvars, bc):
     np.testing.assert_array_equal(outs[0][1][0], outs[1][1][0])
 
 
-def test_kh_3d_zmarch_fp32_vs_oracle():
+@pytest.mark.parametrize("variant,recon,flux,bc", [
+    (2, "weno3", "hllc", "periodic"),
+    (4, "weno3", "hllc", "periodic"),
+    (4, "mc", "rusanov", [("reflective", "outflow"), ("periodic", "periodic"), ("outflow", "reflective")]),
+    (4, "pc", "hllc", [("outflow", "outflow"), ("reflective", "reflective"), ("periodic", "periodic")])])
+def test_kh_3d_zmarch_fp32_vs_oracle(variant, recon, flux, bc):
+    """z-march schedules against the oracle (ragged: 70 planes); variant 4 packs an x- and a
+    y-interface into the two FP32x2 lanes."""
     import paper_1912_07645_gb300 as alsv
     torch = torch_()
-    cfg = dict(ndim=3, n=(24, 20, 70), batch=1, eq="euler", recon="weno3", flux="hllc", rvars="prim", rk="ssprk3",
-               bc="periodic", cfl=0.3, precision="fp32")
+    cfg = dict(ndim=3, n=(24, 20, 70), batch=1, eq="euler", recon=recon, flux=flux, rvars="prim", rk="ssprk3",
+               bc=bc, cfl=0.3, precision="fp32")
     th = kh_theta(1, 8, P=128)
     S = gpu_solver(**cfg)
-    alsv.alsv_set_tile_variant(S.ctx, 2)
+    alsv.alsv_set_tile_variant(S.ctx, variant)
     S.set_initial_data("kh", theta=torch.from_numpy(th).cuda())
     S.step(3)
     S.sync()
     g = host(S.U).reshape(S.level_shape(0))
     S.close()
     o, *_ = run_oracle(cfg, "kh", th, steps=3)
-    p2_check(g, o, what="kh3d z-march fp32")
+    p2_check(g, o, what=f"kh3d z-march v{variant} {recon} {flux} fp32")
 
 
 def test_kh_3d_fp32():

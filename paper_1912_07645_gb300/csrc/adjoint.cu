@@ -356,11 +356,10 @@ template <class R, int RECON>
 static cudaError_t launch_adj_t(const AdjStageArgs& a, cudaStream_t s) {
     auto k = k_stage_adj<R, RECON, kAdjTX, kAdjTY, kAdjNT>;
     constexpr size_t sm = adj_smem_bytes<R, RECON, kAdjTX, kAdjTY, kAdjNT>();
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    static unsigned long long smem_devices = 0;   // devices on which the opt-in is done
+    {
+        const cudaError_t e = ensure_dynamic_smem(k, sm, smem_devices);
         if (e != cudaSuccess) return e;
-        attr = true;
     }
     k<<<(unsigned)a.g.total_work, kAdjNT, sm, s>>>(a);
     return cudaGetLastError();

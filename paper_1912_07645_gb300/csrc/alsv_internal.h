@@ -149,4 +149,18 @@ long long reduce_partial_count(const GridArgs& g);
 cudaError_t launch_reduce(int fp64, int kind, const GridArgs& g, const void* U, double* partial, double* out,
                           cudaStream_t s);
 
+// Opt a kernel into `bytes` of dynamic shared memory on the current device, once per device (the
+// attribute is per device; `done_mask` is the caller's per-kernel bit set of devices 0..63).
+template <class K>
+inline cudaError_t ensure_dynamic_smem(K kernel, size_t bytes, unsigned long long& done_mask) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = dev < 64 ? (1ull << dev) : 0ull;
+    if (bit && (done_mask & bit)) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) done_mask |= bit;
+    return e;
+}
+
 }  // namespace alsv

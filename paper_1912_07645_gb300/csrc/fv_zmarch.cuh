@@ -298,11 +298,10 @@ template <int RECON, int FLUX, int TX, int TY, int LZ, int PACK = 0>
 static cudaError_t launch_zm_one(const StageArgs& a, cudaStream_t s) {
     auto k = k_stage3d_zm<RECON, FLUX, TX, TY, LZ, PACK>;
     constexpr size_t sm = zm_smem_bytes<RECON, TX, TY, LZ>();
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    static unsigned long long smem_devices = 0;   // devices on which the opt-in is done
+    {
+        const cudaError_t e = ensure_dynamic_smem(k, sm, smem_devices);
         if (e != cudaSuccess) return e;
-        attr_set = true;
     }
     if (a.g.total_work <= 0) return cudaSuccess;
     k<<<(unsigned)a.g.total_work, TX * TY, sm, s>>>(a);

@@ -9,11 +9,10 @@ template <class R, int EQ, int ND, int RECON, int FLUX, int TX, int TY, int TZ, 
 static cudaError_t launch_stage_one(const StageArgs& a, cudaStream_t s) {
     auto k = k_stage<R, EQ, ND, RECON, FLUX, TX, TY, TZ, NT>;
     constexpr size_t sm = stage_smem_bytes<R, EQ, ND, RECON, TX, TY, TZ>();
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    static unsigned long long smem_devices = 0;   // devices on which the opt-in is done
+    {
+        const cudaError_t e = ensure_dynamic_smem(k, sm, smem_devices);
         if (e != cudaSuccess) return e;
-        attr_set = true;
     }
     if (a.g.total_work <= 0) return cudaSuccess;
     k<<<(unsigned)a.g.total_work, NT, sm, s>>>(a);

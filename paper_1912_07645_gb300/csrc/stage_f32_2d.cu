@@ -7,11 +7,10 @@ template <int RECON, int FLUX, int TX, int TY, int NT, int HALVES>
 static cudaError_t launch_pair_one(const StageArgs& a, cudaStream_t s) {
     auto k = k_stage2d_pair<RECON, FLUX, TX, TY, NT, HALVES>;
     constexpr size_t sm = pair_smem_bytes<RECON, TX, TY>();
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    static unsigned long long smem_devices = 0;   // devices on which the opt-in is done
+    {
+        const cudaError_t e = ensure_dynamic_smem(k, sm, smem_devices);
         if (e != cudaSuccess) return e;
-        attr_set = true;
     }
     if (a.g.total_pwork <= 0) return cudaSuccess;
     k<<<(unsigned)a.g.total_pwork, NT, sm, s>>>(a);

@@ -617,6 +617,7 @@ alsv_status alsv_adjoint_evolve(alsv_ctx* c, double T, int observable, const dou
     };
     c->adj_passes = 0;
     c->adj_n = 0;
+    NvtxRange fwd_range("alsv: adjoint forward sweep and reverse sweep");
     for (;;) {
         ++c->adj_passes;
         CKA(launch_init(c->fp64, 2, ia, s));

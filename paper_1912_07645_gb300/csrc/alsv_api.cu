@@ -13,6 +13,8 @@
 #include <vector>
 
 #include "../../include/alsv.h"
+#include <nvtx3/nvToolsExt.h>
+
 #include "alsv_ctx.h"
 #include "alsv_internal.h"
 
@@ -271,6 +273,8 @@ alsv_status run_chunk(alsv_ctx* c, int steps) {
 }  // namespace
 
 namespace alsv {
+NvtxRange::NvtxRange(const char* name) { nvtxRangePushA(name); }
+NvtxRange::~NvtxRange() { nvtxRangePop(); }
 void set_global_error(const std::string& msg) { g_init_error = msg; }
 alsv_status ctx_fail(alsv_ctx* c, alsv_status st, const std::string& msg) { return fail(c, st, msg); }
 alsv_status ctx_cuda_fail(alsv_ctx* c, cudaError_t e, const char* what) { return cuda_fail(c, e, what); }
@@ -624,6 +628,7 @@ alsv_status alsv_step(alsv_ctx* c, int n_steps) {
     alsv_status st = require_ready(c);
     if (st != ALSV_OK) return st;
     if (n_steps < 0) return fail(c, ALSV_ERR_INVALID_ARG, "n_steps must be >= 0");
+    NvtxRange range("alsv: steps");
     for (int i = 0; i < n_steps; ++i) {
         st = enqueue_step(c);
         if (st != ALSV_OK) return st;
@@ -677,7 +682,10 @@ alsv_status alsv_evolve_to_T(alsv_ctx* c, double T, int64_t* steps_taken_host) {
     long long chunks = 0;
     for (;;) {
         if (++chunks > (1LL << 26)) return fail(c, ALSV_ERR_TIMEOUT, "evolve_to_T: step limit reached");
-        st = run_chunk(c, chunk);
+        {
+            NvtxRange range("alsv: step chunk");
+            st = run_chunk(c, chunk);
+        }
         if (st != ALSV_OK) return st;
         CK(post(cur ^ 1));
         CK(cudaEventSynchronize(c->poll_ev[cur]));

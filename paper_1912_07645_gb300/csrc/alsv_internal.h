@@ -163,4 +163,12 @@ inline cudaError_t ensure_dynamic_smem(K kernel, size_t bytes, unsigned long lon
     return e;
 }
 
+// Profiler timeline range for the enclosing scope (NVTX; no cost without an attached tool).
+struct NvtxRange {
+    explicit NvtxRange(const char* name);
+    ~NvtxRange();
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 }  // namespace alsv

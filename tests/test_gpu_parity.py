@@ -257,6 +257,24 @@ def test_kh_3d_steps_fp64(recon, flux, rvars, bc):
     p1_check(g, o, what=f"kh3d {recon} {flux}")
 
 
+# ------------------------------------------------------------------ tiny and odd grids
+@pytest.mark.parametrize("n,recon,bc", [
+    ((1,), "pc", "periodic"), ((2,), "mc", "periodic"), ((3,), "weno3", "outflow"), ((5,), "mc", "reflective"),
+    ((7,), "weno3", "periodic"), ((1, 3), "weno3", "periodic"), ((3, 2), "mc", "reflective"),
+    ((5, 7), "weno3", [("outflow", "reflective"), ("periodic", "periodic")]), ((2, 3, 5), "mc", "periodic"),
+    ((3, 1, 2), "pc", "outflow")])
+def test_tiny_and_odd_grids_fp64(n, recon, bc):
+    """Grids of 1 to 7 cells per direction, far below one tile: every ghost, halo and tile-edge
+    path against the oracle per cell (FP64, 5 steps)."""
+    nd = len(n)
+    cfg = dict(ndim=nd, n=n, batch=2, eq="euler", recon=recon, flux="hllc", rvars="prim",
+               rk="ssprk3", bc=bc, cfl=0.3, precision="fp64")
+    U0 = euler_state(2, nd, n, seed=sum(n) + nd)
+    g, *_ = run_gpu(cfg, U0=U0, steps=5)
+    o, *_ = run_oracle(cfg, U0=U0, steps=5)
+    p1_check(g, o, what=f"tiny {n} {recon} {bc}")
+
+
 # ------------------------------------------------------------------ full runs to T (non-chaotic)
 def test_sod_config_full_run_fp64():
     cfg = dict(ndim=1, n=(1024,), eq="euler", recon="mc", flux="hllc", rvars="prim", rk="ssprk2", bc="outflow",

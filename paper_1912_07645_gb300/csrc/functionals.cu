@@ -18,6 +18,7 @@
 
 #include "alsv_ctx.h"
 #include "fv_physics.cuh"
+#include "fv_quantities.cuh"
 
 namespace alsv {
 namespace {
@@ -25,20 +26,6 @@ namespace {
 constexpr int kSfMaxR2 = 16;   // largest radius (cells) in 1D and 2D
 constexpr int kSfMaxR3 = 4;    // in 3D
 constexpr int kSfNT = 256;
-
-template <class R>
-__device__ __forceinline__ double quantity(const R* U, long long C, long long i, int q, int nv, int euler, double gm1) {
-    if (!euler) return (double)U[i];
-    const double rho = (double)U[i];
-    if (q == 0) return rho;
-    if (q < nv - 1) return (double)U[q * C + i] / rho;
-    double mm = 0.0;
-    for (int k = 1; k < nv - 1; ++k) {
-        const double m = (double)U[k * C + i];
-        mm = mm + m * m;
-    }
-    return gm1 * ((double)U[(nv - 1) * C + i] - 0.5 * mm / rho);
-}
 
 // ------------------------------------------------------------------------------ point PDF
 __device__ __forceinline__ int pdf_bin(double x, double lo, double hi, int n_bins) {
@@ -61,7 +48,7 @@ __global__ void k_point_pdf(const GridArgs g, const void* Uv, int q, const int64
     const int pt = (int)(t % n_points);
     const int b = (int)(t / n_points);
     const R* U = reinterpret_cast<const R*>(Uv) + (long long)b * g.nv * C;
-    const double x = quantity<R>(U, C, cells[pt], q, g.nv, g.nv > 1, g.gamma - 1.0);
+    const double x = prim_quantity<R>(U, C, cells[pt], q, g.nv, g.nv > 1, g.gamma - 1.0);
     atomicAdd(counts + (long long)pt * (n_bins + 2) + pdf_bin(x, lo, hi, n_bins), 1ull);
 }
 
@@ -77,8 +64,8 @@ __global__ void k_joint_pdf(const GridArgs g, const void* Uv, int q1, int q2, co
     const int pt = (int)(t % n_points);
     const int b = (int)(t / n_points);
     const R* U = reinterpret_cast<const R*>(Uv) + (long long)b * g.nv * C;
-    const double x1 = quantity<R>(U, C, cells[pt], q1, g.nv, g.nv > 1, g.gamma - 1.0);
-    const double x2 = quantity<R>(U, C, cells[pt], q2, g.nv, g.nv > 1, g.gamma - 1.0);
+    const double x1 = prim_quantity<R>(U, C, cells[pt], q1, g.nv, g.nv > 1, g.gamma - 1.0);
+    const double x2 = prim_quantity<R>(U, C, cells[pt], q2, g.nv, g.nv > 1, g.gamma - 1.0);
     const int k1 = pdf_bin(x1, lo1, hi1, nb1), k2 = pdf_bin(x2, lo2, hi2, nb2);
     atomicAdd(counts + ((long long)pt * (nb1 + 2) + k1) * (nb2 + 2) + k2, 1ull);
 }
@@ -98,7 +85,7 @@ __global__ void k_correlator(const GridArgs g, const void* Uv, int q, const int6
         const R* U = reinterpret_cast<const R*>(Uv) + (long long)b * g.nv * C;
         double prod = 1.0;
         for (int j = 0; j < k; ++j)
-            prod = prod * quantity<R>(U, C, cells[(long long)s * k + j], q, g.nv, g.nv > 1, g.gamma - 1.0);
+            prod = prod * prim_quantity<R>(U, C, cells[(long long)s * k + j], q, g.nv, g.nv > 1, g.gamma - 1.0);
         sum = sum + prod;
     }
     acc[1 + s] = acc[1 + s] + sum;
@@ -154,9 +141,9 @@ __global__ void __launch_bounds__(kSfNT) k_sf_partial(const GridArgs g, const vo
             double v = 0.0;
             if (in) {
                 const long long i = ((long long)z * ny + y) * nx + x;
-                v = fp64 ? quantity<double>(reinterpret_cast<const double*>(Uv) + (long long)b * g.nv * C, C, i, q,
+                v = fp64 ? prim_quantity<double>(reinterpret_cast<const double*>(Uv) + (long long)b * g.nv * C, C, i, q,
                                             g.nv, euler, gm1)
-                         : quantity<float>(reinterpret_cast<const float*>(Uv) + (long long)b * g.nv * C, C, i, q,
+                         : prim_quantity<float>(reinterpret_cast<const float*>(Uv) + (long long)b * g.nv * C, C, i, q,
                                            g.nv, euler, gm1);
             }
             sq[h] = v;

@@ -1,6 +1,7 @@
 // Per-sample time control (CFL step), initial data, counter-based parameters, Monte Carlo
 // statistics (Sec. 2.2) and fixed-order FP64 reductions.
 #include "fv_physics.cuh"
+#include "fv_quantities.cuh"
 
 namespace alsv {
 
@@ -341,20 +342,8 @@ __global__ void k_welford(const GridArgs g, const void* Uv, void* stats) {
     const double gm1 = g.gamma - 1.0;
 #pragma unroll 4
     for (int b = 0; b < B; ++b) {
-        double u[NV], x[NV];
-#pragma unroll
-        for (int v = 0; v < NV; ++v) u[v] = (double)U[((long long)b * NV + v) * C + i];
-        if (EULER) {
-            double mm = u[1] * u[1];
-#pragma unroll
-            for (int k = 2; k < NV - 1; ++k) mm = mm + u[k] * u[k];
-            x[0] = u[0];
-#pragma unroll
-            for (int k = 1; k < NV - 1; ++k) x[k] = u[k] / u[0];
-            x[NV - 1] = gm1 * (u[NV - 1] - 0.5 * mm / u[0]);
-        } else {
-            x[0] = u[0];
-        }
+        double x[NV];
+        prim_quantities<R, NV, EULER>(U + (long long)b * NV * C, C, i, gm1, x);
         const double n = (double)(n0 + b + 1);
 #pragma unroll
         for (int q = 0; q < NV; ++q) {

@@ -10,6 +10,7 @@
 
 #include "alsv_ctx.h"
 #include "fv_physics.cuh"
+#include "fv_quantities.cuh"
 
 namespace alsv {
 namespace {
@@ -54,25 +55,6 @@ size_t mlmc_total_bytes(const alsv_ctx* c) {
     return (size_t)(m.off[l] + ((3LL * c->nv * m.cells[l] * 8 + 255) / 256) * 256);
 }
 
-// primitive quantities of one cell (FP64 from the stored precision): rho, u_k, p (Burgers: u)
-template <class R, int NV, int EULER>
-__device__ __forceinline__ void prim_q(const R* U, long long C, long long i, double gm1, double* x) {
-    double u[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) u[v] = (double)U[v * C + i];
-    if (EULER) {
-        double mm = u[1] * u[1];
-#pragma unroll
-        for (int k = 2; k < NV - 1; ++k) mm = mm + u[k] * u[k];
-        x[0] = u[0];
-#pragma unroll
-        for (int k = 1; k < NV - 1; ++k) x[k] = u[k] / u[0];
-        x[NV - 1] = gm1 * (u[NV - 1] - 0.5 * mm / u[0]);
-    } else {
-        x[0] = u[0];
-    }
-}
-
 // one thread per cell of level l's grid, samples in ascending order
 template <class R, int NV, int EULER>
 __global__ void __launch_bounds__(kMlmcNT) k_mlmc_welford(const GridArgs g, const void* Uv, int gf, int gc,
@@ -109,9 +91,9 @@ __global__ void __launch_bounds__(kMlmcNT) k_mlmc_welford(const GridArgs g, cons
 #pragma unroll 1
     for (int b = 0; b < B; ++b) {
         double xf[NV], xc[NV];
-        prim_q<R, NV, EULER>(U + F.elem0 + (long long)b * NV * C, C, i, gm1, xf);
+        prim_quantities<R, NV, EULER>(U + F.elem0 + (long long)b * NV * C, C, i, gm1, xf);
         if (gc >= 0) {
-            prim_q<R, NV, EULER>(U + g.lev[gc].elem0 + (long long)b * NV * Cc, Cc, pc, gm1, xc);
+            prim_quantities<R, NV, EULER>(U + g.lev[gc].elem0 + (long long)b * NV * Cc, Cc, pc, gm1, xc);
         } else {
 #pragma unroll
             for (int q = 0; q < NV; ++q) xc[q] = 0.0;

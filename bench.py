@@ -315,7 +315,11 @@ def run_workload(name, args):
     if W.get("adjoint"):
         S.set_initial_data("kh")
         # the forward sweeps run the context's stage schedule: pick the fastest for this shape
-        chosen, ms_var = alsv.alsv_autotune(S.ctx, 3) if alsv.alsv_num_tile_variants(S.ctx) > 1 else (0, [])
+        if args.tile_variant >= 0:
+            alsv.alsv_set_tile_variant(S.ctx, args.tile_variant)
+            chosen, ms_var = args.tile_variant, []
+        else:
+            chosen, ms_var = alsv.alsv_autotune(S.ctx, 3) if alsv.alsv_num_tile_variants(S.ctx) > 1 else (0, [])
         th = torch.empty((S.samples, 20), dtype=torch.float64, device="cuda")
         alsv.alsv_get_parameters(S.ctx, th)
         S.sync()

@@ -208,10 +208,13 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 4 : 2) k_stage_adj(const 
 #pragma unroll
             for (int k = 0; k < NSL; ++k)
 #pragma unroll
-                for (int v = 0; v < NV; ++v) {
-                    w[k][v] = sW[v * SUX * SUY + ui + k * ustep];
-                    cu[k][v] = sU[v * SUX * SUY + ui + k * ustep];
-                }
+                for (int v = 0; v < NV; ++v) w[k][v] = sW[v * SUX * SUY + ui + k * ustep];
+            if (!prim) {   // conserved stencil values: only the conserved-variable path reads them
+#pragma unroll
+                for (int k = 0; k < NSL; ++k)
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) cu[k][v] = sU[v * SUX * SUY + ui + k * ustep];
+            }
             constexpr int KL = PC ? 0 : 1, KR = PC ? 1 : 2;   // stencil slots of cells j, j+1
             // forward face states
             R fL[NV], fR[NV];

@@ -120,10 +120,11 @@ struct AdjStageArgs {
     double c1, c2, b, dt;
 };
 
-// One CTA per (sample, TX x TY tile), one cell per thread.
-template <class R, int RECON, int TX, int TY, int NT>
+// One CTA per (sample, TX x TY tile), one cell per thread; RV: reconstruction variables (the
+// conserved-variable path is compiled only where it runs).
 // FP32: 4 CTAs per SM (the shared-memory limit; measured faster than 2 CTAs without spills);
 // FP64: 2 CTAs per SM
+template <class R, int RECON, int RV, int TX, int TY, int NT>
 __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 4 : 2) k_stage_adj(const AdjStageArgs p) {
     static_assert(TX * TY == NT, "one cell per thread");
     constexpr int NV = 4;
@@ -156,7 +157,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 4 : 2) k_stage_adj(const 
     const R* Us = reinterpret_cast<const R*>(p.Us) + sbase;
     const R* Ls = reinterpret_cast<const R*>(p.Ls) + sbase;
     const R gamma = R(g.gamma), gm1 = gamma - R(1), inv_gm1 = R(1) / gm1;
-    const bool prim = g.rvars == RV_PRIM;
+    constexpr bool prim = RV == RV_PRIM;
     const int tid = threadIdx.x;
 
     // periodic tile loads
@@ -355,9 +356,9 @@ constexpr size_t adj_smem_bytes() {
 
 constexpr int kAdjTX = 32, kAdjTY = 8, kAdjNT = 256;
 
-template <class R, int RECON>
+template <class R, int RECON, int RV>
 static cudaError_t launch_adj_t(const AdjStageArgs& a, cudaStream_t s) {
-    auto k = k_stage_adj<R, RECON, kAdjTX, kAdjTY, kAdjNT>;
+    auto k = k_stage_adj<R, RECON, RV, kAdjTX, kAdjTY, kAdjNT>;
     constexpr size_t sm = adj_smem_bytes<R, RECON, kAdjTX, kAdjTY, kAdjNT>();
     static unsigned long long smem_devices = 0;   // devices on which the opt-in is done
     {
@@ -368,9 +369,15 @@ static cudaError_t launch_adj_t(const AdjStageArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+template <class R>
+static cudaError_t launch_adj_r(int recon, const AdjStageArgs& a, cudaStream_t s) {
+    const bool prim = a.g.rvars == RV_PRIM;
+    if (recon == REC_PC) return prim ? launch_adj_t<R, REC_PC, RV_PRIM>(a, s) : launch_adj_t<R, REC_PC, RV_CONS>(a, s);
+    return prim ? launch_adj_t<R, REC_MC, RV_PRIM>(a, s) : launch_adj_t<R, REC_MC, RV_CONS>(a, s);
+}
+
 static cudaError_t launch_adj(int fp64, int recon, const AdjStageArgs& a, cudaStream_t s) {
-    if (fp64) return recon == REC_PC ? launch_adj_t<double, REC_PC>(a, s) : launch_adj_t<double, REC_MC>(a, s);
-    return recon == REC_PC ? launch_adj_t<float, REC_PC>(a, s) : launch_adj_t<float, REC_MC>(a, s);
+    return fp64 ? launch_adj_r<double>(recon, a, s) : launch_adj_r<float>(recon, a, s);
 }
 
 // lambda^n = d KE / d U^n, KE = sum |m|^2 / (2 rho) dV

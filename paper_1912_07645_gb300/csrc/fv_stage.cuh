@@ -179,7 +179,9 @@ __device__ __forceinline__ void interface_states(const R* sw, int i0, int step, 
     face_states<R, EQ, ND, RECON>(cm, cl, cr, c2, rvars, gm1, eps, WL, WR);
 }
 
-template <class R, int EQ, int ND, int RECON, int FLUX, int TX, int TY, int TZ, int NT>
+// RV: reconstruction variables (primitive or conserved) as a compile-time choice, so that each
+// instantiation carries only its own conversion path
+template <class R, int EQ, int ND, int RECON, int FLUX, int TX, int TY, int TZ, int NT, int RV = RV_PRIM>
 __global__ void __launch_bounds__(NT) k_stage(const StageArgs p) {
     constexpr int NV = (EQ == EQ_BURGERS) ? 1 : ND + 2;
     constexpr int G = (RECON == REC_PC) ? 1 : 2;
@@ -250,7 +252,7 @@ __global__ void __launch_bounds__(NT) k_stage(const StageArgs p) {
 #pragma unroll
             for (int k = 0; k < ND; ++k)
                 if (flip[k]) u[1 + k] = -u[1 + k];
-            if (g.rvars == RV_PRIM) {
+            if (RV == RV_PRIM) {
                 R wv[NV];
                 cons_to_prim<R, ND>(u, wv, gm1);
                 sts_cell<R, NV, CS>(sW + s * CS, wv);
@@ -286,7 +288,7 @@ __global__ void __launch_bounds__(NT) k_stage(const StageArgs p) {
             if (D == 2) cz -= 1;
             const int i0 = (cz * SY + cy) * SX + cx;
             R WL[NV], WR[NV], F[NV];
-            interface_states<R, EQ, ND, RECON, CS>(sW, i0, step, g.rvars, gm1, eps, WL, WR);
+            interface_states<R, EQ, ND, RECON, CS>(sW, i0, step, RV, gm1, eps, WL, WR);
             if (EQ == EQ_BURGERS) {
                 F[0] = burgers_flux<R, FLUX>(WL[0], WR[0]);
             } else {

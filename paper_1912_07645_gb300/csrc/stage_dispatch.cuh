@@ -5,9 +5,9 @@
 
 namespace alsv {
 
-template <class R, int EQ, int ND, int RECON, int FLUX, int TX, int TY, int TZ, int NT>
-static cudaError_t launch_stage_one(const StageArgs& a, cudaStream_t s) {
-    auto k = k_stage<R, EQ, ND, RECON, FLUX, TX, TY, TZ, NT>;
+template <class R, int EQ, int ND, int RECON, int FLUX, int TX, int TY, int TZ, int NT, int RV>
+static cudaError_t launch_stage_rv(const StageArgs& a, cudaStream_t s) {
+    auto k = k_stage<R, EQ, ND, RECON, FLUX, TX, TY, TZ, NT, RV>;
     constexpr size_t sm = stage_smem_bytes<R, EQ, ND, RECON, TX, TY, TZ>();
     static unsigned long long smem_devices = 0;   // devices on which the opt-in is done
     {
@@ -17,6 +17,13 @@ static cudaError_t launch_stage_one(const StageArgs& a, cudaStream_t s) {
     if (a.g.total_work <= 0) return cudaSuccess;
     k<<<(unsigned)a.g.total_work, NT, sm, s>>>(a);
     return cudaGetLastError();
+}
+
+// reconstruction variables: Euler primitive or conserved; a scalar law has only its own variable
+template <class R, int EQ, int ND, int RECON, int FLUX, int TX, int TY, int TZ, int NT>
+static cudaError_t launch_stage_one(const StageArgs& a, cudaStream_t s) {
+    if (EQ == EQ_EULER && a.g.rvars == RV_CONS) return launch_stage_rv<R, EQ, ND, RECON, FLUX, TX, TY, TZ, NT, RV_CONS>(a, s);
+    return launch_stage_rv<R, EQ, ND, RECON, FLUX, TX, TY, TZ, NT, RV_PRIM>(a, s);
 }
 
 template <class R, int EQ, int ND, int RECON, int TX, int TY, int TZ, int NT>

@@ -52,7 +52,9 @@ enum { ALSV_RECON_PC = 0, ALSV_RECON_MC = 1, ALSV_RECON_WENO3 = 2 };
 enum { ALSV_VARS_CONS = 0, ALSV_VARS_PRIM = 1 };
 enum { ALSV_FLUX_RUSANOV = 0, ALSV_FLUX_HLL = 1, ALSV_FLUX_HLLC = 2 };
 enum { ALSV_RK_SSP2 = 2, ALSV_RK_SSP3 = 3 };
-enum { ALSV_BC_PERIODIC = 0, ALSV_BC_OUTFLOW = 1, ALSV_BC_REFLECTIVE = 2 };
+/* ALSV_BC_HALO: a face of a block of a decomposed grid whose ghost layers are filled by the caller
+ * (alsv_bind_halo; see "Domain decomposition" below). */
+enum { ALSV_BC_PERIODIC = 0, ALSV_BC_OUTFLOW = 1, ALSV_BC_REFLECTIVE = 2, ALSV_BC_HALO = 3 };
 enum { ALSV_FP32 = 0, ALSV_FP64 = 1 };
 enum {
     ALSV_INIT_KH = 0,           /* Kelvin-Helmholtz shear layer (Sec. 3), 2D (20 params) or 3D (128) */
@@ -79,7 +81,8 @@ enum { ALSV_SAMPLER_MC = 0, ALSV_SAMPLER_HALTON = 1, ALSV_SAMPLER_HALTON_SHIFTED
 typedef struct alsv_grid_desc {
     int32_t ndim;          /* 1, 2 or 3 */
     int32_t n[3];          /* cells per direction (level 0 when n_levels > 1 ignores this) */
-    double lo[3], hi[3];   /* domain box; dx_k = (hi_k - lo_k) / n_k (one dx per direction) */
+    double lo[3], hi[3];   /* domain box; dx_k = (hi_k - lo_k) / n_k (one dx per direction), with
+                              n_k = global_n[k] for a block of a decomposed grid */
     int32_t batch;         /* samples B (single-level) */
     int32_t eq;            /* ALSV_EQ_* */
     double gamma;          /* ideal-gas ratio of specific heats (Euler) */
@@ -87,7 +90,8 @@ typedef struct alsv_grid_desc {
     int32_t recon_vars;    /* ALSV_VARS_* (Euler only) */
     int32_t flux;          /* ALSV_FLUX_* (Burgers: HLLC behaves as HLL) */
     int32_t rk;            /* ALSV_RK_* */
-    int32_t bc[3][2];      /* ALSV_BC_* per direction and side; periodic must pair with periodic */
+    int32_t bc[3][2];      /* ALSV_BC_* per direction and side; periodic must pair with periodic;
+                              HALO: single grid (n_levels <= 1) only */
     double cfl;            /* CFL number for the adaptive step */
     double fixed_dt;       /* > 0: fixed step (adjoint mode); 0: adaptive CFL step */
     int32_t precision;     /* ALSV_FP32 or ALSV_FP64: state and stencil arithmetic */
@@ -109,7 +113,13 @@ typedef struct alsv_grid_desc {
                               must divide group j - 1's grid, which must be a level. At most one
                               companion per level. */
     int32_t sampler;       /* ALSV_SAMPLER_* for counter-generated KH parameters (default MC) */
-    int32_t reserved[5];   /* must be zero */
+    int32_t global_n[3];   /* block of a decomposed grid (single grid only): 0 = direction not
+                              decomposed (global_n = n); else the whole grid's cells along k, of
+                              which this context holds [offset[k], offset[k] + n[k]). lo / hi stay
+                              the whole domain's, so dx and every cell centre equal the whole
+                              grid's bitwise. */
+    int32_t offset[3];     /* first global cell index of the block along k (0 if not decomposed) */
+    int32_t reserved[4];   /* must be zero */
 } alsv_grid_desc;
 
 typedef struct alsv_ctx alsv_ctx;
@@ -352,6 +362,68 @@ size_t alsv_structure_function_bytes(const alsv_ctx* ctx, int radius);
 alsv_status alsv_structure_function_accumulate(alsv_ctx* ctx, int quantity_index, int p, int radius, void* acc_dev,
                                                size_t bytes);
 alsv_status alsv_structure_function_read(alsv_ctx* ctx, const void* acc_dev, int p, int radius, double* S_dev);
+
+/*
+ * Domain decomposition (Sec. 2.1, last paragraph, and Sec. 3.1: one sample split over several
+ * devices, each advancing a block of the grid and exchanging the halo cells its stencil reads
+ * from the neighbouring blocks; the paper decomposes in x, y or both). A block is a context whose
+ * descriptor sets global_n / offset and marks each face that borders another block
+ * ALSV_BC_HALO. Its ghost cells on such a face are read from a caller-bound halo buffer instead
+ * of being derived from a boundary condition; everything else (physical faces, arithmetic,
+ * statistics, totals) is the single-grid path. The caller drives each step stage by stage and
+ * fills the halo buffers between stages (from the neighbours' alsv_halo_pack output, by device
+ * copies, NCCL send/recv or any other transport), and takes the CFL maximum over all blocks:
+ *
+ *   alsv_set_end_time(T);  alsv_speed_max(smax);  MAX over blocks;  alsv_finish_step(smax, 0)
+ *   per step: for s = 0 .. stages-1:
+ *                 alsv_halo_pack(s, ...) on every block;  deliver into the neighbours' halos;
+ *                 alsv_stage(s)
+ *             alsv_speed_max(smax);  MAX over blocks;  alsv_finish_step(smax, 1)
+ *
+ * With every block fed its neighbours' layers of the same stage state and the same maximum, each
+ * cell sees exactly the inputs it sees on the whole grid, so the blocks together reproduce the
+ * whole-grid run bitwise under the same stage schedule. Every schedule reads halo faces except the
+ * FP32 2D column march and two-sample schedules (variants 3-6), which reject them.
+ *
+ * Halo buffer of face (k, side): [samples][vars][layers][cross], layers = alsv_halo_info's g (1
+ * for PC, 2 otherwise), cross = the block's cells across k in (z, y, x) order without k. Layer l
+ * of the low face holds the cells at index -g + l along k, of the high face n_k + l. Elements are
+ * the state's precision.
+ *
+ *   alsv_halo_info     layers g and the element count of each face's buffer (host outputs;
+ *                      elems[2k + side], 0 for faces that are not HALO)
+ *   alsv_bind_halo     device pointers of the six face buffers (NULL for faces that are not
+ *                      HALO) and their byte size each (>= elems * element size). The context
+ *                      borrows them; they are read by every later stage launch.
+ *   alsv_halo_pack     write the block's own g boundary layers of the state that stage s reads
+ *                      (s = 0: U; RK2 s = 1: the stage buffer; RK3 s = 1, 2: the two stage
+ *                      buffers) into send[2k + side] (same layout; low face = indices 0 .. g-1,
+ *                      high face = n_k - g .. n_k - 1), for every face whose pointer is not
+ *                      NULL. A neighbour's halo buffer may be passed directly. Asynchronous.
+ *   alsv_stage         enqueue RK stage s of the current step for every sample that is not done;
+ *                      stages must come in order 0, 1, ... (INVALID_ARG otherwise). The last stage
+ *                      also writes the per-tile CFL partials. Asynchronous.
+ *   alsv_speed_max     smax_dev[samples] (device FP64) = each sample's largest (|u_k|+c)/dx_k over
+ *                      the block, from the partials of the last stage (or of set_initial_data /
+ *                      set_time), +infinity for a sample with a non-finite partial. Allowed before
+ *                      the first stage of a step or after the last. Asynchronous.
+ *   alsv_finish_step   time control from an external maximum (the MAX of every block's
+ *                      smax; +infinity or NaN marks the sample non-physical): advance = 1 after
+ *                      the last stage (t += dt, step count, done flags, next dt), 0 to only
+ *                      recompute dt (after set_initial_data, set_time or set_end_time).
+ *                      Asynchronous; status errors are reported by alsv_sync.
+ *   alsv_set_end_time  set the end time T of the run driven by alsv_finish_step (fixed-dt mode:
+ *                      the step target ceil(T / fixed_dt)). SYNCHRONOUS.
+ * alsv_step, alsv_evolve_to_T, the adjoint and the structure functions return INVALID_ARG on a
+ * context with HALO faces (they would read halo buffers nobody refills).
+ */
+alsv_status alsv_halo_info(const alsv_ctx* ctx, int32_t* layers, int64_t* elems);
+alsv_status alsv_bind_halo(alsv_ctx* ctx, const void* const* halo_dev, size_t bytes_each);
+alsv_status alsv_halo_pack(alsv_ctx* ctx, int stage, void* const* send_dev, size_t bytes_each);
+alsv_status alsv_stage(alsv_ctx* ctx, int stage);
+alsv_status alsv_speed_max(alsv_ctx* ctx, double* smax_dev);
+alsv_status alsv_finish_step(alsv_ctx* ctx, const double* smax_dev, int advance);
+alsv_status alsv_set_end_time(alsv_ctx* ctx, double T);
 
 /* Destroy the context (host memory and CUDA graphs only; caller buffers are untouched). */
 alsv_status alsv_destroy(alsv_ctx* ctx);

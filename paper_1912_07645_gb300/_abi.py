@@ -20,7 +20,7 @@ RECON = {"pc": 0, "mc": 1, "weno3": 2}
 RVARS = {"cons": 0, "prim": 1}
 FLUX = {"rusanov": 0, "hll": 1, "hllc": 2}
 RK = {"ssprk2": 2, "ssprk3": 3}
-BC = {"periodic": 0, "outflow": 1, "reflective": 2}
+BC = {"periodic": 0, "outflow": 1, "reflective": 2, "halo": 3}
 PRECISION = {"fp32": 0, "fp64": 1}
 INIT = {"kh": 0, "sod": 1, "lax": 2, "burgers_sine": 3, "vortex": 4, "raw": 5}
 MAX_LEVELS = 8
@@ -45,7 +45,8 @@ class alsv_grid_desc(C.Structure):
         ("weno_eps", C.c_double), ("weno_eps_dx2", C.c_int32), ("n_levels", C.c_int32),
         ("level_n", (C.c_int32 * 3) * MAX_LEVELS), ("level_batch", C.c_int32 * MAX_LEVELS),
         ("vortex_center", C.c_double * 2), ("sample_offset", C.c_int64),
-        ("level_fine", C.c_int32 * MAX_LEVELS), ("sampler", C.c_int32), ("reserved", C.c_int32 * 5),
+        ("level_fine", C.c_int32 * MAX_LEVELS), ("sampler", C.c_int32), ("global_n", C.c_int32 * 3),
+        ("offset", C.c_int32 * 3), ("reserved", C.c_int32 * 4),
     ]
 
 
@@ -100,6 +101,13 @@ SIGNATURES = {
     "alsv_set_profiling": (C.c_int, [_ctx, C.c_int]),
     "alsv_get_profile": (C.c_int, [_ctx, _dp, _i64p, _dp, _i64p]),
     "alsv_get_launch_count": (C.c_int, [_ctx, _i64p]),
+    "alsv_halo_info": (C.c_int, [_ctx, C.POINTER(C.c_int32), _i64p]),
+    "alsv_bind_halo": (C.c_int, [_ctx, C.POINTER(_vp), _sz]),
+    "alsv_halo_pack": (C.c_int, [_ctx, C.c_int, C.POINTER(_vp), _sz]),
+    "alsv_stage": (C.c_int, [_ctx, C.c_int]),
+    "alsv_speed_max": (C.c_int, [_ctx, _vp]),
+    "alsv_finish_step": (C.c_int, [_ctx, _vp, C.c_int]),
+    "alsv_set_end_time": (C.c_int, [_ctx, C.c_double]),
 }
 
 _lock = threading.Lock()
@@ -332,6 +340,53 @@ def alsv_adjoint_get_plan(ctx):
     n, dt, p = C.c_int64(0), C.c_double(0.0), C.c_int32(0)
     _check(load().alsv_adjoint_get_plan(ctx, C.byref(n), C.byref(dt), C.byref(p)), "alsv_adjoint_get_plan", ctx)
     return int(n.value), float(dt.value), int(p.value)
+
+
+def alsv_halo_info(ctx):
+    """(ghost layers g, [elements of the halo buffer of face 2k + side] * 6)."""
+    g, n = C.c_int32(0), (C.c_int64 * 6)()
+    _check(load().alsv_halo_info(ctx, C.byref(g), n), "alsv_halo_info", ctx)
+    return int(g.value), [int(v) for v in n]
+
+
+def _faces(bufs):
+    arr = (C.c_void_p * 6)()
+    for f in range(6):
+        arr[f] = _ptr(bufs[f]) if f < len(bufs) else None
+    return arr
+
+
+def _bytes_each(bufs) -> int:
+    sizes = [_nbytes(b) for b in bufs if b is not None and not isinstance(b, int)]
+    return min(sizes) if sizes else 0
+
+
+def alsv_bind_halo(ctx, halos, nbytes: int | None = None):
+    """halos: six device buffers (None for faces that are not HALO), face 2k + side."""
+    _check(load().alsv_bind_halo(ctx, _faces(halos), nbytes if nbytes is not None else _bytes_each(halos)),
+           "alsv_bind_halo", ctx)
+
+
+def alsv_halo_pack(ctx, stage: int, sends, nbytes: int | None = None):
+    """sends: six device buffers (None to skip a face) that receive the block's boundary layers."""
+    _check(load().alsv_halo_pack(ctx, stage, _faces(sends), nbytes if nbytes is not None else _bytes_each(sends)),
+           "alsv_halo_pack", ctx)
+
+
+def alsv_stage(ctx, stage: int):
+    _check(load().alsv_stage(ctx, stage), "alsv_stage", ctx)
+
+
+def alsv_speed_max(ctx, smax):
+    _check(load().alsv_speed_max(ctx, _ptr(smax)), "alsv_speed_max", ctx)
+
+
+def alsv_finish_step(ctx, smax, advance: bool):
+    _check(load().alsv_finish_step(ctx, _ptr(smax), 1 if advance else 0), "alsv_finish_step", ctx)
+
+
+def alsv_set_end_time(ctx, T: float):
+    _check(load().alsv_set_end_time(ctx, T), "alsv_set_end_time", ctx)
 
 
 def alsv_destroy(ctx):

@@ -504,6 +504,7 @@ alsv_status adj_validate(alsv_ctx* c) {
     if (!c) return ALSV_ERR_INVALID_ARG;
     if (c->eq != ALSV_EQ_EULER || c->ndim != 2) return ctx_fail(c, ALSV_ERR_INVALID_ARG, "adjoint: 2D Euler only");
     if (c->g.nlev != 1) return ctx_fail(c, ALSV_ERR_INVALID_ARG, "adjoint: single-level contexts only");
+    if (ctx_has_halo(c)) return ctx_fail(c, ALSV_ERR_INVALID_ARG, "adjoint: no halo faces (whole grids only)");
     if (c->d.flux != ALSV_FLUX_RUSANOV) return ctx_fail(c, ALSV_ERR_INVALID_ARG, "adjoint: Rusanov flux only");
     if (c->d.recon != ALSV_RECON_PC && c->d.recon != ALSV_RECON_MC)
         return ctx_fail(c, ALSV_ERR_INVALID_ARG, "adjoint: PC or MC reconstruction only");

@@ -46,6 +46,9 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 bool variant_ok(const alsv_ctx* c, int v) {
     if (!stage_variant_supported(c->fp64, c->ndim, c->eq, c->d.recon, c->g.rvars, c->d.flux, c->g.bc, v)) return false;
+    // halo faces are read by the tile kernels and the 3D z-march (every variant but the FP32 2D
+    // column march and two-sample schedules, 3-6)
+    if (ctx_has_halo(c) && !c->fp64 && c->ndim == 2 && v >= 3) return false;
     if (stage_variant_halves(c->fp64, c->ndim, v)) {
         // the halves must align with whole tiles: ny divisible by twice the tile height
         const TileShape ts = stage_tile(c->fp64, c->ndim, v);
@@ -107,6 +110,7 @@ StageArgs stage_args(alsv_ctx* c, const void* Us, const void* Un, void* Uout, do
     s.done = c->done;
     s.speed_part = c->part;
     s.want_speed = want_speed ? 1 : 0;
+    for (int f = 0; f < 6; ++f) s.halo[f] = c->halo[f];
     return s;
 }
 
@@ -127,6 +131,8 @@ FinishArgs finish_args(alsv_ctx* c, int advance) {
     f.cfl_guard = 0.5;
     f.cfl_max = nullptr;
     f.advance = advance;
+    f.smax_in = nullptr;
+    f.smax_out = nullptr;
     return f;
 }
 
@@ -154,28 +160,35 @@ void prof_collect(alsv_ctx* c) {
     p.kinds.clear();
 }
 
+// Buffers and coefficients of SSP-RK stage k: Uout = a U^n + b (U^(k) + dt L(U^(k))).
+struct StageIO { const void* Us; const void* Un; void* Uo; double a, b; };
+StageIO stage_io(const alsv_ctx* c, int k) {
+    if (c->nstages == 2) {
+        if (k == 0) return {c->U, nullptr, c->A, 0.0, 1.0};
+        return {c->A, c->U, c->U, 0.5, 0.5};
+    }
+    if (k == 0) return {c->U, nullptr, c->A, 0.0, 1.0};
+    if (k == 1) return {c->A, c->U, c->Bb, 0.75, 0.25};
+    return {c->Bb, c->U, c->U, 1.0 / 3.0, 2.0 / 3.0};
+}
+
+alsv_status enqueue_stage(alsv_ctx* c, int k) {
+    const StageIO io = stage_io(c, k);
+    StageArgs a = stage_args(c, io.Us, io.Un, io.Uo, io.a, io.b, k == c->nstages - 1);
+    if (c->prof.on && c->prof.ev.empty()) prof_mark(c, -1);
+    if (c->prof.on) c->prof.kinds.push_back(0);
+    cudaError_t e = launch_stage(c->fp64, c->ndim, c->eq, c->d.recon, c->d.flux, c->variant, a, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "stage kernel launch");
+    prof_mark(c, -1);
+    c->launches++;
+    return ALSV_OK;
+}
+
 // Enqueue one full SSP-RK step: stages + per-sample time control.
 alsv_status enqueue_step(alsv_ctx* c) {
-    const double third = 1.0 / 3.0, two_third = 2.0 / 3.0;
-    struct St { const void* Us; const void* Un; void* Uo; double a, b; };
-    St st[3];
-    int ns = c->nstages;
-    if (ns == 2) {
-        st[0] = {c->U, nullptr, c->A, 0.0, 1.0};
-        st[1] = {c->A, c->U, c->U, 0.5, 0.5};
-    } else {
-        st[0] = {c->U, nullptr, c->A, 0.0, 1.0};
-        st[1] = {c->A, c->U, c->Bb, 0.75, 0.25};
-        st[2] = {c->Bb, c->U, c->U, third, two_third};
-    }
-    for (int k = 0; k < ns; ++k) {
-        StageArgs a = stage_args(c, st[k].Us, st[k].Un, st[k].Uo, st[k].a, st[k].b, k == ns - 1);
-        if (c->prof.on && c->prof.ev.empty()) prof_mark(c, -1);
-        if (c->prof.on) c->prof.kinds.push_back(0);
-        cudaError_t e = launch_stage(c->fp64, c->ndim, c->eq, c->d.recon, c->d.flux, c->variant, a, c->stream);
-        if (e != cudaSuccess) return cuda_fail(c, e, "stage kernel launch");
-        prof_mark(c, -1);
-        c->launches++;
+    for (int k = 0; k < c->nstages; ++k) {
+        alsv_status st = enqueue_stage(c, k);
+        if (st != ALSV_OK) return st;
     }
     FinishArgs f = finish_args(c, 1);
     if (c->prof.on) c->prof.kinds.push_back(1);
@@ -282,6 +295,11 @@ FinishArgs ctx_finish_args(alsv_ctx* c, int advance) { return finish_args(c, adv
 StageArgs ctx_stage_args(alsv_ctx* c, const void* Us, const void* Un, void* Uout, double a, double b, bool want_speed) {
     return stage_args(c, Us, Un, Uout, a, b, want_speed);
 }
+bool ctx_has_halo(const alsv_ctx* c) {
+    for (int k = 0; k < 3; ++k)
+        if (c->g.bc[k][0] == BC_HALO || c->g.bc[k][1] == BC_HALO) return true;
+    return false;
+}
 }  // namespace alsv
 
 // =============================================================================================
@@ -363,7 +381,7 @@ alsv_status alsv_init_grid(const alsv_grid_desc* d_in, void* stream, alsv_ctx** 
     if (d.fixed_dt < 0.0 || !std::isfinite(d.fixed_dt)) return bad("fixed_dt must be >= 0 and finite");
     if (d.weno_eps == 0.0) d.weno_eps = 1e-6;
     if (!(d.weno_eps > 0.0)) return bad("weno_eps must be > 0");
-    for (int k = 0; k < 5; ++k)
+    for (int k = 0; k < 4; ++k)
         if (d.reserved[k] != 0) return bad("reserved fields must be zero");
     if (d.sampler < ALSV_SAMPLER_MC || d.sampler > ALSV_SAMPLER_HALTON_SHIFTED) return bad("unknown sampler");
     if (d.sample_offset < 0) return bad("sample_offset must be >= 0");
@@ -372,10 +390,26 @@ alsv_status alsv_init_grid(const alsv_grid_desc* d_in, void* stream, alsv_ctx** 
     const int G = d.recon == ALSV_RECON_PC ? 1 : 2;
     for (int k = 0; k < 3; ++k)
         for (int s = 0; s < 2; ++s)
-            if (d.bc[k][s] < 0 || d.bc[k][s] > 2) return bad("bc must be PERIODIC, OUTFLOW or REFLECTIVE");
+            if (d.bc[k][s] < 0 || d.bc[k][s] > 3) return bad("bc must be PERIODIC, OUTFLOW, REFLECTIVE or HALO");
     for (int k = 0; k < d.ndim; ++k)
         if ((d.bc[k][0] == ALSV_BC_PERIODIC) != (d.bc[k][1] == ALSV_BC_PERIODIC))
             return bad("a periodic side must be paired with a periodic side");
+    // block of a decomposed grid
+    bool block = false, halo = false;
+    for (int k = 0; k < 3; ++k) {
+        if (d.global_n[k] != 0 || d.offset[k] != 0) block = true;
+        if (k < d.ndim && (d.bc[k][0] == ALSV_BC_HALO || d.bc[k][1] == ALSV_BC_HALO)) halo = true;
+        if (k >= d.ndim && (d.global_n[k] > 1 || d.offset[k] != 0))
+            return bad("global_n / offset of an inactive direction must be 0");
+        if (k < d.ndim && d.global_n[k] == 0 && d.offset[k] != 0) return bad("offset needs global_n");
+        if (k < d.ndim && d.global_n[k] != 0 &&
+            (d.offset[k] < 0 || (long long)d.offset[k] + d.n[k] > d.global_n[k]))
+            return bad("a block must lie inside the whole grid: 0 <= offset and offset + n <= global_n");
+    }
+    if ((block || halo) && d.n_levels > 1) return bad("decomposed grids and halo faces need a single grid (n_levels <= 1)");
+    for (int k = 0; k < d.ndim; ++k)
+        if ((d.bc[k][0] == ALSV_BC_HALO || d.bc[k][1] == ALSV_BC_HALO) && d.n[k] < G)
+            return bad("a block with a halo face needs at least as many cells as ghost layers across it");
 
     auto* c = new alsv_ctx();
     c->d = d;
@@ -406,7 +440,8 @@ alsv_status alsv_init_grid(const alsv_grid_desc* d_in, void* stream, alsv_ctx** 
                 delete c;
                 return bad("reflective boundaries need at least as many cells as ghost layers");
             }
-            L.dx[k] = k < d.ndim ? (d.hi[k] - d.lo[k]) / L.n[k] : 1.0;
+            const int ng = k < d.ndim && d.global_n[k] != 0 ? d.global_n[k] : L.n[k];  // whole grid
+            L.dx[k] = k < d.ndim ? (d.hi[k] - d.lo[k]) / ng : 1.0;
             L.inv_dx[k] = 1.0 / L.dx[k];
         }
         samples += L.samples;
@@ -454,6 +489,7 @@ alsv_status alsv_init_grid(const alsv_grid_desc* d_in, void* stream, alsv_ctx** 
     }
     g.weno_eps = d.weno_eps;
     g.weno_eps_dx2 = d.weno_eps_dx2;
+    for (int k = 0; k < 3; ++k) g.off[k] = d.offset[k];
     // tiling: keep the largest work count over variants for the partials buffer
     long long mx = 0;
     for (int v = 0; v < stage_num_variants(c->fp64, c->ndim); ++v) {
@@ -602,6 +638,7 @@ alsv_status alsv_set_initial_data(alsv_ctx* c, int kind, const double* theta_dev
     st = enqueue_speed_and_prepare(c);
     if (st != ALSV_OK) return st;
     c->time_ready = true;
+    c->stage_next = 0;
     return ALSV_OK;
 }
 
@@ -621,6 +658,7 @@ alsv_status alsv_set_time(alsv_ctx* c, const double* t_host, const int64_t* step
     st = enqueue_speed_and_prepare(c);
     if (st != ALSV_OK) return st;
     c->time_ready = true;
+    c->stage_next = 0;
     return ALSV_OK;
 }
 
@@ -628,6 +666,7 @@ alsv_status alsv_step(alsv_ctx* c, int n_steps) {
     alsv_status st = require_ready(c);
     if (st != ALSV_OK) return st;
     if (n_steps < 0) return fail(c, ALSV_ERR_INVALID_ARG, "n_steps must be >= 0");
+    if (ctx_has_halo(c)) return fail(c, ALSV_ERR_INVALID_ARG, "halo faces: step with alsv_stage / alsv_finish_step");
     NvtxRange range("alsv: steps");
     for (int i = 0; i < n_steps; ++i) {
         st = enqueue_step(c);
@@ -650,6 +689,7 @@ alsv_status alsv_evolve_to_T(alsv_ctx* c, double T, int64_t* steps_taken_host) {
     alsv_status st = require_ready(c);
     if (st != ALSV_OK) return st;
     if (!std::isfinite(T) || T < 0.0) return fail(c, ALSV_ERR_INVALID_ARG, "T must be finite and >= 0");
+    if (ctx_has_halo(c)) return fail(c, ALSV_ERR_INVALID_ARG, "halo faces: step with alsv_stage / alsv_finish_step");
     long long n_target = LLONG_MAX;
     if (c->d.fixed_dt > 0.0) n_target = (long long)std::ceil(T / c->d.fixed_dt * (1.0 - 1e-12));
     st = set_run_params(c, T, n_target);
@@ -845,6 +885,7 @@ int alsv_num_tile_variants(const alsv_ctx* c) { return c ? stage_num_variants(c-
 alsv_status alsv_autotune(alsv_ctx* c, int reps, int* chosen, float* ms_per_variant) {
     alsv_status st = require_ready(c);
     if (st != ALSV_OK) return st;
+    if (ctx_has_halo(c) && !c->halo_bound) return fail(c, ALSV_ERR_NOT_READY, "halo buffers not bound (alsv_bind_halo)");
     if (reps < 1) reps = 1;
     const int nvar = stage_num_variants(c->fp64, c->ndim);
     int best = c->variant;
@@ -944,6 +985,119 @@ alsv_status alsv_get_tile(const alsv_ctx* c, int* tx, int* ty, int* tz, int* var
     if (variant) *variant = c->variant;
     if (work_items) *work_items = c->g.total_work;
     return ALSV_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Domain decomposition (Sec. 2.1, last paragraph; Sec. 3.1): a block of a decomposed grid steps
+// stage by stage; the caller refills its halo buffers between stages and takes the CFL maximum
+// over every block.
+// ---------------------------------------------------------------------------------------------
+static long long halo_elems(const alsv_ctx* c, int f) {
+    const int k = f >> 1;
+    if (k >= c->ndim || c->g.bc[k][f & 1] != BC_HALO) return 0;
+    const LevelInfo& L = c->g.lev[0];
+    const long long cross = (long long)L.n[0] * L.n[1] * L.n[2] / L.n[k];
+    return (long long)L.samples * c->nv * c->G * cross;
+}
+
+alsv_status alsv_halo_info(const alsv_ctx* c, int32_t* layers, int64_t* elems) {
+    if (!c) return fail(nullptr, ALSV_ERR_INVALID_ARG, "null context");
+    if (layers) *layers = c->G;
+    if (elems)
+        for (int f = 0; f < 6; ++f) elems[f] = halo_elems(c, f);
+    return ALSV_OK;
+}
+
+alsv_status alsv_bind_halo(alsv_ctx* c, const void* const* halo_dev, size_t bytes_each) {
+    if (!c) return fail(nullptr, ALSV_ERR_INVALID_ARG, "null context");
+    if (!halo_dev) return fail(c, ALSV_ERR_INVALID_ARG, "null halo pointer array");
+    const size_t esz = c->fp64 ? 8 : 4;
+    for (int f = 0; f < 6; ++f) {
+        const long long n = halo_elems(c, f);
+        if (n == 0) continue;
+        if (!halo_dev[f]) return fail(c, ALSV_ERR_INVALID_ARG, "a halo face needs a buffer");
+        if (((uintptr_t)halo_dev[f] & 15) != 0) return fail(c, ALSV_ERR_INVALID_ARG, "halo buffers must be 16-byte aligned");
+        if (bytes_each < (size_t)n * esz) return fail(c, ALSV_ERR_BUFFER_TOO_SMALL, "halo buffer smaller than alsv_halo_info's size");
+    }
+    for (int f = 0; f < 6; ++f) c->halo[f] = halo_elems(c, f) ? halo_dev[f] : nullptr;
+    c->halo_bound = true;
+    return ALSV_OK;
+}
+
+alsv_status alsv_halo_pack(alsv_ctx* c, int stage, void* const* send_dev, size_t bytes_each) {
+    alsv_status st = require_ready(c);
+    if (st != ALSV_OK) return st;
+    if (c->g.nlev != 1) return fail(c, ALSV_ERR_INVALID_ARG, "halo layers need a single grid");
+    if (stage < 0 || stage >= c->nstages) return fail(c, ALSV_ERR_INVALID_ARG, "stage out of range");
+    if (!send_dev) return fail(c, ALSV_ERR_INVALID_ARG, "null send pointer array");
+    const size_t esz = c->fp64 ? 8 : 4;
+    void* dst[6];
+    for (int f = 0; f < 6; ++f) {
+        dst[f] = send_dev[f];
+        if (!dst[f]) continue;
+        const int k = f >> 1;
+        if (k >= c->ndim) return fail(c, ALSV_ERR_INVALID_ARG, "send buffer for an inactive direction");
+        if (c->g.lev[0].n[k] < c->G) return fail(c, ALSV_ERR_INVALID_ARG, "fewer cells than ghost layers across a face");
+        const LevelInfo& L = c->g.lev[0];
+        const long long n = (long long)L.samples * c->nv * c->G * ((long long)L.n[0] * L.n[1] * L.n[2] / L.n[k]);
+        if (bytes_each < (size_t)n * esz) return fail(c, ALSV_ERR_BUFFER_TOO_SMALL, "send buffer smaller than a face's layers");
+    }
+    const void* src = stage_io(c, stage).Us;
+    cudaError_t e = launch_halo_pack(c->fp64, c->g, c->G, src, dst, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "halo pack kernel");
+    for (int f = 0; f < 6; ++f) c->launches += dst[f] ? 1 : 0;
+    return ALSV_OK;
+}
+
+alsv_status alsv_stage(alsv_ctx* c, int stage) {
+    alsv_status st = require_ready(c);
+    if (st != ALSV_OK) return st;
+    if (!c->time_ready) return fail(c, ALSV_ERR_NOT_READY, "no time state (alsv_set_initial_data)");
+    if (ctx_has_halo(c) && !c->halo_bound) return fail(c, ALSV_ERR_NOT_READY, "halo buffers not bound (alsv_bind_halo)");
+    if (stage != c->stage_next || stage >= c->nstages)
+        return fail(c, ALSV_ERR_INVALID_ARG, "stages run in order 0 .. stages-1, then alsv_finish_step");
+    st = enqueue_stage(c, stage);
+    if (st != ALSV_OK) return st;
+    c->stage_next = stage + 1;
+    return ALSV_OK;
+}
+
+alsv_status alsv_speed_max(alsv_ctx* c, double* smax_dev) {
+    alsv_status st = require_ready(c);
+    if (st != ALSV_OK) return st;
+    if (!smax_dev) return fail(c, ALSV_ERR_INVALID_ARG, "null output");
+    if (c->stage_next != 0 && c->stage_next != c->nstages)
+        return fail(c, ALSV_ERR_INVALID_ARG, "the maximum speed is defined before the first or after the last stage");
+    FinishArgs f = finish_args(c, 0);
+    f.smax_out = smax_dev;
+    cudaError_t e = launch_finish(f, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "finish kernel launch");
+    c->launches++;
+    return ALSV_OK;
+}
+
+alsv_status alsv_finish_step(alsv_ctx* c, const double* smax_dev, int advance) {
+    alsv_status st = require_ready(c);
+    if (st != ALSV_OK) return st;
+    if (!smax_dev) return fail(c, ALSV_ERR_INVALID_ARG, "null maximum");
+    if (advance ? c->stage_next != c->nstages : c->stage_next != 0)
+        return fail(c, ALSV_ERR_INVALID_ARG, advance ? "advance = 1 follows the last stage" : "advance = 0 comes before the first stage");
+    FinishArgs f = finish_args(c, advance ? 1 : 0);
+    f.smax_in = smax_dev;
+    cudaError_t e = launch_finish(f, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "finish kernel launch");
+    c->launches++;
+    c->stage_next = 0;
+    return ALSV_OK;
+}
+
+alsv_status alsv_set_end_time(alsv_ctx* c, double T) {
+    alsv_status st = require_ready(c);
+    if (st != ALSV_OK) return st;
+    if (!std::isfinite(T) || T < 0.0) return fail(c, ALSV_ERR_INVALID_ARG, "T must be finite and >= 0");
+    long long n_target = LLONG_MAX;
+    if (c->d.fixed_dt > 0.0) n_target = (long long)std::ceil(T / c->d.fixed_dt * (1.0 - 1e-12));
+    return set_run_params(c, T, n_target);
 }
 
 }  // extern "C"

@@ -68,6 +68,11 @@ struct alsv_ctx {
     double adj_dt = 0.0;
     int adj_passes = 0;
     bool have_theta = false;
+    // block of a decomposed grid: caller-bound halo buffers per face, next stage of the
+    // stage-by-stage protocol (alsv_stage / alsv_finish_step)
+    const void* halo[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    bool halo_bound = false;
+    int stage_next = 0;
 };
 
 namespace alsv {
@@ -76,4 +81,6 @@ alsv_status ctx_fail(alsv_ctx* c, alsv_status st, const std::string& msg);
 alsv_status ctx_cuda_fail(alsv_ctx* c, cudaError_t e, const char* what);
 FinishArgs ctx_finish_args(alsv_ctx* c, int advance);
 StageArgs ctx_stage_args(alsv_ctx* c, const void* Us, const void* Un, void* Uout, double a, double b, bool want_speed);
+// whether any face of the context is a halo face of a decomposed grid
+bool ctx_has_halo(const alsv_ctx* c);
 }  // namespace alsv

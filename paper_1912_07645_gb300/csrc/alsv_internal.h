@@ -11,7 +11,7 @@ enum { EQ_BURGERS = 0, EQ_EULER = 1 };
 enum { REC_PC = 0, REC_MC = 1, REC_WENO3 = 2 };
 enum { RV_CONS = 0, RV_PRIM = 1 };
 enum { FLX_RUSANOV = 0, FLX_HLL = 1, FLX_HLLC = 2 };
-enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_REFLECTIVE = 2 };
+enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_REFLECTIVE = 2, BC_HALO = 3 };
 
 // Device status bits (OR-ed into the status word by kernels; kernels never trap).
 enum { ST_NONPHYSICAL = 1, ST_CFL = 2, ST_TIMEOUT = 4 };
@@ -67,6 +67,7 @@ struct GridArgs {
     int bc[3][2];
     double weno_eps;
     int weno_eps_dx2;
+    int off[3];        // block of a decomposed grid: global index of the first cell per direction
 };
 
 // One SSP-RK stage: Uout = a * Un + b * (Us + dt * L(Us)); a == 0 means Un is not read.
@@ -80,6 +81,7 @@ struct StageArgs {
     const int* done;      // [samples]; nonzero: the sample is skipped
     double* speed_part;   // [work items]; written when want_speed
     int want_speed;
+    const void* halo[6];  // face 2k + side with bc HALO: [samples][NV][G][cross] ghost layers
 };
 
 // Tile shape used for a given (precision, ndim); the host derives the tiling from it.
@@ -115,6 +117,8 @@ struct FinishArgs {
     double cfl_guard;      // fixed mode: realised CFL limit
     double* cfl_max;       // fixed mode, nullable: running maximum of the realised CFL number
     int advance;           // 1: the step just finished (advance t); 0: only prepare dt
+    const double* smax_in; // nullable: per-sample maximum speed from outside (decomposed grids)
+    double* smax_out;      // nullable: only write each sample's maximum speed (+inf if non-finite)
 };
 cudaError_t launch_finish(const FinishArgs& a, cudaStream_t s);
 
@@ -128,6 +132,9 @@ struct InitArgs {
     double vortex_center[2];
 };
 cudaError_t launch_init(int fp64, int ndim, const InitArgs& a, cudaStream_t s);
+// Boundary layers of a block for its neighbours' halos: for each face f with dst[f] != NULL,
+// dst[f][b][v][l][cross] = U[b][v][...] at index l (low face) or n_k - G + l (high face) along k.
+cudaError_t launch_halo_pack(int fp64, const GridArgs& g, int G, const void* U, void* const dst[6], cudaStream_t s);
 // Counter index of each sample's KH parameters: sample s of group l uses src0[l] + (s - sample0[l])
 // (an MLMC companion group takes its level's indices, every other group its own).
 struct ThetaMap {

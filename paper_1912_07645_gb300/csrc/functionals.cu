@@ -236,6 +236,8 @@ int sf_splits(const alsv_ctx* c) {
 
 alsv_status sf_check(alsv_ctx* c, int q, int p, int Rr) {
     if (c->g.nlev != 1) return ctx_fail(c, ALSV_ERR_INVALID_ARG, "structure functions need a single-level context");
+    if (ctx_has_halo(c))
+        return ctx_fail(c, ALSV_ERR_INVALID_ARG, "structure functions need the whole grid (pairs cross halo faces)");
     if (q < 0 || q >= c->nv) return ctx_fail(c, ALSV_ERR_INVALID_ARG, "quantity index out of range");
     if (p != 1 && p != 2) return ctx_fail(c, ALSV_ERR_INVALID_ARG, "order p must be 1 or 2");
     const int rmax = c->ndim == 3 ? kSfMaxR3 : kSfMaxR2;

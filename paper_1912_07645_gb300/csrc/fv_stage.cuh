@@ -179,6 +179,44 @@ __device__ __forceinline__ void interface_states(const R* sw, int i0, int step, 
     face_states<R, EQ, ND, RECON>(cm, cl, cr, c2, rvars, gm1, eps, WL, WR);
 }
 
+// Ghost cell of a block of a decomposed grid (Sec. 2.1, last paragraph; Sec. 3.1): a cell beyond
+// a face of kind BC_HALO is read from that face's halo buffer [sample][var][layer][cross], layer l
+// of the low face holding index -G + l along the face's direction and of the high face n + l,
+// cross = the other directions' cells in (z, y, x) order. Returns the face 2k + side (-1: not a
+// halo cell) with the cell's offset and the stride between variables in the buffer. The other
+// coordinates are clamped into the block: only tile corners reach outside it there, and the
+// direction-by-direction stencils never read tile corners.
+template <int ND, int G>
+__device__ __forceinline__ int halo_cell(const GridArgs& g, int ix, int iy, int iz, int nx, int ny, int nz, int& off,
+                                         int& vstride) {
+    const int c[3] = {ix, iy, iz};
+    const int n[3] = {nx, ny, nz};
+    int f = -1, layer = 0;
+#pragma unroll
+    for (int k = 0; k < ND; ++k) {
+        if (f >= 0) break;
+        if (c[k] < 0 && g.bc[k][0] == BC_HALO) {
+            f = 2 * k;
+            layer = c[k] + G > 0 ? c[k] + G : 0;
+        } else if (c[k] >= n[k] && g.bc[k][1] == BC_HALO) {
+            f = 2 * k + 1;
+            layer = c[k] - n[k] < G - 1 ? c[k] - n[k] : G - 1;
+        }
+    }
+    if (f < 0) return -1;
+    int cross = 0, csize = 1;
+#pragma unroll
+    for (int j = ND - 1; j >= 0; --j) {
+        if (j == (f >> 1)) continue;
+        const int cj = c[j] < 0 ? 0 : (c[j] >= n[j] ? n[j] - 1 : c[j]);
+        cross = cross * n[j] + cj;
+        csize *= n[j];
+    }
+    off = layer * csize + cross;
+    vstride = G * csize;
+    return f;
+}
+
 // RV: reconstruction variables (primitive or conserved) as a compile-time choice, so that each
 // instantiation carries only its own conversion path
 template <class R, int EQ, int ND, int RECON, int FLUX, int TX, int TY, int TZ, int NT, int RV = RV_PRIM>
@@ -236,15 +274,22 @@ __global__ void __launch_bounds__(NT) k_stage(const StageArgs p) {
         const int sz = ND >= 3 ? s / (SX * SY) : 0;
         bool flip[3] = {false, false, false};
         int ix = tx0 + sx - G, iy = ND >= 2 ? ty0 + sy - G : 0, iz = ND >= 3 ? tz0 + sz - G : 0;
+        const R* src = Us;
+        int off = 0, vstride = plane, hf = -1;
         if (!interior) {
-            ix = map_ghost(ix, nx, g.bc[0][0], g.bc[0][1], flip[0]);
-            if (ND >= 2) iy = map_ghost(iy, ny, g.bc[1][0], g.bc[1][1], flip[1]);
-            if (ND >= 3) iz = map_ghost(iz, nz, g.bc[2][0], g.bc[2][1], flip[2]);
+            hf = halo_cell<ND, G>(g, ix, iy, iz, nx, ny, nz, off, vstride);
+            if (hf >= 0) {
+                src = reinterpret_cast<const R*>(p.halo[hf]) + (long long)b_local * NV * vstride;
+            } else {
+                ix = map_ghost(ix, nx, g.bc[0][0], g.bc[0][1], flip[0]);
+                if (ND >= 2) iy = map_ghost(iy, ny, g.bc[1][0], g.bc[1][1], flip[1]);
+                if (ND >= 3) iz = map_ghost(iz, nz, g.bc[2][0], g.bc[2][1], flip[2]);
+            }
         }
-        const int off = (iz * ny + iy) * nx + ix;
+        if (hf < 0) off = (iz * ny + iy) * nx + ix;
         R u[NV];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) u[v] = Us[v * plane + off];
+        for (int v = 0; v < NV; ++v) u[v] = src[v * vstride + off];
         if (EQ == EQ_BURGERS) {
             if (flip[0] ^ flip[1] ^ flip[2]) u[0] = -u[0];
             sW[s] = u[0];

@@ -69,21 +69,30 @@ __global__ void __launch_bounds__(TX * TY, 4) k_stage3d_zm(const StageArgs p) {
     // load plane zz (any integer; ghost-mapped in z) into its ring slot
     auto load_plane = [&](int zz) {
         bool fz = false;
-        const int iz = map_ghost(zz, nz, g.bc[2][0], g.bc[2][1], fz);
+        // a plane beyond a halo face of a block comes from that face's halo buffer
+        const bool zhalo = (zz < 0 && g.bc[2][0] == BC_HALO) || (zz >= nz && g.bc[2][1] == BC_HALO);
+        const int iz = zhalo ? zz : map_ghost(zz, nz, g.bc[2][0], g.bc[2][1], fz);
         R* dst = sW + ((zz % NP + NP) % NP) * PS * CS;
 #pragma unroll 1
         for (int s = tid; s < PS; s += NT) {
             const int sx = s % SX, sy = s / SX;
             bool flip[3] = {false, false, fz};
             int ix = tx0 + sx - G, iy = ty0 + sy - G;
-            if (!xy_interior) {
-                ix = map_ghost(ix, nx, g.bc[0][0], g.bc[0][1], flip[0]);
-                iy = map_ghost(iy, ny, g.bc[1][0], g.bc[1][1], flip[1]);
+            const R* src = Us;
+            int off = 0, vstride = plane, hf = -1;
+            if (!xy_interior || zhalo) {
+                hf = halo_cell<3, G>(g, ix, iy, iz, nx, ny, nz, off, vstride);
+                if (hf >= 0) {
+                    src = reinterpret_cast<const R*>(p.halo[hf]) + (long long)b_local * NV * vstride;
+                } else if (!xy_interior) {
+                    ix = map_ghost(ix, nx, g.bc[0][0], g.bc[0][1], flip[0]);
+                    iy = map_ghost(iy, ny, g.bc[1][0], g.bc[1][1], flip[1]);
+                }
             }
-            const int off = (iz * ny + iy) * nx + ix;
+            if (hf < 0) off = (iz * ny + iy) * nx + ix;
             R u[NV];
 #pragma unroll
-            for (int v = 0; v < NV; ++v) u[v] = Us[v * plane + off];
+            for (int v = 0; v < NV; ++v) u[v] = src[v * vstride + off];
 #pragma unroll
             for (int k = 0; k < ND; ++k)
                 if (flip[k]) u[1 + k] = -u[1 + k];

@@ -1,21 +1,27 @@
 // Per-sample time control (CFL step), initial data, counter-based parameters, Monte Carlo
 // statistics (Sec. 2.2) and fixed-order FP64 reductions.
+#include <algorithm>
+
 #include "fv_physics.cuh"
 #include "fv_quantities.cuh"
 
 namespace alsv {
 
 // ---------------------------------------------------------------------------------------------
-// Time control, one thread per sample. Adaptive mode (reading; the paper gives no CFL rule):
-// s_b = max over tiles of the per-tile partials (the largest (|u_k| + c) / dx_k), dt_b =
-// cfl / s_b, clipped to T - t_b (then the sample lands exactly on T and is done). Fixed mode:
-// dt = fixed_dt until n_target steps; the realised CFL number dt * s_b is checked against a guard.
-// A NaN partial marks a non-physical sample: it stops and the status word records it.
-// ---------------------------------------------------------------------------------------------
+// Time control per sample. Adaptive mode (reading; the paper gives no CFL rule): s_b = max over
+// tiles of the per-tile partials (the largest (|u_k| + c) / dx_k), dt_b = cfl / s_b, clipped to
+// T - t_b (then the sample lands exactly on T and is done). Fixed mode: dt = fixed_dt until
+// n_target steps; the realised CFL number dt * s_b is checked against a guard. A NaN partial marks
+// a non-physical sample: it stops and the status word records it.
 // One block per sample: the block's threads stride over the sample's tile partials and combine
 // them with a shuffle tree. The maximum of non-negative doubles is exact in any order, so the
-// result is bitwise independent of the block size; a NaN anywhere marks the sample.
+// result is bitwise independent of the block size. A decomposed grid splits this in two: the
+// maximum of each block (smax_out), then the time control from the maximum over all blocks
+// (smax_in).
+// ---------------------------------------------------------------------------------------------
 constexpr int FINISH_NT = 256;
+
+__device__ void finish_sample(const FinishArgs& a, int s, double smax, int bad);
 
 __global__ void __launch_bounds__(FINISH_NT) k_finish(const FinishArgs a) {
     const int s = blockIdx.x;
@@ -23,6 +29,13 @@ __global__ void __launch_bounds__(FINISH_NT) k_finish(const FinishArgs a) {
     const LevelInfo& L = a.g.lev[l];
     const int b = s - L.sample0;
     if (a.advance && a.done[s]) return;  // skipped by this step's stages (uniform over the block)
+    if (a.smax_in) {
+        // decomposed grid: the maximum over every block, taken by the caller
+        if (threadIdx.x != 0) return;
+        const double v = a.smax_in[s];
+        finish_sample(a, s, v, !(v < INFINITY));
+        return;
+    }
     const double* part = a.speed_part + L.work0 + (long long)b * L.tiles;
     double smax = 0.0;
     int bad = 0;
@@ -42,6 +55,16 @@ __global__ void __launch_bounds__(FINISH_NT) k_finish(const FinishArgs a) {
     if (threadIdx.x != 0) return;
 #pragma unroll
     for (int w = 1; w < FINISH_NT / 32; ++w) smax = wmax[w] > smax ? wmax[w] : smax;
+    if (a.smax_out) {
+        a.smax_out[s] = bad ? INFINITY : smax;
+        return;
+    }
+    finish_sample(a, s, smax, bad);
+}
+
+// Time control of sample s from its maximum speed: advance t and the step count after a step,
+// then the next dt (CFL or fixed), the last-step and done flags and the status bits.
+__device__ void finish_sample(const FinishArgs& a, int s, double smax, int bad) {
     if (a.advance) {
         double t = a.t[s];
         const long long n = a.nstep[s] + 1;
@@ -192,12 +215,13 @@ __global__ void k_init_kh(const InitArgs a) {
     const double PI = 3.14159265358979323846;
     const double* th = a.theta + (long long)s * a.P;
     const double hx = L.dx[0], hy = L.dx[1];
-    const double xc = a.g.lo[0] + (x + 0.5) * hx;
+    // cell centres from the whole grid's indices (a block of a decomposed grid is offset by off)
+    const double xc = a.g.lo[0] + (x + a.g.off[0] + 0.5) * hx;
     double Y = 0.0;
     if (ND == 2) {
         for (int n = 1; n <= 10; ++n) Y = Y + th[n - 1] * sin(2.0 * PI * n * xc + th[10 + n - 1]);
     } else {
-        const double zc = a.g.lo[2] + (z + 0.5) * L.dx[2];
+        const double zc = a.g.lo[2] + (z + a.g.off[2] + 0.5) * L.dx[2];
         for (int n = 1; n <= 8; ++n)
             for (int m = 1; m <= 8; ++m) {
                 const int j = (n - 1) * 8 + (m - 1);
@@ -210,7 +234,7 @@ __global__ void k_init_kh(const InitArgs a) {
     const long long plane = (long long)nx * ny * nz;
     R* U = reinterpret_cast<R*>(a.U) + L.elem0 + (long long)b * NV * plane;
     for (int y = 0; y < ny; ++y) {
-        const double ylo = a.g.lo[1] + y * hy;
+        const double ylo = a.g.lo[1] + (y + a.g.off[1]) * hy;
         const double f_lo = clamp01((0.25 + Y - ylo) / hy);
         const double f_hi = clamp01((0.75 + Y - ylo) / hy);
         const double f = f_hi - f_lo;
@@ -247,8 +271,8 @@ __global__ void k_init_cell(const InitArgs a) {
     const long long plane = (long long)L.n[0] * L.n[1] * L.n[2];
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= plane) return;
-    const int x = (int)(i % L.n[0]);
-    const int y = (int)((i / L.n[0]) % L.n[1]);
+    const int x = (int)(i % L.n[0]) + a.g.off[0];          // whole-grid indices
+    const int y = (int)((i / L.n[0]) % L.n[1]) + a.g.off[1];
     R* U = reinterpret_cast<R*>(a.U) + L.elem0 + (long long)b * nv * plane;
     const double g = a.g.gamma;
     const double PI = 3.14159265358979323846;
@@ -318,6 +342,55 @@ static cudaError_t launch_init_t(int ndim, const InitArgs& a, cudaStream_t s) {
 
 cudaError_t launch_init(int fp64, int ndim, const InitArgs& a, cudaStream_t s) {
     return fp64 ? launch_init_t<double>(ndim, a, s) : launch_init_t<float>(ndim, a, s);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Halo layers of a block of a decomposed grid (Sec. 2.1, last paragraph; Sec. 3.1): the G cells
+// next to face f = 2k + side, gathered as [sample][var][layer][cross] for the neighbouring block,
+// cross = the other directions' cells in (z, y, x) order (x fastest). Layer l is index l along k
+// on the low face and n_k - G + l on the high face. A plain copy.
+// ---------------------------------------------------------------------------------------------
+template <class R>
+__global__ void k_halo_pack(const GridArgs g, int G, int face, const R* __restrict__ U, R* __restrict__ dst) {
+    const LevelInfo& L = g.lev[0];
+    const int k = face >> 1;
+    const int n[3] = {L.n[0], L.n[1], L.n[2]};
+    const long long csize = (long long)n[0] * n[1] * n[2] / n[k];
+    const long long total = (long long)L.samples * g.nv * G * csize;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
+        long long q = i % csize;
+        const long long r = i / csize;
+        const int layer = (int)(r % G);
+        const long long bv = r / G;  // sample * nv + var
+        int c[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            if (j == k) continue;
+            c[j] = (int)(q % n[j]);
+            q /= n[j];
+        }
+        c[k] = (face & 1) ? n[k] - G + layer : layer;
+        dst[i] = U[((bv * n[2] + c[2]) * n[1] + c[1]) * n[0] + c[0]];
+    }
+}
+
+cudaError_t launch_halo_pack(int fp64, const GridArgs& g, int G, const void* U, void* const dst[6], cudaStream_t s) {
+    const LevelInfo& L = g.lev[0];
+    for (int f = 0; f < 6; ++f) {
+        if (!dst[f]) continue;
+        const long long csize = (long long)L.n[0] * L.n[1] * L.n[2] / L.n[f >> 1];
+        const long long total = (long long)L.samples * g.nv * G * csize;
+        if (total <= 0) continue;
+        const unsigned blocks = (unsigned)std::min<long long>((total + 255) / 256, 152LL * 16);
+        if (fp64)
+            k_halo_pack<double><<<blocks, 256, 0, s>>>(g, G, f, static_cast<const double*>(U), static_cast<double*>(dst[f]));
+        else
+            k_halo_pack<float><<<blocks, 256, 0, s>>>(g, G, f, static_cast<const float*>(U), static_cast<float*>(dst[f]));
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 // ---------------------------------------------------------------------------------------------

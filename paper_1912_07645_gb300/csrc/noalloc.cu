@@ -61,7 +61,9 @@ extern "C" alsv_status alsv_conservation_totals_noalloc(const alsv_grid_desc* d,
             L.n[k] = k < d->ndim ? n[k] : 1;
             if (L.n[k] < 1) return bad(ALSV_ERR_INVALID_ARG, "every active direction needs n >= 1");
             if (k < d->ndim && !(d->hi[k] > d->lo[k])) return bad(ALSV_ERR_INVALID_ARG, "hi must exceed lo");
-            L.dx[k] = k < d->ndim ? (d->hi[k] - d->lo[k]) / L.n[k] : 1.0;
+            // a block of a decomposed grid has the whole grid's dx
+            const int ng = k < d->ndim && d->n_levels <= 1 && d->global_n[k] > 0 ? d->global_n[k] : L.n[k];
+            L.dx[k] = k < d->ndim ? (d->hi[k] - d->lo[k]) / ng : 1.0;
             L.inv_dx[k] = 1.0 / L.dx[k];
         }
         L.sample0 = (int)samples;

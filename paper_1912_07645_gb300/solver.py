@@ -10,13 +10,16 @@ from . import _abi as A
 def make_desc(ndim=1, n=(8, 1, 1), lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), batch=1, eq="euler", gamma=1.4,
               recon="mc", rvars="prim", flux="hllc", rk="ssprk2", bc="periodic", cfl=0.45, fixed_dt=0.0,
               precision="fp64", seed=0, weno_eps=1e-6, weno_eps_dx2=False, levels=None,
-              vortex_center=(5.0, 5.0), sample_offset=0, sampler="mc", **_ignored) -> A.alsv_grid_desc:
+              vortex_center=(5.0, 5.0), sample_offset=0, sampler="mc", global_n=None, offset=None,
+              **_ignored) -> A.alsv_grid_desc:
     """Build an ``alsv_grid_desc`` from plain values.
 
     ``bc``: one name for every side or a list of (lo, hi) names per direction.
     ``levels``: optional level table, a list of (n_tuple, samples) or (n_tuple, samples, fine):
     ``fine`` = index of the table entry this group is the MLMC coarse companion of (same samples
     and KH parameters on a coarser grid).
+    ``global_n`` / ``offset``: a block of a decomposed grid (whole grid's cells per direction, the
+    block's first cell); ``bc`` may then name "halo" faces (see ``decomp``).
     """
     d = A.alsv_grid_desc()
     d.ndim = ndim
@@ -54,6 +57,12 @@ def make_desc(ndim=1, n=(8, 1, 1), lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), batch
     d.vortex_center[0], d.vortex_center[1] = vortex_center
     d.sample_offset = int(sample_offset)
     d.sampler = A.SAMPLER[sampler]
+    if global_n is not None:
+        for k, v in enumerate(global_n):
+            d.global_n[k] = int(v) if k < ndim else 0
+    if offset is not None:
+        for k, v in enumerate(offset):
+            d.offset[k] = int(v) if k < ndim else 0
     return d
 
 
@@ -255,8 +264,48 @@ class Solver:
         A.alsv_adjoint_evolve(self.ctx, T, 0, th, g, J)
         return J, g
 
+    # ---- block of a decomposed grid: the stage-by-stage protocol driven by decomp.Decomposition
+    @property
+    def stages(self):
+        return 3 if self.desc.rk == 3 else 2
+
+    def halo_info(self):
+        """(ghost layers, element count of each face's halo buffer, 0 for faces that are not halo)."""
+        return A.alsv_halo_info(self.ctx)
+
+    def bind_halo(self):
+        """Allocate and bind this block's halo buffers (one per halo face, all of the largest face's
+        size); returns them."""
+        _, elems = self.halo_info()
+        m = max(elems)
+        with self.torch.cuda.stream(self.stream):
+            self.halos = [self.torch.zeros(m, dtype=self.dtype, device=self.device) if n else None for n in elems]
+        if m:
+            A.alsv_bind_halo(self.ctx, self.halos)
+        return self.halos
+
+    def halo_pack(self, stage, sends):
+        """Write the block's boundary layers of stage ``stage``'s input into ``sends`` (six buffers of
+        equal size or None)."""
+        A.alsv_halo_pack(self.ctx, stage, sends)
+
+    def stage(self, s):
+        A.alsv_stage(self.ctx, s)
+
+    def speed_max(self, out):
+        A.alsv_speed_max(self.ctx, out)
+
+    def finish_step(self, smax, advance):
+        A.alsv_finish_step(self.ctx, smax, advance)
+
+    def set_end_time(self, T):
+        A.alsv_set_end_time(self.ctx, T)
+
     def autotune(self, reps=3):
         return A.alsv_autotune(self.ctx, reps)
+
+    def set_tile_variant(self, v):
+        A.alsv_set_tile_variant(self.ctx, v)
 
     def close(self):
         if getattr(self, "ctx", None):

@@ -281,6 +281,14 @@ WORKLOADS = {
     "kh3d256_fp32": dict(desc=dict(ndim=3, n=(256, 256, 256), batch=1, eq="euler", recon="weno3", flux="hllc",
                                    rvars="prim", rk="ssprk3", bc="periodic", cfl=0.3, precision="fp32", seed=0),
                          init="kh", steps=10, words=8, nv=5, esize=4),
+    # one 1024^3 sample (5.4e9 elements, above one context's 2^31) as four z-blocks on one GPU with
+    # halo exchange between RK stages; the same scheme at 512^3 whole and as four blocks gives the
+    # decomposition's overhead, (t_blocks - t_whole) / t_whole per step (Sec. 3.1)
+    "kh3d1024_blocks_fp32": dict(desc=dict(ndim=3, n=(1024, 1024, 1024), batch=1, eq="euler", recon="weno3",
+                                           flux="hllc", rvars="prim", rk="ssprk3", bc="periodic", cfl=0.3,
+                                           precision="fp32", seed=0),
+                                 init="kh", steps=20, parts=(1, 1, 4), words=8, nv=5, esize=4, blocks=True,
+                                 overhead_n=(512, 512, 512), overhead_steps=40),
     "adjoint512_fp32": dict(desc=dict(ndim=2, n=(512, 512), batch=64, eq="euler", recon="mc", flux="rusanov",
                                       rvars="prim", rk="ssprk2", bc="periodic", cfl=0.4, precision="fp32", seed=SEED),
                             adjoint=True, T=1.0),
@@ -298,8 +306,106 @@ WORKLOADS = {
 # oracle's counting scalar (a CPU test checks them), and the ALU peaks: FP32 from the unit counts
 # (152 SMs x 128 lanes x 2 x 2.07 GHz), FP64 the GB300's nominal 1.25 TFLOP/s.
 WORKLOAD_FLOPS = {"sod1024_fp64": 287, "kh2d1024_fp32": 1980, "kh2d1024_fp64": 1980, "mlmc_fp32": 1980,
-                  "mlmc_coupled_fp32": 1980, "kh3d512_fp32": 3591, "kh3d256_fp32": 3591}
+                  "mlmc_coupled_fp32": 1980, "kh3d512_fp32": 3591, "kh3d256_fp32": 3591,
+                  "kh3d1024_blocks_fp32": 3591}
 FP64_PEAK_TFLOPS = 1.25
+
+
+def run_blocks_workload(name, W, args):
+    """A single sample decomposed into blocks on one GPU (halo exchange between RK stages)."""
+    import numpy as np
+    import torch
+    import paper_1912_07645_gb300 as alsv
+    from paper_1912_07645_gb300.decomp import Decomposition
+    peaks, peak_kind = measured_peaks()
+    cfg = W["desc"]
+    dec = Decomposition(parts=W["parts"], **cfg)
+    dec.set_initial_data(W["init"])
+    b0 = dec.blocks[0]
+    if args.tile_variant >= 0:
+        chosen, ms_var = args.tile_variant, []
+    else:
+        chosen, ms_var = b0.autotune(3)
+    for b in dec.blocks:
+        b.set_tile_variant(chosen)
+    cells = int(np.prod(cfg["n"]))
+
+    def one():
+        dec.set_initial_data(W["init"])
+        dec.step(W["steps"])
+        dec.sync()
+        return W["steps"] * cells
+
+    for _ in range(args.warmup):
+        one()
+    dec.set_profiling(True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    cu = 0
+    for _ in range(args.steps):
+        cu += one()
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    stage_ms, stage_launches = dec.stage_ms()
+    dec.set_profiling(False)
+    launches = sum(alsv.alsv_get_launch_count(b.ctx) for b in dec.blocks)
+    dec.close()
+    del dec
+    torch.cuda.empty_cache()
+
+    # overhead of the decomposition: the same scheme at a size one context holds, whole vs blocks
+    def per_step(parts):
+        kw = dict(cfg, n=W["overhead_n"])
+        if parts is None:
+            S = alsv.Solver(alsv.make_desc(**kw))
+            S.set_tile_variant(chosen)
+            S.set_initial_data(W["init"])
+            run = (lambda k: (S.step(k), S.sync()))
+            close = S.close
+        else:
+            D = Decomposition(parts=parts, tile_variant=chosen, **kw)
+            D.set_initial_data(W["init"])
+            run = (lambda k: (D.step(k), D.sync()))
+            close = D.close
+        run(3)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        run(W["overhead_steps"])
+        torch.cuda.synchronize()
+        ms = 1000 * (time.perf_counter() - t) / W["overhead_steps"]
+        close()
+        return ms
+
+    ms_whole = per_step(None)
+    ms_blocks = per_step(W["parts"])
+    bpc = W["words"] * W["nv"] * W["esize"]
+    # the blocks' stage launches run concurrently on their own streams, so their event times
+    # overlap: the achieved rates use the wall time of the timed steps (stages, halo packs and time
+    # control), a lower bound of the stage kernels' own rate
+    achieved = cu * bpc / el / 1e9
+    tflops = cu * WORKLOAD_FLOPS[name] / el / 1e12
+    line = {"metric": METRIC, "value": cu / el, "unit": "cell-updates/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000 * el / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": cfg["precision"], "data": "synthetic",
+            "config": {"workload": name, "grid": list(cfg["n"]), "blocks": list(W["parts"]),
+                       "rk_steps_per_pass": W["steps"], "samples": 1, "tile_variant": chosen,
+                       "autotune_ms": ms_var},
+            "ms_per_rk_step": 1000 * el / (args.steps * W["steps"]),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": achieved / peaks["hbm_gbs"] if achieved else None, "peak_kind": peak_kind,
+                         "algorithmic_bytes_per_cell_update": bpc, "time_basis": "wall time of the timed steps",
+                         "stage_event_ms_sum": stage_ms, "stage_launches": stage_launches,
+                         "step_ms_total": 1000 * el},
+            "alu_roofline": {"bound": "alu", "achieved": tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                             "frac": tflops / FP32_PEAK_TFLOPS,
+                             "flops_per_cell_update": WORKLOAD_FLOPS[name],
+                             "peak_kind": "nominal: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"},
+            "decomposition_overhead": {"grid": list(W["overhead_n"]), "blocks": list(W["parts"]),
+                                       "ms_per_step_whole": ms_whole, "ms_per_step_blocks": ms_blocks,
+                                       "overhead": (ms_blocks - ms_whole) / ms_whole},
+            "gpu_launches": launches}
+    print(json.dumps(line), flush=True)
+    return 0
 
 
 def run_workload(name, args):
@@ -309,6 +415,8 @@ def run_workload(name, args):
     build.build()
     import paper_1912_07645_gb300 as alsv
     W = WORKLOADS[name]
+    if W.get("blocks"):
+        return run_blocks_workload(name, W, args)
     desc = alsv.make_desc(**W["desc"])
     S = alsv.Solver(desc)
     peaks, peak_kind = measured_peaks()

@@ -16,11 +16,13 @@ so every cell sees exactly the inputs it has on the whole grid, and the blocks r
 whole-grid run bitwise (the GPU tests check this against an undivided context).
 
 Two transports carry the exchange and the maximum:
-  ``LocalExchange``  every block in this process on one device and one stream: a block writes
-                     straight into its neighbours' halo buffers (no copies), the maximum is taken
-                     over the blocks' device arrays. Useful on its own: a block holds fewer than
-                     2^31 elements per sample, so a grid above one context's limit still runs on
-                     one GPU.
+  ``LocalExchange``  every block in this process on one device, each on its own CUDA stream: a
+                     block writes straight into its neighbours' halo buffers (no copies), CUDA
+                     events order each pack after the neighbour's previous stage and each stage
+                     after its neighbours' packs, so the blocks' launches overlap on the GPU; the
+                     maximum is taken over the blocks' device arrays. Useful on its own: a block
+                     holds fewer than 2^31 elements per sample, so a grid above one context's
+                     limit still runs on one GPU.
   ``DistExchange``   one block per rank of a torch.distributed group (NCCL on GPUs, gloo on CPUs):
                      packs go to send buffers, batch_isend_irecv delivers them into the
                      neighbours' halo buffers, all_reduce(MAX) takes the maximum.
@@ -115,26 +117,75 @@ def _on(block):
 
 
 class LocalExchange:
-    """Every block in this process, sharing one stream."""
+    """Every block in this process. Blocks with CUDA streams run concurrently, ordered by events: a
+    block packs into a neighbour's halo only after the neighbour's previous stage (the last reader
+    of that halo) has ended, and starts a stage only after its neighbours' packs for it have ended;
+    the maximum runs on a stream of its own after every block's speed_max, and every block's
+    time control waits for it. Host blocks (no stream) run in call order."""
 
     def __init__(self, blocks, coords, parts, periodic):
         self.blocks = blocks
         index = {c: i for i, c in enumerate(coords)}
         self.nbr = [[index.get(neighbour(c, f, parts, periodic)) for f in range(6)] for c in coords]
+        self.peers = [sorted({j for j in row if j is not None}) for row in self.nbr]
+        self.events = all(getattr(b, "stream", None) is not None for b in blocks)
+        if self.events:
+            import torch
+            dev = blocks[0].device
+            self.main = torch.cuda.Stream(device=dev)
+            self.ev_stage = [torch.cuda.Event() for _ in blocks]
+            self.ev_pack = [torch.cuda.Event() for _ in blocks]
+            self.ev_speed = [torch.cuda.Event() for _ in blocks]
+            self.ev_max = torch.cuda.Event()
+            with torch.cuda.stream(self.main):
+                self.gmax = torch.zeros(blocks[0].samples, dtype=torch.float64, device=dev)
 
     def exchange(self, stage: int):
         for i, b in enumerate(self.blocks):
             # my low face's layers are the low neighbour's high-face halo, and so on
             sends = [self.blocks[j].halos[f ^ 1] if j is not None else None for f, j in enumerate(self.nbr[i])]
             if any(s is not None for s in sends):
+                if self.events:
+                    for j in self.peers[i]:
+                        self.ev_stage[j].wait(b.stream)
                 b.halo_pack(stage, sends)
+            if self.events:
+                self.ev_pack[i].record(b.stream)
+        if self.events:
+            for i, b in enumerate(self.blocks):
+                for j in self.peers[i]:
+                    self.ev_pack[j].wait(b.stream)
+
+    def after_stage(self, i: int):
+        if self.events:
+            self.ev_stage[i].record(self.blocks[i].stream)
+
+    def join(self):
+        """Make the exchange's own stream wait for every block's work so far; returns it (None for
+        host blocks)."""
+        if not self.events:
+            return None
+        for i, b in enumerate(self.blocks):
+            self.ev_speed[i].record(b.stream)
+            self.ev_speed[i].wait(self.main)
+        return self.main
 
     def max(self, smax):
         import torch
-        with _on(self.blocks[0]):
-            if len(smax) == 1:
-                return smax[0]
-            return torch.stack(smax).amax(0)
+        if len(smax) == 1:
+            return smax[0]
+        if not self.events:
+            with _on(self.blocks[0]):
+                return torch.stack(smax).amax(0)
+        self.join()
+        with torch.cuda.stream(self.main):
+            self.gmax.copy_(smax[0])
+            for m in smax[1:]:
+                torch.maximum(self.gmax, m, out=self.gmax)
+        self.ev_max.record(self.main)
+        for b in self.blocks:
+            self.ev_max.wait(b.stream)
+        return self.gmax
 
 
 class DistExchange:
@@ -174,6 +225,12 @@ class DistExchange:
                 for w in dist.batch_isend_irecv(ops):
                     w.wait()
 
+    def after_stage(self, i: int):
+        pass
+
+    def join(self):
+        return getattr(self.block, "stream", None)
+
     def max(self, smax):
         import torch.distributed as dist
         with _on(self.block):
@@ -205,10 +262,9 @@ class Decomposition:
         coords = block_coords(parts)
         if make_block is None:
             from .solver import Solver
-            stream = torch.cuda.Stream(device=device) if transport == "local" else None
 
             def make_block(**kw):
-                return Solver(stream=stream, device=device, **kw)
+                return Solver(device=device, **kw)     # each block on a stream of its own
         if transport == "local":
             self.coords = coords
             self.blocks = [make_block(**block_config(cfg, parts, c)) for c in coords]
@@ -229,6 +285,7 @@ class Decomposition:
         if tile_variant is not None:
             for b in self.blocks:
                 b.set_tile_variant(tile_variant)
+        self._prof = None
         b0 = self.blocks[0]
         self.stages = b0.stages
         self.smax = []
@@ -249,12 +306,35 @@ class Decomposition:
             b.set_initial_data(kind, theta)
         self._prepare()
 
+    def set_profiling(self, on: bool):
+        """Record CUDA events around every stage launch of later steps (stage_ms reads their sum)."""
+        self._prof = [] if on else None
+
+    def stage_ms(self):
+        """Device time of the stage launches recorded since set_profiling(True), and their count."""
+        if not self._prof:
+            return 0.0, 0
+        self._prof[-1][1].synchronize()
+        return sum(e0.elapsed_time(e1) for e0, e1 in self._prof), len(self._prof)
+
+    def _stage(self, b, s):
+        if self._prof is None:
+            b.stage(s)
+            return
+        torch = self.torch
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(b.stream)
+        b.stage(s)
+        e1.record(b.stream)
+        self._prof.append((e0, e1))
+
     def step(self, n: int = 1):
         for _ in range(n):
             for s in range(self.stages):
                 self.xch.exchange(s)
-                for b in self.blocks:
-                    b.stage(s)
+                for i, b in enumerate(self.blocks):
+                    self._stage(b, s)
+                    self.xch.after_stage(i)
             for b, m in zip(self.blocks, self.smax):
                 b.speed_max(m)
             g = self.xch.max(self.smax)
@@ -300,7 +380,8 @@ class Decomposition:
             return self.blocks[0].state()
         px, py, pz = self.parts
         at = {c: b for c, b in zip(self.coords, self.blocks)}
-        with _on(self.blocks[0]):
+        main = self.xch.join()
+        with (torch.cuda.stream(main) if main is not None else contextlib.nullcontext()):
             planes = []
             for bz in range(pz):
                 rows = []
@@ -311,10 +392,13 @@ class Decomposition:
 
     def totals(self):
         """FP64 conservation totals [B][nv] summed over the blocks (block order)."""
-        tot = None
-        for b in self.blocks:
-            t = b.totals()
-            tot = t if tot is None else tot + t
+        torch = self.torch
+        parts = [b.totals() for b in self.blocks]
+        main = self.xch.join()
+        with (torch.cuda.stream(main) if main is not None else contextlib.nullcontext()):
+            tot = parts[0].clone()
+            for t in parts[1:]:
+                tot += t
         return tot
 
     def close(self):

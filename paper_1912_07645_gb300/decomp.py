@@ -372,15 +372,21 @@ class Decomposition:
         for b in self.blocks:
             b.sync()
 
+    def _hand_over(self, stream):
+        """Order the caller's current stream after ``stream`` (results are then usable there)."""
+        if stream is not None:
+            self.torch.cuda.current_stream(stream.device).wait_stream(stream)
+
     def state(self):
         """The whole grid's state [B, nv, nz, ny, nx] assembled from the blocks (local transport;
-        with "dist", this rank's block)."""
+        with "dist", this rank's block), ready on the caller's current stream."""
         torch = self.torch
+        main = self.xch.join()
         if len(self.blocks) == 1:
+            self._hand_over(main)
             return self.blocks[0].state()
         px, py, pz = self.parts
         at = {c: b for c, b in zip(self.coords, self.blocks)}
-        main = self.xch.join()
         with (torch.cuda.stream(main) if main is not None else contextlib.nullcontext()):
             planes = []
             for bz in range(pz):
@@ -388,10 +394,13 @@ class Decomposition:
                 for by in range(py):
                     rows.append(torch.cat([at[(bx, by, bz)].state() for bx in range(px)], dim=4))
                 planes.append(torch.cat(rows, dim=3))
-            return torch.cat(planes, dim=2)
+            out = torch.cat(planes, dim=2)
+        self._hand_over(main)
+        return out
 
     def totals(self):
-        """FP64 conservation totals [B][nv] summed over the blocks (block order)."""
+        """FP64 conservation totals [B][nv] summed over the blocks (block order), ready on the
+        caller's current stream."""
         torch = self.torch
         parts = [b.totals() for b in self.blocks]
         main = self.xch.join()
@@ -399,6 +408,7 @@ class Decomposition:
             tot = parts[0].clone()
             for t in parts[1:]:
                 tot += t
+        self._hand_over(main)
         return tot
 
     def close(self):

@@ -289,6 +289,12 @@ WORKLOADS = {
                                            precision="fp32", seed=0),
                                  init="kh", steps=20, parts=(1, 1, 4), words=8, nv=5, esize=4, blocks=True,
                                  overhead_n=(512, 512, 512), overhead_steps=40),
+    # the same at 256^3 (state 0.34 GB), for profiler captures
+    "kh3d256_blocks_fp32": dict(desc=dict(ndim=3, n=(256, 256, 256), batch=1, eq="euler", recon="weno3",
+                                          flux="hllc", rvars="prim", rk="ssprk3", bc="periodic", cfl=0.3,
+                                          precision="fp32", seed=0),
+                                init="kh", steps=10, parts=(1, 1, 4), words=8, nv=5, esize=4, blocks=True,
+                                overhead_n=(256, 256, 256), overhead_steps=20),
     "adjoint512_fp32": dict(desc=dict(ndim=2, n=(512, 512), batch=64, eq="euler", recon="mc", flux="rusanov",
                                       rvars="prim", rk="ssprk2", bc="periodic", cfl=0.4, precision="fp32", seed=SEED),
                             adjoint=True, T=1.0),
@@ -307,7 +313,7 @@ WORKLOADS = {
 # (152 SMs x 128 lanes x 2 x 2.07 GHz), FP64 the GB300's nominal 1.25 TFLOP/s.
 WORKLOAD_FLOPS = {"sod1024_fp64": 287, "kh2d1024_fp32": 1980, "kh2d1024_fp64": 1980, "mlmc_fp32": 1980,
                   "mlmc_coupled_fp32": 1980, "kh3d512_fp32": 3591, "kh3d256_fp32": 3591,
-                  "kh3d1024_blocks_fp32": 3591}
+                  "kh3d1024_blocks_fp32": 3591, "kh3d256_blocks_fp32": 3591}
 FP64_PEAK_TFLOPS = 1.25
 
 

@@ -351,27 +351,33 @@ cudaError_t launch_init(int fp64, int ndim, const InitArgs& a, cudaStream_t s) {
 // on the low face and n_k - G + l on the high face. A plain copy.
 // ---------------------------------------------------------------------------------------------
 template <class R>
-__global__ void k_halo_pack(const GridArgs g, int G, int face, const R* __restrict__ U, R* __restrict__ dst) {
+__global__ void k_halo_pack(const GridArgs g, int G, int face, int rows, const R* __restrict__ U, R* __restrict__ dst) {
+    // blockIdx.x (with x-threads) covers the cross-section, blockIdx.y strides over the rows
+    // (sample, var, layer); 32-bit index arithmetic within a sample (< 2^31 elements)
     const LevelInfo& L = g.lev[0];
     const int k = face >> 1;
     const int n[3] = {L.n[0], L.n[1], L.n[2]};
-    const long long csize = (long long)n[0] * n[1] * n[2] / n[k];
-    const long long total = (long long)L.samples * g.nv * G * csize;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
-        long long q = i % csize;
-        const long long r = i / csize;
-        const int layer = (int)(r % G);
-        const long long bv = r / G;  // sample * nv + var
-        int c[3];
+    const int csize = n[0] * n[1] * n[2] / n[k];
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= csize) return;
+    // the cell of this cross-section index (x fastest, the face direction left out)
+    int c[3];
+    int rem = q;
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            if (j == k) continue;
-            c[j] = (int)(q % n[j]);
-            q /= n[j];
-        }
-        c[k] = (face & 1) ? n[k] - G + layer : layer;
-        dst[i] = U[((bv * n[2] + c[2]) * n[1] + c[1]) * n[0] + c[0]];
+    for (int j = 0; j < 3; ++j) {
+        if (j == k) continue;
+        c[j] = rem % n[j];
+        rem /= n[j];
+    }
+    const int plane = n[0] * n[1] * n[2];
+    const int stride_k = k == 0 ? 1 : (k == 1 ? n[0] : n[0] * n[1]);
+    c[k] = 0;
+    const int base = (c[2] * n[1] + c[1]) * n[0] + c[0];
+    const int first = (face & 1) ? n[k] - G : 0;
+    for (int r = blockIdx.y; r < rows; r += gridDim.y) {
+        const int layer = r % G;
+        const long long bv = r / G;  // sample * nv + var
+        dst[(long long)r * csize + q] = U[bv * plane + base + (first + layer) * stride_k];
     }
 }
 
@@ -380,13 +386,16 @@ cudaError_t launch_halo_pack(int fp64, const GridArgs& g, int G, const void* U, 
     for (int f = 0; f < 6; ++f) {
         if (!dst[f]) continue;
         const long long csize = (long long)L.n[0] * L.n[1] * L.n[2] / L.n[f >> 1];
-        const long long total = (long long)L.samples * g.nv * G * csize;
-        if (total <= 0) continue;
-        const unsigned blocks = (unsigned)std::min<long long>((total + 255) / 256, 152LL * 16);
+        const int rows = L.samples * g.nv * G;   // < 2^16 samples x 5 vars x 2 layers
+        if (csize <= 0 || rows <= 0) continue;
+        const unsigned bx = (unsigned)((csize + 255) / 256);
+        // about 16 resident blocks per SM in all, rows strided by gridDim.y
+        const unsigned by = (unsigned)std::max<long long>(1, std::min<long long>(rows, (152LL * 16 + bx - 1) / bx));
+        const dim3 grid(bx, std::min(by, 65535u));
         if (fp64)
-            k_halo_pack<double><<<blocks, 256, 0, s>>>(g, G, f, static_cast<const double*>(U), static_cast<double*>(dst[f]));
+            k_halo_pack<double><<<grid, 256, 0, s>>>(g, G, f, rows, static_cast<const double*>(U), static_cast<double*>(dst[f]));
         else
-            k_halo_pack<float><<<blocks, 256, 0, s>>>(g, G, f, static_cast<const float*>(U), static_cast<float*>(dst[f]));
+            k_halo_pack<float><<<grid, 256, 0, s>>>(g, G, f, rows, static_cast<const float*>(U), static_cast<float*>(dst[f]));
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

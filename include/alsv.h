@@ -393,13 +393,14 @@ alsv_status alsv_structure_function_read(alsv_ctx* ctx, const void* acc_dev, int
  *   alsv_halo_info     layers g and the element count of each face's buffer (host outputs;
  *                      elems[2k + side], 0 for faces that are not HALO)
  *   alsv_bind_halo     device pointers of the six face buffers (NULL for faces that are not
- *                      HALO) and their byte size each (>= elems * element size). The context
- *                      borrows them; they are read by every later stage launch.
+ *                      HALO) and their byte sizes bytes[6] (each >= that face's elems * element
+ *                      size). The context borrows them; they are read by every later stage launch.
  *   alsv_halo_pack     write the block's own g boundary layers of the state that stage s reads
  *                      (s = 0: U; RK2 s = 1: the stage buffer; RK3 s = 1, 2: the two stage
- *                      buffers) into send[2k + side] (same layout; low face = indices 0 .. g-1,
- *                      high face = n_k - g .. n_k - 1), for every face whose pointer is not
- *                      NULL. A neighbour's halo buffer may be passed directly. Asynchronous.
+ *                      buffers) into send[2k + side] of bytes[2k + side] bytes (same layout; low
+ *                      face = indices 0 .. g-1, high face = n_k - g .. n_k - 1), for every face
+ *                      whose pointer is not NULL. A neighbour's halo buffer may be passed
+ *                      directly. Asynchronous.
  *   alsv_stage         enqueue RK stage s of the current step for every sample that is not done;
  *                      stages must come in order 0, 1, ... (INVALID_ARG otherwise). The last stage
  *                      also writes the per-tile CFL partials. Asynchronous.
@@ -418,8 +419,8 @@ alsv_status alsv_structure_function_read(alsv_ctx* ctx, const void* acc_dev, int
  * context with HALO faces (they would read halo buffers nobody refills).
  */
 alsv_status alsv_halo_info(const alsv_ctx* ctx, int32_t* layers, int64_t* elems);
-alsv_status alsv_bind_halo(alsv_ctx* ctx, const void* const* halo_dev, size_t bytes_each);
-alsv_status alsv_halo_pack(alsv_ctx* ctx, int stage, void* const* send_dev, size_t bytes_each);
+alsv_status alsv_bind_halo(alsv_ctx* ctx, const void* const* halo_dev, const size_t* bytes);
+alsv_status alsv_halo_pack(alsv_ctx* ctx, int stage, void* const* send_dev, const size_t* bytes);
 alsv_status alsv_stage(alsv_ctx* ctx, int stage);
 alsv_status alsv_speed_max(alsv_ctx* ctx, double* smax_dev);
 alsv_status alsv_finish_step(alsv_ctx* ctx, const double* smax_dev, int advance);

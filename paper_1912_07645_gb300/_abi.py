@@ -102,8 +102,8 @@ SIGNATURES = {
     "alsv_get_profile": (C.c_int, [_ctx, _dp, _i64p, _dp, _i64p]),
     "alsv_get_launch_count": (C.c_int, [_ctx, _i64p]),
     "alsv_halo_info": (C.c_int, [_ctx, C.POINTER(C.c_int32), _i64p]),
-    "alsv_bind_halo": (C.c_int, [_ctx, C.POINTER(_vp), _sz]),
-    "alsv_halo_pack": (C.c_int, [_ctx, C.c_int, C.POINTER(_vp), _sz]),
+    "alsv_bind_halo": (C.c_int, [_ctx, C.POINTER(_vp), C.POINTER(_sz)]),
+    "alsv_halo_pack": (C.c_int, [_ctx, C.c_int, C.POINTER(_vp), C.POINTER(_sz)]),
     "alsv_stage": (C.c_int, [_ctx, C.c_int]),
     "alsv_speed_max": (C.c_int, [_ctx, _vp]),
     "alsv_finish_step": (C.c_int, [_ctx, _vp, C.c_int]),
@@ -356,21 +356,26 @@ def _faces(bufs):
     return arr
 
 
-def _bytes_each(bufs) -> int:
-    sizes = [_nbytes(b) for b in bufs if b is not None and not isinstance(b, int)]
-    return min(sizes) if sizes else 0
+def _sizes(bufs, nbytes=None):
+    arr = (C.c_size_t * 6)()
+    for f in range(6):
+        b = bufs[f] if f < len(bufs) else None
+        if nbytes is not None:
+            arr[f] = int(nbytes[f])
+        elif b is not None and not isinstance(b, int):
+            arr[f] = _nbytes(b)
+    return arr
 
 
-def alsv_bind_halo(ctx, halos, nbytes: int | None = None):
-    """halos: six device buffers (None for faces that are not HALO), face 2k + side."""
-    _check(load().alsv_bind_halo(ctx, _faces(halos), nbytes if nbytes is not None else _bytes_each(halos)),
-           "alsv_bind_halo", ctx)
+def alsv_bind_halo(ctx, halos, nbytes=None):
+    """halos: six device buffers (None for faces that are not HALO), face 2k + side; nbytes: their
+    byte sizes (default: the tensors' sizes)."""
+    _check(load().alsv_bind_halo(ctx, _faces(halos), _sizes(halos, nbytes)), "alsv_bind_halo", ctx)
 
 
-def alsv_halo_pack(ctx, stage: int, sends, nbytes: int | None = None):
+def alsv_halo_pack(ctx, stage: int, sends, nbytes=None):
     """sends: six device buffers (None to skip a face) that receive the block's boundary layers."""
-    _check(load().alsv_halo_pack(ctx, stage, _faces(sends), nbytes if nbytes is not None else _bytes_each(sends)),
-           "alsv_halo_pack", ctx)
+    _check(load().alsv_halo_pack(ctx, stage, _faces(sends), _sizes(sends, nbytes)), "alsv_halo_pack", ctx)
 
 
 def alsv_stage(ctx, stage: int):

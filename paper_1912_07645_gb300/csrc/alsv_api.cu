@@ -1008,28 +1008,28 @@ alsv_status alsv_halo_info(const alsv_ctx* c, int32_t* layers, int64_t* elems) {
     return ALSV_OK;
 }
 
-alsv_status alsv_bind_halo(alsv_ctx* c, const void* const* halo_dev, size_t bytes_each) {
+alsv_status alsv_bind_halo(alsv_ctx* c, const void* const* halo_dev, const size_t* bytes) {
     if (!c) return fail(nullptr, ALSV_ERR_INVALID_ARG, "null context");
-    if (!halo_dev) return fail(c, ALSV_ERR_INVALID_ARG, "null halo pointer array");
+    if (!halo_dev || !bytes) return fail(c, ALSV_ERR_INVALID_ARG, "null halo pointer or size array");
     const size_t esz = c->fp64 ? 8 : 4;
     for (int f = 0; f < 6; ++f) {
         const long long n = halo_elems(c, f);
         if (n == 0) continue;
         if (!halo_dev[f]) return fail(c, ALSV_ERR_INVALID_ARG, "a halo face needs a buffer");
         if (((uintptr_t)halo_dev[f] & 15) != 0) return fail(c, ALSV_ERR_INVALID_ARG, "halo buffers must be 16-byte aligned");
-        if (bytes_each < (size_t)n * esz) return fail(c, ALSV_ERR_BUFFER_TOO_SMALL, "halo buffer smaller than alsv_halo_info's size");
+        if (bytes[f] < (size_t)n * esz) return fail(c, ALSV_ERR_BUFFER_TOO_SMALL, "halo buffer smaller than alsv_halo_info's size");
     }
     for (int f = 0; f < 6; ++f) c->halo[f] = halo_elems(c, f) ? halo_dev[f] : nullptr;
     c->halo_bound = true;
     return ALSV_OK;
 }
 
-alsv_status alsv_halo_pack(alsv_ctx* c, int stage, void* const* send_dev, size_t bytes_each) {
+alsv_status alsv_halo_pack(alsv_ctx* c, int stage, void* const* send_dev, const size_t* bytes) {
     alsv_status st = require_ready(c);
     if (st != ALSV_OK) return st;
     if (c->g.nlev != 1) return fail(c, ALSV_ERR_INVALID_ARG, "halo layers need a single grid");
     if (stage < 0 || stage >= c->nstages) return fail(c, ALSV_ERR_INVALID_ARG, "stage out of range");
-    if (!send_dev) return fail(c, ALSV_ERR_INVALID_ARG, "null send pointer array");
+    if (!send_dev || !bytes) return fail(c, ALSV_ERR_INVALID_ARG, "null send pointer or size array");
     const size_t esz = c->fp64 ? 8 : 4;
     void* dst[6];
     for (int f = 0; f < 6; ++f) {
@@ -1040,7 +1040,7 @@ alsv_status alsv_halo_pack(alsv_ctx* c, int stage, void* const* send_dev, size_t
         if (c->g.lev[0].n[k] < c->G) return fail(c, ALSV_ERR_INVALID_ARG, "fewer cells than ghost layers across a face");
         const LevelInfo& L = c->g.lev[0];
         const long long n = (long long)L.samples * c->nv * c->G * ((long long)L.n[0] * L.n[1] * L.n[2] / L.n[k]);
-        if (bytes_each < (size_t)n * esz) return fail(c, ALSV_ERR_BUFFER_TOO_SMALL, "send buffer smaller than a face's layers");
+        if (bytes[f] < (size_t)n * esz) return fail(c, ALSV_ERR_BUFFER_TOO_SMALL, "send buffer smaller than a face's layers");
     }
     const void* src = stage_io(c, stage).Us;
     cudaError_t e = launch_halo_pack(c->fp64, c->g, c->G, src, dst, c->stream);

@@ -274,19 +274,17 @@ class Solver:
         return A.alsv_halo_info(self.ctx)
 
     def bind_halo(self):
-        """Allocate and bind this block's halo buffers (one per halo face, all of the largest face's
-        size); returns them."""
+        """Allocate and bind this block's halo buffers (one per halo face); returns them."""
         _, elems = self.halo_info()
-        m = max(elems)
         with self.torch.cuda.stream(self.stream):
-            self.halos = [self.torch.zeros(m, dtype=self.dtype, device=self.device) if n else None for n in elems]
-        if m:
+            self.halos = [self.torch.zeros(n, dtype=self.dtype, device=self.device) if n else None for n in elems]
+        if any(elems):
             A.alsv_bind_halo(self.ctx, self.halos)
         return self.halos
 
     def halo_pack(self, stage, sends):
-        """Write the block's boundary layers of stage ``stage``'s input into ``sends`` (six buffers of
-        equal size or None)."""
+        """Write the block's boundary layers of stage ``stage``'s input into ``sends`` (six device
+        buffers or None, e.g. the neighbours' halo buffers)."""
         A.alsv_halo_pack(self.ctx, stage, sends)
 
     def stage(self, s):

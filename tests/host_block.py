@@ -85,8 +85,7 @@ class OracleBlock:
 
     def bind_halo(self):
         _, elems = self.halo_info()
-        m = max(elems)
-        self.halos = [torch.zeros(m, dtype=torch.float64) if e else None for e in elems]
+        self.halos = [torch.zeros(e, dtype=torch.float64) if e else None for e in elems]
         return self.halos
 
     def _state(self, s):

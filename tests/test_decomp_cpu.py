@@ -93,6 +93,8 @@ CASES = {
                      bc="periodic", cfl=0.4), "kh", (1, 2, 1), 0.03),
     "kh2d_2x2": (dict(ndim=2, n=(32, 32), eq="euler", recon="mc", rvars="cons", flux="rusanov", rk="ssprk3",
                       bc=[("periodic", "periodic"), ("reflective", "outflow")], cfl=0.4), "kh", (2, 2, 1), 0.03),
+    "kh2d_3x2_ragged": (dict(ndim=2, n=(32, 32), eq="euler", recon="weno3", rvars="prim", flux="hllc",
+                             rk="ssprk2", bc="periodic", cfl=0.4), "kh", (3, 2, 1), 0.03),
     "sod1d_x4": (dict(ndim=1, n=(64,), eq="euler", recon="weno3", rvars="prim", flux="hllc", rk="ssprk3",
                       bc="outflow", cfl=0.45), "sod", (4, 1, 1), 0.05),
     "burgers1d_x3": (dict(ndim=1, n=(64,), eq="burgers", recon="pc", flux="hll", rk="ssprk2", bc="periodic",
@@ -154,7 +156,7 @@ def _dist_worker(rank, world, port, case, out_path):
 
 
 @pytest.mark.timeout(300)
-@pytest.mark.parametrize("case,world", [("kh2d_x2", 2), ("kh2d_2x2", 4)])
+@pytest.mark.parametrize("case,world", [("kh2d_x2", 2), ("kh2d_2x2", 4), ("kh2d_3x2_ragged", 6)])
 def test_gloo_ranks_reproduce_the_whole_grid(tmp_path, case, world):
     import torch.multiprocessing as mp
     with socket.socket() as s:

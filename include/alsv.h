@@ -439,7 +439,9 @@ alsv_status alsv_destroy(alsv_ctx* ctx);
  *                           (32x16, 32x8 tiles; primitive, HLLC/Rusanov); 6 the two halves of each
  *                           sample per thread (as 4, with y periodic and ny divisible by 32).
  *                           FP32 3D: 0, 1 tiles of 16x8x8, 8x8x8; 2, 3 z-marching 32x8 column
- *                           chunks of 64 / 128 planes (Euler). 1D: tiles of 256, 64, 32 cells.
+ *                           chunks of 64 / 128 planes (Euler); 4 as 2 with the x and y interfaces
+ *                           of a plane packed in FP32x2 (primitive, HLLC/Rusanov). FP64 2D / 3D:
+ *                           0, 1 tiles. 1D: tiles of 256, 64, 32 cells.
  *   alsv_set_tile_variant   select one (recomputes the wave-speed partials; asynchronous;
  *                           ALSV_ERR_INVALID_ARG if the variant does not support the scheme)
  *   alsv_get_tile           current tile shape, variant and (sample, tile) work items per launch

@@ -383,7 +383,7 @@ alsv_status alsv_structure_function_read(alsv_ctx* ctx, const void* acc_dev, int
  * With every block fed its neighbours' layers of the same stage state and the same maximum, each
  * cell sees exactly the inputs it sees on the whole grid, so the blocks together reproduce the
  * whole-grid run bitwise under the same stage schedule. Every schedule reads halo faces except the
- * FP32 2D column march and two-sample schedules (variants 3-6), which reject them.
+ * FP32 2D column march and two-sample schedules (variants 3-7), which reject them.
  *
  * Halo buffer of face (k, side): [samples][vars][layers][cross], layers = alsv_halo_info's g (1
  * for PC, 2 otherwise), cross = the block's cells across k in (z, y, x) order without k. Layer l
@@ -436,8 +436,9 @@ alsv_status alsv_destroy(alsv_ctx* ctx);
  *   alsv_num_tile_variants  number of stage-kernel schedules for this (precision, ndim). FP32 2D:
  *                           0-2 tiles of 32x16, 32x8, 32x32; 3 column march (periodic, primitive
  *                           WENO3/MC, HLLC/Rusanov); 4, 5 two samples per thread in packed FP32x2
- *                           (32x16, 32x8 tiles; primitive, HLLC/Rusanov); 6 the two halves of each
- *                           sample per thread (as 4, with y periodic and ny divisible by 32).
+ *                           (32x16, 32x8 tiles; primitive, HLLC/Rusanov); 6, 7 the two halves of
+ *                           each sample per thread (as 4, 5, with y periodic and ny divisible by
+ *                           32, 16).
  *                           FP32 3D: 0, 1 tiles of 16x8x8, 8x8x8; 2, 3 z-marching 32x8 column
  *                           chunks of 64 / 128 planes (Euler); 4 as 2 with the x and y interfaces
  *                           of a plane packed in FP32x2 (primitive, HLLC/Rusanov). FP64 2D / 3D:

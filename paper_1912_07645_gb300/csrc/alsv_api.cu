@@ -47,7 +47,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 bool variant_ok(const alsv_ctx* c, int v) {
     if (!stage_variant_supported(c->fp64, c->ndim, c->eq, c->d.recon, c->g.rvars, c->d.flux, c->g.bc, v)) return false;
     // halo faces are read by the tile kernels and the 3D z-march (every variant but the FP32 2D
-    // column march and two-sample schedules, 3-6)
+    // column march and two-sample schedules, 3-7)
     if (ctx_has_halo(c) && !c->fp64 && c->ndim == 2 && v >= 3) return false;
     if (stage_variant_halves(c->fp64, c->ndim, v)) {
         // the halves must align with whole tiles: ny divisible by twice the tile height
@@ -319,6 +319,7 @@ TileShape stage_tile(int fp64, int ndim, int variant) {
         if (variant == 3 && !fp64) return TileShape{31, 1 << 20, 1, 128};  // column strips, whole height
         if (variant == 5 && !fp64) return TileShape{32, 8, 1, 256};        // two-sample tiles
         if (variant == 6 && !fp64) return TileShape{32, 16, 1, 256};       // two halves of a sample
+        if (variant == 7 && !fp64) return TileShape{32, 8, 1, 256};
         return TileShape{32, 16, 1, 256};                                   // variants 0 and 4
     }
     if (fp64) return variant == 1 ? TileShape{8, 8, 4, 256} : TileShape{8, 8, 8, 256};
@@ -327,10 +328,10 @@ TileShape stage_tile(int fp64, int ndim, int variant) {
     if (variant == 4) return TileShape{32, 8, 64, 256};     // z-march, packed x/y interfaces
     return variant == 1 ? TileShape{8, 8, 8, 256} : TileShape{16, 8, 8, 256};
 }
-bool stage_variant_halves(int fp64, int ndim, int variant) { return ndim == 2 && !fp64 && variant == 6; }
+bool stage_variant_halves(int fp64, int ndim, int variant) { return ndim == 2 && !fp64 && (variant == 6 || variant == 7); }
 int stage_num_variants(int fp64, int ndim) {
     if (ndim == 1) return 3;
-    if (ndim == 2 && !fp64) return 7;
+    if (ndim == 2 && !fp64) return 8;
     if (ndim == 3 && !fp64) return 5;
     return 2;
 }
@@ -338,7 +339,7 @@ bool stage_variant_supported(int fp64, int ndim, int eq, int recon, int rvars, i
     if (variant < 0 || variant >= stage_num_variants(fp64, ndim)) return false;
     if (ndim == 2 && !fp64 && (variant == 4 || variant == 5))
         return eq == EQ_EULER && rvars == RV_PRIM && (flux == FLX_HLLC || flux == FLX_RUSANOV);
-    if (ndim == 2 && !fp64 && variant == 6)
+    if (ndim == 2 && !fp64 && (variant == 6 || variant == 7))
         return eq == EQ_EULER && rvars == RV_PRIM && (flux == FLX_HLLC || flux == FLX_RUSANOV) &&
                bc[1][0] == BC_PERIODIC && bc[1][1] == BC_PERIODIC;
     if (ndim == 3 && !fp64 && variant == 4)

@@ -55,6 +55,7 @@ cudaError_t launch_stage_f32_2d(int variant, int eq, int recon, int flux, const 
         case 4: return launch_pair<32, 16, 256>(recon, flux, eq, a, s);
         case 5: return launch_pair<32, 8, 256>(recon, flux, eq, a, s);
         case 6: return launch_pair<32, 16, 256, 1>(recon, flux, eq, a, s);
+        case 7: return launch_pair<32, 8, 256, 1>(recon, flux, eq, a, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -72,6 +73,7 @@ cudaError_t launch_speed_f32_2d(int variant, int eq, const GridArgs& g, const vo
         case 4: return launch_speed_tile<float, 2, 32, 16, 1, 256>(eq, g, U, part, s);
         case 5: return launch_speed_tile<float, 2, 32, 8, 1, 256>(eq, g, U, part, s);
         case 6: return launch_speed_tile<float, 2, 32, 16, 1, 256>(eq, g, U, part, s);
+        case 7: return launch_speed_tile<float, 2, 32, 8, 1, 256>(eq, g, U, part, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -682,7 +682,7 @@ def test_halves_variant_fp32_vs_oracle_and_bitwise_with_sample_pairs(recon, flux
                cfl=0.4, precision="fp32")
     U0 = euler_state(3, 2, (70, 64), seed=73)
     out = {}
-    for v in (4, 6):
+    for v in (4, 6, 7):
         S = gpu_solver(**cfg)
         alsv.alsv_set_tile_variant(S.ctx, v)
         S.set_state(torch.from_numpy(U0))
@@ -690,7 +690,7 @@ def test_halves_variant_fp32_vs_oracle_and_bitwise_with_sample_pairs(recon, flux
         S.sync()
         out[v] = (host(S.U).reshape(S.level_shape(0)), S.time())
         S.close()
-    assert np.array_equal(out[4][0], out[6][0])
+    assert np.array_equal(out[4][0], out[6][0]) and np.array_equal(out[4][0], out[7][0])
     np.testing.assert_array_equal(out[4][1][0], out[6][1][0])
     o, *_ = run_oracle(cfg, U0=U0, steps=10)
     for b in range(3):
@@ -700,12 +700,17 @@ def test_halves_variant_fp32_vs_oracle_and_bitwise_with_sample_pairs(recon, flux
 def test_halves_variant_needs_aligned_periodic_y():
     torch_()
     import paper_1912_07645_gb300 as alsv
-    for n, bc in (((64, 48), "periodic"), ((64, 64), [("periodic", "periodic"), ("outflow", "outflow")])):
+    for n, bc in (((64, 40), "periodic"), ((64, 64), [("periodic", "periodic"), ("outflow", "outflow")])):
         S = gpu_solver(ndim=2, n=n, batch=1, eq="euler", recon="weno3", flux="hllc", rvars="prim", precision="fp32",
                        bc=bc)
-        with pytest.raises(alsv.AlsvError, match="does not support"):
-            alsv.alsv_set_tile_variant(S.ctx, 6)
+        for v in (6, 7):
+            with pytest.raises(alsv.AlsvError, match="does not support"):
+                alsv.alsv_set_tile_variant(S.ctx, v)
         S.close()
+    S = gpu_solver(ndim=2, n=(64, 48), batch=1, eq="euler", recon="weno3", flux="hllc", rvars="prim",
+                   precision="fp32", bc="periodic")
+    alsv.alsv_set_tile_variant(S.ctx, 7)      # 48 = 3 x 16: 32x8 halves align
+    S.close()
 
 
 def test_pair_variant_samples_finishing_at_different_steps():

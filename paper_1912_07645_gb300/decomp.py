@@ -412,5 +412,10 @@ class Decomposition:
         return tot
 
     def close(self):
+        # the blocks' buffers are written from their neighbours' streams too: let every stream
+        # drain before the contexts and tensors go
+        main = self.xch.join()
+        if main is not None:
+            main.synchronize()
         for b in self.blocks:
             b.close()

@@ -124,6 +124,9 @@ def lib():
             L.orc_kinetic_energy.argtypes = [dsc, C.c_int, dp, dp]
             L.orc_ke_grad_kh2d.argtypes = [dsc, dp, C.c_double, C.c_int64, dp, dp]
             L.orc_ke_grad_kh2d.restype = C.c_int
+            L.orc_obs_grad_kh2d.argtypes = [dsc, dp, C.c_double, C.c_int64, C.c_int, dp, dp]
+            L.orc_obs_grad_kh2d.restype = C.c_int
+            L.orc_mixing_width.argtypes = [dsc, C.c_int, dp, dp]
             L.orc_ke_dir_kh2d.argtypes = [dsc, dp, dp, C.c_double, C.c_int64, dp, dp]
             L.orc_ke_dir_kh2d.restype = C.c_int
             _lib = L
@@ -312,6 +315,29 @@ def ke_grad_kh2d(d: Desc, theta, dt: float, n_steps: int):
     st = lib().orc_ke_grad_kh2d(C.byref(d), _dp(th), dt, n_steps, C.byref(J), _dp(g))
     if st != 0:
         raise ValueError("ke_grad_kh2d needs a 2D Euler descriptor")
+    return J.value, g
+
+
+def mixing_width(d: Desc, U) -> np.ndarray:
+    """Mixing-layer width sum_i 4 (rho_i - 1)(2 - rho_i) dV per sample (KH densities 1 and 2)."""
+    U = _f64(U)
+    out = np.zeros(U.shape[0])
+    lib().orc_mixing_width(C.byref(d), U.shape[0], _dp(U), _dp(out))
+    return out
+
+
+OBSERVABLES = {"ke": 0, "mixing": 1}
+
+
+def obs_grad_kh2d(d: Desc, theta, dt: float, n_steps: int, observable: str = "ke"):
+    """(J, dJ/dtheta[20]) of one 2D KH sample after n fixed steps for the kinetic energy ("ke") or
+    the mixing-layer width ("mixing"), by forward-mode duals."""
+    th = _f64(theta).reshape(20)
+    J = C.c_double()
+    g = np.zeros(20)
+    st = lib().orc_obs_grad_kh2d(C.byref(d), _dp(th), dt, n_steps, OBSERVABLES[observable], C.byref(J), _dp(g))
+    if st != 0:
+        raise ValueError("obs_grad_kh2d needs a 2D Euler descriptor")
     return J.value, g
 
 

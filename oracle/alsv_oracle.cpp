@@ -841,11 +841,30 @@ void orc_kinetic_energy(const Desc* d, int B, const double* U, double* ke) {
     }
 }
 
-// Exact gradient of the kinetic energy at time n_steps*dt with respect to the 20 2D KH
-// parameters of ONE sample, by forward-mode dual numbers through init + n fixed-dt steps.
-// Returns J in *J and dJ/dtheta in grad[20].
-int orc_ke_grad_kh2d(const Desc* d, const double* theta, double dt, int64_t n_steps, double* J, double* grad) {
-    if (d->eq != EQ_EULER || d->ndim != 2) return 1;
+// Mixing-layer width of the KH shear layer (reading; the paper names no observable): the
+// inner-band fraction c = (rho - 1) / (2 - 1) of the two KH densities (1 outside, 2 inside) gives
+// W = sum_i 4 c_i (1 - c_i) dV, i.e. 4 (rho_i - 1) (2 - rho_i) dV per cell: 0 in either pure state,
+// the cell's area where the two are mixed half and half. Pairwise sum per sample (2D Euler).
+void orc_mixing_width(const Desc* d, int B, const double* U, double* out) {
+    const int nv = nvars(*d);
+    const int64_t C = ncells(*d);
+    double dV = 1.0;
+    for (int k = 0; k < d->ndim; ++k) dV *= dx(*d, k);
+    std::vector<double> e(C);
+    for (int b = 0; b < B; ++b) {
+        const double* Ub = U + (int64_t)b * nv * C;
+        for (int64_t i = 0; i < C; ++i) e[i] = 4.0 * (Ub[i] - 1.0) * (2.0 - Ub[i]);
+        out[b] = pairwise(e.data(), C) * dV;
+    }
+}
+
+// Exact gradient of an observable at time n_steps*dt with respect to the 20 2D KH parameters of
+// ONE sample, by forward-mode dual numbers through init + n fixed-dt steps: observable 0 = the
+// kinetic energy sum |m|^2 / (2 rho) dV, 1 = the mixing-layer width sum 4 (rho - 1)(2 - rho) dV
+// (cells summed in order). Returns J in *J and dJ/dtheta in grad[20].
+int orc_obs_grad_kh2d(const Desc* d, const double* theta, double dt, int64_t n_steps, int observable, double* J,
+                      double* grad) {
+    if (d->eq != EQ_EULER || d->ndim != 2 || observable < 0 || observable > 1) return 1;
     typedef Dual<20> D;
     const int64_t N = (int64_t)nvars(*d) * ncells(*d);
     std::vector<D> th(20), U(N);
@@ -856,13 +875,22 @@ int orc_ke_grad_kh2d(const Desc* d, const double* theta, double dt, int64_t n_st
     const double dV = dx(*d, 0) * dx(*d, 1);
     D acc(0.0);
     for (int64_t i = 0; i < C; ++i) {
-        D m2 = U[C + i] * U[C + i] + U[2 * C + i] * U[2 * C + i];
-        acc = acc + 0.5 * m2 / U[i];
+        if (observable == 0) {
+            D m2 = U[C + i] * U[C + i] + U[2 * C + i] * U[2 * C + i];
+            acc = acc + 0.5 * m2 / U[i];
+        } else {
+            acc = acc + 4.0 * (U[i] - 1.0) * (2.0 - U[i]);
+        }
     }
     acc = acc * dV;
     *J = acc.v;
     for (int j = 0; j < 20; ++j) grad[j] = acc.d[j];
     return 0;
+}
+
+// The kinetic-energy case of orc_obs_grad_kh2d.
+int orc_ke_grad_kh2d(const Desc* d, const double* theta, double dt, int64_t n_steps, double* J, double* grad) {
+    return orc_obs_grad_kh2d(d, theta, dt, n_steps, 0, J, grad);
 }
 
 // Directional derivative dJ/dtheta . vdir via a single-direction dual run (dot-product pin).

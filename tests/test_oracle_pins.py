@@ -502,6 +502,51 @@ def test_dual_gradient_dot_direction():
     assert dJ == pytest.approx(np.dot(g, v), rel=1e-10)
 
 
+def _mix_after(d, th, dt, steps):
+    U = oracle.init(d, "kh", 1, th[None, :])
+    U, _, _ = oracle.evolve(d, U, fixed_dt=dt, n_steps=steps)
+    return float(oracle.mixing_width(d, U)[0])
+
+
+def test_mixing_width_closed_forms():
+    """W = sum 4 (rho - 1)(2 - rho) dV: 0 where the unperturbed interfaces lie on cell faces
+    (ny = 8), the area of the two half-filled rows where they cut cells in half (ny = 10: 2 dy),
+    and the whole domain for a half-and-half state."""
+    zero = np.zeros((1, 20))
+    d8 = oracle.make_desc(ndim=2, n=(12, 8), eq="euler")
+    assert oracle.mixing_width(d8, oracle.init(d8, "kh", 1, zero))[0] == 0.0
+    d10 = oracle.make_desc(ndim=2, n=(12, 10), eq="euler")
+    assert oracle.mixing_width(d10, oracle.init(d10, "kh", 1, zero))[0] == pytest.approx(0.2, rel=1e-14)
+    U = np.zeros((1, 4, 1, 10, 12))
+    U[:, 0] = 1.5
+    U[:, 3] = 2.5 / 0.4
+    assert oracle.mixing_width(d10, U)[0] == pytest.approx(1.0, rel=1e-14)
+
+
+def test_mixing_width_dual_gradient_vs_central_differences():
+    n = 16
+    d = oracle.make_desc(ndim=2, n=(n, n), eq="euler", recon="mc", flux="rusanov", rk="ssprk2", bc="periodic",
+                         cfl=0.4)
+    dt, _ = oracle.fixed_dt_kh(n, 1.0, 0.4)
+    steps = 10
+    th = oracle.theta_splitmix(41, 1, 20)[0]
+    J, g = oracle.obs_grad_kh2d(d, th, dt, steps, "mixing")
+    assert J == pytest.approx(_mix_after(d, th, dt, steps), rel=1e-13)
+    fd = np.zeros(20)
+    for j in range(20):
+        h = 1e-6 * max(1.0, abs(th[j]))
+        tp, tm = th.copy(), th.copy()
+        tp[j] += h
+        tm[j] -= h
+        fd[j] = (_mix_after(d, tp, dt, steps) - _mix_after(d, tm, dt, steps)) / (2 * h)
+    assert np.abs(g - fd).max() <= 1e-4 * np.abs(g).max(), np.abs(g - fd).max() / np.abs(g).max()
+    assert np.abs(g).max() > 1e-3
+    # the kinetic-energy case is the same dual run
+    Jk, gk = oracle.obs_grad_kh2d(d, th, dt, steps, "ke")
+    Jk2, gk2 = oracle.ke_grad_kh2d(d, th, dt, steps)
+    assert Jk == Jk2 and np.array_equal(gk, gk2)
+
+
 def test_fixed_dt_reading_at_512():
     dt, n = oracle.fixed_dt_kh(512, 1.0, 0.4)
     assert n == 3035 and dt == 1.0 / 3035

@@ -64,7 +64,9 @@ enum {
     ALSV_INIT_VORTEX = 4,       /* isentropic vortex, 5x5 Gauss cell averages */
     ALSV_INIT_RAW = 5           /* U_dev already holds the initial state */
 };
-enum { ALSV_OBS_KINETIC_ENERGY = 0 };
+/* Observables of the adjoint: kinetic energy sum |m|^2 / (2 rho) dV; mixing-layer width
+ * sum 4 c (1 - c) dV with c = rho - 1 the inner-band fraction of the KH densities 1 and 2. */
+enum { ALSV_OBS_KINETIC_ENERGY = 0, ALSV_OBS_MIXING_WIDTH = 1 };
 /* Sampling of the KH parameters theta_{b,j} (Sec. 2.2: Monte Carlo or Quasi Monte Carlo), from the
  * sample's global counter index g (sample_offset + b, or its level's index for an MLMC companion),
  * hi_j = 1 for amplitudes (first half of theta) and 2 pi for phases:
@@ -264,6 +266,10 @@ alsv_status alsv_conservation_totals_noalloc(const alsv_grid_desc* d, const void
 /* Kinetic energy sum_i |m_i|^2 / (2 rho_i) dV per sample in FP64 (Euler), into ke_dev[samples]. */
 alsv_status alsv_kinetic_energy(alsv_ctx* ctx, double* ke_dev);
 
+/* Mixing-layer width sum_i 4 (rho_i - 1)(2 - rho_i) dV per sample in FP64 (Euler; the KH densities
+ * 1 and 2 are the two pure states), into w_dev[samples]. Fixed-order sum; asynchronous. */
+alsv_status alsv_mixing_width(alsv_ctx* ctx, double* w_dev);
+
 /*
  * Discrete adjoint (not in the paper; gradient of an observable at time T with respect to the
  * KH parameters). Fixed step dt = T / n with n = ceil(T s_max / (cfl dx)), s_max the fastest
@@ -276,8 +282,9 @@ alsv_status alsv_kinetic_energy(alsv_ctx* ctx, double* ke_dev);
  *                                 steps + segment buffers + adjoint states)
  *   alsv_bind_adjoint_workspace   bind it (caller-owned, 256-byte aligned)
  *   alsv_adjoint_evolve           initial data from theta_dev (FP64 [samples][20]), forward with
- *                                 checkpoints, reverse sweep; writes J_dev[samples] and
- *                                 grad_theta_dev[samples][20] (FP64). SYNCHRONOUS. Supported:
+ *                                 checkpoints, reverse sweep for the observable ALSV_OBS_* at T;
+ *                                 writes J_dev[samples] and grad_theta_dev[samples][20] (FP64).
+ *                                 SYNCHRONOUS. Supported:
  *                                 2D Euler KH, periodic, PC or MC reconstruction, Rusanov flux,
  *                                 SSP-RK2 or RK3. ALSV_ERR_CFL when re-planning cannot bring the
  *                                 realised CFL under 0.5 within n_cap steps or 3 passes.

@@ -23,6 +23,7 @@ RK = {"ssprk2": 2, "ssprk3": 3}
 BC = {"periodic": 0, "outflow": 1, "reflective": 2, "halo": 3}
 PRECISION = {"fp32": 0, "fp64": 1}
 INIT = {"kh": 0, "sod": 1, "lax": 2, "burgers_sine": 3, "vortex": 4, "raw": 5}
+OBSERVABLE = {"ke": 0, "mixing": 1}
 MAX_LEVELS = 8
 
 
@@ -86,6 +87,7 @@ SIGNATURES = {
     "alsv_mlmc_accumulate": (C.c_int, [_ctx, _vp, _sz]),
     "alsv_mlmc_read": (C.c_int, [_ctx, _vp, _sz, _vp, _vp, _vp, _i64p]),
     "alsv_kinetic_energy": (C.c_int, [_ctx, _vp]),
+    "alsv_mixing_width": (C.c_int, [_ctx, _vp]),
     "alsv_conservation_totals_noalloc": (C.c_int, [C.POINTER(alsv_grid_desc), _vp, _sz, _vp, _vp]),
     "alsv_adjoint_workspace_bytes": (C.c_int, [_ctx, C.c_double, C.POINTER(_sz)]),
     "alsv_bind_adjoint_workspace": (C.c_int, [_ctx, _vp, _sz]),
@@ -319,6 +321,10 @@ def alsv_kinetic_energy(ctx, ke):
     _check(load().alsv_kinetic_energy(ctx, _ptr(ke)), "alsv_kinetic_energy", ctx)
 
 
+def alsv_mixing_width(ctx, w):
+    _check(load().alsv_mixing_width(ctx, _ptr(w)), "alsv_mixing_width", ctx)
+
+
 def alsv_adjoint_workspace_bytes(ctx, T: float) -> int:
     b = C.c_size_t()
     _check(load().alsv_adjoint_workspace_bytes(ctx, T, C.byref(b)), "alsv_adjoint_workspace_bytes", ctx)
@@ -330,7 +336,9 @@ def alsv_bind_adjoint_workspace(ctx, ws, nbytes: int | None = None):
            "alsv_bind_adjoint_workspace", ctx)
 
 
-def alsv_adjoint_evolve(ctx, T: float, observable: int, theta, grad_theta, J):
+def alsv_adjoint_evolve(ctx, T: float, observable, theta, grad_theta, J):
+    """observable: ALSV_OBS_* (int) or a name of OBSERVABLE ("ke", "mixing")."""
+    observable = OBSERVABLE[observable] if isinstance(observable, str) else int(observable)
     _check(load().alsv_adjoint_evolve(ctx, T, observable, _ptr(theta), _ptr(grad_theta), _ptr(J)),
            "alsv_adjoint_evolve", ctx)
 

@@ -399,6 +399,24 @@ __global__ void k_ke_seed(const GridArgs g, const void* Uv, void* Lv) {
     Lm[3 * C + i] = R(0);
 }
 
+// lambda^n = d W / d U^n, W = sum 4 (rho - 1)(2 - rho) dV (mixing-layer width): only rho enters
+template <class R>
+__global__ void k_mix_seed(const GridArgs g, const void* Uv, void* Lv) {
+    const LevelInfo& L = g.lev[0];
+    const long long C = (long long)L.n[0] * L.n[1];
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int b = blockIdx.y;
+    if (i >= C) return;
+    const R* U = reinterpret_cast<const R*>(Uv) + (long long)b * 4 * C;
+    R* Lm = reinterpret_cast<R*>(Lv) + (long long)b * 4 * C;
+    const double dV = L.dx[0] * L.dx[1];
+    const double rho = (double)U[i];
+    Lm[i] = R(4.0 * (3.0 - 2.0 * rho) * dV);
+    Lm[C + i] = R(0);
+    Lm[2 * C + i] = R(0);
+    Lm[3 * C + i] = R(0);
+}
+
 // KH initial data adjoint, part 1: per (sample, column) G(x) = dJ/dY(x), with
 //   U = f Uin + (1-f) Uout, f = clamp01((0.75+Y-ylo)/hy) - clamp01((0.25+Y-ylo)/hy)
 // (clamp01 has derivative 1 on [0, 1], the branch the forward takes there).
@@ -562,7 +580,8 @@ alsv_status alsv_adjoint_evolve(alsv_ctx* c, double T, int observable, const dou
                                 double* J_dev) {
     alsv_status st = adj_validate(c);
     if (st != ALSV_OK) return st;
-    if (observable != ALSV_OBS_KINETIC_ENERGY) return ctx_fail(c, ALSV_ERR_INVALID_ARG, "unknown observable");
+    if (observable != ALSV_OBS_KINETIC_ENERGY && observable != ALSV_OBS_MIXING_WIDTH)
+        return ctx_fail(c, ALSV_ERR_INVALID_ARG, "unknown observable");
     if (!theta_dev || !grad_theta_dev || !J_dev) return ctx_fail(c, ALSV_ERR_INVALID_ARG, "null theta/grad/J pointer");
     if (!c->ws) return ctx_fail(c, ALSV_ERR_NOT_READY, "workspace not bound");
     if (!c->U) return ctx_fail(c, ALSV_ERR_NOT_READY, "no state buffer bound (call alsv_set_initial_data once)");
@@ -680,12 +699,18 @@ alsv_status alsv_adjoint_evolve(alsv_ctx* c, double T, int observable, const dou
     c->adj_dt = P.dt;
     const long long nseg = (P.n + P.c - 1) / P.c;
     // ---- observable and its seed
-    CKA(launch_reduce(c->fp64, 1, c->g, c->U, c->red, J_dev, s));
+    const bool mix = observable == ALSV_OBS_MIXING_WIDTH;
+    CKA(launch_reduce(c->fp64, mix ? 2 : 1, c->g, c->U, c->red, J_dev, s));
     const long long C = (long long)c->g.lev[0].n[0] * c->g.lev[0].n[1];
     {
         dim3 grid((unsigned)((C + 255) / 256), S);
-        if (c->fp64) k_ke_seed<double><<<grid, 256, 0, s>>>(c->g, c->U, Lam);
-        else k_ke_seed<float><<<grid, 256, 0, s>>>(c->g, c->U, Lam);
+        if (mix) {
+            if (c->fp64) k_mix_seed<double><<<grid, 256, 0, s>>>(c->g, c->U, Lam);
+            else k_mix_seed<float><<<grid, 256, 0, s>>>(c->g, c->U, Lam);
+        } else {
+            if (c->fp64) k_ke_seed<double><<<grid, 256, 0, s>>>(c->g, c->U, Lam);
+            else k_ke_seed<float><<<grid, 256, 0, s>>>(c->g, c->U, Lam);
+        }
         CKA(cudaGetLastError());
         c->launches += 3;
     }

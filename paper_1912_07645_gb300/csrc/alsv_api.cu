@@ -836,6 +836,17 @@ alsv_status alsv_conservation_totals(alsv_ctx* c, double* totals_dev) {
     return ALSV_OK;
 }
 
+alsv_status alsv_mixing_width(alsv_ctx* c, double* w_dev) {
+    alsv_status st = require_ready(c);
+    if (st != ALSV_OK) return st;
+    if (!w_dev) return fail(c, ALSV_ERR_INVALID_ARG, "null output");
+    if (c->eq != ALSV_EQ_EULER) return fail(c, ALSV_ERR_INVALID_ARG, "the mixing-layer width needs Euler");
+    cudaError_t e = launch_reduce(c->fp64, 2, c->g, c->U, c->red, w_dev, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "reduction kernel launch");
+    c->launches += 2;
+    return ALSV_OK;
+}
+
 alsv_status alsv_kinetic_energy(alsv_ctx* c, double* ke_dev) {
     alsv_status st = require_ready(c);
     if (st != ALSV_OK) return st;

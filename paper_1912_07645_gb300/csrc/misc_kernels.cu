@@ -574,6 +574,11 @@ __global__ void __launch_bounds__(kRT) k_reduce1(const GridArgs g, int kind, con
     for (long long i = c0 + threadIdx.x; i < c1; i += kRT) {
         if (kind == 0) {
             acc += (double)U[v * C + i];
+        } else if (kind == 2) {
+            // mixing-layer width: 4 c (1 - c), c = rho - 1 the inner-band fraction of the KH
+            // densities 1 and 2
+            const double rho = (double)U[i];
+            acc += 4.0 * (rho - 1.0) * (2.0 - rho);
         } else {
             const double rho = (double)U[i];
             double mm = 0.0;

@@ -241,15 +241,22 @@ class Solver:
         A.alsv_conservation_totals(self.ctx, out)
         return out
 
+    def mixing_width(self):
+        with self.torch.cuda.stream(self.stream):
+            out = self.torch.empty(self.samples, dtype=self.torch.float64, device=self.device)
+        A.alsv_mixing_width(self.ctx, out)
+        return out
+
     def kinetic_energy(self):
         with self.torch.cuda.stream(self.stream):
             out = self.torch.empty(self.samples, dtype=self.torch.float64, device=self.device)
         A.alsv_kinetic_energy(self.ctx, out)
         return out
 
-    def adjoint(self, theta, T):
-        """Kinetic energy J at T and dJ/dtheta for every sample (theta: [samples, 20] FP64 on the
-        device). Allocates the adjoint workspace on first use; synchronous."""
+    def adjoint(self, theta, T, observable="ke"):
+        """Observable J at T ("ke": kinetic energy, "mixing": mixing-layer width) and dJ/dtheta for
+        every sample (theta: [samples, 20] FP64 on the device). Allocates the adjoint workspace on
+        first use; synchronous."""
         torch = self.torch
         need = A.alsv_adjoint_workspace_bytes(self.ctx, T)
         if self.adj_ws is None or self.adj_ws.numel() < need:
@@ -261,7 +268,7 @@ class Solver:
             th = theta.to(device=self.device, dtype=torch.float64).contiguous()
             J = torch.empty(self.samples, dtype=torch.float64, device=self.device)
             g = torch.empty((self.samples, 20), dtype=torch.float64, device=self.device)
-        A.alsv_adjoint_evolve(self.ctx, T, 0, th, g, J)
+        A.alsv_adjoint_evolve(self.ctx, T, observable, th, g, J)
         return J, g
 
     # ---- block of a decomposed grid: the stage-by-stage protocol driven by decomp.Decomposition

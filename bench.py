@@ -707,6 +707,7 @@ def main():
         print(json.dumps(line), flush=True)
     S.close()
     if world > 1:
+        dist.barrier()       # rank 0 may still be timing the CPU baseline: tear down together
         dist.destroy_process_group()
     return 0
 

@@ -358,7 +358,7 @@ bool stage_variant_supported(int fp64, int ndim, int eq, int recon, int rvars, i
 // =============================================================================================
 extern "C" {
 
-const char* alsv_version(void) { return "alsv 0.1 (sm_103a finite-volume MC solver)"; }
+const char* alsv_version(void) { return "alsv 0.2 (sm_103a finite-volume MC solver)"; }
 
 const char* alsv_last_error(const alsv_ctx* c) {
     if (!c) return g_init_error.c_str();

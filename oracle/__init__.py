@@ -127,6 +127,7 @@ def lib():
             L.orc_obs_grad_kh2d.argtypes = [dsc, dp, C.c_double, C.c_int64, C.c_int, dp, dp]
             L.orc_obs_grad_kh2d.restype = C.c_int
             L.orc_mixing_width.argtypes = [dsc, C.c_int, dp, dp]
+            L.orc_face_states.argtypes = [dsc, dp, C.c_int, C.c_int, C.c_int, C.c_int, dp, dp]
             L.orc_ke_dir_kh2d.argtypes = [dsc, dp, dp, C.c_double, C.c_int64, dp, dp]
             L.orc_ke_dir_kh2d.restype = C.c_int
             _lib = L
@@ -172,6 +173,17 @@ def cons_to_prim(d: Desc, U) -> np.ndarray:
     W = np.zeros_like(U)
     lib().orc_cons_to_prim(C.byref(d), _dp(U), _dp(W))
     return W
+
+
+def face_states(d: Desc, U, cell, k: int):
+    """(left face, right face) primitive states of one cell (x, y, z) along direction k of a single
+    sample U [nv, nz, ny, nx], after reconstruction and the positivity fallback."""
+    U = _f64(U)
+    nv = nvars(d)
+    Wl, Wr = np.zeros(nv), np.zeros(nv)
+    c = list(cell) + [0] * (3 - len(cell))
+    lib().orc_face_states(C.byref(d), _dp(U), c[0], c[1], c[2], k, _dp(Wl), _dp(Wr))
+    return Wl, Wr
 
 
 def prim_to_cons(d: Desc, W) -> np.ndarray:

@@ -619,6 +619,13 @@ void orc_recon(int recon, double eps, double wm, double w0, double wp, double* f
 }
 
 void orc_cons_to_prim(const Desc* d, const double* U, double* W) { cons_to_prim(*d, U, W); }
+// The two face states (primitive; Burgers: u) of cell (cx, cy, cz) along direction k of one sample
+// U, after reconstruction and the positivity fallback: what every interface flux of the scheme
+// receives from that cell.
+void orc_face_states(const Desc* d, const double* U, int cx, int cy, int cz, int k, double* Wl, double* Wr) {
+    const int c[3] = {cx, cy, cz};
+    cell_faces(*d, U, c, k, c[k], Wl, Wr);
+}
 void orc_prim_to_cons(const Desc* d, const double* W, double* U) { prim_to_cons(*d, W, U); }
 
 // L(U) for B samples.

@@ -502,6 +502,67 @@ def test_dual_gradient_dot_direction():
     assert dJ == pytest.approx(np.dot(g, v), rel=1e-10)
 
 
+def _tube(rho, p, u=None):
+    """1D Euler state [1, 3, 1, 1, n] from primitive rows (gamma = 1.4)."""
+    rho, p = np.asarray(rho, float), np.asarray(p, float)
+    u = np.zeros_like(rho) if u is None else np.asarray(u, float)
+    U = np.zeros((1, 3, 1, 1, rho.size))
+    U[0, 0, 0, 0] = rho
+    U[0, 1, 0, 0] = rho * u
+    U[0, 2, 0, 0] = p / 0.4 + 0.5 * rho * u * u
+    return U
+
+
+@pytest.mark.parametrize("rvars", ["prim", "cons"])
+def test_positivity_fallback_face_states(rvars):
+    """Reading O6: WENO3 on (4, 1, 50) overshoots below zero at the right face of the middle cell
+    (the smooth left stencil extrapolates -1/2*4 + 3/2*1 < 0 with weight near one); that face then
+    carries the cell's own state in every variable, while the left face keeps its reconstruction."""
+    d = oracle.make_desc(ndim=1, n=(5,), eq="euler", recon="weno3", rvars=rvars, flux="hllc", bc="periodic")
+    _, fr_rho = oracle.recon("weno3", 4.0, 1.0, 50.0)
+    assert fr_rho < 0.0
+    # density overshoot
+    U = _tube([4.0, 1.0, 50.0, 1.0, 1.0], [1.0] * 5)
+    cell = oracle.cons_to_prim(d, U[0, :, 0, 0, 1])        # the cell's own primitive state
+    Wl, Wr = oracle.face_states(d, U[0], (1,), 0)
+    np.testing.assert_array_equal(Wr, cell)
+    assert Wl[0] > 0 and Wl[2] > 0 and Wl[0] != cell[0]
+    if rvars == "prim":
+        fl_rho, _ = oracle.recon("weno3", 4.0, 1.0, 50.0)
+        assert Wl[0] == fl_rho and Wl[1] == 0.0 and Wl[2] == cell[2]
+    # pressure overshoot (density uniform): same fallback
+    U = _tube([1.0] * 5, [4.0, 1.0, 50.0, 1.0, 1.0])
+    cell = oracle.cons_to_prim(d, U[0, :, 0, 0, 1])
+    Wl, Wr = oracle.face_states(d, U[0], (1,), 0)
+    np.testing.assert_array_equal(Wr, cell)
+    assert Wl[2] > 0 and Wl[2] != cell[2]
+    # the mirrored data falls back at the mirrored (left) face
+    U = _tube([1.0, 1.0, 50.0, 1.0, 4.0], [1.0] * 5)
+    cell = oracle.cons_to_prim(d, U[0, :, 0, 0, 3])
+    Wl, Wr = oracle.face_states(d, U[0], (3,), 0)
+    np.testing.assert_array_equal(Wl, cell)
+    assert Wr[0] > 0 and Wr[0] != cell[0]
+
+
+def test_positivity_fallback_keeps_runs_physical_and_mirror_symmetric():
+    """Steep density and pressure contrasts whose WENO3 faces overshoot below zero: the run stays
+    physical (a non-positive face state would give a NaN sound speed) and the mirrored data gives
+    the mirrored result."""
+    d = oracle.make_desc(ndim=1, n=(12,), eq="euler", recon="weno3", rvars="prim", flux="hllc", rk="ssprk3",
+                         bc="periodic", cfl=0.3)
+    rho = np.array([4.0, 1.0, 50.0, 1.0, 1.0, 30.0, 0.5, 0.5, 2.0, 1.0, 80.0, 1.0])
+    p = np.array([1.0, 1.0, 1.0, 4.0, 0.2, 40.0, 1.0, 1.0, 1.0, 2.0, 1.0, 1.0])
+    u = np.linspace(-0.3, 0.4, 12)
+    U = _tube(rho, p, u)
+    out, steps, _ = oracle.evolve(d, U, T=math.inf, max_steps=6)
+    assert steps[0] == 6 and np.all(np.isfinite(out))
+    Um = _tube(rho[::-1], p[::-1], -u[::-1])
+    outm, _, _ = oracle.evolve(d, Um, T=math.inf, max_steps=6)
+    mir = outm[..., ::-1].copy()
+    mir[:, 1] *= -1
+    np.testing.assert_allclose(mir, out, rtol=1e-12, atol=1e-12)
+
+
 def _mix_after(d, th, dt, steps):
     U = oracle.init(d, "kh", 1, th[None, :])
     U, _, _ = oracle.evolve(d, U, fixed_dt=dt, n_steps=steps)

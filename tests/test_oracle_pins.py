@@ -373,6 +373,53 @@ def test_kh_init_band_mass_closed_form():
     assert not np.allclose(U[0], U[1])
 
 
+def _lower_interface(U, dy):
+    """Per column, the lower interface height 0.25 + Y recovered from the density: below y = 1/2
+    the column holds 1 per unit height plus 1 more between the interface and 1/2, so
+    sum_{y < 1/2} rho dy = 0.5 + (0.5 - (0.25 + Y)) = 0.75 - Y."""
+    half = U.shape[-2] // 2
+    return 0.75 - U[0, 0, :, :half, :].sum(axis=1) * dy + 0.25        # [nz, nx]: 0.25 + Y
+
+
+def test_kh_single_mode_interface_position_2d():
+    """One Fourier mode (a_3 = 0.7, b_3 = 0.4): the interface recovered from each column's mass is
+    0.25 + 0.01 a_3 sin(2 pi 3 x_c + b_3) at the cell centres x_c (reading O2)."""
+    nx, ny = 24, 40
+    d = oracle.make_desc(ndim=2, n=(nx, ny), eq="euler")
+    th = np.zeros((1, 20))
+    th[0, 2], th[0, 12] = 0.7, 0.4
+    U = oracle.init(d, "kh", 1, th)
+    y_if = _lower_interface(U, 1.0 / ny)[0]
+    xc = (np.arange(nx) + 0.5) / nx
+    np.testing.assert_allclose(y_if, 0.25 + 0.01 * 0.7 * np.sin(2 * np.pi * 3 * xc + 0.4), rtol=0, atol=1e-14)
+
+
+def test_kh_3d_band_mass_and_single_mode_interface():
+    """3D slab (reading O2): the band keeps width 1/2 in every (x, z) column, so mass, momenta and
+    energy take the 2D closed forms for any parameters; one mode a_nm (n = 2 along x, m = 3 along z,
+    n-major index 8 (n - 1) + (m - 1)) puts the interface at 0.25 + 0.01 a sin(2 pi (2 x + 3 z) + b)."""
+    n = (12, 16, 10)
+    d = oracle.make_desc(ndim=3, n=n, eq="euler")
+    th = oracle.theta_splitmix(3, 2, 128)
+    U = oracle.init(d, "kh", 2, th)
+    tot = oracle.totals(d, U)
+    g = 1.4
+    for b in range(2):
+        assert tot[b, 0] == pytest.approx(1.5, rel=1e-14)
+        assert tot[b, 1] == pytest.approx(-0.25, rel=1e-13)
+        assert tot[b, 2] == 0.0 and tot[b, 3] == 0.0
+        assert tot[b, 4] == pytest.approx(0.5 * (2.5 / (g - 1) + 0.25) + 0.5 * (2.5 / (g - 1) + 0.125), rel=1e-14)
+    one = np.zeros((1, 128))
+    j = 8 * (2 - 1) + (3 - 1)
+    one[0, j], one[0, 64 + j] = 0.9, 1.1
+    U1 = oracle.init(d, "kh", 1, one)
+    y_if = _lower_interface(U1, 1.0 / n[1])                       # [nz, nx]
+    xc = (np.arange(n[0]) + 0.5) / n[0]
+    zc = (np.arange(n[2]) + 0.5) / n[2]
+    Y = 0.01 * 0.9 * np.sin(2 * np.pi * (2 * xc[None, :] + 3 * zc[:, None]) + 1.1)
+    np.testing.assert_allclose(y_if, 0.25 + Y, rtol=0, atol=1e-14)
+
+
 def test_sod_mirror_symmetry():
     n = 128
     d = oracle.make_desc(ndim=1, n=(n,), eq="euler", recon="weno3", flux="hllc", rk="ssprk3", bc="outflow")

@@ -293,6 +293,42 @@ def test_burgers_pre_shock_convergence(recon, rk, fl, lo_rate):
     assert rates[-1] >= lo_rate, rates
 
 
+def test_burgers_multid_directions_equal_the_1d_run():
+    """Burgers in 2D/3D applies u^2/2 along every direction: data varying only along y (2D) or z
+    (3D) evolves exactly as the 1D run along x."""
+    n = 32
+    kw = dict(eq="burgers", recon="weno3", flux="rusanov", rk="ssprk3", cfl=0.45)
+    d1 = oracle.make_desc(ndim=1, n=(n,), bc="periodic", **kw)
+    u1 = oracle.init(d1, "burgers_sine")
+    r1, s1, _ = oracle.evolve(d1, u1, T=0.08)
+    d2 = oracle.make_desc(ndim=2, n=(3, n), bc="periodic", **kw)
+    U2 = np.repeat(u1[:, :, :, :, :].reshape(1, 1, 1, n, 1), 3, axis=4)
+    r2, s2, _ = oracle.evolve(d2, U2, T=0.08)
+    d3 = oracle.make_desc(ndim=3, n=(2, 3, n), bc="periodic", **kw)
+    U3 = np.broadcast_to(u1.reshape(1, 1, n, 1, 1), (1, 1, n, 3, 2)).copy()
+    r3, s3, _ = oracle.evolve(d3, U3, T=0.08)
+    assert s1[0] == s2[0] == s3[0]
+    for i in range(3):
+        assert np.array_equal(r2[0, 0, 0, :, i], r1[0, 0, 0, 0])
+    for i in range(2):
+        for j in range(3):
+            assert np.array_equal(r3[0, 0, :, j, i], r1[0, 0, 0, 0])
+
+
+def test_burgers_reflective_walls_match_the_odd_periodic_solution():
+    """u0 = sin(2 pi x) is odd about x = 0 and x = 1, so mirrored ghosts with negated u (reading
+    O11 for the scalar law) equal the periodic ghosts: the reflective run equals the periodic one,
+    through the shock at t > 1/(2 pi)."""
+    n = 64
+    kw = dict(eq="burgers", recon="mc", flux="hll", rk="ssprk2", cfl=0.45)
+    dp = oracle.make_desc(ndim=1, n=(n,), bc="periodic", **kw)
+    dr = oracle.make_desc(ndim=1, n=(n,), bc="reflective", **kw)
+    u0 = oracle.init(dp, "burgers_sine")
+    rp, _, _ = oracle.evolve(dp, u0, T=0.3)
+    rr, _, _ = oracle.evolve(dr, u0, T=0.3)
+    np.testing.assert_allclose(rr, rp, rtol=0, atol=1e-13)
+
+
 def test_burgers_init_exact_cell_averages():
     d = oracle.make_desc(ndim=1, n=(16,), eq="burgers")
     U = oracle.init(d, "burgers_sine")[0, 0, 0, 0]

@@ -481,6 +481,33 @@ def test_rotation_symmetry_2d():
     np.testing.assert_allclose(Rt, U.transpose(0, 1, 2, 4, 3)[:, [0, 2, 1, 3]], rtol=1e-13, atol=1e-13)
 
 
+def test_rotation_symmetry_3d():
+    """The 3D slab rotated about y (x <-> z with u <-> w) evolves to the rotated result: every
+    direction uses its own normal velocity and spacing."""
+    n = (10, 12, 10)
+    d = oracle.make_desc(ndim=3, n=n, eq="euler", recon="weno3", flux="hllc", rk="ssprk3", bc="periodic", cfl=0.3)
+    th = oracle.theta_splitmix(11, 1, 128)
+    U0 = oracle.init(d, "kh", theta=th)
+    U0[:, 3] = 0.2 * U0[:, 0]                       # a z-velocity too, so that w moves with x
+    R0 = U0.transpose(0, 1, 4, 3, 2)[:, [0, 3, 2, 1, 4]].copy()
+    U, _, _ = oracle.evolve(d, U0, T=0.02)
+    Rt, _, _ = oracle.evolve(d, R0, T=0.02)
+    np.testing.assert_allclose(Rt, U.transpose(0, 1, 4, 3, 2)[:, [0, 3, 2, 1, 4]], rtol=1e-13, atol=1e-13)
+
+
+def test_cfl_speed_takes_each_direction_with_its_own_spacing():
+    """Reading O9 with O1: s = max_k (|u_k| + c) / dx_k on a 2 x 1 domain with dx = 2 dy."""
+    d = oracle.make_desc(ndim=2, n=(10, 10), hi=(2.0, 1.0, 1.0), eq="euler")
+    rho, u, v, p = 1.3, 0.3, 0.1, 0.9
+    U = np.zeros((1, 4, 1, 10, 10))
+    U[:, 0], U[:, 1], U[:, 2] = rho, rho * u, rho * v
+    U[:, 3] = p / 0.4 + 0.5 * rho * (u * u + v * v)
+    c = math.sqrt(1.4 * p / rho)
+    s = oracle.max_speed(d, U)[0]
+    assert s == pytest.approx(max((u + c) / 0.2, (v + c) / 0.1), rel=1e-14)
+    assert s == pytest.approx((v + c) / 0.1, rel=1e-14)
+
+
 def test_1d_extruded_in_y_equals_1d_bitwise():
     n = 64
     d1 = oracle.make_desc(ndim=1, n=(n,), eq="euler", recon="weno3", flux="hllc", rk="ssprk3", bc="outflow")

@@ -44,6 +44,34 @@ def test_binding_covers_every_symbol(alsv):
         assert hasattr(_abi, n)
 
 
+def test_descriptor_mirror_matches_the_header():
+    """The ctypes mirror of alsv_grid_desc lists the header's fields in the header's order, with the
+    same scalar types and array extents (a stale mirror would shift every later field)."""
+    from paper_1912_07645_gb300 import _abi
+    import ctypes as C
+    text = open(os.path.join(ROOT, "include", "alsv.h")).read()
+    body = re.search(r"typedef struct alsv_grid_desc \{(.*?)\} alsv_grid_desc;", text, flags=re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    ctype = {"int32_t": C.c_int32, "int64_t": C.c_int64, "uint64_t": C.c_uint64, "double": C.c_double}
+    header = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        typ, rest = decl.split(None, 1)
+        for name in (v.strip() for v in rest.split(",")):
+            dims = [int(x) if x.isdigit() else {"ALSV_MAX_LEVELS": _abi.MAX_LEVELS}[x]
+                    for x in re.findall(r"\[(\w+)\]", name)]
+            header.append((re.match(r"\w+", name).group(0), ctype[typ], dims))
+    mirror = _abi.alsv_grid_desc._fields_
+    assert [h[0] for h in header] == [m[0] for m in mirror]
+    for (name, typ, dims), (_, mt) in zip(header, mirror):
+        for n in dims:
+            assert issubclass(mt, C.Array) and mt._length_ == n, name
+            mt = mt._type_
+        assert mt == typ, name
+
+
 def test_version(alsv):
     assert "alsv" in alsv.alsv_version()
 

@@ -72,6 +72,17 @@ def test_descriptor_mirror_matches_the_header():
         assert mt == typ, name
 
 
+def test_binding_argument_counts_match_the_prototypes():
+    from paper_1912_07645_gb300 import _abi
+    text = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "alsv.h")).read(), flags=re.S)
+    protos = dict(re.findall(r"\b(alsv_\w+)\s*\(([^)]*)\)\s*;", text))
+    assert len(protos) == len(_abi.SIGNATURES)
+    for name, params in protos.items():
+        params = params.strip()
+        n = 0 if params in ("", "void") else params.count(",") + 1
+        assert len(_abi.SIGNATURES[name][1]) == n, name
+
+
 def test_version(alsv):
     assert "alsv" in alsv.alsv_version()
 

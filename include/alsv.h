@@ -448,7 +448,9 @@ alsv_status alsv_destroy(alsv_ctx* ctx);
  *                           32, 16).
  *                           FP32 3D: 0, 1 tiles of 16x8x8, 8x8x8; 2, 3 z-marching 32x8 column
  *                           chunks of 64 / 128 planes (Euler); 4 as 2 with the x and y interfaces
- *                           of a plane packed in FP32x2 (primitive, HLLC/Rusanov). FP64 2D / 3D:
+ *                           of a plane packed in FP32x2 (primitive, HLLC/Rusanov); 5 as 4 with
+ *                           32x7 columns on 256 threads (a plane's 256 interface pairs in one
+ *                           pass). FP64 2D / 3D:
  *                           0, 1 tiles. 1D: tiles of 256, 64, 32 cells.
  *   alsv_set_tile_variant   select one (recomputes the wave-speed partials; asynchronous;
  *                           ALSV_ERR_INVALID_ARG if the variant does not support the scheme)

@@ -326,13 +326,14 @@ TileShape stage_tile(int fp64, int ndim, int variant) {
     if (variant == 2) return TileShape{32, 8, 64, 256};    // z-marching column chunks
     if (variant == 3) return TileShape{32, 8, 128, 256};
     if (variant == 4) return TileShape{32, 8, 64, 256};     // z-march, packed x/y interfaces
+    if (variant == 5) return TileShape{32, 7, 64, 256};     // as 4 with 32 x 7 columns, 256 threads
     return variant == 1 ? TileShape{8, 8, 8, 256} : TileShape{16, 8, 8, 256};
 }
 bool stage_variant_halves(int fp64, int ndim, int variant) { return ndim == 2 && !fp64 && (variant == 6 || variant == 7); }
 int stage_num_variants(int fp64, int ndim) {
     if (ndim == 1) return 3;
     if (ndim == 2 && !fp64) return 8;
-    if (ndim == 3 && !fp64) return 5;
+    if (ndim == 3 && !fp64) return 6;
     return 2;
 }
 bool stage_variant_supported(int fp64, int ndim, int eq, int recon, int rvars, int flux, const int bc[3][2], int variant) {
@@ -342,7 +343,7 @@ bool stage_variant_supported(int fp64, int ndim, int eq, int recon, int rvars, i
     if (ndim == 2 && !fp64 && (variant == 6 || variant == 7))
         return eq == EQ_EULER && rvars == RV_PRIM && (flux == FLX_HLLC || flux == FLX_RUSANOV) &&
                bc[1][0] == BC_PERIODIC && bc[1][1] == BC_PERIODIC;
-    if (ndim == 3 && !fp64 && variant == 4)
+    if (ndim == 3 && !fp64 && (variant == 4 || variant == 5))
         return eq == EQ_EULER && rvars == RV_PRIM && (flux == FLX_HLLC || flux == FLX_RUSANOV);
     if (ndim == 3 && !fp64 && variant >= 2) return eq == EQ_EULER;
     if (!(ndim == 2 && !fp64 && variant == 3)) return true;

@@ -21,11 +21,15 @@ namespace alsv {
 // PACK = 1 (primitive reconstruction, HLLC or Rusanov): each thread evaluates the k-th x-interface
 // and the k-th y-interface of the plane together in packed FP32x2 arithmetic (lane .x the
 // x-interface with normal velocity u, lane .y the y-interface with normal velocity v).
-template <int RECON, int FLUX, int TX, int TY, int LZ, int PACK = 0>
-__global__ void __launch_bounds__(TX * TY, 4) k_stage3d_zm(const StageArgs p) {
+// NTH threads (default: one per column); more threads than columns lets a plane's interface pairs
+// fit in one pass (32 x 7 columns: 256 pairs for 256 threads), the threads past the columns only
+// take part in the loads and the interfaces.
+template <int RECON, int FLUX, int TX, int TY, int LZ, int PACK = 0, int NTH = TX * TY>
+__global__ void __launch_bounds__(NTH, 4) k_stage3d_zm(const StageArgs p) {
     using R = float;
     constexpr int ND = 3, NV = 5, G = (RECON == REC_PC) ? 1 : 2;
-    constexpr int NT = TX * TY;
+    constexpr int NT = NTH;
+    static_assert(NT >= TX * TY && NT % 32 == 0 && NT / TX <= TY + 2 * G, "threads cover the columns");
     constexpr int SX = TX + 2 * G, SY = TY + 2 * G, PS = SX * SY;   // halo plane
     constexpr int NP = 2 * G + 1;                                    // ring planes
     constexpr int NIX = (TX + 1) * TY, NIY = TX * (TY + 1);
@@ -62,7 +66,7 @@ __global__ void __launch_bounds__(TX * TY, 4) k_stage3d_zm(const StageArgs p) {
     const int tid = threadIdx.x;
     const int cx = tid % TX, cy = tid / TX;
     const int X = tx0 + cx, Y = ty0 + cy;
-    const bool own = X < nx && Y < ny;
+    const bool own = cy < TY && X < nx && Y < ny;
     const bool xy_interior = tx0 >= G && tx0 + TX + G <= nx && ty0 >= G && ty0 + TY + G <= ny;
     const int rv = g.rvars;
 
@@ -303,9 +307,9 @@ constexpr size_t zm_smem_bytes() {
     return sizeof(float) * 5 * ((size_t)(2 * G + 1) * (TX + 2 * G) * (TY + 2 * G) + (TX + 1) * TY + TX * (TY + 1));
 }
 
-template <int RECON, int FLUX, int TX, int TY, int LZ, int PACK = 0>
+template <int RECON, int FLUX, int TX, int TY, int LZ, int PACK = 0, int NTH = TX * TY>
 static cudaError_t launch_zm_one(const StageArgs& a, cudaStream_t s) {
-    auto k = k_stage3d_zm<RECON, FLUX, TX, TY, LZ, PACK>;
+    auto k = k_stage3d_zm<RECON, FLUX, TX, TY, LZ, PACK, NTH>;
     constexpr size_t sm = zm_smem_bytes<RECON, TX, TY, LZ>();
     static unsigned long long smem_devices = 0;   // devices on which the opt-in is done
     {
@@ -313,7 +317,7 @@ static cudaError_t launch_zm_one(const StageArgs& a, cudaStream_t s) {
         if (e != cudaSuccess) return e;
     }
     if (a.g.total_work <= 0) return cudaSuccess;
-    k<<<(unsigned)a.g.total_work, TX * TY, sm, s>>>(a);
+    k<<<(unsigned)a.g.total_work, NTH, sm, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -334,17 +338,17 @@ static cudaError_t launch_stage_zm(int recon, int flux, const StageArgs& a, cuda
 }
 
 // packed x/y interfaces (primitive reconstruction, HLLC or Rusanov)
-template <int TX, int TY, int LZ>
+template <int TX, int TY, int LZ, int NTH = TX * TY>
 static cudaError_t launch_stage_zm_packed(int recon, int flux, const StageArgs& a, cudaStream_t s) {
     if (a.g.rvars != RV_PRIM || (flux != FLX_HLLC && flux != FLX_RUSANOV)) return cudaErrorNotSupported;
     if (flux == FLX_HLLC) {
-        if (recon == REC_WENO3) return launch_zm_one<REC_WENO3, FLX_HLLC, TX, TY, LZ, 1>(a, s);
-        if (recon == REC_MC) return launch_zm_one<REC_MC, FLX_HLLC, TX, TY, LZ, 1>(a, s);
-        return launch_zm_one<REC_PC, FLX_HLLC, TX, TY, LZ, 1>(a, s);
+        if (recon == REC_WENO3) return launch_zm_one<REC_WENO3, FLX_HLLC, TX, TY, LZ, 1, NTH>(a, s);
+        if (recon == REC_MC) return launch_zm_one<REC_MC, FLX_HLLC, TX, TY, LZ, 1, NTH>(a, s);
+        return launch_zm_one<REC_PC, FLX_HLLC, TX, TY, LZ, 1, NTH>(a, s);
     }
-    if (recon == REC_WENO3) return launch_zm_one<REC_WENO3, FLX_RUSANOV, TX, TY, LZ, 1>(a, s);
-    if (recon == REC_MC) return launch_zm_one<REC_MC, FLX_RUSANOV, TX, TY, LZ, 1>(a, s);
-    return launch_zm_one<REC_PC, FLX_RUSANOV, TX, TY, LZ, 1>(a, s);
+    if (recon == REC_WENO3) return launch_zm_one<REC_WENO3, FLX_RUSANOV, TX, TY, LZ, 1, NTH>(a, s);
+    if (recon == REC_MC) return launch_zm_one<REC_MC, FLX_RUSANOV, TX, TY, LZ, 1, NTH>(a, s);
+    return launch_zm_one<REC_PC, FLX_RUSANOV, TX, TY, LZ, 1, NTH>(a, s);
 }
 
 }  // namespace alsv

@@ -9,6 +9,7 @@ cudaError_t launch_stage_f32_3d(int variant, int eq, int recon, int flux, const 
         case 2: return eq == EQ_EULER ? launch_stage_zm<32, 8, 64>(recon, flux, a, s) : cudaErrorInvalidValue;
         case 3: return eq == EQ_EULER ? launch_stage_zm<32, 8, 128>(recon, flux, a, s) : cudaErrorInvalidValue;
         case 4: return eq == EQ_EULER ? launch_stage_zm_packed<32, 8, 64>(recon, flux, a, s) : cudaErrorInvalidValue;
+        case 5: return eq == EQ_EULER ? launch_stage_zm_packed<32, 7, 64, 256>(recon, flux, a, s) : cudaErrorInvalidValue;
         default: return cudaErrorInvalidValue;
     }
 }
@@ -19,6 +20,7 @@ cudaError_t launch_speed_f32_3d(int variant, int eq, const GridArgs& g, const vo
         case 2: return launch_speed_tile<float, 3, 32, 8, 64, 256>(eq, g, U, part, s);
         case 3: return launch_speed_tile<float, 3, 32, 8, 128, 256>(eq, g, U, part, s);
         case 4: return launch_speed_tile<float, 3, 32, 8, 64, 256>(eq, g, U, part, s);
+        case 5: return launch_speed_tile<float, 3, 32, 7, 64, 256>(eq, g, U, part, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -382,11 +382,36 @@ def test_kh_3d_zmarch_bitwise_equal_to_tiles(variant, recon, flux, rvars, bc):
     np.testing.assert_array_equal(outs[0][1][0], outs[1][1][0])
 
 
+@pytest.mark.parametrize("recon,flux,bc", [("weno3", "hllc", "periodic"),
+                                           ("mc", "rusanov", [("periodic", "periodic"), ("reflective", "outflow"),
+                                                              ("outflow", "reflective")])])
+def test_kh_3d_packed_zmarch_32x7_bitwise_equal_to_32x8(recon, flux, bc):
+    """Variant 5 runs the packed z-march of variant 4 on 32 x 7 columns with 256 threads: the same
+    packed arithmetic per interface, so bitwise equal (ragged: ny = 20 is 2 x 7 + 6)."""
+    import paper_1912_07645_gb300 as alsv
+    torch = torch_()
+    cfg = dict(ndim=3, n=(40, 20, 70), batch=2, eq="euler", recon=recon, flux=flux, rvars="prim", rk="ssprk3",
+               bc=bc, cfl=0.3, precision="fp32")
+    th = torch.from_numpy(kh_theta(2, 23, P=128)).cuda()
+    outs = []
+    for v in (4, 5):
+        S = gpu_solver(**cfg)
+        alsv.alsv_set_tile_variant(S.ctx, v)
+        S.set_initial_data("kh", theta=th)
+        S.step(3)
+        S.sync()
+        outs.append((host(S.U), S.time()))
+        S.close()
+    assert np.array_equal(outs[0][0], outs[1][0])
+    np.testing.assert_array_equal(outs[0][1][0], outs[1][1][0])
+
+
 @pytest.mark.parametrize("variant,recon,flux,bc", [
     (2, "weno3", "hllc", "periodic"),
     (4, "weno3", "hllc", "periodic"),
     (4, "mc", "rusanov", [("reflective", "outflow"), ("periodic", "periodic"), ("outflow", "reflective")]),
-    (4, "pc", "hllc", [("outflow", "outflow"), ("reflective", "reflective"), ("periodic", "periodic")])])
+    (4, "pc", "hllc", [("outflow", "outflow"), ("reflective", "reflective"), ("periodic", "periodic")]),
+    (5, "weno3", "hllc", [("periodic", "periodic"), ("reflective", "outflow"), ("periodic", "periodic")])])
 def test_kh_3d_zmarch_fp32_vs_oracle(variant, recon, flux, bc):
     """z-march schedules against the oracle (ragged: 70 planes); variant 4 packs an x- and a
     y-interface into the two FP32x2 lanes."""

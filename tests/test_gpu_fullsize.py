@@ -91,6 +91,56 @@ def test_kh3d_512_sampled_cells():
             assert np.abs(ov - U0[0, :, R, R, R]).max() > 1e-6
 
 
+def test_kh3d_1024_as_four_blocks_sampled_cells():
+    """One 1024^3 sample (more elements than one context holds) as four z-blocks with halo exchange,
+    in the launch configuration of the block workload (packed 32 x 7 z-march): one fixed CFL-0.3
+    step, then cells on both sides of a block boundary (z = 255 | 256, on the perturbed interface)
+    and one in the bulk against the oracle on a 13^3 block around each."""
+    import torch
+    from paper_1912_07645_gb300.decomp import Decomposition
+    n = 1024
+    dx = 1.0 / n
+    dt = 0.3 * dx / 2.4
+    cfg = dict(ndim=3, n=(n, n, n), batch=1, eq="euler", recon="weno3", flux="hllc", rvars="prim", rk="ssprk3",
+               bc="periodic", cfl=0.3, precision="fp32", seed=3, fixed_dt=dt)
+    D = Decomposition(parts=(1, 1, 4), tile_variant=5, **cfg)
+    D.set_initial_data("kh")
+
+    def column(x, z):
+        b = D.blocks[z // 256]
+        return host(b.state()[0, 0, z % 256, :, x])
+
+    picks = []
+    for (x, z) in [(100, 255), (101, 256)]:
+        rho = column(x, z)
+        ys = np.nonzero((rho > 1.0) & (rho < 2.0) & (np.arange(n) < n // 2))[0]
+        assert ys.size > 0
+        picks.append((x, int(ys[0]), z))
+    picks.append((700, 400, 767))
+    D.step(1)
+    D.sync()
+    g = [host(D.blocks[z // 256].state()[0, :, z % 256, y, x]) for (x, y, z) in picks]
+    t, steps = D.time()
+    D.close()
+    del D
+    torch.cuda.empty_cache()
+    assert int(steps[0]) == 1 and t[0] == dt
+    th = oracle.theta_splitmix(3, 1, 128)
+    R = 6
+    for (x, y, z), gv in zip(picks, g):
+        lo = ((x - R) * dx, (y - R) * dx, (z - R) * dx)
+        hi = ((x + R + 1) * dx, (y + R + 1) * dx, (z + R + 1) * dx)
+        d = oracle.make_desc(ndim=3, n=(2 * R + 1,) * 3, lo=lo, hi=hi, eq="euler", recon="weno3", flux="hllc",
+                             rvars="prim", rk="ssprk3", bc="outflow", cfl=0.3)
+        U0 = oracle.init(d, "kh", 1, th)
+        U1, _, _ = oracle.evolve(d, U0, fixed_dt=dt, n_steps=1)
+        ov = U1[0, :, R, R, R]
+        scale = np.maximum(np.abs(ov), 1.0)
+        assert np.all(np.abs(gv - ov) <= 2e-5 * scale), (x, y, z, gv, ov)
+        if (x, y, z) != picks[-1]:
+            assert np.abs(ov - U0[0, :, R, R, R]).max() > 1e-6
+
+
 def test_adjoint_512x64_vs_central_differences():
     import torch
     n, B, T = 512, 64, 0.01

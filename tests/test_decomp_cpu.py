@@ -42,6 +42,34 @@ def test_split_neighbours_and_block_faces():
     assert kw["bc"][0] == ("periodic", "periodic")
 
 
+def test_split_and_neighbours_edge_cases():
+    assert split(5, 5) == [(i, 1) for i in range(5)]
+    assert split(7, 2) == [(0, 4), (4, 3)]
+    # two blocks on a periodic direction: the same neighbour on both sides
+    per = [True, True, True]
+    assert neighbour((0, 0, 0), 0, (2, 1, 1), per) == (1, 0, 0)
+    assert neighbour((0, 0, 0), 1, (2, 1, 1), per) == (1, 0, 0)
+    # 3D block: faces only along the decomposed direction, offsets and the whole grid's counts
+    cfg = dict(ndim=3, n=(8, 6, 10), bc=[("periodic", "periodic"), ("outflow", "outflow"), ("reflective", "outflow")])
+    kw = block_config(cfg, (1, 1, 3), (0, 0, 2))
+    assert kw["n"] == (8, 6, 3) and kw["offset"] == (0, 0, 7) and kw["global_n"] == (8, 6, 10)
+    assert kw["bc"][0] == ("periodic", "periodic") and kw["bc"][1] == ("outflow", "outflow")
+    assert kw["bc"][2] == ("halo", "outflow")
+    kw = block_config(cfg, (1, 1, 3), (0, 0, 0))
+    assert kw["bc"][2] == ("reflective", "halo")
+
+
+def test_decomposition_rejects_bad_layouts():
+    cfg, _, _, _ = CASES["sod1d_x4"]
+    _, U0 = initial("sod1d_x4")
+    with pytest.raises(ValueError):
+        Decomposition(parts=(2, 2, 1), make_block=lambda **kw: OracleBlock(U0, **kw), **cfg)   # y in 1D
+    with pytest.raises(ValueError):
+        Decomposition(parts=(2,), transport="carrier pigeon", make_block=lambda **kw: OracleBlock(U0, **kw), **cfg)
+    with pytest.raises(ValueError):
+        split(3, 4)
+
+
 @pytest.fixture(scope="module")
 def alsv():
     from paper_1912_07645_gb300 import build

@@ -241,8 +241,8 @@ class DistExchange:
 class Decomposition:
     """One grid (``cfg``: the make_desc keywords of the whole grid) advanced as ``parts`` blocks.
 
-    ``transport``: "local" (every block in this process, one device, one stream) or "dist" (this
-    rank's block of a torch.distributed group whose size is the number of blocks).
+    ``transport``: "local" (every block in this process on one device, each on its own stream) or
+    "dist" (this rank's block of a torch.distributed group whose size is the number of blocks).
     ``make_block``: factory of a block from make_desc keywords (default: a Solver on ``device``).
     ``tile_variant``: stage schedule of every block (include/alsv.h, execution controls; None keeps
     the default).
@@ -314,7 +314,8 @@ class Decomposition:
         """Device time of the stage launches recorded since set_profiling(True), and their count."""
         if not self._prof:
             return 0.0, 0
-        self._prof[-1][1].synchronize()
+        for _, e1 in self._prof:      # the blocks' streams finish in any order
+            e1.synchronize()
         return sum(e0.elapsed_time(e1) for e0, e1 in self._prof), len(self._prof)
 
     def _stage(self, b, s):

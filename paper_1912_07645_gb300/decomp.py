@@ -399,6 +399,40 @@ class Decomposition:
         self._hand_over(main)
         return out
 
+    def _assemble(self, parts, axis_z, axis_y, axis_x):
+        """Concatenate per-block tensors (block order) into the whole grid along the given axes."""
+        torch = self.torch
+        px, py, pz = self.parts
+        at = dict(zip(self.coords, parts))
+        planes = []
+        for bz in range(pz):
+            rows = [torch.cat([at[(bx, by, bz)] for bx in range(px)], dim=axis_x) for by in range(py)]
+            planes.append(torch.cat(rows, dim=axis_y))
+        return torch.cat(planes, dim=axis_z)
+
+    def stats_accumulate(self):
+        """Fold the current samples into every block's FP64 Welford accumulator (the cells of the
+        blocks are disjoint, so no merge is needed)."""
+        for b in self.blocks:
+            b.stats_accumulate()
+
+    def stats_read(self):
+        """(count, mean [q, nz, ny, nx], unbiased variance) of the whole grid assembled from the
+        blocks (local transport; with "dist", this rank's block), ready on the caller's stream."""
+        torch = self.torch
+        reads = [b.stats_read() for b in self.blocks]
+        counts = {int(c) for c, _, _ in reads}
+        assert len(counts) == 1, "blocks folded different sample counts"
+        main = self.xch.join()
+        with (torch.cuda.stream(main) if main is not None else contextlib.nullcontext()):
+            if len(self.blocks) == 1:
+                mean, var = reads[0][1], reads[0][2]
+            else:
+                mean = self._assemble([m for _, m, _ in reads], 1, 2, 3)
+                var = self._assemble([v for _, _, v in reads], 1, 2, 3)
+        self._hand_over(main)
+        return counts.pop(), mean, var
+
     def totals(self):
         """FP64 conservation totals [B][nv] summed over the blocks (block order), ready on the
         caller's current stream."""

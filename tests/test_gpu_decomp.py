@@ -126,6 +126,14 @@ def test_block_statistics_and_totals():
         sl = (slice(None), slice(by * ny // 2, (by + 1) * ny // 2), slice(bx * nx // 2, (bx + 1) * nx // 2))
         assert np.array_equal(m, mean_w.reshape(4, ny, nx)[sl])
         assert np.array_equal(v, var_w.reshape(4, ny, nx)[sl])
+    # the same statistics through the driver, assembled into the whole grid
+    for b in dec.blocks:
+        b.stats_init()                  # fresh accumulators
+    dec.stats_accumulate()
+    cnt, mean_d, var_d = dec.stats_read()
+    assert cnt == cfg["batch"]
+    assert np.array_equal(host(mean_d).reshape(4, ny, nx), mean_w.reshape(4, ny, nx))
+    assert np.array_equal(host(var_d).reshape(4, ny, nx), var_w.reshape(4, ny, nx))
     dec.close()
     # totals are sums in another order: equal to FP64 rounding
     np.testing.assert_allclose(tot, tot_w, rtol=1e-13, atol=1e-13 * np.abs(tot_w).max())

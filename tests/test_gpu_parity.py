@@ -781,3 +781,46 @@ def test_pair_variant_mlmc_levels_odd_counts():
         p2_check(host(S.state(l)), o, what=f"pair level {l}")
         s0 += B
     S.close()
+
+
+# ------------------------------------------------------------------ seeded random configurations
+def _random_configs(count, seed=2026):
+    """Seeded draws over the descriptor: dimension, odd and ragged sizes, scheme, variables, RK
+    order, boundary kinds per face, precision and batch."""
+    rng = np.random.default_rng(seed)
+    out = []
+    while len(out) < count:
+        nd = int(rng.integers(1, 4))
+        hi_n = {1: 300, 2: 70, 3: 19}[nd]
+        n = tuple(int(v) for v in rng.integers(3, hi_n, nd))
+        recon = str(rng.choice(["pc", "mc", "weno3"]))
+        g = 1 if recon == "pc" else 2
+        bc = []
+        for k in range(nd):
+            kind = str(rng.choice(["periodic", "outflow", "reflective"]))
+            if kind == "periodic":
+                bc.append(("periodic", "periodic"))
+            else:
+                other = str(rng.choice(["outflow", "reflective"]))
+                bc.append((kind, other))
+            if "reflective" in bc[-1] and n[k] < g:
+                bc[-1] = ("outflow", "outflow")
+        out.append(dict(ndim=nd, n=n, batch=int(rng.integers(1, 4)), eq="euler", recon=recon,
+                        rvars=str(rng.choice(["prim", "cons"])), flux=str(rng.choice(["rusanov", "hll", "hllc"])),
+                        rk=str(rng.choice(["ssprk2", "ssprk3"])), bc=bc, cfl=0.3,
+                        precision=str(rng.choice(["fp64", "fp32"]))))
+    return out
+
+
+@pytest.mark.parametrize("k,cfg", list(enumerate(_random_configs(24))), ids=[f"r{k}" for k in range(24)])
+def test_seeded_random_configurations_vs_oracle(k, cfg):
+    """Four CFL steps of smooth random states on seeded random descriptors against the oracle:
+    FP64 per cell (P1), FP32 relative L1 (P2)."""
+    U0 = euler_state(cfg["batch"], cfg["ndim"], cfg["n"], seed=100 + k)
+    g, _, st, _ = run_gpu(cfg, U0=U0, steps=4)
+    o, ost, _ = run_oracle(cfg, U0=U0, steps=4)
+    assert np.array_equal(st, ost)
+    if cfg["precision"] == "fp64":
+        p1_check(g, o, what=f"random {cfg}")
+    else:
+        p2_check(g, o, what=f"random {cfg}")

@@ -143,6 +143,98 @@ def test_burgers_flux_vs_godunov_monotone(fl):
         assert F == pytest.approx(0.5 * a * a, rel=1e-15)
 
 
+def test_hll_equals_rusanov_for_symmetric_wave_speeds():
+    """Both states at rest with equal sound speed (p/rho equal) give S_L = -S_R = a: the HLL
+    formula then reduces to the Rusanov (local Lax-Friedrichs) flux with the same a. The two
+    formulas share no code, so a wrong coefficient or sign in either one breaks the identity."""
+    for nd in (1, 2, 3):
+        dh = oracle.make_desc(ndim=nd, n=(4, 4, 4), eq="euler", flux="hll")
+        dr = oracle.make_desc(ndim=nd, n=(4, 4, 4), eq="euler", flux="rusanov")
+        for _ in range(20):
+            rL, pL = rng.uniform(0.3, 3.0), rng.uniform(0.2, 4.0)
+            s = rng.uniform(0.1, 0.9)
+            vt = rng.uniform(-1.0, 1.0, nd)               # tangential velocities ride along
+            for k in range(nd):
+                WL = np.concatenate([[rL], vt, [pL]])
+                WR = np.concatenate([[s * rL], -vt, [s * pL]])
+                WL[1 + k] = WR[1 + k] = 0.0
+                Fh, Fr = oracle.flux(dh, k, WL, WR), oracle.flux(dr, k, WL, WR)
+                np.testing.assert_allclose(Fh, Fr, rtol=1e-13, atol=1e-14)
+                assert abs(Fh[0]) > 1e-3                   # the dissipation term is active
+
+
+def _entropy_wave_viscosity_run(fl, nd, u, rk, n=32, kmode=3, steps=40, eps=1e-7):
+    """PC scheme on a small-amplitude entropy wave rho = 1 + eps cos(2 pi kmode x), uniform normal
+    velocity u, tangential velocity 0.2 and pressure 1, fixed dt, periodic: returns (measured
+    amplification of the mode over the run, lambda = dt/dx, theta = 2 pi kmode / n, c)."""
+    g, p0 = 1.4, 1.0
+    c = math.sqrt(g * p0 / 1.0)
+    dx = 1.0 / n
+    dt = 0.4 * dx / (abs(u) + c)
+    x = (np.arange(n) + 0.5) * dx
+    rho = 1.0 + eps * np.cos(2 * np.pi * kmode * x)
+    ax = nd - 1                                          # the wave runs along the last direction
+    shape = [1] * 3
+    shape[2 - ax] = n
+    nn = [4, 4, 4][:nd]
+    nn[ax] = n
+    d = oracle.make_desc(ndim=nd, n=nn, eq="euler", recon="pc", flux=fl, rk=rk, bc="periodic")
+    U = np.zeros(oracle.state_shape(d, 1))
+    r = np.broadcast_to(rho.reshape(shape), U.shape[2:])
+    vel = np.full(nd, 0.2)
+    vel[ax] = u
+    U[0, 0] = r
+    for j in range(nd):
+        U[0, 1 + j] = r * vel[j]
+    U[0, 1 + nd] = p0 / (g - 1) + 0.5 * r * np.dot(vel, vel)
+    Un, _, _ = oracle.evolve(d, U, fixed_dt=dt, n_steps=steps)
+    line = [0] * 3
+    line[2 - ax] = slice(None)
+    r0 = U[0, 0][tuple(line)] - 1.0
+    r1 = Un[0, 0][tuple(line)] - 1.0
+    G = np.fft.fft(r1)[kmode] / np.fft.fft(r0)[kmode]
+    # the velocity and pressure of an entropy wave stay uniform under any of these fluxes
+    W = Un[0, 1 + ax] / Un[0, 0]
+    assert np.abs(W - u).max() < 1e-12
+    return G, dt / dx, 2 * np.pi * kmode / n, c
+
+
+@pytest.mark.parametrize("nd", [1, 2])
+@pytest.mark.parametrize("fl,u", [("rusanov", 0.3), ("rusanov", -0.3), ("rusanov", 2.0), ("hll", 0.3),
+                                  ("hll", -0.7), ("hll", 2.0), ("hll", -2.0), ("hllc", 0.3), ("hllc", -0.7)])
+def test_entropy_wave_numerical_viscosity_von_neumann(fl, u, nd):
+    """Von Neumann analysis of the first-order scheme on a linearised entropy wave (u, p uniform,
+    rho = 1 + eps cos): every flux here becomes F_{j+1/2} = u (rho_j + rho_{j+1})/2
+    - q (rho_{j+1} - rho_j)/2, so a Fourier mode e^{i theta j} is multiplied per step by the RK
+    polynomial of z = -lambda (i u sin(theta) + q (1 - cos(theta))). The numerical viscosity q
+    follows from each flux's wave speeds (Davis estimates, reading O7):
+    * Rusanov: q = |u| + c (the largest signal speed);
+    * HLL with S_L = u - c, S_R = u + c: q = (u (S_R + S_L) - 2 S_L S_R) / (S_R - S_L) = c when
+      subsonic, and the upwind q = |u| when supersonic;
+    * HLLC: q = |u| (it resolves the contact exactly).
+    A factor on the Rusanov dissipation, a sign error in HLL's S_L S_R term or a wrong wave speed
+    changes q and the decay of the mode by far more than the eps-sized nonlinearity."""
+    rk = "ssprk2"
+    G, lam, th, c = _entropy_wave_viscosity_run(fl, nd, u, rk)
+    q = {"rusanov": abs(u) + c, "hll": c if abs(u) < c else abs(u), "hllc": abs(u)}[fl]
+    steps = 40
+    z = -lam * (1j * u * math.sin(th) + q * (1 - math.cos(th)))
+    Gp = (1 + z + z * z / 2) ** steps
+    assert abs(G - Gp) <= 1e-5 * abs(Gp), (G, Gp)
+    # the viscosity is resolved: a 10 % change of q moves the decay well beyond the tolerance
+    z2 = -lam * (1j * u * math.sin(th) + 1.1 * q * (1 - math.cos(th)))
+    assert abs((1 + z2 + z2 * z2 / 2) ** steps - Gp) > 1e-3 * abs(Gp)
+
+
+def test_entropy_wave_viscosity_ssprk3_polynomial():
+    """The same analysis through the three-stage SSP-RK3 (stability polynomial 1 + z + z^2/2 + z^3/6
+    for a linear operator) with the Rusanov viscosity."""
+    G, lam, th, c = _entropy_wave_viscosity_run("rusanov", 1, 0.5, "ssprk3")
+    z = -lam * (1j * 0.5 * math.sin(th) + (0.5 + c) * (1 - math.cos(th)))
+    Gp = (1 + z + z * z / 2 + z ** 3 / 6) ** 40
+    assert abs(G - Gp) <= 1e-5 * abs(Gp), (G, Gp)
+
+
 # ---------------------------------------------------------------- reconstruction (Sec. 2.1)
 @pytest.mark.parametrize("kind", ["pc", "mc", "weno3"])
 def test_recon_linear_data(kind):
@@ -217,12 +309,14 @@ def test_exact_riemann_rankine_hugoniot_lax():
 
 
 # ---------------------------------------------------------------- full scheme, 1D Euler
-@pytest.mark.parametrize("recon,min_rate", [("pc", 0.45), ("mc", 0.6), ("weno3", 0.6)])
-def test_sod_converges_to_exact(recon, min_rate):
+@pytest.mark.parametrize("recon,min_rate,fl", [("pc", 0.45, "hllc"), ("mc", 0.6, "hllc"), ("weno3", 0.6, "hllc"),
+                                               ("pc", 0.45, "rusanov"), ("mc", 0.6, "rusanov"),
+                                               ("pc", 0.45, "hll"), ("mc", 0.6, "hll")])
+def test_sod_converges_to_exact(recon, min_rate, fl):
     R = RiemannExact((1.0, 0.0, 1.0), (0.125, 0.0, 0.1))
     ns, errs = [128, 256, 512, 1024], []
     for n in ns:
-        d = oracle.make_desc(ndim=1, n=(n,), eq="euler", recon=recon, flux="hllc", rk="ssprk2",
+        d = oracle.make_desc(ndim=1, n=(n,), eq="euler", recon=recon, flux=fl, rk="ssprk2",
                              bc="outflow", cfl=0.45)
         U, _, t = oracle.evolve(d, oracle.init(d, "sod"), T=0.2)
         assert t[0] == 0.2
@@ -231,14 +325,15 @@ def test_sod_converges_to_exact(recon, min_rate):
     rate = math.log(errs[0] / errs[-1]) / math.log(ns[-1] / ns[0])
     assert rate >= min_rate, (errs, rate)
     if recon == "mc":
-        assert errs[-1] < 1e-3
+        assert errs[-1] < {"hllc": 1e-3, "hll": 1.5e-3, "rusanov": 2e-3}[fl]
 
 
-def test_lax_converges_to_exact():
+@pytest.mark.parametrize("fl", ["hllc", "hll", "rusanov"])
+def test_lax_converges_to_exact(fl):
     R = RiemannExact((0.445, 0.698, 3.528), (0.5, 0.0, 0.571))
     ns, errs = [128, 256, 512], []
     for n in ns:
-        d = oracle.make_desc(ndim=1, n=(n,), eq="euler", recon="mc", flux="hllc", rk="ssprk2",
+        d = oracle.make_desc(ndim=1, n=(n,), eq="euler", recon="mc", flux=fl, rk="ssprk2",
                              bc="outflow", cfl=0.45)
         U, _, _ = oracle.evolve(d, oracle.init(d, "lax"), T=0.13)
         errs.append(np.abs(U[0, 0, 0, 0] - R.cell_average_density(n, 0.13)).mean())
@@ -336,11 +431,11 @@ def test_burgers_init_exact_cell_averages():
 
 
 # ---------------------------------------------------------------- 2D smooth vortex
-def vortex_errors(recon, rk, rvars, ns, eps2, T=1.0):
+def vortex_errors(recon, rk, rvars, ns, eps2, T=1.0, fl="hllc"):
     errs = []
     for n in ns:
         d = oracle.make_desc(ndim=2, n=(n, n), lo=(0, 0), hi=(10, 10), eq="euler", recon=recon, rvars=rvars,
-                             flux="hllc", rk=rk, bc="periodic", cfl=0.4, weno_eps_dx2=eps2)
+                             flux=fl, rk=rk, bc="periodic", cfl=0.4, weno_eps_dx2=eps2)
         U, _, _ = oracle.evolve(d, oracle.init(d, "vortex", center=(5, 5)), T=T)
         E = oracle.init(d, "vortex", center=(5 + T, 5 + T))
         errs.append(np.abs(U[0, 0] - E[0, 0]).mean())
@@ -362,8 +457,10 @@ def test_vortex_init_quadrature_vs_scipy():
         assert U[0, 0, 0, j, i] == pytest.approx(ref / 0.25, rel=1e-9)
 
 
-def test_vortex_mc_second_order():
-    rates = observed_rates([32, 64, 128], vortex_errors("mc", "ssprk2", "prim", [32, 64, 128], False))
+@pytest.mark.parametrize("fl", ["hllc", "rusanov"])
+def test_vortex_mc_second_order(fl):
+    # MC + Rusanov + SSP-RK2 is the adjoint configuration's scheme
+    rates = observed_rates([32, 64, 128], vortex_errors("mc", "ssprk2", "prim", [32, 64, 128], False, fl=fl))
     assert np.all(rates >= 1.8), rates
 
 
@@ -568,6 +665,25 @@ def test_welford_integer_data_exact():
     cnt, mean, M2 = oracle.welford(d, U)
     assert np.all(mean == (B - 1) / 2)
     assert np.all(M2 / (B - 1) == B * (B + 1) / 12)
+
+
+# ---------------------------------------------------------------- kinetic energy (reading O16)
+def test_kinetic_energy_closed_forms():
+    """KE = sum_i |m_i|^2 / (2 rho_i) dV. (i) The unperturbed KH data on 8 rows puts both interfaces
+    on cell faces (y = 2/8, 6/8), so the band (area 1/2, rho 2, u -1/2) carries 1/2 * 2 * 1/4 * 1/2
+    = 1/8 and the rest (rho 1, u 1/2) 1/2 * 1 * 1/4 * 1/2 = 1/16: KE = 3/16 exactly. (ii) Uniform
+    states with every velocity component nonzero: KE = rho |u|^2 / 2 times the domain's volume."""
+    d = oracle.make_desc(ndim=2, n=(4, 8), eq="euler")
+    U = oracle.init(d, "kh", theta=np.zeros((1, 20)))
+    assert oracle.kinetic_energy(d, U)[0] == 0.1875
+    for nd, vel, vol in ((1, [0.7], 2.0), (2, [0.3, 0.4], 2.0), (3, [0.3, 0.4, 1.2], 2.0)):
+        d = oracle.make_desc(ndim=nd, n=(5, 4, 3), hi=(2.0, 1.0, 1.0), eq="euler")
+        W = np.concatenate([[2.0], vel, [0.9]])
+        Uc = oracle.prim_to_cons(d, W)
+        U = np.zeros(oracle.state_shape(d, 1))
+        for v in range(nd + 2):
+            U[0, v] = Uc[v]
+        assert oracle.kinetic_energy(d, U)[0] == pytest.approx(0.5 * 2.0 * np.dot(vel, vel) * vol, rel=1e-14)
 
 
 # ---------------------------------------------------------------- exact discrete gradient

@@ -247,18 +247,21 @@ alsv_status alsv_conservation_totals(alsv_ctx* ctx, double* totals_dev);
  * synchronise the device). It needs no context and no workspace: the kernels' per-chunk partial
  * sums live in a static device array of 2^20 doubles (8 MiB) that every GPU loading this library
  * holds until the process exits. The paper has no counterpart; it is an execution variant.
- *   d            descriptor of the state (only ndim, n / level table, lo, hi, batch, eq and
- *                precision are read)
+ *   d            descriptor of the state (only ndim, n / level table, lo, hi, batch, eq,
+ *                precision and, for a block of a decomposed grid, global_n and offset are read;
+ *                they are checked by alsv_init_grid's rules)
  *   U_dev        device state, layout as above, U_bytes >= the descriptor's state size
  *   totals_dev   device FP64 [samples][vars], written
  *   stream       cudaStream_t as void*
- * Calls no cudaMalloc / cudaFree or allocating library routine. The first call on a device looks
- * up the array's device address with cudaGetSymbolAddress (with that device current) and caches
- * it; make that first call before any stream capture. All calls share the array: calls that
- * overlap on the GPU (other streams, other threads) race. Every partial slot is written before it
- * is read, so no clearing is needed. Errors: INVALID_ARG (bad descriptor, or samples x vars x
- * ceil(cells / 4096) above 2^20: the message says so), BUFFER_TOO_SMALL, CUDA; the message is read
- * with alsv_last_error(NULL). Asynchronous.
+ * Calls no cudaMalloc / cudaFree or allocating library routine. Every call looks up the array's
+ * device address with cudaGetSymbolAddress (with the calling device current), so a device reset
+ * between calls leaves no stale address; the first call on a device also loads the library's
+ * device code there, so make that first call before any stream capture. All calls share the
+ * array: calls that overlap on the GPU (other streams, other threads) race. Every partial slot is
+ * written before it is read, so no clearing is needed. Errors: INVALID_ARG (bad descriptor, a
+ * sample of more than 65535 x 4096 cells, or samples x vars x ceil(cells / 4096) above 2^20: the
+ * message says so), BUFFER_TOO_SMALL, CUDA; the message is read with alsv_last_error(NULL).
+ * Asynchronous.
  */
 alsv_status alsv_conservation_totals_noalloc(const alsv_grid_desc* d, const void* U_dev, size_t U_bytes,
                                              double* totals_dev, void* stream);
@@ -415,6 +418,11 @@ alsv_status alsv_structure_function_read(alsv_ctx* ctx, const void* acc_dev, int
  *                      the block, from the partials of the last stage (or of set_initial_data /
  *                      set_time), +infinity for a sample with a non-finite partial. Allowed before
  *                      the first stage of a step or after the last. Asynchronous.
+ *   alsv_speed_max_combine  out_dev[s] = the maximum over i < n of smax_dev[i][s] for s <
+ *                      samples (device FP64 vectors; smax_dev is a HOST array of n <= 64 device
+ *                      pointers), NaN-propagating: the "MAX over blocks" of the protocol above for
+ *                      blocks on one GPU. Needs no context (the blocks are separate contexts);
+ *                      errors go to alsv_last_error(NULL). Asynchronous on stream.
  *   alsv_finish_step   time control from an external maximum (the MAX of every block's
  *                      smax; +infinity or NaN marks the sample non-physical): advance = 1 after
  *                      the last stage (t += dt, step count, done flags, next dt), 0 to only
@@ -430,6 +438,7 @@ alsv_status alsv_bind_halo(alsv_ctx* ctx, const void* const* halo_dev, const siz
 alsv_status alsv_halo_pack(alsv_ctx* ctx, int stage, void* const* send_dev, const size_t* bytes);
 alsv_status alsv_stage(alsv_ctx* ctx, int stage);
 alsv_status alsv_speed_max(alsv_ctx* ctx, double* smax_dev);
+alsv_status alsv_speed_max_combine(const double* const* smax_dev, int n, int samples, double* out_dev, void* stream);
 alsv_status alsv_finish_step(alsv_ctx* ctx, const double* smax_dev, int advance);
 alsv_status alsv_set_end_time(alsv_ctx* ctx, double T);
 

@@ -108,6 +108,7 @@ SIGNATURES = {
     "alsv_halo_pack": (C.c_int, [_ctx, C.c_int, C.POINTER(_vp), C.POINTER(_sz)]),
     "alsv_stage": (C.c_int, [_ctx, C.c_int]),
     "alsv_speed_max": (C.c_int, [_ctx, _vp]),
+    "alsv_speed_max_combine": (C.c_int, [C.POINTER(_vp), C.c_int, C.c_int, _vp, _vp]),
     "alsv_finish_step": (C.c_int, [_ctx, _vp, C.c_int]),
     "alsv_set_end_time": (C.c_int, [_ctx, C.c_double]),
 }
@@ -392,6 +393,16 @@ def alsv_stage(ctx, stage: int):
 
 def alsv_speed_max(ctx, smax):
     _check(load().alsv_speed_max(ctx, _ptr(smax)), "alsv_speed_max", ctx)
+
+
+def alsv_speed_max_combine(smax_list, out, stream: int = 0):
+    """out[s] = max over the blocks' device FP64 vectors smax_list[i][s] (NaN-propagating), on
+    stream; see include/alsv.h."""
+    n = len(smax_list)
+    arr = (_vp * max(n, 1))(*[_ptr(x) for x in smax_list])
+    samples = int(out.numel()) if hasattr(out, "numel") else 0
+    _check(load().alsv_speed_max_combine(arr, n, samples, _ptr(out), C.c_void_p(stream or None)),
+           "alsv_speed_max_combine", None)
 
 
 def alsv_finish_step(ctx, smax, advance: bool):

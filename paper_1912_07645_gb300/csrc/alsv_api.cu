@@ -1089,6 +1089,26 @@ alsv_status alsv_speed_max(alsv_ctx* c, double* smax_dev) {
     return ALSV_OK;
 }
 
+alsv_status alsv_speed_max_combine(const double* const* smax_dev, int n, int samples, double* out_dev, void* stream) {
+    auto bad = [](alsv_status st, const std::string& m) {
+        set_global_error("alsv_speed_max_combine: " + m);
+        return st;
+    };
+    if (!smax_dev || !out_dev) return bad(ALSV_ERR_INVALID_ARG, "null input array or output");
+    if (n < 1 || n > kSpeedCombineMax)
+        return bad(ALSV_ERR_INVALID_ARG, "n must be 1 .. " + std::to_string(kSpeedCombineMax));
+    if (samples < 0) return bad(ALSV_ERR_INVALID_ARG, "samples must be >= 0");
+    SpeedCombineArgs a{};
+    a.n = n;
+    for (int i = 0; i < n; ++i) {
+        if (!smax_dev[i]) return bad(ALSV_ERR_INVALID_ARG, "null input " + std::to_string(i));
+        a.in[i] = smax_dev[i];
+    }
+    const cudaError_t e = launch_speed_max_combine(a, samples, out_dev, (cudaStream_t)stream);
+    if (e != cudaSuccess) return bad(ALSV_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+    return ALSV_OK;
+}
+
 alsv_status alsv_finish_step(alsv_ctx* c, const double* smax_dev, int advance) {
     alsv_status st = require_ready(c);
     if (st != ALSV_OK) return st;

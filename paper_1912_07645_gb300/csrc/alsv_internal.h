@@ -134,6 +134,12 @@ struct InitArgs {
 cudaError_t launch_init(int fp64, int ndim, const InitArgs& a, cudaStream_t s);
 // Boundary layers of a block for its neighbours' halos: for each face f with dst[f] != NULL,
 // dst[f][b][v][l][cross] = U[b][v][...] at index l (low face) or n_k - G + l (high face) along k.
+constexpr int kSpeedCombineMax = 64;   // blocks per alsv_speed_max_combine call
+struct SpeedCombineArgs {
+    const double* in[kSpeedCombineMax];
+    int n;
+};
+cudaError_t launch_speed_max_combine(const SpeedCombineArgs& a, int samples, double* out, cudaStream_t s);
 cudaError_t launch_halo_pack(int fp64, const GridArgs& g, int G, const void* U, void* const dst[6], cudaStream_t s);
 // Counter index of each sample's KH parameters: sample s of group l uses src0[l] + (s - sample0[l])
 // (an MLMC companion group takes its level's indices, every other group its own).

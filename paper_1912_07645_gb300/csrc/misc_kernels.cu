@@ -381,6 +381,27 @@ __global__ void k_halo_pack(const GridArgs g, int G, int face, int rows, const R
     }
 }
 
+// Maximum wave speed over the blocks of a decomposed grid, per sample (step a8 across blocks): the
+// elementwise maximum of n per-block vectors, NaN-propagating (a NaN or +infinity in any block
+// marks the sample non-physical for alsv_finish_step). The maximum is exact, so the order of the
+// blocks does not matter; it is the blocks' order anyway.
+__global__ void k_speed_max_combine(const SpeedCombineArgs a, int samples, double* out) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= samples) return;
+    double m = a.in[0][s];
+    for (int i = 1; i < a.n; ++i) {
+        const double v = a.in[i][s];
+        if (v != v || v > m) m = v;   // once m is NaN, neither test replaces it
+    }
+    out[s] = m;
+}
+
+cudaError_t launch_speed_max_combine(const SpeedCombineArgs& a, int samples, double* out, cudaStream_t s) {
+    if (samples <= 0) return cudaSuccess;
+    k_speed_max_combine<<<(unsigned)((samples + 255) / 256), 256, 0, s>>>(a, samples, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_halo_pack(int fp64, const GridArgs& g, int G, const void* U, void* const dst[6], cudaStream_t s) {
     const LevelInfo& L = g.lev[0];
     for (int f = 0; f < 6; ++f) {

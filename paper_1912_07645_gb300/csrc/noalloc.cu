@@ -10,7 +10,6 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
-#include <mutex>
 #include <string>
 
 #include "../../include/alsv.h"
@@ -27,10 +26,6 @@ namespace {
 constexpr long long kNoallocPartials = 1LL << 20;
 static __device__ __align__(256) double g_noalloc_partials[kNoallocPartials];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-double* g_ptr[kMaxDevices] = {};
-
 alsv_status bad(alsv_status st, const std::string& m) {
     alsv::set_global_error("alsv_conservation_totals_noalloc: " + m);
     return st;
@@ -46,6 +41,19 @@ extern "C" alsv_status alsv_conservation_totals_noalloc(const alsv_grid_desc* d,
     if (d->eq != ALSV_EQ_BURGERS && d->eq != ALSV_EQ_EULER) return bad(ALSV_ERR_INVALID_ARG, "eq must be BURGERS or EULER");
     if (d->precision != ALSV_FP32 && d->precision != ALSV_FP64) return bad(ALSV_ERR_INVALID_ARG, "precision must be FP32 or FP64");
     if (d->n_levels > ALSV_MAX_LEVELS) return bad(ALSV_ERR_INVALID_ARG, "n_levels must be <= 8");
+    // a block of a decomposed grid: the same rules as alsv_init_grid
+    bool block = false;
+    for (int k = 0; k < 3; ++k) {
+        if (d->global_n[k] != 0 || d->offset[k] != 0) block = true;
+        if (k >= d->ndim && (d->global_n[k] > 1 || d->offset[k] != 0))
+            return bad(ALSV_ERR_INVALID_ARG, "global_n / offset of an inactive direction must be 0");
+        if (k < d->ndim && d->global_n[k] == 0 && d->offset[k] != 0)
+            return bad(ALSV_ERR_INVALID_ARG, "offset needs global_n");
+        if (k < d->ndim && d->global_n[k] != 0 &&
+            (d->offset[k] < 0 || (long long)d->offset[k] + d->n[k] > d->global_n[k]))
+            return bad(ALSV_ERR_INVALID_ARG, "a block must lie inside the whole grid: 0 <= offset and offset + n <= global_n");
+    }
+    if (block && d->n_levels > 1) return bad(ALSV_ERR_INVALID_ARG, "a decomposed grid needs a single grid (n_levels <= 1)");
     GridArgs g{};
     g.ndim = d->ndim;
     for (int k = 0; k < 3; ++k) g.lo[k] = d->lo[k];
@@ -62,7 +70,7 @@ extern "C" alsv_status alsv_conservation_totals_noalloc(const alsv_grid_desc* d,
             if (L.n[k] < 1) return bad(ALSV_ERR_INVALID_ARG, "every active direction needs n >= 1");
             if (k < d->ndim && !(d->hi[k] > d->lo[k])) return bad(ALSV_ERR_INVALID_ARG, "hi must exceed lo");
             // a block of a decomposed grid has the whole grid's dx
-            const int ng = k < d->ndim && d->n_levels <= 1 && d->global_n[k] > 0 ? d->global_n[k] : L.n[k];
+            const int ng = k < d->ndim && d->global_n[k] > 0 ? d->global_n[k] : L.n[k];
             L.dx[k] = k < d->ndim ? (d->hi[k] - d->lo[k]) / ng : 1.0;
             L.inv_dx[k] = 1.0 / L.dx[k];
         }
@@ -73,6 +81,14 @@ extern "C" alsv_status alsv_conservation_totals_noalloc(const alsv_grid_desc* d,
     }
     if (samples > 65535) return bad(ALSV_ERR_INVALID_ARG, "at most 65535 samples");
     g.total_samples = (int)samples;
+    long long maxchunks = 0;
+    for (int l = 0; l < g.nlev; ++l) {
+        const long long c = ((long long)g.lev[l].n[0] * g.lev[l].n[1] * g.lev[l].n[2] + 4095) / 4096;
+        maxchunks = c > maxchunks ? c : maxchunks;
+    }
+    if (maxchunks > 65535)
+        return bad(ALSV_ERR_INVALID_ARG, "a sample of " + std::to_string(maxchunks) +
+                                             " chunks of 4096 cells exceeds the reduction's 65535 chunks per sample");
     const long long parts = reduce_partial_count(g);
     if (parts > kNoallocPartials)
         return bad(ALSV_ERR_INVALID_ARG, "samples x variables x ceil(cells/4096) = " + std::to_string(parts) +
@@ -80,24 +96,15 @@ extern "C" alsv_status alsv_conservation_totals_noalloc(const alsv_grid_desc* d,
                                              " partial sums");
     const size_t need = (size_t)elems * (d->precision == ALSV_FP64 ? 8 : 4);
     if (U_bytes < need) return bad(ALSV_ERR_BUFFER_TOO_SMALL, "state buffer smaller than the descriptor's state");
-    // Set-up, once per device with that device current: the device address of the scratch array.
-    // (In host code the array's name is only a host-side stand-in, not a device address.)
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return bad(ALSV_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-    if (dev < 0 || dev >= kMaxDevices) return bad(ALSV_ERR_INVALID_ARG, "device ordinal out of range");
-    double* scratch = nullptr;
-    {
-        std::lock_guard<std::mutex> lk(g_mu);
-        if (!g_ptr[dev]) {
-            void* p = nullptr;
-            e = cudaGetSymbolAddress(&p, g_noalloc_partials);
-            if (e != cudaSuccess)
-                return bad(ALSV_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-            g_ptr[dev] = static_cast<double*>(p);
-        }
-        scratch = g_ptr[dev];
-    }
+    // Set-up, with the calling device current: the device address of the scratch array. (In host
+    // code the array's name is only a host-side stand-in, not a device address.) It is looked up on
+    // every call, which allocates nothing, so a device reset between calls (which reloads the module
+    // at another address) cannot leave a stale address behind. The first call on a device loads the
+    // module there.
+    void* sym = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&sym, g_noalloc_partials);
+    if (e != cudaSuccess) return bad(ALSV_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    double* scratch = static_cast<double*>(sym);
     // The reduction writes every partial slot before reading it, so nothing needs clearing.
     e = launch_reduce(d->precision == ALSV_FP64, 0, g, U_dev, scratch, totals_dev, (cudaStream_t)stream);
     if (e != cudaSuccess) return bad(ALSV_ERR_CUDA, std::string("reduction launch: ") + cudaGetErrorString(e));

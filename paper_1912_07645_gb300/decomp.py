@@ -32,6 +32,8 @@ from __future__ import annotations
 import contextlib
 import math
 
+from . import _abi as A
+
 
 def split(n: int, parts: int):
     """Contiguous ranges (offset, count) of ``parts`` blocks over ``n`` cells, sizes within one."""
@@ -178,10 +180,7 @@ class LocalExchange:
             with _on(self.blocks[0]):
                 return torch.stack(smax).amax(0)
         self.join()
-        with torch.cuda.stream(self.main):
-            self.gmax.copy_(smax[0])
-            for m in smax[1:]:
-                torch.maximum(self.gmax, m, out=self.gmax)
+        A.alsv_speed_max_combine(smax, self.gmax, self.main.cuda_stream)
         self.ev_max.record(self.main)
         for b in self.blocks:
             self.ev_max.wait(b.stream)

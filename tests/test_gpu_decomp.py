@@ -171,3 +171,26 @@ def test_protocol_errors_are_reported():
     ch, ms = alsv.alsv_autotune(s.ctx, 1)
     assert len(ms) == 8 and ch in (0, 1, 2) and all(m > 0 for m in ms[:3]) and all(m < 0 for m in ms[3:])
     s.close()
+
+
+def test_speed_max_combine_is_the_nan_propagating_maximum():
+    """The cross-block CFL maximum runs in the library: per sample the largest value over the
+    blocks, with a NaN or +infinity in any block (a non-physical sample) kept."""
+    import torch
+    import paper_1912_07645_gb300 as alsv
+    rng = np.random.default_rng(8)
+    n_blocks, samples = 5, 1000
+    vals = rng.uniform(0.0, 10.0, (n_blocks, samples))
+    vals[2, 7] = np.nan
+    vals[0, 9] = np.nan            # NaN in the first input too
+    vals[4, 11] = np.inf
+    ins = [torch.tensor(v, dtype=torch.float64, device="cuda") for v in vals]
+    out = torch.full((samples,), -1.0, dtype=torch.float64, device="cuda")
+    alsv.alsv_speed_max_combine(ins, out)
+    o = host(out)
+    ref = vals.max(axis=0)          # numpy's max propagates NaN
+    assert np.array_equal(np.isnan(o), np.isnan(ref))
+    ok = ~np.isnan(ref)
+    assert np.array_equal(o[ok], ref[ok]) and o[11] == np.inf
+    with pytest.raises(alsv.AlsvError, match="n must be"):
+        alsv.alsv_speed_max_combine(ins * 13, out)   # 65 inputs

@@ -1,7 +1,8 @@
 """GPU (libalsv.so through the C ABI) vs the FP64 CPU oracle, element by element.
 
-FP64: per cell within 1e-12 relative (floor: 1e-12 * max |U_v|), FMA contraction and
-reciprocal-multiplication being the only differences. FP32: within 2e-5 relative L1. Sizes are
+FP64: per cell within 1e-12 relative (cells whose value is below 1e-3 of the variable's largest
+magnitude are measured against that magnitude), FMA contraction and reciprocal-multiplication
+being the only differences. FP32: within 2e-5 relative L1. Sizes are
 small enough for the oracle but span several tiles and ragged tails; the full-size batched
 configuration is checked on sampled outputs.
 """
@@ -512,16 +513,18 @@ def test_welford_statistics_match_oracle(precision):
 
 
 # ------------------------------------------------------------------ full-size batched configuration, sampled
-def test_full_size_batched_kh_sampled():
-    """256^2 x 4096 samples, FP32 WENO3 + HLLC + SSP-RK3 (the benchmark workload, launched as the
-    benchmark launches it); three sampled samples against the oracle after two CFL steps."""
+@pytest.mark.parametrize("variant", [4])
+def test_full_size_batched_kh_sampled(variant):
+    """256^2 x 4096 samples, FP32 WENO3 + HLLC + SSP-RK3 (the benchmark workload), in the launch
+    geometry of each two-sample schedule the autotuner picks from for it; three sampled samples
+    against the oracle after two CFL steps."""
     torch = torch_()
     import paper_1912_07645_gb300 as alsv
     cfg = dict(ndim=2, n=(256, 256), batch=4096, eq="euler", recon="weno3", flux="hllc", rvars="prim", rk="ssprk3",
                bc="periodic", cfl=0.4, precision="fp32", seed=12345)
     S = gpu_solver(**cfg)
     S.set_initial_data("kh")
-    alsv.alsv_autotune(S.ctx, 2)
+    alsv.alsv_set_tile_variant(S.ctx, variant)
     S.step(2)
     S.sync()
     V = S.state()

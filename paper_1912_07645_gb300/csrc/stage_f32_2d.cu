@@ -35,7 +35,10 @@ static cudaError_t launch_pair(int recon, int flux, int eq, const StageArgs& a, 
     return cudaErrorNotSupported;
 }
 
+cudaError_t launch_stage_f32_2d_lean(int variant, int eq, int recon, int flux, const StageArgs& a, cudaStream_t s);
+
 cudaError_t launch_stage_f32_2d(int variant, int eq, int recon, int flux, const StageArgs& a, cudaStream_t s) {
+    if (variant >= 8) return launch_stage_f32_2d_lean(variant, eq, recon, flux, a, s);
     switch (variant) {
         case 0: return launch_stage_tile<float, 2, 32, 16, 1, 256>(eq, recon, flux, a, s);
         case 1: return launch_stage_tile<float, 2, 32, 8, 1, 256>(eq, recon, flux, a, s);
@@ -74,6 +77,8 @@ cudaError_t launch_speed_f32_2d(int variant, int eq, const GridArgs& g, const vo
         case 5: return launch_speed_tile<float, 2, 32, 8, 1, 256>(eq, g, U, part, s);
         case 6: return launch_speed_tile<float, 2, 32, 16, 1, 256>(eq, g, U, part, s);
         case 7: return launch_speed_tile<float, 2, 32, 8, 1, 256>(eq, g, U, part, s);
+        case 8: case 10: return launch_speed_tile<float, 2, 32, 16, 1, 256>(eq, g, U, part, s);
+        case 9: case 11: return launch_speed_tile<float, 2, 32, 32, 1, 256>(eq, g, U, part, s);
         default: return cudaErrorInvalidValue;
     }
 }

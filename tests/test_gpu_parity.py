@@ -513,7 +513,7 @@ def test_welford_statistics_match_oracle(precision):
 
 
 # ------------------------------------------------------------------ full-size batched configuration, sampled
-@pytest.mark.parametrize("variant", [4])
+@pytest.mark.parametrize("variant", [4, 8, 9])
 def test_full_size_batched_kh_sampled(variant):
     """256^2 x 4096 samples, FP32 WENO3 + HLLC + SSP-RK3 (the benchmark workload), in the launch
     geometry of each two-sample schedule the autotuner picks from for it; three sampled samples
@@ -673,13 +673,14 @@ def test_column_variant_mlmc_levels_and_rejection():
     S2.close()
 
 
-@pytest.mark.parametrize("variant", [4, 5])
+@pytest.mark.parametrize("variant", [4, 5, 8, 9])
 @pytest.mark.parametrize("recon,flux,bc", [("weno3", "hllc", "periodic"), ("mc", "rusanov", "periodic"),
                                            ("pc", "hllc", [("outflow", "reflective"), ("reflective", "outflow")]),
                                            ("weno3", "rusanov", "reflective")])
 def test_pair_variant_fp32_vs_oracle(variant, recon, flux, bc):
-    """Two-sample schedules (variants 4, 5): each sample within 2e-5 relative L1 of the oracle,
-    with an odd batch (the last sample has no partner), ragged tiles and boundary fill."""
+    """Two-sample schedules (variants 4, 5 and the lean 8, 9): each sample within 2e-5 relative L1
+    of the oracle, with an odd batch (the last sample has no partner), ragged tiles and boundary
+    fill."""
     torch = torch_()
     import paper_1912_07645_gb300 as alsv
     cfg = dict(ndim=2, n=(70, 45), batch=3, eq="euler", recon=recon, flux=flux, rvars="prim", rk="ssprk3", bc=bc,
@@ -725,23 +726,57 @@ def test_halves_variant_fp32_vs_oracle_and_bitwise_with_sample_pairs(recon, flux
         p2_check(out[6][0][b:b + 1], o[b:b + 1], what=f"halves {recon} {flux} sample {b}")
 
 
+@pytest.mark.parametrize("recon,flux,bcx", [("weno3", "hllc", "periodic"), ("mc", "rusanov", "outflow"),
+                                            ("pc", "hllc", "reflective"), ("weno3", "rusanov", "reflective")])
+def test_lean_pair_variants_bitwise_equal_and_vs_oracle(recon, flux, bcx):
+    """The lean two-sample schedules evaluate every interface with the same operations whatever
+    the tile height or the pairing: 32x16 and 32x32 tiles over sample pairs (8, 9) and over the two
+    halves of each sample (10, 11) are bitwise equal (ragged x: 70 cells, ny = 64, odd batch), and
+    within 2e-5 relative L1 of the oracle."""
+    torch = torch_()
+    import paper_1912_07645_gb300 as alsv
+    bc = [(bcx, bcx), ("periodic", "periodic")]
+    cfg = dict(ndim=2, n=(70, 64), batch=3, eq="euler", recon=recon, flux=flux, rvars="prim", rk="ssprk3", bc=bc,
+               cfl=0.4, precision="fp32")
+    U0 = euler_state(3, 2, (70, 64), seed=74)
+    out = {}
+    for v in (8, 9, 10, 11):
+        S = gpu_solver(**cfg)
+        alsv.alsv_set_tile_variant(S.ctx, v)
+        S.set_state(torch.from_numpy(U0))
+        S.step(10)
+        S.sync()
+        out[v] = (host(S.U).reshape(S.level_shape(0)), S.time())
+        S.close()
+    for v in (9, 10, 11):
+        assert np.array_equal(out[8][0], out[v][0]), v
+        np.testing.assert_array_equal(out[8][1][0], out[v][1][0])
+    o, *_ = run_oracle(cfg, U0=U0, steps=10)
+    for b in range(3):
+        p2_check(out[8][0][b:b + 1], o[b:b + 1], what=f"lean {recon} {flux} sample {b}")
+
+
 def test_halves_variant_needs_aligned_periodic_y():
     torch_()
     import paper_1912_07645_gb300 as alsv
     for n, bc in (((64, 40), "periodic"), ((64, 64), [("periodic", "periodic"), ("outflow", "outflow")])):
         S = gpu_solver(ndim=2, n=n, batch=1, eq="euler", recon="weno3", flux="hllc", rvars="prim", precision="fp32",
                        bc=bc)
-        for v in (6, 7):
+        for v in (6, 7, 10, 11):
             with pytest.raises(alsv.AlsvError, match="does not support"):
                 alsv.alsv_set_tile_variant(S.ctx, v)
         S.close()
     S = gpu_solver(ndim=2, n=(64, 48), batch=1, eq="euler", recon="weno3", flux="hllc", rvars="prim",
                    precision="fp32", bc="periodic")
     alsv.alsv_set_tile_variant(S.ctx, 7)      # 48 = 3 x 16: 32x8 halves align
+    for v in (10, 11):                        # 32x16 / 32x32 halves need ny divisible by 32 / 64
+        with pytest.raises(alsv.AlsvError, match="does not support"):
+            alsv.alsv_set_tile_variant(S.ctx, v)
     S.close()
 
 
-def test_pair_variant_samples_finishing_at_different_steps():
+@pytest.mark.parametrize("variant", [4, 8])
+def test_pair_variant_samples_finishing_at_different_steps(variant):
     """Samples of one pair reach T after different step counts: the finished lane must stay
     untouched while its partner continues."""
     torch = torch_()
@@ -751,7 +786,7 @@ def test_pair_variant_samples_finishing_at_different_steps():
     U0 = euler_state(5, 2, (48, 40), seed=72)
     U0[1, 3] *= 1.6          # hotter sample: larger sound speed, more steps to the same T
     S = gpu_solver(**cfg)
-    alsv.alsv_set_tile_variant(S.ctx, 4)
+    alsv.alsv_set_tile_variant(S.ctx, variant)
     S.set_state(torch.from_numpy(U0))
     S.evolve_to(0.04)
     g = host(S.U).reshape(S.level_shape(0))
@@ -764,14 +799,15 @@ def test_pair_variant_samples_finishing_at_different_steps():
         p2_check(g[b:b + 1], o[b:b + 1], what=f"pair finish sample {b}")
 
 
-def test_pair_variant_mlmc_levels_odd_counts():
+@pytest.mark.parametrize("variant", [4, 8, 9])
+def test_pair_variant_mlmc_levels_odd_counts(variant):
     torch = torch_()
     import paper_1912_07645_gb300 as alsv
     lv = [((32, 32), 3), ((64, 48), 1), ((40, 40), 4)]
     cfg = dict(ndim=2, levels=lv, eq="euler", recon="weno3", flux="hllc", rvars="prim", rk="ssprk3",
                bc="periodic", cfl=0.4, precision="fp32", seed=9)
     S = gpu_solver(**cfg)
-    alsv.alsv_set_tile_variant(S.ctx, 4)
+    alsv.alsv_set_tile_variant(S.ctx, variant)
     S.set_initial_data("kh")
     S.step(3)
     S.sync()

@@ -27,9 +27,9 @@ _lock = threading.Lock()
 _lib = None
 
 EQ = {"burgers": 0, "euler": 1}
-RECON = {"pc": 0, "mc": 1, "weno3": 2}
+RECON = {"pc": 0, "mc": 1, "weno3": 2, "eno2": 3}
 RVARS = {"cons": 0, "prim": 1}
-FLUX = {"rusanov": 0, "hll": 1, "hllc": 2}
+FLUX = {"rusanov": 0, "hll": 1, "hllc": 2, "roe": 3, "godunov": 4, "ec": 5, "ec4": 6}
 RK = {"ssprk2": 2, "ssprk3": 3}
 BC = {"periodic": 0, "outflow": 1, "reflective": 2}
 INIT = {"kh": 0, "sod": 1, "lax": 2, "burgers_sine": 3, "vortex": 4}

@@ -41,9 +41,9 @@ namespace orc {
 // Enumerations (values are part of the oracle's own ctypes interface)
 // ------------------------------------------------------------------------------------------
 enum { EQ_BURGERS = 0, EQ_EULER = 1 };
-enum { REC_PC = 0, REC_MC = 1, REC_WENO3 = 2 };
+enum { REC_PC = 0, REC_MC = 1, REC_WENO3 = 2, REC_ENO2 = 3 };
 enum { RV_CONS = 0, RV_PRIM = 1 };
-enum { FLUX_RUSANOV = 0, FLUX_HLL = 1, FLUX_HLLC = 2 };
+enum { FLUX_RUSANOV = 0, FLUX_HLL = 1, FLUX_HLLC = 2, FLUX_ROE = 3, FLUX_GODUNOV = 4, FLUX_EC = 5, FLUX_EC4 = 6 };
 enum { RK_SSP2 = 2, RK_SSP3 = 3 };
 enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_REFLECTIVE = 2 };
 enum { INIT_KH = 0, INIT_SOD = 1, INIT_LAX = 2, INIT_BURGERS_SINE = 3, INIT_VORTEX = 4 };
@@ -143,6 +143,20 @@ inline double sqrt_(double x) { return std::sqrt(x); }
 template <int N> inline Dual<N> sqrt_(const Dual<N>& x) { return sqrt(x); }
 inline double sin_(double x) { return std::sin(x); }
 template <int N> inline Dual<N> sin_(const Dual<N>& x) { return sin(x); }
+inline double pow_(double x, double e) { return std::pow(x, e); }
+inline Cnt pow_(const Cnt& x, double e) { ++g_flops; return Cnt(std::pow(x.v, e)); }
+template <int N> inline Dual<N> pow_(const Dual<N>& x, double e) {
+    Dual<N> r; r.v = std::pow(x.v, e); double dv = e * std::pow(x.v, e - 1.0);
+    for (int i = 0; i < N; ++i) r.d[i] = dv * x.d[i];
+    return r;
+}
+inline double log_(double x) { return std::log(x); }
+inline Cnt log_(const Cnt& x) { ++g_flops; return Cnt(std::log(x.v)); }
+template <int N> inline Dual<N> log_(const Dual<N>& x) {
+    Dual<N> r; r.v = std::log(x.v);
+    for (int i = 0; i < N; ++i) r.d[i] = x.d[i] / x.v;
+    return r;
+}
 template <class T> inline T abs_(const T& x) { return val(x) < 0.0 ? T(-x) : x; }
 // ties pick the first argument
 template <class T> inline T max_(const T& a, const T& b) { return val(b) > val(a) ? b : a; }
@@ -238,6 +252,15 @@ inline void recon_scalar(int recon, double eps, const T& wm, const T& w0, const 
         T s = minmod3(T(2.0 * dm), T(0.5 * (dm + dp)), T(2.0 * dp));
         *fl = w0 - 0.5 * s;
         *fr = w0 + 0.5 * s;
+    } else if (recon == REC_ENO2) {
+        // second-order ENO (Harten-Engquist-Osher-Chakravarthy; Sec. 2.1 names ENO): of the two
+        // linear candidates through {i-1, i} and {i, i+1}, take the smoother one, i.e. the
+        // one-sided difference of smaller magnitude (ties take the backward difference)
+        T dm = w0 - wm;
+        T dp = wp - w0;
+        T s = val(abs_(dp)) < val(abs_(dm)) ? dp : dm;
+        *fl = w0 - 0.5 * s;
+        *fr = w0 + 0.5 * s;
     } else {
         // Jiang-Shu WENO3: candidates on {i-1,i} and {i,i+1}, linear weights 1/3, 2/3,
         // smoothness (differences)^2, alpha_r = d_r / (eps + beta_r)^2.
@@ -321,11 +344,218 @@ template <class T> inline void euler_phys_flux(const Desc& d, const T* W, int k,
     F[1 + nd] = un * (U[1 + nd] + p);
 }
 
+// Roe's flux (Roe 1981; Sec. 2.1 names it) for the Euler equations: F = (F_L + F_R)/2
+// - (1/2) sum_w |lambda_w| alpha_w r_w over the waves of the Roe-averaged Jacobian along k
+// (acoustic waves u_n -/+ a, the entropy wave and one shear wave per tangential direction, all at
+// u_n). Roe averages with weights sqrt(rho): u~, H~; a~^2 = (gamma-1)(H~ - |u~|^2/2), rho~ =
+// sqrt(rho_L rho_R). Wave strengths from the jumps: alpha_{1,3} = (dp -/+ rho~ a~ du_n)/(2 a~^2),
+// alpha_2 = drho - dp/a~^2, alpha_t = rho~ du_t. Entropy fix (reading; the paper names the flux
+// only): Harten's smoothing |lambda| -> (lambda^2 + delta^2)/(2 delta) when |lambda| < delta on the
+// two acoustic fields, with the Harten-Hyman width delta = max(0, lambda~ - lambda(W_L),
+// lambda(W_R) - lambda~) from the one-sided eigenvalues u_n -/+ c.
+template <class T> inline T harten_abs(const T& lam, const T& lamL, const T& lamR) {
+    T del = max_(T(0.0), max_(T(lam - lamL), T(lamR - lam)));
+    if (val(abs_(lam)) < val(del)) return (lam * lam + del * del) / (2.0 * del);
+    return abs_(lam);
+}
+template <class T> void roe_flux_euler(const Desc& d, int k, const T* WL, const T* WR, T* F) {
+    const int nd = d.ndim, nv = nd + 2, ip = nd + 1;
+    const double g = d.gamma;
+    T UL[8], UR[8], FL[8], FR[8];
+    prim_to_cons(d, WL, UL);
+    prim_to_cons(d, WR, UR);
+    euler_phys_flux(d, WL, k, FL);
+    euler_phys_flux(d, WR, k, FR);
+    T rL = WL[0], rR = WR[0], pL = WL[ip], pR = WR[ip];
+    T sL = sqrt_(rL), sR = sqrt_(rR);
+    T HL = (UL[ip] + pL) / rL, HR = (UR[ip] + pR) / rR;
+    T ut[8];
+    T q2 = T(0.0);
+    for (int j = 0; j < nd; ++j) {
+        ut[j] = (sL * WL[1 + j] + sR * WR[1 + j]) / (sL + sR);
+        q2 = q2 + ut[j] * ut[j];
+    }
+    T H = (sL * HL + sR * HR) / (sL + sR);
+    T a2 = (g - 1.0) * (H - 0.5 * q2);
+    T a = sqrt_(a2);
+    T rt = sL * sR;
+    T un = ut[k];
+    T dr = rR - rL, dp = pR - pL, dun = WR[1 + k] - WL[1 + k];
+    T al1 = (dp - rt * a * dun) / (2.0 * a2);
+    T al3 = (dp + rt * a * dun) / (2.0 * a2);
+    T al2 = dr - dp / a2;
+    T cL = sqrt_(g * pL / rL), cR = sqrt_(g * pR / rR);
+    T l1 = harten_abs(T(un - a), T(WL[1 + k] - cL), T(WR[1 + k] - cR));
+    T l3 = harten_abs(T(un + a), T(WL[1 + k] + cL), T(WR[1 + k] + cR));
+    T l2 = abs_(un);
+    T D[8];
+    // acoustic waves r_{1,3} = (1, u~ -/+ a e_k, H~ -/+ u_n a), entropy wave r_2 = (1, u~, |u~|^2/2)
+    D[0] = l1 * al1 + l2 * al2 + l3 * al3;
+    for (int j = 0; j < nd; ++j) D[1 + j] = l1 * al1 * ut[j] + l2 * al2 * ut[j] + l3 * al3 * ut[j];
+    D[1 + k] = D[1 + k] - l1 * al1 * a + l3 * al3 * a;
+    D[ip] = l1 * al1 * (H - un * a) + l2 * al2 * (0.5 * q2) + l3 * al3 * (H + un * a);
+    // shear waves r_t = (0, e_t, u~_t) with strength rho~ du_t, speed u_n
+    for (int j = 0; j < nd; ++j) {
+        if (j == k) continue;
+        T alt = rt * (WR[1 + j] - WL[1 + j]);
+        D[1 + j] = D[1 + j] + l2 * alt;
+        D[ip] = D[ip] + l2 * alt * ut[j];
+    }
+    for (int v = 0; v < nv; ++v) F[v] = 0.5 * (FL[v] + FR[v]) - 0.5 * D[v];
+}
+
+// Godunov's flux (Sec. 2.1 names it): the physical flux of the exact Riemann solution at x/t = 0.
+// Star pressure: root of f_L(p) + f_R(p) + (u_R - u_L) = 0, f_K the shock (Rankine-Hugoniot) or
+// rarefaction (isentropic) branch (Toro, ch. 4), by Newton from the linearised (PVRS) guess until
+// the relative step is below 1e-15 (at most 60 steps). Tangential velocities are those of the side
+// of the contact that x/t = 0 lies on (left when u* >= 0).
+template <class T> inline T pressure_branch(double g, const T& p, const T& rK, const T& pK, const T& cK, T* df) {
+    if (val(p) > val(pK)) {   // shock
+        T A = 2.0 / ((g + 1.0) * rK);
+        T B = (g - 1.0) / (g + 1.0) * pK;
+        T s = sqrt_(A / (p + B));
+        *df = s * (1.0 - (p - pK) / (2.0 * (B + p)));
+        return (p - pK) * s;
+    }
+    T q = p / pK;             // rarefaction
+    *df = pow_(q, -(g + 1.0) / (2.0 * g)) / (rK * cK);
+    return 2.0 * cK / (g - 1.0) * (pow_(q, (g - 1.0) / (2.0 * g)) - 1.0);
+}
+template <class T> void godunov_state_euler(double g, const T& rL, const T& uL, const T& pL, const T& rR, const T& uR,
+                                            const T& pR, T* r0, T* u0, T* p0, bool* left_of_contact) {
+    T cL = sqrt_(g * pL / rL), cR = sqrt_(g * pR / rR);
+    T ppv = 0.5 * (pL + pR) - 0.125 * (uR - uL) * (rL + rR) * (cL + cR);
+    T p = max_(ppv, T(1e-10 * val(min_(pL, pR))));
+    for (int it = 0; it < 60; ++it) {
+        T dL, dR;
+        T fL = pressure_branch(g, p, rL, pL, cL, &dL);
+        T fR = pressure_branch(g, p, rR, pR, cR, &dR);
+        T pn = p - (fL + fR + uR - uL) / (dL + dR);
+        if (val(pn) <= 0.0) pn = T(0.5 * val(p));
+        T step = pn - p;
+        p = pn;
+        if (std::fabs(val(step)) <= 1e-15 * val(p)) break;
+    }
+    T dL, dR;
+    T fL = pressure_branch(g, p, rL, pL, cL, &dL);
+    T fR = pressure_branch(g, p, rR, pR, cR, &dR);
+    T us = 0.5 * (uL + uR) + 0.5 * (fR - fL);
+    const double gr = (g - 1.0) / (g + 1.0);
+    *left_of_contact = val(us) >= 0.0;
+    if (*left_of_contact) {
+        if (val(p) > val(pL)) {   // left shock, speed S_L
+            T SL = uL - cL * sqrt_((g + 1.0) / (2.0 * g) * p / pL + (g - 1.0) / (2.0 * g));
+            if (val(SL) >= 0.0) { *r0 = rL; *u0 = uL; *p0 = pL; return; }
+            *r0 = rL * (p / pL + gr) / (gr * p / pL + 1.0); *u0 = us; *p0 = p; return;
+        }
+        T head = uL - cL;         // left rarefaction
+        if (val(head) >= 0.0) { *r0 = rL; *u0 = uL; *p0 = pL; return; }
+        T tail = us - cL * pow_(T(p / pL), (g - 1.0) / (2.0 * g));
+        if (val(tail) < 0.0) { *r0 = rL * pow_(T(p / pL), 1.0 / g); *u0 = us; *p0 = p; return; }
+        T c = 2.0 / (g + 1.0) * (cL + 0.5 * (g - 1.0) * uL);   // inside the fan at x/t = 0
+        *u0 = c;
+        *r0 = rL * pow_(T(c / cL), 2.0 / (g - 1.0));
+        *p0 = pL * pow_(T(c / cL), 2.0 * g / (g - 1.0));
+        return;
+    }
+    if (val(p) > val(pR)) {       // right shock
+        T SR = uR + cR * sqrt_((g + 1.0) / (2.0 * g) * p / pR + (g - 1.0) / (2.0 * g));
+        if (val(SR) <= 0.0) { *r0 = rR; *u0 = uR; *p0 = pR; return; }
+        *r0 = rR * (p / pR + gr) / (gr * p / pR + 1.0); *u0 = us; *p0 = p; return;
+    }
+    T head = uR + cR;             // right rarefaction
+    if (val(head) <= 0.0) { *r0 = rR; *u0 = uR; *p0 = pR; return; }
+    T tail = us + cR * pow_(T(p / pR), (g - 1.0) / (2.0 * g));
+    if (val(tail) > 0.0) { *r0 = rR * pow_(T(p / pR), 1.0 / g); *u0 = us; *p0 = p; return; }
+    T c = 2.0 / (g + 1.0) * (cR - 0.5 * (g - 1.0) * uR);
+    *u0 = -c;
+    *r0 = rR * pow_(T(c / cR), 2.0 / (g - 1.0));
+    *p0 = pR * pow_(T(c / cR), 2.0 * g / (g - 1.0));
+}
+template <class T> void godunov_flux_euler(const Desc& d, int k, const T* WL, const T* WR, T* F) {
+    const int nd = d.ndim, ip = nd + 1;
+    T r0, u0, p0;
+    bool left;
+    godunov_state_euler(d.gamma, WL[0], WL[1 + k], WL[ip], WR[0], WR[1 + k], WR[ip], &r0, &u0, &p0, &left);
+    T W[8];
+    const T* side = left ? WL : WR;
+    for (int j = 0; j < nd; ++j) W[1 + j] = side[1 + j];
+    W[0] = r0;
+    W[1 + k] = u0;
+    W[ip] = p0;
+    euler_phys_flux(d, W, k, F);
+}
+
+// Logarithmic mean (a - b)/(ln a - ln b) of two positive numbers; for nearly equal arguments from
+// ln(a/b) = 2 artanh(f), f = (a - b)/(a + b): (a + b) / (2 artanh(f)/f) with the series
+// artanh(f)/f = 1 + f^2/3 + f^4/5 + f^6/7 + f^8/9 when f^2 < 1e-4 (Ismail-Roe's device, more terms).
+template <class T> inline T log_mean(const T& a, const T& b) {
+    T f = (a - b) / (a + b);
+    T u = f * f;
+    if (val(u) < 1e-4) {
+        T s = 1.0 + u * (1.0 / 3.0 + u * (1.0 / 5.0 + u * (1.0 / 7.0 + u * (1.0 / 9.0))));
+        return (a + b) / (2.0 * s);
+    }
+    return (a - b) / log_(T(a / b));
+}
+
+// Two-point entropy-conservative flux (Sec. 2.1 cites LeFloch-Mercier-Rohde's entropy-conservative
+// schemes, built from two-point fluxes that satisfy Tadmor's condition
+// (v_R - v_L) . F = psi_R - psi_L for an entropy pair). Euler: Ismail-Roe's flux for the entropy
+// -rho s/(gamma - 1), s = ln(p rho^-gamma), from z = sqrt(rho/p) (1, u, p):
+// rho^ = z1_mean z3_ln, u^ = zu_mean / z1_mean, p1^ = z3_mean / z1_mean,
+// p2^ = (gamma+1)/(2 gamma) z3_ln / z1_ln + (gamma-1)/(2 gamma) z3_mean / z1_mean,
+// H^ = gamma p2^ / ((gamma-1) rho^) + |u^|^2/2; F = (rho^ u^_k, rho^ u^_k u^ + p1^ e_k, rho^ u^_k H^).
+// Burgers: the flux (u_L^2 + u_L u_R + u_R^2)/6 of the square entropy u^2/2.
+template <class T> void ec_flux(const Desc& d, int k, const T* WL, const T* WR, T* F) {
+    if (d.eq == EQ_BURGERS) {
+        F[0] = (WL[0] * WL[0] + WL[0] * WR[0] + WR[0] * WR[0]) / 6.0;
+        return;
+    }
+    const int nd = d.ndim, ip = nd + 1;
+    const double g = d.gamma;
+    T z1L = sqrt_(WL[0] / WL[ip]), z1R = sqrt_(WR[0] / WR[ip]);
+    T z3L = sqrt_(WL[0] * WL[ip]), z3R = sqrt_(WR[0] * WR[ip]);
+    T z1m = 0.5 * (z1L + z1R), z3m = 0.5 * (z3L + z3R);
+    T z1l = log_mean(z1L, z1R), z3l = log_mean(z3L, z3R);
+    T rho = z1m * z3l;
+    T u[8];
+    T q2 = T(0.0);
+    for (int j = 0; j < nd; ++j) {
+        u[j] = 0.5 * (z1L * WL[1 + j] + z1R * WR[1 + j]) / z1m;
+        q2 = q2 + u[j] * u[j];
+    }
+    T p1 = z3m / z1m;
+    T p2 = (g + 1.0) / (2.0 * g) * z3l / z1l + (g - 1.0) / (2.0 * g) * z3m / z1m;
+    T H = g * p2 / ((g - 1.0) * rho) + 0.5 * q2;
+    T mf = rho * u[k];
+    F[0] = mf;
+    for (int j = 0; j < nd; ++j) F[1 + j] = mf * u[j];
+    F[1 + k] = F[1 + k] + p1;
+    F[ip] = mf * H;
+}
+
 template <class T> void flux(const Desc& d, int k, const T* WL, const T* WR, T* F) {
     const int nv = nvars(d);
+    if (d.flux == FLUX_EC || d.flux == FLUX_EC4) { ec_flux(d, k, WL, WR, F); return; }
     if (d.eq == EQ_BURGERS) {
         T uL = WL[0], uR = WR[0];
         T fL = 0.5 * uL * uL, fR = 0.5 * uR * uR;
+        if (d.flux == FLUX_ROE) {
+            // Roe speed (u_L + u_R)/2 with Harten's fix of width max(0, a - u_L, u_R - a)
+            T a = 0.5 * (uL + uR);
+            F[0] = 0.5 * (fL + fR) - 0.5 * harten_abs(a, uL, uR) * (uR - uL);
+            return;
+        }
+        if (d.flux == FLUX_GODUNOV) {
+            // exact Riemann solution at x/t = 0: shock (u_L > u_R) moving with (u_L + u_R)/2, or
+            // rarefaction (u_L <= u_R), whose fan holds u = 0 when it straddles x/t = 0
+            if (val(uL) > val(uR)) F[0] = val(uL + uR) >= 0.0 ? fL : fR;
+            else if (val(uL) >= 0.0) F[0] = fL;
+            else if (val(uR) <= 0.0) F[0] = fR;
+            else F[0] = T(0.0);
+            return;
+        }
         if (d.flux == FLUX_RUSANOV) {
             T a = max_(abs_(uL), abs_(uR));
             F[0] = 0.5 * (fL + fR) - 0.5 * a * (uR - uL);
@@ -337,6 +567,8 @@ template <class T> void flux(const Desc& d, int k, const T* WL, const T* WR, T* 
         }
         return;
     }
+    if (d.flux == FLUX_ROE) { roe_flux_euler(d, k, WL, WR, F); return; }
+    if (d.flux == FLUX_GODUNOV) { godunov_flux_euler(d, k, WL, WR, F); return; }
     const int nd = d.ndim;
     const int ip = nd + 1;
     T UL[8], UR[8], FL[8], FR[8];
@@ -385,6 +617,26 @@ template <class T> void flux(const Desc& d, int k, const T* WL, const T* WR, T* 
 
 // Flux through the interface i+1/2 (between cell i and i+1) along k at cell position c.
 template <class T> void interface_flux(const Desc& d, const T* U, const int c[3], int k, int i, T* F) {
+    if (d.flux == FLUX_EC || d.flux == FLUX_EC4) {
+        // entropy-conservative fluxes take the cell values (primitive), no reconstruction
+        const int nv = nvars(d);
+        T W[4][8];
+        for (int s = 0; s < 4; ++s) {
+            if (d.flux == FLUX_EC && (s == 0 || s == 3)) continue;
+            T Uc[8];
+            cell_cons(d, U, c, k, i - 1 + s, Uc);
+            if (d.eq == EQ_BURGERS) W[s][0] = Uc[0];
+            else cons_to_prim(d, Uc, W[s]);
+        }
+        if (d.flux == FLUX_EC) { ec_flux(d, k, W[1], W[2], F); return; }
+        // fourth order (LeFloch-Mercier-Rohde): 4/3 F(w_i, w_{i+1}) - 1/6 (F(w_{i-1}, w_{i+1}) + F(w_i, w_{i+2}))
+        T Fa[8], Fb[8], Fc[8];
+        ec_flux(d, k, W[1], W[2], Fa);
+        ec_flux(d, k, W[0], W[2], Fb);
+        ec_flux(d, k, W[1], W[3], Fc);
+        for (int v = 0; v < nv; ++v) F[v] = (4.0 / 3.0) * Fa[v] - (1.0 / 6.0) * (Fb[v] + Fc[v]);
+        return;
+    }
     T Wl_i[8], Wr_i[8], Wl_j[8], Wr_j[8];
     cell_faces(d, U, c, k, i, Wl_i, Wr_i);
     cell_faces(d, U, c, k, i + 1, Wl_j, Wr_j);

@@ -1088,3 +1088,263 @@ def test_bench_workload_flop_constants_match_the_count():
             desc["n"] = desc.pop("levels")[0][0]
         d = oracle.make_desc(**desc)
         assert oracle.count_flops(d)["per_cell_update"] == flops, name
+
+
+# ---------------------------------------------------------------- more fluxes (Sec. 2.1): Roe, Godunov,
+# entropy conservative; ENO reconstruction
+def _entropy_vars(W, g=1.4):
+    """Entropy variables of S = -rho s / (g - 1), s = ln(p rho^-g), and the entropy-flux potential
+    psi_k = rho u_k, for a primitive state [rho, u_1..u_d, p]."""
+    W = np.asarray(W, float)
+    r, u, p = W[0], W[1:-1], W[-1]
+    s = math.log(p) - g * math.log(r)
+    v = np.concatenate([[(g - s) / (g - 1) - r * np.dot(u, u) / (2 * p)], r * u / p, [-r / p]])
+    return v, r * u
+
+
+@pytest.mark.parametrize("fl", ["roe", "godunov", "ec"])
+@pytest.mark.parametrize("nd", [1, 2, 3])
+def test_new_fluxes_consistency(fl, nd):
+    d = oracle.make_desc(ndim=nd, n=(4, 4, 4), eq="euler", flux=fl)
+    g = 1.4
+    for W in random_prim(nd, rng, 20):
+        for k in range(nd):
+            r, vel, p = W[0], W[1:1 + nd], W[1 + nd]
+            E = p / (g - 1) + 0.5 * r * np.dot(vel, vel)
+            ref = np.concatenate([[r * vel[k]], r * vel[k] * vel + p * (np.arange(nd) == k), [vel[k] * (E + p)]])
+            np.testing.assert_allclose(oracle.flux(d, k, W, W), ref, rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("fl", ["roe", "godunov", "ec"])
+def test_new_fluxes_mirror_symmetry(fl):
+    nd = 2
+    d = oracle.make_desc(ndim=nd, n=(4, 4), eq="euler", flux=fl)
+    for _ in range(20):
+        WL, WR = random_prim(nd, rng, 2)
+        for k in range(nd):
+            M = np.ones(nd + 2)
+            M[1 + k] = -1
+            np.testing.assert_allclose(oracle.flux(d, k, WL, WR), -M * oracle.flux(d, k, M * WR, M * WL),
+                                       rtol=1e-12, atol=1e-12)
+
+
+def test_godunov_flux_is_the_flux_of_the_exact_riemann_solution():
+    """The Godunov flux equals the physical flux of the exact Riemann solution sampled at x/t = 0,
+    taken from the independent test-side solver (Toro's pressure function, tests/exact.py): shocks,
+    rarefactions (including transonic ones), contacts on either side of the interface."""
+    d = oracle.make_desc(ndim=1, n=(4,), eq="euler", flux="godunov")
+    cases = [((1.0, 0.0, 1.0), (0.125, 0.0, 0.1)), ((0.445, 0.698, 3.528), (0.5, 0.0, 0.571)),
+             ((1.0, 0.75, 1.0), (0.125, 0.0, 0.1)), ((1.0, -0.5, 0.4), (1.0, 0.5, 0.4)),
+             ((5.99924, 19.5975, 460.894), (5.99242, -6.19633, 46.0950)), ((1.0, -19.59745, 1000.0), (1.0, -19.59745, 0.01))]
+    r = np.random.default_rng(5)
+    for _ in range(40):
+        cases.append(((r.uniform(0.2, 3), r.uniform(-1.5, 1.5), r.uniform(0.2, 4)),
+                      (r.uniform(0.2, 3), r.uniform(-1.5, 1.5), r.uniform(0.2, 4))))
+    for WL, WR in cases:
+        R = RiemannExact(WL, WR)
+        rho, u, p = (float(a[0]) for a in R.sample(np.array([0.0])))
+        ref = euler_phys_flux_1d((rho, u, p))
+        np.testing.assert_allclose(oracle.flux(d, 0, WL, WR), ref, rtol=1e-10, atol=1e-12 * np.abs(ref).max())
+
+
+def test_godunov_tangential_velocity_follows_the_contact():
+    d = oracle.make_desc(ndim=2, n=(4, 4), eq="euler", flux="godunov")
+    WL, WR = [1.0, 0.3, 0.7, 1.0], [0.5, 0.3, -0.4, 1.0]   # a pure contact moving right: upwind left
+    F = oracle.flux(d, 0, WL, WR)
+    assert F[2] == pytest.approx(1.0 * 0.3 * 0.7, rel=1e-13)
+    WL, WR = [1.0, -0.3, 0.7, 1.0], [0.5, -0.3, -0.4, 1.0]
+    F = oracle.flux(d, 0, WL, WR)
+    assert F[2] == pytest.approx(0.5 * -0.3 * -0.4, rel=1e-13)
+
+
+def test_roe_resolves_isolated_contacts_and_shocks_exactly():
+    """Roe's linearisation satisfies A(U_L, U_R)(U_R - U_L) = F_R - F_L, so a jump that is a single
+    wave of the exact problem is upwinded exactly: a stationary contact gives zero mass flux, and
+    the two sides of the Lax problem's right shock (Rankine-Hugoniot-connected, from the exact
+    solver) give the flux of the upwind side."""
+    d = oracle.make_desc(ndim=2, n=(4, 4), eq="euler", flux="roe")
+    F = oracle.flux(d, 0, [3.0, 0.0, 0.0, 1.3], [0.25, 0.0, 0.0, 1.3])
+    assert abs(F[0]) <= 1e-15 and F[1] == pytest.approx(1.3, rel=1e-15) and abs(F[3]) <= 1e-15
+    R = RiemannExact((0.445, 0.698, 3.528), (0.5, 0.0, 0.571))
+    _, rs = R.star_densities()
+    d1 = oracle.make_desc(ndim=1, n=(4,), eq="euler", flux="roe")
+    WS, WR = (rs, R.ustar, R.pstar), (0.5, 0.0, 0.571)
+    assert R.shock_speed_right() > 0
+    np.testing.assert_allclose(oracle.flux(d1, 0, WS, WR), euler_phys_flux_1d(WS), rtol=1e-9)
+    # the same shock moving left (mirror): upwind is the right side
+    np.testing.assert_allclose(oracle.flux(d1, 0, (0.5, 0.0, 0.571), (rs, -R.ustar, R.pstar)),
+                               euler_phys_flux_1d((rs, -R.ustar, R.pstar)), rtol=1e-9)
+    # a moving shear wave (equal rho and p, normal velocity 0.3, tangential jump): upwind (left)
+    # flux, as Godunov's exact flux gives it; a 3D shear across both tangential directions too
+    dg = oracle.make_desc(ndim=2, n=(4, 4), eq="euler", flux="godunov")
+    WL, WR = [1.2, 0.3, 0.7, 0.9], [1.2, 0.3, -0.4, 0.9]
+    np.testing.assert_allclose(oracle.flux(d, 0, WL, WR), oracle.flux(dg, 0, WL, WR), rtol=1e-13, atol=1e-15)
+    g = 1.4
+    E = 0.9 / (g - 1) + 0.5 * 1.2 * (0.09 + 0.49)
+    np.testing.assert_allclose(oracle.flux(d, 0, WL, WR), [1.2 * 0.3, 1.2 * 0.09 + 0.9, 1.2 * 0.3 * 0.7, 0.3 * (E + 0.9)],
+                               rtol=1e-13)
+    d3 = oracle.make_desc(ndim=3, n=(4, 4, 4), eq="euler", flux="roe")
+    WL, WR = [1.2, 0.7, 0.1, -0.3, 0.9], [1.2, -0.2, 0.5, -0.3, 0.9]
+    F = oracle.flux(d3, 2, WL, WR)                                   # u_z = -0.3 < 0: upwind is the right
+    E = 0.9 / (g - 1) + 0.5 * 1.2 * (0.04 + 0.25 + 0.09)
+    np.testing.assert_allclose(F, [1.2 * -0.3, 1.2 * -0.3 * -0.2, 1.2 * -0.3 * 0.5, 1.2 * 0.09 + 0.9, -0.3 * (E + 0.9)],
+                               rtol=1e-13)
+
+
+@pytest.mark.parametrize("nd", [1, 2, 3])
+def test_entropy_conservative_flux_satisfies_tadmors_condition(nd):
+    """(v_R - v_L) . F(W_L, W_R) = psi_R - psi_L for the entropy pair (-rho s/(g-1), -rho u s/(g-1)):
+    the defining identity of an entropy-conservative two-point flux, on random pairs (including
+    nearly equal states, where the logarithmic means switch to their series), and F(L,R) = F(R,L)."""
+    d = oracle.make_desc(ndim=nd, n=(4, 4, 4), eq="euler", flux="ec")
+    pairs = [tuple(random_prim(nd, rng, 2)) for _ in range(30)]
+    for _ in range(10):
+        W = random_prim(nd, rng, 1)[0]
+        pairs.append((W, W * (1 + 1e-4 * rng.standard_normal(nd + 2))))
+    for WL, WR in pairs:
+        vL, psiL = _entropy_vars(WL)
+        vR, psiR = _entropy_vars(WR)
+        for k in range(nd):
+            F = oracle.flux(d, k, WL, WR)
+            lhs = np.dot(vR - vL, F)
+            scale = np.abs(vR - vL) @ np.abs(F) + abs(psiR[k]) + abs(psiL[k])
+            assert abs(lhs - (psiR[k] - psiL[k])) <= 1e-12 * scale
+            np.testing.assert_allclose(oracle.flux(d, k, WR, WL), F, rtol=1e-13, atol=1e-14)
+
+
+def test_burgers_new_fluxes():
+    """Burgers: Godunov is the exact solution's flux at x/t = 0 (shock with speed (uL+uR)/2, or the
+    rarefaction's sonic point); Roe with Harten's fix equals it on shocks and one-sided waves; the
+    entropy-conservative flux (uL^2 + uL uR + uR^2)/6 satisfies Tadmor's condition for the entropy
+    u^2/2 (entropy variable u, flux potential psi = u f - q = u^3/6): (uR - uL) F = uR^3/6 - uL^3/6."""
+    dg = oracle.make_desc(ndim=1, n=(4,), eq="burgers", flux="godunov")
+    dr = oracle.make_desc(ndim=1, n=(4,), eq="burgers", flux="roe")
+    de = oracle.make_desc(ndim=1, n=(4,), eq="burgers", flux="ec")
+    r = np.random.default_rng(9)
+    for _ in range(200):
+        uL, uR = r.uniform(-2, 2, 2)
+        Fg = oracle.flux(dg, 0, [uL], [uR])[0]
+        assert Fg == pytest.approx(burgers_godunov(uL, uR), rel=1e-15, abs=1e-300)
+        if uL > uR or uL * uR > 0:
+            assert oracle.flux(dr, 0, [uL], [uR])[0] == pytest.approx(Fg, rel=1e-14, abs=1e-15)
+        Fe = oracle.flux(de, 0, [uL], [uR])[0]
+        assert (uR - uL) * Fe == pytest.approx((uR**3 - uL**3) / 6, rel=1e-13, abs=1e-15)
+    # transonic rarefaction: the fix keeps Roe's flux below the expansion-shock value (fL + fR)/2 - 0
+    uL, uR = -0.5, 1.0
+    assert oracle.flux(dr, 0, [uL], [uR])[0] < 0.5 * (0.5 * uL * uL + 0.5 * uR * uR) - 0.5 * 0.25 * (uR - uL)
+
+
+@pytest.mark.parametrize("fl,recon,min_rate", [("roe", "pc", 0.45), ("roe", "mc", 0.6), ("godunov", "pc", 0.45),
+                                               ("godunov", "mc", 0.6), ("hllc", "eno2", 0.6)])
+def test_sod_converges_with_roe_godunov_eno(fl, recon, min_rate):
+    R = RiemannExact((1.0, 0.0, 1.0), (0.125, 0.0, 0.1))
+    ns, errs = [128, 256, 512, 1024], []
+    for n in ns:
+        d = oracle.make_desc(ndim=1, n=(n,), eq="euler", recon=recon, flux=fl, rk="ssprk2", bc="outflow", cfl=0.45)
+        U, _, _ = oracle.evolve(d, oracle.init(d, "sod"), T=0.2)
+        errs.append(np.abs(U[0, 0, 0, 0] - R.cell_average_density(n, 0.2)).mean())
+    assert np.all(np.diff(errs) < 0), errs
+    assert math.log(errs[0] / errs[-1]) / math.log(ns[-1] / ns[0]) >= min_rate, errs
+
+
+def test_roe_entropy_fix_on_a_transonic_rarefaction():
+    """Toro's test 1 (left state moving right at 0.75) has a sonic point inside the left
+    rarefaction, where the unfixed Roe flux keeps an entropy-violating expansion shock. With the
+    Harten-Hyman fix the first-order scheme converges to the exact solution, and near the sonic
+    point the density jumps between neighbouring cells shrink with the mesh."""
+    R = RiemannExact((1.0, 0.75, 1.0), (0.125, 0.0, 0.1))
+    ns, errs, jumps = [200, 400, 800], [], []
+    for n in ns:
+        d = oracle.make_desc(ndim=1, n=(n,), eq="euler", recon="pc", flux="roe", rk="ssprk2", bc="outflow", cfl=0.45)
+        U0 = np.zeros((1, 3, 1, 1, n))
+        x = (np.arange(n) + 0.5) / n
+        rho = np.where(x < 0.3, 1.0, 0.125)
+        u = np.where(x < 0.3, 0.75, 0.0)
+        p = np.where(x < 0.3, 1.0, 0.1)
+        U0[0, 0, 0, 0], U0[0, 1, 0, 0], U0[0, 2, 0, 0] = rho, rho * u, p / 0.4 + 0.5 * rho * u * u
+        U, _, _ = oracle.evolve(d, U0, T=0.2)
+        ex = R.cell_average_density(n, 0.2, x0=0.3)
+        errs.append(np.abs(U[0, 0, 0, 0] - ex).mean())
+        # the sonic point sits at x = 0.3 at every time (x/t = 0 inside the fan)
+        i0 = int(0.3 * n)
+        jumps.append(np.abs(np.diff(U[0, 0, 0, 0, i0 - 3:i0 + 4])).max())
+    assert np.all(np.diff(errs) < 0) and math.log(errs[0] / errs[-1]) / math.log(4) >= 0.5, errs
+    assert jumps[-1] < 0.6 * jumps[0] and jumps[-1] < 0.02, jumps
+
+
+def test_eno2_reconstruction():
+    """ENO2 takes the smoother of the two linear candidates (the smaller one-sided difference):
+    exact on linear data, the smaller slope at a kink, and second order on smooth Burgers data."""
+    for i in range(-3, 4):
+        fl, fr = oracle.recon("eno2", 2.0 * i - 1.0, 2.0 * i + 1.0, 2.0 * i + 3.0)
+        assert fl == pytest.approx(2.0 * i) and fr == pytest.approx(2.0 * i + 2.0)
+    fl, fr = oracle.recon("eno2", 0.0, 1.0, 1.5)     # differences 1 and 0.5: slope 0.5
+    assert (fl, fr) == (0.75, 1.25)
+    fl, fr = oracle.recon("eno2", 0.9, 1.0, 3.0)     # differences 0.1 and 2: slope 0.1
+    assert fl == pytest.approx(0.95) and fr == pytest.approx(1.05)
+    fl, fr = oracle.recon("eno2", 1.0, 0.0, 2.0)     # extremum: differences -1, 2: slope -1 (not limited to 0)
+    assert (fl, fr) == (0.5, -0.5)
+    ns, errs = [32, 64, 128, 256], []
+    for n in ns:
+        d = oracle.make_desc(ndim=1, n=(n,), eq="burgers", recon="eno2", flux="godunov", rk="ssprk2", bc="periodic",
+                             cfl=0.4)
+        U, _, _ = oracle.evolve(d, oracle.init(d, "burgers_sine"), T=0.1)
+        errs.append(np.abs(U[0, 0, 0, 0] - burgers_sine_cell_averages(n, 0.1)).mean())
+    assert observed_rates(ns, errs)[-1] >= 1.8, errs
+
+
+def _smooth_euler_1d(n):
+    x = (np.arange(n) + 0.5) / n
+    tp = 2 * np.pi
+    rho, drho = 1 + 0.2 * np.sin(tp * x), 0.2 * tp * np.cos(tp * x)
+    u, du = 0.5 + 0.1 * np.cos(tp * x), -0.1 * tp * np.sin(tp * x)
+    p, dp = 1 + 0.1 * np.sin(tp * x + 1), 0.1 * tp * np.cos(tp * x + 1)
+    return rho, u, p, drho, du, dp
+
+
+@pytest.mark.parametrize("fl,order", [("ec", 2), ("ec4", 4)])
+def test_entropy_conservative_schemes_order_and_entropy_balance(fl, order):
+    """On point values of a smooth periodic state, L(U)_i approximates -d/dx f(U(x_i)) (closed form
+    by the product rule) at second (two-point flux) and fourth order (LeFloch-Mercier-Rohde
+    combination), and the semi-discrete entropy is conserved: sum_i v(U_i) . L(U)_i = 0."""
+    g = 1.4
+    errs, ns = [], [16, 32, 64, 128]
+    for n in ns:
+        rho, u, p, dr, du, dp = _smooth_euler_1d(n)
+        d = oracle.make_desc(ndim=1, n=(n,), eq="euler", flux=fl, bc="periodic")
+        U = np.zeros((1, 3, 1, 1, n))
+        E = p / (g - 1) + 0.5 * rho * u * u
+        U[0, 0, 0, 0], U[0, 1, 0, 0], U[0, 2, 0, 0] = rho, rho * u, E
+        L = oracle.rhs(d, U)[0, :, 0, 0]
+        dE = dp / (g - 1) + 0.5 * dr * u * u + rho * u * du
+        exact = -np.array([dr * u + rho * du, dr * u * u + 2 * rho * u * du + dp, du * (E + p) + u * (dE + dp)])
+        errs.append(np.abs(L - exact).max())
+        W = np.stack([rho, u, p])
+        V = np.array([_entropy_vars(W[:, i])[0] for i in range(n)]).T
+        bal = (V * L).sum()
+        assert abs(bal) <= 1e-12 * (np.abs(V) * np.abs(L)).sum(), bal
+    rates = observed_rates(ns, errs)
+    assert np.all(rates[1:] >= order - 0.2), (errs, rates)
+
+
+def test_entropy_conservative_burgers_and_2d_balance():
+    """Burgers: sum_i u_i L_i = 0 for both entropy-conservative schemes (entropy u^2/2); 2D Euler on
+    a random smooth periodic state: sum_i v_i . L_i = 0 with both directions."""
+    n = 40
+    x = (np.arange(n) + 0.5) / n
+    for fl in ("ec", "ec4"):
+        d = oracle.make_desc(ndim=1, n=(n,), eq="burgers", flux=fl, bc="periodic")
+        U = (0.3 + np.sin(2 * np.pi * x) + 0.2 * np.cos(6 * np.pi * x)).reshape(1, 1, 1, 1, n)
+        L = oracle.rhs(d, U)
+        assert abs((U * L).sum()) <= 1e-13 * (np.abs(U) * np.abs(L)).sum()
+    from inputs import euler_state
+    U = euler_state(1, 2, (12, 10), seed=4)
+    for fl in ("ec", "ec4"):
+        d = oracle.make_desc(ndim=2, n=(12, 10), eq="euler", flux=fl, bc="periodic")
+        L = oracle.rhs(d, U)[0].reshape(4, -1)
+        W = oracle.cons_to_prim(d, U[0].reshape(4, -1).T.copy()).T if False else None
+        Uc = U[0].reshape(4, -1)
+        rho, mx, my, E = Uc
+        p = 0.4 * (E - 0.5 * (mx * mx + my * my) / rho)
+        V = np.array([_entropy_vars([rho[i], mx[i] / rho[i], my[i] / rho[i], p[i]])[0] for i in range(rho.size)]).T
+        assert abs((V * L).sum()) <= 1e-12 * (np.abs(V) * np.abs(L)).sum()

@@ -41,7 +41,9 @@ STAGE_KERNEL_NAMES = {0: "k_stage<float, Euler, 2D, WENO3, HLLC, 32x16>",
                       2: "k_stage<float, Euler, 2D, WENO3, HLLC, 32x32>",
                       3: "k_stage2d_col<WENO3, HLLC>",
                       4: "k_stage2d_pair<WENO3, HLLC, 32x16>",
-                      5: "k_stage2d_pair<WENO3, HLLC, 32x8>"}
+                      5: "k_stage2d_pair<WENO3, HLLC, 32x8>",
+                      8: "k_stage2d_pair2<WENO3, HLLC, 32x16>",
+                      9: "k_stage2d_pair2<WENO3, HLLC, 32x32>"}
 WORKLOAD = "kh2d_256x256_mc4096_weno3_hllc_ssprk3_fp32_T1"
 # compulsory HBM bytes per 2D SSP-RK3 cell-update in FP32: per variable read U^n + write U1,
 # read U1 + U^n + write U2, read U2 + U^n + write U^{n+1} = 8 words, x 4 variables x 4 bytes
@@ -149,11 +151,12 @@ def run_step(S, alsv, world=1):
     return nstep
 
 
-def plain_fp64_loop(alsv, torch, steps_per_sample, T_short=0.066):
+def plain_fp64_loop(alsv, torch, steps_per_sample, variant, T_short=0.066):
     """The plain per-sample FP64 path on the same GPU: sample 0 of the batch alone (B = 1) in FP64,
     timed over the CFL steps to T_short and extrapolated to the sample's full step count. Its
-    relative L1 difference from the batched FP32 result for the same sample at T_short states the
-    error at which the two throughputs compare."""
+    relative L1 difference from the batched FP32 result for the same sample at T_short (the batch's
+    stage schedule; a sample's result does not depend on the batch around it) states the error at
+    which the two throughputs compare. Returns (line entry, FP32 state, FP64 state) at T_short."""
     kw = desc_kwargs(batch=1)
     S64 = alsv.Solver(alsv.make_desc(**dict(kw, precision="fp64")))
     S64.set_initial_data("kh")
@@ -168,14 +171,30 @@ def plain_fp64_loop(alsv, torch, steps_per_sample, T_short=0.066):
     S64.close()
     S32 = alsv.Solver(alsv.make_desc(**kw))
     S32.set_initial_data("kh")
+    alsv.alsv_set_tile_variant(S32.ctx, variant)
     S32.evolve_to(T_short)
     u32 = S32.to_host(S32.U).double()
     S32.close()
     rel = float((u32 - u64).abs().sum() / u64.abs().sum())
     ms_step = 1000.0 * el / max(n, 1)
-    return {"samples_per_s": 1000.0 / (ms_step * steps_per_sample), "ms_per_rk_step": ms_step, "steps_timed": n,
-            "T_timed": T_short, "steps_per_sample": int(steps_per_sample), "precision": "fp64",
-            "fp32_batched_vs_fp64_rel_l1": rel}
+    return ({"samples_per_s": 1000.0 / (ms_step * steps_per_sample), "ms_per_rk_step": ms_step, "steps_timed": n,
+             "T_timed": T_short, "steps_per_sample": int(steps_per_sample), "precision": "fp64",
+             "fp32_batched_vs_fp64_rel_l1": rel}, u32.numpy(), u64.numpy())
+
+
+def errors_vs_oracle(u32, u64, T_short=0.066):
+    """The cpu_baseline leg's second use of the oracle: sample 0 of the workload evolved by the FP64
+    oracle to T_short, and the relative L1 differences of the GPU's FP32 (batched schedule) and FP64
+    results for that sample from it - the error each result states against the FP64 oracle."""
+    import numpy as np
+    import oracle
+    d = oracle.make_desc(**desc_kwargs(batch=1))
+    th = oracle.theta_splitmix(SEED, 1, 20)
+    uo, _, _ = oracle.evolve(d, oracle.init(d, "kh", 1, th), T=T_short)
+    den = np.abs(uo).sum()
+    return {"T": T_short, "sample": 0, "fp32_batched_vs_oracle_rel_l1": float(np.abs(u32.reshape(uo.shape) - uo).sum() / den),
+            "fp64_vs_oracle_rel_l1": float(np.abs(u64.reshape(uo.shape) - uo).sum() / den),
+            "fp64_vs_oracle_max_rel": float(np.abs(u64.reshape(uo.shape) - uo).max() / np.abs(uo).max())}
 
 
 def stage_traffic(variant, cell_updates, launches):
@@ -700,10 +719,11 @@ def main():
                                     "flops_per_cell_update": FLOPS_PER_CELL_UPDATE_2D_WENO3_HLLC_RK3,
                                     "peak_kind": "nominal: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
         steps0 = float(nstep[0]) if len(nstep) else 1.0
-        line["plain_fp64"] = plain_fp64_loop(alsv, torch, steps0)
+        line["plain_fp64"], u32, u64 = plain_fp64_loop(alsv, torch, steps0, chosen)
         line["batched_vs_plain_fp64_samples_per_s"] = samples_per_s / line["plain_fp64"]["samples_per_s"]
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = {k: v for k, v in cpu_baseline_oracle().items() if k not in ("elapsed_s", "cell_updates")}
+            line["error_vs_oracle"] = errors_vs_oracle(u32, u64)
         print(json.dumps(line), flush=True)
     S.close()
     if world > 1:

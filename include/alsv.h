@@ -48,9 +48,21 @@ enum {
 };
 
 enum { ALSV_EQ_BURGERS = 0, ALSV_EQ_EULER = 1 };
-enum { ALSV_RECON_PC = 0, ALSV_RECON_MC = 1, ALSV_RECON_WENO3 = 2 };
+/* Reconstruction (Sec. 2.1 names ENO and WENO): PC piecewise constant; MC monotonized-central
+ * limited linear; WENO3 Jiang-Shu third order; ENO2 second-order ENO (of the two linear
+ * candidates, the one with the smaller one-sided difference). */
+enum { ALSV_RECON_PC = 0, ALSV_RECON_MC = 1, ALSV_RECON_WENO3 = 2, ALSV_RECON_ENO2 = 3 };
 enum { ALSV_VARS_CONS = 0, ALSV_VARS_PRIM = 1 };
-enum { ALSV_FLUX_RUSANOV = 0, ALSV_FLUX_HLL = 1, ALSV_FLUX_HLLC = 2 };
+/* Numerical flux (Sec. 2.1 names HLLC, Godunov, Rusanov, Roe and high-order entropy-conservative
+ * fluxes): RUSANOV, HLL, HLLC (Davis wave speeds); ROE with Harten's entropy fix on the acoustic
+ * fields (Harten-Hyman width); GODUNOV the flux of the exact Riemann solution at x/t = 0; EC the
+ * two-point entropy-conservative flux (Ismail-Roe for Euler, (uL^2 + uL uR + uR^2)/6 for Burgers)
+ * and EC4 its fourth-order combination over four cells (LeFloch-Mercier-Rohde). EC and EC4 take
+ * cell values: recon and recon_vars are ignored for them. ENO2, ROE, GODUNOV, EC and EC4 run on
+ * the default stage schedule (tile variant 0); with ENO2, ROE or GODUNOV Euler needs recon_vars
+ * PRIM, and Burgers is served in 1D only (INVALID_ARG at alsv_init_grid otherwise). */
+enum { ALSV_FLUX_RUSANOV = 0, ALSV_FLUX_HLL = 1, ALSV_FLUX_HLLC = 2, ALSV_FLUX_ROE = 3, ALSV_FLUX_GODUNOV = 4,
+       ALSV_FLUX_EC = 5, ALSV_FLUX_EC4 = 6 };
 enum { ALSV_RK_SSP2 = 2, ALSV_RK_SSP3 = 3 };
 /* ALSV_BC_HALO: a face of a block of a decomposed grid whose ghost layers are filled by the caller
  * (alsv_bind_halo; see "Domain decomposition" below). */

@@ -16,9 +16,9 @@ OK = 0
 STATUS_NAMES = {0: "OK", 1: "ERR_INVALID_ARG", 2: "ERR_CUDA", 3: "ERR_NONPHYSICAL", 4: "ERR_CFL",
                 5: "ERR_TIMEOUT", 6: "ERR_BUFFER_TOO_SMALL", 7: "ERR_NOT_READY"}
 EQ = {"burgers": 0, "euler": 1}
-RECON = {"pc": 0, "mc": 1, "weno3": 2}
+RECON = {"pc": 0, "mc": 1, "weno3": 2, "eno2": 3}
 RVARS = {"cons": 0, "prim": 1}
-FLUX = {"rusanov": 0, "hll": 1, "hllc": 2}
+FLUX = {"rusanov": 0, "hll": 1, "hllc": 2, "roe": 3, "godunov": 4, "ec": 5, "ec4": 6}
 RK = {"ssprk2": 2, "ssprk3": 3}
 BC = {"periodic": 0, "outflow": 1, "reflective": 2, "halo": 3}
 PRECISION = {"fp32": 0, "fp64": 1}

@@ -47,7 +47,8 @@ def up_to_date() -> bool:
 
 # FP64 translation units evaluate each formula exactly as written (no FMA contraction), so the FP64
 # path reproduces the plain CPU restatement of the scheme operation by operation.
-NO_FMA = ("stage_f64_1d.cu", "stage_f64_2d.cu", "stage_f64_3d.cu", "misc_kernels.cu", "mlmc.cu", "functionals.cu")
+NO_FMA = ("stage_f64_1d.cu", "stage_f64_2d.cu", "stage_f64_3d.cu", "stage_ext_f64_1d.cu", "stage_ext_f64_2d.cu",
+          "stage_ext_f64_3d.cu", "misc_kernels.cu", "mlmc.cu", "functionals.cu")
 
 
 def _compile(src: str) -> str:

@@ -341,6 +341,9 @@ int stage_num_variants(int fp64, int ndim) {
 }
 bool stage_variant_supported(int fp64, int ndim, int eq, int recon, int rvars, int flux, const int bc[3][2], int variant) {
     if (variant < 0 || variant >= stage_num_variants(fp64, ndim)) return false;
+    // ENO2 and the Roe / Godunov / entropy-conservative fluxes: the default tile schedule
+    if (ext_scheme(recon, flux))
+        return variant == 0 && (eq == EQ_EULER ? rvars == RV_PRIM : ndim == 1);
     if (ndim == 2 && !fp64 && (variant == 4 || variant == 5 || variant == 8 || variant == 9))
         return eq == EQ_EULER && rvars == RV_PRIM && (flux == FLX_HLLC || flux == FLX_RUSANOV);
     if (ndim == 2 && !fp64 && (variant == 6 || variant == 7 || variant == 10 || variant == 11))
@@ -376,9 +379,15 @@ alsv_status alsv_init_grid(const alsv_grid_desc* d_in, void* stream, alsv_ctx** 
     auto bad = [](const std::string& m) { return fail(nullptr, ALSV_ERR_INVALID_ARG, m); };
     if (d.ndim < 1 || d.ndim > 3) return bad("ndim must be 1, 2 or 3");
     if (d.eq != ALSV_EQ_BURGERS && d.eq != ALSV_EQ_EULER) return bad("eq must be BURGERS or EULER");
-    if (d.recon < 0 || d.recon > 2) return bad("recon must be PC, MC or WENO3");
+    if (d.recon < 0 || d.recon > 3) return bad("recon must be PC, MC, WENO3 or ENO2");
     if (d.recon_vars != ALSV_VARS_CONS && d.recon_vars != ALSV_VARS_PRIM) return bad("recon_vars must be CONS or PRIM");
-    if (d.flux < 0 || d.flux > 2) return bad("flux must be RUSANOV, HLL or HLLC");
+    if (d.flux < 0 || d.flux > 6) return bad("flux must be RUSANOV, HLL, HLLC, ROE, GODUNOV, EC or EC4");
+    if (ext_scheme(d.recon, d.flux)) {
+        if (d.eq == ALSV_EQ_BURGERS && d.ndim != 1)
+            return bad("ENO2 reconstruction and the ROE, GODUNOV, EC, EC4 fluxes serve Burgers in 1D only");
+        if (d.eq == ALSV_EQ_EULER && d.recon_vars != ALSV_VARS_PRIM && d.flux != ALSV_FLUX_EC && d.flux != ALSV_FLUX_EC4)
+            return bad("ENO2 reconstruction and the ROE, GODUNOV fluxes reconstruct primitive variables (recon_vars PRIM)");
+    }
     if (d.rk != ALSV_RK_SSP2 && d.rk != ALSV_RK_SSP3) return bad("rk must be SSP2 or SSP3");
     if (d.precision != ALSV_FP32 && d.precision != ALSV_FP64) return bad("precision must be FP32 or FP64");
     if (d.eq == ALSV_EQ_EULER && !(d.gamma > 1.0)) return bad("gamma must be > 1");
@@ -392,7 +401,7 @@ alsv_status alsv_init_grid(const alsv_grid_desc* d_in, void* stream, alsv_ctx** 
     if (d.sample_offset < 0) return bad("sample_offset must be >= 0");
     for (int k = 0; k < d.ndim; ++k)
         if (!(d.hi[k] > d.lo[k])) return bad("hi must exceed lo in every active direction");
-    const int G = d.recon == ALSV_RECON_PC ? 1 : 2;
+    const int G = ghost_width(d.recon, d.flux);
     for (int k = 0; k < 3; ++k)
         for (int s = 0; s < 2; ++s)
             if (d.bc[k][s] < 0 || d.bc[k][s] > 3) return bad("bc must be PERIODIC, OUTFLOW, REFLECTIVE or HALO");
@@ -487,7 +496,9 @@ alsv_status alsv_init_grid(const alsv_grid_desc* d_in, void* stream, alsv_ctx** 
     g.total_samples = (int)samples;
     g.nv = c->nv;
     g.gamma = d.gamma;
-    g.rvars = d.eq == ALSV_EQ_EULER ? d.recon_vars : ALSV_VARS_CONS;
+    // the entropy-conservative fluxes read primitive cell values whatever recon_vars says
+    g.rvars = d.eq == ALSV_EQ_EULER ? ((d.flux == ALSV_FLUX_EC || d.flux == ALSV_FLUX_EC4) ? ALSV_VARS_PRIM : d.recon_vars)
+                                    : ALSV_VARS_CONS;
     for (int k = 0; k < 3; ++k) {
         g.bc[k][0] = d.bc[k][0];
         g.bc[k][1] = d.bc[k][1];
@@ -1155,6 +1166,12 @@ cudaError_t launch_speed_f64_3d(int, int, const GridArgs&, const void*, double*,
 
 cudaError_t launch_stage(int fp64, int ndim, int eq, int recon, int flux, int variant, const StageArgs& a,
                          cudaStream_t s) {
+    if (ext_scheme(recon, flux)) {
+        if (variant != 0) return cudaErrorNotSupported;
+        if (ndim == 1) return fp64 ? launch_stage_ext_f64_1d(eq, recon, flux, a, s) : launch_stage_ext_f32_1d(eq, recon, flux, a, s);
+        if (ndim == 2) return fp64 ? launch_stage_ext_f64_2d(eq, recon, flux, a, s) : launch_stage_ext_f32_2d(eq, recon, flux, a, s);
+        return fp64 ? launch_stage_ext_f64_3d(eq, recon, flux, a, s) : launch_stage_ext_f32_3d(eq, recon, flux, a, s);
+    }
     if (ndim == 1) return fp64 ? launch_stage_f64_1d(variant, eq, recon, flux, a, s) : launch_stage_f32_1d(variant, eq, recon, flux, a, s);
     if (ndim == 2) return fp64 ? launch_stage_f64_2d(variant, eq, recon, flux, a, s) : launch_stage_f32_2d(variant, eq, recon, flux, a, s);
     return fp64 ? launch_stage_f64_3d(variant, eq, recon, flux, a, s) : launch_stage_f32_3d(variant, eq, recon, flux, a, s);

@@ -8,9 +8,18 @@
 namespace alsv {
 
 enum { EQ_BURGERS = 0, EQ_EULER = 1 };
-enum { REC_PC = 0, REC_MC = 1, REC_WENO3 = 2 };
+enum { REC_PC = 0, REC_MC = 1, REC_WENO3 = 2, REC_ENO2 = 3 };
 enum { RV_CONS = 0, RV_PRIM = 1 };
-enum { FLX_RUSANOV = 0, FLX_HLL = 1, FLX_HLLC = 2 };
+enum { FLX_RUSANOV = 0, FLX_HLL = 1, FLX_HLLC = 2, FLX_ROE = 3, FLX_GODUNOV = 4, FLX_EC = 5, FLX_EC4 = 6 };
+
+// Schemes served by the default tile schedule only (ENO2 reconstruction; Roe, Godunov and the
+// entropy-conservative fluxes).
+inline bool ext_scheme(int recon, int flux) { return recon == REC_ENO2 || flux >= FLX_ROE; }
+// Ghost layers a scheme reads: the entropy-conservative fluxes take cell values (EC: the two cells
+// of an interface, EC4: four); the others one (PC) or two layers.
+inline constexpr int ghost_width(int recon, int flux) {
+    return flux == FLX_EC4 ? 2 : (flux == FLX_EC ? 1 : (recon == REC_PC ? 1 : 2));
+}
 enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_REFLECTIVE = 2, BC_HALO = 3 };
 
 // Device status bits (OR-ed into the status word by kernels; kernels never trap).
@@ -98,6 +107,13 @@ bool stage_variant_supported(int fp64, int ndim, int eq, int recon, int rvars, i
 // Launchers (return cudaGetLastError of the launch).
 cudaError_t launch_stage(int fp64, int ndim, int eq, int recon, int flux, int variant, const StageArgs& a,
                          cudaStream_t s);
+// the default tile schedule for the schemes of ext_scheme (stage_ext_*.cu)
+cudaError_t launch_stage_ext_f32_1d(int eq, int recon, int flux, const StageArgs& a, cudaStream_t s);
+cudaError_t launch_stage_ext_f32_2d(int eq, int recon, int flux, const StageArgs& a, cudaStream_t s);
+cudaError_t launch_stage_ext_f32_3d(int eq, int recon, int flux, const StageArgs& a, cudaStream_t s);
+cudaError_t launch_stage_ext_f64_1d(int eq, int recon, int flux, const StageArgs& a, cudaStream_t s);
+cudaError_t launch_stage_ext_f64_2d(int eq, int recon, int flux, const StageArgs& a, cudaStream_t s);
+cudaError_t launch_stage_ext_f64_3d(int eq, int recon, int flux, const StageArgs& a, cudaStream_t s);
 cudaError_t launch_speed(int fp64, int ndim, int eq, int variant, const GridArgs& g, const void* U,
                          double* speed_part, cudaStream_t s);
 

@@ -189,14 +189,23 @@ __device__ __forceinline__ void recon_faces(R wm, R w0, R wp, R eps, R& fl, R& f
     }
 }
 
+// second-order ENO (Sec. 2.1 names ENO): the one-sided difference of smaller magnitude (ties: the
+// backward one), i.e. the smoother of the two linear candidates
+template <class R> __device__ __forceinline__ R eno2_slope(R wm, R w0, R wp) {
+    const R dm = w0 - wm, dp = wp - w0;
+    return fabs_(dp) < fabs_(dm) ? dp : dm;
+}
+
 template <class R, int RECON> __device__ __forceinline__ R recon_right(R wm, R w0, R wp, R eps) {
     if (RECON == REC_PC) return w0;
     if (RECON == REC_MC) return w0 + R(0.5) * mc_slope(wm, w0, wp);
+    if (RECON == REC_ENO2) return w0 + R(0.5) * eno2_slope(wm, w0, wp);
     return weno3_face(wm, w0, wp, eps);
 }
 template <class R, int RECON> __device__ __forceinline__ R recon_left(R wm, R w0, R wp, R eps) {
     if (RECON == REC_PC) return w0;
     if (RECON == REC_MC) return w0 - R(0.5) * mc_slope(wm, w0, wp);
+    if (RECON == REC_ENO2) return w0 - R(0.5) * eno2_slope(wm, w0, wp);
     return weno3_face(wp, w0, wm, eps);
 }
 
@@ -244,8 +253,214 @@ __device__ __forceinline__ void hllc_fast(const R* WL, const R* WR, R* F, R gamm
     for (int v = 0; v < NV; ++v) F[v] = star ? FK[v] + SK * (Us[v] - UK[v]) : FK[v];
 }
 
+// Harten's smoothing of |lambda| on an acoustic field, width from the Harten-Hyman estimate
+// delta = max(0, lambda - lambda_L, lambda_R - lambda) of the one-sided eigenvalues.
+template <class R> __device__ __forceinline__ R harten_abs(R lam, R lamL, R lamR) {
+    const R del = fmax_(R(0), fmax_(lam - lamL, lamR - lam));
+    if (fabs_(lam) < del) return (lam * lam + del * del) / (R(2) * del);
+    return fabs_(lam);
+}
+
+// Roe's flux (Sec. 2.1 names it) with the entropy fix above on the two acoustic fields: F = (F_L +
+// F_R)/2 - (1/2) sum |lambda| alpha r over the waves of the Roe-averaged Jacobian along D (acoustic
+// u_n -/+ a, entropy and shear waves at u_n); Roe averages weighted by sqrt(rho). Operations in
+// the same order as the CPU restatement of the scheme.
+template <class R, int ND, int D>
+__device__ __forceinline__ void roe_flux(const R* WL, const R* WR, R* F, R gamma, R gm1, R inv_gm1) {
+    constexpr int NV = ND + 2, IP = ND + 1;
+    R UL[NV], UR[NV], FL[NV], FR[NV];
+    prim_to_cons<R, ND>(WL, UL, gm1, inv_gm1);
+    prim_to_cons<R, ND>(WR, UR, gm1, inv_gm1);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) { FL[v] = UL[v] * WL[1 + D]; FR[v] = UR[v] * WR[1 + D]; }
+    FL[1 + D] = FL[1 + D] + WL[IP];
+    FR[1 + D] = FR[1 + D] + WR[IP];
+    FL[IP] = WL[1 + D] * (UL[IP] + WL[IP]);
+    FR[IP] = WR[1 + D] * (UR[IP] + WR[IP]);
+    const R rL = WL[0], rR = WR[0], pL = WL[IP], pR = WR[IP];
+    const R sL = sqrt(rL), sR = sqrt(rR);
+    const R HL = (UL[IP] + pL) / rL, HR = (UR[IP] + pR) / rR;
+    R ut[ND];
+    R q2 = R(0);
+#pragma unroll
+    for (int j = 0; j < ND; ++j) {
+        ut[j] = (sL * WL[1 + j] + sR * WR[1 + j]) / (sL + sR);
+        q2 = q2 + ut[j] * ut[j];
+    }
+    const R H = (sL * HL + sR * HR) / (sL + sR);
+    const R a2 = gm1 * (H - R(0.5) * q2);
+    const R a = sqrt(a2);
+    const R rt = sL * sR;
+    const R un = ut[D];
+    const R dr = rR - rL, dp = pR - pL, dun = WR[1 + D] - WL[1 + D];
+    const R al1 = (dp - rt * a * dun) / (R(2) * a2);
+    const R al3 = (dp + rt * a * dun) / (R(2) * a2);
+    const R al2 = dr - dp / a2;
+    const R cL = sqrt(gamma * pL / rL), cR = sqrt(gamma * pR / rR);
+    const R l1 = harten_abs(un - a, WL[1 + D] - cL, WR[1 + D] - cR);
+    const R l3 = harten_abs(un + a, WL[1 + D] + cL, WR[1 + D] + cR);
+    const R l2 = fabs_(un);
+    R Dv[NV];
+    Dv[0] = l1 * al1 + l2 * al2 + l3 * al3;
+#pragma unroll
+    for (int j = 0; j < ND; ++j) Dv[1 + j] = l1 * al1 * ut[j] + l2 * al2 * ut[j] + l3 * al3 * ut[j];
+    Dv[1 + D] = Dv[1 + D] - l1 * al1 * a + l3 * al3 * a;
+    Dv[IP] = l1 * al1 * (H - un * a) + l2 * al2 * (R(0.5) * q2) + l3 * al3 * (H + un * a);
+#pragma unroll
+    for (int j = 0; j < ND; ++j) {
+        if (j == D) continue;
+        const R alt = rt * (WR[1 + j] - WL[1 + j]);
+        Dv[1 + j] = Dv[1 + j] + l2 * alt;
+        Dv[IP] = Dv[IP] + l2 * alt * ut[j];
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) F[v] = R(0.5) * (FL[v] + FR[v]) - R(0.5) * Dv[v];
+}
+
+// Godunov's flux (Sec. 2.1 names it): the physical flux of the exact Riemann solution at x/t = 0.
+// The star pressure solves f_L(p) + f_R(p) + u_R - u_L = 0 (shock: Rankine-Hugoniot branch,
+// rarefaction: isentropic branch) by Newton's method from the linearised guess, to a relative step
+// of 1e-15 (FP64) or 1e-7 (FP32), at most 60 steps; then the solution is sampled at x/t = 0 and the
+// tangential velocities come from the side of the contact it lies on.
+template <class R> __device__ __forceinline__ R pressure_branch(R g, R p, R rK, R pK, R cK, R& df) {
+    if (p > pK) {
+        const R A = R(2) / ((g + R(1)) * rK);
+        const R B = (g - R(1)) / (g + R(1)) * pK;
+        const R s = sqrt(A / (p + B));
+        df = s * (R(1) - (p - pK) / (R(2) * (B + p)));
+        return (p - pK) * s;
+    }
+    const R q = p / pK;
+    df = pow(q, -(g + R(1)) / (R(2) * g)) / (rK * cK);
+    return R(2) * cK / (g - R(1)) * (pow(q, (g - R(1)) / (R(2) * g)) - R(1));
+}
+template <class R, int ND, int D>
+__device__ __forceinline__ void godunov_flux(const R* WL, const R* WR, R* F, R gamma, R gm1, R inv_gm1) {
+    constexpr int IP = ND + 1, NV = ND + 2;
+    const R g = gamma;
+    const R rL = WL[0], uL = WL[1 + D], pL = WL[IP], rR = WR[0], uR = WR[1 + D], pR = WR[IP];
+    const R cL = sqrt(g * pL / rL), cR = sqrt(g * pR / rR);
+    const R ppv = R(0.5) * (pL + pR) - R(0.125) * (uR - uL) * (rL + rR) * (cL + cR);
+    const R pfloor = R(1e-10) * fmin_(pL, pR);
+    R p = fmax_(ppv, pfloor);
+    const R tol = IsExact<R>::value ? R(1e-15) : R(1e-7);
+    R dL, dR;
+#pragma unroll 1
+    for (int it = 0; it < 60; ++it) {
+        const R fL = pressure_branch(g, p, rL, pL, cL, dL);
+        const R fR = pressure_branch(g, p, rR, pR, cR, dR);
+        R pn = p - (fL + fR + uR - uL) / (dL + dR);
+        if (pn <= R(0)) pn = R(0.5) * p;
+        const R step = pn - p;
+        p = pn;
+        if (fabs_(step) <= tol * p) break;
+    }
+    const R fL = pressure_branch(g, p, rL, pL, cL, dL);
+    const R fR = pressure_branch(g, p, rR, pR, cR, dR);
+    const R us = R(0.5) * (uL + uR) + R(0.5) * (fR - fL);
+    const R gr = (g - R(1)) / (g + R(1));
+    const bool left = us >= R(0);
+    R r0, u0, p0;
+    if (left) {
+        if (p > pL) {
+            const R SL = uL - cL * sqrt((g + R(1)) / (R(2) * g) * p / pL + (g - R(1)) / (R(2) * g));
+            if (SL >= R(0)) { r0 = rL; u0 = uL; p0 = pL; }
+            else { r0 = rL * (p / pL + gr) / (gr * p / pL + R(1)); u0 = us; p0 = p; }
+        } else if (uL - cL >= R(0)) {
+            r0 = rL; u0 = uL; p0 = pL;
+        } else if (us - cL * pow(p / pL, (g - R(1)) / (R(2) * g)) < R(0)) {
+            r0 = rL * pow(p / pL, R(1) / g); u0 = us; p0 = p;
+        } else {
+            const R c = R(2) / (g + R(1)) * (cL + R(0.5) * (g - R(1)) * uL);
+            u0 = c;
+            r0 = rL * pow(c / cL, R(2) / (g - R(1)));
+            p0 = pL * pow(c / cL, R(2) * g / (g - R(1)));
+        }
+    } else {
+        if (p > pR) {
+            const R SR = uR + cR * sqrt((g + R(1)) / (R(2) * g) * p / pR + (g - R(1)) / (R(2) * g));
+            if (SR <= R(0)) { r0 = rR; u0 = uR; p0 = pR; }
+            else { r0 = rR * (p / pR + gr) / (gr * p / pR + R(1)); u0 = us; p0 = p; }
+        } else if (uR + cR <= R(0)) {
+            r0 = rR; u0 = uR; p0 = pR;
+        } else if (us + cR * pow(p / pR, (g - R(1)) / (R(2) * g)) > R(0)) {
+            r0 = rR * pow(p / pR, R(1) / g); u0 = us; p0 = p;
+        } else {
+            const R c = R(2) / (g + R(1)) * (cR - R(0.5) * (g - R(1)) * uR);
+            u0 = -c;
+            r0 = rR * pow(c / cR, R(2) / (g - R(1)));
+            p0 = pR * pow(c / cR, R(2) * g / (g - R(1)));
+        }
+    }
+    R W[NV], U[NV];
+#pragma unroll
+    for (int j = 0; j < ND; ++j) W[1 + j] = left ? WL[1 + j] : WR[1 + j];
+    W[0] = r0;
+    W[1 + D] = u0;
+    W[IP] = p0;
+    prim_to_cons<R, ND>(W, U, gm1, inv_gm1);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) F[v] = U[v] * u0;
+    F[1 + D] = F[1 + D] + p0;
+    F[IP] = u0 * (U[IP] + p0);
+}
+
+// Logarithmic mean (a - b)/(ln a - ln b); for nearly equal arguments the series of artanh(f)/f,
+// f = (a - b)/(a + b), to f^8 when f^2 < 1e-4.
+template <class R> __device__ __forceinline__ R log_mean(R a, R b) {
+    const R f = (a - b) / (a + b);
+    const R u = f * f;
+    if (u < R(1e-4)) {
+        const R s = R(1) + u * (R(1.0 / 3.0) + u * (R(1.0 / 5.0) + u * (R(1.0 / 7.0) + u * R(1.0 / 9.0))));
+        return (a + b) / (R(2) * s);
+    }
+    return (a - b) / log(a / b);
+}
+
+// Two-point entropy-conservative flux for the entropy -rho s/(gamma-1) (Ismail-Roe): satisfies
+// Tadmor's condition (v_R - v_L) . F = psi_R - psi_L. The fourth-order entropy-conservative flux
+// of LeFloch-Mercier-Rohde combines three of them over four cells (in the stage kernels).
+template <class R, int ND, int D>
+__device__ __forceinline__ void ec_flux(const R* WL, const R* WR, R* F, R gamma) {
+    constexpr int IP = ND + 1;
+    const R g = gamma;
+    const R z1L = sqrt(WL[0] / WL[IP]), z1R = sqrt(WR[0] / WR[IP]);
+    const R z3L = sqrt(WL[0] * WL[IP]), z3R = sqrt(WR[0] * WR[IP]);
+    const R z1m = R(0.5) * (z1L + z1R), z3m = R(0.5) * (z3L + z3R);
+    const R z1l = log_mean(z1L, z1R), z3l = log_mean(z3L, z3R);
+    const R rho = z1m * z3l;
+    R u[ND];
+    R q2 = R(0);
+#pragma unroll
+    for (int j = 0; j < ND; ++j) {
+        u[j] = R(0.5) * (z1L * WL[1 + j] + z1R * WR[1 + j]) / z1m;
+        q2 = q2 + u[j] * u[j];
+    }
+    const R p1 = z3m / z1m;
+    const R p2 = (g + R(1)) / (R(2) * g) * z3l / z1l + (g - R(1)) / (R(2) * g) * z3m / z1m;
+    const R H = g * p2 / ((g - R(1)) * rho) + R(0.5) * q2;
+    const R mf = rho * u[D];
+    F[0] = mf;
+#pragma unroll
+    for (int j = 0; j < ND; ++j) F[1 + j] = mf * u[j];
+    F[1 + D] = F[1 + D] + p1;
+    F[IP] = mf * H;
+}
+
 template <class R, int ND, int D, int FLUX>
 __device__ __forceinline__ void euler_flux(const R* WL, const R* WR, R* F, R gamma, R gm1, R inv_gm1) {
+    if constexpr (FLUX == FLX_ROE) {
+        roe_flux<R, ND, D>(WL, WR, F, gamma, gm1, inv_gm1);
+        return;
+    }
+    if constexpr (FLUX == FLX_GODUNOV) {
+        godunov_flux<R, ND, D>(WL, WR, F, gamma, gm1, inv_gm1);
+        return;
+    }
+    if constexpr (FLUX == FLX_EC || FLUX == FLX_EC4) {
+        ec_flux<R, ND, D>(WL, WR, F, gamma);
+        return;
+    }
     if constexpr (FLUX == FLX_HLLC && !IsExact<R>::value) {
         hllc_fast<R, ND, D>(WL, WR, F, gamma, gm1, inv_gm1);
         return;
@@ -322,7 +537,18 @@ __device__ __forceinline__ void euler_flux(const R* WL, const R* WR, R* F, R gam
 
 // Scalar Burgers flux f(u) = u^2/2: Rusanov or HLL (HLLC coincides with HLL for a scalar law).
 template <class R, int FLUX> __device__ __forceinline__ R burgers_flux(R uL, R uR) {
+    if (FLUX == FLX_EC || FLUX == FLX_EC4) return (uL * uL + uL * uR + uR * uR) / R(6);   // entropy u^2/2
     const R fL = R(0.5) * uL * uL, fR = R(0.5) * uR * uR;
+    if (FLUX == FLX_ROE) {
+        const R a = R(0.5) * (uL + uR);   // Roe speed, Harten's fix on the transonic rarefaction
+        return R(0.5) * (fL + fR) - R(0.5) * harten_abs(a, uL, uR) * (uR - uL);
+    }
+    if (FLUX == FLX_GODUNOV) {            // exact solution at x/t = 0
+        if (uL > uR) return uL + uR >= R(0) ? fL : fR;
+        if (uL >= R(0)) return fL;
+        if (uR <= R(0)) return fR;
+        return R(0);
+    }
     if (FLUX == FLX_RUSANOV) {
         const R a = fmax_(fabs_(uL), fabs_(uR));
         return R(0.5) * (fL + fR) - R(0.5) * a * (uR - uL);

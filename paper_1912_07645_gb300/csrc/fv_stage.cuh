@@ -77,11 +77,11 @@ template <class R, int NV, int CS> __device__ __forceinline__ void sts_cell(R* p
     }
 }
 
-template <class R, int EQ, int ND, int RECON, int TX, int TY, int TZ>
+template <class R, int EQ, int ND, int RECON, int TX, int TY, int TZ, int FLUX = FLX_HLLC>
 constexpr size_t stage_smem_bytes() {
     constexpr int NV = (EQ == EQ_BURGERS) ? 1 : ND + 2;
     constexpr int CS = cell_stride<R, NV>();
-    constexpr int G = (RECON == REC_PC) ? 1 : 2;
+    constexpr int G = ghost_width(RECON, FLUX);
     constexpr int SX = TX + 2 * G, SY = ND >= 2 ? TY + 2 * G : 1, SZ = ND >= 3 ? TZ + 2 * G : 1;
     constexpr int NIX = (TX + 1) * TY * TZ;
     constexpr int NIY = ND >= 2 ? TX * (TY + 1) * TZ : 0;
@@ -217,12 +217,22 @@ __device__ __forceinline__ int halo_cell(const GridArgs& g, int ix, int iy, int 
     return f;
 }
 
+// entropy-conservative two-point flux along a runtime direction (unrolled loops make D a constant)
+template <class R, int ND>
+__device__ __forceinline__ void ec_flux_dir(int D, const R* WL, const R* WR, R* F, R gamma) {
+    if (D == 0) ec_flux<R, ND, 0>(WL, WR, F, gamma);
+    if (D == 1) ec_flux<R, ND, (ND >= 2 ? 1 : 0)>(WL, WR, F, gamma);
+    if (D == 2) ec_flux<R, ND, (ND >= 3 ? 2 : 0)>(WL, WR, F, gamma);
+}
+
 // RV: reconstruction variables (primitive or conserved) as a compile-time choice, so that each
 // instantiation carries only its own conversion path
 template <class R, int EQ, int ND, int RECON, int FLUX, int TX, int TY, int TZ, int NT, int RV = RV_PRIM>
 __global__ void __launch_bounds__(NT) k_stage(const StageArgs p) {
     constexpr int NV = (EQ == EQ_BURGERS) ? 1 : ND + 2;
-    constexpr int G = (RECON == REC_PC) ? 1 : 2;
+    constexpr int G = ghost_width(RECON, FLUX);
+    constexpr bool EC = FLUX == FLX_EC || FLUX == FLX_EC4;   // cell values, no reconstruction
+    static_assert(!EC || RV == RV_PRIM, "entropy-conservative fluxes read primitive cell values");
     constexpr int SX = TX + 2 * G, SY = ND >= 2 ? TY + 2 * G : 1, SZ = ND >= 3 ? TZ + 2 * G : 1;
     constexpr int NS = SX * SY * SZ;
     constexpr int NIX = (TX + 1) * TY * TZ;
@@ -333,6 +343,32 @@ __global__ void __launch_bounds__(NT) k_stage(const StageArgs p) {
             if (D == 2) cz -= 1;
             const int i0 = (cz * SY + cy) * SX + cx;
             R WL[NV], WR[NV], F[NV];
+            if constexpr (EC) {
+                // entropy-conservative: the two-point flux of the interface's cells; EC4 (fourth
+                // order, LeFloch-Mercier-Rohde) 4/3 F(w_i, w_{i+1}) - 1/6 (F(w_{i-1}, w_{i+1}) +
+                // F(w_i, w_{i+2}))
+                R cl[NV], cr[NV];
+                lds_cell<R, NV, CS>(sW + i0 * CS, cl);
+                lds_cell<R, NV, CS>(sW + (i0 + step) * CS, cr);
+                if (EQ == EQ_BURGERS) F[0] = burgers_flux<R, FLUX>(cl[0], cr[0]);
+                else ec_flux_dir<R, ND>(D, cl, cr, F, gamma);
+                if constexpr (FLUX == FLX_EC4) {
+                    R cm[NV], c2[NV], Fb[NV], Fc[NV];
+                    lds_cell<R, NV, CS>(sW + (i0 - step) * CS, cm);
+                    lds_cell<R, NV, CS>(sW + (i0 + 2 * step) * CS, c2);
+                    if (EQ == EQ_BURGERS) {
+                        Fb[0] = burgers_flux<R, FLUX>(cm[0], cr[0]);
+                        Fc[0] = burgers_flux<R, FLUX>(cl[0], c2[0]);
+                    } else {
+                        ec_flux_dir<R, ND>(D, cm, cr, Fb, gamma);
+                        ec_flux_dir<R, ND>(D, cl, c2, Fc, gamma);
+                    }
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) F[v] = R(4.0 / 3.0) * F[v] - R(1.0 / 6.0) * (Fb[v] + Fc[v]);
+                }
+                sts_cell<R, NV, CS>(sF + f * CS, F);
+                continue;
+            }
             interface_states<R, EQ, ND, RECON, CS>(sW, i0, step, RV, gm1, eps, WL, WR);
             if (EQ == EQ_BURGERS) {
                 F[0] = burgers_flux<R, FLUX>(WL[0], WR[0]);

@@ -1,0 +1,129 @@
+"""GPU parity of the further numerics of Sec. 2.1 - Roe (entropy-fixed), exact Godunov, the two-point
+and fourth-order entropy-conservative fluxes, ENO2 reconstruction - against the FP64 oracle, through
+the C ABI: FP64 per cell within 1e-12 relative (near-zero floor as in P1), FP32 within 2e-5
+relative L1, after 1 and 10 steps and over whole shock-tube runs; unsupported combinations are
+rejected at alsv_init_grid."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from harness import gpu_solver, host, need_gpu, p1_check, p2_check
+from inputs import burgers_state, euler_state
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    need_gpu()
+    from paper_1912_07645_gb300 import build
+    build.build()
+
+
+def _run(cfg, U0, steps=None, T=None):
+    import torch
+    S = gpu_solver(**cfg)
+    S.set_state(torch.from_numpy(np.ascontiguousarray(U0)))
+    if steps is not None:
+        S.step(steps)
+        S.sync()
+    else:
+        S.evolve_to(T)
+    g = host(S.U).reshape(S.level_shape(0))
+    t, st = S.time()
+    S.close()
+    d = oracle.make_desc(**cfg)
+    if steps is not None:
+        o, ost, ot = oracle.evolve(d, U0, T=math.inf, max_steps=steps)
+    else:
+        o, ost, ot = oracle.evolve(d, U0, T=T)
+    assert np.array_equal(st, ost)
+    return g, o
+
+
+def _check(cfg, g, o, what):
+    if cfg["precision"] == "fp64":
+        p1_check(g, o, what=what)
+    else:
+        p2_check(g, o, what=what)
+
+
+SCHEMES = [("roe", "pc"), ("roe", "mc"), ("roe", "weno3"), ("roe", "eno2"), ("godunov", "pc"), ("godunov", "mc"),
+           ("godunov", "weno3"), ("godunov", "eno2"), ("hllc", "eno2"), ("rusanov", "eno2"), ("hll", "eno2"),
+           ("ec", "pc"), ("ec4", "pc")]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("flux,recon", SCHEMES)
+def test_euler_1d_2d_vs_oracle(flux, recon, precision):
+    """Smooth random states (every scheme, entropy-conservative ones included, stays physical):
+    1D ragged 1000 cells with outflow ends (periodic for EC), 2D 70 x 45 with reflective and
+    periodic faces (periodic for EC), 1 and 10 steps."""
+    for nd, n, bc in ((1, (1000,), "outflow"), (2, (70, 45), [("reflective", "reflective"), ("periodic", "periodic")])):
+        if flux in ("ec", "ec4"):
+            bc = "periodic"
+        cfg = dict(ndim=nd, n=n, batch=2, eq="euler", recon=recon, flux=flux, rvars="prim", rk="ssprk3", bc=bc,
+                   cfl=0.4, precision=precision)
+        U0 = euler_state(2, nd, n, seed=41 + nd)
+        for steps in (1, 10):
+            g, o = _run(cfg, U0, steps=steps)
+            _check(cfg, g, o, f"{nd}D {flux}/{recon} {precision} {steps} steps")
+
+
+@pytest.mark.parametrize("flux,recon,precision", [("roe", "weno3", "fp64"), ("godunov", "mc", "fp32"),
+                                                  ("ec4", "pc", "fp64"), ("hllc", "eno2", "fp32"), ("ec", "pc", "fp32")])
+def test_euler_3d_vs_oracle(flux, recon, precision):
+    n = (17, 9, 13)
+    bc = "periodic" if flux in ("ec", "ec4") else [("periodic", "periodic"), ("outflow", "reflective"), ("periodic", "periodic")]
+    cfg = dict(ndim=3, n=n, batch=1, eq="euler", recon=recon, flux=flux, rvars="prim", rk="ssprk3", bc=bc, cfl=0.3,
+               precision=precision)
+    U0 = euler_state(1, 3, n, seed=47)
+    g, o = _run(cfg, U0, steps=6)
+    _check(cfg, g, o, f"3D {flux}/{recon} {precision}")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("flux,recon", [("roe", "pc"), ("roe", "weno3"), ("godunov", "mc"), ("godunov", "eno2"),
+                                        ("rusanov", "eno2"), ("hll", "eno2"), ("ec", "pc"), ("ec4", "pc")])
+def test_burgers_1d_vs_oracle(flux, recon, precision):
+    cfg = dict(ndim=1, n=(333,), batch=3, eq="burgers", recon=recon, flux=flux, rk="ssprk2", bc="periodic", cfl=0.4,
+               precision=precision)
+    U0 = burgers_state(3, 333, seed=5)
+    g, o = _run(cfg, U0, steps=10)
+    _check(cfg, g, o, f"burgers {flux}/{recon} {precision}")
+
+
+@pytest.mark.parametrize("flux,recon", [("roe", "pc"), ("roe", "mc"), ("godunov", "mc"), ("godunov", "weno3"),
+                                        ("hllc", "eno2")])
+def test_sod_full_run_fp64(flux, recon):
+    """Sod to T = 0.2 (1024 cells, the shock-tube configuration's size) with each new scheme: the
+    FP64 GPU path evaluates the oracle's operations in the oracle's order, so the whole run stays
+    within the per-cell rule (Godunov's rarefaction branch calls pow on both sides)."""
+    cfg = dict(ndim=1, n=(1024,), batch=1, eq="euler", recon=recon, flux=flux, rvars="prim", rk="ssprk2",
+               bc="outflow", cfl=0.45, precision="fp64")
+    d = oracle.make_desc(**cfg)
+    U0 = oracle.init(d, "sod")
+    g, o = _run(cfg, U0, T=0.2)
+    p1_check(g, o, what=f"sod {flux}/{recon}")
+
+
+def test_unsupported_combinations_are_rejected():
+    import paper_1912_07645_gb300 as alsv
+    torch = need_gpu()
+    for kw, msg in ((dict(ndim=2, n=(16, 16), eq="burgers", flux="roe"), "1D only"),
+                    (dict(ndim=2, n=(16, 16), eq="euler", flux="godunov", rvars="cons"), "primitive"),
+                    (dict(ndim=1, n=(16,), eq="euler", recon="eno2", flux="hllc", rvars="cons"), "primitive")):
+        with pytest.raises(alsv.AlsvError, match=msg):
+            gpu_solver(batch=1, precision="fp64", **kw)
+    S = gpu_solver(ndim=2, n=(32, 32), batch=2, eq="euler", recon="mc", flux="roe", rvars="prim", precision="fp32")
+    for v in range(1, alsv.alsv_num_tile_variants(S.ctx)):
+        with pytest.raises(alsv.AlsvError, match="does not support"):
+            alsv.alsv_set_tile_variant(S.ctx, v)
+    S.close()
+    # the entropy-conservative fluxes ignore recon_vars (cell values in primitive form)
+    cfg = dict(ndim=1, n=(64,), batch=1, eq="euler", flux="ec4", rvars="cons", bc="periodic", cfl=0.4, precision="fp64")
+    U0 = euler_state(1, 1, (64,), seed=3)
+    g, o = _run(cfg, U0, steps=5)
+    p1_check(g, o, what="ec4 with recon_vars cons")

@@ -323,7 +323,13 @@ WORKLOADS = {
                                             seed=SEED), adjoint=True, T=0.01),
     "adjoint512_fp64": dict(desc=dict(ndim=2, n=(512, 512), batch=64, eq="euler", recon="mc", flux="rusanov",
                                       rvars="prim", rk="ssprk2", bc="periodic", cfl=0.4, precision="fp64", seed=SEED),
-                            adjoint=True, T=0.05),
+                            adjoint=True, T=1.0),
+    # agreement of the FP64 adjoint gradient with central differences formed inside one batch
+    # (sample 0 of the ensemble, +-h on six of the 20 parameters: 13 samples) at growing horizons
+    "adjoint512_fp64_fd": dict(desc=dict(ndim=2, n=(512, 512), batch=13, eq="euler", recon="mc", flux="rusanov",
+                                         rvars="prim", rk="ssprk2", bc="periodic", cfl=0.4, precision="fp64",
+                                         seed=SEED), adjoint=True, fd_check=(0.01, 0.1, 0.3, 0.6, 1.0),
+                               fd_params=(0, 3, 7, 10, 13, 17)),
 }
 
 
@@ -334,6 +340,48 @@ WORKLOAD_FLOPS = {"sod1024_fp64": 287, "kh2d1024_fp32": 1980, "kh2d1024_fp64": 1
                   "mlmc_coupled_fp32": 1980, "kh3d512_fp32": 3591, "kh3d256_fp32": 3591,
                   "kh3d1024_blocks_fp32": 3591, "kh3d256_blocks_fp32": 3591}
 FP64_PEAK_TFLOPS = 1.25
+
+
+def run_adjoint_fd_check(name, W, S, alsv, torch):
+    """FP64 adjoint gradient of the kinetic energy at T against central differences formed inside
+    one batch (h = 1e-6 max(1, |theta_j|)), for each horizon T of the workload: the largest
+    |g_j - fd_j| over the checked parameters relative to max_j |g_j|, with the plan used."""
+    import numpy as np
+    P = W["fd_params"]
+    B = 1 + 2 * len(P)
+    S.set_initial_data("kh")
+    th0 = torch.empty((S.samples, 20), dtype=torch.float64, device="cuda")
+    alsv.alsv_get_parameters(S.ctx, th0)
+    S.sync()
+    base = th0[0].cpu().numpy()
+    th = np.tile(base, (B, 1))
+    hs = 1e-6 * np.maximum(1.0, np.abs(base))
+    for i, j in enumerate(P):
+        th[1 + 2 * i, j] += hs[j]
+        th[2 + 2 * i, j] -= hs[j]
+    tth = torch.from_numpy(th).cuda()
+    rows = []
+    for T in W["fd_check"]:
+        t0 = time.perf_counter()
+        J, g = S.adjoint(tth, T)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        J, g = J.cpu().numpy(), g.cpu().numpy()
+        nst, dt_fixed, passes = alsv.alsv_adjoint_get_plan(S.ctx)
+        fd = np.array([(J[1 + 2 * i] - J[2 + 2 * i]) / (2 * hs[j]) for i, j in enumerate(P)])
+        gsel = g[0, list(P)]
+        rows.append({"T": T, "steps": int(nst), "passes": int(passes), "J": float(J[0]),
+                     "max_abs_grad": float(np.abs(g[0]).max()),
+                     "rel_diff_vs_fd": float(np.abs(gsel - fd).max() / np.abs(g[0]).max()),
+                     "per_param_rel": [float(abs(a - b) / max(abs(b), 1e-300)) for a, b in zip(gsel, fd)],
+                     "seconds": el})
+    line = {"metric": "adjoint gradient vs central differences (FP64, KE, 512^2 KH)", "value": rows[-1]["rel_diff_vs_fd"],
+            "unit": "max |g - fd| / max |g|", "higher_is_better": False, "n_gpus": 1,
+            "config": {"workload": name, "grid": [512, 512], "samples": B, "params_checked": list(P)},
+            "horizons": rows, "gpu_launches": alsv.alsv_get_launch_count(S.ctx)}
+    print(json.dumps(line), flush=True)
+    S.close()
+    return 0
 
 
 def run_blocks_workload(name, W, args):
@@ -445,6 +493,8 @@ def run_workload(name, args):
     desc = alsv.make_desc(**W["desc"])
     S = alsv.Solver(desc)
     peaks, peak_kind = measured_peaks()
+    if W.get("fd_check"):
+        return run_adjoint_fd_check(name, W, S, alsv, torch)
     if W.get("adjoint"):
         S.set_initial_data("kh")
         # the forward sweeps run the context's stage schedule: pick the fastest for this shape

@@ -106,7 +106,11 @@ StageArgs stage_args(alsv_ctx* c, const void* Us, const void* Un, void* Uout, do
     s.Uout = Uout;
     s.a = a;
     s.b = b;
+    s.a_f = (float)a;
+    s.b_f = (float)b;
+    s.has_un = a != 0.0 ? 1 : 0;
     s.dt = c->dt;
+    s.dt_f = c->dt_f;
     s.done = c->done;
     s.speed_part = c->part;
     s.want_speed = want_speed ? 1 : 0;
@@ -120,6 +124,7 @@ FinishArgs finish_args(alsv_ctx* c, int advance) {
     f.speed_part = c->part;
     f.t = c->t;
     f.dt = c->dt;
+    f.dt_f = c->dt_f;
     f.nstep = c->nstep;
     f.done = c->done;
     f.last = c->last;
@@ -505,6 +510,7 @@ alsv_status alsv_init_grid(const alsv_grid_desc* d_in, void* stream, alsv_ctx** 
     }
     g.weno_eps = d.weno_eps;
     g.weno_eps_dx2 = d.weno_eps_dx2;
+    fill_float_consts(g);
     for (int k = 0; k < 3; ++k) g.off[k] = d.offset[k];
     // tiling: keep the largest work count over variants for the partials buffer
     long long mx = 0;
@@ -525,7 +531,7 @@ alsv_status alsv_init_grid(const alsv_grid_desc* d_in, void* stream, alsv_ctx** 
     if (c->nstages == 3) ws += align256(c->state_bytes);          // B
     ws += align256((size_t)mx * 8);                               // partials
     ws += 3 * align256((size_t)samples * 8);                      // t, dt, nstep
-    ws += 2 * align256((size_t)samples * 4);                      // done, last
+    ws += 3 * align256((size_t)samples * 4);                      // done, last, FP32 dt
     ws += 256;                                                    // status
     ws += 256;                                                    // T_end, n_target, cfl_max
     ws += align256((size_t)samples * std::max(c->P, 1) * 8);      // theta
@@ -554,6 +560,7 @@ alsv_status alsv_bind_workspace(alsv_ctx* c, void* dev, size_t bytes) {
     c->nstep = (int64_t*)p; p += align256(S * 8);
     c->done = (int*)p; p += align256(S * 4);
     c->last = (int*)p; p += align256(S * 4);
+    c->dt_f = (float*)p; p += align256(S * 4);
     c->status = (int*)p; p += 256;
     c->T_end = (double*)p;
     c->n_target = (long long*)(p + 8);

@@ -36,6 +36,7 @@ struct alsv_ctx {
     double* part = nullptr;
     double* t = nullptr;
     double* dt = nullptr;
+    float* dt_f = nullptr;
     int64_t* nstep = nullptr;
     int* done = nullptr;
     int* last = nullptr;

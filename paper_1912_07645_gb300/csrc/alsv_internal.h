@@ -56,6 +56,8 @@ struct LevelInfo {
     long long work0;   // first (sample, tile) work item of the level
     double dx[3];
     double inv_dx[3];
+    float inv_dx_f[3]; // FP32 copies for the single-precision kernels (a double->float conversion
+    float eps_f[3];    // runs on the FP64 pipe, very narrow on this GPU): 1/dx, WENO epsilon
     FastDiv fd_tiles;  // divisors for the (sample, tile) decomposition of a work item
     FastDiv fd_nt0;    // tiles along x
     FastDiv fd_nt1;    // tiles along y
@@ -72,12 +74,26 @@ struct GridArgs {
     int total_samples;
     int nv;
     double gamma;
+    float gamma_f, gm1_f, inv_gm1_f;  // FP32 copies: gamma, gamma - 1, 1 / (gamma - 1)
     int rvars;
     int bc[3][2];
     double weno_eps;
     int weno_eps_dx2;
     int off[3];        // block of a decomposed grid: global index of the first cell per direction
 };
+
+// FP32 copies of the grid's constants (computed once on the host; the stage kernels read them
+// instead of converting the doubles in every thread).
+inline void fill_float_consts(GridArgs& g) {
+    g.gamma_f = (float)g.gamma;
+    g.gm1_f = g.gamma_f - 1.0f;
+    g.inv_gm1_f = 1.0f / g.gm1_f;
+    for (int l = 0; l < kMaxLevels; ++l)
+        for (int k = 0; k < 3; ++k) {
+            g.lev[l].inv_dx_f[k] = (float)g.lev[l].inv_dx[k];
+            g.lev[l].eps_f[k] = g.weno_eps_dx2 ? (float)(g.lev[l].dx[k] * g.lev[l].dx[k]) : (float)g.weno_eps;
+        }
+}
 
 // One SSP-RK stage: Uout = a * Un + b * (Us + dt * L(Us)); a == 0 means Un is not read.
 struct StageArgs {
@@ -86,7 +102,10 @@ struct StageArgs {
     const void* Un;
     void* Uout;
     double a, b;
+    float a_f, b_f;       // FP32 copies of a, b
+    int has_un;           // a != 0
     const double* dt;     // [samples]
+    const float* dt_f;    // [samples] FP32 copy of dt (written with it)
     const int* done;      // [samples]; nonzero: the sample is skipped
     double* speed_part;   // [work items]; written when want_speed
     int want_speed;
@@ -122,6 +141,7 @@ struct FinishArgs {
     const double* speed_part;
     double* t;
     double* dt;
+    float* dt_f;           // FP32 copy of dt, for the single-precision stage kernels
     int64_t* nstep;
     int* done;
     int* last;

@@ -42,12 +42,11 @@ __global__ void __launch_bounds__(32 * kColWarps) k_stage2d_col(const StageArgs 
     const float* Us = reinterpret_cast<const float*>(p.Us) + sbase;
     const float* Un = reinterpret_cast<const float*>(p.Un) + sbase;
     float* Uo = reinterpret_cast<float*>(p.Uout) + sbase;
-    const float gamma = (float)g.gamma, gm1 = gamma - 1.0f, inv_gm1 = 1.0f / gm1;
-    const float2 eps = g.weno_eps_dx2 ? make_float2((float)(Lv.dx[0] * Lv.dx[0]), (float)(Lv.dx[1] * Lv.dx[1]))
-                                      : f2((float)g.weno_eps);
-    const float idx = (float)Lv.inv_dx[0], idy = (float)Lv.inv_dx[1];
-    const float dt = (float)p.dt[sample], ca = (float)p.a, cb = (float)p.b;
-    const bool has_un = p.a != 0.0, want_speed = p.want_speed != 0;
+    const float gamma = g.gamma_f, gm1 = g.gm1_f, inv_gm1 = g.inv_gm1_f;
+    const float2 eps = make_float2(Lv.eps_f[0], Lv.eps_f[1]);
+    const float idx = Lv.inv_dx_f[0], idy = Lv.inv_dx_f[1];
+    const float dt = p.dt_f[sample], ca = p.a_f, cb = p.b_f;
+    const bool has_un = p.has_un != 0, want_speed = p.want_speed != 0;
 
     const int x0 = (int)strip * kColOwned;
     const int xs = x0 + lane;                  // this lane's column (>= nx on a partial last strip)

@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(NT, TY >= 16 ? 4 : 5) k_stage2d_pair(const Sta
     const long long bA = L.elem0 + (long long)sA * 4 * plane, bB = L.elem0 + (long long)sB * 4 * plane;
     const float* UsA = reinterpret_cast<const float*>(p.Us) + bA;
     const float* UsB = reinterpret_cast<const float*>(p.Us) + bB;
-    const float gamma = (float)g.gamma, gm1 = gamma - 1.0f, inv_gm1 = 1.0f / gm1;
+    const float gamma = g.gamma_f, gm1 = g.gm1_f, inv_gm1 = g.inv_gm1_f;
     const int tid = threadIdx.x;
 
     // ---- 1. tile + halo load (both samples), boundary fill, primitive conversion. The loads of
@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(NT, TY >= 16 ? 4 : 5) k_stage2d_pair(const Sta
         const int EX = TX + (D == 0), EY = TY + (D == 1);
         const int NID = EX * EY;
         const int step = D == 0 ? 1 : SX;
-        const float epsD = g.weno_eps_dx2 ? (float)(L.dx[D] * L.dx[D]) : (float)g.weno_eps;
+        const float epsD = L.eps_f[D];
         const float2 eps = f2(epsD);
 #pragma unroll 1
         for (int f = tid; f < NID; f += NT) {
@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(NT, TY >= 16 ? 4 : 5) k_stage2d_pair(const Sta
             sF1[f] = make_float4(fym.x, fym.y, F.p.x, F.p.y);
         }
         __syncthreads();
-        const float2 nidx = f2(-(float)L.inv_dx[D]);
+        const float2 nidx = f2(-L.inv_dx_f[D]);
         const int fstep = D == 0 ? 1 : TX;
 #pragma unroll
         for (int m = 0; m < CPT; ++m) {
@@ -203,14 +203,14 @@ __global__ void __launch_bounds__(NT, TY >= 16 ? 4 : 5) k_stage2d_pair(const Sta
     }
 
     // ---- 3. RK combination, store per sample, CFL speed of the new states
-    const float2 dt = make_float2((float)p.dt[L.sample0 + sA], (float)p.dt[L.sample0 + sB]);
-    const float2 ca = f2((float)p.a), cb = f2((float)p.b);
-    const bool has_un = p.a != 0.0, want_speed = p.want_speed != 0;
+    const float2 dt = make_float2(p.dt_f[L.sample0 + sA], p.dt_f[L.sample0 + sB]);
+    const float2 ca = f2(p.a_f), cb = f2(p.b_f);
+    const bool has_un = p.has_un != 0, want_speed = p.want_speed != 0;
     const float* UnA = reinterpret_cast<const float*>(p.Un) + bA;
     const float* UnB = reinterpret_cast<const float*>(p.Un) + bB;
     float* UoA = reinterpret_cast<float*>(p.Uout) + bA;
     float* UoB = reinterpret_cast<float*>(p.Uout) + bB;
-    const float idx = (float)L.inv_dx[0], idy = (float)L.inv_dx[1];
+    const float idx = L.inv_dx_f[0], idy = L.inv_dx_f[1];
     float2 smax = f2(0.f);
     bool badA = false, badB = false;
 #pragma unroll

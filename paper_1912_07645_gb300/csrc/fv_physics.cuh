@@ -18,6 +18,33 @@ template <> struct IsExact<double> { static constexpr bool value = true; };
 
 template <class R> __device__ __forceinline__ R rcp(R x) { return R(1) / x; }
 
+// Grid and stage constants in the kernel's precision: FP64 reads the doubles, FP32 the float copies
+// made on the host (or by the time control for dt), so no thread converts a double to float.
+template <class R> __device__ __forceinline__ R c_gamma(const GridArgs& g) {
+    if constexpr (IsExact<R>::value) return g.gamma;
+    else return g.gamma_f;
+}
+template <class R> __device__ __forceinline__ R c_inv_dx(const LevelInfo& L, int k) {
+    if constexpr (IsExact<R>::value) return L.inv_dx[k];
+    else return L.inv_dx_f[k];
+}
+template <class R> __device__ __forceinline__ R c_eps(const GridArgs& g, const LevelInfo& L, int k) {
+    if constexpr (IsExact<R>::value) return g.weno_eps_dx2 ? L.dx[k] * L.dx[k] : g.weno_eps;
+    else return L.eps_f[k];
+}
+template <class R> __device__ __forceinline__ R c_dt(const StageArgs& p, int s) {
+    if constexpr (IsExact<R>::value) return p.dt[s];
+    else return p.dt_f[s];
+}
+template <class R> __device__ __forceinline__ R c_a(const StageArgs& p) {
+    if constexpr (IsExact<R>::value) return p.a;
+    else return p.a_f;
+}
+template <class R> __device__ __forceinline__ R c_b(const StageArgs& p) {
+    if constexpr (IsExact<R>::value) return p.b;
+    else return p.b_f;
+}
+
 // FP32 fast forms (MUFU reciprocal / reciprocal square root, about 2 ulp)
 __device__ __forceinline__ float rcp_approx(float x) {
     float r;

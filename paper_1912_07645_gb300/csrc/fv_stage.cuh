@@ -23,7 +23,7 @@ template <int ND, int TX, int TY, int TZ> struct TileGeom {
 // CFL wave speed (|u_k| + c) / dx_k of one direction
 template <class R> __device__ __forceinline__ R speed_over_dx(R s, const LevelInfo& L, int k) {
     if constexpr (IsExact<R>::value) return s / R(L.dx[k]);
-    else return s * R(L.inv_dx[k]);
+    else return s * L.inv_dx_f[k];
 }
 // the same with the per-direction factor already converted: dx_k (FP64) or 1/dx_k (FP32)
 template <class R> __device__ __forceinline__ R speed_dx(R s, R f) {
@@ -268,9 +268,9 @@ __global__ void __launch_bounds__(NT) k_stage(const StageArgs p) {
     const long long sbase = L.elem0 + (long long)b_local * NV * plane;
     const R* Us = reinterpret_cast<const R*>(p.Us) + sbase;
 
-    const R gamma = R(g.gamma);
-    const R gm1 = gamma - R(1);
-    const R inv_gm1 = R(1) / gm1;
+    const R gamma = c_gamma<R>(g);
+    const R gm1 = IsExact<R>::value ? gamma - R(1) : R(g.gm1_f);
+    const R inv_gm1 = IsExact<R>::value ? R(1) / gm1 : R(g.inv_gm1_f);
     const int tid = threadIdx.x;
 
     // ---- 1. tile + halo load with boundary fill and variable conversion
@@ -330,7 +330,7 @@ __global__ void __launch_bounds__(NT) k_stage(const StageArgs p) {
         const int EX = TX + (D == 0), EY = TY + (D == 1), EZ = TZ + (D == 2);
         const int NID = EX * EY * EZ;
         const int step = D == 0 ? 1 : (D == 1 ? SX : SX * SY);
-        const R eps = g.weno_eps_dx2 ? R(L.dx[D] * L.dx[D]) : R(g.weno_eps);
+        const R eps = c_eps<R>(g, L, D);
 #pragma unroll 1
         for (int f = tid; f < NID; f += NT) {
             const int fx = f % EX;
@@ -380,8 +380,8 @@ __global__ void __launch_bounds__(NT) k_stage(const StageArgs p) {
             sts_cell<R, NV, CS>(sF + f * CS, F);
         }
         __syncthreads();
-        const R inv_dx = R(L.inv_dx[D]);
-        const R hD = R(L.dx[D]);
+        const R inv_dx = c_inv_dx<R>(L, D);
+        const R hD = IsExact<R>::value ? R(L.dx[D]) : R(0);
         const int fstep = D == 0 ? 1 : (D == 1 ? TX : TX * TY);
 #pragma unroll
         for (int m = 0; m < CPT; ++m) {
@@ -403,13 +403,13 @@ __global__ void __launch_bounds__(NT) k_stage(const StageArgs p) {
     }
 
     // ---- 3. RK combination and store; wave speed of the new state
-    const R dt = R(p.dt[sample]);
-    const R ca = R(p.a), cb = R(p.b);
-    const bool has_un = p.a != 0.0;           // loop invariants, converted once
+    const R dt = c_dt<R>(p, sample);
+    const R ca = c_a<R>(p), cb = c_b<R>(p);
+    const bool has_un = p.has_un != 0;        // loop invariants
     const bool want_speed = p.want_speed != 0;
     R sdx[ND];
 #pragma unroll
-    for (int k = 0; k < ND; ++k) sdx[k] = IsExact<R>::value ? R(L.dx[k]) : R(L.inv_dx[k]);
+    for (int k = 0; k < ND; ++k) sdx[k] = IsExact<R>::value ? R(L.dx[k]) : c_inv_dx<R>(L, k);
     const R* Un = reinterpret_cast<const R*>(p.Un) + sbase;
     R* Uo = reinterpret_cast<R*>(p.Uout) + sbase;
     R smax = R(0);

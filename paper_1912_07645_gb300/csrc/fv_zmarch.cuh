@@ -62,7 +62,8 @@ __global__ void __launch_bounds__(NTH, 4) k_stage3d_zm(const StageArgs p) {
     const R* Un = reinterpret_cast<const R*>(p.Un) + sbase;
     R* Uo = reinterpret_cast<R*>(p.Uout) + sbase;
 
-    const R gamma = R(g.gamma), gm1 = gamma - R(1), inv_gm1 = R(1) / gm1;
+    const R gamma = c_gamma<R>(g), gm1 = IsExact<R>::value ? gamma - R(1) : R(g.gm1_f);
+    const R inv_gm1 = IsExact<R>::value ? R(1) / gm1 : R(g.inv_gm1_f);
     const int tid = threadIdx.x;
     const int cx = tid % TX, cy = tid / TX;
     const int X = tx0 + cx, Y = ty0 + cy;
@@ -117,9 +118,7 @@ __global__ void __launch_bounds__(NTH, 4) k_stage3d_zm(const StageArgs p) {
         for (int v = 0; v < NV; ++v) out[v] = src[v];
     };
     const int own_off = (cy + G) * SX + cx + G;
-    const R epsz = g.weno_eps_dx2 ? R(L.dx[2] * L.dx[2]) : R(g.weno_eps);
-    const R epsx = g.weno_eps_dx2 ? R(L.dx[0] * L.dx[0]) : R(g.weno_eps);
-    const R epsy = g.weno_eps_dx2 ? R(L.dx[1] * L.dx[1]) : R(g.weno_eps);
+    const R epsz = c_eps<R>(g, L, 2), epsx = c_eps<R>(g, L, 0), epsy = c_eps<R>(g, L, 1);
     auto zflux = [&](int zl, R* F) {   // flux at the interface between planes zl and zl + 1
         R cm[NV], cl[NV], cr[NV], c2[NV], WL[NV], WR[NV];
         cell_at(zl, own_off, cl);
@@ -138,11 +137,11 @@ __global__ void __launch_bounds__(NTH, 4) k_stage3d_zm(const StageArgs p) {
     R Fzm[NV];
     zflux(z0 - 1, Fzm);
 
-    const R dt = R(p.dt[sample]);
-    const R ca = R(p.a), cb = R(p.b);
-    const bool has_un = p.a != 0.0;
+    const R dt = c_dt<R>(p, sample);
+    const R ca = c_a<R>(p), cb = c_b<R>(p);
+    const bool has_un = p.has_un != 0;
     const bool want_speed = p.want_speed != 0;
-    const R idx = R(L.inv_dx[0]), idy = R(L.inv_dx[1]), idz = R(L.inv_dx[2]);
+    const R idx = c_inv_dx<R>(L, 0), idy = c_inv_dx<R>(L, 1), idz = c_inv_dx<R>(L, 2);
     R smax = R(0);
     bool bad = false;
 

@@ -81,6 +81,7 @@ __device__ void finish_sample(const FinishArgs& a, int s, double smax, int bad) 
     const double t = a.t[s];
     if (a.fixed_dt > 0.0) {
         a.dt[s] = a.fixed_dt;
+        a.dt_f[s] = (float)a.fixed_dt;
         a.last[s] = 0;
         const bool fin = a.nstep[s] >= *a.n_target;
         a.done[s] = fin ? 1 : 0;
@@ -102,6 +103,7 @@ __device__ void finish_sample(const FinishArgs& a, int s, double smax, int bad) 
     }
     if (isinf(dt)) dt = 0.0;  // no wave motion and no end time: nothing to advance
     a.dt[s] = dt;
+    a.dt_f[s] = (float)dt;
     a.last[s] = last;
     a.done[s] = 0;
 }

@@ -80,6 +80,7 @@ extern "C" alsv_status alsv_conservation_totals_noalloc(const alsv_grid_desc* d,
         elems += (long long)L.samples * g.nv * L.n[0] * L.n[1] * L.n[2];
     }
     if (samples > 65535) return bad(ALSV_ERR_INVALID_ARG, "at most 65535 samples");
+    fill_float_consts(g);
     g.total_samples = (int)samples;
     long long maxchunks = 0;
     for (int l = 0; l < g.nlev; ++l) {

@@ -171,7 +171,31 @@ def test_initial_data_fp64(case):
     g, *_ = run_gpu(cfg, init, th, steps=0)
     d = oracle.make_desc(**cfg)
     o = oracle.init(d, init, cfg.get("batch", 1), th, center=cfg.get("vortex_center", (5, 5)))
-    p1_check(g, o, rel=1e-13, what=case)
+    if init != "kh":
+        p1_check(g, o, rel=1e-13, what=case)
+        return
+    # KH: the interface height Y = 0.01 sum a sin(...) comes from CUDA's sin on the GPU and the C
+    # library's on the host, each within an ulp of the exact value but not always the same double.
+    # A height that differs by d moves the band's volume fraction in the cut cell by d / dy, so the
+    # cell's value moves by |U_in - U_out| d / dy: near zero where the blend of the two states
+    # passes through zero (the x-momentum 0.5 - 1.5 f), where per-cell relative error means little.
+    # Bound: 1e-13 |o| + |U_in - U_out| * 4 ulp(sum_n |0.01 a_n|) / dy, per variable.
+    g_ = 1.4
+    U_in = np.array([2.0, -1.0, 0.0, 0.0, 2.5 / (g_ - 1) + 0.25])
+    U_out = np.array([1.0, 0.5, 0.0, 0.0, 2.5 / (g_ - 1) + 0.125])
+    nv = o.shape[1]
+    jump = np.abs(U_in - U_out)[[0, 1] + list(range(2, nv - 1)) + [4]][:nv]
+    dy = 1.0 / cfg["n"][1]
+    P = th.shape[1] // 2
+    for b in range(o.shape[0]):
+        dY = 4 * np.spacing(0.01 * np.abs(th[b, :P]).sum())
+        for v in range(nv):
+            tol = 1e-13 * np.abs(o[b, v]) + jump[v] * dY / dy
+            bad = np.abs(g[b, v] - o[b, v]) > tol
+            assert not bad.any(), (case, b, v, np.abs(g[b, v] - o[b, v])[bad][:5], tol[bad][:5])
+    # and the cut cells do carry the sin difference: elsewhere the values are bitwise equal
+    far = (np.abs(o[:, 0] - 1.0) < 1e-300) | (np.abs(o[:, 0] - 2.0) < 1e-300)
+    assert np.array_equal(g[:, 0][far], o[:, 0][far])
 
 
 # ------------------------------------------------------------------ one and ten steps, FP64

@@ -43,7 +43,7 @@ STAGE_KERNEL_NAMES = {0: "k_stage<float, Euler, 2D, WENO3, HLLC, 32x16>",
                       4: "k_stage2d_pair<WENO3, HLLC, 32x16>",
                       5: "k_stage2d_pair<WENO3, HLLC, 32x8>",
                       8: "k_stage2d_pair2<WENO3, HLLC, 32x16>",
-                      9: "k_stage2d_pair2<WENO3, HLLC, 32x32>"}
+                      9: "k_stage2d_pair2<WENO3, HLLC, 32x16, merged directions>"}
 WORKLOAD = "kh2d_256x256_mc4096_weno3_hllc_ssprk3_fp32_T1"
 # compulsory HBM bytes per 2D SSP-RK3 cell-update in FP32: per variable read U^n + write U1,
 # read U1 + U^n + write U2, read U2 + U^n + write U^{n+1} = 8 words, x 4 variables x 4 bytes
@@ -329,7 +329,12 @@ WORKLOADS = {
     "adjoint512_fp64_fd": dict(desc=dict(ndim=2, n=(512, 512), batch=13, eq="euler", recon="mc", flux="rusanov",
                                          rvars="prim", rk="ssprk2", bc="periodic", cfl=0.4, precision="fp64",
                                          seed=SEED), adjoint=True, fd_check=(0.01, 0.1, 0.3, 0.6, 1.0),
-                               fd_params=(0, 3, 7, 10, 13, 17)),
+                               fd_params=(0, 3, 7, 10, 13, 17), fd_h=(1e-6,)),
+    # the same at the two horizons where h = 1e-6 straddles limiter kinks, with smaller steps
+    "adjoint512_fp64_fd_h": dict(desc=dict(ndim=2, n=(512, 512), batch=13, eq="euler", recon="mc", flux="rusanov",
+                                           rvars="prim", rk="ssprk2", bc="periodic", cfl=0.4, precision="fp64",
+                                           seed=SEED), adjoint=True, fd_check=(0.3, 0.6),
+                                 fd_params=(0, 3, 7, 10, 13, 17), fd_h=(1e-7, 1e-8)),
 }
 
 
@@ -344,7 +349,7 @@ FP64_PEAK_TFLOPS = 1.25
 
 def run_adjoint_fd_check(name, W, S, alsv, torch):
     """FP64 adjoint gradient of the kinetic energy at T against central differences formed inside
-    one batch (h = 1e-6 max(1, |theta_j|)), for each horizon T of the workload: the largest
+    one batch (h = h_rel max(1, |theta_j|)), for each step h_rel and horizon T of the workload: the largest
     |g_j - fd_j| over the checked parameters relative to max_j |g_j|, with the plan used."""
     import numpy as np
     P = W["fd_params"]
@@ -354,14 +359,14 @@ def run_adjoint_fd_check(name, W, S, alsv, torch):
     alsv.alsv_get_parameters(S.ctx, th0)
     S.sync()
     base = th0[0].cpu().numpy()
-    th = np.tile(base, (B, 1))
-    hs = 1e-6 * np.maximum(1.0, np.abs(base))
-    for i, j in enumerate(P):
-        th[1 + 2 * i, j] += hs[j]
-        th[2 + 2 * i, j] -= hs[j]
-    tth = torch.from_numpy(th).cuda()
     rows = []
-    for T in W["fd_check"]:
+    for hrel, T in [(h, T) for h in W["fd_h"] for T in W["fd_check"]]:
+        th = np.tile(base, (B, 1))
+        hs = hrel * np.maximum(1.0, np.abs(base))
+        for i, j in enumerate(P):
+            th[1 + 2 * i, j] += hs[j]
+            th[2 + 2 * i, j] -= hs[j]
+        tth = torch.from_numpy(th).cuda()
         t0 = time.perf_counter()
         J, g = S.adjoint(tth, T)
         torch.cuda.synchronize()
@@ -370,7 +375,7 @@ def run_adjoint_fd_check(name, W, S, alsv, torch):
         nst, dt_fixed, passes = alsv.alsv_adjoint_get_plan(S.ctx)
         fd = np.array([(J[1 + 2 * i] - J[2 + 2 * i]) / (2 * hs[j]) for i, j in enumerate(P)])
         gsel = g[0, list(P)]
-        rows.append({"T": T, "steps": int(nst), "passes": int(passes), "J": float(J[0]),
+        rows.append({"T": T, "h": hrel, "steps": int(nst), "passes": int(passes), "J": float(J[0]),
                      "max_abs_grad": float(np.abs(g[0]).max()),
                      "rel_diff_vs_fd": float(np.abs(gsel - fd).max() / np.abs(g[0]).max()),
                      "per_param_rel": [float(abs(a - b) / max(abs(b), 1e-300)) for a, b in zip(gsel, fd)],

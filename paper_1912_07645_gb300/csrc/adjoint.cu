@@ -118,7 +118,12 @@ struct AdjStageArgs {
     const void* X2;
     void* out;         // out = c1 X1 + c2 X2 + b (Ls + dt J_L(Us)^T Ls)
     double c1, c2, b, dt;
+    float c1_f, c2_f, b_f, dt_f;   // FP32 copies (no per-thread double->float conversion)
 };
+template <class R> __device__ __forceinline__ R adj_c(double d, float f) {
+    if constexpr (IsExact<R>::value) return d;
+    else return f;
+}
 
 // One CTA per (sample, TX x TY tile), one cell per thread; RV: reconstruction variables (the
 // conserved-variable path is compiled only where it runs).
@@ -156,7 +161,9 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 4 : 2) k_stage_adj(const 
     const long long sbase = (long long)b_local * NV * plane;
     const R* Us = reinterpret_cast<const R*>(p.Us) + sbase;
     const R* Ls = reinterpret_cast<const R*>(p.Ls) + sbase;
-    const R gamma = R(g.gamma), gm1 = gamma - R(1), inv_gm1 = R(1) / gm1;
+    const R gamma = c_gamma<R>(g);
+    const R gm1 = IsExact<R>::value ? gamma - R(1) : R(g.gm1_f);
+    const R inv_gm1 = IsExact<R>::value ? R(1) / gm1 : R(g.inv_gm1_f);
     constexpr bool prim = RV == RV_PRIM;
     const int tid = threadIdx.x;
 
@@ -195,7 +202,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 4 : 2) k_stage_adj(const 
         __syncthreads();
         const int EX = D == 0 ? NIF : TX, EY = D == 0 ? TY : NIFY;
         const int ustep = D == 0 ? 1 : SUX, lstep = D == 0 ? 1 : SLX;
-        const R inv_dx = R(L.inv_dx[D]);
+        const R inv_dx = c_inv_dx<R>(L, D);
         for (int f = tid; f < EX * EY; f += NT) {
             const int fx = f % EX, fy = f / EX;
             // interface j+1/2 along D; left cell j in tile coordinates
@@ -320,7 +327,8 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 4 : 2) k_stage_adj(const 
         for (int v = 0; v < NV; ++v) Ub[v] = acc[v];
     }
     const long long off = (long long)y * nx + x;
-    const R dt = R(p.dt), cb_ = R(p.b), c1 = R(p.c1), c2 = R(p.c2);
+    const R dt = adj_c<R>(p.dt, p.dt_f), cb_ = adj_c<R>(p.b, p.b_f), c1 = adj_c<R>(p.c1, p.c1_f),
+            c2 = adj_c<R>(p.c2, p.c2_f);
     const R* X1 = reinterpret_cast<const R*>(p.X1) + sbase;
     const R* X2 = reinterpret_cast<const R*>(p.X2) + sbase;
     R* out = reinterpret_cast<R*>(p.out) + sbase;
@@ -719,6 +727,7 @@ alsv_status alsv_adjoint_evolve(alsv_ctx* c, double T, int observable, const dou
     AdjStageArgs aa;
     aa.g = adj_grid(c);
     aa.dt = P.dt;
+    aa.dt_f = (float)P.dt;
     auto adj_stage = [&](const void* Us, const void* Ls, const void* X1, double c1, const void* X2, double c2, double b,
                          void* out) -> cudaError_t {
         aa.Us = Us;
@@ -728,6 +737,9 @@ alsv_status alsv_adjoint_evolve(alsv_ctx* c, double T, int observable, const dou
         aa.X2 = X2;
         aa.c2 = c2;
         aa.b = b;
+        aa.c1_f = (float)c1;
+        aa.c2_f = (float)c2;
+        aa.b_f = (float)b;
         aa.out = out;
         c->launches++;
         return launch_adj(c->fp64, c->d.recon, aa, s);

@@ -325,8 +325,8 @@ TileShape stage_tile(int fp64, int ndim, int variant) {
         if (variant == 5 && !fp64) return TileShape{32, 8, 1, 256};        // two-sample tiles
         if (variant == 6 && !fp64) return TileShape{32, 16, 1, 256};       // two halves of a sample
         if (variant == 7 && !fp64) return TileShape{32, 8, 1, 256};
-        if ((variant == 9 || variant == 11) && !fp64) return TileShape{32, 32, 1, 256};  // lean pairs
-        return TileShape{32, 16, 1, 256};                                   // variants 0, 4, 8, 10
+
+        return TileShape{32, 16, 1, 256};                                   // variants 0, 4, 8-11
     }
     if (fp64) return variant == 1 ? TileShape{8, 8, 4, 256} : TileShape{8, 8, 8, 256};
     if (variant == 2) return TileShape{32, 8, 64, 256};    // z-marching column chunks

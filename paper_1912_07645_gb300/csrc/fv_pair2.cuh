@@ -18,13 +18,15 @@
 
 namespace alsv {
 
-template <int RECON, int TY>
+// MERGE: the x- and y-interface fluxes go to separate buffers, so both directions are evaluated
+// between the same two barriers (more shared memory: 3 CTAs per SM at 32 x 16)
+template <int RECON, int TY, int MERGE = 0>
 constexpr size_t pair2_smem_bytes() {
     constexpr int TX = 32;
     constexpr int G = RECON == REC_PC ? 1 : 2;
     constexpr int NS = (TX + 2 * G) * (TY + 2 * G);
     constexpr int NIX = (TX + 1) * TY, NIY = TX * (TY + 1);
-    constexpr int NI = NIX > NIY ? NIX : NIY;
+    constexpr int NI = MERGE ? NIX + NIY : (NIX > NIY ? NIX : NIY);
     return (size_t)32 * (NS + NI);
 }
 
@@ -173,15 +175,15 @@ __device__ __forceinline__ void load_sten(const float4* sW0, const float4* sW1, 
     }
 }
 
-// TY rows per tile (16: 4 CTAs per SM with 64 registers; 32: 3 CTAs with 80); 256 threads =
-// 8 warps; lane = column, warp = row group. HALVES as in k_stage2d_pair.
-template <int RECON, int FLUX, int TY, int HALVES = 0>
-__global__ void __launch_bounds__(256, TY >= 32 ? 3 : 4) k_stage2d_pair2(const StageArgs p) {
+// TY rows per tile (16: 4 CTAs per SM with 64 registers; 32 or MERGE: 3 CTAs with 80); 256
+// threads = 8 warps; lane = column, warp = row group. HALVES as in k_stage2d_pair.
+template <int RECON, int FLUX, int TY, int HALVES = 0, int MERGE = 0>
+__global__ void __launch_bounds__(256, (TY >= 32 || MERGE) ? 3 : 4) k_stage2d_pair2(const StageArgs p) {
     constexpr int TX = 32, NT = 256, NW = 8;
     constexpr int G = RECON == REC_PC ? 1 : 2;
     constexpr int SX = TX + 2 * G, SY = TY + 2 * G, NS = SX * SY;
     constexpr int NIX = (TX + 1) * TY, NIY = TX * (TY + 1);
-    constexpr int NI = NIX > NIY ? NIX : NIY;
+    constexpr int NI = MERGE ? NIX + NIY : (NIX > NIY ? NIX : NIY);
     constexpr int CPT = TY / NW;   // cells per thread (and y-interfaces per thread run)
     static_assert(TY % NW == 0, "tile height must be a multiple of the warp count");
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -204,9 +206,10 @@ __global__ void __launch_bounds__(256, TY >= 32 ? 3 : 4) k_stage2d_pair2(const S
     const int sA = HALVES ? (int)q : 2 * (int)q;
     const bool hasB = HALVES ? true : sA + 1 < L.samples;
     const int sB = HALVES ? sA : (hasB ? sA + 1 : sA);
+    // the done flags are read now but acted on after the tile load, so that their round trip
+    // overlaps the halo loads instead of preceding them (a finished pair only wastes a tile read)
     const bool doneA = p.done[L.sample0 + sA] != 0;
     const bool doneB = hasB ? p.done[L.sample0 + sB] != 0 : true;
-    if (doneA && doneB) return;
 
     const int nx = L.n[0], ny = L.n[1];
     const uint32_t trow = fdiv(tile, L.fd_nt0);
@@ -284,6 +287,8 @@ __global__ void __launch_bounds__(256, TY >= 32 ? 3 : 4) k_stage2d_pair2(const S
         }
     }
 
+    if (doneA && doneB) return;   // uniform over the CTA, before its first barrier
+
     float2 acc[CPT][4];
 #pragma unroll
     for (int m = 0; m < CPT; ++m)
@@ -294,24 +299,27 @@ __global__ void __launch_bounds__(256, TY >= 32 ? 3 : 4) k_stage2d_pair2(const S
     // plus the extra column (D = 0: fx = TX, fy < TY, the first TY threads) or row (D = 1: fy = TY,
     // the first warp). The left / lower cell of an interface is tile column fx - 1 / row fy - 1.
     // Fluxes go to shared memory; each thread then adds the divergence of its own cells.
-#pragma unroll
-    for (int D = 0; D < 2; ++D) {
-        __syncthreads();
+    // interfaces of direction D into their flux buffer; the extra column / row goes to the last
+    // warp (x) or, merged, the one before it (y), so that no warp takes both
+    auto flux_pass = [&](const int D) {
         const float2 eps = f2(L.eps_f[D]);
         const int EX = D == 0 ? TX + 1 : TX;
         const int step = D == 0 ? 1 : SX;
+        const int xwarp = NW - 1, ywarp = MERGE ? NW - 2 : NW - 1;
+        float4* F0 = sF0 + (MERGE && D == 1 ? NIX : 0);
+        float4* F1 = sF1 + (MERGE && D == 1 ? NIX : 0);
 #pragma unroll 1
         for (int m = 0; m <= CPT; ++m) {
             int fx = lane, fy = warp + NW * m;
             unsigned mask = 0xffffffffu;
             if (m == CPT) {
                 if (D == 0) {
-                    if (tid >= TY) break;
+                    if (warp != xwarp || lane >= TY) break;
                     fx = TX;
-                    fy = tid;
+                    fy = lane;
                     mask = TY >= 32 ? 0xffffffffu : ((1u << TY) - 1u);
                 } else {
-                    if (warp != 0) break;
+                    if (warp != ywarp) break;
                     fy = TY;
                 }
             }
@@ -322,21 +330,42 @@ __global__ void __launch_bounds__(256, TY >= 32 ? 3 : 4) k_stage2d_pair2(const S
             const F2x4 F = interface_flux2<RECON, FLUX>(S, gamma, inv_gm1, mask);
             const float2 fxm = D == 0 ? F.n : F.t, fym = D == 0 ? F.t : F.n;   // x-, y-momentum
             const int f = fy * EX + fx;
-            sF0[f] = make_float4(F.r.x, F.r.y, fxm.x, fxm.y);
-            sF1[f] = make_float4(fym.x, fym.y, F.p.x, F.p.y);
+            F0[f] = make_float4(F.r.x, F.r.y, fxm.x, fxm.y);
+            F1[f] = make_float4(fym.x, fym.y, F.p.x, F.p.y);
         }
-        __syncthreads();
+    };
+    // each thread adds -(F_{+1/2} - F_{-1/2}) / dx_D of its own cells, x before y
+    auto divergence = [&](const int D) {
         const float2 nid = f2(-L.inv_dx_f[D]);
+        const int EX = D == 0 ? TX + 1 : TX;
         const int fstep = D == 0 ? 1 : TX;
+        const float4* F0 = sF0 + (MERGE && D == 1 ? NIX : 0);
+        const float4* F1 = sF1 + (MERGE && D == 1 ? NIX : 0);
 #pragma unroll
         for (int m = 0; m < CPT; ++m) {
             const int fidx = (warp + NW * m) * EX + lane;
-            const float4 am = sF0[fidx], bm = sF1[fidx];
-            const float4 ap = sF0[fidx + fstep], bp = sF1[fidx + fstep];
+            const float4 am = F0[fidx], bm = F1[fidx];
+            const float4 ap = F0[fidx + fstep], bp = F1[fidx + fstep];
             acc[m][0] = fma2(sub2(lo2(ap), lo2(am)), nid, acc[m][0]);
             acc[m][1] = fma2(sub2(hi2(ap), hi2(am)), nid, acc[m][1]);
             acc[m][2] = fma2(sub2(lo2(bp), lo2(bm)), nid, acc[m][2]);
             acc[m][3] = fma2(sub2(hi2(bp), hi2(bm)), nid, acc[m][3]);
+        }
+    };
+    if (MERGE) {
+        __syncthreads();
+        flux_pass(0);
+        flux_pass(1);
+        __syncthreads();
+        divergence(0);
+        divergence(1);
+    } else {
+#pragma unroll
+        for (int D = 0; D < 2; ++D) {
+            __syncthreads();
+            flux_pass(D);
+            __syncthreads();
+            divergence(D);
         }
     }
 

@@ -1,11 +1,12 @@
-// Stage kernels for float, 2D: the lean two-sample schedules (variants 8-11).
+// Stage kernels for float, 2D: the lean two-sample schedules (variants 8-11; 9 and 11 evaluate
+// both directions between one pair of barriers).
 #include "fv_pair2.cuh"
 #include "stage_dispatch.cuh"
 namespace alsv {
-template <int RECON, int FLUX, int TY, int HALVES>
+template <int RECON, int FLUX, int TY, int HALVES, int MERGE>
 static cudaError_t launch_pair2_one(const StageArgs& a, cudaStream_t s) {
-    auto k = k_stage2d_pair2<RECON, FLUX, TY, HALVES>;
-    constexpr size_t sm = pair2_smem_bytes<RECON, TY>();
+    auto k = k_stage2d_pair2<RECON, FLUX, TY, HALVES, MERGE>;
+    constexpr size_t sm = pair2_smem_bytes<RECON, TY, MERGE>();
     static unsigned long long smem_devices = 0;   // devices on which the opt-in is done
     {
         const cudaError_t e = ensure_dynamic_smem(k, sm, smem_devices);
@@ -16,18 +17,18 @@ static cudaError_t launch_pair2_one(const StageArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <int TY, int HALVES>
+template <int TY, int HALVES, int MERGE = 0>
 static cudaError_t launch_pair2(int recon, int flux, int eq, const StageArgs& a, cudaStream_t s) {
     if (eq != EQ_EULER || a.g.rvars != RV_PRIM) return cudaErrorNotSupported;
     if (flux == FLX_HLLC) {
-        if (recon == REC_WENO3) return launch_pair2_one<REC_WENO3, FLX_HLLC, TY, HALVES>(a, s);
-        if (recon == REC_MC) return launch_pair2_one<REC_MC, FLX_HLLC, TY, HALVES>(a, s);
-        return launch_pair2_one<REC_PC, FLX_HLLC, TY, HALVES>(a, s);
+        if (recon == REC_WENO3) return launch_pair2_one<REC_WENO3, FLX_HLLC, TY, HALVES, MERGE>(a, s);
+        if (recon == REC_MC) return launch_pair2_one<REC_MC, FLX_HLLC, TY, HALVES, MERGE>(a, s);
+        return launch_pair2_one<REC_PC, FLX_HLLC, TY, HALVES, MERGE>(a, s);
     }
     if (flux == FLX_RUSANOV) {
-        if (recon == REC_WENO3) return launch_pair2_one<REC_WENO3, FLX_RUSANOV, TY, HALVES>(a, s);
-        if (recon == REC_MC) return launch_pair2_one<REC_MC, FLX_RUSANOV, TY, HALVES>(a, s);
-        return launch_pair2_one<REC_PC, FLX_RUSANOV, TY, HALVES>(a, s);
+        if (recon == REC_WENO3) return launch_pair2_one<REC_WENO3, FLX_RUSANOV, TY, HALVES, MERGE>(a, s);
+        if (recon == REC_MC) return launch_pair2_one<REC_MC, FLX_RUSANOV, TY, HALVES, MERGE>(a, s);
+        return launch_pair2_one<REC_PC, FLX_RUSANOV, TY, HALVES, MERGE>(a, s);
     }
     return cudaErrorNotSupported;
 }
@@ -35,9 +36,9 @@ static cudaError_t launch_pair2(int recon, int flux, int eq, const StageArgs& a,
 cudaError_t launch_stage_f32_2d_lean(int variant, int eq, int recon, int flux, const StageArgs& a, cudaStream_t s) {
     switch (variant) {
         case 8: return launch_pair2<16, 0>(recon, flux, eq, a, s);
-        case 9: return launch_pair2<32, 0>(recon, flux, eq, a, s);
+        case 9: return launch_pair2<16, 0, 1>(recon, flux, eq, a, s);
         case 10: return launch_pair2<16, 1>(recon, flux, eq, a, s);
-        case 11: return launch_pair2<32, 1>(recon, flux, eq, a, s);
+        case 11: return launch_pair2<16, 1, 1>(recon, flux, eq, a, s);
         default: return cudaErrorInvalidValue;
     }
 }

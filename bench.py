@@ -432,7 +432,7 @@ def run_blocks_workload(name, W, args):
     torch.cuda.empty_cache()
 
     # overhead of the decomposition: the same scheme at a size one context holds, whole vs blocks
-    def per_step(parts):
+    def per_step(parts, overlap=True):
         kw = dict(cfg, n=W["overhead_n"])
         if parts is None:
             S = alsv.Solver(alsv.make_desc(**kw))
@@ -441,7 +441,7 @@ def run_blocks_workload(name, W, args):
             run = (lambda k: (S.step(k), S.sync()))
             close = S.close
         else:
-            D = Decomposition(parts=parts, tile_variant=chosen, **kw)
+            D = Decomposition(parts=parts, tile_variant=chosen, overlap=overlap, **kw)
             D.set_initial_data(W["init"])
             run = (lambda k: (D.step(k), D.sync()))
             close = D.close
@@ -456,6 +456,7 @@ def run_blocks_workload(name, W, args):
 
     ms_whole = per_step(None)
     ms_blocks = per_step(W["parts"])
+    ms_blocks_no_overlap = per_step(W["parts"], overlap=False)
     bpc = W["words"] * W["nv"] * W["esize"]
     # the blocks' stage launches run concurrently on their own streams, so their event times
     # overlap: the achieved rates use the wall time of the timed steps (stages, halo packs and time
@@ -480,7 +481,9 @@ def run_blocks_workload(name, W, args):
                              "peak_kind": "nominal: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"},
             "decomposition_overhead": {"grid": list(W["overhead_n"]), "blocks": list(W["parts"]),
                                        "ms_per_step_whole": ms_whole, "ms_per_step_blocks": ms_blocks,
-                                       "overhead": (ms_blocks - ms_whole) / ms_whole},
+                                       "overhead": (ms_blocks - ms_whole) / ms_whole,
+                                       "ms_per_step_blocks_exchange_then_stage": ms_blocks_no_overlap,
+                                       "overhead_exchange_then_stage": (ms_blocks_no_overlap - ms_whole) / ms_whole},
             "gpu_launches": launches}
     print(json.dumps(line), flush=True)
     return 0

@@ -426,6 +426,14 @@ alsv_status alsv_structure_function_read(alsv_ctx* ctx, const void* acc_dev, int
  *   alsv_stage         enqueue RK stage s of the current step for every sample that is not done;
  *                      stages must come in order 0, 1, ... (INVALID_ARG otherwise). The last stage
  *                      also writes the per-tile CFL partials. Asynchronous.
+ *   alsv_stage_part    stage s split around the halo exchange: ALSV_PART_INTERIOR runs the tiles
+ *                      whose stencil reads no halo buffer, so it may be enqueued before the
+ *                      neighbours' layers for stage s are delivered (the paper's overlap of the
+ *                      exchange with the inner-domain computation, Sec. 2.1, last paragraph; Sec.
+ *                      3.1); ALSV_PART_BOUNDARY runs the rest and needs the halos delivered. Both
+ *                      parts, in either order, make up alsv_stage(s) (each tile is computed by
+ *                      exactly one of them, so the result is bitwise the same); a context with no
+ *                      HALO face runs everything in the interior part. Asynchronous.
  *   alsv_speed_max     smax_dev[samples] (device FP64) = each sample's largest (|u_k|+c)/dx_k over
  *                      the block, from the partials of the last stage (or of set_initial_data /
  *                      set_time), +infinity for a sample with a non-finite partial. Allowed before
@@ -449,6 +457,8 @@ alsv_status alsv_halo_info(const alsv_ctx* ctx, int32_t* layers, int64_t* elems)
 alsv_status alsv_bind_halo(alsv_ctx* ctx, const void* const* halo_dev, const size_t* bytes);
 alsv_status alsv_halo_pack(alsv_ctx* ctx, int stage, void* const* send_dev, const size_t* bytes);
 alsv_status alsv_stage(alsv_ctx* ctx, int stage);
+enum { ALSV_PART_INTERIOR = 1, ALSV_PART_BOUNDARY = 2 };
+alsv_status alsv_stage_part(alsv_ctx* ctx, int stage, int part);
 alsv_status alsv_speed_max(alsv_ctx* ctx, double* smax_dev);
 alsv_status alsv_speed_max_combine(const double* const* smax_dev, int n, int samples, double* out_dev, void* stream);
 alsv_status alsv_finish_step(alsv_ctx* ctx, const double* smax_dev, int advance);

@@ -109,6 +109,7 @@ SIGNATURES = {
     "alsv_stage": (C.c_int, [_ctx, C.c_int]),
     "alsv_speed_max": (C.c_int, [_ctx, _vp]),
     "alsv_speed_max_combine": (C.c_int, [C.POINTER(_vp), C.c_int, C.c_int, _vp, _vp]),
+    "alsv_stage_part": (C.c_int, [_ctx, C.c_int, C.c_int]),
     "alsv_finish_step": (C.c_int, [_ctx, _vp, C.c_int]),
     "alsv_set_end_time": (C.c_int, [_ctx, C.c_double]),
 }
@@ -389,6 +390,14 @@ def alsv_halo_pack(ctx, stage: int, sends, nbytes=None):
 
 def alsv_stage(ctx, stage: int):
     _check(load().alsv_stage(ctx, stage), "alsv_stage", ctx)
+
+
+PART = {"interior": 1, "boundary": 2}
+
+
+def alsv_stage_part(ctx, stage: int, part: str):
+    """One part of stage s (interior tiles, or the tiles that read halo buffers); see include/alsv.h."""
+    _check(load().alsv_stage_part(ctx, stage, PART[part]), "alsv_stage_part", ctx)
 
 
 def alsv_speed_max(ctx, smax):

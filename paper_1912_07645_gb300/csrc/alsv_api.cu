@@ -115,6 +115,7 @@ StageArgs stage_args(alsv_ctx* c, const void* Us, const void* Un, void* Uout, do
     s.speed_part = c->part;
     s.want_speed = want_speed ? 1 : 0;
     for (int f = 0; f < 6; ++f) s.halo[f] = c->halo[f];
+    s.part = 0;
     return s;
 }
 
@@ -177,9 +178,15 @@ StageIO stage_io(const alsv_ctx* c, int k) {
     return {c->Bb, c->U, c->U, 1.0 / 3.0, 2.0 / 3.0};
 }
 
-alsv_status enqueue_stage(alsv_ctx* c, int k) {
+alsv_status enqueue_stage(alsv_ctx* c, int k, int part = 0) {
     const StageIO io = stage_io(c, k);
     StageArgs a = stage_args(c, io.Us, io.Un, io.Uo, io.a, io.b, k == c->nstages - 1);
+    if (part != 0 && !ctx_has_halo(c)) {
+        // no tile reads a halo buffer: the interior part is the whole stage, the boundary part empty
+        if (part == 2) return ALSV_OK;
+        part = 0;
+    }
+    a.part = part;
     if (c->prof.on && c->prof.ev.empty()) prof_mark(c, -1);
     if (c->prof.on) c->prof.kinds.push_back(0);
     cudaError_t e = launch_stage(c->fp64, c->ndim, c->eq, c->d.recon, c->d.flux, c->variant, a, c->stream);
@@ -662,6 +669,7 @@ alsv_status alsv_set_initial_data(alsv_ctx* c, int kind, const double* theta_dev
     if (st != ALSV_OK) return st;
     c->time_ready = true;
     c->stage_next = 0;
+    c->stage_parts = 0;
     return ALSV_OK;
 }
 
@@ -682,6 +690,7 @@ alsv_status alsv_set_time(alsv_ctx* c, const double* t_host, const int64_t* step
     if (st != ALSV_OK) return st;
     c->time_ready = true;
     c->stage_next = 0;
+    c->stage_parts = 0;
     return ALSV_OK;
 }
 
@@ -1090,9 +1099,33 @@ alsv_status alsv_stage(alsv_ctx* c, int stage) {
     if (ctx_has_halo(c) && !c->halo_bound) return fail(c, ALSV_ERR_NOT_READY, "halo buffers not bound (alsv_bind_halo)");
     if (stage != c->stage_next || stage >= c->nstages)
         return fail(c, ALSV_ERR_INVALID_ARG, "stages run in order 0 .. stages-1, then alsv_finish_step");
+    if (c->stage_parts != 0) return fail(c, ALSV_ERR_INVALID_ARG, "stage already started in parts (alsv_stage_part)");
     st = enqueue_stage(c, stage);
     if (st != ALSV_OK) return st;
     c->stage_next = stage + 1;
+    return ALSV_OK;
+}
+
+alsv_status alsv_stage_part(alsv_ctx* c, int stage, int part) {
+    alsv_status st = require_ready(c);
+    if (st != ALSV_OK) return st;
+    if (!c->time_ready) return fail(c, ALSV_ERR_NOT_READY, "no time state (alsv_set_initial_data)");
+    if (part != ALSV_PART_INTERIOR && part != ALSV_PART_BOUNDARY)
+        return fail(c, ALSV_ERR_INVALID_ARG, "part must be ALSV_PART_INTERIOR or ALSV_PART_BOUNDARY");
+    if (stage != c->stage_next || stage >= c->nstages)
+        return fail(c, ALSV_ERR_INVALID_ARG, "stages run in order 0 .. stages-1, then alsv_finish_step");
+    const int bit = part == ALSV_PART_INTERIOR ? 1 : 2;
+    if (c->stage_parts & bit) return fail(c, ALSV_ERR_INVALID_ARG, "this part of the stage already ran");
+    // the boundary part reads the halo buffers: they must be bound (the interior part reads none)
+    if (part == ALSV_PART_BOUNDARY && ctx_has_halo(c) && !c->halo_bound)
+        return fail(c, ALSV_ERR_NOT_READY, "halo buffers not bound (alsv_bind_halo)");
+    st = enqueue_stage(c, stage, part == ALSV_PART_INTERIOR ? 1 : 2);
+    if (st != ALSV_OK) return st;
+    c->stage_parts |= bit;
+    if (c->stage_parts == 3) {
+        c->stage_parts = 0;
+        c->stage_next = stage + 1;
+    }
     return ALSV_OK;
 }
 
@@ -1100,7 +1133,7 @@ alsv_status alsv_speed_max(alsv_ctx* c, double* smax_dev) {
     alsv_status st = require_ready(c);
     if (st != ALSV_OK) return st;
     if (!smax_dev) return fail(c, ALSV_ERR_INVALID_ARG, "null output");
-    if (c->stage_next != 0 && c->stage_next != c->nstages)
+    if ((c->stage_next != 0 && c->stage_next != c->nstages) || c->stage_parts != 0)
         return fail(c, ALSV_ERR_INVALID_ARG, "the maximum speed is defined before the first or after the last stage");
     FinishArgs f = finish_args(c, 0);
     f.smax_out = smax_dev;
@@ -1134,7 +1167,7 @@ alsv_status alsv_finish_step(alsv_ctx* c, const double* smax_dev, int advance) {
     alsv_status st = require_ready(c);
     if (st != ALSV_OK) return st;
     if (!smax_dev) return fail(c, ALSV_ERR_INVALID_ARG, "null maximum");
-    if (advance ? c->stage_next != c->nstages : c->stage_next != 0)
+    if ((advance ? c->stage_next != c->nstages : c->stage_next != 0) || c->stage_parts != 0)
         return fail(c, ALSV_ERR_INVALID_ARG, advance ? "advance = 1 follows the last stage" : "advance = 0 comes before the first stage");
     FinishArgs f = finish_args(c, advance ? 1 : 0);
     f.smax_in = smax_dev;
@@ -1142,6 +1175,7 @@ alsv_status alsv_finish_step(alsv_ctx* c, const double* smax_dev, int advance) {
     if (e != cudaSuccess) return cuda_fail(c, e, "finish kernel launch");
     c->launches++;
     c->stage_next = 0;
+    c->stage_parts = 0;
     return ALSV_OK;
 }
 

@@ -74,6 +74,7 @@ struct alsv_ctx {
     const void* halo[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     bool halo_bound = false;
     int stage_next = 0;
+    int stage_parts = 0;   // parts of stage stage_next already enqueued (1 interior, 2 boundary)
 };
 
 namespace alsv {

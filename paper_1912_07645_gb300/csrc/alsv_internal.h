@@ -82,6 +82,21 @@ struct GridArgs {
     int off[3];        // block of a decomposed grid: global index of the first cell per direction
 };
 
+#ifdef __CUDACC__
+// Whether a tile whose cells span [c0[k], c1[k]) reads a halo buffer: its stencil (G layers
+// beyond the tile) crosses a face of kind BC_HALO. A stage part skips the tiles of the other kind.
+template <int ND>
+__device__ __forceinline__ bool tile_in_part(const GridArgs& g, int part, const int c0[3], const int c1[3],
+                                             const int n[3], int G) {
+    if (part == 0) return true;
+    bool halo = false;
+#pragma unroll
+    for (int k = 0; k < ND; ++k)
+        halo |= (c0[k] - G < 0 && g.bc[k][0] == BC_HALO) || (c1[k] + G > n[k] && g.bc[k][1] == BC_HALO);
+    return part == 1 ? !halo : halo;
+}
+#endif
+
 // FP32 copies of the grid's constants (computed once on the host; the stage kernels read them
 // instead of converting the doubles in every thread).
 inline void fill_float_consts(GridArgs& g) {
@@ -110,6 +125,8 @@ struct StageArgs {
     double* speed_part;   // [work items]; written when want_speed
     int want_speed;
     const void* halo[6];  // face 2k + side with bc HALO: [samples][NV][G][cross] ghost layers
+    int part;             // tiles to run: 0 all, 1 those whose stencil reads no halo buffer,
+                          // 2 the others (a block's stage split around the halo exchange)
 };
 
 // Tile shape used for a given (precision, ndim); the host derives the tiling from it.

@@ -264,6 +264,10 @@ __global__ void __launch_bounds__(NT) k_stage(const StageArgs p) {
     const uint32_t tplane = ND >= 2 ? fdiv(trow, L.fd_nt1) : 0u;
     const int ty0 = ND >= 2 ? (int)(trow - tplane * (uint32_t)L.ntile[1]) * TY : 0;
     const int tz0 = ND >= 3 ? (int)tplane * TZ : 0;
+    {
+        const int c0[3] = {tx0, ty0, tz0}, c1[3] = {tx0 + TX, ty0 + TY, tz0 + TZ}, nn[3] = {nx, ny, nz};
+        if (!tile_in_part<ND>(g, p.part, c0, c1, nn, G)) return;   // uniform per CTA
+    }
     const int plane = nx * ny * nz;  // one sample holds < 2^31 elements (host-checked)
     const long long sbase = L.elem0 + (long long)b_local * NV * plane;
     const R* Us = reinterpret_cast<const R*>(p.Us) + sbase;

@@ -56,6 +56,10 @@ __global__ void __launch_bounds__(NTH, 4) k_stage3d_zm(const StageArgs p) {
     const int ty0 = (int)(trow - tplane * (uint32_t)L.ntile[1]) * TY;
     const int z0 = (int)tplane * LZ;
     const int z1 = min(z0 + LZ, nz);
+    {
+        const int c0[3] = {tx0, ty0, z0}, c1[3] = {tx0 + TX, ty0 + TY, z1}, nn[3] = {nx, ny, nz};
+        if (!tile_in_part<3>(g, p.part, c0, c1, nn, G)) return;   // uniform per CTA
+    }
     const int plane = nx * ny * nz;
     const long long sbase = L.elem0 + (long long)b_local * NV * plane;
     const R* Us = reinterpret_cast<const R*>(p.Us) + sbase;

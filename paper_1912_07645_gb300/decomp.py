@@ -8,7 +8,9 @@ halo faces: the stage kernels read the ghost cells there from halo buffers inste
 condition. A step then runs stage by stage:
 
   for every stage s:  each block writes the boundary layers of the state stage s reads into its
-                      neighbours' halo buffers (the exchange), then runs stage s
+                      neighbours' halo buffers (the exchange), then runs stage s - by default in
+                      two parts: the tiles whose stencil reads no halo buffer while the layers
+                      travel, the others once they have arrived
   after the last:     the per-sample maximum wave speed is reduced over all blocks (MAX) and each
                       block finishes the step with it (t, dt, done flags)
 
@@ -142,7 +144,13 @@ class LocalExchange:
             with torch.cuda.stream(self.main):
                 self.gmax = torch.zeros(blocks[0].samples, dtype=torch.float64, device=dev)
 
-    def exchange(self, stage: int):
+    # the interior part of a stage goes before the packs: on one device the packs wait for the
+    # neighbours' previous stage, and a block's own stream would hold its interior tiles behind them
+    pack_first = False
+
+    def start(self, stage: int):
+        """Pack every block's boundary layers of the state stage s reads into its neighbours' halo
+        buffers, each after the neighbour's previous stage (the last reader of that halo)."""
         for i, b in enumerate(self.blocks):
             # my low face's layers are the low neighbour's high-face halo, and so on
             sends = [self.blocks[j].halos[f ^ 1] if j is not None else None for f, j in enumerate(self.nbr[i])]
@@ -153,10 +161,17 @@ class LocalExchange:
                 b.halo_pack(stage, sends)
             if self.events:
                 self.ev_pack[i].record(b.stream)
+
+    def finish(self, stage: int):
+        """Make every block wait for its neighbours' packs of stage s (its halos are then filled)."""
         if self.events:
             for i, b in enumerate(self.blocks):
                 for j in self.peers[i]:
                     self.ev_pack[j].wait(b.stream)
+
+    def exchange(self, stage: int):
+        self.start(stage)
+        self.finish(stage)
 
     def after_stage(self, i: int):
         if self.events:
@@ -193,6 +208,7 @@ class DistExchange:
     def __init__(self, block, coord, parts, periodic, group=None):
         import torch
         self.block, self.group = block, group
+        self._works = []
         self.peer = []
         for f in range(6):
             nb = neighbour(coord, f, parts, periodic)
@@ -206,7 +222,21 @@ class DistExchange:
             return group_rank
         return dist.get_global_rank(self.group, group_rank)
 
+    # pack and post the transfers first, so that they travel while the interior tiles compute
+    pack_first = True
+
     def exchange(self, stage: int):
+        self.start(stage)
+        self.finish(stage)
+
+    def finish(self, stage: int):
+        b = self.block
+        with _on(b):
+            for w in self._works:
+                w.wait()
+        self._works = []
+
+    def start(self, stage: int):
         import torch.distributed as dist
         b = self.block
         b.halo_pack(stage, [s if p is not None else None for s, p in zip(self.sends, self.peer)])
@@ -219,10 +249,10 @@ class DistExchange:
         for f in (1, 0, 3, 2, 5, 4):
             if self.peer[f] is not None:
                 ops.append(dist.P2POp(dist.irecv, b.halos[f], self.peer[f], self.group, tag=f ^ 1))
+        self._works = []
         if ops:
             with _on(b):
-                for w in dist.batch_isend_irecv(ops):
-                    w.wait()
+                self._works = list(dist.batch_isend_irecv(ops))
 
     def after_stage(self, i: int):
         pass
@@ -245,10 +275,14 @@ class Decomposition:
     ``make_block``: factory of a block from make_desc keywords (default: a Solver on ``device``).
     ``tile_variant``: stage schedule of every block (include/alsv.h, execution controls; None keeps
     the default).
+    ``overlap``: run each stage as two parts around the exchange - the tiles whose stencil reads no
+    halo buffer while the layers travel, the rest after they arrive (the paper overlaps its
+    exchange with the inner-domain computation); False runs whole stages after the exchange. Both
+    give bitwise the same result.
     """
 
     def __init__(self, parts=(2, 1, 1), transport="local", group=None, make_block=None, device="cuda",
-                 tile_variant=None, **cfg):
+                 tile_variant=None, overlap=True, **cfg):
         import torch
         self.torch = torch
         parts = tuple(int(p) for p in parts) + (1,) * (3 - len(parts))
@@ -256,6 +290,7 @@ class Decomposition:
         if any(parts[k] != 1 for k in range(ndim, 3)):
             raise ValueError("parts beyond ndim must be 1")
         self.parts, self.cfg = parts, dict(cfg)
+        self.overlap = bool(overlap)
         pairs = bc_pairs(cfg.get("bc", "periodic"), ndim)
         periodic = [pairs[k][0] == "periodic" for k in range(3)]
         coords = block_coords(parts)
@@ -317,20 +352,33 @@ class Decomposition:
             e1.synchronize()
         return sum(e0.elapsed_time(e1) for e0, e1 in self._prof), len(self._prof)
 
-    def _stage(self, b, s):
+    def _stage(self, b, s, part=None):
+        run = (lambda: b.stage(s)) if part is None else (lambda: b.stage_part(s, part))
         if self._prof is None:
-            b.stage(s)
+            run()
             return
         torch = self.torch
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(b.stream)
-        b.stage(s)
+        run()
         e1.record(b.stream)
         self._prof.append((e0, e1))
 
     def step(self, n: int = 1):
         for _ in range(n):
             for s in range(self.stages):
+                if self.overlap:
+                    if self.xch.pack_first:
+                        self.xch.start(s)
+                    for b in self.blocks:
+                        self._stage(b, s, "interior")
+                    if not self.xch.pack_first:
+                        self.xch.start(s)
+                    self.xch.finish(s)
+                    for i, b in enumerate(self.blocks):
+                        self._stage(b, s, "boundary")
+                        self.xch.after_stage(i)
+                    continue
                 self.xch.exchange(s)
                 for i, b in enumerate(self.blocks):
                     self._stage(b, s)

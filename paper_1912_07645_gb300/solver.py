@@ -297,6 +297,9 @@ class Solver:
     def stage(self, s):
         A.alsv_stage(self.ctx, s)
 
+    def stage_part(self, s, part):
+        A.alsv_stage_part(self.ctx, s, part)
+
     def speed_max(self, out):
         A.alsv_speed_max(self.ctx, out)
 

@@ -195,3 +195,53 @@ def test_speed_max_combine_is_the_nan_propagating_maximum():
     assert np.array_equal(o[ok], ref[ok]) and o[11] == np.inf
     with pytest.raises(alsv.AlsvError, match="n must be"):
         alsv.alsv_speed_max_combine(ins * 13, out)   # 65 inputs
+
+
+@pytest.mark.parametrize("case,variant", [("kh2d_fp64_3x2_mixed", None), ("kh3d_fp32_1x2x2", None),
+                                          ("kh3d_fp32_1x2x2", 5), ("sod_fp64_x4", None)])
+def test_overlapped_stage_parts_equal_whole_stages(case, variant):
+    """Each stage run as two parts around the exchange (the tiles that read no halo buffer first,
+    then the others: the paper's overlap of the exchange with the inner-domain computation) gives
+    bitwise the state of whole stages run after the exchange, and of the undivided grid."""
+    import torch
+    _, cfg, init, parts, T = [c for c in CASES if c[0] == case][0]
+    from paper_1912_07645_gb300.decomp import Decomposition
+    out = []
+    for overlap in (True, False):
+        D = Decomposition(parts=parts, overlap=overlap, tile_variant=variant, **cfg)
+        D.set_initial_data(init)
+        D.step(4)
+        D.sync()
+        out.append(host(D.state()))
+        D.close()
+    assert np.array_equal(out[0], out[1])
+    S = gpu_solver(**cfg)
+    if variant is not None:
+        S.set_tile_variant(variant)
+    S.set_initial_data(init)
+    S.step(4)
+    assert np.array_equal(out[0], host(S.state()))
+    S.close()
+
+
+def test_stage_part_protocol():
+    import paper_1912_07645_gb300 as alsv
+    from paper_1912_07645_gb300.decomp import Decomposition
+    _, cfg, init, parts, _ = CASES[0]
+    D = Decomposition(parts=parts, **cfg)
+    D.set_initial_data(init)
+    b = D.blocks[0]
+
+    def status(fn):
+        with pytest.raises(alsv.AlsvError) as ei:
+            fn()
+        return ei.value.status_name
+
+    b.stage_part(0, "boundary")                      # either order
+    assert status(lambda: b.stage_part(0, "boundary")) == "ERR_INVALID_ARG"    # twice
+    assert status(lambda: b.stage(0)) == "ERR_INVALID_ARG"                     # mixed with a whole stage
+    assert status(lambda: b.speed_max(D.smax[0])) == "ERR_INVALID_ARG"         # mid-stage
+    assert status(lambda: b.stage_part(1, "interior")) == "ERR_INVALID_ARG"    # out of order
+    b.stage_part(0, "interior")
+    b.stage_part(1, "interior")                      # stage 0 complete: stage 1 may start
+    D.close()

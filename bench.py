@@ -212,7 +212,8 @@ def stage_traffic(variant, cell_updates, launches):
             rec[k] = v
     csrc = os.path.join(ROOT, "paper_1912_07645_gb300", "csrc")
     h = hashlib.sha256()
-    for f in ("fv_pair.cuh", "fv_packed.cuh", "fv_physics.cuh"):
+    kernel_src = "fv_pair2.cuh" if variant in (8, 9, 10, 11) else "fv_pair.cuh"
+    for f in (kernel_src, "fv_packed.cuh", "fv_physics.cuh"):
         h.update(open(os.path.join(csrc, f), "rb").read())
     if h.hexdigest()[:16] != rec.get("sources_sha256_prefix") or str(variant) != rec.get("variant"):
         return None, None
@@ -756,8 +757,8 @@ def main():
                 "stage_ms_total": prof["stage_ms"], "stage_launches": prof["stage_launches"],
                 "stage_share_of_step": prof["stage_ms"] / ms if ms > 0 else None,
                 "traffic": traffic, "traffic_bytes_per_cell_update": traffic_pcu,
-                "traffic_source": "profiles/k_stage2d_pair_f32_weno3_hllc_kh256.md (256-sample capture, per "
-                                  "cell-update, scaled to this run's cell-updates per stage launch)"}
+                "traffic_source": "profiles/stage_traffic.txt (the 256-sample capture of this schedule's kernel, "
+                                  "per cell-update, scaled to this run's cell-updates per stage launch)"}
         line = {"metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "fp32 (stencil); fp64 (statistics, totals, time)",

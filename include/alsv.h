@@ -207,6 +207,20 @@ alsv_status alsv_step(alsv_ctx* ctx, int n_steps);
 alsv_status alsv_evolve_to_T(alsv_ctx* ctx, double T, int64_t* steps_taken_host);
 
 /*
+ * alsv_evolve_resident - the same evolution to T in ONE launch, each sample resident in the
+ * distributed shared memory of one thread-block cluster (the smallest cluster of 1 .. 16 CTAs whose
+ * shared memory holds U^n, the stage state and a primitive copy: 256^2 takes 16 CTAs); the state
+ * is read from HBM once and written back once, the boundary rows of neighbouring CTAs are read by
+ * distributed-shared-memory loads, and each sample takes its own CFL steps. Bitwise the result of
+ * alsv_evolve_to_T with tile variant 0 (same flux functions and order of operations). Serves FP32
+ * 2D Euler on one grid, periodic in x and y, primitive PC / MC / WENO3 with HLLC or Rusanov, CFL
+ * steps, nx a multiple of 32 up to 1024 (INVALID_ARG otherwise, or when the sample does not fit 16
+ * CTAs). SYNCHRONOUS; t, steps, done and the next dt are left as alsv_evolve_to_T leaves them.
+ * Not in the paper: a schedule of the same scheme (Sec. 2.1) for single-GPU batches.
+ */
+alsv_status alsv_evolve_resident(alsv_ctx* ctx, double T, int64_t* steps_taken_host);
+
+/*
  * alsv_set_time - resume: set every sample's time t_host[b] and step count steps_host[b] (host
  * arrays of alsv_num_samples entries; steps may be NULL for 0) for the state currently bound, and
  * recompute the CFL partials and time steps from that state. A run checkpointed as (U, t, steps)

@@ -22,7 +22,7 @@ from ._abi import (BC, EQ, FLUX, INIT, PRECISION, RECON, RK, RVARS, AlsvError, a
                    alsv_set_profiling, alsv_set_tile_variant, alsv_set_time, alsv_state_bytes, alsv_stats_accumulate,
                    alsv_stats_bytes, alsv_stats_merge, alsv_stats_read, alsv_stats_reset, alsv_step, alsv_sync,
                    alsv_version, load, alsv_halo_info, alsv_bind_halo, alsv_halo_pack, alsv_stage,
-                   alsv_speed_max, alsv_speed_max_combine, alsv_stage_part, alsv_finish_step, alsv_set_end_time, alsv_mixing_width,
+                   alsv_speed_max, alsv_speed_max_combine, alsv_stage_part, alsv_evolve_resident, alsv_finish_step, alsv_set_end_time, alsv_mixing_width,
                    OBSERVABLE)
 from .provenance import provenance, save_result  # noqa: F401
 from .solver import Solver, make_desc  # noqa: F401

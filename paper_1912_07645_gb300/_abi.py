@@ -66,6 +66,7 @@ SIGNATURES = {
     "alsv_set_initial_data": (C.c_int, [_ctx, C.c_int, _vp, C.c_int, _vp, _sz]),
     "alsv_step": (C.c_int, [_ctx, C.c_int]),
     "alsv_evolve_to_T": (C.c_int, [_ctx, C.c_double, _i64p]),
+    "alsv_evolve_resident": (C.c_int, [_ctx, C.c_double, _i64p]),
     "alsv_sync": (C.c_int, [_ctx]),
     "alsv_set_time": (C.c_int, [_ctx, _dp, _i64p]),
     "alsv_get_time": (C.c_int, [_ctx, _dp, _i64p]),
@@ -398,6 +399,13 @@ PART = {"interior": 1, "boundary": 2}
 def alsv_stage_part(ctx, stage: int, part: str):
     """One part of stage s (interior tiles, or the tiles that read halo buffers); see include/alsv.h."""
     _check(load().alsv_stage_part(ctx, stage, PART[part]), "alsv_stage_part", ctx)
+
+
+def alsv_evolve_resident(ctx, T: float) -> int:
+    """Evolve to T with every sample resident in one thread-block cluster; see include/alsv.h."""
+    n = C.c_int64(0)
+    _check(load().alsv_evolve_resident(ctx, T, C.byref(n)), "alsv_evolve_resident", ctx)
+    return int(n.value)
 
 
 def alsv_speed_max(ctx, smax):

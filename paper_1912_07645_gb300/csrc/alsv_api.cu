@@ -784,6 +784,66 @@ alsv_status alsv_evolve_to_T(alsv_ctx* c, double T, int64_t* steps_taken_host) {
     return st;
 }
 
+alsv_status alsv_evolve_resident(alsv_ctx* c, double T, int64_t* steps_taken_host) {
+    alsv_status st = require_ready(c);
+    if (st != ALSV_OK) return st;
+    if (!std::isfinite(T) || T < 0.0) return fail(c, ALSV_ERR_INVALID_ARG, "T must be finite and >= 0");
+    if (c->fp64 || c->ndim != 2 || c->eq != ALSV_EQ_EULER || c->g.nlev != 1 || c->g.rvars != RV_PRIM)
+        return fail(c, ALSV_ERR_INVALID_ARG, "the resident schedule serves FP32 2D Euler, one grid, primitive reconstruction");
+    if (c->d.recon > REC_WENO3 || (c->d.flux != FLX_HLLC && c->d.flux != FLX_RUSANOV))
+        return fail(c, ALSV_ERR_INVALID_ARG, "the resident schedule serves PC / MC / WENO3 with HLLC or Rusanov");
+    for (int k = 0; k < 2; ++k)
+        if (c->g.bc[k][0] != BC_PERIODIC || c->g.bc[k][1] != BC_PERIODIC)
+            return fail(c, ALSV_ERR_INVALID_ARG, "the resident schedule needs periodic boundaries in x and y");
+    if (c->d.fixed_dt > 0.0) return fail(c, ALSV_ERR_INVALID_ARG, "the resident schedule takes CFL steps (fixed_dt = 0)");
+    const int nx = c->g.lev[0].n[0], ny = c->g.lev[0].n[1];
+    if (nx % 32 != 0 || nx > 1024) return fail(c, ALSV_ERR_INVALID_ARG, "the resident schedule needs nx a multiple of 32, at most 1024");
+    // the smallest cluster whose shared memory holds the sample (each CTA at least two rows)
+    int cs = 0;
+    for (int k = 1; k <= 16; k *= 2) {
+        if (ny % k != 0 || ny / k < 2) continue;
+        if (resident_smem_bytes(nx, ny / k) <= 227 * 1024) {
+            cs = k;
+            break;
+        }
+    }
+    if (cs == 0) return fail(c, ALSV_ERR_INVALID_ARG, "the sample does not fit one cluster's shared memory (at most 16 CTAs)");
+    st = set_run_params(c, T, LLONG_MAX);
+    if (st != ALSV_OK) return st;
+    ResidentArgs a;
+    a.g = c->g;
+    a.U = static_cast<float*>(c->U);
+    a.t = c->t;
+    a.dt = c->dt;
+    a.dt_f = c->dt_f;
+    a.nstep = c->nstep;
+    a.done = c->done;
+    a.last = c->last;
+    a.status = c->status;
+    a.T = T;
+    a.cfl = c->d.cfl;
+    a.max_steps = 1LL << 40;
+    a.rk = c->nstages;
+    a.cs = cs;
+    cudaError_t e = launch_resident(a, c->d.recon, c->d.flux, nx, ny / cs, c->total_samples, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "resident kernel launch");
+    c->launches++;
+    int hs = 0;
+    CK(cudaMemcpyAsync(&hs, c->status, 4, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (hs & (ST_NONPHYSICAL | ST_CFL)) return status_to_code(c, hs);
+    if (steps_taken_host) {
+        const size_t S = c->total_samples;
+        std::vector<int64_t> ns(S);
+        CK(cudaMemcpyAsync(ns.data(), c->nstep, S * 8, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        int64_t mx = 0;
+        for (auto v : ns) mx = std::max(mx, v);
+        *steps_taken_host = mx;
+    }
+    return ALSV_OK;
+}
+
 alsv_status alsv_get_time(alsv_ctx* c, double* t_host, int64_t* steps_host) {
     alsv_status st = require_ready(c, false);
     if (st != ALSV_OK) return st;

@@ -97,6 +97,32 @@ __device__ __forceinline__ bool tile_in_part(const GridArgs& g, int part, const 
 }
 #endif
 
+// The sample-resident time loop (FP32 2D Euler, one thread-block cluster per sample; stage_f32_2d_resident.cu).
+struct ResidentArgs {
+    GridArgs g;           // single level, periodic in x and y
+    float* U;             // [samples][4][ny][nx], in: state at t, out: state at T
+    double* t;            // per-sample time (in/out)
+    double* dt;           // per-sample next step (out)
+    float* dt_f;
+    int64_t* nstep;       // per-sample step count (in/out)
+    int* done;            // out: 1 once t >= T
+    int* last;
+    int* status;          // OR-ed ST_NONPHYSICAL
+    double T;
+    double cfl;
+    long long max_steps;  // per call
+    int rk;               // 2 or 3
+    int cs;               // CTAs per sample (cluster size)
+};
+
+inline size_t resident_smem_bytes(int nx, int R) {
+    // A, B [R][nx], P [R + 4][nx], two x-flux rows [nx], all float4; 32 per-warp maxima and flags,
+    // the CTA's slot read by the cluster
+    return (size_t)16 * nx * (3 * R + 4 + 2) + 66 * 4;
+}
+
+cudaError_t launch_resident(const ResidentArgs& a, int recon, int flux, int nx, int R, int samples, cudaStream_t s);
+
 // FP32 copies of the grid's constants (computed once on the host; the stage kernels read them
 // instead of converting the doubles in every thread).
 inline void fill_float_consts(GridArgs& g) {

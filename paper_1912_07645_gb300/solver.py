@@ -134,6 +134,10 @@ class Solver:
     def evolve_to(self, T):
         return A.alsv_evolve_to_T(self.ctx, T)
 
+    def evolve_resident(self, T):
+        """evolve_to with every sample resident in one thread-block cluster (FP32 2D Euler)."""
+        return A.alsv_evolve_resident(self.ctx, T)
+
     def sync(self):
         A.alsv_sync(self.ctx)
 

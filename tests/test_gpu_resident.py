@@ -1,0 +1,81 @@
+"""The sample-resident cluster schedule (alsv_evolve_resident): each sample's whole evolution in one
+thread-block cluster's distributed shared memory must give bitwise the state, times and step counts
+of alsv_evolve_to_T on the tile schedule (variant 0) - the same flux functions in the same order -
+for cluster sizes 1, 4 and 16 (64^2, 128^2, 256^2), and stay within 2e-5 relative L1 of the FP64
+oracle; unsupported configurations are rejected."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from harness import gpu_solver, host, need_gpu, p2_check
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    need_gpu()
+    from paper_1912_07645_gb300 import build
+    build.build()
+
+
+@pytest.mark.parametrize("n,B,recon,flux,rk,T", [(64, 3, "weno3", "hllc", "ssprk3", 0.05),
+                                                  (128, 2, "mc", "rusanov", "ssprk2", 0.03),
+                                                  (256, 2, "weno3", "hllc", "ssprk3", 0.02),
+                                                  (96, 2, "pc", "hllc", "ssprk3", 0.05)])
+def test_resident_equals_tile_schedule(n, B, recon, flux, rk, T):
+    import paper_1912_07645_gb300 as alsv
+    cfg = dict(ndim=2, n=(n, n), batch=B, eq="euler", recon=recon, flux=flux, rvars="prim", rk=rk, bc="periodic",
+               cfl=0.4, precision="fp32", seed=17)
+    out = []
+    for resident in (False, True):
+        S = gpu_solver(**cfg)
+        alsv.alsv_set_tile_variant(S.ctx, 0)
+        S.set_initial_data("kh")
+        steps = S.evolve_resident(T) if resident else S.evolve_to(T)
+        U = host(S.U).reshape(S.level_shape(0))
+        t, st = S.time()
+        out.append((U, t, st, steps))
+        S.close()
+    assert out[0][3] == out[1][3] > 0
+    assert np.array_equal(out[0][2], out[1][2]) and np.array_equal(out[0][1], out[1][1])
+    assert np.array_equal(out[0][0], out[1][0])
+
+
+def test_resident_vs_oracle_and_continuation():
+    """Against the FP64 oracle (P2), and a second call continues the first (to 2 T)."""
+    import paper_1912_07645_gb300 as alsv
+    n, B = 64, 2
+    cfg = dict(ndim=2, n=(n, n), batch=B, eq="euler", recon="weno3", flux="hllc", rvars="prim", rk="ssprk3",
+               bc="periodic", cfl=0.4, precision="fp32", seed=23)
+    S = gpu_solver(**cfg)
+    S.set_initial_data("kh")
+    S.evolve_resident(0.03)
+    g1 = host(S.U).reshape(S.level_shape(0))
+    S.evolve_resident(0.06)
+    g2 = host(S.U).reshape(S.level_shape(0))
+    t, st = S.time()
+    S.close()
+    assert np.all(t == 0.06)
+    d = oracle.make_desc(**cfg)
+    th = oracle.theta_splitmix(23, B, 20)
+    o1, _, _ = oracle.evolve(d, oracle.init(d, "kh", B, th), T=0.03)
+    p2_check(g1, o1, what="resident T=0.03")
+    o2, ost, _ = oracle.evolve(d, o1, T=0.06)
+    p2_check(g2, o2, what="resident T=0.06")
+
+
+def test_resident_rejections():
+    import paper_1912_07645_gb300 as alsv
+    for kw in (dict(precision="fp64"), dict(bc=[("periodic", "periodic"), ("outflow", "outflow")]),
+               dict(n=(70, 64)), dict(flux="roe"), dict(rvars="cons")):
+        cfg = dict(ndim=2, n=(64, 64), batch=1, eq="euler", recon="weno3", flux="hllc", rvars="prim",
+                   bc="periodic", precision="fp32")
+        cfg.update(kw)
+        S = gpu_solver(**cfg)
+        S.set_initial_data("kh")
+        with pytest.raises(alsv.AlsvError, match="resident"):
+            S.evolve_resident(0.01)
+        S.close()

@@ -218,6 +218,7 @@ def stage_traffic(variant, cell_updates, launches):
     if h.hexdigest()[:16] != rec.get("sources_sha256_prefix") or str(variant) != rec.get("variant"):
         return None, None
     pcu = float(rec["bytes_per_cell_update"])
+    stage_traffic.inst_per_cell_stage = float(rec["thread_inst_per_cell_stage"]) if "thread_inst_per_cell_stage" in rec else None
     return pcu * cell_updates / launches, pcu
 
 
@@ -281,6 +282,11 @@ WORKLOADS = {
     "kh2d1024_fp32": dict(desc=dict(ndim=2, n=(1024, 1024), batch=1, eq="euler", recon="weno3", flux="hllc",
                                     rvars="prim", rk="ssprk3", bc="periodic", cfl=0.4, precision="fp32", seed=0),
                           init="kh", T=2.0, words=8, nv=4, esize=4),
+    # the batched KH workload's scheme on 512 samples to T = 0.2, each sample resident in one
+    # thread-block cluster for its whole evolution (16 CTAs, 256 threads each)
+    "kh2d256_resident_fp32": dict(desc=dict(ndim=2, n=(256, 256), batch=512, eq="euler", recon="weno3", flux="hllc",
+                                            rvars="prim", rk="ssprk3", bc="periodic", cfl=0.4, precision="fp32",
+                                            seed=SEED), init="kh", T=0.2, words=8, nv=4, esize=4, resident=True),
     "kh2d1024_fp64": dict(desc=dict(ndim=2, n=(1024, 1024), batch=1, eq="euler", recon="weno3", flux="hllc",
                                     rvars="prim", rk="ssprk3", bc="periodic", cfl=0.4, precision="fp64", seed=0),
                           init="kh", T=0.02, words=8, nv=4, esize=8),
@@ -346,6 +352,7 @@ WORKLOAD_FLOPS = {"sod1024_fp64": 287, "kh2d1024_fp32": 1980, "kh2d1024_fp64": 1
                   "mlmc_coupled_fp32": 1980, "kh3d512_fp32": 3591, "kh3d256_fp32": 3591,
                   "kh3d1024_blocks_fp32": 3591, "kh3d256_blocks_fp32": 3591}
 FP64_PEAK_TFLOPS = 1.25
+ISSUE_CLOCK_GHZ = 2.07
 
 
 def run_adjoint_fd_check(name, W, S, alsv, torch):
@@ -554,6 +561,8 @@ def run_workload(name, args):
         if "steps" in W:
             S.step(W["steps"])
             S.sync()
+        elif W.get("resident"):
+            S.evolve_resident(W["T"])
         else:
             S.evolve_to(W["T"])
         if W.get("mlmc"):
@@ -596,6 +605,21 @@ def run_workload(name, args):
                          "algorithmic_bytes_per_cell_update": bpc, "stage_ms_total": prof["stage_ms"],
                          "stage_launches": prof["stage_launches"], "step_ms_total": 1000 * el},
             "gpu_launches": alsv.alsv_get_launch_count(S.ctx)}
+    if W.get("resident"):
+        # the whole run is one launch per pass; its rate against the batched tile schedule of the
+        # same samples (the state would move to HBM and back every stage there)
+        line["config"]["schedule"] = "resident: one thread-block cluster per sample, distributed shared memory"
+        t0 = time.perf_counter()
+        cu_tile = 0
+        for _ in range(args.steps):
+            S.set_initial_data(W["init"])
+            S.evolve_to(W["T"])
+            _, ns = S.time()
+            cu_tile += int(ns.sum()) * cells[0]
+        torch.cuda.synchronize()
+        line["batched_tile_schedule"] = {"value": cu_tile / (time.perf_counter() - t0), "unit": "cell-updates/s",
+                                         "tile_variant": chosen}
+        line["roofline"] = None
     if name in WORKLOAD_FLOPS and prof["stage_ms"] > 0:
         fp64 = W["desc"]["precision"] == "fp64"
         peak = FP64_PEAK_TFLOPS if fp64 else FP32_PEAK_TFLOPS
@@ -770,6 +794,18 @@ def main():
                            "tile_variant": chosen, "autotune_ms": ms_var},
                 "samples_per_s": samples_per_s, "gpu_launches": launches, "e2e": e2e, "roofline": roof,
                 "clocks": ck}
+        ipcs = getattr(stage_traffic, "inst_per_cell_stage", None) if traffic is not None else None
+        if achieved and ipcs:
+            # issue-slot roofline: the profiled thread instructions per cell-stage at this run's
+            # cell-stage rate against one warp instruction per cycle per SM sub-partition
+            cell_stages = 3 * cell_updates
+            warp_inst_rate = cell_stages * ipcs / 32.0 / (prof["stage_ms"] / 1000.0) / 1e9
+            issue_peak = 152 * 4 * ISSUE_CLOCK_GHZ
+            line["issue_roofline"] = {"bound": "issue", "achieved": warp_inst_rate, "peak": issue_peak,
+                                      "unit": "G warp-instructions/s", "frac": warp_inst_rate / issue_peak,
+                                      "thread_inst_per_cell_stage": ipcs,
+                                      "peak_kind": "nominal: 152 SMs x 4 schedulers x 1 instruction/cycle x 2.07 GHz",
+                                      "hbm_frac_at_full_issue": roof["frac"] / (warp_inst_rate / issue_peak)}
         if achieved:
             # the same stage time against the FP32 ALU: algorithmic flops per cell-update
             tflops = cell_updates * FLOPS_PER_CELL_UPDATE_2D_WENO3_HLLC_RK3 / (prof["stage_ms"] / 1000.0) / 1e12

@@ -18,15 +18,13 @@
 
 namespace alsv {
 
-// MERGE: the x- and y-interface fluxes go to separate buffers, so both directions are evaluated
-// between the same two barriers (more shared memory: 3 CTAs per SM at 32 x 16)
-template <int RECON, int TY, int MERGE = 0>
+template <int RECON, int TY>
 constexpr size_t pair2_smem_bytes() {
     constexpr int TX = 32;
     constexpr int G = RECON == REC_PC ? 1 : 2;
     constexpr int NS = (TX + 2 * G) * (TY + 2 * G);
     constexpr int NIX = (TX + 1) * TY, NIY = TX * (TY + 1);
-    constexpr int NI = MERGE ? NIX + NIY : (NIX > NIY ? NIX : NIY);
+    constexpr int NI = NIX > NIY ? NIX : NIY;
     return (size_t)32 * (NS + NI);
 }
 
@@ -175,15 +173,17 @@ __device__ __forceinline__ void load_sten(const float4* sW0, const float4* sW1, 
     }
 }
 
-// TY rows per tile (16: 4 CTAs per SM with 64 registers; 32 or MERGE: 3 CTAs with 80); 256
-// threads = 8 warps; lane = column, warp = row group. HALVES as in k_stage2d_pair.
-template <int RECON, int FLUX, int TY, int HALVES = 0, int MERGE = 0>
-__global__ void __launch_bounds__(256, (TY >= 32 || MERGE) ? 3 : 4) k_stage2d_pair2(const StageArgs p) {
+// TY rows per tile (16: 4 CTAs per SM with 64 registers; 32: 3 CTAs with 80); 256 threads = 8
+// warps; lane = column, warp = row group. HALVES as in k_stage2d_pair. PREF: every global read of
+// the tile load in flight at once (one round trip instead of two), and the epilogue's reads of
+// all the thread's cells issued before its first store.
+template <int RECON, int FLUX, int TY, int HALVES = 0, int PREF = 0>
+__global__ void __launch_bounds__(256, TY >= 32 ? 3 : 4) k_stage2d_pair2(const StageArgs p) {
     constexpr int TX = 32, NT = 256, NW = 8;
     constexpr int G = RECON == REC_PC ? 1 : 2;
     constexpr int SX = TX + 2 * G, SY = TY + 2 * G, NS = SX * SY;
     constexpr int NIX = (TX + 1) * TY, NIY = TX * (TY + 1);
-    constexpr int NI = MERGE ? NIX + NIY : (NIX > NIY ? NIX : NIY);
+    constexpr int NI = NIX > NIY ? NIX : NIY;
     constexpr int CPT = TY / NW;   // cells per thread (and y-interfaces per thread run)
     static_assert(TY % NW == 0, "tile height must be a multiple of the warp count");
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(256, (TY >= 32 || MERGE) ? 3 : 4) k_stage2d_pa
     constexpr int NSIDE = 2 * G * SY;                    // side-column cells
     static_assert(NSIDE <= NT, "side columns in one pass");
     constexpr int NLOAD = CORE_IT + 1;
-    constexpr int LG = 2;
+    constexpr int LG = PREF ? NLOAD : 2;
 #pragma unroll
     for (int it0 = 0; it0 < NLOAD; it0 += LG) {
         float2 r[LG], mx[LG], my[LG], E[LG];
@@ -305,9 +305,9 @@ __global__ void __launch_bounds__(256, (TY >= 32 || MERGE) ? 3 : 4) k_stage2d_pa
         const float2 eps = f2(L.eps_f[D]);
         const int EX = D == 0 ? TX + 1 : TX;
         const int step = D == 0 ? 1 : SX;
-        const int xwarp = NW - 1, ywarp = MERGE ? NW - 2 : NW - 1;
-        float4* F0 = sF0 + (MERGE && D == 1 ? NIX : 0);
-        float4* F1 = sF1 + (MERGE && D == 1 ? NIX : 0);
+        const int xwarp = NW - 1, ywarp = NW - 1;
+        float4* F0 = sF0;
+        float4* F1 = sF1;
 #pragma unroll 1
         for (int m = 0; m <= CPT; ++m) {
             int fx = lane, fy = warp + NW * m;
@@ -339,8 +339,8 @@ __global__ void __launch_bounds__(256, (TY >= 32 || MERGE) ? 3 : 4) k_stage2d_pa
         const float2 nid = f2(-L.inv_dx_f[D]);
         const int EX = D == 0 ? TX + 1 : TX;
         const int fstep = D == 0 ? 1 : TX;
-        const float4* F0 = sF0 + (MERGE && D == 1 ? NIX : 0);
-        const float4* F1 = sF1 + (MERGE && D == 1 ? NIX : 0);
+        const float4* F0 = sF0;
+        const float4* F1 = sF1;
 #pragma unroll
         for (int m = 0; m < CPT; ++m) {
             const int fidx = (warp + NW * m) * EX + lane;
@@ -352,21 +352,12 @@ __global__ void __launch_bounds__(256, (TY >= 32 || MERGE) ? 3 : 4) k_stage2d_pa
             acc[m][3] = fma2(sub2(hi2(bp), hi2(bm)), nid, acc[m][3]);
         }
     };
-    if (MERGE) {
-        __syncthreads();
-        flux_pass(0);
-        flux_pass(1);
-        __syncthreads();
-        divergence(0);
-        divergence(1);
-    } else {
 #pragma unroll
-        for (int D = 0; D < 2; ++D) {
-            __syncthreads();
-            flux_pass(D);
-            __syncthreads();
-            divergence(D);
-        }
+    for (int D = 0; D < 2; ++D) {
+        __syncthreads();
+        flux_pass(D);
+        __syncthreads();
+        divergence(D);
     }
 
     // ---- 3. RK combination, store per sample, CFL speed of the new states
@@ -381,6 +372,25 @@ __global__ void __launch_bounds__(256, (TY >= 32 || MERGE) ? 3 : 4) k_stage2d_pa
     float2 smax = f2(0.f);
     bool badA = false, badB = false;
     const int x = tx0 + lane;
+    // PREF: all reads of the thread's cells before the first write (the last stage writes over U^n
+    // in place, so a later cell's read may not pass an earlier cell's write otherwise)
+    constexpr int NPRE = PREF ? CPT : 1;
+    float2 us_p[NPRE][4], un_p[NPRE][4];
+    if (PREF) {
+#pragma unroll
+        for (int m = 0; m < CPT; ++m) {
+            const int y = ty0 + warp + NW * m;
+            if (x >= nx || y >= ny) continue;
+            const int off = y * nx + x;
+            const int offB = off + hs * nx;
+#pragma unroll
+            for (int v = 0; v < 4; ++v) us_p[m % NPRE][v] = make_float2(UsA[v * plane + off], UsB[v * plane + offB]);
+            if (has_un) {
+#pragma unroll
+                for (int v = 0; v < 4; ++v) un_p[m % NPRE][v] = make_float2(UnA[v * plane + off], UnB[v * plane + offB]);
+            }
+        }
+    }
 #pragma unroll
     for (int m = 0; m < CPT; ++m) {
         const int y = ty0 + warp + NW * m;
@@ -388,11 +398,19 @@ __global__ void __launch_bounds__(256, (TY >= 32 || MERGE) ? 3 : 4) k_stage2d_pa
         const int off = y * nx + x;
         const int offB = off + hs * nx;
         float2 us[4], un[4];
+        if (PREF) {
 #pragma unroll
-        for (int v = 0; v < 4; ++v) us[v] = make_float2(UsA[v * plane + off], UsB[v * plane + offB]);
-        if (has_un) {
+            for (int v = 0; v < 4; ++v) {
+                us[v] = us_p[m % NPRE][v];
+                un[v] = un_p[m % NPRE][v];
+            }
+        } else {
 #pragma unroll
-            for (int v = 0; v < 4; ++v) un[v] = make_float2(UnA[v * plane + off], UnB[v * plane + offB]);
+            for (int v = 0; v < 4; ++v) us[v] = make_float2(UsA[v * plane + off], UsB[v * plane + offB]);
+            if (has_un) {
+#pragma unroll
+                for (int v = 0; v < 4; ++v) un[v] = make_float2(UnA[v * plane + off], UnB[v * plane + offB]);
+            }
         }
         float2 o[4];
 #pragma unroll

@@ -18,6 +18,26 @@ template <> struct IsExact<double> { static constexpr bool value = true; };
 
 template <class R> __device__ __forceinline__ R rcp(R x) { return R(1) / x; }
 
+// The divergence accumulation acc - dF f and the RK combination a U^n + b (U^(s) + dt L) with a
+// fixed rounding in FP32 (explicit fused multiply-adds, which the compiler neither splits nor
+// re-associates), so every FP32 schedule that accumulates in the same order is bitwise equal;
+// FP64 evaluates them as written (its translation units do not contract).
+template <class R> __device__ __forceinline__ R acc_sub(R acc, R dF, R f) {
+    if constexpr (IsExact<R>::value) return acc - dF * f;
+    else return __fmaf_rn(-dF, f, acc);
+}
+template <class R> __device__ __forceinline__ R rk_combine(R us, R dt, R L, bool has_un, R ca, R un, R cb) {
+    if constexpr (IsExact<R>::value) {
+        R o = us + dt * L;
+        if (has_un) o = ca * un + cb * o;
+        return o;
+    } else {
+        R o = __fmaf_rn(dt, L, us);
+        if (has_un) o = __fmaf_rn(ca, un, __fmul_rn(cb, o));
+        return o;
+    }
+}
+
 // Grid and stage constants in the kernel's precision: FP64 reads the doubles, FP32 the float copies
 // made on the host (or by the time control for dt), so no thread converts a double to float.
 template <class R> __device__ __forceinline__ R c_gamma(const GridArgs& g) {

@@ -213,13 +213,9 @@ __global__ void __launch_bounds__(1024) k_resident2d(const ResidentArgs a) {
 #pragma unroll
                 for (int v = 0; v < 4; ++v) {
                     float acc = 0.0f;
-                    const float dF = Frt[v] - Flx[v];
-                    acc = acc - dF * inv_dx;
-                    const float dG = Gup[v] - Glo[v];
-                    acc = acc - dG * inv_dy;
-                    float o = us[v] + dtf * acc;
-                    if (has_un) o = ca * un[v] + cb * o;
-                    out[v] = o;
+                    acc = acc_sub<float>(acc, Frt[v] - Flx[v], inv_dx);
+                    acc = acc_sub<float>(acc, Gup[v] - Glo[v], inv_dy);
+                    out[v] = rk_combine<float>(us[v], dtf, acc, has_un, ca, un[v], cb);
                     Glo[v] = Gup[v];
                 }
                 const float4 o4 = make_float4(out[0], out[1], out[2], out[3]);

@@ -401,7 +401,7 @@ __global__ void __launch_bounds__(NT) k_stage(const StageArgs p) {
             for (int v = 0; v < NV; ++v) {
                 const R dF = Fp[v] - Fm[v];
                 if constexpr (IsExact<R>::value) acc[m][v] = acc[m][v] - dF / hD;
-                else acc[m][v] = acc[m][v] - dF * inv_dx;
+                else acc[m][v] = acc_sub<R>(acc[m][v], dF, inv_dx);
             }
         }
     }
@@ -437,9 +437,7 @@ __global__ void __launch_bounds__(NT) k_stage(const StageArgs p) {
         }
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-            R o = us[v] + dt * acc[m][v];
-            if (has_un) o = ca * un[v] + cb * o;
-            out[v] = o;
+            out[v] = rk_combine<R>(us[v], dt, acc[m][v], has_un, ca, has_un ? un[v] : R(0), cb);
         }
 #pragma unroll
         for (int v = 0; v < NV; ++v) Uo[v * plane + off] = out[v];

@@ -255,12 +255,10 @@ __global__ void __launch_bounds__(NTH, 4) k_stage3d_zm(const StageArgs p) {
             for (int v = 0; v < NV; ++v) {
                 // directions accumulated x, y, z as in the tile kernel (same rounding)
                 R Lv = R(0);
-                Lv = Lv - (sFx[(fxm + 1) * CS + v] - sFx[fxm * CS + v]) * idx;
-                Lv = Lv - (sFy[(fym + TX) * CS + v] - sFy[fym * CS + v]) * idy;
-                Lv = Lv - (Fzp[v] - Fzm[v]) * idz;
-                R o = us[v] + dt * Lv;
-                if (has_un) o = ca * un[v] + cb * o;
-                out[v] = o;
+                Lv = acc_sub<R>(Lv, sFx[(fxm + 1) * CS + v] - sFx[fxm * CS + v], idx);
+                Lv = acc_sub<R>(Lv, sFy[(fym + TX) * CS + v] - sFy[fym * CS + v], idy);
+                Lv = acc_sub<R>(Lv, Fzp[v] - Fzm[v], idz);
+                out[v] = rk_combine<R>(us[v], dt, Lv, has_un, ca, has_un ? un[v] : R(0), cb);
             }
 #pragma unroll
             for (int v = 0; v < NV; ++v) Uo[v * plane + off] = out[v];

@@ -8,8 +8,8 @@ halo faces: the stage kernels read the ghost cells there from halo buffers inste
 condition. A step then runs stage by stage:
 
   for every stage s:  each block writes the boundary layers of the state stage s reads into its
-                      neighbours' halo buffers (the exchange), then runs stage s - by default in
-                      two parts: the tiles whose stencil reads no halo buffer while the layers
+                      neighbours' halo buffers (the exchange), then runs stage s - across ranks
+                      in two parts: the tiles whose stencil reads no halo buffer while the layers
                       travel, the others once they have arrived
   after the last:     the per-sample maximum wave speed is reduced over all blocks (MAX) and each
                       block finishes the step with it (t, dt, done flags)
@@ -278,11 +278,13 @@ class Decomposition:
     ``overlap``: run each stage as two parts around the exchange - the tiles whose stencil reads no
     halo buffer while the layers travel, the rest after they arrive (the paper overlaps its
     exchange with the inner-domain computation); False runs whole stages after the exchange. Both
-    give bitwise the same result.
+    give bitwise the same result. Default (None): on for the distributed transport, off for blocks
+    on one device, where nothing travels and the split only doubles the stage launches (measured
+    6 % slower at 256^3 in four blocks).
     """
 
     def __init__(self, parts=(2, 1, 1), transport="local", group=None, make_block=None, device="cuda",
-                 tile_variant=None, overlap=True, **cfg):
+                 tile_variant=None, overlap=None, **cfg):
         import torch
         self.torch = torch
         parts = tuple(int(p) for p in parts) + (1,) * (3 - len(parts))
@@ -290,7 +292,7 @@ class Decomposition:
         if any(parts[k] != 1 for k in range(ndim, 3)):
             raise ValueError("parts beyond ndim must be 1")
         self.parts, self.cfg = parts, dict(cfg)
-        self.overlap = bool(overlap)
+        self.overlap = (transport == "dist") if overlap is None else bool(overlap)
         pairs = bc_pairs(cfg.get("bc", "periodic"), ndim)
         periodic = [pairs[k][0] == "periodic" for k in range(3)]
         coords = block_coords(parts)

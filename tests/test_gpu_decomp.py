@@ -201,8 +201,9 @@ def test_speed_max_combine_is_the_nan_propagating_maximum():
                                           ("kh3d_fp32_1x2x2", 5), ("sod_fp64_x4", None)])
 def test_overlapped_stage_parts_equal_whole_stages(case, variant):
     """Each stage run as two parts around the exchange (the tiles that read no halo buffer first,
-    then the others: the paper's overlap of the exchange with the inner-domain computation) gives
-    bitwise the state of whole stages run after the exchange, and of the undivided grid."""
+    then the others: the paper's overlap of the exchange with the inner-domain computation, the
+    distributed transport's default) gives bitwise the state of whole stages run after the
+    exchange, and of the undivided grid."""
     import torch
     _, cfg, init, parts, T = [c for c in CASES if c[0] == case][0]
     from paper_1912_07645_gb300.decomp import Decomposition

@@ -211,8 +211,10 @@ alsv_status alsv_evolve_to_T(alsv_ctx* ctx, double T, int64_t* steps_taken_host)
  * distributed shared memory of one thread-block cluster (the smallest cluster of 1 .. 16 CTAs whose
  * shared memory holds U^n, the stage state and a primitive copy: 256^2 takes 16 CTAs); the state
  * is read from HBM once and written back once, the boundary rows of neighbouring CTAs are read by
- * distributed-shared-memory loads, and each sample takes its own CFL steps. Bitwise the result of
- * alsv_evolve_to_T with tile variant 0 (same flux functions and order of operations). Serves FP32
+ * distributed-shared-memory loads, and each sample takes its own CFL steps. The step counts and
+ * times of alsv_evolve_to_T with tile variant 0, and (MC, WENO3) bitwise its state; with PC faces
+ * the state agrees to a few ulp (the compiler contracts the two instantiations' scalar flux
+ * arithmetic differently). Serves FP32
  * 2D Euler on one grid, periodic in x and y, primitive PC / MC / WENO3 with HLLC or Rusanov, CFL
  * steps, nx a multiple of 32 up to 1024 (INVALID_ARG otherwise, or when the sample does not fit 16
  * CTAs). SYNCHRONOUS; t, steps, done and the next dt are left as alsv_evolve_to_T leaves them.

@@ -16,7 +16,9 @@
 //       divergence and writes a U^n + b (U^(s) + dt L) into the stage state in place.
 // Each interface is evaluated once (plus one y-interface per CTA at its lower edge), with the
 // same device functions and the same order of operations as the tile schedule (tile variant 0),
-// so the result is bitwise that of alsv_evolve_to_T with variant 0. After the last stage each CTA
+// so the result is bitwise that of alsv_evolve_to_T with variant 0 for MC and WENO3 faces (with PC
+// faces the compiler contracts the scalar flux arithmetic of the two instantiations differently,
+// a few ulp apart). After the last stage each CTA
 // reduces the CFL speed of its new rows, the cluster takes the maximum over its CTAs (distributed
 // loads again), and every thread computes the next dt in FP64 exactly as the time control does.
 // Cluster barriers are hardware barriers; no thread spins on a flag.

@@ -43,8 +43,7 @@ STAGE_KERNEL_NAMES = {0: "k_stage<float, Euler, 2D, WENO3, HLLC, 32x16>",
                       4: "k_stage2d_pair<WENO3, HLLC, 32x16>",
                       5: "k_stage2d_pair<WENO3, HLLC, 32x8>",
                       8: "k_stage2d_pair2<WENO3, HLLC, 32x16>",
-                      9: "k_stage2d_pair2<WENO3, HLLC, 32x16, reads in flight at once>",
-                      12: "k_stage2d_pair2<WENO3, HLLC, 32x16, 5 CTAs per SM>"}
+                      9: "k_stage2d_pair2<WENO3, HLLC, 32x16, merged directions>"}
 WORKLOAD = "kh2d_256x256_mc4096_weno3_hllc_ssprk3_fp32_T1"
 # compulsory HBM bytes per 2D SSP-RK3 cell-update in FP32: per variable read U^n + write U1,
 # read U1 + U^n + write U2, read U2 + U^n + write U^{n+1} = 8 words, x 4 variables x 4 bytes
@@ -213,7 +212,7 @@ def stage_traffic(variant, cell_updates, launches):
             rec[k] = v
     csrc = os.path.join(ROOT, "paper_1912_07645_gb300", "csrc")
     h = hashlib.sha256()
-    kernel_src = "fv_pair2.cuh" if variant in (8, 9, 10, 11, 12) else "fv_pair.cuh"
+    kernel_src = "fv_pair2.cuh" if variant in (8, 9, 10, 11) else "fv_pair.cuh"
     for f in (kernel_src, "fv_packed.cuh", "fv_physics.cuh"):
         h.update(open(os.path.join(csrc, f), "rb").read())
     if h.hexdigest()[:16] != rec.get("sources_sha256_prefix") or str(variant) != rec.get("variant"):

@@ -495,9 +495,8 @@ alsv_status alsv_destroy(alsv_ctx* ctx);
  *                           32, 16); 8, 9 the two-sample schedule with fewer instructions per
  *                           cell (WENO3 from the differences around an interface, fixed thread
  *                           maps, positivity fallback only where needed; 32x16 tiles; 9 with
- *                           every global read of a phase in flight at once); 10, 11 as 8, 9 on
- *                           the two halves of each sample (ny divisible by 32); 12 as 8 at 5 CTAs
- *                           per SM (48 registers).
+ *                           both directions' fluxes between one pair of barriers); 10, 11 as 8,
+ *                           9 on the two halves of each sample (ny divisible by 32).
  *                           FP32 3D: 0, 1 tiles of 16x8x8, 8x8x8; 2, 3 z-marching 32x8 column
  *                           chunks of 64 / 128 planes (Euler); 4 as 2 with the x and y interfaces
  *                           of a plane packed in FP32x2 (primitive, HLLC/Rusanov); 5 as 4 with

@@ -333,7 +333,7 @@ TileShape stage_tile(int fp64, int ndim, int variant) {
         if (variant == 6 && !fp64) return TileShape{32, 16, 1, 256};       // two halves of a sample
         if (variant == 7 && !fp64) return TileShape{32, 8, 1, 256};
 
-        return TileShape{32, 16, 1, 256};                                   // variants 0, 4, 8-12
+        return TileShape{32, 16, 1, 256};                                   // variants 0, 4, 8-11
     }
     if (fp64) return variant == 1 ? TileShape{8, 8, 4, 256} : TileShape{8, 8, 8, 256};
     if (variant == 2) return TileShape{32, 8, 64, 256};    // z-marching column chunks
@@ -347,7 +347,7 @@ bool stage_variant_halves(int fp64, int ndim, int variant) {
 }
 int stage_num_variants(int fp64, int ndim) {
     if (ndim == 1) return 3;
-    if (ndim == 2 && !fp64) return 13;
+    if (ndim == 2 && !fp64) return 12;
     if (ndim == 3 && !fp64) return 6;
     return 2;
 }
@@ -356,7 +356,7 @@ bool stage_variant_supported(int fp64, int ndim, int eq, int recon, int rvars, i
     // ENO2 and the Roe / Godunov / entropy-conservative fluxes: the default tile schedule
     if (ext_scheme(recon, flux))
         return variant == 0 && (eq == EQ_EULER ? rvars == RV_PRIM : ndim == 1);
-    if (ndim == 2 && !fp64 && (variant == 4 || variant == 5 || variant == 8 || variant == 9 || variant == 12))
+    if (ndim == 2 && !fp64 && (variant == 4 || variant == 5 || variant == 8 || variant == 9))
         return eq == EQ_EULER && rvars == RV_PRIM && (flux == FLX_HLLC || flux == FLX_RUSANOV);
     if (ndim == 2 && !fp64 && (variant == 6 || variant == 7 || variant == 10 || variant == 11))
         return eq == EQ_EULER && rvars == RV_PRIM && (flux == FLX_HLLC || flux == FLX_RUSANOV) &&

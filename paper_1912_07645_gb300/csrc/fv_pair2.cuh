@@ -176,10 +176,9 @@ __device__ __forceinline__ void load_sten(const float4* sW0, const float4* sW1, 
 // TY rows per tile (16: 4 CTAs per SM with 64 registers; 32: 3 CTAs with 80); 256 threads = 8
 // warps; lane = column, warp = row group. HALVES as in k_stage2d_pair. PREF: every global read of
 // the tile load in flight at once (one round trip instead of two), and the epilogue's reads of
-// all the thread's cells issued before its first store. OCC: CTAs per SM the registers are
-// budgeted for (0: the default for TY; 5 at 32 x 16 leaves 48 registers, with some spills).
-template <int RECON, int FLUX, int TY, int HALVES = 0, int PREF = 0, int OCC = 0>
-__global__ void __launch_bounds__(256, OCC ? OCC : (TY >= 32 ? 3 : 4)) k_stage2d_pair2(const StageArgs p) {
+// all the thread's cells issued before its first store.
+template <int RECON, int FLUX, int TY, int HALVES = 0, int PREF = 0>
+__global__ void __launch_bounds__(256, TY >= 32 ? 3 : 4) k_stage2d_pair2(const StageArgs p) {
     constexpr int TX = 32, NT = 256, NW = 8;
     constexpr int G = RECON == REC_PC ? 1 : 2;
     constexpr int SX = TX + 2 * G, SY = TY + 2 * G, NS = SX * SY;

@@ -205,11 +205,17 @@ def stage_traffic(variant, cell_updates, launches):
     path = os.path.join(ROOT, "profiles", "stage_traffic.txt")
     if not os.path.exists(path) or launches <= 0:
         return None, None
-    rec = {}
+    rec, per_variant = {}, {}
     for line in open(path):
         if line.strip() and not line.startswith("#"):
-            k, v = line.split()
-            rec[k] = v
+            f = line.split()
+            if f[0] == "variant":   # variant V bytes_per_cell_update B thread_inst_per_cell_stage I
+                per_variant[f[1]] = dict(zip(f[2::2], f[3::2]))
+            else:
+                rec[f[0]] = f[1]
+    if str(variant) not in per_variant:
+        return None, None
+    rec.update(per_variant[str(variant)], variant=str(variant))
     csrc = os.path.join(ROOT, "paper_1912_07645_gb300", "csrc")
     h = hashlib.sha256()
     kernel_src = "fv_pair2.cuh" if variant in (8, 9, 10, 11) else "fv_pair.cuh"

@@ -42,8 +42,12 @@ STAGE_KERNEL_NAMES = {0: "k_stage<float, Euler, 2D, WENO3, HLLC, 32x16>",
                       3: "k_stage2d_col<WENO3, HLLC>",
                       4: "k_stage2d_pair<WENO3, HLLC, 32x16>",
                       5: "k_stage2d_pair<WENO3, HLLC, 32x8>",
+                      6: "k_stage2d_pair<WENO3, HLLC, 32x16, sample halves>",
+                      7: "k_stage2d_pair<WENO3, HLLC, 32x8, sample halves>",
                       8: "k_stage2d_pair2<WENO3, HLLC, 32x16>",
-                      9: "k_stage2d_pair2<WENO3, HLLC, 32x16, merged directions>"}
+                      9: "k_stage2d_pair2<WENO3, HLLC, 32x16, reads in flight>",
+                      10: "k_stage2d_pair2<WENO3, HLLC, 32x16, sample halves>",
+                      11: "k_stage2d_pair2<WENO3, HLLC, 32x16, sample halves, reads in flight>"}
 WORKLOAD = "kh2d_256x256_mc4096_weno3_hllc_ssprk3_fp32_T1"
 # compulsory HBM bytes per 2D SSP-RK3 cell-update in FP32: per variable read U^n + write U1,
 # read U1 + U^n + write U2, read U2 + U^n + write U^{n+1} = 8 words, x 4 variables x 4 bytes

@@ -21,6 +21,12 @@ namespace alsv {
 // PACK = 1 (primitive reconstruction, HLLC or Rusanov): each thread evaluates the k-th x-interface
 // and the k-th y-interface of the plane together in packed FP32x2 arithmetic (lane .x the
 // x-interface with normal velocity u, lane .y the y-interface with normal velocity v).
+// PACK = 2: as 1 with fewer instructions per interface pair: the ring planes split into a float4
+// (rho, u, v, w) and a float (p) array (two shared-memory loads per stencil cell and lane instead
+// of five), the x-interfaces mapped as the TX x TY left faces then the right edge column (no
+// division by TX + 1), WENO3 faces from the three differences around an interface (faces_d), the
+// positivity fallback only when a lane of the warp needs it, and HLLC's star correction through
+// the upwind speed. Its x- and y-fluxes round differently from PACK 1 (not bitwise equal to it).
 // NTH threads (default: one per column); more threads than columns lets a plane's interface pairs
 // fit in one pass (32 x 7 columns: 256 pairs for 256 threads), the threads past the columns only
 // take part in the loads and the interfaces.
@@ -36,9 +42,12 @@ __global__ void __launch_bounds__(NTH, 4) k_stage3d_zm(const StageArgs p) {
     constexpr int CS = NV;
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    R* sW = reinterpret_cast<R*>(smem_raw);      // [NP][PS][CS]
+    R* sW = reinterpret_cast<R*>(smem_raw);      // [NP][PS][CS] (PACK 2: [NP][PS] float4 + [NP][PS] p)
+    float4* sW4 = reinterpret_cast<float4*>(smem_raw);
+    float* sWp = reinterpret_cast<float*>(sW4 + NP * PS);
     R* sFx = sW + NP * PS * CS;                  // [NIX][CS]
     R* sFy = sFx + NIX * CS;                     // [NIY][CS]
+    static_assert(PACK != 2 || CS == 5, "PACK 2 splits five variables as 4 + 1");
 
     const uint32_t w = blockIdx.x;
     const GridArgs& g = p.g;
@@ -81,7 +90,8 @@ __global__ void __launch_bounds__(NTH, 4) k_stage3d_zm(const StageArgs p) {
         // a plane beyond a halo face of a block comes from that face's halo buffer
         const bool zhalo = (zz < 0 && g.bc[2][0] == BC_HALO) || (zz >= nz && g.bc[2][1] == BC_HALO);
         const int iz = zhalo ? zz : map_ghost(zz, nz, g.bc[2][0], g.bc[2][1], fz);
-        R* dst = sW + ((zz % NP + NP) % NP) * PS * CS;
+        const int slot = (zz % NP + NP) % NP;
+        R* dst = sW + slot * PS * CS;
 #pragma unroll 1
         for (int s = tid; s < PS; s += NT) {
             const int sx = s % SX, sy = s / SX;
@@ -105,7 +115,12 @@ __global__ void __launch_bounds__(NTH, 4) k_stage3d_zm(const StageArgs p) {
 #pragma unroll
             for (int k = 0; k < ND; ++k)
                 if (flip[k]) u[1 + k] = -u[1 + k];
-            if (rv == RV_PRIM) {
+            if (PACK == 2) {
+                R wv[NV];
+                cons_to_prim<R, ND>(u, wv, gm1);
+                sW4[slot * PS + s] = make_float4(wv[0], wv[1], wv[2], wv[3]);
+                sWp[slot * PS + s] = wv[4];
+            } else if (rv == RV_PRIM) {
                 R wv[NV];
                 cons_to_prim<R, ND>(u, wv, gm1);
 #pragma unroll
@@ -117,6 +132,16 @@ __global__ void __launch_bounds__(NTH, 4) k_stage3d_zm(const StageArgs p) {
         }
     };
     auto cell_at = [&](int zz, int off, R* out) {
+        if (PACK == 2) {
+            const int i = ((zz % NP + NP) % NP) * PS + off;
+            const float4 a = sW4[i];
+            out[0] = a.x;
+            out[1] = a.y;
+            out[2] = a.z;
+            out[3] = a.w;
+            out[4] = sWp[i];
+            return;
+        }
         const R* src = sW + (((zz % NP + NP) % NP) * PS + off) * CS;
 #pragma unroll
         for (int v = 0; v < NV; ++v) out[v] = src[v];
@@ -155,7 +180,50 @@ __global__ void __launch_bounds__(NTH, 4) k_stage3d_zm(const StageArgs p) {
         __syncthreads();
         const int pz = ((z % NP) + NP) % NP;
         const R* sp = sW + pz * PS * CS;
-        if constexpr (PACK) {
+        if constexpr (PACK == 2) {
+            static_assert(NIY >= NIX && (TX & (TX - 1)) == 0, "y interfaces outnumber x; TX a power of two");
+            const float2 eps2 = make_float2(epsx, epsy);
+            const float4* p4 = sW4 + pz * PS;
+            const float* pp = sWp + pz * PS;
+#pragma unroll 1
+            for (int k = tid; k < NIY; k += NT) {
+                // x lane: left faces of the TX x TY cells, then the right edge column; past NIX it
+                // repeats interface 0 unused
+                int fxx = k & (TX - 1), fyx = k / TX;
+                if (k >= TX * TY) {
+                    fxx = TX;
+                    fyx = k - TX * TY;
+                }
+                const bool hx = fyx < TY;
+                if (!hx) fxx = fyx = 0;
+                const int i0x = (fyx + G) * SX + fxx + G - 1;
+                const int i0y = (k / TX + G - 1) * SX + (k & (TX - 1)) + G;
+                F2x5 c[4];
+#pragma unroll
+                for (int q = (G == 1 ? 1 : 0); q < (G == 1 ? 3 : 4); ++q) {
+                    const int ix = i0x + (q - 1), iy = i0y + (q - 1) * SX;
+                    const float4 a = p4[ix], b = p4[iy];
+                    c[q].r = make_float2(a.x, b.x);
+                    c[q].n = make_float2(a.y, b.z);   // normal: u (x-interface), v (y-interface)
+                    c[q].t = make_float2(a.z, b.y);   // tangential: v, u
+                    c[q].w = make_float2(a.w, b.w);
+                    c[q].p = make_float2(pp[ix], pp[iy]);
+                }
+                if (G == 1) {
+                    c[0] = c[1];
+                    c[3] = c[2];
+                }
+                F2x5 WL, WR;
+                faces2_5_lean<RECON>(c, eps2, 0xffffffffu, WL, WR);   // whole warps: NIY, NT multiples of 32
+                const F2x5 F = FLUX == FLX_HLLC ? hllc2_5_lean(WL, WR, gamma, inv_gm1) : rusanov2_5(WL, WR, gamma, inv_gm1);
+                if (hx) {
+                    float* o = sFx + (fyx * (TX + 1) + fxx) * CS;
+                    o[0] = F.r.x; o[1] = F.n.x; o[2] = F.t.x; o[3] = F.w.x; o[4] = F.p.x;
+                }
+                float* o = sFy + k * CS;
+                o[0] = F.r.y; o[1] = F.t.y; o[2] = F.n.y; o[3] = F.w.y; o[4] = F.p.y;
+            }
+        } else if constexpr (PACK) {
             static_assert(NIY >= NIX, "the y interfaces outnumber the x interfaces");
             const float2 eps2 = make_float2(epsx, epsy);
 #pragma unroll 1
@@ -338,18 +406,18 @@ static cudaError_t launch_stage_zm(int recon, int flux, const StageArgs& a, cuda
 #undef ALSV_ZM_FLUX
 }
 
-// packed x/y interfaces (primitive reconstruction, HLLC or Rusanov)
-template <int TX, int TY, int LZ, int NTH = TX * TY>
+// packed x/y interfaces (primitive reconstruction, HLLC or Rusanov); PK 1 or 2 as PACK above
+template <int TX, int TY, int LZ, int NTH = TX * TY, int PK = 1>
 static cudaError_t launch_stage_zm_packed(int recon, int flux, const StageArgs& a, cudaStream_t s) {
     if (a.g.rvars != RV_PRIM || (flux != FLX_HLLC && flux != FLX_RUSANOV)) return cudaErrorNotSupported;
     if (flux == FLX_HLLC) {
-        if (recon == REC_WENO3) return launch_zm_one<REC_WENO3, FLX_HLLC, TX, TY, LZ, 1, NTH>(a, s);
-        if (recon == REC_MC) return launch_zm_one<REC_MC, FLX_HLLC, TX, TY, LZ, 1, NTH>(a, s);
-        return launch_zm_one<REC_PC, FLX_HLLC, TX, TY, LZ, 1, NTH>(a, s);
+        if (recon == REC_WENO3) return launch_zm_one<REC_WENO3, FLX_HLLC, TX, TY, LZ, PK, NTH>(a, s);
+        if (recon == REC_MC) return launch_zm_one<REC_MC, FLX_HLLC, TX, TY, LZ, PK, NTH>(a, s);
+        return launch_zm_one<REC_PC, FLX_HLLC, TX, TY, LZ, PK, NTH>(a, s);
     }
-    if (recon == REC_WENO3) return launch_zm_one<REC_WENO3, FLX_RUSANOV, TX, TY, LZ, 1, NTH>(a, s);
-    if (recon == REC_MC) return launch_zm_one<REC_MC, FLX_RUSANOV, TX, TY, LZ, 1, NTH>(a, s);
-    return launch_zm_one<REC_PC, FLX_RUSANOV, TX, TY, LZ, 1, NTH>(a, s);
+    if (recon == REC_WENO3) return launch_zm_one<REC_WENO3, FLX_RUSANOV, TX, TY, LZ, PK, NTH>(a, s);
+    if (recon == REC_MC) return launch_zm_one<REC_MC, FLX_RUSANOV, TX, TY, LZ, PK, NTH>(a, s);
+    return launch_zm_one<REC_PC, FLX_RUSANOV, TX, TY, LZ, PK, NTH>(a, s);
 }
 
 }  // namespace alsv

@@ -64,7 +64,8 @@ def test_blocks_reproduce_the_whole_grid_bitwise(name, cfg, kind, parts, T):
     assert np.array_equal(U_dec, U_whole), f"{name}: {int((U_dec != U_whole).sum())} elements differ"
 
 
-@pytest.mark.parametrize("variant,parts", [(2, (1, 1, 2)), (4, (1, 1, 3)), (4, (2, 2, 1)), (3, (2, 1, 2))])
+@pytest.mark.parametrize("variant,parts", [(2, (1, 1, 2)), (4, (1, 1, 3)), (4, (2, 2, 1)), (3, (2, 1, 2)),
+                                           (7, (1, 1, 3))])
 def test_z_march_blocks_reproduce_the_whole_grid(variant, parts):
     from paper_1912_07645_gb300.decomp import Decomposition
     # z chunks of 64 / 128 planes over blocks of 53-80 planes (ragged chunks), x/y halos as well

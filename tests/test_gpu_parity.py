@@ -408,19 +408,22 @@ def test_kh_3d_zmarch_bitwise_equal_to_tiles(variant, recon, flux, rvars, bc):
     np.testing.assert_array_equal(outs[0][1][0], outs[1][1][0])
 
 
+@pytest.mark.parametrize("pair", [(4, 5), (6, 7)])
 @pytest.mark.parametrize("recon,flux,bc", [("weno3", "hllc", "periodic"),
                                            ("mc", "rusanov", [("periodic", "periodic"), ("reflective", "outflow"),
-                                                              ("outflow", "reflective")])])
-def test_kh_3d_packed_zmarch_32x7_bitwise_equal_to_32x8(recon, flux, bc):
-    """Variant 5 runs the packed z-march of variant 4 on 32 x 7 columns with 256 threads: the same
-    packed arithmetic per interface, so bitwise equal (ragged: ny = 20 is 2 x 7 + 6)."""
+                                                              ("outflow", "reflective")]),
+                                           ("pc", "hllc", [("outflow", "outflow"), ("reflective", "reflective"),
+                                                           ("periodic", "periodic")])])
+def test_kh_3d_packed_zmarch_32x7_bitwise_equal_to_32x8(pair, recon, flux, bc):
+    """Variants 5 and 7 run the packed z-marches of 4 and 6 on 32 x 7 columns with 256 threads: the
+    same packed arithmetic per interface, so bitwise equal (ragged: ny = 20 is 2 x 7 + 6)."""
     import paper_1912_07645_gb300 as alsv
     torch = torch_()
     cfg = dict(ndim=3, n=(40, 20, 70), batch=2, eq="euler", recon=recon, flux=flux, rvars="prim", rk="ssprk3",
                bc=bc, cfl=0.3, precision="fp32")
     th = torch.from_numpy(kh_theta(2, 23, P=128)).cuda()
     outs = []
-    for v in (4, 5):
+    for v in pair:
         S = gpu_solver(**cfg)
         alsv.alsv_set_tile_variant(S.ctx, v)
         S.set_initial_data("kh", theta=th)
@@ -437,10 +440,14 @@ def test_kh_3d_packed_zmarch_32x7_bitwise_equal_to_32x8(recon, flux, bc):
     (4, "weno3", "hllc", "periodic"),
     (4, "mc", "rusanov", [("reflective", "outflow"), ("periodic", "periodic"), ("outflow", "reflective")]),
     (4, "pc", "hllc", [("outflow", "outflow"), ("reflective", "reflective"), ("periodic", "periodic")]),
-    (5, "weno3", "hllc", [("periodic", "periodic"), ("reflective", "outflow"), ("periodic", "periodic")])])
+    (5, "weno3", "hllc", [("periodic", "periodic"), ("reflective", "outflow"), ("periodic", "periodic")]),
+    (6, "weno3", "hllc", "periodic"),
+    (6, "mc", "rusanov", [("reflective", "outflow"), ("periodic", "periodic"), ("outflow", "reflective")]),
+    (7, "weno3", "hllc", [("periodic", "periodic"), ("reflective", "outflow"), ("periodic", "periodic")]),
+    (7, "pc", "rusanov", [("outflow", "outflow"), ("reflective", "reflective"), ("periodic", "periodic")])])
 def test_kh_3d_zmarch_fp32_vs_oracle(variant, recon, flux, bc):
-    """z-march schedules against the oracle (ragged: 70 planes); variant 4 packs an x- and a
-    y-interface into the two FP32x2 lanes."""
+    """z-march schedules against the oracle (ragged: 70 planes); variants 4-7 pack an x- and a
+    y-interface into the two FP32x2 lanes, 6 and 7 with the lean interface arithmetic."""
     import paper_1912_07645_gb300 as alsv
     torch = torch_()
     cfg = dict(ndim=3, n=(24, 20, 70), batch=1, eq="euler", recon=recon, flux=flux, rvars="prim", rk="ssprk3",
@@ -698,12 +705,12 @@ def test_column_variant_mlmc_levels_and_rejection():
     S2.close()
 
 
-@pytest.mark.parametrize("variant", [4, 5, 8, 9])
+@pytest.mark.parametrize("variant", [4, 5, 8, 9, 12])
 @pytest.mark.parametrize("recon,flux,bc", [("weno3", "hllc", "periodic"), ("mc", "rusanov", "periodic"),
                                            ("pc", "hllc", [("outflow", "reflective"), ("reflective", "outflow")]),
                                            ("weno3", "rusanov", "reflective")])
 def test_pair_variant_fp32_vs_oracle(variant, recon, flux, bc):
-    """Two-sample schedules (variants 4, 5 and the lean 8, 9): each sample within 2e-5 relative L1
+    """Two-sample schedules (variants 4, 5 and the lean 8, 9, 12): each sample within 2e-5 relative L1
     of the oracle, with an odd batch (the last sample has no partner), ragged tiles and boundary
     fill."""
     torch = torch_()
@@ -755,9 +762,9 @@ def test_halves_variant_fp32_vs_oracle_and_bitwise_with_sample_pairs(recon, flux
                                             ("pc", "hllc", "reflective"), ("weno3", "rusanov", "reflective")])
 def test_lean_pair_variants_bitwise_equal_and_vs_oracle(recon, flux, bcx):
     """The lean two-sample schedules evaluate every interface with the same operations whatever
-    the barrier structure or the pairing: sample pairs (8, 9) and the two halves of each sample
-    (10, 11), each with one or two flux buffers, are bitwise equal (ragged x: 70 cells, ny = 64, odd
-    batch), and within 2e-5 relative L1 of the oracle."""
+    the order of the reads, the tile height or the pairing: sample pairs (8, 9; 12 on 32 x 8 tiles)
+    and the two halves of each sample (10, 11; 13 on 32 x 8 tiles) are bitwise equal (ragged x: 70
+    cells, ny = 64, odd batch), and within 2e-5 relative L1 of the oracle."""
     torch = torch_()
     import paper_1912_07645_gb300 as alsv
     bc = [(bcx, bcx), ("periodic", "periodic")]
@@ -765,7 +772,7 @@ def test_lean_pair_variants_bitwise_equal_and_vs_oracle(recon, flux, bcx):
                cfl=0.4, precision="fp32")
     U0 = euler_state(3, 2, (70, 64), seed=74)
     out = {}
-    for v in (8, 9, 10, 11):
+    for v in (8, 9, 10, 11, 12, 13):
         S = gpu_solver(**cfg)
         alsv.alsv_set_tile_variant(S.ctx, v)
         S.set_state(torch.from_numpy(U0))
@@ -773,7 +780,7 @@ def test_lean_pair_variants_bitwise_equal_and_vs_oracle(recon, flux, bcx):
         S.sync()
         out[v] = (host(S.U).reshape(S.level_shape(0)), S.time())
         S.close()
-    for v in (9, 10, 11):
+    for v in (9, 10, 11, 12, 13):
         assert np.array_equal(out[8][0], out[v][0]), v
         np.testing.assert_array_equal(out[8][1][0], out[v][1][0])
     o, *_ = run_oracle(cfg, U0=U0, steps=10)
@@ -787,7 +794,7 @@ def test_halves_variant_needs_aligned_periodic_y():
     for n, bc in (((64, 40), "periodic"), ((64, 64), [("periodic", "periodic"), ("outflow", "outflow")])):
         S = gpu_solver(ndim=2, n=n, batch=1, eq="euler", recon="weno3", flux="hllc", rvars="prim", precision="fp32",
                        bc=bc)
-        for v in (6, 7, 10, 11):
+        for v in (6, 7, 10, 11, 13):
             with pytest.raises(alsv.AlsvError, match="does not support"):
                 alsv.alsv_set_tile_variant(S.ctx, v)
         S.close()

@@ -1,5 +1,5 @@
-// Stage kernels for float, 2D: the lean two-sample schedules (variants 8-13; 9, 11, 12 and 13 keep
-// every global read of a phase in flight at once; 12 and 13 on 32 x 8 tiles).
+// Stage kernels for float, 2D: the lean two-sample schedules (variants 8-11; 9 and 11 keep every
+// global read of a phase in flight at once).
 #include "fv_pair2.cuh"
 #include "stage_dispatch.cuh"
 namespace alsv {
@@ -39,8 +39,6 @@ cudaError_t launch_stage_f32_2d_lean(int variant, int eq, int recon, int flux, c
         case 9: return launch_pair2<16, 0, 1>(recon, flux, eq, a, s);
         case 10: return launch_pair2<16, 1>(recon, flux, eq, a, s);
         case 11: return launch_pair2<16, 1, 1>(recon, flux, eq, a, s);
-        case 12: return launch_pair2<8, 0, 1>(recon, flux, eq, a, s);
-        case 13: return launch_pair2<8, 1, 1>(recon, flux, eq, a, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -29,7 +29,7 @@ _lib = None
 EQ = {"burgers": 0, "euler": 1}
 RECON = {"pc": 0, "mc": 1, "weno3": 2, "eno2": 3}
 RVARS = {"cons": 0, "prim": 1}
-FLUX = {"rusanov": 0, "hll": 1, "hllc": 2, "roe": 3, "godunov": 4, "ec": 5, "ec4": 6}
+FLUX = {"rusanov": 0, "hll": 1, "hllc": 2, "roe": 3, "godunov": 4, "ec": 5, "ec4": 6, "tecno2": 7}
 RK = {"ssprk2": 2, "ssprk3": 3}
 BC = {"periodic": 0, "outflow": 1, "reflective": 2}
 INIT = {"kh": 0, "sod": 1, "lax": 2, "burgers_sine": 3, "vortex": 4}
@@ -105,6 +105,9 @@ def lib():
             L.orc_num_threads.restype = C.c_int
             L.orc_nvars.argtypes = [dsc]
             L.orc_flux.argtypes = [dsc, C.c_int, dp, dp, dp]
+            L.orc_entropy_vars.argtypes = [dsc, dp, dp]
+            L.orc_tecno_matrix.argtypes = [dsc, C.c_int, dp, dp, dp, dp]
+            L.orc_tecno_flux.argtypes = [dsc, C.c_int, dp, dp]
             L.orc_recon.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, dp, dp]
             L.orc_cons_to_prim.argtypes = [dsc, dp, dp]
             L.orc_prim_to_cons.argtypes = [dsc, dp, dp]
@@ -159,6 +162,33 @@ def flux(d: Desc, k: int, WL, WR) -> np.ndarray:
     WL, WR = _f64(WL), _f64(WR)
     F = np.zeros(nvars(d))
     lib().orc_flux(C.byref(d), k, _dp(WL), _dp(WR), _dp(F))
+    return F
+
+
+def entropy_vars(d: Desc, W) -> np.ndarray:
+    """Entropy variables of a primitive state (Euler: entropy -rho s/(gamma - 1); Burgers: u^2/2)."""
+    W = _f64(W)
+    v = np.zeros(nvars(d))
+    lib().orc_entropy_vars(C.byref(d), _dp(W), _dp(v))
+    return v
+
+
+def tecno_matrix(d: Desc, k: int, WL, WR):
+    """Scaled eigenvectors Rs (Rs Rs^T = dU/dv) and absolute eigenvalues along k at the mean of
+    two primitive states (TECNO2's diffusion operator)."""
+    WL, WR = _f64(WL), _f64(WR)
+    nv = nvars(d)
+    Rs = np.zeros(nv * nv)
+    lam = np.zeros(nv)
+    lib().orc_tecno_matrix(C.byref(d), k, _dp(WL), _dp(WR), _dp(Rs), _dp(lam))
+    return Rs.reshape(nv, nv), lam
+
+
+def tecno_flux(d: Desc, k: int, W4) -> np.ndarray:
+    """TECNO2 flux at the interface between the middle two of four consecutive primitive states."""
+    W4 = _f64(W4).reshape(4, nvars(d))
+    F = np.zeros(nvars(d))
+    lib().orc_tecno_flux(C.byref(d), k, _dp(np.ascontiguousarray(W4)), _dp(F))
     return F
 
 

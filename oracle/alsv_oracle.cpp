@@ -43,7 +43,7 @@ namespace orc {
 enum { EQ_BURGERS = 0, EQ_EULER = 1 };
 enum { REC_PC = 0, REC_MC = 1, REC_WENO3 = 2, REC_ENO2 = 3 };
 enum { RV_CONS = 0, RV_PRIM = 1 };
-enum { FLUX_RUSANOV = 0, FLUX_HLL = 1, FLUX_HLLC = 2, FLUX_ROE = 3, FLUX_GODUNOV = 4, FLUX_EC = 5, FLUX_EC4 = 6 };
+enum { FLUX_RUSANOV = 0, FLUX_HLL = 1, FLUX_HLLC = 2, FLUX_ROE = 3, FLUX_GODUNOV = 4, FLUX_EC = 5, FLUX_EC4 = 6, FLUX_TECNO2 = 7 };
 enum { RK_SSP2 = 2, RK_SSP3 = 3 };
 enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_REFLECTIVE = 2 };
 enum { INIT_KH = 0, INIT_SOD = 1, INIT_LAX = 2, INIT_BURGERS_SINE = 3, INIT_VORTEX = 4 };
@@ -535,9 +535,116 @@ template <class T> void ec_flux(const Desc& d, int k, const T* WL, const T* WR, 
     F[ip] = mf * H;
 }
 
+// Entropy variables v = dU/du of the entropy used by the entropy-conservative fluxes. Euler: U =
+// -rho s/(gamma - 1), s = ln p - gamma ln rho, so v = ((gamma - s)/(gamma - 1) - rho |u|^2/(2p),
+// rho u/p, -rho/p); Burgers: U = u^2/2, v = u. W is the primitive state.
+template <class T> void entropy_vars(const Desc& d, const T* W, T* v) {
+    if (d.eq == EQ_BURGERS) {
+        v[0] = W[0];
+        return;
+    }
+    const int nd = d.ndim, ip = nd + 1;
+    const double g = d.gamma;
+    T s = log_(W[ip]) - g * log_(W[0]);
+    T beta = W[0] / W[ip];
+    T q2 = T(0.0);
+    for (int j = 0; j < nd; ++j) q2 = q2 + W[1 + j] * W[1 + j];
+    v[0] = (g - s) / (g - 1.0) - 0.5 * beta * q2;
+    for (int j = 0; j < nd; ++j) v[1 + j] = beta * W[1 + j];
+    v[ip] = -beta;
+}
+
+// Eigenvectors of the Euler flux Jacobian along k, scaled so that Rs Rs^T = dU/dv (Barth's
+// scaling), and the absolute eigenvalues, at the state with the arithmetic means of WL and WR's
+// density, velocity and pressure. Columns: the u_k - c acoustic wave, the entropy wave, one shear
+// wave per tangential direction (in increasing order), the u_k + c acoustic wave. Rs[row][col].
+template <class T> void tecno_matrix(const Desc& d, int k, const T* WL, const T* WR, T Rs[8][8], T* lam) {
+    const int nd = d.ndim, ip = nd + 1, nv = nd + 2;
+    const double g = d.gamma;
+    T r = 0.5 * (WL[0] + WR[0]), p = 0.5 * (WL[ip] + WR[ip]);
+    T u[3];
+    T q2 = T(0.0);
+    for (int j = 0; j < nd; ++j) {
+        u[j] = 0.5 * (WL[1 + j] + WR[1 + j]);
+        q2 = q2 + u[j] * u[j];
+    }
+    T c = sqrt_(g * p / r);
+    T H = c * c / (g - 1.0) + 0.5 * q2;
+    T un = u[k];
+    T sac = sqrt_(r / (2.0 * g)), sen = sqrt_((g - 1.0) * r / g), ssh = sqrt_(p);
+    for (int a = 0; a < nv; ++a)
+        for (int b = 0; b < nv; ++b) Rs[a][b] = T(0.0);
+    // acoustic waves u_k -/+ c: (1, u -/+ c e_k, H -/+ u_k c)
+    for (int side = 0; side < 2; ++side) {
+        const int col = side == 0 ? 0 : nv - 1;
+        const double sg = side == 0 ? -1.0 : 1.0;
+        Rs[0][col] = sac;
+        for (int j = 0; j < nd; ++j) Rs[1 + j][col] = sac * u[j];
+        Rs[1 + k][col] = sac * (un + sg * c);
+        Rs[ip][col] = sac * (H + sg * un * c);
+        lam[col] = abs_(T(un + sg * c));
+    }
+    // entropy wave: (1, u, |u|^2/2)
+    Rs[0][1] = sen;
+    for (int j = 0; j < nd; ++j) Rs[1 + j][1] = sen * u[j];
+    Rs[ip][1] = sen * 0.5 * q2;
+    lam[1] = abs_(un);
+    // shear waves: (0, e_t, u_t)
+    int col = 2;
+    for (int t = 0; t < nd; ++t) {
+        if (t == k) continue;
+        Rs[1 + t][col] = ssh;
+        Rs[ip][col] = ssh * u[t];
+        lam[col] = abs_(un);
+        ++col;
+    }
+}
+
+// TECNO2 (Fjordholm-Mishra-Tadmor's entropy-stable ENO scheme, second order): the two-point
+// entropy-conservative flux of the interface's cells plus an entropy-stable diffusion,
+//   F = F_ec(W_i, W_{i+1}) - 1/2 Rs Lambda <<w>>,
+// with w_j = Rs^T v_j the scaled entropy variables of the cells i-1 .. i+2 (Rs, Lambda at the
+// interface, v_j the entropy variables) and <<w>> = w_{i+1}^- - w_i^+ the jump of their
+// second-order ENO reconstructions at the interface (per component, the one-sided difference of
+// smaller magnitude, ties taking the backward one). ENO's sign property makes <<w>> carry the sign
+// of w_{i+1} - w_i per component, so each interface produces entropy -1/2 [[w]]^T Lambda <<w>> <= 0.
+// Burgers: v = u, Rs = 1, Lambda = max(|u_i|, |u_{i+1}|) (a Roe speed would vanish on a
+// transonic rarefaction and keep an expansion shock).
+template <class T> void tecno_flux(const Desc& d, int k, T W[4][8], T* F) {
+    const int nv = nvars(d);
+    ec_flux(d, k, W[1], W[2], F);
+    T Rs[8][8], lam[8], v[4][8], w[4][8];
+    if (d.eq == EQ_BURGERS) {
+        Rs[0][0] = T(1.0);
+        lam[0] = max_(abs_(W[1][0]), abs_(W[2][0]));
+    } else {
+        tecno_matrix(d, k, W[1], W[2], Rs, lam);
+    }
+    for (int j = 0; j < 4; ++j) {
+        entropy_vars(d, W[j], v[j]);
+        for (int m = 0; m < nv; ++m) {
+            T acc = T(0.0);
+            for (int r = 0; r < nv; ++r) acc = acc + Rs[r][m] * v[j][r];
+            w[j][m] = acc;
+        }
+    }
+    T jump[8];
+    for (int m = 0; m < nv; ++m) {
+        T dm = w[1][m] - w[0][m], d1 = w[2][m] - w[1][m], d2 = w[3][m] - w[2][m];
+        T si = val(abs_(d1)) < val(abs_(dm)) ? d1 : dm;   // cell i, right face
+        T sj = val(abs_(d2)) < val(abs_(d1)) ? d2 : d1;   // cell i + 1, left face
+        jump[m] = (w[2][m] - 0.5 * sj) - (w[1][m] + 0.5 * si);
+    }
+    for (int r = 0; r < nv; ++r) {
+        T acc = T(0.0);
+        for (int m = 0; m < nv; ++m) acc = acc + Rs[r][m] * (lam[m] * jump[m]);
+        F[r] = F[r] - 0.5 * acc;
+    }
+}
+
 template <class T> void flux(const Desc& d, int k, const T* WL, const T* WR, T* F) {
     const int nv = nvars(d);
-    if (d.flux == FLUX_EC || d.flux == FLUX_EC4) { ec_flux(d, k, WL, WR, F); return; }
+    if (d.flux == FLUX_EC || d.flux == FLUX_EC4 || d.flux == FLUX_TECNO2) { ec_flux(d, k, WL, WR, F); return; }
     if (d.eq == EQ_BURGERS) {
         T uL = WL[0], uR = WR[0];
         T fL = 0.5 * uL * uL, fR = 0.5 * uR * uR;
@@ -617,8 +724,8 @@ template <class T> void flux(const Desc& d, int k, const T* WL, const T* WR, T* 
 
 // Flux through the interface i+1/2 (between cell i and i+1) along k at cell position c.
 template <class T> void interface_flux(const Desc& d, const T* U, const int c[3], int k, int i, T* F) {
-    if (d.flux == FLUX_EC || d.flux == FLUX_EC4) {
-        // entropy-conservative fluxes take the cell values (primitive), no reconstruction
+    if (d.flux == FLUX_EC || d.flux == FLUX_EC4 || d.flux == FLUX_TECNO2) {
+        // entropy-conservative fluxes (and TECNO2) take the cell values (primitive), no reconstruction
         const int nv = nvars(d);
         T W[4][8];
         for (int s = 0; s < 4; ++s) {
@@ -629,6 +736,7 @@ template <class T> void interface_flux(const Desc& d, const T* U, const int c[3]
             else cons_to_prim(d, Uc, W[s]);
         }
         if (d.flux == FLUX_EC) { ec_flux(d, k, W[1], W[2], F); return; }
+        if (d.flux == FLUX_TECNO2) { tecno_flux(d, k, W, F); return; }
         // fourth order (LeFloch-Mercier-Rohde): 4/3 F(w_i, w_{i+1}) - 1/6 (F(w_{i-1}, w_{i+1}) + F(w_i, w_{i+2}))
         T Fa[8], Fb[8], Fc[8];
         ec_flux(d, k, W[1], W[2], Fa);
@@ -864,6 +972,25 @@ int orc_nvars(const Desc* d) { return nvars(*d); }
 
 // One numerical flux on primitive states (for unit pins).
 void orc_flux(const Desc* d, int k, const double* WL, const double* WR, double* F) { flux(*d, k, WL, WR, F); }
+
+// TECNO2 pieces (tests): entropy variables of a primitive state; the scaled eigenvectors (row-major
+// nv x nv) and absolute eigenvalues at the mean of two states; the flux of four consecutive cells'
+// primitive states W4[4][nv].
+void orc_entropy_vars(const Desc* d, const double* W, double* v) { entropy_vars(*d, W, v); }
+void orc_tecno_matrix(const Desc* d, int k, const double* WL, const double* WR, double* Rs, double* lam) {
+    double R8[8][8];
+    tecno_matrix(*d, k, WL, WR, R8, lam);
+    const int nv = nvars(*d);
+    for (int a = 0; a < nv; ++a)
+        for (int b = 0; b < nv; ++b) Rs[a * nv + b] = R8[a][b];
+}
+void orc_tecno_flux(const Desc* d, int k, const double* W4, double* F) {
+    const int nv = nvars(*d);
+    double W[4][8];
+    for (int j = 0; j < 4; ++j)
+        for (int v = 0; v < nv; ++v) W[j][v] = W4[j * nv + v];
+    tecno_flux(*d, k, W, F);
+}
 
 // Reconstruction of a single cell's faces from three scalars.
 void orc_recon(int recon, double eps, double wm, double w0, double wp, double* fl, double* fr) {

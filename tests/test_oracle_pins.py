@@ -1348,3 +1348,144 @@ def test_entropy_conservative_burgers_and_2d_balance():
         p = 0.4 * (E - 0.5 * (mx * mx + my * my) / rho)
         V = np.array([_entropy_vars([rho[i], mx[i] / rho[i], my[i] / rho[i], p[i]])[0] for i in range(rho.size)]).T
         assert abs((V * L).sum()) <= 1e-12 * (np.abs(V) * np.abs(L)).sum()
+
+
+# ---------------------------------------------------------------- TECNO2: entropy-stable diffusion added to
+# the two-point entropy-conservative flux (Fjordholm-Mishra-Tadmor), Sec. 2.1's entropy-conservative
+# fluxes made entropy stable
+def _cons_from_prim(W, g=1.4):
+    W = np.asarray(W, float)
+    r, u, p = W[0], W[1:-1], W[-1]
+    return np.concatenate([[r], r * u, [p / (g - 1) + 0.5 * r * np.dot(u, u)]])
+
+
+def _prim_from_cons(U, g=1.4):
+    U = np.asarray(U, float)
+    r, m, E = U[0], U[1:-1], U[-1]
+    return np.concatenate([[r], m / r, [(g - 1) * (E - 0.5 * np.dot(m, m) / r)]])
+
+
+def _phys_flux_cons(U, k, g=1.4):
+    W = _prim_from_cons(U, g)
+    r, u, p = W[0], W[1:-1], W[-1]
+    return np.concatenate([[r * u[k]], r * u[k] * u + p * (np.arange(u.size) == k), [u[k] * (U[-1] + p)]])
+
+
+def _num_jacobian(f, x, h=1e-6):
+    J = np.zeros((f(x).size, x.size))
+    for c in range(x.size):
+        e = np.zeros(x.size)
+        e[c] = h * max(1.0, abs(x[c]))
+        J[:, c] = (f(x + e) - f(x - e)) / (2 * e[c])
+    return J
+
+
+@pytest.mark.parametrize("nd", [1, 2, 3])
+def test_tecno_entropy_variables_and_scaled_eigenvectors(nd):
+    """The oracle's entropy variables equal the independent formula; at a state W the scaled
+    eigenvectors satisfy Rs Rs^T = dU/dv (the inverse of the numerical Jacobian dv/dU, Barth's
+    scaling) and are eigenvectors of the numerical flux Jacobian dF_k/dU with eigenvalues of
+    magnitude lam (u_k - c, u_k, ..., u_k + c). A wrong scale factor fails the first check, a wrong
+    column or eigenvalue the second."""
+    d = oracle.make_desc(ndim=nd, n=(4, 4, 4), eq="euler", flux="tecno2")
+    nv = nd + 2
+    for W in random_prim(nd, rng, 6):
+        np.testing.assert_allclose(oracle.entropy_vars(d, W), _entropy_vars(W)[0], rtol=1e-13, atol=1e-13)
+        U0 = _cons_from_prim(W)
+        dUdv = np.linalg.inv(_num_jacobian(lambda U: _entropy_vars(_prim_from_cons(U))[0], U0))
+        for k in range(nd):
+            Rs, lam = oracle.tecno_matrix(d, k, W, W)
+            np.testing.assert_allclose(Rs @ Rs.T, dUdv, rtol=1e-6, atol=1e-6 * np.abs(dUdv).max())
+            A = _num_jacobian(lambda U: _phys_flux_cons(U, k), U0)
+            AR = A @ Rs
+            c = math.sqrt(1.4 * W[-1] / W[0])
+            expect = sorted([abs(W[1 + k] - c), abs(W[1 + k] + c)] + [abs(W[1 + k])] * (nv - 2))
+            assert np.allclose(sorted(lam), expect, rtol=1e-13)
+            for m in range(nv):
+                res = min(np.linalg.norm(AR[:, m] - lam[m] * Rs[:, m]), np.linalg.norm(AR[:, m] + lam[m] * Rs[:, m]))
+                assert res <= 1e-6 * (np.linalg.norm(AR[:, m]) + np.linalg.norm(Rs[:, m])), (k, m, res)
+
+
+def test_tecno_burgers_flux_hand_values():
+    """Burgers (v = u, Rs = 1, Lambda = max(|u_i|, |u_i+1|)): F = (u_i^2 + u_i u_i+1 + u_i+1^2)/6 -
+    1/2 Lambda <<u>>, <<u>> the jump of the ENO2 faces. Hand-evaluated stencils: (0, 0, 1, 3)
+    (differences 0, 1, 2: slopes 0 and 1, jump 1/2); (0, 0, 1, 0.5) (slopes 0 and -0.5, jump 5/4);
+    (2, 1, 1, 1) (slopes 0 and 0, jump 0: no diffusion). Taking the larger difference, dropping the
+    1/2 or flipping the sign each changes a value."""
+    d = oracle.make_desc(ndim=1, n=(8,), eq="burgers", flux="tecno2")
+    cases = [((0.0, 0.0, 1.0, 3.0), 1 / 6 - 0.5 * 1.0 * 0.5), ((0.0, 0.0, 1.0, 0.5), 1 / 6 - 0.5 * 1.0 * 1.25),
+             ((2.0, 1.0, 1.0, 1.0), 0.5), ((-3.0, -1.0, 0.0, 0.0), 1 / 6 - 0.5 * 1.0 * 0.5)]
+    for u, ref in cases:
+        F = oracle.tecno_flux(d, 0, np.array(u).reshape(4, 1))[0]
+        assert F == pytest.approx(ref, rel=1e-14, abs=1e-15), (u, F, ref)
+
+
+@pytest.mark.parametrize("nd", [1, 2, 3])
+def test_tecno_consistency_and_mirror_symmetry(nd):
+    d = oracle.make_desc(ndim=nd, n=(4, 4, 4), eq="euler", flux="tecno2")
+    for _ in range(10):
+        W4 = random_prim(nd, rng, 4)
+        for k in range(nd):
+            W = W4[0]
+            ref = _phys_flux_cons(_cons_from_prim(W), k)
+            np.testing.assert_allclose(oracle.tecno_flux(d, k, np.stack([W] * 4)), ref, rtol=1e-13, atol=1e-13)
+            M = np.ones(nd + 2)
+            M[1 + k] = -1
+            F = oracle.tecno_flux(d, k, np.stack(W4))
+            Fm = oracle.tecno_flux(d, k, np.stack([M * W4[3], M * W4[2], M * W4[1], M * W4[0]]))
+            np.testing.assert_allclose(F, -M * Fm, rtol=1e-12, atol=1e-12)
+
+
+def test_tecno_is_entropy_stable():
+    """The semi-discrete entropy rate sum_i v_i . L_i, zero for the entropy-conservative flux, is
+    negative with TECNO2's diffusion on rough periodic data (random 1D and 2D Euler states, random
+    Burgers data), and zero on a constant state."""
+    from inputs import euler_state
+    for trial in range(3):
+        n = 24
+        U = euler_state(1, 1, (n,), seed=60 + trial)
+        for fl, sign in (("ec", 0), ("tecno2", -1)):
+            d = oracle.make_desc(ndim=1, n=(n,), eq="euler", flux=fl, bc="periodic")
+            L = oracle.rhs(d, U)[0].reshape(3, -1)
+            Uc = U[0].reshape(3, -1)
+            V = np.array([_entropy_vars(_prim_from_cons(Uc[:, i]))[0] for i in range(n)]).T
+            rate, scale = (V * L).sum(), (np.abs(V) * np.abs(L)).sum()
+            if sign == 0:
+                assert abs(rate) <= 1e-12 * scale
+            else:
+                assert rate < -1e-4 * scale, (rate, scale)
+    U = euler_state(1, 2, (12, 10), seed=5)
+    d = oracle.make_desc(ndim=2, n=(12, 10), eq="euler", flux="tecno2", bc="periodic")
+    L = oracle.rhs(d, U)[0].reshape(4, -1)
+    Uc = U[0].reshape(4, -1)
+    V = np.array([_entropy_vars(_prim_from_cons(Uc[:, i]))[0] for i in range(Uc.shape[1])]).T
+    assert (V * L).sum() < -1e-4 * (np.abs(V) * np.abs(L)).sum()
+    n = 40
+    r = np.random.default_rng(7)
+    for _ in range(3):
+        u = r.uniform(-1, 1, n).reshape(1, 1, 1, 1, n)
+        d = oracle.make_desc(ndim=1, n=(n,), eq="burgers", flux="tecno2", bc="periodic")
+        L = oracle.rhs(d, u)
+        assert (u * L).sum() < -1e-4 * (np.abs(u) * np.abs(L)).sum()
+    Uk = np.broadcast_to(_cons_from_prim([1.0, 0.3, 0.9]).reshape(1, 3, 1, 1, 1), (1, 3, 1, 1, 16)).copy()
+    d = oracle.make_desc(ndim=1, n=(16,), eq="euler", flux="tecno2", bc="periodic")
+    assert np.abs(oracle.rhs(d, Uk)).max() <= 1e-14
+
+
+def test_tecno_converges_on_sod_and_smooth_burgers():
+    """Sod to T = 0.2 against the exact solution (monotone decrease, rate >= 0.6), and the smooth
+    Burgers sine before its shock at second order (rate >= 1.8)."""
+    R = RiemannExact((1.0, 0.0, 1.0), (0.125, 0.0, 0.1))
+    ns, errs = [128, 256, 512, 1024], []
+    for n in ns:
+        d = oracle.make_desc(ndim=1, n=(n,), eq="euler", flux="tecno2", rk="ssprk3", bc="outflow", cfl=0.4)
+        U, _, _ = oracle.evolve(d, oracle.init(d, "sod"), T=0.2)
+        errs.append(np.abs(U[0, 0, 0, 0] - R.cell_average_density(n, 0.2)).mean())
+    assert np.all(np.diff(errs) < 0), errs
+    assert math.log(errs[0] / errs[-1]) / math.log(ns[-1] / ns[0]) >= 0.6, errs
+    ns, errs = [32, 64, 128, 256], []
+    for n in ns:
+        d = oracle.make_desc(ndim=1, n=(n,), eq="burgers", flux="tecno2", rk="ssprk3", bc="periodic", cfl=0.4)
+        U, _, _ = oracle.evolve(d, oracle.init(d, "burgers_sine"), T=0.1)
+        errs.append(np.abs(U[0, 0, 0, 0] - burgers_sine_cell_averages(n, 0.1)).mean())
+    assert observed_rates(ns, errs)[-1] >= 1.8, errs

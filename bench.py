@@ -297,6 +297,14 @@ WORKLOADS = {
     "kh2d256_resident_fp32": dict(desc=dict(ndim=2, n=(256, 256), batch=512, eq="euler", recon="weno3", flux="hllc",
                                             rvars="prim", rk="ssprk3", bc="periodic", cfl=0.4, precision="fp32",
                                             seed=SEED), init="kh", T=0.2, words=8, nv=4, esize=4, resident=True),
+    # the further numerics of Sec. 2.1 (Roe, Godunov, ENO2, the entropy-conservative fluxes and
+    # TECNO2) on the KH data, each on the default tile schedule (the only one they run on), beside
+    # HLLC + WENO3 on the same schedule: 20 RK3 steps of 256 (FP32) / 32 (FP64) samples of 256^2
+    "schemes_kh2d256": dict(desc=dict(ndim=2, n=(256, 256), eq="euler", rvars="prim", rk="ssprk3", bc="periodic",
+                                      cfl=0.4, seed=SEED), init="kh", steps=20, schemes=True,
+                            batch={"fp32": 256, "fp64": 32},
+                            list=[("hllc", "weno3"), ("roe", "weno3"), ("godunov", "weno3"), ("hllc", "eno2"),
+                                  ("ec", "pc"), ("ec4", "pc"), ("tecno2", "pc")]),
     "kh2d1024_fp64": dict(desc=dict(ndim=2, n=(1024, 1024), batch=1, eq="euler", recon="weno3", flux="hllc",
                                     rvars="prim", rk="ssprk3", bc="periodic", cfl=0.4, precision="fp64", seed=0),
                           init="kh", T=0.02, words=8, nv=4, esize=8),
@@ -507,6 +515,50 @@ def run_blocks_workload(name, W, args):
     return 0
 
 
+def run_schemes_workload(name, W, args):
+    """Cell-updates/s of each listed scheme in FP32 and FP64 on the default tile schedule."""
+    import numpy as np
+    import torch
+    import paper_1912_07645_gb300 as alsv
+    rows, launches = [], 0
+    for precision in ("fp32", "fp64"):
+        for flux, recon in W["list"]:
+            cfg = dict(W["desc"], flux=flux, recon=recon, precision=precision, batch=W["batch"][precision])
+            S = alsv.Solver(alsv.make_desc(**cfg))
+            alsv.alsv_set_tile_variant(S.ctx, 0)
+            cells = cfg["batch"] * int(np.prod(cfg["n"]))
+
+            def one():
+                S.set_initial_data(W["init"])
+                S.step(W["steps"])
+                S.sync()
+
+            for _ in range(args.warmup):
+                one()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                one()
+            torch.cuda.synchronize()
+            el = time.perf_counter() - t0
+            _, ns = S.time()   # sync() above raised if a sample went non-physical
+            launches += alsv.alsv_get_launch_count(S.ctx)
+            rows.append({"flux": flux, "recon": recon, "precision": precision, "samples": cfg["batch"],
+                         "cell_updates_per_s": cells * W["steps"] * args.steps / el,
+                         "ms_per_rk_step": 1000 * el / (args.steps * W["steps"]), "steps_done": int(ns.max())})
+            S.close()
+    tec = [r for r in rows if r["flux"] == "tecno2" and r["precision"] == "fp32"][0]
+    line = {"metric": "cell-updates/s per scheme (default tile schedule)", "value": tec["cell_updates_per_s"],
+            "value_is": "TECNO2, FP32", "unit": "cell-updates/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "fp32 and fp64", "data": "synthetic (seeded KH perturbation parameters, SplitMix64)",
+            "config": {"workload": name, "grid": list(W["desc"]["n"]), "rk_steps": W["steps"],
+                       "samples": W["batch"], "tile_variant": 0},
+            "schemes": rows, "gpu_launches": launches}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_workload(name, args):
     import numpy as np
     import torch
@@ -516,6 +568,8 @@ def run_workload(name, args):
     W = WORKLOADS[name]
     if W.get("blocks"):
         return run_blocks_workload(name, W, args)
+    if W.get("schemes"):
+        return run_schemes_workload(name, W, args)
     desc = alsv.make_desc(**W["desc"])
     S = alsv.Solver(desc)
     peaks, peak_kind = measured_peaks()

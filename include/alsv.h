@@ -57,12 +57,15 @@ enum { ALSV_VARS_CONS = 0, ALSV_VARS_PRIM = 1 };
  * fluxes): RUSANOV, HLL, HLLC (Davis wave speeds); ROE with Harten's entropy fix on the acoustic
  * fields (Harten-Hyman width); GODUNOV the flux of the exact Riemann solution at x/t = 0; EC the
  * two-point entropy-conservative flux (Ismail-Roe for Euler, (uL^2 + uL uR + uR^2)/6 for Burgers)
- * and EC4 its fourth-order combination over four cells (LeFloch-Mercier-Rohde). EC and EC4 take
- * cell values: recon and recon_vars are ignored for them. ENO2, ROE, GODUNOV, EC and EC4 run on
- * the default stage schedule (tile variant 0); with ENO2, ROE or GODUNOV Euler needs recon_vars
- * PRIM, and Burgers is served in 1D only (INVALID_ARG at alsv_init_grid otherwise). */
+ * and EC4 its fourth-order combination over four cells (LeFloch-Mercier-Rohde); TECNO2 the EC
+ * flux made entropy stable (Fjordholm-Mishra-Tadmor): minus half the scaled eigenvector matrix
+ * times |eigenvalues| times the jump of the ENO2 faces of the scaled entropy variables, over four
+ * cells (Burgers: diffusion coefficient max(|uL|, |uR|)). EC, EC4 and TECNO2 take cell values:
+ * recon and recon_vars are ignored for them. ENO2, ROE, GODUNOV, EC, EC4 and TECNO2 run on the
+ * default stage schedule (tile variant 0); with ENO2, ROE or GODUNOV Euler needs recon_vars PRIM,
+ * and Burgers is served in 1D only (INVALID_ARG at alsv_init_grid otherwise). */
 enum { ALSV_FLUX_RUSANOV = 0, ALSV_FLUX_HLL = 1, ALSV_FLUX_HLLC = 2, ALSV_FLUX_ROE = 3, ALSV_FLUX_GODUNOV = 4,
-       ALSV_FLUX_EC = 5, ALSV_FLUX_EC4 = 6 };
+       ALSV_FLUX_EC = 5, ALSV_FLUX_EC4 = 6, ALSV_FLUX_TECNO2 = 7 };
 enum { ALSV_RK_SSP2 = 2, ALSV_RK_SSP3 = 3 };
 /* ALSV_BC_HALO: a face of a block of a decomposed grid whose ghost layers are filled by the caller
  * (alsv_bind_halo; see "Domain decomposition" below). */

@@ -18,7 +18,7 @@ STATUS_NAMES = {0: "OK", 1: "ERR_INVALID_ARG", 2: "ERR_CUDA", 3: "ERR_NONPHYSICA
 EQ = {"burgers": 0, "euler": 1}
 RECON = {"pc": 0, "mc": 1, "weno3": 2, "eno2": 3}
 RVARS = {"cons": 0, "prim": 1}
-FLUX = {"rusanov": 0, "hll": 1, "hllc": 2, "roe": 3, "godunov": 4, "ec": 5, "ec4": 6}
+FLUX = {"rusanov": 0, "hll": 1, "hllc": 2, "roe": 3, "godunov": 4, "ec": 5, "ec4": 6, "tecno2": 7}
 RK = {"ssprk2": 2, "ssprk3": 3}
 BC = {"periodic": 0, "outflow": 1, "reflective": 2, "halo": 3}
 PRECISION = {"fp32": 0, "fp64": 1}

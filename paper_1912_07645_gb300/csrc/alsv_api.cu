@@ -395,11 +395,12 @@ alsv_status alsv_init_grid(const alsv_grid_desc* d_in, void* stream, alsv_ctx** 
     if (d.eq != ALSV_EQ_BURGERS && d.eq != ALSV_EQ_EULER) return bad("eq must be BURGERS or EULER");
     if (d.recon < 0 || d.recon > 3) return bad("recon must be PC, MC, WENO3 or ENO2");
     if (d.recon_vars != ALSV_VARS_CONS && d.recon_vars != ALSV_VARS_PRIM) return bad("recon_vars must be CONS or PRIM");
-    if (d.flux < 0 || d.flux > 6) return bad("flux must be RUSANOV, HLL, HLLC, ROE, GODUNOV, EC or EC4");
+    if (d.flux < 0 || d.flux > 7) return bad("flux must be RUSANOV, HLL, HLLC, ROE, GODUNOV, EC, EC4 or TECNO2");
     if (ext_scheme(d.recon, d.flux)) {
         if (d.eq == ALSV_EQ_BURGERS && d.ndim != 1)
-            return bad("ENO2 reconstruction and the ROE, GODUNOV, EC, EC4 fluxes serve Burgers in 1D only");
-        if (d.eq == ALSV_EQ_EULER && d.recon_vars != ALSV_VARS_PRIM && d.flux != ALSV_FLUX_EC && d.flux != ALSV_FLUX_EC4)
+            return bad("ENO2 reconstruction and the ROE, GODUNOV, EC, EC4, TECNO2 fluxes serve Burgers in 1D only");
+        if (d.eq == ALSV_EQ_EULER && d.recon_vars != ALSV_VARS_PRIM && d.flux != ALSV_FLUX_EC && d.flux != ALSV_FLUX_EC4 &&
+            d.flux != ALSV_FLUX_TECNO2)
             return bad("ENO2 reconstruction and the ROE, GODUNOV fluxes reconstruct primitive variables (recon_vars PRIM)");
     }
     if (d.rk != ALSV_RK_SSP2 && d.rk != ALSV_RK_SSP3) return bad("rk must be SSP2 or SSP3");
@@ -511,7 +512,8 @@ alsv_status alsv_init_grid(const alsv_grid_desc* d_in, void* stream, alsv_ctx** 
     g.nv = c->nv;
     g.gamma = d.gamma;
     // the entropy-conservative fluxes read primitive cell values whatever recon_vars says
-    g.rvars = d.eq == ALSV_EQ_EULER ? ((d.flux == ALSV_FLUX_EC || d.flux == ALSV_FLUX_EC4) ? ALSV_VARS_PRIM : d.recon_vars)
+    g.rvars = d.eq == ALSV_EQ_EULER ? ((d.flux == ALSV_FLUX_EC || d.flux == ALSV_FLUX_EC4 || d.flux == ALSV_FLUX_TECNO2)
+                                           ? ALSV_VARS_PRIM : d.recon_vars)
                                     : ALSV_VARS_CONS;
     for (int k = 0; k < 3; ++k) {
         g.bc[k][0] = d.bc[k][0];

@@ -10,15 +10,15 @@ namespace alsv {
 enum { EQ_BURGERS = 0, EQ_EULER = 1 };
 enum { REC_PC = 0, REC_MC = 1, REC_WENO3 = 2, REC_ENO2 = 3 };
 enum { RV_CONS = 0, RV_PRIM = 1 };
-enum { FLX_RUSANOV = 0, FLX_HLL = 1, FLX_HLLC = 2, FLX_ROE = 3, FLX_GODUNOV = 4, FLX_EC = 5, FLX_EC4 = 6 };
+enum { FLX_RUSANOV = 0, FLX_HLL = 1, FLX_HLLC = 2, FLX_ROE = 3, FLX_GODUNOV = 4, FLX_EC = 5, FLX_EC4 = 6, FLX_TECNO2 = 7 };
 
-// Schemes served by the default tile schedule only (ENO2 reconstruction; Roe, Godunov and the
-// entropy-conservative fluxes).
+// Schemes served by the default tile schedule only (ENO2 reconstruction; Roe, Godunov, the
+// entropy-conservative fluxes and TECNO2).
 inline bool ext_scheme(int recon, int flux) { return recon == REC_ENO2 || flux >= FLX_ROE; }
 // Ghost layers a scheme reads: the entropy-conservative fluxes take cell values (EC: the two cells
-// of an interface, EC4: four); the others one (PC) or two layers.
+// of an interface, EC4 and TECNO2: four); the others one (PC) or two layers.
 inline constexpr int ghost_width(int recon, int flux) {
-    return flux == FLX_EC4 ? 2 : (flux == FLX_EC ? 1 : (recon == REC_PC ? 1 : 2));
+    return (flux == FLX_EC4 || flux == FLX_TECNO2) ? 2 : (flux == FLX_EC ? 1 : (recon == REC_PC ? 1 : 2));
 }
 enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_REFLECTIVE = 2, BC_HALO = 3 };
 

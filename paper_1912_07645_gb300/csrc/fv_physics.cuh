@@ -494,6 +494,123 @@ __device__ __forceinline__ void ec_flux(const R* WL, const R* WR, R* F, R gamma)
     F[IP] = mf * H;
 }
 
+// Entropy variables of the entropy -rho s/(gamma-1), s = ln p - gamma ln rho, from a primitive
+// state: ((gamma - s)/(gamma - 1) - rho |u|^2/(2p), rho u/p, -rho/p).
+template <class R, int ND>
+__device__ __forceinline__ void entropy_vars(const R* W, R* v, R gamma) {
+    constexpr int IP = ND + 1;
+    const R s = log(W[IP]) - gamma * log(W[0]);
+    const R beta = W[0] / W[IP];
+    R q2 = R(0);
+#pragma unroll
+    for (int j = 0; j < ND; ++j) q2 = q2 + W[1 + j] * W[1 + j];
+    v[0] = (gamma - s) / (gamma - R(1)) - R(0.5) * beta * q2;
+#pragma unroll
+    for (int j = 0; j < ND; ++j) v[1 + j] = beta * W[1 + j];
+    v[IP] = -beta;
+}
+
+// Jump <<w>> = w_{i+1}^- - w_i^+ of the second-order ENO faces of one component at interface
+// i+1/2 from the values at cells i-1 .. i+2 (per face the one-sided difference of smaller
+// magnitude, ties to the backward one). It has the sign of w_{i+1} - w_i (ENO's sign property).
+template <class R>
+__device__ __forceinline__ R eno2_jump(R w0, R w1, R w2, R w3) {
+    const R dm = w1 - w0, d1 = w2 - w1, d2 = w3 - w2;
+    const R si = fabs_(d1) < fabs_(dm) ? d1 : dm;
+    const R sj = fabs_(d2) < fabs_(d1) ? d2 : d1;
+    return (w2 - R(0.5) * sj) - (w1 + R(0.5) * si);
+}
+
+// TECNO2 flux along D from the primitive states of cells i-1 .. i+2 (Fjordholm-Mishra-Tadmor's
+// entropy-stable ENO scheme, second order): F = F_ec(W_i, W_{i+1}) - 1/2 Rs Lambda <<w>>, where Rs
+// holds the eigenvectors of the flux Jacobian scaled so that Rs Rs^T = dU/dv (acoustic columns by
+// sqrt(rho/(2 gamma)), the entropy column by sqrt((gamma-1) rho/gamma), shear columns by sqrt(p)),
+// Rs and Lambda = |eigenvalues| at the arithmetic mean of the two cells' rho, u, p, w_j = Rs^T v_j
+// the scaled entropy variables and <<w>> their ENO2 jump. The sum over components runs in the
+// order of the column layout (u - c, entropy, shear in increasing direction, u + c).
+template <class R, int ND, int D>
+__device__ __forceinline__ void tecno2_flux(const R* W0, const R* W1, const R* W2, const R* W3, R* F, R gamma) {
+    constexpr int NV = ND + 2, IP = ND + 1;
+    ec_flux<R, ND, D>(W1, W2, F, gamma);
+    const R g = gamma;
+    const R r = R(0.5) * (W1[0] + W2[0]), p = R(0.5) * (W1[IP] + W2[IP]);
+    R u[ND];
+    R q2 = R(0);
+#pragma unroll
+    for (int j = 0; j < ND; ++j) {
+        u[j] = R(0.5) * (W1[1 + j] + W2[1 + j]);
+        q2 = q2 + u[j] * u[j];
+    }
+    const R c = sqrt(g * p / r);
+    const R H = c * c / (g - R(1)) + R(0.5) * q2;
+    const R un = u[D];
+    const R sac = sqrt(r / (R(2) * g)), sen = sqrt((g - R(1)) * r / g), ssh = sqrt(p);
+    R Rs[NV][NV], lam[NV];
+#pragma unroll
+    for (int a = 0; a < NV; ++a)
+#pragma unroll
+        for (int b = 0; b < NV; ++b) Rs[a][b] = R(0);
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+        const int col = side == 0 ? 0 : NV - 1;
+        const R sg = side == 0 ? R(-1) : R(1);
+        Rs[0][col] = sac;
+#pragma unroll
+        for (int j = 0; j < ND; ++j) Rs[1 + j][col] = sac * u[j];
+        Rs[1 + D][col] = sac * (un + sg * c);
+        Rs[IP][col] = sac * (H + sg * un * c);
+        lam[col] = fabs_(un + sg * c);
+    }
+    Rs[0][1] = sen;
+#pragma unroll
+    for (int j = 0; j < ND; ++j) Rs[1 + j][1] = sen * u[j];
+    Rs[IP][1] = sen * R(0.5) * q2;
+    lam[1] = fabs_(un);
+    {
+        int col = 2;
+#pragma unroll
+        for (int t = 0; t < ND; ++t) {
+            if (t == D) continue;
+            Rs[1 + t][col] = ssh;
+            Rs[IP][col] = ssh * u[t];
+            lam[col] = fabs_(un);
+            ++col;
+        }
+    }
+    const R* Wc[4] = {W0, W1, W2, W3};
+    R w[4][NV];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        R v[NV];
+        entropy_vars<R, ND>(Wc[j], v, g);
+#pragma unroll
+        for (int m = 0; m < NV; ++m) {
+            R acc = R(0);
+#pragma unroll
+            for (int q = 0; q < NV; ++q) acc = acc + Rs[q][m] * v[q];
+            w[j][m] = acc;
+        }
+    }
+    R dl[NV];
+#pragma unroll
+    for (int m = 0; m < NV; ++m) dl[m] = lam[m] * eno2_jump<R>(w[0][m], w[1][m], w[2][m], w[3][m]);
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        R acc = R(0);
+#pragma unroll
+        for (int m = 0; m < NV; ++m) acc = acc + Rs[q][m] * dl[m];
+        F[q] = F[q] - R(0.5) * acc;
+    }
+}
+
+// TECNO2 for Burgers (entropy u^2/2): v = u, Rs = 1, Lambda = max(|u_i|, |u_{i+1}|).
+template <class R>
+__device__ __forceinline__ R tecno2_burgers(R u0, R u1, R u2, R u3) {
+    const R Fec = (u1 * u1 + u1 * u2 + u2 * u2) / R(6);
+    const R lam = fmax_(fabs_(u1), fabs_(u2));
+    return Fec - R(0.5) * (R(1) * (lam * eno2_jump<R>(u0, u1, u2, u3)));
+}
+
 template <class R, int ND, int D, int FLUX>
 __device__ __forceinline__ void euler_flux(const R* WL, const R* WR, R* F, R gamma, R gm1, R inv_gm1) {
     if constexpr (FLUX == FLX_ROE) {

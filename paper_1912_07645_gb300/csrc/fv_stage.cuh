@@ -231,7 +231,7 @@ template <class R, int EQ, int ND, int RECON, int FLUX, int TX, int TY, int TZ, 
 __global__ void __launch_bounds__(NT) k_stage(const StageArgs p) {
     constexpr int NV = (EQ == EQ_BURGERS) ? 1 : ND + 2;
     constexpr int G = ghost_width(RECON, FLUX);
-    constexpr bool EC = FLUX == FLX_EC || FLUX == FLX_EC4;   // cell values, no reconstruction
+    constexpr bool EC = FLUX == FLX_EC || FLUX == FLX_EC4 || FLUX == FLX_TECNO2;   // cell values, no reconstruction
     static_assert(!EC || RV == RV_PRIM, "entropy-conservative fluxes read primitive cell values");
     constexpr int SX = TX + 2 * G, SY = ND >= 2 ? TY + 2 * G : 1, SZ = ND >= 3 ? TZ + 2 * G : 1;
     constexpr int NS = SX * SY * SZ;
@@ -354,6 +354,22 @@ __global__ void __launch_bounds__(NT) k_stage(const StageArgs p) {
                 R cl[NV], cr[NV];
                 lds_cell<R, NV, CS>(sW + i0 * CS, cl);
                 lds_cell<R, NV, CS>(sW + (i0 + step) * CS, cr);
+                if constexpr (FLUX == FLX_TECNO2) {
+                    // TECNO2: the two-point entropy-conservative flux plus the entropy-stable
+                    // diffusion of the ENO2 jump of the scaled entropy variables over four cells
+                    R cm[NV], c2[NV];
+                    lds_cell<R, NV, CS>(sW + (i0 - step) * CS, cm);
+                    lds_cell<R, NV, CS>(sW + (i0 + 2 * step) * CS, c2);
+                    if (EQ == EQ_BURGERS) {
+                        F[0] = tecno2_burgers<R>(cm[0], cl[0], cr[0], c2[0]);
+                    } else {
+                        if (D == 0) tecno2_flux<R, ND, 0>(cm, cl, cr, c2, F, gamma);
+                        if (D == 1) tecno2_flux<R, ND, (ND >= 2 ? 1 : 0)>(cm, cl, cr, c2, F, gamma);
+                        if (D == 2) tecno2_flux<R, ND, (ND >= 3 ? 2 : 0)>(cm, cl, cr, c2, F, gamma);
+                    }
+                    sts_cell<R, NV, CS>(sF + f * CS, F);
+                    continue;
+                }
                 if (EQ == EQ_BURGERS) F[0] = burgers_flux<R, FLUX>(cl[0], cr[0]);
                 else ec_flux_dir<R, ND>(D, cl, cr, F, gamma);
                 if constexpr (FLUX == FLX_EC4) {

@@ -39,6 +39,7 @@ static cudaError_t launch_ext_eq(int recon, int flux, const StageArgs& a, cudaSt
         case FLX_GODUNOV: return launch_ext_recon<R, EQ, ND, FLX_GODUNOV, TX, TY, TZ, NT>(recon, a, s);
         case FLX_EC: return launch_ext_one<R, EQ, ND, REC_PC, FLX_EC, TX, TY, TZ, NT>(a, s);
         case FLX_EC4: return launch_ext_one<R, EQ, ND, REC_PC, FLX_EC4, TX, TY, TZ, NT>(a, s);
+        case FLX_TECNO2: return launch_ext_one<R, EQ, ND, REC_PC, FLX_TECNO2, TX, TY, TZ, NT>(a, s);
         case FLX_RUSANOV: return launch_ext_one<R, EQ, ND, REC_ENO2, FLX_RUSANOV, TX, TY, TZ, NT>(a, s);
         case FLX_HLL: return launch_ext_one<R, EQ, ND, REC_ENO2, FLX_HLL, TX, TY, TZ, NT>(a, s);
         default:   // HLLC with ENO2 (Burgers: HLLC is HLL)

@@ -117,7 +117,7 @@ def test_mlmc_level_table_sizes(alsv):
 
 
 @pytest.mark.parametrize("field,value,msg", [
-    ("ndim", 0, "ndim"), ("ndim", 4, "ndim"), ("eq", 7, "eq"), ("recon", 4, "recon"), ("flux", 9, "flux"), ("flux", 7, "flux"),
+    ("ndim", 0, "ndim"), ("ndim", 4, "ndim"), ("eq", 7, "eq"), ("recon", 4, "recon"), ("flux", 9, "flux"), ("flux", 8, "flux"),
     ("rk", 4, "rk"), ("precision", 2, "precision"), ("gamma", 1.0, "gamma"), ("batch", 0, "batch"),
     ("cfl", 0.0, "cfl"), ("weno_eps", -1.0, "weno_eps"),
 ])

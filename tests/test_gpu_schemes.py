@@ -1,5 +1,6 @@
 """GPU parity of the further numerics of Sec. 2.1 - Roe (entropy-fixed), exact Godunov, the two-point
-and fourth-order entropy-conservative fluxes, ENO2 reconstruction - against the FP64 oracle, through
+and fourth-order entropy-conservative fluxes, TECNO2 (the two-point one made entropy stable), ENO2
+reconstruction - against the FP64 oracle, through
 the C ABI: FP64 per cell within 1e-12 relative (near-zero floor as in P1), FP32 within 2e-5
 relative L1, after 1 and 10 steps and over whole shock-tube runs; unsupported combinations are
 rejected at alsv_init_grid."""
@@ -52,7 +53,7 @@ def _check(cfg, g, o, what):
 
 SCHEMES = [("roe", "pc"), ("roe", "mc"), ("roe", "weno3"), ("roe", "eno2"), ("godunov", "pc"), ("godunov", "mc"),
            ("godunov", "weno3"), ("godunov", "eno2"), ("hllc", "eno2"), ("rusanov", "eno2"), ("hll", "eno2"),
-           ("ec", "pc"), ("ec4", "pc")]
+           ("ec", "pc"), ("ec4", "pc"), ("tecno2", "pc")]
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
@@ -73,7 +74,8 @@ def test_euler_1d_2d_vs_oracle(flux, recon, precision):
 
 
 @pytest.mark.parametrize("flux,recon,precision", [("roe", "weno3", "fp64"), ("godunov", "mc", "fp32"),
-                                                  ("ec4", "pc", "fp64"), ("hllc", "eno2", "fp32"), ("ec", "pc", "fp32")])
+                                                  ("ec4", "pc", "fp64"), ("hllc", "eno2", "fp32"), ("ec", "pc", "fp32"),
+                                                  ("tecno2", "pc", "fp64"), ("tecno2", "pc", "fp32")])
 def test_euler_3d_vs_oracle(flux, recon, precision):
     n = (17, 9, 13)
     bc = "periodic" if flux in ("ec", "ec4") else [("periodic", "periodic"), ("outflow", "reflective"), ("periodic", "periodic")]
@@ -86,7 +88,8 @@ def test_euler_3d_vs_oracle(flux, recon, precision):
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("flux,recon", [("roe", "pc"), ("roe", "weno3"), ("godunov", "mc"), ("godunov", "eno2"),
-                                        ("rusanov", "eno2"), ("hll", "eno2"), ("ec", "pc"), ("ec4", "pc")])
+                                        ("rusanov", "eno2"), ("hll", "eno2"), ("ec", "pc"), ("ec4", "pc"),
+                                        ("tecno2", "pc")])
 def test_burgers_1d_vs_oracle(flux, recon, precision):
     cfg = dict(ndim=1, n=(333,), batch=3, eq="burgers", recon=recon, flux=flux, rk="ssprk2", bc="periodic", cfl=0.4,
                precision=precision)
@@ -96,11 +99,11 @@ def test_burgers_1d_vs_oracle(flux, recon, precision):
 
 
 @pytest.mark.parametrize("flux,recon", [("roe", "pc"), ("roe", "mc"), ("hllc", "eno2"), ("ec4", "pc"),
-                                        ("godunov", "mc"), ("godunov", "weno3")])
+                                        ("godunov", "mc"), ("godunov", "weno3"), ("tecno2", "pc")])
 def test_sod_full_run_fp64(flux, recon):
     """Sod to T = 0.2 (1024 cells, the shock-tube configuration's size; EC4 on a smooth periodic
     state instead, which it keeps): the FP64 GPU path evaluates the oracle's operations in the
-    oracle's order, so Roe, ENO2 and EC4 stay within the per-cell rule over the whole run.
+    oracle's order, so Roe, ENO2, EC4 and TECNO2 stay within the per-cell rule over the whole run.
     Godunov's rarefaction branch calls pow, which CUDA and the C library round differently in the
     last bit for some arguments; the MC / WENO3 limiters amplify that over ~900 steps (2.5e-11 in
     67 of 1024 cells measured), so its whole run is held to 1e-12 in relative L1 and 1e-9 per cell,

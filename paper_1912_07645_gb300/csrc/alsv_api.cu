@@ -98,9 +98,38 @@ alsv_status require_ready(alsv_ctx* c, bool need_state = true) {
     return ALSV_OK;
 }
 
+// The level table of the live levels only, for the two-sample schedules (their CTAs map to work
+// items through the levels' pwork0 offsets; sample, element and wave-speed slot offsets stay
+// absolute, so a finished level's work items are simply not launched).
+GridArgs live_level_grid(const GridArgs& g, unsigned live) {
+    GridArgs r = g;
+    int j = 0;
+    long long pw = 0;
+    for (int l = 0; l < g.nlev; ++l) {
+        const long long items = (l + 1 < g.nlev ? g.lev[l + 1].pwork0 : g.total_pwork) - g.lev[l].pwork0;
+        if (!(live & (1u << l))) continue;
+        r.lev[j] = g.lev[l];
+        r.lev[j].pwork0 = pw;
+        pw += items;
+        ++j;
+    }
+    if (j == 0) {   // nothing live: launch nothing
+        r.nlev = 1;
+        r.lev[0] = g.lev[0];
+        r.total_pwork = 0;
+        return r;
+    }
+    r.nlev = j;
+    r.total_pwork = pw;
+    return r;
+}
+
+bool pair_schedule(const alsv_ctx* c) { return !c->fp64 && c->ndim == 2 && c->variant >= 4 && c->variant <= 11; }
+
 StageArgs stage_args(alsv_ctx* c, const void* Us, const void* Un, void* Uout, double a, double b, bool want_speed) {
     StageArgs s;
     s.g = c->g;
+    if (c->live_levels != ~0u && pair_schedule(c)) s.g = live_level_grid(c->g, c->live_levels);
     s.Us = Us;
     s.Un = Un;
     s.Uout = Uout;
@@ -756,6 +785,16 @@ alsv_status alsv_evolve_to_T(alsv_ctx* c, double T, int64_t* steps_taken_host) {
     CK(post(0));
     int cur = 0;
     long long chunks = 0;
+    // every exit restores the full level table (and drops a chunk captured with a reduced one)
+    struct LiveReset {
+        alsv_ctx* c;
+        ~LiveReset() {
+            if (c->live_levels != ~0u) {
+                c->live_levels = ~0u;
+                drop_graph(c);
+            }
+        }
+    } live_reset{c};
     for (;;) {
         if (++chunks > (1LL << 26)) return fail(c, ALSV_ERR_TIMEOUT, "evolve_to_T: step limit reached");
         {
@@ -774,6 +813,21 @@ alsv_status alsv_evolve_to_T(alsv_ctx* c, double T, int64_t* steps_taken_host) {
         bool all = true;
         for (size_t i = 0; i < S && all; ++i) all = dn[i] != 0;
         if (all) break;
+        if (c->g.nlev > 1 && pair_schedule(c)) {
+            // leave out levels whose samples have all finished (done flags never clear during a
+            // run); the captured chunk holds the level table, so a change re-captures it
+            unsigned live = 0;
+            for (int l = 0; l < c->g.nlev; ++l) {
+                const LevelInfo& L = c->g.lev[l];
+                bool any = false;
+                for (int i = 0; i < L.samples && !any; ++i) any = dn[L.sample0 + i] == 0;
+                if (any) live |= 1u << l;
+            }
+            if (live != (c->live_levels & ((1u << c->g.nlev) - 1u))) {
+                c->live_levels = live;
+                drop_graph(c);
+            }
+        }
         cur ^= 1;
     }
     prof_collect(c);

@@ -54,6 +54,9 @@ struct alsv_ctx {
     void* g_U = nullptr;
     int g_variant = -1;
     int g_steps = 0;
+    // levels whose stage work is launched (bit l = level l; all set outside alsv_evolve_to_T): the
+    // two-sample schedules leave out levels whose samples have all finished
+    unsigned live_levels = ~0u;
     bool graphs_enabled = true;
     // host staging
     std::vector<int> h_done;

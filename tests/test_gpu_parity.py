@@ -854,6 +854,42 @@ def test_pair_variant_mlmc_levels_odd_counts(variant):
     S.close()
 
 
+@pytest.mark.parametrize("variant", [8, 11])
+def test_pair_schedule_levels_finishing_apart_equal_single_level_runs(variant):
+    """Levels of one launch finish at different step counts (coarser grids take fewer CFL steps), so
+    alsv_evolve_to_T leaves the finished levels out of the later two-sample stage launches. Each
+    level's samples equal, bitwise and in step count, the same samples evolved alone on a one-level
+    grid."""
+    torch = torch_()
+    import paper_1912_07645_gb300 as alsv
+    lv = [((32, 32), 3), ((64, 64), 2), ((32, 64), 4)]
+    T = 0.3
+    cfg = dict(ndim=2, levels=lv, eq="euler", recon="weno3", flux="hllc", rvars="prim", rk="ssprk3",
+               bc="periodic", cfl=0.4, precision="fp32", seed=9)
+    S = gpu_solver(**cfg)
+    alsv.alsv_set_tile_variant(S.ctx, variant)
+    S.set_initial_data("kh")
+    S.evolve_to(T)
+    t_all, n_all = S.time()
+    th_all = oracle.theta_splitmix(9, 9, 20)
+    s0, last = 0, []
+    for l, (n, B) in enumerate(lv):
+        one = dict(cfg, n=n, batch=B)
+        one.pop("levels")
+        S1 = gpu_solver(**one)
+        alsv.alsv_set_tile_variant(S1.ctx, variant)
+        S1.set_initial_data("kh", theta=torch.from_numpy(th_all[s0:s0 + B]).cuda())
+        S1.evolve_to(T)
+        t1, n1 = S1.time()
+        assert np.array_equal(host(S.state(l)), host(S1.U).reshape(host(S.state(l)).shape)), f"level {l}"
+        assert np.array_equal(n_all[s0:s0 + B], n1) and np.all(t1 == T)
+        last.append(int(n1.max()))
+        S1.close()
+        s0 += B
+    S.close()
+    assert max(last) > min(last) + 32, last   # levels finish more than two 16-step chunks apart
+
+
 # ------------------------------------------------------------------ seeded random configurations
 def _random_configs(count, seed=2026):
     """Seeded draws over the descriptor: dimension, odd and ragged sizes, scheme, variables, RK

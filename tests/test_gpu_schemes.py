@@ -103,11 +103,13 @@ def test_burgers_1d_vs_oracle(flux, recon, precision):
 def test_sod_full_run_fp64(flux, recon):
     """Sod to T = 0.2 (1024 cells, the shock-tube configuration's size; EC4 on a smooth periodic
     state instead, which it keeps): the FP64 GPU path evaluates the oracle's operations in the
-    oracle's order, so Roe, ENO2, EC4 and TECNO2 stay within the per-cell rule over the whole run.
+    oracle's order, so Roe, ENO2 and EC4 stay within the per-cell rule over the whole run.
     Godunov's rarefaction branch calls pow, which CUDA and the C library round differently in the
     last bit for some arguments; the MC / WENO3 limiters amplify that over ~900 steps (2.5e-11 in
-    67 of 1024 cells measured), so its whole run is held to 1e-12 in relative L1 and 1e-9 per cell,
-    its 1- and 10-step runs to the per-cell rule (test_euler_1d_2d_vs_oracle)."""
+    67 of 1024 cells measured). TECNO2's entropy variables call log, with the same last-bit
+    differences, amplified to 9.6e-12 in 19 of 1024 cells over the run. These two whole runs are
+    held to 1e-12 in relative L1 and 1e-9 per cell, their 1- and 10-step runs to the per-cell rule
+    (test_euler_1d_2d_vs_oracle)."""
     cfg = dict(ndim=1, n=(1024,), batch=1, eq="euler", recon=recon, flux=flux, rvars="prim", rk="ssprk2",
                bc="outflow", cfl=0.45, precision="fp64")
     d = oracle.make_desc(**cfg)
@@ -116,12 +118,12 @@ def test_sod_full_run_fp64(flux, recon):
         cfg["bc"] = "periodic"
         U0 = euler_state(1, 1, (1024,), seed=8)
     g, o = _run(cfg, U0, T=0.2)
-    if flux != "godunov":
+    if flux not in ("godunov", "tecno2"):
         p1_check(g, o, what=f"sod {flux}/{recon}")
         return
     for v in range(3):
         assert np.abs(g[:, v] - o[:, v]).sum() <= 1e-12 * np.abs(o[:, v]).sum()
-    p1_check(g, o, rel=1e-9, what=f"sod {flux}/{recon} (pow rounding)")
+    p1_check(g, o, rel=1e-9, what=f"sod {flux}/{recon} (pow / log rounding)")
 
 
 def test_unsupported_combinations_are_rejected():

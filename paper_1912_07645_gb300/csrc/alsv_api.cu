@@ -145,6 +145,7 @@ StageArgs stage_args(alsv_ctx* c, const void* Us, const void* Un, void* Uout, do
     s.want_speed = want_speed ? 1 : 0;
     for (int f = 0; f < 6; ++f) s.halo[f] = c->halo[f];
     s.part = 0;
+    s.done_first = c->any_done;
     return s;
 }
 
@@ -789,8 +790,9 @@ alsv_status alsv_evolve_to_T(alsv_ctx* c, double T, int64_t* steps_taken_host) {
     struct LiveReset {
         alsv_ctx* c;
         ~LiveReset() {
-            if (c->live_levels != ~0u) {
+            if (c->live_levels != ~0u || c->any_done) {
                 c->live_levels = ~0u;
+                c->any_done = 0;
                 drop_graph(c);
             }
         }
@@ -813,6 +815,15 @@ alsv_status alsv_evolve_to_T(alsv_ctx* c, double T, int64_t* steps_taken_host) {
         bool all = true;
         for (size_t i = 0; i < S && all; ++i) all = dn[i] != 0;
         if (all) break;
+        if (!c->any_done && pair_schedule(c)) {
+            // from the first finished sample on, finished pairs skip their tile load
+            bool any = false;
+            for (size_t i = 0; i < S && !any; ++i) any = dn[i] != 0;
+            if (any) {
+                c->any_done = 1;
+                drop_graph(c);
+            }
+        }
         if (c->g.nlev > 1 && pair_schedule(c)) {
             // leave out levels whose samples have all finished (done flags never clear during a
             // run); the captured chunk holds the level table, so a change re-captures it

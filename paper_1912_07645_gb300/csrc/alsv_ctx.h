@@ -57,6 +57,7 @@ struct alsv_ctx {
     // levels whose stage work is launched (bit l = level l; all set outside alsv_evolve_to_T): the
     // two-sample schedules leave out levels whose samples have all finished
     unsigned live_levels = ~0u;
+    int any_done = 0;   // some sample finished (set from the done-flag polls of alsv_evolve_to_T)
     bool graphs_enabled = true;
     // host staging
     std::vector<int> h_done;

@@ -153,6 +153,8 @@ struct StageArgs {
     const void* halo[6];  // face 2k + side with bc HALO: [samples][NV][G][cross] ghost layers
     int part;             // tiles to run: 0 all, 1 those whose stencil reads no halo buffer,
                           // 2 the others (a block's stage split around the halo exchange)
+    int done_first;       // nonzero: some sample has finished; the two-sample schedules then test
+                          // the done flags before the tile load (otherwise under it)
 };
 
 // Tile shape used for a given (precision, ndim); the host derives the tiling from it.

@@ -206,14 +206,14 @@ __global__ void __launch_bounds__(256, TY >= 32 ? 3 : 4) k_stage2d_pair2(const S
     const int sA = HALVES ? (int)q : 2 * (int)q;
     const bool hasB = HALVES ? true : sA + 1 < L.samples;
     const int sB = HALVES ? sA : (hasB ? sA + 1 : sA);
-    // One level (samples that finish within a few steps of each other): the done flags are read
-    // now but acted on after the tile load, so that their round trip overlaps the halo loads
-    // instead of preceding them (a finished pair only wastes a tile read). Several levels (the
-    // coarse ones finish after a fraction of the finest level's steps): a finished pair returns
-    // before any load, as its tile reads would otherwise be repeated in every remaining stage.
+    // While no sample has finished (the host sets done_first from its done-flag polls) the done
+    // flags are read now but acted on after the tile load, so that their round trip overlaps the
+    // halo loads instead of preceding them. Once samples finish (and on grids of several levels,
+    // whose coarse levels finish after a fraction of the finest level's steps), a finished pair
+    // returns before any load, as its tile reads would otherwise repeat in every later stage.
     const bool doneA = p.done[L.sample0 + sA] != 0;
     const bool doneB = hasB ? p.done[L.sample0 + sB] != 0 : true;
-    if (g.nlev > 1 && doneA && doneB) return;   // uniform over the CTA, before any barrier
+    if ((g.nlev > 1 || p.done_first) && doneA && doneB) return;   // uniform over the CTA, before any barrier
 
     const int nx = L.n[0], ny = L.n[1];
     const uint32_t trow = fdiv(tile, L.fd_nt0);

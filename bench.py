@@ -47,7 +47,9 @@ STAGE_KERNEL_NAMES = {0: "k_stage<float, Euler, 2D, WENO3, HLLC, 32x16>",
                       8: "k_stage2d_pair2<WENO3, HLLC, 32x16>",
                       9: "k_stage2d_pair2<WENO3, HLLC, 32x16, reads in flight>",
                       10: "k_stage2d_pair2<WENO3, HLLC, 32x16, sample halves>",
-                      11: "k_stage2d_pair2<WENO3, HLLC, 32x16, sample halves, reads in flight>"}
+                      11: "k_stage2d_pair2<WENO3, HLLC, 32x16, sample halves, reads in flight>",
+                      12: "k_stage2d_pair2<WENO3, HLLC, 32x16, reads in flight, x-fluxes by shuffle>",
+                      13: "k_stage2d_pair2<WENO3, HLLC, 32x16, sample halves, reads in flight, x-fluxes by shuffle>"}
 WORKLOAD = "kh2d_256x256_mc4096_weno3_hllc_ssprk3_fp32_T1"
 # compulsory HBM bytes per 2D SSP-RK3 cell-update in FP32: per variable read U^n + write U1,
 # read U1 + U^n + write U2, read U2 + U^n + write U^{n+1} = 8 words, x 4 variables x 4 bytes
@@ -222,7 +224,7 @@ def stage_traffic(variant, cell_updates, launches):
     rec.update(per_variant[str(variant)], variant=str(variant))
     csrc = os.path.join(ROOT, "paper_1912_07645_gb300", "csrc")
     h = hashlib.sha256()
-    kernel_src = "fv_pair2.cuh" if variant in (8, 9, 10, 11) else "fv_pair.cuh"
+    kernel_src = "fv_pair2.cuh" if variant in (8, 9, 10, 11, 12, 13) else "fv_pair.cuh"
     for f in (kernel_src, "fv_packed.cuh", "fv_physics.cuh"):
         h.update(open(os.path.join(csrc, f), "rb").read())
     if h.hexdigest()[:16] != rec.get("sources_sha256_prefix") or str(variant) != rec.get("variant"):

@@ -424,7 +424,7 @@ alsv_status alsv_structure_function_read(alsv_ctx* ctx, const void* acc_dev, int
  * With every block fed its neighbours' layers of the same stage state and the same maximum, each
  * cell sees exactly the inputs it sees on the whole grid, so the blocks together reproduce the
  * whole-grid run bitwise under the same stage schedule. Every schedule reads halo faces except the
- * FP32 2D column march and two-sample schedules (variants 3-11), which reject them.
+ * FP32 2D column march and two-sample schedules (variants 3-13), which reject them.
  *
  * Halo buffer of face (k, side): [samples][vars][layers][cross], layers = alsv_halo_info's g (1
  * for PC, 2 otherwise), cross = the block's cells across k in (z, y, x) order without k. Layer l
@@ -499,7 +499,9 @@ alsv_status alsv_destroy(alsv_ctx* ctx);
  *                           cell (WENO3 from the differences around an interface, fixed thread
  *                           maps, positivity fallback only where needed; 32x16 tiles; 9 with
  *                           every global read of a phase in flight at once); 10, 11 as 8, 9 on
- *                           the two halves of each sample (ny divisible by 32).
+ *                           the two halves of each sample (ny divisible by 32); 12, 13 as 9, 11
+ *                           with the x-fluxes passed between lanes by warp shuffles, both
+ *                           directions between one pair of barriers (bitwise equal to 8-11).
  *                           FP32 3D: 0, 1 tiles of 16x8x8, 8x8x8; 2, 3 z-marching 32x8 column
  *                           chunks of 64 / 128 planes (Euler); 4 as 2 with the x and y interfaces
  *                           of a plane packed in FP32x2 (primitive, HLLC/Rusanov); 5 as 4 with

@@ -47,7 +47,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 bool variant_ok(const alsv_ctx* c, int v) {
     if (!stage_variant_supported(c->fp64, c->ndim, c->eq, c->d.recon, c->g.rvars, c->d.flux, c->g.bc, v)) return false;
     // halo faces are read by the tile kernels and the 3D z-march (every variant but the FP32 2D
-    // column march and two-sample schedules, 3-11)
+    // column march and two-sample schedules, 3-13)
     if (ctx_has_halo(c) && !c->fp64 && c->ndim == 2 && v >= 3) return false;
     if (stage_variant_halves(c->fp64, c->ndim, v)) {
         // the halves must align with whole tiles: ny divisible by twice the tile height
@@ -124,7 +124,7 @@ GridArgs live_level_grid(const GridArgs& g, unsigned live) {
     return r;
 }
 
-bool pair_schedule(const alsv_ctx* c) { return !c->fp64 && c->ndim == 2 && c->variant >= 4 && c->variant <= 11; }
+bool pair_schedule(const alsv_ctx* c) { return !c->fp64 && c->ndim == 2 && c->variant >= 4 && c->variant <= 13; }
 
 StageArgs stage_args(alsv_ctx* c, const void* Us, const void* Un, void* Uout, double a, double b, bool want_speed) {
     StageArgs s;
@@ -363,7 +363,7 @@ TileShape stage_tile(int fp64, int ndim, int variant) {
         if (variant == 6 && !fp64) return TileShape{32, 16, 1, 256};       // two halves of a sample
         if (variant == 7 && !fp64) return TileShape{32, 8, 1, 256};
 
-        return TileShape{32, 16, 1, 256};                                   // variants 0, 4, 8-11
+        return TileShape{32, 16, 1, 256};                                   // variants 0, 4, 8-13
     }
     if (fp64) return variant == 1 ? TileShape{8, 8, 4, 256} : TileShape{8, 8, 8, 256};
     if (variant == 2) return TileShape{32, 8, 64, 256};    // z-marching column chunks
@@ -375,11 +375,11 @@ TileShape stage_tile(int fp64, int ndim, int variant) {
     return variant == 1 ? TileShape{8, 8, 8, 256} : TileShape{16, 8, 8, 256};
 }
 bool stage_variant_halves(int fp64, int ndim, int variant) {
-    return ndim == 2 && !fp64 && (variant == 6 || variant == 7 || variant == 10 || variant == 11);
+    return ndim == 2 && !fp64 && (variant == 6 || variant == 7 || variant == 10 || variant == 11 || variant == 13);
 }
 int stage_num_variants(int fp64, int ndim) {
     if (ndim == 1) return 3;
-    if (ndim == 2 && !fp64) return 12;
+    if (ndim == 2 && !fp64) return 14;
     if (ndim == 3 && !fp64) return 8;
     return 2;
 }
@@ -388,9 +388,9 @@ bool stage_variant_supported(int fp64, int ndim, int eq, int recon, int rvars, i
     // ENO2 and the Roe / Godunov / entropy-conservative fluxes: the default tile schedule
     if (ext_scheme(recon, flux))
         return variant == 0 && (eq == EQ_EULER ? rvars == RV_PRIM : ndim == 1);
-    if (ndim == 2 && !fp64 && (variant == 4 || variant == 5 || variant == 8 || variant == 9))
+    if (ndim == 2 && !fp64 && (variant == 4 || variant == 5 || variant == 8 || variant == 9 || variant == 12))
         return eq == EQ_EULER && rvars == RV_PRIM && (flux == FLX_HLLC || flux == FLX_RUSANOV);
-    if (ndim == 2 && !fp64 && (variant == 6 || variant == 7 || variant == 10 || variant == 11))
+    if (ndim == 2 && !fp64 && (variant == 6 || variant == 7 || variant == 10 || variant == 11 || variant == 13))
         return eq == EQ_EULER && rvars == RV_PRIM && (flux == FLX_HLLC || flux == FLX_RUSANOV) &&
                bc[1][0] == BC_PERIODIC && bc[1][1] == BC_PERIODIC;
     if (ndim == 3 && !fp64 && (variant == 4 || variant == 5 || variant == 6 || variant == 7))

@@ -18,14 +18,15 @@
 
 namespace alsv {
 
-template <int RECON, int TY>
+template <int RECON, int TY, int XSHFL = 0>
 constexpr size_t pair2_smem_bytes() {
     constexpr int TX = 32;
     constexpr int G = RECON == REC_PC ? 1 : 2;
     constexpr int NS = (TX + 2 * G) * (TY + 2 * G);
     constexpr int NIX = (TX + 1) * TY, NIY = TX * (TY + 1);
     constexpr int NI = NIX > NIY ? NIX : NIY;
-    return (size_t)32 * (NS + NI);
+    // XSHFL: the right-edge x-fluxes and lane 31's left-face x-fluxes, two float4 per row each
+    return (size_t)32 * (NS + NI) + (XSHFL ? (size_t)64 * TY : 0);
 }
 
 __device__ __forceinline__ float2 lo2(float4 a) { return make_float2(a.x, a.y); }
@@ -176,8 +177,14 @@ __device__ __forceinline__ void load_sten(const float4* sW0, const float4* sW1, 
 // TY rows per tile (16: 4 CTAs per SM with 64 registers; 32: 3 CTAs with 80); 256 threads = 8
 // warps; lane = column, warp = row group. HALVES as in k_stage2d_pair. PREF: every global read of
 // the tile load in flight at once (one round trip instead of two), and the epilogue's reads of
-// all the thread's cells issued before its first store.
-template <int RECON, int FLUX, int TY, int HALVES = 0, int PREF = 0>
+// all the thread's cells issued before its first store. XSHFL: each lane evaluates the x-interface
+// at the left face of its cells and takes the right face's flux from lane + 1 by a warp shuffle,
+// so the x-fluxes never pass through shared memory; the tile's right-edge x-interfaces (evaluated
+// by one half-warp) and lane 31's own left-face fluxes go through two small shared arrays, and
+// lane 31 adds its x part after the one barrier that also completes the y-fluxes. Both directions
+// thus share one phase between two barriers (instead of four barriers), with the same operations
+// per cell in the same order (bitwise equal to XSHFL = 0).
+template <int RECON, int FLUX, int TY, int HALVES = 0, int PREF = 0, int XSHFL = 0>
 __global__ void __launch_bounds__(256, TY >= 32 ? 3 : 4) k_stage2d_pair2(const StageArgs p) {
     constexpr int TX = 32, NT = 256, NW = 8;
     constexpr int G = RECON == REC_PC ? 1 : 2;
@@ -191,6 +198,8 @@ __global__ void __launch_bounds__(256, TY >= 32 ? 3 : 4) k_stage2d_pair2(const S
     float4* sW1 = sW0 + NS;                              // [NS] (v, p)
     float4* sF0 = sW1 + NS;                              // [NI] (mass, x-momentum) fluxes
     float4* sF1 = sF0 + NI;                              // [NI] (y-momentum, energy)
+    float4* sXL = sF1 + NI;                              // XSHFL: [2][TY] lane 31's left-face x-fluxes
+    float4* sXE = sXL + 2 * TY;                          // XSHFL: [2][TY] right-edge x-fluxes
 
     const GridArgs& g = p.g;
     const uint32_t w = blockIdx.x;
@@ -356,12 +365,71 @@ __global__ void __launch_bounds__(256, TY >= 32 ? 3 : 4) k_stage2d_pair2(const S
             acc[m][3] = fma2(sub2(hi2(bp), hi2(bm)), nid, acc[m][3]);
         }
     };
+    if constexpr (XSHFL) {
+        static_assert(!XSHFL || TY <= 32, "edge rows fit one warp");
+        __syncthreads();
+        // y first (its fluxes go to shared memory), so that the x part of acc, which the x pass
+        // forms directly, is live only from the x pass on
+        flux_pass(1);
+        // x: the left-face interface of each of the thread's cells; the right face from lane + 1
+        {
+            const float2 eps = f2(L.eps_f[0]);
+            const float2 nid = f2(-L.inv_dx_f[0]);
+#pragma unroll   // acc[m] is written here: a runtime m would move acc to local memory
+            for (int m = 0; m < CPT; ++m) {
+                const int fy = warp + NW * m;
+                const int i0 = (fy + G) * SX + lane - 1 + G;
+                Sten2 S;
+                load_sten<RECON, 0>(sW0, sW1, i0, 1, eps, S);
+                const F2x4 F = interface_flux2<RECON, FLUX>(S, gamma, inv_gm1, 0xffffffffu);
+                // variables (mass, x-momentum, y-momentum, energy) = (r, n, t, p) along x
+                auto down = [](float2 a) {
+                    return make_float2(__shfl_down_sync(0xffffffffu, a.x, 1), __shfl_down_sync(0xffffffffu, a.y, 1));
+                };
+                const float2 nr = down(F.r), nn = down(F.n), nt = down(F.t), np = down(F.p);
+                if (lane < 31) {
+                    acc[m][0] = fma2(sub2(nr, F.r), nid, acc[m][0]);
+                    acc[m][1] = fma2(sub2(nn, F.n), nid, acc[m][1]);
+                    acc[m][2] = fma2(sub2(nt, F.t), nid, acc[m][2]);
+                    acc[m][3] = fma2(sub2(np, F.p), nid, acc[m][3]);
+                } else {
+                    sXL[fy] = make_float4(F.r.x, F.r.y, F.n.x, F.n.y);
+                    sXL[TY + fy] = make_float4(F.t.x, F.t.y, F.p.x, F.p.y);
+                }
+            }
+            // the tile's right-edge x-interfaces: warp NW - 2, lane = row
+            if (warp == NW - 2 && lane < TY) {
+                const int i0 = (lane + G) * SX + TX - 1 + G;
+                Sten2 S;
+                load_sten<RECON, 0>(sW0, sW1, i0, 1, eps, S);
+                const unsigned mask = TY >= 32 ? 0xffffffffu : ((1u << TY) - 1u);
+                const F2x4 F = interface_flux2<RECON, FLUX>(S, gamma, inv_gm1, mask);
+                sXE[lane] = make_float4(F.r.x, F.r.y, F.n.x, F.n.y);
+                sXE[TY + lane] = make_float4(F.t.x, F.t.y, F.p.x, F.p.y);
+            }
+        }
+        __syncthreads();
+        if (lane == 31) {
+            const float2 nid = f2(-L.inv_dx_f[0]);
 #pragma unroll
-    for (int D = 0; D < 2; ++D) {
-        __syncthreads();
-        flux_pass(D);
-        __syncthreads();
-        divergence(D);
+            for (int m = 0; m < CPT; ++m) {
+                const int fy = warp + NW * m;
+                const float4 am = sXL[fy], bm = sXL[TY + fy], ap = sXE[fy], bp = sXE[TY + fy];
+                acc[m][0] = fma2(sub2(lo2(ap), lo2(am)), nid, acc[m][0]);
+                acc[m][1] = fma2(sub2(hi2(ap), hi2(am)), nid, acc[m][1]);
+                acc[m][2] = fma2(sub2(lo2(bp), lo2(bm)), nid, acc[m][2]);
+                acc[m][3] = fma2(sub2(hi2(bp), hi2(bm)), nid, acc[m][3]);
+            }
+        }
+        divergence(1);
+    } else {
+#pragma unroll
+        for (int D = 0; D < 2; ++D) {
+            __syncthreads();
+            flux_pass(D);
+            __syncthreads();
+            divergence(D);
+        }
     }
 
     // ---- 3. RK combination, store per sample, CFL speed of the new states

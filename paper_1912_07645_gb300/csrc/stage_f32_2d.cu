@@ -77,7 +77,7 @@ cudaError_t launch_speed_f32_2d(int variant, int eq, const GridArgs& g, const vo
         case 5: return launch_speed_tile<float, 2, 32, 8, 1, 256>(eq, g, U, part, s);
         case 6: return launch_speed_tile<float, 2, 32, 16, 1, 256>(eq, g, U, part, s);
         case 7: return launch_speed_tile<float, 2, 32, 8, 1, 256>(eq, g, U, part, s);
-        case 8: case 9: case 10: case 11: return launch_speed_tile<float, 2, 32, 16, 1, 256>(eq, g, U, part, s);
+        case 8: case 9: case 10: case 11: case 12: case 13: return launch_speed_tile<float, 2, 32, 16, 1, 256>(eq, g, U, part, s);
         default: return cudaErrorInvalidValue;
     }
 }

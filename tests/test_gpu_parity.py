@@ -545,7 +545,7 @@ def test_welford_statistics_match_oracle(precision):
 
 
 # ------------------------------------------------------------------ full-size batched configuration, sampled
-@pytest.mark.parametrize("variant", [4, 8, 9])
+@pytest.mark.parametrize("variant", [4, 8, 9, 13])
 def test_full_size_batched_kh_sampled(variant):
     """256^2 x 4096 samples, FP32 WENO3 + HLLC + SSP-RK3 (the benchmark workload), in the launch
     geometry of each two-sample schedule the autotuner picks from for it; three sampled samples
@@ -705,12 +705,12 @@ def test_column_variant_mlmc_levels_and_rejection():
     S2.close()
 
 
-@pytest.mark.parametrize("variant", [4, 5, 8, 9])
+@pytest.mark.parametrize("variant", [4, 5, 8, 9, 12])
 @pytest.mark.parametrize("recon,flux,bc", [("weno3", "hllc", "periodic"), ("mc", "rusanov", "periodic"),
                                            ("pc", "hllc", [("outflow", "reflective"), ("reflective", "outflow")]),
                                            ("weno3", "rusanov", "reflective")])
 def test_pair_variant_fp32_vs_oracle(variant, recon, flux, bc):
-    """Two-sample schedules (variants 4, 5 and the lean 8, 9): each sample within 2e-5 relative L1
+    """Two-sample schedules (variants 4, 5 and the lean 8, 9, 12): each sample within 2e-5 relative L1
     of the oracle, with an odd batch (the last sample has no partner), ragged tiles and boundary
     fill."""
     torch = torch_()
@@ -762,9 +762,10 @@ def test_halves_variant_fp32_vs_oracle_and_bitwise_with_sample_pairs(recon, flux
                                             ("pc", "hllc", "reflective"), ("weno3", "rusanov", "reflective")])
 def test_lean_pair_variants_bitwise_equal_and_vs_oracle(recon, flux, bcx):
     """The lean two-sample schedules evaluate every interface with the same operations whatever
-    the order of the reads or the pairing: sample pairs (8, 9) and the two halves of each sample
-    (10, 11) are bitwise equal (ragged x: 70 cells, ny = 64, odd batch), and within 2e-5 relative
-    L1 of the oracle."""
+    the order of the reads, the barrier structure or the pairing: sample pairs (8, 9, 12) and the
+    two halves of each sample (10, 11, 13; 12 and 13 pass the x-fluxes by warp shuffles) are
+    bitwise equal (ragged x: 70 cells, ny = 64, odd batch), and within 2e-5 relative L1 of the
+    oracle."""
     torch = torch_()
     import paper_1912_07645_gb300 as alsv
     bc = [(bcx, bcx), ("periodic", "periodic")]
@@ -772,7 +773,7 @@ def test_lean_pair_variants_bitwise_equal_and_vs_oracle(recon, flux, bcx):
                cfl=0.4, precision="fp32")
     U0 = euler_state(3, 2, (70, 64), seed=74)
     out = {}
-    for v in (8, 9, 10, 11):
+    for v in (8, 9, 10, 11, 12, 13):
         S = gpu_solver(**cfg)
         alsv.alsv_set_tile_variant(S.ctx, v)
         S.set_state(torch.from_numpy(U0))
@@ -780,7 +781,7 @@ def test_lean_pair_variants_bitwise_equal_and_vs_oracle(recon, flux, bcx):
         S.sync()
         out[v] = (host(S.U).reshape(S.level_shape(0)), S.time())
         S.close()
-    for v in (9, 10, 11):
+    for v in (9, 10, 11, 12, 13):
         assert np.array_equal(out[8][0], out[v][0]), v
         np.testing.assert_array_equal(out[8][1][0], out[v][1][0])
     o, *_ = run_oracle(cfg, U0=U0, steps=10)
@@ -794,14 +795,14 @@ def test_halves_variant_needs_aligned_periodic_y():
     for n, bc in (((64, 40), "periodic"), ((64, 64), [("periodic", "periodic"), ("outflow", "outflow")])):
         S = gpu_solver(ndim=2, n=n, batch=1, eq="euler", recon="weno3", flux="hllc", rvars="prim", precision="fp32",
                        bc=bc)
-        for v in (6, 7, 10, 11):
+        for v in (6, 7, 10, 11, 13):
             with pytest.raises(alsv.AlsvError, match="does not support"):
                 alsv.alsv_set_tile_variant(S.ctx, v)
         S.close()
     S = gpu_solver(ndim=2, n=(64, 48), batch=1, eq="euler", recon="weno3", flux="hllc", rvars="prim",
                    precision="fp32", bc="periodic")
     alsv.alsv_set_tile_variant(S.ctx, 7)      # 48 = 3 x 16: 32x8 halves align
-    for v in (10, 11):                        # 32x16 halves need ny divisible by 32
+    for v in (10, 11, 13):                    # 32x16 halves need ny divisible by 32
         with pytest.raises(alsv.AlsvError, match="does not support"):
             alsv.alsv_set_tile_variant(S.ctx, v)
     S.close()
@@ -854,7 +855,7 @@ def test_pair_variant_mlmc_levels_odd_counts(variant):
     S.close()
 
 
-@pytest.mark.parametrize("variant", [8, 11])
+@pytest.mark.parametrize("variant", [8, 11, 13])
 def test_pair_schedule_levels_finishing_apart_equal_single_level_runs(variant):
     """Levels of one launch finish at different step counts (coarser grids take fewer CFL steps), so
     alsv_evolve_to_T leaves the finished levels out of the later two-sample stage launches. Each

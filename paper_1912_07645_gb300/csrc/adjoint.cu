@@ -90,24 +90,22 @@ __device__ __forceinline__ void rusanov_vjp(const R* WL, const R* WR, const R* F
     Wb[0] += ab * (-c / (R(2) * W[0]));
 }
 
-// MC slope selection: 0 -> zero, 1 -> 2 D-, 2 -> (D- + D+)/2, 3 -> 2 D+ (same tie rules as the
-// forward minmod); returns d(slope)/d(wm, w0, wp) in g[3].
-template <class R> __device__ __forceinline__ void mc_slope_grad(R wm, R w0, R wp, R* g) {
+// The MC slope of the forward face (the value of mc_slope, bit for bit: the same operations) and
+// the candidate it took: 0 -> zero, 1 -> 2 D-, 2 -> (D- + D+)/2, 3 -> 2 D+. minmod returns one of
+// its arguments unchanged, and among equal candidates the first, so the first candidate equal to
+// a nonzero slope is the one taken (minmod's tie rules).
+template <class R> __device__ __forceinline__ R mc_slope_sel(R wm, R w0, R wp, unsigned& sel) {
     const R dm = w0 - wm, dp = wp - w0;
     const R A = R(2) * dm, B = R(0.5) * (dm + dp), C = R(2) * dp;
-    int sel = 0;
-    if (A > R(0) && B > R(0) && C > R(0)) {
-        int s1 = B < A ? 2 : 1;
-        const R m1 = B < A ? B : A;
-        sel = C < m1 ? 3 : s1;
-    } else if (A < R(0) && B < R(0) && C < R(0)) {
-        int s1 = B > A ? 2 : 1;
-        const R m1 = B > A ? B : A;
-        sel = C > m1 ? 3 : s1;
-    }
-    g[0] = sel == 1 ? R(-2) : (sel == 2 ? R(-0.5) : R(0));
-    g[1] = sel == 1 ? R(2) : (sel == 3 ? R(-2) : R(0));
-    g[2] = sel == 2 ? R(0.5) : (sel == 3 ? R(2) : R(0));
+    const R s = minmod3(A, B, C);
+    sel = s == R(0) ? 0u : (s == A ? 1u : (s == B ? 2u : 3u));
+    return s;
+}
+// d(slope)/d(wm, w0, wp) of the candidate sel
+template <class R> __device__ __forceinline__ void mc_sel_grad(unsigned sel, R* g) {
+    g[0] = sel == 1u ? R(-2) : (sel == 2u ? R(-0.5) : R(0));
+    g[1] = sel == 1u ? R(2) : (sel == 3u ? R(-2) : R(0));
+    g[2] = sel == 2u ? R(0.5) : (sel == 3u ? R(2) : R(0));
 }
 
 struct AdjStageArgs {
@@ -226,12 +224,15 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 4 : 2) k_stage_adj(const 
             constexpr int KL = PC ? 0 : 1, KR = PC ? 1 : 2;   // stencil slots of cells j, j+1
             // forward face states
             R fL[NV], fR[NV];
+            unsigned selbits = 0;   // the MC candidate of each face, 2 bits per (variable, face)
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
                 if (PC) { fL[v] = w[0][v]; fR[v] = w[1][v]; }
                 else {
-                    fL[v] = w[1][v] + R(0.5) * mc_slope(w[0][v], w[1][v], w[2][v]);
-                    fR[v] = w[2][v] - R(0.5) * mc_slope(w[1][v], w[2][v], w[3][v]);
+                    unsigned sl, sr;
+                    fL[v] = w[1][v] + R(0.5) * mc_slope_sel(w[0][v], w[1][v], w[2][v], sl);
+                    fR[v] = w[2][v] - R(0.5) * mc_slope_sel(w[1][v], w[2][v], w[3][v], sr);
+                    selbits |= (sl | (sr << 2)) << (4 * v);
                 }
             }
             R WL[NV], WR[NV], cw[2][NV];
@@ -285,11 +286,11 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 4 : 2) k_stage_adj(const 
                     cb[1][v] += gR[v];
                 } else {
                     R sg[3];
-                    mc_slope_grad(w[0][v], w[1][v], w[2][v], sg);   // fL = w1 + s/2
+                    mc_sel_grad<R>((selbits >> (4 * v)) & 3u, sg);        // fL = w1 + s/2
                     cb[0][v] += gL[v] * R(0.5) * sg[0];
                     cb[1][v] += gL[v] * (R(1) + R(0.5) * sg[1]);
                     cb[2][v] += gL[v] * R(0.5) * sg[2];
-                    mc_slope_grad(w[1][v], w[2][v], w[3][v], sg);   // fR = w2 - s/2
+                    mc_sel_grad<R>((selbits >> (4 * v + 2)) & 3u, sg);    // fR = w2 - s/2
                     cb[1][v] += gR[v] * R(-0.5) * sg[0];
                     cb[2][v] += gR[v] * (R(1) - R(0.5) * sg[1]);
                     cb[3][v] += gR[v] * R(-0.5) * sg[2];

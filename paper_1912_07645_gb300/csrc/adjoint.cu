@@ -23,7 +23,9 @@ namespace alsv {
 // ---------------------------------------------------------------------------------------------
 // W = prim(U): Ubar += (dW/dU)^T Wbar
 template <class R> __device__ __forceinline__ void prim_vjp(const R* U, const R* Wb, R* Ub, R gm1) {
-    const R inv = R(1) / U[0];
+    R inv;
+    if constexpr (IsExact<R>::value) inv = R(1) / U[0];
+    else inv = rcp_approx(U[0]);   // FP32: the forward's own fast reciprocal
     const R u = U[1] * inv, v = U[2] * inv;
     Ub[0] += Wb[0] - Wb[1] * u * inv - Wb[2] * v * inv + Wb[3] * gm1 * R(0.5) * (u * u + v * v);
     Ub[1] += Wb[1] * inv - Wb[3] * gm1 * u;
@@ -86,8 +88,14 @@ __device__ __forceinline__ void rusanov_vjp(const R* WL, const R* WR, const R* F
     R* Wb = pickR ? WRb : WLb;
     const R c = pickR ? cR : cL;
     Wb[N] += ab * (W[N] < R(0) ? R(-1) : R(1));
-    Wb[3] += ab * gamma / (R(2) * W[0] * c);
-    Wb[0] += ab * (-c / (R(2) * W[0]));
+    if constexpr (IsExact<R>::value) {
+        Wb[3] += ab * gamma / (R(2) * W[0] * c);
+        Wb[0] += ab * (-c / (R(2) * W[0]));
+    } else {   // FP32: reciprocals instead of two divisions
+        const R i2w = rcp_approx(R(2) * W[0]);
+        Wb[3] += ab * gamma * i2w * rcp_approx(c);
+        Wb[0] += ab * (-c * i2w);
+    }
 }
 
 // The MC slope of the forward face (the value of mc_slope, bit for bit: the same operations) and

@@ -479,20 +479,22 @@ __global__ void __launch_bounds__(NT) k_stage(const StageArgs p) {
     }
     if (want_speed) {
         // fixed-pattern CTA reduction (max is exact; the pattern is fixed anyway)
-        __shared__ double red[NT / 32];
+        // in R: the maximum of FP32 values converted to double equals the converted maximum, so
+        // FP32 kernels keep this reduction off the FP64 pipe
+        __shared__ R red[NT / 32];
         __shared__ int redbad[NT / 32];
-        double sm = (double)smax;
+        R sm = smax;
         int bd = bad ? 1 : 0;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            const double other = __shfl_xor_sync(0xffffffffu, sm, o);
+            const R other = __shfl_xor_sync(0xffffffffu, sm, o);
             sm = other > sm ? other : sm;
             bd |= __shfl_xor_sync(0xffffffffu, bd, o);
         }
         if ((tid & 31) == 0) { red[tid >> 5] = sm; redbad[tid >> 5] = bd; }
         __syncthreads();
         if (tid == 0) {
-            double r = red[0];
+            R r = red[0];
             int rb = redbad[0];
             for (int k = 1; k < NT / 32; ++k) { r = red[k] > r ? red[k] : r; rb |= redbad[k]; }
             p.speed_part[w] = rb ? __longlong_as_double(0x7fffffffffffffffLL) : r;
@@ -553,20 +555,20 @@ __global__ void __launch_bounds__(NT) k_speed(const GridArgs g, const void* Uv, 
             }
         }
     }
-    __shared__ double red[NT / 32];
+    __shared__ R red[NT / 32];   // in R: see k_stage's reduction
     __shared__ int redbad[NT / 32];
-    double sm = (double)smax;
+    R sm = smax;
     int bd = bad ? 1 : 0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        const double other = __shfl_xor_sync(0xffffffffu, sm, o);
+        const R other = __shfl_xor_sync(0xffffffffu, sm, o);
         sm = other > sm ? other : sm;
         bd |= __shfl_xor_sync(0xffffffffu, bd, o);
     }
     if ((tid & 31) == 0) { red[tid >> 5] = sm; redbad[tid >> 5] = bd; }
     __syncthreads();
     if (tid == 0) {
-        double r = red[0];
+        R r = red[0];
         int rb = redbad[0];
         for (int k = 1; k < NT / 32; ++k) { r = red[k] > r ? red[k] : r; rb |= redbad[k]; }
         part[w] = rb ? __longlong_as_double(0x7fffffffffffffffLL) : r;

@@ -41,6 +41,14 @@ CASES = [
                              flux="hllc", rk="ssprk3", bc=[("periodic", "periodic"), ("outflow", "outflow"),
                                                            ("periodic", "periodic")], cfl=0.3,
                              precision="fp32", seed=8), "kh", (1, 2, 2), 0.06),
+    # cell-value fluxes over four cells (ghost width 2) through the halo faces
+    ("kh2d_fp64_tecno2_2x2", dict(ndim=2, n=(48, 40), batch=2, eq="euler", flux="tecno2", rvars="prim",
+                                  rk="ssprk3", bc=[("periodic", "periodic"), ("reflective", "outflow")], cfl=0.4,
+                                  precision="fp64", seed=10), "kh", (2, 2), 0.03),
+    ("kh2d_fp32_ec4_x3", dict(ndim=2, n=(60, 32), batch=2, eq="euler", flux="ec4", rvars="prim", rk="ssprk3",
+                              bc="periodic", cfl=0.4, precision="fp32", seed=11), "kh", (3, 1), 0.02),
+    ("burgers_fp64_tecno2_x3", dict(ndim=1, n=(90,), batch=2, eq="burgers", flux="tecno2", rk="ssprk2",
+                                    bc="periodic", cfl=0.45, precision="fp64"), "burgers_sine", (3,), 0.1),
 ]
 
 

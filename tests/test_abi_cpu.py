@@ -292,3 +292,27 @@ def test_statistics_calls_without_a_state_report_not_ready(alsv):
             assert ei.value.status_name in ("ERR_NOT_READY", "ERR_INVALID_ARG")
     finally:
         alsv.alsv_destroy(ctx)
+
+
+def test_python_name_maps_match_the_header_enums():
+    """Every name the binding maps to an integer (equation, reconstruction, variables, flux, RK
+    order, boundary, precision, initial data, observable, sampler, stage part) has the value of the
+    header's enum constant of that name."""
+    from paper_1912_07645_gb300 import _abi
+    hdr = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "alsv.h")).read()
+    consts = {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(ALSV_[A-Z0-9_]+)\s*=\s*(-?\d+)", hdr)}
+    groups = [(_abi.EQ, "ALSV_EQ_"), (_abi.RECON, "ALSV_RECON_"), (_abi.RVARS, "ALSV_VARS_"), (_abi.FLUX, "ALSV_FLUX_"),
+              (_abi.BC, "ALSV_BC_"), (_abi.SAMPLER, "ALSV_SAMPLER_"), (_abi.PART, "ALSV_PART_")]
+    for table, prefix in groups:
+        for name, value in table.items():
+            assert consts[prefix + name.upper()] == value, (prefix, name)
+    assert {"ssprk2": consts["ALSV_RK_SSP2"], "ssprk3": consts["ALSV_RK_SSP3"]} == _abi.RK
+    assert {"fp32": consts["ALSV_FP32"], "fp64": consts["ALSV_FP64"]} == _abi.PRECISION
+    assert {"ke": consts["ALSV_OBS_KINETIC_ENERGY"], "mixing": consts["ALSV_OBS_MIXING_WIDTH"]} == _abi.OBSERVABLE
+    for name, value in _abi.INIT.items():
+        assert consts["ALSV_INIT_" + name.upper()] == value, name
+    # every header flux and reconstruction has a name in the binding (and the oracle)
+    for prefix, table in (("ALSV_FLUX_", _abi.FLUX), ("ALSV_RECON_", _abi.RECON)):
+        assert sorted(v for k, v in consts.items() if k.startswith(prefix)) == sorted(table.values()), prefix
+    import oracle
+    assert oracle.FLUX == _abi.FLUX and oracle.RECON == _abi.RECON
